@@ -1,0 +1,404 @@
+"""Plain FP64 CPU oracle of piCholesky k-fold cross-validation.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this module.  It shares no code
+with the CUDA library (``paper_1404_0466_gb300``) and never imports it; inputs
+reach both sides only through the seeded generators in
+``paper_1404_0466_gb300.synth``, which the callers pass in as arrays.
+
+The steps follow the paper's method in its own order (Kuang, Gittens, Hamid,
+arXiv 1404.0466):
+
+1. k folds of contiguous rows (Sec. 1: k-fold cross-validation; the split
+   itself is not specified, contiguous floor boundaries are used).
+2. Training Hessian and right-hand side per fold, H_f = X_tr^T X_tr and
+   B_f = X_tr^T Y_tr (Sec. 3.1, Eq. 2), by direct sums over the kept rows.
+3. A grid of q log-spaced lambdas, scaled by tau = tr(X^T X) / d of the full
+   data so one grid is shared by all folds (Sec. 6.3 uses a fixed range; the
+   scale makes the range dimensionless).
+4. g sampled lambdas at evenly spaced grid indices including both ends
+   (Sec. 6.3: "sparsely sample 4 lambda values from those 31").
+5. Exact Cholesky factors at the sampled lambdas (Algorithm 1, step 1).
+6. Target matrix T (g x D) of vectorised lower triangles (Algorithm 1, step 2;
+   Sec. 5: any ordering gives the same coefficients entrywise).
+7. Observation matrix V (g x (r+1)) of a polynomial basis at the sampled
+   lambdas (Algorithm 1, steps 3-4; monomials, or Chebyshev polynomials which
+   Sec. 3.3 names as the more stable choice).
+8. Theta = argmin ||T - V Theta||_F (Algorithm 1, steps 5-6) by Householder QR.
+9. For each of the q lambdas: interpolated factor L_t = sum_m phi_m(lambda_t)
+   Theta_m (Sec. 3.3, last paragraph), forward and back substitution for the c
+   right-hand sides (Sec. 3.2), hold-out mean squared error.
+10. Mean over folds, argmin over the grid (Sec. 3.1).
+
+Exact cross-validation (``Chol`` of Sec. 6.2) is the same with the exact factor
+at every lambda.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import pathlib
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = pathlib.Path(__file__).resolve().parent
+_SRC = _HERE / "pichol_oracle.c"
+_BUILD = _HERE / "_build"
+_SO = _BUILD / "liboracle.so"
+_lib = None
+
+BASIS_MONO = "mono"          # phi_m(lambda) = (lambda / lambda_s_max)^m      (Algorithm 1)
+BASIS_CHEB_LOG = "cheb_log"  # phi_m(lambda) = T_m(u), u affine in log lambda  (Sec. 3.3)
+
+
+class NotSPD(RuntimeError):
+    """Cholesky met a non-positive pivot (Sec. 3.2 needs H + lambda I > 0)."""
+
+    def __init__(self, pivot: int):
+        super().__init__(f"matrix not positive definite at pivot {pivot}")
+        self.pivot = pivot
+
+
+def build(force: bool = False) -> pathlib.Path:
+    """Compile the C part of the oracle with gcc (plain -O2, IEEE arithmetic)."""
+    _BUILD.mkdir(exist_ok=True)
+    if force or not _SO.exists() or _SO.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _BUILD / f"liboracle.{os.getpid()}.so"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp",
+                               "-o", str(tmp), str(_SRC), "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _get():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(str(build()))
+        i64, dp = ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+        lib.orc_normal_blocks.argtypes = [i64, i64, i64, dp, dp, i64, i64, dp, dp]
+        lib.orc_normal_blocks.restype = None
+        lib.orc_cholesky.argtypes = [i64, dp, dp]
+        lib.orc_cholesky.restype = i64
+        lib.orc_forward.argtypes = [i64, i64, dp, dp, dp]
+        lib.orc_forward.restype = None
+        lib.orc_backward.argtypes = [i64, i64, dp, dp, dp]
+        lib.orc_backward.restype = None
+        lib.orc_holdout_sse.argtypes = [i64, i64, i64, dp, dp, dp]
+        lib.orc_holdout_sse.restype = ctypes.c_double
+        lib.orc_lstsq_householder.argtypes = [i64, i64, dp, i64, dp, dp]
+        lib.orc_lstsq_householder.restype = ctypes.c_int
+        lib.orc_vec_lower.argtypes = [i64, dp, dp]
+        lib.orc_vec_lower.restype = None
+        lib.orc_unvec_lower.argtypes = [i64, dp, dp]
+        lib.orc_unvec_lower.restype = None
+        lib.orc_eval_poly.argtypes = [i64, i64, dp, dp, dp]
+        lib.orc_eval_poly.restype = None
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ----------------------------------------------------------------------------
+# primitives (thin wrappers over the C loops)
+# ----------------------------------------------------------------------------
+
+def normal_blocks(X, Y, skip0: int = 0, skip1: int = 0):
+    """H = X_kept^T X_kept, B = X_kept^T Y_kept, rows [skip0, skip1) left out (Eq. 2)."""
+    X, Y = _f64(X), _f64(Y)
+    n, d = X.shape
+    c = Y.shape[1]
+    H = np.empty((d, d))
+    B = np.empty((d, c))
+    _get().orc_normal_blocks(n, d, c, _p(X), _p(Y), skip0, skip1, _p(H), _p(B))
+    return H, B
+
+
+def cholesky(A) -> np.ndarray:
+    """Lower Cholesky factor of A (Sec. 3.2); raises NotSPD on a non-positive pivot."""
+    A = _f64(A)
+    d = A.shape[0]
+    L = np.empty((d, d))
+    piv = _get().orc_cholesky(d, _p(A), _p(L))
+    if piv >= 0:
+        raise NotSPD(int(piv))
+    return L
+
+
+def forward(L, B) -> np.ndarray:
+    """Z with L Z = B (Sec. 3.2)."""
+    L, B = _f64(L), _f64(B)
+    d, c = B.shape
+    Z = np.empty((d, c))
+    _get().orc_forward(d, c, _p(L), _p(B), _p(Z))
+    return Z
+
+
+def backward(L, Z) -> np.ndarray:
+    """W with L^T W = Z (Sec. 3.2)."""
+    L, Z = _f64(L), _f64(Z)
+    d, c = Z.shape
+    W = np.empty((d, c))
+    _get().orc_backward(d, c, _p(L), _p(Z), _p(W))
+    return W
+
+
+def solve_factored(L, B) -> np.ndarray:
+    """W = (L L^T)^{-1} B by forward then back substitution (Sec. 3.2)."""
+    return backward(L, forward(L, B))
+
+
+def holdout_sse(Xv, Yv, W) -> float:
+    """||Y_v - X_v W||_F^2 evaluated directly."""
+    Xv, Yv, W = _f64(Xv), _f64(Yv), _f64(W)
+    nv, d = Xv.shape
+    return float(_get().orc_holdout_sse(nv, d, Yv.shape[1], _p(Xv), _p(Yv), _p(W)))
+
+
+def lstsq(V, T) -> np.ndarray:
+    """Theta = argmin ||T - V Theta||_F (Algorithm 1, steps 5-6) by Householder QR."""
+    V, T = _f64(V), _f64(T)
+    g, p = V.shape
+    D = T.shape[1]
+    Theta = np.empty((p, D))
+    rc = _get().orc_lstsq_householder(g, p, _p(V), D, _p(T), _p(Theta))
+    if rc:
+        raise np.linalg.LinAlgError("observation matrix V is rank deficient")
+    return Theta
+
+
+def vec_lower(L) -> np.ndarray:
+    """Row-wise vectorisation of the lower triangle (Sec. 5), length d(d+1)/2."""
+    L = _f64(L)
+    d = L.shape[0]
+    v = np.empty(d * (d + 1) // 2)
+    _get().orc_vec_lower(d, _p(L), _p(v))
+    return v
+
+
+def unvec_lower(v, d: int) -> np.ndarray:
+    v = _f64(v)
+    L = np.empty((d, d))
+    _get().orc_unvec_lower(d, _p(v), _p(L))
+    return L
+
+
+def eval_poly(phi, Theta) -> np.ndarray:
+    """sum_m phi[m] * Theta[m, :] (Sec. 3.3, evaluating the D polynomials)."""
+    phi, Theta = _f64(phi), _f64(Theta)
+    p, D = Theta.shape
+    out = np.empty(D)
+    _get().orc_eval_poly(p, D, _p(phi), _p(Theta), _p(out))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# the method's small host-side steps
+# ----------------------------------------------------------------------------
+
+def fold_offsets(n: int, k: int) -> list[int]:
+    """Fold f holds rows [floor(f n / k), floor((f+1) n / k))."""
+    return [(f * n) // k for f in range(k + 1)]
+
+
+def trace_scale(X) -> float:
+    """tau = tr(X^T X) / d = (sum of squares of all entries of X) / d."""
+    X = _f64(X)
+    s = 0.0
+    for row in X:
+        s += float(np.dot(row, row))
+    return s / X.shape[1]
+
+
+def lambda_grid(tau: float, q: int, lo: float, hi: float) -> np.ndarray:
+    """lambda_t = tau * lo * (hi / lo)^(t / (q - 1)), t = 0..q-1 (log-spaced)."""
+    if q == 1:
+        return np.array([tau * lo])
+    t = np.arange(q, dtype=np.float64)
+    return tau * lo * (hi / lo) ** (t / (q - 1))
+
+
+def sample_indices(q: int, g: int) -> list[int]:
+    """g grid indices evenly spread over 0..q-1, both ends included,
+    idx_i = round(i (q-1) / (g-1)) with halves rounded up."""
+    if g == 1:
+        return [0]
+    return [(2 * i * (q - 1) + (g - 1)) // (2 * (g - 1)) for i in range(g)]
+
+
+def basis_values(kind: str, lam, lam_s, p: int) -> np.ndarray:
+    """Rows phi(lambda) = [phi_0 .. phi_{p-1}] for each lambda in ``lam``.
+
+    mono     : phi_m = (lambda / max(lam_s))^m.  Dividing by the largest sampled
+               lambda spans the same polynomial space as Algorithm 1's monomials
+               and leaves the fitted function unchanged.
+    cheb_log : phi_m = T_m(u), u = 2 (ln lambda - ln min lam_s) /
+               (ln max lam_s - ln min lam_s) - 1, T_m the Chebyshev polynomials
+               of the first kind (T_0 = 1, T_1 = u, T_{m+1} = 2 u T_m - T_{m-1}).
+    """
+    lam = np.atleast_1d(np.asarray(lam, dtype=np.float64))
+    lam_s = np.asarray(lam_s, dtype=np.float64)
+    out = np.empty((lam.size, p))
+    if kind == BASIS_MONO:
+        x = lam / lam_s.max()
+        for m in range(p):
+            out[:, m] = x ** m
+    elif kind == BASIS_CHEB_LOG:
+        a, b = np.log(lam_s.min()), np.log(lam_s.max())
+        u = 2.0 * (np.log(lam) - a) / (b - a) - 1.0
+        out[:, 0] = 1.0
+        if p > 1:
+            out[:, 1] = u
+        for m in range(2, p):
+            out[:, m] = 2.0 * u * out[:, m - 1] - out[:, m - 2]
+    else:
+        raise ValueError(f"unknown basis {kind!r}")
+    return out
+
+
+def basis_derivs(kind: str, lam, lam_s, p: int) -> np.ndarray:
+    """d phi_m / d lambda at each lambda (for the hold-out gradient)."""
+    lam = np.atleast_1d(np.asarray(lam, dtype=np.float64))
+    lam_s = np.asarray(lam_s, dtype=np.float64)
+    out = np.zeros((lam.size, p))
+    if kind == BASIS_MONO:
+        s = lam_s.max()
+        x = lam / s
+        for m in range(1, p):
+            out[:, m] = m * x ** (m - 1) / s
+    elif kind == BASIS_CHEB_LOG:
+        a, b = np.log(lam_s.min()), np.log(lam_s.max())
+        u = 2.0 * (np.log(lam) - a) / (b - a) - 1.0
+        du = 2.0 / ((b - a) * lam)
+        T = np.zeros((lam.size, p))
+        dT = np.zeros((lam.size, p))
+        T[:, 0] = 1.0
+        if p > 1:
+            T[:, 1] = u
+            dT[:, 1] = 1.0
+        for m in range(2, p):
+            T[:, m] = 2.0 * u * T[:, m - 1] - T[:, m - 2]
+            dT[:, m] = 2.0 * T[:, m - 1] + 2.0 * u * dT[:, m - 1] - dT[:, m - 2]
+        out = dT * du[:, None]
+    else:
+        raise ValueError(f"unknown basis {kind!r}")
+    return out
+
+
+def diag_unusable(diag: np.ndarray) -> bool:
+    """An interpolated factor whose diagonal has an entry <= 0, or one smaller
+    than 1e3 * eps * max |diag|, does not define a usable solve; such a
+    (fold, lambda) is scored +inf and left out of the argmin."""
+    m = float(np.max(np.abs(diag))) if diag.size else 0.0
+    thr = 1e3 * np.finfo(np.float64).eps * m
+    return bool(np.any(diag <= 0.0) or np.any(np.abs(diag) <= thr))
+
+
+def argmin_first(values: np.ndarray) -> int:
+    """Index of the smallest finite value, ties to the smallest index; -1 if none."""
+    best, best_t = np.inf, -1
+    for t, v in enumerate(values):
+        if np.isfinite(v) and v < best:
+            best, best_t = v, t
+    return best_t
+
+
+# ----------------------------------------------------------------------------
+# the full cross-validation
+# ----------------------------------------------------------------------------
+
+@dataclass
+class CVResult:
+    lam: np.ndarray                 # q lambda values
+    sample_idx: list                # g grid indices that were factored exactly
+    E: np.ndarray                   # k x q hold-out MSE
+    Ebar: np.ndarray                # q, mean over folds
+    t_star: int                     # argmin of Ebar
+    unusable: np.ndarray            # k x q bool, interpolated diagonal unusable
+    tau: float
+    factors: dict = field(default_factory=dict)   # (f, s) -> L (keep=True)
+    theta: dict = field(default_factory=dict)     # f -> Theta (p x D, row-wise vec)
+    W: dict = field(default_factory=dict)         # (f, t) -> W (d x c)
+    H: dict = field(default_factory=dict)         # f -> H_f
+    B: dict = field(default_factory=dict)         # f -> B_f
+
+
+def cv(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e1,
+       basis: str = BASIS_MONO, exact: bool = False, scale_by_trace: bool = True,
+       folds=None, lam_idx=None, keep: bool = False) -> CVResult:
+    """k-fold CV of ridge regression over q lambdas, piCholesky (default) or
+    exact Cholesky at every lambda (``exact=True``, ``Chol`` of Sec. 6.2).
+
+    ``folds`` restricts the work to some folds and ``lam_idx`` to some grid
+    indices (entries outside are NaN); the grid, the samples and the fit are
+    unchanged by either.
+    """
+    X, Y = _f64(X), _f64(Y)
+    n, d = X.shape
+    c = Y.shape[1]
+    p = r + 1
+    if not exact and not (g > r):
+        raise ValueError("piCholesky needs g > r sampled lambdas (Algorithm 1)")
+    offs = fold_offsets(n, k)
+    tau = trace_scale(X) if scale_by_trace else 1.0
+    lam = lambda_grid(tau, q, lo, hi)
+    sidx = sample_indices(q, g) if not exact else list(range(q))
+    folds = list(range(k)) if folds is None else list(folds)
+    tsel = list(range(q)) if lam_idx is None else list(lam_idx)
+
+    E = np.full((k, q), np.nan)
+    bad = np.zeros((k, q), dtype=bool)
+    res = CVResult(lam=lam, sample_idx=sidx, E=E, Ebar=None, t_star=-1, unusable=bad, tau=tau)
+
+    for f in folds:
+        r0, r1 = offs[f], offs[f + 1]
+        nv = r1 - r0
+        Hf, Bf = normal_blocks(X, Y, r0, r1)
+        Xv, Yv = X[r0:r1], Y[r0:r1]
+        if keep:
+            res.H[f], res.B[f] = Hf, Bf
+        if exact:
+            for t in tsel:
+                L = cholesky(Hf + lam[t] * np.eye(d))
+                W = solve_factored(L, Bf)
+                E[f, t] = holdout_sse(Xv, Yv, W) / (nv * c)
+                if keep:
+                    res.W[(f, t)] = W
+            continue
+        # Algorithm 1, steps 1-2: exact factors at the samples, stacked as rows of T
+        lam_s = lam[sidx]
+        T = np.empty((g, d * (d + 1) // 2))
+        for s in range(g):
+            L = cholesky(Hf + lam_s[s] * np.eye(d))
+            T[s] = vec_lower(L)
+            if keep:
+                res.factors[(f, s)] = L
+        # steps 3-6: observation matrix and least-squares coefficients
+        V = basis_values(basis, lam_s, lam_s, p)
+        Theta = lstsq(V, T)
+        if keep:
+            res.theta[f] = Theta
+        # evaluation at every grid lambda, two triangular solves, hold-out error
+        Phi = basis_values(basis, lam, lam_s, p)
+        for t in tsel:
+            Lt = unvec_lower(eval_poly(Phi[t], Theta), d)
+            if diag_unusable(np.diag(Lt)):
+                bad[f, t] = True
+                E[f, t] = np.inf
+                continue
+            W = solve_factored(Lt, Bf)
+            E[f, t] = holdout_sse(Xv, Yv, W) / (nv * c)
+            if keep:
+                res.W[(f, t)] = W
+    if len(folds) == k:
+        res.Ebar = E.mean(axis=0)
+        res.t_star = argmin_first(res.Ebar)
+    return res

@@ -1,0 +1,8 @@
+"""GB300-native piCholesky cross-validation (arXiv 1404.0466).
+
+The compute path lives in ``libpichol.so`` (hand-written sm_103a CUDA behind a
+C ABI, declared in ``include/pichol.h``); ``binding`` marshals arguments to it.
+Importing the package does not load the library; ``binding.lib()`` does, and
+raises if it has not been built.
+"""
+__all__ = ["binding", "synth"]

@@ -1,0 +1,400 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these compares the oracle with itself: each check uses a closed form,
+a hand-derived fixture, an invariant, a library routine for a special case, or
+a bound stated in the paper (Kuang, Gittens, Hamid, arXiv 1404.0466).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_1404_0466_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+EPS = np.finfo(np.float64).eps
+
+
+def _spd(rng, d, cond=100.0):
+    Q = synth.haar_orthogonal(rng, d)
+    ev = np.geomspace(1.0, 1.0 / cond, d)
+    return (Q * ev) @ Q.T
+
+
+def _golden_chol():
+    rows = []
+    with open(os.path.join(GOLDEN, "chol_closed_form.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            name, d, lam, A, L = [s.strip() for s in line.split("|")]
+            d = int(d)
+            rows.append((name, d, float(lam),
+                         np.array(A.split(), dtype=float).reshape(d, d),
+                         np.array(L.split(), dtype=float).reshape(d, d)))
+    return rows
+
+
+# --------------------------------------------------------------------------
+# Cholesky factor and triangular solves (Sec. 3.2)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", _golden_chol(), ids=lambda c: c[0])
+def test_cholesky_closed_form(case):
+    name, d, lam, A, L_ref = case
+    L = orc.cholesky(A + lam * np.eye(d))
+    np.testing.assert_allclose(L, L_ref, rtol=1e-15, atol=1e-15)
+
+
+@pytest.mark.parametrize("d", [1, 7, 64, 131])
+def test_cholesky_residual_and_structure(d):
+    rng = np.random.default_rng(10 + d)
+    A = _spd(rng, d, cond=1e4)
+    L = orc.cholesky(A)
+    assert np.all(np.triu(L, 1) == 0.0)
+    assert np.all(np.diag(L) > 0)
+    res = np.linalg.norm(L @ L.T - A) / np.linalg.norm(A)
+    assert res <= 4 * d * EPS, res
+
+
+def test_cholesky_matches_library():
+    rng = np.random.default_rng(3)
+    A = _spd(rng, 90, cond=1e6)
+    np.testing.assert_allclose(orc.cholesky(A), np.linalg.cholesky(A), rtol=0, atol=1e-12)
+
+
+def test_cholesky_rejects_indefinite():
+    rng = np.random.default_rng(4)
+    Q = synth.haar_orthogonal(rng, 12)
+    ev = np.linspace(1.0, 2.0, 12)
+    ev[5] = -0.5
+    A = (Q * ev) @ Q.T
+    with pytest.raises(orc.NotSPD) as ei:
+        orc.cholesky(A)
+    assert 0 <= ei.value.pivot < 12
+
+
+def test_triangular_solves_match_library():
+    rng = np.random.default_rng(5)
+    d, c = 77, 6
+    A = _spd(rng, d, cond=1e3)
+    L = np.linalg.cholesky(A)
+    B = rng.standard_normal((d, c))
+    Z = orc.forward(L, B)
+    np.testing.assert_allclose(L @ Z, B, rtol=0, atol=1e-12 * np.abs(B).max() * d)
+    W = orc.backward(L, Z)
+    np.testing.assert_allclose(L.T @ W, Z, rtol=0, atol=1e-12 * np.abs(Z).max() * d)
+    np.testing.assert_allclose(orc.solve_factored(L, B), np.linalg.solve(A, B), rtol=1e-9, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# ridge solution (Eq. 1-2) against closed forms
+# --------------------------------------------------------------------------
+
+def test_ridge_matches_eigendecomposition_closed_form():
+    """Eq. `reg_normal_equation_svd` restated on H = Q diag(mu) Q^T:
+    W(lambda) = Q diag(1 / (mu + lambda)) Q^T B."""
+    p = synth.spectral_gaussian(300, 40, 3, seed=11)
+    H, B = orc.normal_blocks(p.X, p.Y)
+    mu, Q = np.linalg.eigh(p.X.T @ p.X)
+    for lam in [1e-3, 0.1, 10.0, 1e3]:
+        W = orc.solve_factored(orc.cholesky(H + lam * np.eye(40)), B)
+        W_ref = Q @ ((Q.T @ (p.X.T @ p.Y)) / (mu + lam)[:, None])
+        np.testing.assert_allclose(W, W_ref, rtol=1e-10, atol=1e-12 * np.abs(W_ref).max())
+
+
+def test_ridge_matches_augmented_least_squares():
+    """Eq. 1 is the least-squares problem [X; sqrt(lambda) I] W ~ [Y; 0]."""
+    rng = np.random.default_rng(12)
+    n, d, c, lam = 40, 9, 2, 0.37
+    X = rng.standard_normal((n, d))
+    Y = rng.standard_normal((n, c))
+    H, B = orc.normal_blocks(X, Y)
+    W = orc.solve_factored(orc.cholesky(H + lam * np.eye(d)), B)
+    Xa = np.vstack([X, math.sqrt(lam) * np.eye(d)])
+    Ya = np.vstack([Y, np.zeros((d, c))])
+    W_ref = np.linalg.lstsq(Xa, Ya, rcond=None)[0]
+    np.testing.assert_allclose(W, W_ref, rtol=1e-11, atol=1e-13)
+
+
+def test_normal_blocks_leave_out_rows():
+    """H_f = X^T X - X_f^T X_f = sum_{j != f} X_j^T X_j (Eq. 2 on the training rows)."""
+    rng = np.random.default_rng(13)
+    n, d, c, k = 103, 17, 4, 5
+    X = rng.standard_normal((n, d))
+    Y = rng.standard_normal((n, c))
+    offs = orc.fold_offsets(n, k)
+    for f in range(k):
+        H, B = orc.normal_blocks(X, Y, offs[f], offs[f + 1])
+        keep = np.r_[0:offs[f], offs[f + 1]:n]
+        np.testing.assert_allclose(H, X[keep].T @ X[keep], rtol=1e-13, atol=1e-12)
+        np.testing.assert_allclose(B, X[keep].T @ Y[keep], rtol=1e-13, atol=1e-12)
+        G = sum(X[offs[j]:offs[j + 1]].T @ X[offs[j]:offs[j + 1]] for j in range(k) if j != f)
+        np.testing.assert_allclose(H, G, rtol=1e-12, atol=1e-12)
+        assert np.array_equal(H, H.T)
+
+
+def test_holdout_sse_direct_and_expansion():
+    """||Y - X W||^2 directly, and the expansion
+    ||Y||^2 - 2 <X^T Y, W> + <W, X^T X W> that the device path uses."""
+    rng = np.random.default_rng(14)
+    X = rng.standard_normal((57, 11))
+    Y = rng.standard_normal((57, 3))
+    W = rng.standard_normal((11, 3))
+    sse = orc.holdout_sse(X, Y, W)
+    ref = float(np.sum((Y - X @ W) ** 2))
+    assert abs(sse - ref) <= 1e-12 * ref
+    G, Bv = X.T @ X, X.T @ Y
+    expn = float(np.sum(Y * Y) - 2 * np.sum(Bv * W) + np.sum(W * (G @ W)))
+    assert abs(expn - ref) <= 1e-10 * ref
+
+
+# --------------------------------------------------------------------------
+# Algorithm 1: basis, observation matrix, least-squares fit
+# --------------------------------------------------------------------------
+
+def test_lstsq_matches_library_and_pseudoinverse():
+    rng = np.random.default_rng(15)
+    V = rng.standard_normal((6, 4))
+    T = rng.standard_normal((6, 33))
+    np.testing.assert_allclose(orc.lstsq(V, T), np.linalg.lstsq(V, T, rcond=None)[0],
+                               rtol=1e-12, atol=1e-13)
+    P = orc.lstsq(V, np.eye(6))        # V^+ (p x g)
+    np.testing.assert_allclose(P @ V, np.eye(4), atol=1e-13)
+
+
+def test_chebyshev_basis_matches_library():
+    lam_s = np.geomspace(0.02, 50.0, 6)
+    lam = np.geomspace(0.02, 50.0, 41)
+    Phi = orc.basis_values(orc.BASIS_CHEB_LOG, lam, lam_s, 5)
+    u = 2 * (np.log(lam) - np.log(0.02)) / (np.log(50.0) - np.log(0.02)) - 1
+    np.testing.assert_allclose(Phi, np.polynomial.chebyshev.chebvander(u, 4), atol=1e-14)
+    assert np.allclose(Phi[[0, -1], 1], [-1.0, 1.0])
+
+
+def test_basis_derivatives_match_finite_differences():
+    lam_s = np.geomspace(0.3, 30.0, 5)
+    lam = np.array([0.5, 2.0, 17.0])
+    for kind in (orc.BASIS_MONO, orc.BASIS_CHEB_LOG):
+        dPhi = orc.basis_derivs(kind, lam, lam_s, 4)
+        h = 1e-6 * lam
+        fd = (orc.basis_values(kind, lam + h, lam_s, 4) - orc.basis_values(kind, lam - h, lam_s, 4)) / (2 * h[:, None])
+        np.testing.assert_allclose(dPhi, fd, rtol=1e-6, atol=1e-9)
+
+
+@pytest.mark.parametrize("kind", [orc.BASIS_MONO, orc.BASIS_CHEB_LOG])
+def test_fit_reproduces_polynomials(kind):
+    """If every column of T is a polynomial of degree <= r in the basis, the
+    least-squares fit of Algorithm 1 returns its coefficients exactly."""
+    rng = np.random.default_rng(16)
+    lam_s = np.geomspace(0.1, 10.0, 6)
+    V = orc.basis_values(kind, lam_s, lam_s, 4)
+    Theta_star = rng.standard_normal((4, 50))
+    np.testing.assert_allclose(orc.lstsq(V, V @ Theta_star), Theta_star, rtol=1e-10, atol=1e-10)
+
+
+def test_monomial_scaling_leaves_the_fit_unchanged():
+    """Algorithm 1 uses raw monomials 1, lambda, lambda^2; dividing lambda by the
+    largest sample spans the same space, so the fitted values agree with a
+    library polynomial fit in the raw variable."""
+    rng = np.random.default_rng(17)
+    lam_s = np.array([0.2, 0.9, 2.5, 4.0])
+    T = rng.standard_normal((4, 7))
+    Theta = orc.lstsq(orc.basis_values(orc.BASIS_MONO, lam_s, lam_s, 3), T)
+    lam = np.array([0.3, 1.7, 3.3])
+    got = orc.basis_values(orc.BASIS_MONO, lam, lam_s, 3) @ Theta
+    for j in range(7):
+        coef = np.polyfit(lam_s, T[:, j], 2)
+        np.testing.assert_allclose(got[:, j], np.polyval(coef, lam), rtol=1e-10, atol=1e-12)
+
+
+def test_vectorisation_round_trip():
+    rng = np.random.default_rng(18)
+    L = np.tril(rng.standard_normal((9, 9)))
+    v = orc.vec_lower(L)
+    assert v.size == 45
+    assert v[0] == L[0, 0] and v[1] == L[1, 0] and v[2] == L[1, 1] and v[3] == L[2, 0]
+    np.testing.assert_array_equal(orc.unvec_lower(v, 9), L)
+
+
+# --------------------------------------------------------------------------
+# small host-side steps
+# --------------------------------------------------------------------------
+
+def test_fold_offsets_partition_rows():
+    for n, k in [(10, 3), (2048, 5), (7, 7), (103, 5)]:
+        o = orc.fold_offsets(n, k)
+        assert o[0] == 0 and o[-1] == n and len(o) == k + 1
+        sizes = np.diff(o)
+        assert sizes.min() >= n // k and sizes.max() <= n // k + 1
+
+
+def test_sample_indices_and_grid():
+    assert orc.sample_indices(31, 4) == [0, 10, 20, 30]
+    assert orc.sample_indices(101, 6) == [0, 20, 40, 60, 80, 100]
+    assert orc.sample_indices(51, 5) == [0, 13, 25, 38, 50]   # 12.5 and 37.5 round up
+    lam = orc.lambda_grid(2.0, 31, 1e-3, 1e1)
+    assert np.isclose(lam[0], 2e-3) and np.isclose(lam[-1], 20.0)
+    np.testing.assert_allclose(np.diff(np.log(lam)), np.log(1e4) / 30, rtol=1e-12)
+
+
+def test_trace_scale():
+    rng = np.random.default_rng(19)
+    X = rng.standard_normal((30, 8))
+    assert np.isclose(orc.trace_scale(X), np.trace(X.T @ X) / 8, rtol=1e-14)
+
+
+def test_argmin_first_ties_and_inf():
+    assert orc.argmin_first(np.array([3.0, 1.0, 1.0, 2.0])) == 1
+    assert orc.argmin_first(np.array([np.inf, 5.0, np.inf])) == 1
+    assert orc.argmin_first(np.array([np.inf, np.nan])) == -1
+
+
+def test_unusable_diagonal_rule():
+    assert orc.diag_unusable(np.array([1.0, -1e-3, 2.0]))
+    assert orc.diag_unusable(np.array([1.0, 1e-20, 2.0]))
+    assert not orc.diag_unusable(np.array([1.0, 1e-3, 2.0]))
+
+
+# --------------------------------------------------------------------------
+# interpolation: nodes, exact cases and the paper's bounds (Sec. 4)
+# --------------------------------------------------------------------------
+
+def test_fit_reproduces_factors_at_nodes_when_g_equals_r_plus_1():
+    """With g = r + 1 the observation matrix V is square and invertible
+    (Algorithm 1 allows g > r), so the polynomials interpolate the sampled
+    factors: L_tilde(lambda_s) = L_s."""
+    p = synth.spectral_gaussian(200, 12, 2, seed=20)
+    for kind in (orc.BASIS_MONO, orc.BASIS_CHEB_LOG):
+        res = orc.cv(p.X, p.Y, k=4, g=3, r=2, q=9, basis=kind, keep=True, folds=[1])
+        lam_s = res.lam[res.sample_idx]
+        Phi = orc.basis_values(kind, lam_s, lam_s, 3)
+        for s in range(3):
+            Lt = orc.unvec_lower(Phi[s] @ res.theta[1], 12)
+            np.testing.assert_allclose(Lt, res.factors[(1, s)], rtol=1e-9, atol=1e-11)
+
+
+def test_pichol_equals_exact_cv_when_every_lambda_is_a_node():
+    """Sampling every grid lambda with r = g - 1 makes the fit interpolate each
+    exact factor, so piCholesky CV equals exact CV (Sec. 6.2, Chol)."""
+    p = synth.spectral_gaussian(160, 10, 3, seed=21)
+    a = orc.cv(p.X, p.Y, k=4, g=4, r=3, q=4, basis=orc.BASIS_CHEB_LOG)
+    b = orc.cv(p.X, p.Y, k=4, g=4, r=3, q=4, exact=True)
+    np.testing.assert_allclose(a.E, b.E, rtol=1e-8)
+    assert a.t_star == b.t_star
+
+
+def test_exact_cv_matches_independent_library_pipeline():
+    """Exact CV hold-out errors against np.linalg.solve on every fold and lambda."""
+    p = synth.spectral_gaussian(150, 14, 2, seed=22)
+    res = orc.cv(p.X, p.Y, k=5, g=1, r=0, q=7, exact=True)
+    X, Y = p.X, p.Y
+    offs = orc.fold_offsets(150, 5)
+    tau = np.trace(X.T @ X) / 14
+    lam = tau * 1e-3 * (1e4) ** (np.arange(7) / 6)
+    for f in range(5):
+        keep = np.r_[0:offs[f], offs[f + 1]:150]
+        H = X[keep].T @ X[keep]
+        B = X[keep].T @ Y[keep]
+        Xv, Yv = X[offs[f]:offs[f + 1]], Y[offs[f]:offs[f + 1]]
+        for t in range(7):
+            W = np.linalg.solve(H + lam[t] * np.eye(14), B)
+            ref = np.mean((Yv - Xv @ W) ** 2)
+            assert abs(res.E[f, t] - ref) <= 1e-10 * ref
+    Ebar = res.E.mean(axis=0)
+    assert res.t_star == int(np.argmin(Ebar))
+
+
+def _kron_sum(L):
+    d = L.shape[0]
+    I = np.eye(d)
+    return np.kron(I, L) + np.kron(L, I)
+
+
+def _vec(M):
+    return M.reshape(-1, order="F")
+
+
+def _unvec(v, d):
+    return v.reshape(d, d, order="F")
+
+
+def _R_and_pieces(h, s):
+    """Quantities of Thm 4.4 at shift s for A = diag(h), built from the
+    d^2 x d^2 Kronecker sums M_s = [[C(A + s I)]] and E_s."""
+    d = h.size
+    L = np.diag(np.sqrt(h + s))
+    M = _kron_sum(L)
+    Mi = np.linalg.inv(M)
+    vI = _vec(np.eye(d))
+    MivI = Mi @ vI
+    E = _kron_sum(_unvec(MivI, d))
+    MiE = Mi @ E
+    R = (np.linalg.norm(MiE, 2) ** 2 * np.linalg.norm(MivI)
+         + np.linalg.norm(Mi, 2) * np.linalg.norm(MiE, 2) * np.linalg.norm(MivI) ** 2)
+    return L, Mi, MivI, E, R
+
+
+def test_taylor_polynomial_and_bound_thm_4_4():
+    """For diagonal A the entries of C(A + lambda I) are sqrt(h_i + lambda); the
+    second-order Taylor polynomial of Thm 4.4 must equal the scalar Taylor
+    polynomial of sqrt, and its error must respect the stated bound."""
+    h = np.array([0.4, 1.3, 2.2])
+    d = h.size
+    D = d * (d + 1) / 2
+    lc = 1.0
+    L, Mi, MivI, E, _ = _R_and_pieces(h, lc)
+    for lam in [0.6, 0.9, 1.25, 1.5]:
+        dl = lam - lc
+        pTS = L + _unvec(dl * MivI - 0.5 * dl ** 2 * (Mi @ E @ MivI), d)
+        l0 = np.sqrt(h + lc)
+        scalar = l0 + dl / (2 * l0) - dl ** 2 / (8 * l0 ** 3)
+        np.testing.assert_allclose(np.diag(pTS), scalar, rtol=1e-12)
+        exact = np.diag(np.sqrt(h + lam))
+        lhs = np.linalg.norm(exact - pTS) / math.sqrt(D)
+        Rmax = max(_R_and_pieces(h, s)[4] for s in np.linspace(min(lam, lc), max(lam, lc), 41))
+        rhs = 2 * abs(dl) ** 3 / (3 * math.sqrt(D)) * Rmax
+        assert lhs <= rhs, (lam, lhs, rhs)
+
+
+def test_main_bound_thm_4_7_diagonal():
+    """Thm 4.7 (r = 2, g = 4 > 3 samples within w of lambda_c, lambda_c > gamma >= w)
+    on a diagonal A, where the derivative formulas of Thm 4.3 hold exactly.
+    The left side uses the oracle's own fit (Algorithm 1)."""
+    h = np.array([0.5, 1.1, 1.9])
+    d = h.size
+    D = d * (d + 1) / 2
+    lc, w, gamma, g = 1.2, 0.3, 0.45, 4
+    lam_s = lc + w * np.array([-1.0, -1 / 3, 1 / 3, 1.0])
+    T = np.stack([orc.vec_lower(orc.cholesky(np.diag(h) + ls * np.eye(d))) for ls in lam_s])
+    Theta = orc.lstsq(orc.basis_values(orc.BASIS_MONO, lam_s, lam_s, 3), T)
+    V = np.stack([np.ones(g), lam_s, lam_s ** 2], axis=1)
+    Vpinv = np.linalg.norm(np.linalg.pinv(V), 2)
+    R = max(_R_and_pieces(h, s)[4] for s in np.linspace(lc - gamma, lc + gamma, 61))
+    rhs = (gamma ** 3 + math.sqrt(g) * w ** 3 * (1 + gamma ** 2) * (lc + 1) * Vpinv) * R / math.sqrt(D)
+    worst = 0.0
+    for lam in np.linspace(lc - gamma, lc + gamma, 31):
+        Lt = orc.unvec_lower(orc.basis_values(orc.BASIS_MONO, [lam], lam_s, 3)[0] @ Theta, d)
+        lhs = np.linalg.norm(np.diag(np.sqrt(h + lam)) - Lt) / math.sqrt(D)
+        worst = max(worst, lhs)
+        assert lhs <= rhs, (lam, lhs, rhs)
+    assert worst > 0.0
+
+
+def test_diagonal_hessian_interpolation_error_is_small():
+    """Diagonal H: the exact factor is diag(sqrt(h + lambda)) and off-diagonal
+    entries stay zero; piCholesky over a narrow range must track it."""
+    h = np.array([1.0, 2.0, 3.0, 5.0])
+    lam_s = np.linspace(0.5, 1.5, 5)
+    T = np.stack([orc.vec_lower(orc.cholesky(np.diag(h) + ls * np.eye(4))) for ls in lam_s])
+    Theta = orc.lstsq(orc.basis_values(orc.BASIS_MONO, lam_s, lam_s, 3), T)
+    # scale of the cubic Taylor remainder of sqrt(h + lambda) about the centre:
+    # max |f'''| w^3 / 6 with f''' = (3/8) (h + lambda)^(-5/2), w = 0.5
+    tol = (3 / 8) * (h + 0.5) ** -2.5 * 0.5 ** 3 / 6
+    for lam in np.linspace(0.5, 1.5, 11):
+        Lt = orc.unvec_lower(orc.basis_values(orc.BASIS_MONO, [lam], lam_s, 3)[0] @ Theta, 4)
+        assert np.all(np.abs(np.diag(Lt) - np.sqrt(h + lam)) <= tol)
+        assert np.abs(np.tril(Lt, -1)).max() < 1e-14

@@ -1,0 +1,209 @@
+/*
+ * pichol.h -- C ABI of the GB300 (sm_103a) piCholesky cross-validation library.
+ *
+ * Method: Kuang, Gittens, Hamid, "Cholesky Factor Interpolation for Efficient
+ * Approximate Cross-Validation" (arXiv 1404.0466).  For k-fold cross-validation
+ * of multi-output ridge regression over a grid of q regularisation values, the
+ * library factors H_f + lambda_s I exactly at g sampled lambdas only
+ * (Algorithm 1, step 1), fits a degree-r polynomial in lambda to every entry of
+ * the lower Cholesky factor (Algorithm 1, steps 2-6), and scores the hold-out
+ * error at all q lambdas through triangular solves with the interpolated
+ * factor (Sec. 3.2 and the last paragraph of Sec. 3.3).
+ *
+ * Conventions shared by every call:
+ *  - Pointers are DEVICE pointers owned by the caller unless marked "host".
+ *  - Matrices are row-major.  X is n x d, Y is n x c, both of the mode's input
+ *    type (double in PICHOL_MODE_FP64, float in PICHOL_MODE_MIXED).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Every compute call only enqueues work on that stream and returns; nothing
+ *    synchronises except pichol_get_info and pichol_destroy.
+ *  - Argument errors are returned immediately and enqueue nothing.  Errors met
+ *    on the device (a non-positive pivot, a bounded wait that ran out) are
+ *    latched in a status word in the workspace: the first one wins, later
+ *    kernels keep running on safe values, and pichol_get_info reports it.  No
+ *    call traps, asserts, aborts or prints.
+ *  - The library allocates no device memory.  The caller provides one
+ *    workspace buffer of pichol_workspace_size() bytes (256-byte aligned) that
+ *    must stay valid, and must not be used by anyone else, while work enqueued
+ *    by this context is in flight.
+ *  - Calls on one context must not overlap on the GPU; use one context per
+ *    concurrent problem.
+ */
+#ifndef PICHOL_H
+#define PICHOL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PICHOL_API __attribute__((visibility("default")))
+#else
+#define PICHOL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PICHOL_OK = 0,
+    PICHOL_ERR_INVALID_ARG = 1,   /* bad size, null pointer, unsupported combination */
+    PICHOL_ERR_NOT_SPD = 2,       /* H_f + lambda I had a non-positive pivot */
+    PICHOL_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    PICHOL_ERR_WORKSPACE = 4,     /* workspace missing, too small or misaligned */
+    PICHOL_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+    PICHOL_ERR_UNSUPPORTED = 6,   /* feature not available in this build / mode */
+    PICHOL_ERR_STATE = 7          /* calls made out of order (e.g. fit before factor) */
+} pichol_status;
+
+typedef enum {
+    /* every step in double precision */
+    PICHOL_MODE_FP64 = 0,
+    /* float inputs; Hessian on tensor cores (TF32, optionally split 3-term),
+     * diagonal Cholesky blocks and the Vandermonde fit in double, panel and
+     * trailing updates, coefficient storage and solves in float, hold-out
+     * scoring with double accumulation, optional refinement with a
+     * double-float residual */
+    PICHOL_MODE_MIXED = 1
+} pichol_mode;
+
+typedef enum {
+    /* phi_m(lambda) = (lambda / max_s lambda_s)^m: the monomials of
+     * Algorithm 1, divided by the largest sample (same fitted polynomial) */
+    PICHOL_BASIS_MONO = 0,
+    /* phi_m(lambda) = T_m(u), u = 2 (ln lambda - ln min lambda_s) /
+     * (ln max lambda_s - ln min lambda_s) - 1: Chebyshev polynomials (named in
+     * Sec. 3.3 as the more stable basis) in log lambda */
+    PICHOL_BASIS_CHEB_LOG = 1
+} pichol_basis;
+
+typedef struct {
+    int64_t n;            /* rows of X and Y, >= k */
+    int64_t d;            /* features, 1 .. 16384 */
+    int64_t c;            /* outputs (right-hand sides), 1 .. 32 */
+    int32_t k;            /* folds, 2 .. 64; fold f = rows [floor(f n/k), floor((f+1) n/k)) */
+    int32_t g;            /* sampled lambdas, r < g <= min(q, 32) (Algorithm 1 needs g > r) */
+    int32_t r;            /* polynomial degree, 0 .. 5 */
+    int32_t q;            /* grid size, 1 .. 4096 */
+    double lam_lo;        /* grid: lambda_t = s * lam_lo * (lam_hi/lam_lo)^(t/(q-1)) */
+    double lam_hi;        /*   with s = tr(X^T X)/d if scale_by_trace else 1; 0 < lo <= hi */
+    int32_t scale_by_trace;
+    int32_t basis;        /* pichol_basis */
+    int32_t mode;         /* pichol_mode */
+    int32_t refine_steps; /* mixed mode: refinement steps after each solve (0..4) */
+    int32_t gram_passes;  /* mixed mode: 1 = plain TF32 products, 3 = split TF32 (hi*hi + hi*lo + lo*hi) */
+    int32_t exact_batch;  /* lambdas factored per batch by pichol_eval_holdout_exact (0 = all q) */
+    int32_t reserved[6];  /* must be zero */
+} pichol_config;
+
+/* First device error, as latched by the kernels. */
+typedef struct {
+    pichol_status code;   /* PICHOL_OK if none */
+    int32_t fold;         /* fold of the failing factorisation, -1 if n/a */
+    int32_t index;        /* sample (or grid index in exact mode), -1 if n/a */
+    int64_t pivot;        /* row of the non-positive pivot, -1 if n/a */
+    int32_t unusable;     /* count of (fold, lambda) pairs whose interpolated
+                             diagonal was <= 1e3 eps max|diag| (scored +inf) */
+} pichol_info;
+
+typedef struct pichol_ctx pichol_ctx;
+
+/* Fills *cfg with defaults: lam_lo = 1e-3, lam_hi = 1e1, scale_by_trace = 1,
+ * basis MONO, mode FP64, refine_steps 0, gram_passes 3, exact_batch 0; the
+ * sizes are left zero. */
+PICHOL_API void pichol_config_default(pichol_config* cfg);
+
+/* Validates cfg and creates a context (host memory only).  *out is NULL on
+ * error.  Every value out of the ranges documented in pichol_config returns
+ * PICHOL_ERR_INVALID_ARG. */
+PICHOL_API pichol_status pichol_create(const pichol_config* cfg, pichol_ctx** out);
+
+/* Bytes of device workspace the context needs. */
+PICHOL_API pichol_status pichol_workspace_size(const pichol_ctx* ctx, size_t* bytes);
+
+/* Attaches the caller's workspace (device pointer, >= pichol_workspace_size
+ * bytes, 256-byte aligned).  Contents need not be initialised: the call zeroes
+ * the status word with a blocking cudaMemset on the current device. */
+PICHOL_API pichol_status pichol_set_workspace(pichol_ctx* ctx, void* workspace, size_t bytes);
+
+/*
+ * Step 1: normal-equation blocks (Sec. 3.1, Eq. 2: H = X^T X, g = X^T y).
+ * For every fold j: G_j = X_j^T X_j (X_j = rows of fold j), Bv_j = X_j^T Y_j,
+ * yy_j = ||Y_j||_F^2; then tau = tr(sum_j G_j)/d, the lambda grid, and the
+ * training right-hand sides B_f = sum_{j != f} Bv_j.  X, Y: device, row-major,
+ * n x d and n x c, double (FP64 mode) or float (mixed mode).  X and Y are only
+ * read during this call's kernels.
+ */
+PICHOL_API pichol_status pichol_hessian(pichol_ctx* ctx, const void* X, const void* Y, void* stream);
+
+/*
+ * Step 2 (Algorithm 1, step 1): exact Cholesky factors L_{f,s} of
+ * H_f + lambda_s I for every fold f and each of the g sampled grid indices
+ * idx_s = round(s (q-1)/(g-1)) (Sec. 6.3: samples taken from the grid), with
+ * H_f = sum_{j != f} G_j.  Blocked right-looking factorisation, all k*g
+ * problems per launch.  A non-positive pivot latches PICHOL_ERR_NOT_SPD.
+ */
+PICHOL_API pichol_status pichol_factor_samples(pichol_ctx* ctx, void* stream);
+
+/*
+ * Step 3 (Algorithm 1, steps 2-6): V[s][m] = phi_m(lambda_s) (g x (r+1)),
+ * P = V^+ by QR in double precision, and Theta_f = P T_f for every fold, where
+ * row s of T_f holds the entries of L_{f,s}.  The coefficients stay in the
+ * workspace (see pichol_export_theta).
+ */
+PICHOL_API pichol_status pichol_fit(pichol_ctx* ctx, void* stream);
+
+/*
+ * Step 4 (Sec. 3.3 evaluation, Sec. 3.2 solves, Sec. 3.1 selection): for every
+ * fold f and grid index t, W_{f,t} = (L~ L~^T)^{-1} B_f with
+ * L~ = sum_m phi_m(lambda_t) Theta_{f,m} built tile by tile on the device, then
+ * E[f*q + t] = ||Y_f - X_f W_{f,t}||_F^2 / (n_f c) evaluated as
+ * (yy_f - 2 <Bv_f, W> + <W, G_f W>) / (n_f c), and *t_star = the smallest t
+ * minimising mean_f E[f*q + t] over finite values (-1 if none).
+ *   E_out   : device, k*q doubles
+ *   t_star  : device, one int32
+ *   W_out   : device or NULL; k*q*d*c values of the mode's type, [f][t][d][c]
+ * A (fold, lambda) whose interpolated diagonal is unusable scores +inf.
+ */
+PICHOL_API pichol_status pichol_eval_holdout(pichol_ctx* ctx, double* E_out, int32_t* t_star,
+                                  void* W_out, void* stream);
+
+/*
+ * Exact-Cholesky cross-validation (the `Chol` comparator of Sec. 6.2) with the
+ * same kernels: factor H_f + lambda_t I at every grid lambda, solve, score.
+ * Needs only pichol_hessian before it.  Same outputs as pichol_eval_holdout.
+ */
+PICHOL_API pichol_status pichol_eval_holdout_exact(pichol_ctx* ctx, double* E_out, int32_t* t_star,
+                                        void* W_out, void* stream);
+
+/* Device copy of the q grid lambdas (after pichol_hessian). */
+PICHOL_API pichol_status pichol_get_lambdas(pichol_ctx* ctx, double* lam_out, void* stream);
+
+/* Inspection (for tests): dense double copies of internal results.
+ *   factor : L_{f,s} (d x d, upper triangle zero) after pichol_factor_samples
+ *   theta  : Theta_{f,m} for m = 0..r, (r+1) x d x d (upper triangles zero) after pichol_fit
+ *   hessian: H_f (d x d, lower triangle mirrored) and B_f (d x c) after pichol_hessian */
+PICHOL_API pichol_status pichol_export_factor(pichol_ctx* ctx, int32_t f, int32_t s, double* L_out, void* stream);
+PICHOL_API pichol_status pichol_export_theta(pichol_ctx* ctx, int32_t f, double* theta_out, void* stream);
+PICHOL_API pichol_status pichol_export_hessian(pichol_ctx* ctx, int32_t f, double* H_out, double* B_out, void* stream);
+
+/* Synchronises `stream` and reports the first latched device error. */
+PICHOL_API pichol_status pichol_get_info(pichol_ctx* ctx, pichol_info* info, void* stream);
+
+/* Clears the latched device status (enqueued on `stream`). */
+PICHOL_API pichol_status pichol_clear_status(pichol_ctx* ctx, void* stream);
+
+/* Number of kernel launches this context has enqueued since creation. */
+PICHOL_API int64_t pichol_launch_count(const pichol_ctx* ctx);
+
+/* Frees the host-side context.  The workspace stays the caller's. */
+PICHOL_API void pichol_destroy(pichol_ctx* ctx);
+
+/* Short text for a status code (static storage). */
+PICHOL_API const char* pichol_status_string(pichol_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PICHOL_H */

@@ -1,0 +1,244 @@
+"""ctypes binding of libpichol (C ABI in include/pichol.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libpichol.so.  Functions named ``pichol_*`` are the raw C entry
+points; ``Context`` owns one C context plus its device workspace (a torch
+uint8 tensor) and exposes the same calls with torch tensors.
+
+There is no fallback: if the library has not been built, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import pathlib
+from dataclasses import dataclass
+
+_PKG = pathlib.Path(__file__).resolve().parent
+LIB_PATH = _PKG / "libpichol.so"
+
+PICHOL_MODE_FP64, PICHOL_MODE_MIXED = 0, 1
+PICHOL_BASIS_MONO, PICHOL_BASIS_CHEB_LOG = 0, 1
+STATUS = {0: "PICHOL_OK", 1: "PICHOL_ERR_INVALID_ARG", 2: "PICHOL_ERR_NOT_SPD", 3: "PICHOL_ERR_CUDA",
+          4: "PICHOL_ERR_WORKSPACE", 5: "PICHOL_ERR_TIMEOUT", 6: "PICHOL_ERR_UNSUPPORTED", 7: "PICHOL_ERR_STATE"}
+
+# every symbol include/pichol.h declares
+EXPORTS = [
+    "pichol_config_default", "pichol_create", "pichol_workspace_size", "pichol_set_workspace",
+    "pichol_hessian", "pichol_factor_samples", "pichol_fit", "pichol_eval_holdout",
+    "pichol_eval_holdout_exact", "pichol_get_lambdas", "pichol_export_factor", "pichol_export_theta",
+    "pichol_export_hessian", "pichol_get_info", "pichol_clear_status", "pichol_launch_count",
+    "pichol_destroy", "pichol_status_string",
+]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int64), ("c", ctypes.c_int64),
+                ("k", ctypes.c_int32), ("g", ctypes.c_int32), ("r", ctypes.c_int32), ("q", ctypes.c_int32),
+                ("lam_lo", ctypes.c_double), ("lam_hi", ctypes.c_double),
+                ("scale_by_trace", ctypes.c_int32), ("basis", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("refine_steps", ctypes.c_int32), ("gram_passes", ctypes.c_int32),
+                ("exact_batch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_int), ("fold", ctypes.c_int32), ("index", ctypes.c_int32),
+                ("pivot", ctypes.c_int64), ("unusable", ctypes.c_int32)]
+
+
+class PicholError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libpichol.so (raises if it was not built; there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not LIB_PATH.exists():
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1404_0466_gb300.build.build()")
+    L = ctypes.CDLL(str(LIB_PATH))
+    vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "pichol_config_default": ([ctypes.POINTER(Config)], None),
+        "pichol_create": ([ctypes.POINTER(Config), ctypes.POINTER(vp)], ctypes.c_int),
+        "pichol_workspace_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+        "pichol_set_workspace": ([vp, vp, ctypes.c_size_t], ctypes.c_int),
+        "pichol_hessian": ([vp, vp, vp, vp], ctypes.c_int),
+        "pichol_factor_samples": ([vp, vp], ctypes.c_int),
+        "pichol_fit": ([vp, vp], ctypes.c_int),
+        "pichol_eval_holdout": ([vp, vp, vp, vp, vp], ctypes.c_int),
+        "pichol_eval_holdout_exact": ([vp, vp, vp, vp, vp], ctypes.c_int),
+        "pichol_get_lambdas": ([vp, vp, vp], ctypes.c_int),
+        "pichol_export_factor": ([vp, i32, i32, vp, vp], ctypes.c_int),
+        "pichol_export_theta": ([vp, i32, vp, vp], ctypes.c_int),
+        "pichol_export_hessian": ([vp, i32, vp, vp, vp], ctypes.c_int),
+        "pichol_get_info": ([vp, ctypes.POINTER(Info), vp], ctypes.c_int),
+        "pichol_clear_status": ([vp, vp], ctypes.c_int),
+        "pichol_launch_count": ([vp], i64),
+        "pichol_destroy": ([vp], None),
+        "pichol_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    del dp
+    _lib = L
+    return L
+
+
+def __getattr__(name):
+    # raw C entry points: binding.pichol_hessian(...) etc.
+    if name.startswith("pichol_"):
+        return getattr(lib(), name)
+    raise AttributeError(name)
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise PicholError(code, where)
+
+
+def _stream_ptr(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+@dataclass
+class CVOutput:
+    E: "object"          # torch float64 (k, q) on device
+    t_star: "object"     # torch int32 (1,) on device
+    W: "object" = None   # torch (k, q, d, c) or None
+
+
+class Context:
+    """One piCholesky cross-validation problem on the current CUDA device."""
+
+    def __init__(self, *, n, d, c, k, g, r, q, lam_lo=1e-3, lam_hi=1e1, basis="mono", mode="fp64",
+                 refine_steps=0, gram_passes=3, exact_batch=0, scale_by_trace=True):
+        import torch
+        L = lib()
+        cfg = Config()
+        L.pichol_config_default(ctypes.byref(cfg))
+        cfg.n, cfg.d, cfg.c, cfg.k, cfg.g, cfg.r, cfg.q = n, d, c, k, g, r, q
+        cfg.lam_lo, cfg.lam_hi = lam_lo, lam_hi
+        cfg.scale_by_trace = 1 if scale_by_trace else 0
+        cfg.basis = {"mono": PICHOL_BASIS_MONO, "cheb_log": PICHOL_BASIS_CHEB_LOG}[basis]
+        cfg.mode = {"fp64": PICHOL_MODE_FP64, "mixed": PICHOL_MODE_MIXED}[mode]
+        cfg.refine_steps, cfg.gram_passes, cfg.exact_batch = refine_steps, gram_passes, exact_batch
+        self.cfg = cfg
+        self.dtype = torch.float64 if mode == "fp64" else torch.float32
+        h = ctypes.c_void_p()
+        _check(L.pichol_create(ctypes.byref(cfg), ctypes.byref(h)), "pichol_create")
+        self._h = h
+        nbytes = ctypes.c_size_t()
+        _check(L.pichol_workspace_size(h, ctypes.byref(nbytes)), "pichol_workspace_size")
+        self.workspace_bytes = nbytes.value
+        self._ws = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device="cuda")
+        _check(L.pichol_set_workspace(h, ctypes.c_void_p(self._ws.data_ptr()), self._ws.numel()),
+               "pichol_set_workspace")
+
+    # -- steps -------------------------------------------------------------
+    def hessian(self, X, Y, stream=None):
+        assert X.is_cuda and Y.is_cuda and X.dtype == self.dtype and Y.dtype == self.dtype
+        assert X.is_contiguous() and Y.is_contiguous()
+        assert tuple(X.shape) == (self.cfg.n, self.cfg.d) and tuple(Y.shape) == (self.cfg.n, self.cfg.c)
+        self._X, self._Y = X, Y   # keep alive while kernels may read them
+        _check(lib().pichol_hessian(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
+                                    ctypes.c_void_p(_stream_ptr(stream))), "pichol_hessian")
+
+    def factor_samples(self, stream=None):
+        _check(lib().pichol_factor_samples(self._h, ctypes.c_void_p(_stream_ptr(stream))), "pichol_factor_samples")
+
+    def fit(self, stream=None):
+        _check(lib().pichol_fit(self._h, ctypes.c_void_p(_stream_ptr(stream))), "pichol_fit")
+
+    def _outputs(self, want_w):
+        import torch
+        cfg = self.cfg
+        E = torch.empty((cfg.k, cfg.q), dtype=torch.float64, device="cuda")
+        t = torch.empty((1,), dtype=torch.int32, device="cuda")
+        W = torch.empty((cfg.k, cfg.q, cfg.d, cfg.c), dtype=self.dtype, device="cuda") if want_w else None
+        return E, t, W
+
+    def eval_holdout(self, want_w=False, out=None, stream=None) -> CVOutput:
+        E, t, W = out if out is not None else self._outputs(want_w)
+        _check(lib().pichol_eval_holdout(self._h, ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                         ctypes.c_void_p(W.data_ptr() if W is not None else 0),
+                                         ctypes.c_void_p(_stream_ptr(stream))), "pichol_eval_holdout")
+        return CVOutput(E, t, W)
+
+    def eval_holdout_exact(self, want_w=False, out=None, stream=None) -> CVOutput:
+        E, t, W = out if out is not None else self._outputs(want_w)
+        _check(lib().pichol_eval_holdout_exact(self._h, ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                               ctypes.c_void_p(W.data_ptr() if W is not None else 0),
+                                               ctypes.c_void_p(_stream_ptr(stream))), "pichol_eval_holdout_exact")
+        return CVOutput(E, t, W)
+
+    def run(self, X, Y, want_w=False, out=None, stream=None) -> CVOutput:
+        """The whole hot path: hessian, factor_samples, fit, eval_holdout."""
+        self.hessian(X, Y, stream)
+        self.factor_samples(stream)
+        self.fit(stream)
+        return self.eval_holdout(want_w, out, stream)
+
+    # -- inspection ----------------------------------------------------------
+    def lambdas(self, stream=None):
+        import torch
+        lam = torch.empty((self.cfg.q,), dtype=torch.float64, device="cuda")
+        _check(lib().pichol_get_lambdas(self._h, ctypes.c_void_p(lam.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
+               "pichol_get_lambdas")
+        return lam
+
+    def export_factor(self, f, s, stream=None):
+        import torch
+        d = self.cfg.d
+        L = torch.empty((d, d), dtype=torch.float64, device="cuda")
+        _check(lib().pichol_export_factor(self._h, f, s, ctypes.c_void_p(L.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
+               "pichol_export_factor")
+        return L
+
+    def export_theta(self, f, stream=None):
+        import torch
+        d = self.cfg.d
+        T = torch.empty((self.cfg.r + 1, d, d), dtype=torch.float64, device="cuda")
+        _check(lib().pichol_export_theta(self._h, f, ctypes.c_void_p(T.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
+               "pichol_export_theta")
+        return T
+
+    def export_hessian(self, f, stream=None):
+        import torch
+        d, c = self.cfg.d, self.cfg.c
+        H = torch.empty((d, d), dtype=torch.float64, device="cuda")
+        B = torch.empty((d, c), dtype=torch.float64, device="cuda")
+        _check(lib().pichol_export_hessian(self._h, f, ctypes.c_void_p(H.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                                           ctypes.c_void_p(_stream_ptr(stream))), "pichol_export_hessian")
+        return H, B
+
+    def info(self, stream=None) -> Info:
+        inf = Info()
+        _check(lib().pichol_get_info(self._h, ctypes.byref(inf), ctypes.c_void_p(_stream_ptr(stream))), "pichol_get_info")
+        return inf
+
+    def clear_status(self, stream=None):
+        _check(lib().pichol_clear_status(self._h, ctypes.c_void_p(_stream_ptr(stream))), "pichol_clear_status")
+
+    def launch_count(self) -> int:
+        return int(lib().pichol_launch_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pichol_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

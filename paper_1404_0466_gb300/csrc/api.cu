@@ -1,0 +1,286 @@
+// C ABI of libpichol: argument checking, workspace planning and the order of
+// kernel launches.  Every call below only enqueues work on the caller's
+// stream; see include/pichol.h for the contract of each entry point.
+#include "internal.cuh"
+
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+using namespace pichol;
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Lay the workspace sections out from `base` (nullptr: only count bytes).
+size_t plan(pichol_ctx* ctx, char* base)
+{
+    const pichol_config& c = ctx->cfg;
+    const int64_t k = c.k, q = c.q, g = c.g, p = ctx->p, dp = ctx->dp, nt = ctx->nt;
+    const int64_t eb = ctx->eb, cc = c.c, ntl = ctx->ntiles;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void* {
+        void* ptr = base ? (void*)(base + off) : nullptr;
+        off += align256(bytes);
+        return ptr;
+    };
+    ctx->status = (DevStatus*)take(sizeof(DevStatus));
+    ctx->scal = (double*)take(8 * sizeof(double));
+    ctx->lam = (double*)take(q * sizeof(double));
+    ctx->lam_s = (double*)take(g * sizeof(double));
+    ctx->pinv = (double*)take(p * g * sizeof(double));
+    ctx->phi = (double*)take(q * p * sizeof(double));
+    ctx->dphi = (double*)take(q * p * sizeof(double));
+    ctx->nfc = (int64_t*)take(k * sizeof(int64_t));
+    ctx->yy = (double*)take(k * sizeof(double));
+    ctx->G = take((size_t)(k * dp * dp * eb));
+    ctx->Bv = take((size_t)(k * dp * cc * eb));
+    ctx->Btr = take((size_t)(k * dp * cc * eb));
+    ctx->F = take((size_t)(ctx->nfac * ntl * TILE_ELEMS * eb));
+    ctx->Linv = (double*)take((size_t)(ctx->nfac * TILE_ELEMS * sizeof(double)));
+    ctx->Theta = take((size_t)(k * ntl * p * TILE_ELEMS * eb));
+    ctx->Dinv = take((size_t)(k * q * nt * TILE_ELEMS * eb));
+    ctx->W = take((size_t)(k * q * dp * cc * eb));
+    const bool refine = c.mode == PICHOL_MODE_MIXED && c.refine_steps > 0;
+    ctx->U = refine ? take((size_t)(2 * k * q * dp * cc * sizeof(float))) : nullptr;
+    ctx->Rres = refine ? take((size_t)(k * q * dp * cc * eb)) : nullptr;
+    ctx->Epart = (double*)take((size_t)(k * q * nt * sizeof(double)));
+    ctx->E = (double*)take((size_t)(k * q * sizeof(double)));
+    ctx->flags = (int*)take((size_t)(k * q * nt * sizeof(int)));
+    ctx->dmax = (float*)take((size_t)(k * q * nt * sizeof(float)));
+    ctx->dmin = (float*)take((size_t)(k * q * nt * sizeof(float)));
+    return off;
+}
+
+pichol_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PICHOL_OK : PICHOL_ERR_CUDA; }
+
+bool ready(const pichol_ctx* ctx) { return ctx && ctx->ws; }
+
+}  // namespace
+
+extern "C" {
+
+void pichol_config_default(pichol_config* cfg)
+{
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->lam_lo = 1e-3;
+    cfg->lam_hi = 1e1;
+    cfg->scale_by_trace = 1;
+    cfg->basis = PICHOL_BASIS_MONO;
+    cfg->mode = PICHOL_MODE_FP64;
+    cfg->refine_steps = 0;
+    cfg->gram_passes = 3;
+    cfg->exact_batch = 0;
+}
+
+pichol_status pichol_create(const pichol_config* cfg, pichol_ctx** out)
+{
+    if (out) *out = nullptr;
+    if (!cfg || !out) return PICHOL_ERR_INVALID_ARG;
+    const pichol_config& c = *cfg;
+    if (c.k < 2 || c.k > MAX_K) return PICHOL_ERR_INVALID_ARG;
+    if (c.n < c.k || c.d < 1 || c.d > 16384 || c.c < 1 || c.c > 32) return PICHOL_ERR_INVALID_ARG;
+    if (c.q < 1 || c.q > 4096) return PICHOL_ERR_INVALID_ARG;
+    if (c.r < 0 || c.r > 5) return PICHOL_ERR_INVALID_ARG;
+    if (c.g <= c.r || c.g > c.q || c.g > MAX_G) return PICHOL_ERR_INVALID_ARG;
+    if (!(c.lam_lo > 0.0) || !(c.lam_hi >= c.lam_lo)) return PICHOL_ERR_INVALID_ARG;
+    if (c.scale_by_trace != 0 && c.scale_by_trace != 1) return PICHOL_ERR_INVALID_ARG;
+    if (c.basis != PICHOL_BASIS_MONO && c.basis != PICHOL_BASIS_CHEB_LOG) return PICHOL_ERR_INVALID_ARG;
+    if (c.mode != PICHOL_MODE_FP64 && c.mode != PICHOL_MODE_MIXED) return PICHOL_ERR_INVALID_ARG;
+    if (c.refine_steps < 0 || c.refine_steps > 4) return PICHOL_ERR_INVALID_ARG;
+    if (c.gram_passes != 1 && c.gram_passes != 3) return PICHOL_ERR_INVALID_ARG;
+    if (c.exact_batch < 0 || c.exact_batch > c.q) return PICHOL_ERR_INVALID_ARG;
+    for (int i = 0; i < 6; ++i)
+        if (c.reserved[i] != 0) return PICHOL_ERR_INVALID_ARG;
+    // the interpolate-on-load solve keeps p coefficient planes and the
+    // right-hand-side blocks of two lambdas in shared memory (227 KB per CTA)
+    if (solve_smem_bytes(c.mode == PICHOL_MODE_FP64 ? 8 : 4, c.r + 1, c.c) > 227 * 1024)
+        return PICHOL_ERR_UNSUPPORTED;
+    pichol_ctx* ctx = new (std::nothrow) pichol_ctx();
+    if (!ctx) return PICHOL_ERR_INVALID_ARG;
+    ctx->cfg = c;
+    ctx->nt = (int)((c.d + TB - 1) / TB);
+    ctx->dp = (int64_t)ctx->nt * TB;
+    ctx->ntiles = num_tiles(ctx->nt);
+    ctx->p = c.r + 1;
+    ctx->eb = c.mode == PICHOL_MODE_FP64 ? 8 : 4;
+    for (int f = 0; f <= c.k; ++f) ctx->offs[f] = (int64_t)f * c.n / c.k;
+    ctx->exact_batch = c.exact_batch > 0 ? c.exact_batch : c.q;
+    ctx->nfac = (int64_t)c.k * (ctx->exact_batch > c.g ? ctx->exact_batch : c.g);
+    ctx->need_bytes = plan(ctx, nullptr);
+    *out = ctx;
+    return PICHOL_OK;
+}
+
+pichol_status pichol_workspace_size(const pichol_ctx* ctx, size_t* bytes)
+{
+    if (!ctx || !bytes) return PICHOL_ERR_INVALID_ARG;
+    *bytes = ctx->need_bytes;
+    return PICHOL_OK;
+}
+
+pichol_status pichol_set_workspace(pichol_ctx* ctx, void* workspace, size_t bytes)
+{
+    if (!ctx || !workspace) return PICHOL_ERR_INVALID_ARG;
+    if (bytes < ctx->need_bytes || ((uintptr_t)workspace & 255u)) return PICHOL_ERR_WORKSPACE;
+    ctx->ws = (char*)workspace;
+    ctx->ws_bytes = bytes;
+    plan(ctx, ctx->ws);
+    ctx->have_hessian = ctx->have_factors = ctx->have_fit = false;
+    // the status word must read "no error" before any kernel runs
+    return cuda_status(cudaMemset(ctx->status, 0, sizeof(DevStatus)));
+}
+
+pichol_status pichol_hessian(pichol_ctx* ctx, const void* X, const void* Y, void* stream)
+{
+    if (!ctx || !X || !Y) return PICHOL_ERR_INVALID_ARG;
+    if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), s);
+    pichol_status st = cuda_status(e == cudaSuccess ? launch_gram(ctx, X, Y, s) : e);
+    ctx->have_hessian = st == PICHOL_OK;
+    ctx->have_factors = ctx->have_fit = false;
+    return st;
+}
+
+pichol_status pichol_factor_samples(pichol_ctx* ctx, void* stream)
+{
+    if (!ctx) return PICHOL_ERR_INVALID_ARG;
+    if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
+    if (!ctx->have_hessian) return PICHOL_ERR_STATE;
+    pichol_status st = cuda_status(launch_factor(ctx, ctx->cfg.g, 0, 0, (cudaStream_t)stream));
+    ctx->have_factors = st == PICHOL_OK;
+    ctx->have_fit = false;
+    return st;
+}
+
+pichol_status pichol_fit(pichol_ctx* ctx, void* stream)
+{
+    if (!ctx) return PICHOL_ERR_INVALID_ARG;
+    if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
+    if (!ctx->have_factors) return PICHOL_ERR_STATE;
+    pichol_status st = cuda_status(launch_fit(ctx, (cudaStream_t)stream));
+    ctx->have_fit = st == PICHOL_OK;
+    return st;
+}
+
+pichol_status pichol_eval_holdout(pichol_ctx* ctx, double* E_out, int32_t* t_star, void* W_out, void* stream)
+{
+    if (!ctx || !E_out || !t_star) return PICHOL_ERR_INVALID_ARG;
+    if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
+    if (!ctx->have_fit) return PICHOL_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = launch_eval(ctx, 0, 0, ctx->cfg.q, s);
+    if (e == cudaSuccess) e = launch_finish(ctx, E_out, t_star, s);
+    if (e == cudaSuccess && W_out) e = launch_copy_w(ctx, W_out, s);
+    return cuda_status(e);
+}
+
+pichol_status pichol_eval_holdout_exact(pichol_ctx* ctx, double* E_out, int32_t* t_star, void* W_out,
+                                        void* stream)
+{
+    if (!ctx || !E_out || !t_star) return PICHOL_ERR_INVALID_ARG;
+    if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
+    if (!ctx->have_hessian) return PICHOL_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int q = ctx->cfg.q, b = (int)ctx->exact_batch;
+    cudaError_t e = cudaSuccess;
+    for (int t0 = 0; t0 < q && e == cudaSuccess; t0 += b) {
+        const int cnt = (q - t0) < b ? (q - t0) : b;
+        e = launch_factor(ctx, cnt, 1, t0, s);
+        if (e == cudaSuccess) e = launch_eval(ctx, 1, t0, cnt, s);
+    }
+    ctx->have_factors = false;   // the sampled factors were overwritten
+    if (e == cudaSuccess) e = launch_finish(ctx, E_out, t_star, s);
+    if (e == cudaSuccess && W_out) e = launch_copy_w(ctx, W_out, s);
+    return cuda_status(e);
+}
+
+pichol_status pichol_get_lambdas(pichol_ctx* ctx, double* lam_out, void* stream)
+{
+    if (!ctx || !lam_out) return PICHOL_ERR_INVALID_ARG;
+    if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
+    if (!ctx->have_hessian) return PICHOL_ERR_STATE;
+    return cuda_status(cudaMemcpyAsync(lam_out, ctx->lam, sizeof(double) * ctx->cfg.q, cudaMemcpyDeviceToDevice,
+                                       (cudaStream_t)stream));
+}
+
+pichol_status pichol_export_factor(pichol_ctx* ctx, int32_t f, int32_t s, double* L_out, void* stream)
+{
+    if (!ctx || !L_out || f < 0 || f >= ctx->cfg.k || s < 0 || s >= ctx->cfg.g) return PICHOL_ERR_INVALID_ARG;
+    if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
+    if (!ctx->have_factors) return PICHOL_ERR_STATE;
+    const int64_t slot = (int64_t)f * ctx->cfg.g + s;
+    const char* src = (const char*)ctx->F + slot * ctx->ntiles * TILE_ELEMS * ctx->eb;
+    return cuda_status(launch_export_tiles(ctx, src, 0, TILE_ELEMS, L_out, (cudaStream_t)stream));
+}
+
+pichol_status pichol_export_theta(pichol_ctx* ctx, int32_t f, double* theta_out, void* stream)
+{
+    if (!ctx || !theta_out || f < 0 || f >= ctx->cfg.k) return PICHOL_ERR_INVALID_ARG;
+    if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
+    if (!ctx->have_fit) return PICHOL_ERR_STATE;
+    const int64_t d = ctx->cfg.d;
+    const char* base = (const char*)ctx->Theta + (int64_t)f * ctx->ntiles * ctx->p * TILE_ELEMS * ctx->eb;
+    for (int m = 0; m < ctx->p; ++m) {
+        cudaError_t e = launch_export_tiles(ctx, base, (int64_t)m * TILE_ELEMS, (int64_t)ctx->p * TILE_ELEMS,
+                                            theta_out + (int64_t)m * d * d, (cudaStream_t)stream);
+        if (e != cudaSuccess) return PICHOL_ERR_CUDA;
+    }
+    return PICHOL_OK;
+}
+
+pichol_status pichol_export_hessian(pichol_ctx* ctx, int32_t f, double* H_out, double* B_out, void* stream)
+{
+    if (!ctx || !H_out || !B_out || f < 0 || f >= ctx->cfg.k) return PICHOL_ERR_INVALID_ARG;
+    if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
+    if (!ctx->have_hessian) return PICHOL_ERR_STATE;
+    return cuda_status(launch_export_hessian(ctx, f, H_out, B_out, (cudaStream_t)stream));
+}
+
+pichol_status pichol_get_info(pichol_ctx* ctx, pichol_info* info, void* stream)
+{
+    if (!ctx || !info) return PICHOL_ERR_INVALID_ARG;
+    if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
+    DevStatus h;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(&h, ctx->status, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return PICHOL_ERR_CUDA;
+    info->code = (pichol_status)h.code;
+    info->fold = h.code ? h.fold : -1;
+    info->index = h.code ? h.index : -1;
+    info->pivot = h.code ? h.pivot : -1;
+    info->unusable = h.unusable;
+    return PICHOL_OK;
+}
+
+pichol_status pichol_clear_status(pichol_ctx* ctx, void* stream)
+{
+    if (!ctx) return PICHOL_ERR_INVALID_ARG;
+    if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
+    return cuda_status(cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), (cudaStream_t)stream));
+}
+
+int64_t pichol_launch_count(const pichol_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+void pichol_destroy(pichol_ctx* ctx) { delete ctx; }
+
+const char* pichol_status_string(pichol_status s)
+{
+    switch (s) {
+    case PICHOL_OK: return "ok";
+    case PICHOL_ERR_INVALID_ARG: return "invalid argument";
+    case PICHOL_ERR_NOT_SPD: return "matrix not positive definite";
+    case PICHOL_ERR_CUDA: return "CUDA runtime error";
+    case PICHOL_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    case PICHOL_ERR_TIMEOUT: return "bounded device wait gave up";
+    case PICHOL_ERR_UNSUPPORTED: return "unsupported";
+    case PICHOL_ERR_STATE: return "calls out of order";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,300 @@
+// Normal-equation blocks (Sec. 3.1, Eq. 2: H = X^T X, g = X^T y) per fold,
+// the lambda grid, and the Vandermonde pseudo-inverse of Algorithm 1.
+//
+//   G_j  = X_j^T X_j   (dense dp x dp, fold j's rows)       k_gram_simt
+//   Bv_j = X_j^T Y_j   (dp x c)                             k_xty
+//   yy_j = ||Y_j||_F^2                                      k_yy
+//   tau, lambda grid, sampled lambdas, V, P = V^+, phi      k_setup
+//   B_f  = sum_{j != f} Bv_j                                k_btrain
+#include "internal.cuh"
+#include <cmath>
+
+namespace pichol {
+
+struct FoldOffs { int64_t o[MAX_K + 1]; };
+
+// ---------------------------------------------------------------------------
+// G_j = X_j^T X_j, one 64 x 64 output tile per CTA (lower tiles; the upper
+// tile is written by mirroring).  Rows are consumed 32 at a time; each chunk
+// sum is accumulated in the working type and folded into a compensated
+// (Kahan) total so that long folds do not lose accuracy.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_gram_simt(const T* __restrict__ X, int64_t d, int64_t dp, FoldOffs fo, T* __restrict__ G)
+{
+    int I, J;
+    tile_coords(blockIdx.x, I, J);
+    const int j = blockIdx.y;
+    const int64_t r0 = fo.o[j], r1 = fo.o[j + 1];
+    __shared__ T As[32][TB];
+    __shared__ T Bs[32][TB];
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    T tot[4][4], cmp[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) { tot[a][b] = T(0); cmp[a][b] = T(0); }
+
+    for (int64_t rb = r0; rb < r1; rb += 32) {
+        for (int qq = tid; qq < 32 * TB; qq += 256) {
+            int rr = qq / TB, cc = qq % TB;
+            int64_t row = rb + rr;
+            int64_t ci = (int64_t)I * TB + cc, cj = (int64_t)J * TB + cc;
+            As[rr][cc] = (row < r1 && ci < d) ? X[row * d + ci] : T(0);
+            Bs[rr][cc] = (row < r1 && cj < d) ? X[row * d + cj] : T(0);
+        }
+        __syncthreads();
+        T acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+#pragma unroll 8
+        for (int kk = 0; kk < 32; ++kk) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {   // Kahan: tot += acc
+                T y = acc[a][b] - cmp[a][b];
+                T t = tot[a][b] + y;
+                cmp[a][b] = (t - tot[a][b]) - y;
+                tot[a][b] = t;
+            }
+        __syncthreads();
+    }
+    T* Gj = G + (int64_t)j * dp * dp;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            int64_t row = (int64_t)I * TB + ty + 16 * a;
+            int64_t col = (int64_t)J * TB + tx + 16 * b;
+            Gj[row * dp + col] = tot[a][b];
+            if (I != J) Gj[col * dp + row] = tot[a][b];
+        }
+}
+
+// ---------------------------------------------------------------------------
+// Bv_j = X_j^T Y_j.  Thread (feature fi, output phase oc) accumulates outputs
+// o = oc + 4u.  32-row chunk sums in the working type, totals in double.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_xty(const T* __restrict__ X, const T* __restrict__ Y, int64_t d, int64_t dp, int64_t c,
+      FoldOffs fo, T* __restrict__ Bv)
+{
+    const int tile = blockIdx.x, j = blockIdx.y;
+    const int fi = threadIdx.x & 63, oc = threadIdx.x >> 6;
+    const int64_t col = (int64_t)tile * TB + fi;
+    const int64_t r0 = fo.o[j], r1 = fo.o[j + 1];
+    double tot[16];
+    T acc[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) tot[u] = 0.0;
+    for (int64_t rb = r0; rb < r1; rb += 32) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) acc[u] = T(0);
+        int64_t re = rb + 32 < r1 ? rb + 32 : r1;
+        for (int64_t row = rb; row < re; ++row) {
+            T x = col < d ? X[row * d + col] : T(0);
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                int64_t o = oc + 4 * u;
+                if (o < c) acc[u] = fma(x, Y[row * c + o], acc[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) tot[u] += (double)acc[u];
+    }
+    T* B = Bv + (int64_t)j * dp * c;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        int64_t o = oc + 4 * u;
+        if (o < c) B[col * c + o] = (T)tot[u];
+    }
+}
+
+// yy_j = ||Y_j||_F^2 in double, fixed reduction order.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_yy(const T* __restrict__ Y, int64_t c, FoldOffs fo, double* __restrict__ yy, int64_t* __restrict__ nfc)
+{
+    const int j = blockIdx.x;
+    if (threadIdx.x == 0) nfc[j] = (fo.o[j + 1] - fo.o[j]) * c;
+    const int64_t a = fo.o[j] * c, b = fo.o[j + 1] * c;
+    double s = 0.0;
+    for (int64_t e = a + threadIdx.x; e < b; e += 256) {
+        double v = (double)Y[e];
+        s += v * v;
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) yy[j] = red[0];
+}
+
+// B_f = sum_{j != f} Bv_j, summed in increasing j.
+template <typename T>
+__global__ void k_btrain(const T* __restrict__ Bv, int k, int64_t len, T* __restrict__ Btr)
+{
+    const int f = blockIdx.y;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int j = 0; j < k; ++j)
+            if (j != f) s += (double)Bv[(int64_t)j * len + e];
+        Btr[(int64_t)f * len + e] = (T)s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Set-up in double precision (one CTA):
+//   tau = tr(sum_j G_j) / d (if scale_by_trace, else 1)
+//   lambda_t = tau lo (hi/lo)^(t/(q-1))                 (Sec. 6.3 grid)
+//   idx_s = round(s (q-1)/(g-1)), lambda_s = lambda_{idx_s}
+//   V[s][m] = phi_m(lambda_s); V = Q R by modified Gram-Schmidt with one
+//   re-orthogonalisation pass; P = R^{-1} Q^T = V^+ (Algorithm 1, steps 3-6)
+//   phi[t][m] = phi_m(lambda_t), dphi[t][m] = d phi_m / d lambda at lambda_t
+// ---------------------------------------------------------------------------
+__device__ inline void basis_eval(int basis, int p, double lam, double a, double b, double smax,
+                                  double* phi, double* dphi)
+{
+    if (basis == PICHOL_BASIS_MONO) {
+        // phi_m = x^m, d phi_m / d lambda = m x^(m-1) / smax, x = lambda / smax
+        double x = lam / smax, xm = 1.0;
+        dphi[0] = 0.0;
+        for (int m = 0; m < p; ++m) {
+            phi[m] = xm;
+            if (m + 1 < p) dphi[m + 1] = (m + 1) * xm / smax;
+            xm *= x;
+        }
+    } else {
+        double u = (b > a) ? 2.0 * (log(lam) - a) / (b - a) - 1.0 : 0.0;
+        double du = (b > a) ? 2.0 / ((b - a) * lam) : 0.0;
+        double t0 = 1.0, t1 = u, d0 = 0.0, d1 = 1.0;
+        phi[0] = 1.0; dphi[0] = 0.0;
+        if (p > 1) { phi[1] = u; dphi[1] = du; }
+        for (int m = 2; m < p; ++m) {
+            double t2 = 2.0 * u * t1 - t0;
+            double d2 = 2.0 * t1 + 2.0 * u * d1 - d0;
+            phi[m] = t2; dphi[m] = d2 * du;
+            t0 = t1; t1 = t2; d0 = d1; d1 = d2;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_setup(const void* G, int mode_fp64, int64_t d, int64_t dp, int k, int g, int p, int q,
+        double lo, double hi, int scale_by_trace, int basis,
+        double* scal, double* lam, double* lam_s, double* pinv, double* phi, double* dphi,
+        DevStatus* st)
+{
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int64_t e = threadIdx.x; e < (int64_t)k * d; e += 256) {
+        int j = (int)(e / d);
+        int64_t i = e % d;
+        int64_t off = (int64_t)j * dp * dp + i * dp + i;
+        s += mode_fp64 ? ((const double*)G)[off] : (double)((const float*)G)[off];
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    double tau = scale_by_trace ? red[0] / (double)d : 1.0;
+    scal[0] = tau;
+    for (int t = 0; t < q; ++t)
+        lam[t] = (q == 1) ? tau * lo : tau * lo * pow(hi / lo, (double)t / (double)(q - 1));
+    for (int i = 0; i < g; ++i) {
+        int idx = (g == 1) ? 0 : (2 * i * (q - 1) + (g - 1)) / (2 * (g - 1));
+        lam_s[i] = lam[idx];
+    }
+    double smin = lam_s[0], smax = lam_s[0];
+    for (int i = 1; i < g; ++i) { smin = fmin(smin, lam_s[i]); smax = fmax(smax, lam_s[i]); }
+    const double a = log(smin), b = log(smax);
+    double V[MAX_G][MAX_P], dummy[MAX_P];
+    for (int i = 0; i < g; ++i) basis_eval(basis, p, lam_s[i], a, b, smax, V[i], dummy);
+    // modified Gram-Schmidt with re-orthogonalisation: V = Q R
+    double Q[MAX_G][MAX_P], R[MAX_P][MAX_P];
+    for (int m = 0; m < p; ++m)
+        for (int l = 0; l < p; ++l) R[m][l] = 0.0;
+    bool ok = true;
+    for (int m = 0; m < p; ++m) {
+        double v[MAX_G];
+        for (int i = 0; i < g; ++i) v[i] = V[i][m];
+        for (int pass = 0; pass < 2; ++pass)
+            for (int l = 0; l < m; ++l) {
+                double dot = 0.0;
+                for (int i = 0; i < g; ++i) dot += Q[i][l] * v[i];
+                R[l][m] += dot;
+                for (int i = 0; i < g; ++i) v[i] -= dot * Q[i][l];
+            }
+        double nrm = 0.0;
+        for (int i = 0; i < g; ++i) nrm += v[i] * v[i];
+        nrm = sqrt(nrm);
+        if (!(nrm > 0.0)) { ok = false; nrm = 1.0; }
+        R[m][m] = nrm;
+        for (int i = 0; i < g; ++i) Q[i][m] = v[i] / nrm;
+    }
+    if (!ok) latch_error(st, PICHOL_ERR_INVALID_ARG, -1, -1, -1);
+    // P = R^{-1} Q^T: back substitution column by column
+    for (int i = 0; i < g; ++i)
+        for (int m = p - 1; m >= 0; --m) {
+            double v = Q[i][m];
+            for (int l = m + 1; l < p; ++l) v -= R[m][l] * pinv[l * g + i];
+            pinv[m * g + i] = v / R[m][m];
+        }
+    for (int t = 0; t < q; ++t) basis_eval(basis, p, lam[t], a, b, smax, phi + t * p, dphi + t * p);
+}
+
+template <typename T>
+static cudaError_t gram_impl(pichol_ctx* ctx, const T* X, const T* Y, cudaStream_t s)
+{
+    const pichol_config& c = ctx->cfg;
+    FoldOffs fo;
+    for (int j = 0; j <= c.k; ++j) fo.o[j] = ctx->offs[j];
+    T* G = (T*)ctx->G;
+    cudaError_t e = cudaMemsetAsync(G, 0, sizeof(T) * (size_t)c.k * ctx->dp * ctx->dp, s);
+    if (e != cudaSuccess) return e;
+    k_gram_simt<T><<<dim3((unsigned)ctx->ntiles, c.k), 256, 0, s>>>(X, c.d, ctx->dp, fo, G);
+    ctx->launches++;
+    e = cudaMemsetAsync(ctx->Bv, 0, sizeof(T) * (size_t)c.k * ctx->dp * c.c, s);
+    if (e != cudaSuccess) return e;
+    k_xty<T><<<dim3(ctx->nt, c.k), 256, 0, s>>>(X, Y, c.d, ctx->dp, c.c, fo, (T*)ctx->Bv);
+    k_yy<T><<<c.k, 256, 0, s>>>(Y, c.c, fo, ctx->yy, ctx->nfc);
+    k_setup<<<1, 256, 0, s>>>(G, c.mode == PICHOL_MODE_FP64, c.d, ctx->dp, c.k, c.g, ctx->p, c.q,
+                              c.lam_lo, c.lam_hi, c.scale_by_trace, c.basis, ctx->scal, ctx->lam,
+                              ctx->lam_s, ctx->pinv, ctx->phi, ctx->dphi, ctx->status);
+    const int64_t len = ctx->dp * c.c;
+    k_btrain<T><<<dim3((unsigned)((len + 255) / 256), c.k), 256, 0, s>>>((const T*)ctx->Bv, c.k, len,
+                                                                          (T*)ctx->Btr);
+    ctx->launches += 4;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram(pichol_ctx* ctx, const void* X, const void* Y, cudaStream_t s)
+{
+    if (ctx->cfg.mode == PICHOL_MODE_FP64)
+        return gram_impl<double>(ctx, (const double*)X, (const double*)Y, s);
+    return gram_impl<float>(ctx, (const float*)X, (const float*)Y, s);
+}
+
+}  // namespace pichol

@@ -1,0 +1,141 @@
+// Internal definitions shared by the CUDA translation units of libpichol.
+//
+// Data layout in device memory (all inside the caller's workspace):
+//  * The matrix side d is padded to dp = 64 * nt (nt = ceil(d / 64)).  Padded
+//    rows/columns of every Hessian are the identity, so the padded Cholesky
+//    factor is diag(L, I) and padded solution rows are zero.
+//  * Lower-triangular matrices (shifted Hessians, Cholesky factors and the
+//    polynomial coefficients of Algorithm 1) are stored tile-major: the 64 x 64
+//    tile (I, J), I >= J, is contiguous (row-major inside the tile) at tile
+//    index I (I + 1) / 2 + J.  This is the GPU analogue of the recursive
+//    vectorisation of Sec. 5: every tile is an aligned contiguous block.
+//  * Theta of fold f is [tile][m][64 x 64]: the (r+1) coefficient planes of one
+//    tile are adjacent, so the solve streams one tile's planes as one block.
+//  * Dense d x d Gram blocks G_j are row-major with leading dimension dp.
+//  * Right-hand sides and solutions are [system][dp][c] row-major.
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <cuda_runtime.h>
+#include <type_traits>
+
+#include "../../include/pichol.h"
+
+namespace pichol {
+
+constexpr int TB = 64;                   // tile side
+constexpr int TILE_ELEMS = TB * TB;
+constexpr int MAX_P = 8;                 // r + 1 <= 8
+constexpr int MAX_G = 32;                // sampled lambdas
+constexpr int MAX_K = 64;                // folds
+
+struct DevStatus {
+    int code;
+    int fold;
+    int index;
+    int unusable;
+    long long pivot;
+    long long pad[3];
+};
+
+__host__ __device__ inline int64_t tile_index(int I, int J) {
+    return (int64_t)I * (I + 1) / 2 + J;
+}
+__host__ __device__ inline int64_t num_tiles(int nt) {
+    return (int64_t)nt * (nt + 1) / 2;
+}
+
+// Recover (I, J), J <= I, from a lower-triangular tile index.
+__host__ __device__ inline void tile_coords(int64_t e, int& I, int& J) {
+    int i = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+    while ((int64_t)(i + 1) * (i + 2) / 2 <= e) ++i;
+    while ((int64_t)i * (i + 1) / 2 > e) --i;
+    I = i;
+    J = (int)(e - (int64_t)i * (i + 1) / 2);
+}
+
+#ifdef __CUDACC__
+// First error wins; the extra fields describe it.
+__device__ inline void latch_error(DevStatus* st, int code, int fold, int index, long long pivot) {
+    if (atomicCAS(&st->code, 0, code) == 0) {
+        st->fold = fold;
+        st->index = index;
+        st->pivot = pivot;
+    }
+}
+#endif
+
+// Byte offset of element (row, col) of a 64 x 64 plane of elements of `esz`
+// bytes in shared memory, with the 16-byte chunks of each row permuted by
+// XOR with (row & 7).  Row-owner 16-byte reads along a row and column-owner
+// scalar reads down a column are both free of bank conflicts.
+__host__ __device__ inline int swz_off(int row, int col, int esz) {
+    int byte = col * esz;
+    int chunk = byte >> 4;
+    return row * (TB * esz) + (((chunk ^ (row & 7)) << 4) | (byte & 15));
+}
+
+}  // namespace pichol
+
+// Host-side context.
+struct pichol_ctx {
+    pichol_config cfg;
+    int64_t dp;          // padded side
+    int nt;              // tiles per side
+    int64_t ntiles;      // lower tiles
+    int p;               // r + 1
+    int eb;              // element bytes of the mode's working type
+    int64_t offs[pichol::MAX_K + 1];
+    int64_t exact_batch; // lambdas per exact batch
+    int64_t nfac;        // factor slots in the factor buffer
+
+    char* ws;
+    size_t ws_bytes;
+    size_t need_bytes;
+
+    // workspace sections (device pointers once the workspace is set)
+    pichol::DevStatus* status;
+    double* scal;        // [0] tau
+    double* lam;         // q
+    double* lam_s;       // g
+    double* pinv;        // p x g
+    double* phi;         // q x p
+    double* dphi;        // q x p
+    void* G;             // k x dp x dp
+    void* Bv;            // k x dp x c
+    double* yy;          // k
+    void* Btr;           // k x dp x c
+    void* F;             // nfac x ntiles x TB^2
+    double* Linv;        // nfac x TB^2 (double)
+    void* Theta;         // k x ntiles x p x TB^2
+    void* Dinv;          // k x q x nt x TB^2
+    void* W;             // k x q x dp x c
+    void* U;             // 2 x k x q x dp x c floats: L~^T W as (hi, lo) (refinement)
+    void* Rres;          // k x q x dp x c (residual / correction)
+    int64_t* nfc;        // k: n_f * c
+    double* Epart;       // k x q x nt
+    double* E;           // k x q
+    int* flags;          // k x q x nt (per-tile diagonal checks: bit0 nonpositive)
+    float* dmax;         // k x q x nt max |diag| of the tile
+    float* dmin;         // k x q x nt min |diag| of the tile
+
+    bool have_hessian, have_factors, have_fit;
+    long long launches;
+};
+
+namespace pichol {
+
+// Launch helpers implemented per translation unit; each returns a cudaError_t.
+cudaError_t launch_gram(pichol_ctx* ctx, const void* X, const void* Y, cudaStream_t s);
+cudaError_t launch_factor(pichol_ctx* ctx, int count, int exact, int t0, cudaStream_t s);
+cudaError_t launch_fit(pichol_ctx* ctx, cudaStream_t s);
+cudaError_t launch_eval(pichol_ctx* ctx, int exact, int t0, int tcount, cudaStream_t s);
+cudaError_t launch_finish(pichol_ctx* ctx, double* E_out, int32_t* t_star, cudaStream_t s);
+cudaError_t launch_export_tiles(pichol_ctx* ctx, const void* tiles, int64_t plane_stride_elems,
+                                int64_t tile_stride_elems, double* out, cudaStream_t s);
+cudaError_t launch_export_hessian(pichol_ctx* ctx, int f, double* H, double* B, cudaStream_t s);
+cudaError_t launch_copy_w(pichol_ctx* ctx, void* W_out, cudaStream_t s);
+size_t solve_smem_bytes(int eb, int p, int64_t c);
+
+}  // namespace pichol

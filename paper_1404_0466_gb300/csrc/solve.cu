@@ -1,0 +1,1021 @@
+// Evaluation of the interpolated factor and the hold-out solves (Sec. 3.3,
+// last paragraph: L(lambda_t) = sum_m phi_m(lambda_t) Theta_m; Sec. 3.2: two
+// triangular solves; Sec. 3.1: hold-out error and the argmin over lambda).
+//
+//   k_diag_inv : for every (fold, lambda, tile row i) the diagonal tile
+//                L~_ii(lambda) is built from Theta and inverted; its diagonal is
+//                checked (an entry <= 0, or <= 1e3 eps max|diag|, makes the
+//                pair unusable and it is scored +inf).
+//   k_solve    : forward (L~ Z = B) and back (L~^T W = Z) block substitution
+//                for a group of LG lambdas of one fold per CTA.  Each
+//                off-diagonal tile's coefficient planes are copied into shared
+//                memory once (cp.async, XOR-swizzled) and evaluated there for
+//                all LG lambdas, so L~(lambda) never exists in global memory.
+//   k_resid    : refinement residual r = B - L~ (L~^T W) with double-float
+//                accumulation (error-free products, compensated sums).
+//   k_score    : E partials <W_I, (G_f W)_I> - 2 <Bv_I, W_I> per tile row.
+//   k_select   : E_f(t), mean over folds, first argmin.
+#include "internal.cuh"
+#include <cfloat>
+
+namespace pichol {
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int N = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    unsigned saddr = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Copy nplanes consecutive 64 x 64 planes (row stride `ld` elements inside a
+// plane, `pstride` elements between planes) into swizzled shared planes.
+template <typename T>
+__device__ __forceinline__ void stage_planes(unsigned char* sdst, const T* gsrc, int nplanes, int64_t ld,
+                                             int64_t pstride)
+{
+    constexpr int CPR = TB * (int)sizeof(T) / 16;   // 16-byte chunks per row
+    constexpr int PB = TILE_ELEMS * (int)sizeof(T); // bytes per plane
+    const int total = nplanes * TB * CPR;
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        const int pl = q / (TB * CPR), rem = q % (TB * CPR);
+        const int row = rem / CPR, ch = rem % CPR;
+        const T* g = gsrc + pl * pstride + row * ld + ch * (16 / (int)sizeof(T));
+        cp_async16(sdst + pl * PB + row * TB * (int)sizeof(T) + ((ch ^ (row & 7)) << 4), g);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T sm_elem(const unsigned char* plane, int row, int col)
+{
+    return *reinterpret_cast<const T*>(plane + swz_off(row, col, sizeof(T)));
+}
+
+// Value of system l's matrix at one element, from the staged coefficient
+// values v[m] (m < NP): sum_m w[l][m] v[m], evaluated as w0 v0 then FMAs in m.
+// In exact mode each system owns its own plane and the value is v[l].
+template <typename T, int NP, int LG, bool EXACT>
+__device__ __forceinline__ T eval_elem(const T (&w)[LG][NP > 0 ? NP : 1], const T* v, int l)
+{
+    if constexpr (EXACT) {
+        return v[l];
+    } else {
+        T s = w[l][0] * v[0];
+#pragma unroll
+        for (int m = 1; m < NP; ++m) s = fma(w[l][m], v[m], s);
+        return s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal tiles: build, check, invert.
+// ---------------------------------------------------------------------------
+struct DiagArgs {
+    const void* src;     // Theta (interp) or factor buffer (exact)
+    void* dinv;          // [f][t][i][64x64]
+    const double* phi;   // [t][p]
+    int* flags;          // [f][t][i]
+    float* dmax;
+    float* dmin;
+    int p, nt, q, t0, per;
+    int64_t ntiles, d;
+};
+
+template <typename T, bool EXACT>
+__global__ void __launch_bounds__(128)
+k_diag_inv(DiagArgs a)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    T (*Ls)[TB + 1] = reinterpret_cast<T (*)[TB + 1]>(dsm);
+    T (*Xs)[TB + 1] = reinterpret_cast<T (*)[TB + 1]>(dsm + sizeof(T) * TB * (TB + 1));
+    __shared__ float rmax[TB], rmin[TB];
+    __shared__ int rbad[TB];
+    const int i = blockIdx.x, t = a.t0 + blockIdx.y, f = blockIdx.z, tid = threadIdx.x;
+    const int64_t ti = tile_index(i, i);
+    T w[MAX_P];
+    const int np = EXACT ? 1 : a.p;
+    if constexpr (!EXACT) {
+        for (int m = 0; m < a.p; ++m) w[m] = (T)a.phi[(int64_t)t * a.p + m];
+    }
+    const T* base;
+    if constexpr (EXACT) {
+        const int pr = f * a.per + (t - a.t0);
+        base = (const T*)a.src + ((int64_t)pr * a.ntiles + ti) * TILE_ELEMS;
+    } else {
+        base = (const T*)a.src + ((int64_t)f * a.ntiles + ti) * a.p * TILE_ELEMS;
+    }
+    for (int e = tid; e < TILE_ELEMS; e += 128) {
+        const int r = e / TB, c = e % TB;
+        T v;
+        if constexpr (EXACT) {
+            v = base[e];
+        } else {
+            v = w[0] * base[e];
+            for (int m = 1; m < np; ++m) v = fma(w[m], base[(int64_t)m * TILE_ELEMS + e], v);
+        }
+        Ls[r][c] = (c <= r) ? v : T(0);
+        Xs[r][c] = T(0);
+    }
+    __syncthreads();
+    if (tid < TB) {
+        const T dv = Ls[tid][tid];
+        const bool valid = (int64_t)i * TB + tid < a.d;
+        rmax[tid] = valid ? (float)fabs((double)dv) : 0.0f;
+        rmin[tid] = valid ? (float)fabs((double)dv) : FLT_MAX;
+        rbad[tid] = (valid && !(dv > T(0))) ? 1 : 0;
+        // inverse column tid by forward substitution on e_tid
+        const int c = tid;
+        Xs[c][c] = T(1) / Ls[c][c];
+        for (int r = c + 1; r < TB; ++r) {
+            T s = T(0);
+            for (int qq = c; qq < r; ++qq) s = fma(Ls[r][qq], Xs[qq][c], s);
+            Xs[r][c] = -s / Ls[r][r];
+        }
+    }
+    __syncthreads();
+    T* out = (T*)a.dinv + (((int64_t)f * a.q + t) * a.nt + i) * TILE_ELEMS;
+    for (int e = tid; e < TILE_ELEMS; e += 128) out[e] = Xs[e / TB][e % TB];
+    if (tid == 0) {
+        float mx = 0.0f, mn = FLT_MAX;
+        int bad = 0;
+        for (int r = 0; r < TB; ++r) { mx = fmaxf(mx, rmax[r]); mn = fminf(mn, rmin[r]); bad |= rbad[r]; }
+        const int64_t o = ((int64_t)f * a.q + t) * a.nt + i;
+        a.flags[o] = bad;
+        a.dmax[o] = mx;
+        a.dmin[o] = mn;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block forward/back substitution with interpolate-on-load tiles.
+// ---------------------------------------------------------------------------
+struct SolveArgs {
+    const void* src;     // Theta [f][tile][p][64x64] or factors [pr][tile][64x64]
+    const void* dinv;    // [f][t][i][64x64]
+    const void* rhs;     // [f][dp][c] (per fold) or [f][t][dp][c] (per system)
+    void* zbuf;          // forward result [f][t][dp][c] (may alias out)
+    void* out;           // solution [f][t][dp][c]
+    const double* phi;   // [t][p]
+    int p, nt, q, t0, tcount, per, rhs_per_system;
+    int64_t ntiles, dp, c;
+};
+
+template <typename T, int LG, int CB, int NP, bool EXACT>
+struct SolveCfg {
+    static constexpr int VN = Vec16<T>::N;
+    static constexpr int CBP = (CB + VN - 1) / VN * VN;
+    static constexpr int NPL = (EXACT ? LG : NP) > LG ? (EXACT ? LG : NP) : LG;  // planes in a stage
+    static constexpr int PB = TILE_ELEMS * (int)sizeof(T);
+    static constexpr int STAGES = (2 * NPL * PB <= 128 * 1024) ? 2 : 1;
+    static constexpr int PLANE_BYTES = STAGES * NPL * PB;
+    static constexpr int ZS_BYTES = 2 * LG * TB * CBP * (int)sizeof(T);
+    static constexpr int R_BYTES = LG * TB * CBP * (int)sizeof(T);
+    static constexpr int SMEM = PLANE_BYTES + ZS_BYTES + R_BYTES;
+};
+
+template <typename T, int LG, int CB, int NP, bool EXACT>
+__global__ void __launch_bounds__(256)
+k_solve(SolveArgs a)
+{
+    using C = SolveCfg<T, LG, CB, NP, EXACT>;
+    constexpr int VN = C::VN, CBP = C::CBP, STAGES = C::STAGES;
+    constexpr int NPS = EXACT ? LG : NP;          // coefficient planes per tile
+    using V = typename Vec16<T>::type;
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* planes = smem;
+    T* Zs = reinterpret_cast<T*>(smem + C::PLANE_BYTES);            // [2][LG][64][CBP]
+    T* Rs = reinterpret_cast<T*>(smem + C::PLANE_BYTES + C::ZS_BYTES); // [LG][64][CBP]
+
+    const int f = blockIdx.y, tid = threadIdx.x;
+    const int r = tid & 63, kq = tid >> 6;
+    const int64_t c = a.c, dp = a.dp;
+    int tl[LG];
+    bool live[LG];
+#pragma unroll
+    for (int l = 0; l < LG; ++l) {
+        const int li = blockIdx.x * LG + l;
+        live[l] = li < a.tcount;
+        tl[l] = a.t0 + (live[l] ? li : a.tcount - 1);
+    }
+    T w[LG][NP > 0 ? NP : 1];
+    if constexpr (!EXACT) {
+#pragma unroll
+        for (int l = 0; l < LG; ++l)
+#pragma unroll
+            for (int m = 0; m < NP; ++m) w[l][m] = (T)a.phi[(int64_t)tl[l] * a.p + m];
+    }
+    const T* src = (const T*)a.src;
+    const T* dinv = (const T*)a.dinv;
+    const T* rhs = (const T*)a.rhs;
+    T* zb = (T*)a.zbuf;
+    T* out = (T*)a.out;
+    // zero the padding columns of the staged right-hand-side blocks once
+    for (int e = tid; e < 2 * LG * TB * CBP; e += 256)
+        if ((e % CBP) >= c) Zs[e] = T(0);
+    for (int e = tid; e < LG * TB * CBP; e += 256)
+        if ((e % CBP) >= c) Rs[e] = T(0);
+
+    auto sys_base = [&](int l) -> int64_t { return ((int64_t)f * a.q + tl[l]) * dp * c; };
+    // pointer to the coefficient planes of tile (I, J) (interp: shared; exact: system 0's)
+    auto tile_src = [&](int I, int J, int l) -> const T* {
+        const int64_t tix = tile_index(I, J);
+        if constexpr (EXACT) {
+            const int pr = f * a.per + (tl[l] - a.t0);
+            return src + ((int64_t)pr * a.ntiles + tix) * TILE_ELEMS;
+        } else {
+            return src + ((int64_t)f * a.ntiles + tix) * a.p * TILE_ELEMS;
+        }
+    };
+    auto issue_planes = [&](int I, int J, int stage) {
+        unsigned char* dst = planes + stage * C::NPL * C::PB;
+        if constexpr (EXACT) {
+#pragma unroll
+            for (int l = 0; l < LG; ++l) stage_planes<T>(dst + l * C::PB, tile_src(I, J, l), 1, TB, TILE_ELEMS);
+        } else {
+            stage_planes<T>(dst, tile_src(I, J, 0), NPS, TB, TILE_ELEMS);
+        }
+        cp_async_commit();
+    };
+    // right-hand-side block j of every live system from buffer `buf` into Zs[zi]
+    constexpr int ZPER = (LG * TB * CB + 255) / 256;
+    auto load_z_regs = [&](const T* buf, int j, T (&zr)[ZPER]) {
+#pragma unroll
+        for (int u = 0; u < ZPER; ++u) {
+            const int e = tid + 256 * u;
+            zr[u] = T(0);
+            if (e < LG * TB * c) {
+                const int l = e / (TB * (int)c), rem = e % (TB * (int)c);
+                zr[u] = buf[sys_base(l) + (int64_t)j * TB * c + rem];
+            }
+        }
+    };
+    auto store_z_regs = [&](int zi, const T (&zr)[ZPER]) {
+#pragma unroll
+        for (int u = 0; u < ZPER; ++u) {
+            const int e = tid + 256 * u;
+            if (e < LG * TB * c) {
+                const int l = e / (TB * (int)c), rem = e % (TB * (int)c);
+                const int kk = rem / (int)c, o = rem % (int)c;
+                Zs[((zi * LG + l) * TB + kk) * CBP + o] = zr[u];
+            }
+        }
+    };
+
+    T acc[LG][CBP];
+    // forward (UPPER = false) then back (UPPER = true)
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool back = pass == 1;
+        const T* zsrc = back ? out : zb;   // solved blocks read during the j loop
+#pragma unroll 1
+        for (int step = 0; step < a.nt; ++step) {
+            const int i = back ? a.nt - 1 - step : step;
+            const int nj = back ? a.nt - 1 - i : i;       // off-diagonal tiles in this row
+#pragma unroll
+            for (int l = 0; l < LG; ++l)
+#pragma unroll
+                for (int o = 0; o < CBP; ++o) acc[l][o] = T(0);
+            if (nj > 0) {
+                auto jof = [&](int jj) { return back ? i + 1 + jj : jj; };
+                T zr[ZPER];
+                if (STAGES == 2) {
+                    issue_planes(back ? jof(0) : i, back ? i : jof(0), 0);
+                    load_z_regs(zsrc, jof(0), zr);
+                    store_z_regs(0, zr);
+                }
+#pragma unroll 1
+                for (int jj = 0; jj < nj; ++jj) {
+                    const int j = jof(jj);
+                    const int stage = (STAGES == 2) ? (jj & 1) : 0;
+                    const int zi = jj & 1;
+                    if (STAGES == 2) {
+                        if (jj + 1 < nj) {
+                            const int jn = jof(jj + 1);
+                            issue_planes(back ? jn : i, back ? i : jn, (jj + 1) & 1);
+                            cp_async_wait<1>();
+                        } else {
+                            cp_async_wait<0>();
+                        }
+                    } else {
+                        issue_planes(back ? j : i, back ? i : j, 0);
+                        load_z_regs(zsrc, j, zr);
+                        store_z_regs(zi, zr);
+                        cp_async_wait<0>();
+                    }
+                    __syncthreads();
+                    if (STAGES == 2 && jj + 1 < nj) load_z_regs(zsrc, jof(jj + 1), zr);
+                    const unsigned char* pl = planes + stage * C::NPL * C::PB;
+                    const T* zs = Zs + zi * LG * TB * CBP;
+                    if (!back) {
+                        // row-owner: row r of tile (i, j), k in [16 kq, 16 kq + 16)
+#pragma unroll 1
+                        for (int ch = 0; ch < 16 / VN; ++ch) {
+                            const int kc = (kq * 16) / VN + ch;
+                            T v[NPS][VN];
+#pragma unroll
+                            for (int m = 0; m < NPS; ++m) {
+                                V x = *reinterpret_cast<const V*>(pl + m * C::PB + r * TB * (int)sizeof(T) +
+                                                                  ((kc ^ (r & 7)) << 4));
+                                memcpy(v[m], &x, 16);
+                            }
+#pragma unroll
+                            for (int e = 0; e < VN; ++e) {
+                                const int kk = kc * VN + e;
+                                T ve[NPS];
+#pragma unroll
+                                for (int m = 0; m < NPS; ++m) ve[m] = v[m][e];
+#pragma unroll
+                                for (int l = 0; l < LG; ++l) {
+                                    const T lv = eval_elem<T, NP, LG, EXACT>(w, ve, l);
+                                    const T* zrow = zs + (l * TB + kk) * CBP;
+#pragma unroll
+                                    for (int o = 0; o < CBP; o += VN) {
+                                        V z4 = *reinterpret_cast<const V*>(zrow + o);
+                                        T zz[VN];
+                                        memcpy(zz, &z4, 16);
+#pragma unroll
+                                        for (int u = 0; u < VN; ++u) acc[l][o + u] = fma(lv, zz[u], acc[l][o + u]);
+                                    }
+                                }
+                            }
+                        }
+                    } else {
+                        // column-owner: column r of tile (j, i), k (its rows) in [16 kq, 16 kq + 16)
+#pragma unroll 4
+                        for (int kk = kq * 16; kk < kq * 16 + 16; ++kk) {
+                            T ve[NPS];
+#pragma unroll
+                            for (int m = 0; m < NPS; ++m) ve[m] = sm_elem<T>(pl + m * C::PB, kk, r);
+#pragma unroll
+                            for (int l = 0; l < LG; ++l) {
+                                const T lv = eval_elem<T, NP, LG, EXACT>(w, ve, l);
+                                const T* zrow = zs + (l * TB + kk) * CBP;
+#pragma unroll
+                                for (int o = 0; o < CBP; o += VN) {
+                                    V z4 = *reinterpret_cast<const V*>(zrow + o);
+                                    T zz[VN];
+                                    memcpy(zz, &z4, 16);
+#pragma unroll
+                                    for (int u = 0; u < VN; ++u) acc[l][o + u] = fma(lv, zz[u], acc[l][o + u]);
+                                }
+                            }
+                        }
+                    }
+                    if (STAGES == 2 && jj + 1 < nj) store_z_regs((jj + 1) & 1, zr);
+                    __syncthreads();
+                }
+            }
+            // reduce the four k-quarters: (((a3 + a2) + a1) + a0)
+#pragma unroll 1
+            for (int qq = 3; qq >= 1; --qq) {
+                if (kq == qq) {
+#pragma unroll
+                    for (int l = 0; l < LG; ++l)
+#pragma unroll
+                        for (int o = 0; o < CBP; ++o) {
+                            T* dst = Rs + (l * TB + r) * CBP + o;
+                            *dst = (qq == 3) ? acc[l][o] : *dst + acc[l][o];
+                        }
+                }
+                __syncthreads();
+            }
+            // right-hand side of the diagonal solve: rhs_i - (sum of off-diagonal products)
+            if (kq == 0) {
+#pragma unroll
+                for (int l = 0; l < LG; ++l)
+#pragma unroll
+                    for (int o = 0; o < CBP; ++o) {
+                        if (o < c) {
+                            T b;
+                            const int64_t row = (int64_t)i * TB + r;
+                            if (back) b = zb[sys_base(l) + row * c + o];
+                            else if (a.rhs_per_system) b = rhs[sys_base(l) + row * c + o];
+                            else b = rhs[(int64_t)f * dp * c + row * c + o];
+                            Rs[(l * TB + r) * CBP + o] = b - (Rs[(l * TB + r) * CBP + o] + acc[l][o]);
+                        }
+                    }
+            }
+            // stage the LG diagonal inverses
+#pragma unroll
+            for (int l = 0; l < LG; ++l)
+                stage_planes<T>(planes + l * C::PB, dinv + (((int64_t)f * a.q + tl[l]) * a.nt + i) * TILE_ELEMS, 1,
+                                TB, TILE_ELEMS);
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncthreads();
+            if (tid < LG * TB) {
+                const int l = tid >> 6, rr = tid & 63;
+                T x[CBP];
+#pragma unroll
+                for (int o = 0; o < CBP; ++o) x[o] = T(0);
+                const unsigned char* pl = planes + l * C::PB;
+                const T* rsl = Rs + l * TB * CBP;
+                if (!back) {
+#pragma unroll 1
+                    for (int kc = 0; kc < TB / VN; ++kc) {
+                        V dv4 = *reinterpret_cast<const V*>(pl + rr * TB * (int)sizeof(T) + ((kc ^ (rr & 7)) << 4));
+                        T dv[VN];
+                        memcpy(dv, &dv4, 16);
+#pragma unroll
+                        for (int e = 0; e < VN; ++e) {
+                            const T* zrow = rsl + (kc * VN + e) * CBP;
+#pragma unroll
+                            for (int o = 0; o < CBP; ++o) x[o] = fma(dv[e], zrow[o], x[o]);
+                        }
+                    }
+                } else {
+#pragma unroll 2
+                    for (int kk = 0; kk < TB; ++kk) {
+                        const T dv = sm_elem<T>(pl, kk, rr);
+                        const T* zrow = rsl + kk * CBP;
+#pragma unroll
+                        for (int o = 0; o < CBP; ++o) x[o] = fma(dv, zrow[o], x[o]);
+                    }
+                }
+                if (live[l]) {
+                    T* dstb = (back ? out : zb) + sys_base(l) + ((int64_t)i * TB + rr) * c;
+#pragma unroll
+                    for (int o = 0; o < CBP; ++o)
+                        if (o < c) dstb[o] = x[o];
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Refinement residual r = B - L~ (L~^T W), double-float accumulation.
+//   pass 0: u_i = sum_{j >= i} L~_ji^T W_j      -> (uhi, ulo)
+//   pass 1: r_i = B_i - sum_{j <= i} L~_ij u_j  -> R (rounded to float)
+// Products are split error-free (p = a*b, e = fma(a, b, -p)); sums use TwoSum.
+// ---------------------------------------------------------------------------
+struct ResidArgs {
+    const float* theta;
+    const float* W;      // pass 0 input
+    const float* uhi;    // pass 1 input
+    const float* ulo;
+    float* ohi;          // pass 0 outputs
+    float* olo;
+    const float* B;      // pass 1: per-fold right-hand side [f][dp][c]
+    float* R;            // pass 1 output [f][t][dp][c]
+    const double* phi;
+    int p, nt, q, t0, tcount;
+    int64_t ntiles, dp, c;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+template <int LG, int CB, int NP, int PASS>
+__global__ void __launch_bounds__(256)
+k_resid(ResidArgs a)
+{
+    constexpr int CBP = (CB + 3) / 4 * 4;
+    constexpr int PB = TILE_ELEMS * 4;
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* planes = smem;                                        // NP planes
+    float* Zh = reinterpret_cast<float*>(smem + NP * PB);                // [LG][64][CBP]
+    float* Zl = Zh + LG * TB * CBP;                                      // [LG][64][CBP]
+    double* Rd = reinterpret_cast<double*>(Zl + LG * TB * CBP);          // [LG][64][CBP]
+    const int i = blockIdx.x, f = blockIdx.z, tid = threadIdx.x;
+    const int r = tid & 63, kq = tid >> 6;
+    const int64_t c = a.c, dp = a.dp;
+    int tl[LG];
+    bool live[LG];
+#pragma unroll
+    for (int l = 0; l < LG; ++l) {
+        const int li = blockIdx.y * LG + l;
+        live[l] = li < a.tcount;
+        tl[l] = a.t0 + (live[l] ? li : a.tcount - 1);
+    }
+    float w[LG][NP];
+#pragma unroll
+    for (int l = 0; l < LG; ++l)
+#pragma unroll
+        for (int m = 0; m < NP; ++m) w[l][m] = (float)a.phi[(int64_t)tl[l] * a.p + m];
+    for (int e = tid; e < LG * TB * CBP; e += 256) { Zh[e] = 0.0f; Zl[e] = 0.0f; }
+    float sh[LG][CBP], sl[LG][CBP];
+#pragma unroll
+    for (int l = 0; l < LG; ++l)
+#pragma unroll
+        for (int o = 0; o < CBP; ++o) { sh[l][o] = 0.0f; sl[l][o] = 0.0f; }
+    const int jlo = PASS == 0 ? i : 0, jhi = PASS == 0 ? a.nt - 1 : i;
+#pragma unroll 1
+    for (int j = jlo; j <= jhi; ++j) {
+        __syncthreads();
+        const int64_t tix = PASS == 0 ? tile_index(j, i) : tile_index(i, j);
+        stage_planes<float>(planes, a.theta + ((int64_t)f * a.ntiles + tix) * a.p * TILE_ELEMS, NP, TB, TILE_ELEMS);
+        cp_async_commit();
+        for (int e = tid; e < LG * TB * c; e += 256) {
+            const int l = e / (TB * (int)c), rem = e % (TB * (int)c);
+            const int kk = rem / (int)c, o = rem % (int)c;
+            const int64_t g = ((int64_t)f * a.q + tl[l]) * dp * c + (int64_t)j * TB * c + rem;
+            if (PASS == 0) {
+                Zh[(l * TB + kk) * CBP + o] = a.W[g];
+            } else {
+                Zh[(l * TB + kk) * CBP + o] = a.uhi[g];
+                Zl[(l * TB + kk) * CBP + o] = a.ulo[g];
+            }
+        }
+        cp_async_wait<0>();
+        __syncthreads();
+#pragma unroll 2
+        for (int kk = kq * 16; kk < kq * 16 + 16; ++kk) {
+            float ve[NP];
+#pragma unroll
+            for (int m = 0; m < NP; ++m)
+                ve[m] = PASS == 0 ? sm_elem<float>(planes + m * PB, kk, r)   // L~_ji[kk][r]: transposed use
+                                  : sm_elem<float>(planes + m * PB, r, kk);  // L~_ij[r][kk]
+#pragma unroll
+            for (int l = 0; l < LG; ++l) {
+                float lv = w[l][0] * ve[0];
+#pragma unroll
+                for (int m = 1; m < NP; ++m) lv = fmaf(w[l][m], ve[m], lv);
+                const float* zh = Zh + (l * TB + kk) * CBP;
+                const float* zl = Zl + (l * TB + kk) * CBP;
+#pragma unroll
+                for (int o = 0; o < CBP; ++o) {
+                    const float pp = lv * zh[o];
+                    const float pe = fmaf(lv, zh[o], -pp);
+                    float s, e;
+                    two_sum(sh[l][o], pp, s, e);
+                    sh[l][o] = s;
+                    sl[l][o] += e + pe + (PASS == 1 ? lv * zl[o] : 0.0f);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // combine the four k-quarters in double
+#pragma unroll 1
+    for (int qq = 3; qq >= 0; --qq) {
+        if (kq == qq) {
+#pragma unroll
+            for (int l = 0; l < LG; ++l)
+#pragma unroll
+                for (int o = 0; o < CBP; ++o) {
+                    const double v = (double)sh[l][o] + (double)sl[l][o];
+                    double* dst = Rd + (l * TB + r) * CBP + o;
+                    *dst = (qq == 3) ? v : *dst + v;
+                }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < LG * TB * c; e += 256) {
+        const int l = e / (TB * (int)c), rem = e % (TB * (int)c);
+        if (!live[l]) continue;
+        const int rr = rem / (int)c, o = rem % (int)c;
+        const double v = Rd[(l * TB + rr) * CBP + o];
+        const int64_t g = ((int64_t)f * a.q + tl[l]) * dp * c + (int64_t)i * TB * c + rem;
+        if (PASS == 0) {
+            const float hi = (float)v;
+            a.ohi[g] = hi;
+            a.olo[g] = (float)(v - (double)hi);
+        } else {
+            const double b = (double)a.B[(int64_t)f * dp * c + (int64_t)i * TB * c + rem];
+            a.R[g] = (float)(b - v);
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_axpy(T* __restrict__ y, const T* __restrict__ x, int64_t n)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        y[e] += x[e];
+}
+
+// ---------------------------------------------------------------------------
+// Hold-out score partials: for tile row I and LG lambdas of fold f,
+//   part = sum_{rows in I} sum_o W[row][o] ((G_f W)[row][o] - 2 Bv_f[row][o])
+// with G_f = X_f^T X_f (the fold's own Gram block, dense).  Products in the
+// working type per 64-column tile, everything above that in double.
+// ---------------------------------------------------------------------------
+struct ScoreArgs {
+    const void* G;       // [j][dp][dp]
+    const void* Bv;      // [j][dp][c]
+    const void* W;       // [f][t][dp][c]
+    double* Epart;       // [f][t][I]
+    int nt, q, t0, tcount;
+    int64_t dp, c;
+};
+
+template <typename T, int LG, int CB>
+__global__ void __launch_bounds__(256)
+k_score(ScoreArgs a)
+{
+    constexpr int VN = Vec16<T>::N;
+    constexpr int CBP = (CB + VN - 1) / VN * VN;
+    constexpr int PB = TILE_ELEMS * (int)sizeof(T);
+    using V = typename Vec16<T>::type;
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* plane = smem;
+    T* Zs = reinterpret_cast<T*>(smem + PB);                 // [LG][64][CBP]
+    double* Ud = reinterpret_cast<double*>(Zs + LG * TB * CBP); // [LG][64][CBP]
+    __shared__ double red[256];
+    const int I = blockIdx.x, f = blockIdx.z, tid = threadIdx.x;
+    const int r = tid & 63, kq = tid >> 6;
+    const int64_t c = a.c, dp = a.dp;
+    int tl[LG];
+    bool live[LG];
+#pragma unroll
+    for (int l = 0; l < LG; ++l) {
+        const int li = blockIdx.y * LG + l;
+        live[l] = li < a.tcount;
+        tl[l] = a.t0 + (live[l] ? li : a.tcount - 1);
+    }
+    const T* G = (const T*)a.G + (int64_t)f * dp * dp;
+    const T* Wt = (const T*)a.W;
+    for (int e = tid; e < LG * TB * CBP; e += 256) Zs[e] = T(0);
+    double tot[LG][CBP];
+#pragma unroll
+    for (int l = 0; l < LG; ++l)
+#pragma unroll
+        for (int o = 0; o < CBP; ++o) tot[l][o] = 0.0;
+#pragma unroll 1
+    for (int J = 0; J < a.nt; ++J) {
+        __syncthreads();
+        stage_planes<T>(plane, G + (int64_t)I * TB * dp + (int64_t)J * TB, 1, dp, 0);
+        cp_async_commit();
+        for (int e = tid; e < LG * TB * c; e += 256) {
+            const int l = e / (TB * (int)c), rem = e % (TB * (int)c);
+            const int kk = rem / (int)c, o = rem % (int)c;
+            Zs[(l * TB + kk) * CBP + o] = Wt[((int64_t)f * a.q + tl[l]) * dp * c + (int64_t)J * TB * c + rem];
+        }
+        cp_async_wait<0>();
+        __syncthreads();
+        T acc[LG][CBP];
+#pragma unroll
+        for (int l = 0; l < LG; ++l)
+#pragma unroll
+            for (int o = 0; o < CBP; ++o) acc[l][o] = T(0);
+#pragma unroll 1
+        for (int ch = 0; ch < 16 / VN; ++ch) {
+            const int kc = (kq * 16) / VN + ch;
+            V x = *reinterpret_cast<const V*>(plane + r * TB * (int)sizeof(T) + ((kc ^ (r & 7)) << 4));
+            T gv[VN];
+            memcpy(gv, &x, 16);
+#pragma unroll
+            for (int e = 0; e < VN; ++e) {
+                const int kk = kc * VN + e;
+#pragma unroll
+                for (int l = 0; l < LG; ++l) {
+                    const T* zrow = Zs + (l * TB + kk) * CBP;
+#pragma unroll
+                    for (int o = 0; o < CBP; ++o) acc[l][o] = fma(gv[e], zrow[o], acc[l][o]);
+                }
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < LG; ++l)
+#pragma unroll
+            for (int o = 0; o < CBP; ++o) tot[l][o] += (double)acc[l][o];
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int qq = 3; qq >= 0; --qq) {
+        if (kq == qq) {
+#pragma unroll
+            for (int l = 0; l < LG; ++l)
+#pragma unroll
+                for (int o = 0; o < CBP; ++o) {
+                    double* dst = Ud + (l * TB + r) * CBP + o;
+                    *dst = (qq == 3) ? tot[l][o] : *dst + tot[l][o];
+                }
+        }
+        __syncthreads();
+    }
+    // per-lambda dot products over this tile row
+    const T* Bv = (const T*)a.Bv + (int64_t)f * dp * c;
+#pragma unroll 1
+    for (int l = 0; l < LG; ++l) {
+        double s = 0.0;
+        if (tid < TB) {
+            const int64_t row = (int64_t)I * TB + tid;
+            const T* wr = Wt + ((int64_t)f * a.q + tl[l]) * dp * c + row * c;
+            for (int o = 0; o < c; ++o) {
+                const double wv = (double)wr[o];
+                s += wv * (Ud[(l * TB + tid) * CBP + o] - 2.0 * (double)Bv[row * c + o]);
+            }
+        }
+        red[tid] = s;
+        __syncthreads();
+        for (int wdt = 128; wdt > 0; wdt >>= 1) {
+            if (tid < wdt) red[tid] += red[tid + wdt];
+            __syncthreads();
+        }
+        if (tid == 0 && live[l]) a.Epart[((int64_t)f * a.q + tl[l]) * a.nt + I] = red[0];
+        __syncthreads();
+    }
+}
+
+// E_f(t) = (yy_f + sum_I part) / (n_f c), +inf if unusable; Ebar; first argmin.
+__global__ void __launch_bounds__(256)
+k_select(const double* __restrict__ Epart, const int* __restrict__ flags, const float* __restrict__ dmax,
+         const float* __restrict__ dmin, const double* __restrict__ yy, const int64_t* __restrict__ nf_c,
+         int k, int q, int nt, double* __restrict__ E_out, double* __restrict__ Eint, int32_t* __restrict__ t_star,
+         DevStatus* st)
+{
+    __shared__ double Ebar[4096];
+    __shared__ int nbad[256];
+    int bad_count = 0;
+    const double thr_rel = 1e3 * DBL_EPSILON;
+    for (int t = threadIdx.x; t < q; t += 256) {
+        double sum = 0.0;
+        for (int f = 0; f < k; ++f) {
+            const int64_t o = ((int64_t)f * q + t) * nt;
+            int bad = 0;
+            float mx = 0.0f, mn = FLT_MAX;
+            double s = yy[f];
+            for (int i = 0; i < nt; ++i) {
+                bad |= flags[o + i];
+                mx = fmaxf(mx, dmax[o + i]);
+                mn = fminf(mn, dmin[o + i]);
+                s += Epart[o + i];
+            }
+            if ((double)mn <= thr_rel * (double)mx) bad = 1;
+            const double e = bad ? INFINITY : s / (double)nf_c[f];
+            bad_count += bad;
+            E_out[(int64_t)f * q + t] = e;
+            Eint[(int64_t)f * q + t] = e;
+            sum += e;
+        }
+        Ebar[t] = sum / (double)k;
+    }
+    nbad[threadIdx.x] = bad_count;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int best = -1;
+        double bv = INFINITY;
+        int nb = 0;
+        for (int t = 0; t < q; ++t) {
+            if (isfinite(Ebar[t]) && Ebar[t] < bv) { bv = Ebar[t]; best = t; }
+        }
+        for (int u = 0; u < 256; ++u) nb += nbad[u];
+        *t_star = best;
+        st->unusable = nb;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host-side launch plumbing
+// ---------------------------------------------------------------------------
+static int pick_cb(int64_t c) { return c <= 4 ? 4 : (c <= 12 ? 12 : 32); }
+
+// Dynamic shared memory the solve kernel needs for a mode (element bytes eb),
+// p coefficient planes and c outputs; mirrors SolveCfg.
+size_t solve_smem_bytes(int eb, int p, int64_t c)
+{
+    const int LG = 2, cb = pick_cb(c), vn = 16 / eb;
+    const int cbp = (cb + vn - 1) / vn * vn;
+    const int np_interp = p > LG ? p : LG;
+    const size_t pb = (size_t)TILE_ELEMS * eb;
+    const size_t stages = (2 * np_interp * pb <= 128 * 1024) ? 2 : 1;
+    return stages * np_interp * pb + (size_t)3 * LG * TB * cbp * eb;
+}
+
+template <typename T, int LG, int CB, int NP, bool EXACT>
+static cudaError_t run_solve(pichol_ctx* ctx, const SolveArgs& sa, cudaStream_t s)
+{
+    using C = SolveCfg<T, LG, CB, NP, EXACT>;
+    static bool done = false;
+    if (!done) {
+        cudaError_t e = cudaFuncSetAttribute(k_solve<T, LG, CB, NP, EXACT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e != cudaSuccess) return e;
+        done = true;
+    }
+    dim3 grid((unsigned)((sa.tcount + LG - 1) / LG), ctx->cfg.k);
+    k_solve<T, LG, CB, NP, EXACT><<<grid, 256, C::SMEM, s>>>(sa);
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
+template <typename T, int LG, int CB, bool EXACT>
+static cudaError_t solve_np(pichol_ctx* ctx, const SolveArgs& sa, cudaStream_t s)
+{
+    if (EXACT) return run_solve<T, LG, CB, 1, EXACT>(ctx, sa, s);
+    switch (ctx->p) {
+    case 1: return run_solve<T, LG, CB, 1, EXACT>(ctx, sa, s);
+    case 2: return run_solve<T, LG, CB, 2, EXACT>(ctx, sa, s);
+    case 3: return run_solve<T, LG, CB, 3, EXACT>(ctx, sa, s);
+    case 4: return run_solve<T, LG, CB, 4, EXACT>(ctx, sa, s);
+    case 5: return run_solve<T, LG, CB, 5, EXACT>(ctx, sa, s);
+    case 6: return run_solve<T, LG, CB, 6, EXACT>(ctx, sa, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T, bool EXACT>
+static cudaError_t solve_dispatch(pichol_ctx* ctx, const SolveArgs& sa, cudaStream_t s)
+{
+    constexpr int LG = 2;
+    switch (pick_cb(ctx->cfg.c)) {
+    case 4: return solve_np<T, LG, 4, EXACT>(ctx, sa, s);
+    case 12: return solve_np<T, LG, 12, EXACT>(ctx, sa, s);
+    default: return solve_np<T, LG, 32, EXACT>(ctx, sa, s);
+    }
+}
+
+template <typename T, int LG, int CB>
+static cudaError_t run_score(pichol_ctx* ctx, const ScoreArgs& sc, cudaStream_t s)
+{
+    constexpr int VN = Vec16<T>::N;
+    constexpr int CBP = (CB + VN - 1) / VN * VN;
+    const int smem = TILE_ELEMS * (int)sizeof(T) + LG * TB * CBP * (int)sizeof(T) + LG * TB * CBP * 8;
+    static bool done = false;
+    if (!done) {
+        cudaError_t e = cudaFuncSetAttribute(k_score<T, LG, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        done = true;
+    }
+    dim3 grid(ctx->nt, (unsigned)((sc.tcount + LG - 1) / LG), ctx->cfg.k);
+    k_score<T, LG, CB><<<grid, 256, smem, s>>>(sc);
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t score_dispatch(pichol_ctx* ctx, const ScoreArgs& sc, cudaStream_t s)
+{
+    switch (pick_cb(ctx->cfg.c)) {
+    case 4: return run_score<T, 2, 4>(ctx, sc, s);
+    case 12: return run_score<T, 2, 12>(ctx, sc, s);
+    default: return run_score<T, 1, 32>(ctx, sc, s);
+    }
+}
+
+template <int LG, int CB, int NP, int PASS>
+static cudaError_t run_resid(pichol_ctx* ctx, const ResidArgs& ra, cudaStream_t s)
+{
+    constexpr int CBP = (CB + 3) / 4 * 4;
+    const int smem = NP * TILE_ELEMS * 4 + 2 * LG * TB * CBP * 4 + LG * TB * CBP * 8;
+    static bool done = false;
+    if (!done) {
+        cudaError_t e = cudaFuncSetAttribute(k_resid<LG, CB, NP, PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        done = true;
+    }
+    dim3 grid(ctx->nt, (unsigned)((ra.tcount + LG - 1) / LG), ctx->cfg.k);
+    k_resid<LG, CB, NP, PASS><<<grid, 256, smem, s>>>(ra);
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
+template <int LG, int CB, int PASS>
+static cudaError_t resid_np(pichol_ctx* ctx, const ResidArgs& ra, cudaStream_t s)
+{
+    switch (ctx->p) {
+    case 1: return run_resid<LG, CB, 1, PASS>(ctx, ra, s);
+    case 2: return run_resid<LG, CB, 2, PASS>(ctx, ra, s);
+    case 3: return run_resid<LG, CB, 3, PASS>(ctx, ra, s);
+    case 4: return run_resid<LG, CB, 4, PASS>(ctx, ra, s);
+    case 5: return run_resid<LG, CB, 5, PASS>(ctx, ra, s);
+    case 6: return run_resid<LG, CB, 6, PASS>(ctx, ra, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int PASS>
+static cudaError_t resid_dispatch(pichol_ctx* ctx, const ResidArgs& ra, cudaStream_t s)
+{
+    switch (pick_cb(ctx->cfg.c)) {
+    case 4: return resid_np<2, 4, PASS>(ctx, ra, s);
+    case 12: return resid_np<2, 12, PASS>(ctx, ra, s);
+    default: return resid_np<1, 32, PASS>(ctx, ra, s);
+    }
+}
+
+template <typename T, bool EXACT>
+static cudaError_t eval_impl(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s)
+{
+    const pichol_config& cf = ctx->cfg;
+    DiagArgs da;
+    da.src = EXACT ? ctx->F : ctx->Theta;
+    da.dinv = ctx->Dinv;
+    da.phi = ctx->phi;
+    da.flags = ctx->flags;
+    da.dmax = ctx->dmax;
+    da.dmin = ctx->dmin;
+    da.p = ctx->p;
+    da.nt = ctx->nt;
+    da.q = cf.q;
+    da.t0 = t0;
+    da.per = (int)ctx->exact_batch;
+    da.ntiles = ctx->ntiles;
+    da.d = cf.d;
+    const int dsm = 2 * (int)sizeof(T) * TB * (TB + 1);
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t ea = cudaFuncSetAttribute(k_diag_inv<T, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm);
+        if (ea != cudaSuccess) return ea;
+        attr_done = true;
+    }
+    k_diag_inv<T, EXACT><<<dim3(ctx->nt, tcount, cf.k), 128, dsm, s>>>(da);
+    ctx->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+
+    SolveArgs sa;
+    sa.src = da.src;
+    sa.dinv = ctx->Dinv;
+    sa.rhs = ctx->Btr;
+    sa.zbuf = ctx->W;
+    sa.out = ctx->W;
+    sa.phi = ctx->phi;
+    sa.p = ctx->p;
+    sa.nt = ctx->nt;
+    sa.q = cf.q;
+    sa.t0 = t0;
+    sa.tcount = tcount;
+    sa.per = (int)ctx->exact_batch;
+    sa.rhs_per_system = 0;
+    sa.ntiles = ctx->ntiles;
+    sa.dp = ctx->dp;
+    sa.c = cf.c;
+    e = solve_dispatch<T, EXACT>(ctx, sa, s);
+    if (e != cudaSuccess) return e;
+
+    if constexpr (std::is_same<T, float>::value && !EXACT) {
+        for (int it = 0; it < cf.refine_steps; ++it) {
+            ResidArgs ra;
+            ra.theta = (const float*)ctx->Theta;
+            ra.W = (const float*)ctx->W;
+            ra.uhi = (const float*)ctx->U;
+            ra.ulo = (const float*)ctx->U + (int64_t)cf.k * cf.q * ctx->dp * cf.c;
+            ra.ohi = (float*)ctx->U;
+            ra.olo = (float*)ctx->U + (int64_t)cf.k * cf.q * ctx->dp * cf.c;
+            ra.B = (const float*)ctx->Btr;
+            ra.R = (float*)ctx->Rres;
+            ra.phi = ctx->phi;
+            ra.p = ctx->p;
+            ra.nt = ctx->nt;
+            ra.q = cf.q;
+            ra.t0 = t0;
+            ra.tcount = tcount;
+            ra.ntiles = ctx->ntiles;
+            ra.dp = ctx->dp;
+            ra.c = cf.c;
+            if ((e = resid_dispatch<0>(ctx, ra, s)) != cudaSuccess) return e;
+            if ((e = resid_dispatch<1>(ctx, ra, s)) != cudaSuccess) return e;
+            SolveArgs sc = sa;
+            sc.rhs = ctx->Rres;
+            sc.rhs_per_system = 1;
+            sc.zbuf = ctx->Rres;
+            sc.out = ctx->Rres;
+            if ((e = solve_dispatch<T, EXACT>(ctx, sc, s)) != cudaSuccess) return e;
+            const int64_t n = (int64_t)cf.k * cf.q * ctx->dp * cf.c;
+            k_axpy<float><<<1024, 256, 0, s>>>((float*)ctx->W, (const float*)ctx->Rres, n);
+            ctx->launches++;
+        }
+    }
+
+    ScoreArgs sc;
+    sc.G = ctx->G;
+    sc.Bv = ctx->Bv;
+    sc.W = ctx->W;
+    sc.Epart = ctx->Epart;
+    sc.nt = ctx->nt;
+    sc.q = cf.q;
+    sc.t0 = t0;
+    sc.tcount = tcount;
+    sc.dp = ctx->dp;
+    sc.c = cf.c;
+    return score_dispatch<T>(ctx, sc, s);
+}
+
+cudaError_t launch_eval(pichol_ctx* ctx, int exact, int t0, int tcount, cudaStream_t s)
+{
+    if (ctx->cfg.mode == PICHOL_MODE_FP64)
+        return exact ? eval_impl<double, true>(ctx, t0, tcount, s) : eval_impl<double, false>(ctx, t0, tcount, s);
+    return exact ? eval_impl<float, true>(ctx, t0, tcount, s) : eval_impl<float, false>(ctx, t0, tcount, s);
+}
+
+cudaError_t launch_finish(pichol_ctx* ctx, double* E_out, int32_t* t_star, cudaStream_t s)
+{
+    const pichol_config& cf = ctx->cfg;
+    k_select<<<1, 256, 0, s>>>(ctx->Epart, ctx->flags, ctx->dmax, ctx->dmin, ctx->yy, ctx->nfc, cf.k, cf.q, ctx->nt,
+                               E_out, ctx->E, t_star, ctx->status);
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_w(pichol_ctx* ctx, void* W_out, cudaStream_t s)
+{
+    const pichol_config& cf = ctx->cfg;
+    const size_t eb = (size_t)ctx->eb;
+    return cudaMemcpy2DAsync(W_out, (size_t)cf.d * cf.c * eb, ctx->W, (size_t)ctx->dp * cf.c * eb,
+                             (size_t)cf.d * cf.c * eb, (size_t)cf.k * cf.q, cudaMemcpyDeviceToDevice, s);
+}
+
+}  // namespace pichol

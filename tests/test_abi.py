@@ -1,0 +1,106 @@
+"""Host-side checks of the C ABI: the library builds, loads without a GPU,
+exports every symbol include/pichol.h declares, and validates arguments."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1404_0466_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return binding.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pichol.h")).read()
+    return sorted(set(re.findall(r"PICHOL_API\s+[\w\s\*]*?\b(pichol_\w+)\s*\(", src)))
+
+
+def test_header_declares_every_binding_export():
+    assert _declared() == sorted(binding.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def _cfg(L, **kw):
+    cfg = binding.Config()
+    L.pichol_config_default(ctypes.byref(cfg))
+    base = dict(n=1000, d=100, c=3, k=5, g=4, r=2, q=31)
+    base.update(kw)
+    for k, v in base.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def _create(L, cfg):
+    h = ctypes.c_void_p()
+    rc = L.pichol_create(ctypes.byref(cfg), ctypes.byref(h))
+    return rc, h
+
+
+def test_defaults(L):
+    cfg = binding.Config()
+    L.pichol_config_default(ctypes.byref(cfg))
+    assert cfg.lam_lo == 1e-3 and cfg.lam_hi == 1e1 and cfg.scale_by_trace == 1
+    assert cfg.mode == binding.PICHOL_MODE_FP64 and cfg.basis == binding.PICHOL_BASIS_MONO
+    assert cfg.gram_passes == 3 and cfg.refine_steps == 0
+
+
+@pytest.mark.parametrize("bad", [
+    dict(k=1), dict(k=65), dict(n=3, k=5), dict(d=0), dict(d=16385), dict(c=0), dict(c=33),
+    dict(q=0), dict(q=4097), dict(r=6), dict(r=-1), dict(g=2, r=2), dict(g=40, q=50), dict(g=8, q=5),
+    dict(lam_lo=0.0), dict(lam_lo=2.0, lam_hi=1.0), dict(basis=7), dict(mode=5),
+    dict(refine_steps=9), dict(gram_passes=2), dict(exact_batch=99), dict(scale_by_trace=2),
+])
+def test_create_rejects_bad_config(L, bad):
+    rc, h = _create(L, _cfg(L, **bad))
+    assert rc == 1 and not h.value
+
+
+def test_create_rejects_nonzero_reserved(L):
+    cfg = _cfg(L)
+    cfg.reserved[2] = 1
+    rc, h = _create(L, cfg)
+    assert rc == 1
+
+
+def test_workspace_size_and_state_errors(L):
+    rc, h = _create(L, _cfg(L, d=130, mode=binding.PICHOL_MODE_MIXED, refine_steps=1))
+    assert rc == 0 and h.value
+    n = ctypes.c_size_t()
+    assert L.pichol_workspace_size(h, ctypes.byref(n)) == 0
+    # d = 130 pads to 192 = 3 tiles; the dense Gram blocks alone are 5 * 192^2 floats
+    assert n.value >= 5 * 192 * 192 * 4
+    # calls before a workspace is attached fail without touching the GPU
+    assert L.pichol_factor_samples(h, None) == 4
+    assert L.pichol_hessian(h, None, None, None) == 1
+    # a misaligned or short workspace is refused before any CUDA call
+    assert L.pichol_set_workspace(h, ctypes.c_void_p(0x1001), n.value) == 4
+    assert L.pichol_set_workspace(h, ctypes.c_void_p(0x1000), n.value - 1) == 4
+    assert L.pichol_launch_count(h) == 0
+    L.pichol_destroy(h)
+
+
+def test_workspace_grows_with_exact_batch(L):
+    sizes = []
+    for eb in (1, 31):
+        rc, h = _create(L, _cfg(L, exact_batch=eb))
+        n = ctypes.c_size_t()
+        L.pichol_workspace_size(h, ctypes.byref(n))
+        sizes.append(n.value)
+        L.pichol_destroy(h)
+    assert sizes[1] > sizes[0]
+
+
+def test_status_strings(L):
+    assert L.pichol_status_string(0) == b"ok"
+    assert b"positive definite" in L.pichol_status_string(2)

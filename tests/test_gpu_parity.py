@@ -1,0 +1,209 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances:
+  * double-precision mode: factor entries and coefficients within 1e-10 of the
+    matrix scale, hold-out errors within 1e-10 relative, identical argmin;
+  * mixed mode: hold-out errors within 1e-4 relative; the selected lambda must
+    be the oracle's, or one whose oracle score is within 1e-4 of the oracle's
+    minimum (the argmin is decided in each side's own precision).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1404_0466_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+MIXED_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+    from paper_1404_0466_gb300 import build
+    build.build()
+    return torch
+
+
+def _ctx(prob, **kw):
+    from paper_1404_0466_gb300 import binding
+    n, d = prob.X.shape
+    c = prob.Y.shape[1]
+    return binding.Context(n=n, d=d, c=c, **kw)
+
+
+def _dev(torch, a, mode):
+    dt = torch.float64 if mode == "fp64" else torch.float32
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dt)
+
+
+def _check_selected(t_gpu, ref, tol):
+    if t_gpu == ref.t_star:
+        return
+    Eb = ref.Ebar
+    assert 0 <= t_gpu < len(Eb) and np.isfinite(Eb[t_gpu]), (t_gpu, ref.t_star)
+    assert Eb[t_gpu] <= Eb[ref.t_star] * (1 + tol), (t_gpu, ref.t_star, Eb[t_gpu], Eb[ref.t_star])
+
+
+# ---------------------------------------------------------------------------
+# double-precision mode, the small case (n=2048, d=256, k=5, g=4, r=2, q=31)
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def fp64_small(torch_mod):
+    torch = torch_mod
+    cfg = synth.FP64_SMALL
+    prob = synth.fp64_small()
+    ref = oracle.cv(prob.X, prob.Y, k=cfg["k"], g=cfg["g"], r=cfg["r"], q=cfg["q"], basis="mono", keep=True)
+    ctx = _ctx(prob, k=cfg["k"], g=cfg["g"], r=cfg["r"], q=cfg["q"], basis="mono", mode="fp64")
+    X, Y = _dev(torch, prob.X, "fp64"), _dev(torch, prob.Y, "fp64")
+    ctx.hessian(X, Y)
+    ctx.factor_samples()
+    ctx.fit()
+    out = ctx.eval_holdout(want_w=True)
+    torch.cuda.synchronize()
+    return dict(prob=prob, ref=ref, ctx=ctx, out=out, X=X, Y=Y)
+
+
+def test_fp64_hessian_blocks(fp64_small):
+    ctx, ref = fp64_small["ctx"], fp64_small["ref"]
+    for f in range(5):
+        H, B = ctx.export_hessian(f)
+        H, B = H.cpu().numpy(), B.cpu().numpy()
+        assert np.max(np.abs(H - ref.H[f])) <= 1e-12 * np.max(np.abs(ref.H[f]))
+        assert np.max(np.abs(B - ref.B[f])) <= 1e-12 * np.max(np.abs(ref.B[f]))
+
+
+def test_fp64_lambda_grid(fp64_small):
+    lam = fp64_small["ctx"].lambdas().cpu().numpy()
+    np.testing.assert_allclose(lam, fp64_small["ref"].lam, rtol=1e-13)
+
+
+def test_fp64_sampled_factors(fp64_small):
+    ctx, ref = fp64_small["ctx"], fp64_small["ref"]
+    for f in range(5):
+        for s in range(4):
+            L = ctx.export_factor(f, s).cpu().numpy()
+            Lr = ref.factors[(f, s)]
+            assert np.max(np.abs(L - Lr)) <= FP64_TOL * np.max(np.abs(Lr)), (f, s)
+
+
+def test_fp64_coefficients(fp64_small):
+    ctx, ref = fp64_small["ctx"], fp64_small["ref"]
+    d = 256
+    for f in range(5):
+        Th = ctx.export_theta(f).cpu().numpy()
+        for m in range(3):
+            Tr = oracle.unvec_lower(ref.theta[f][m], d)
+            scale = max(np.max(np.abs(oracle.unvec_lower(ref.theta[f][mm], d))) for mm in range(3))
+            assert np.max(np.abs(Th[m] - Tr)) <= 1e-9 * scale, (f, m)
+
+
+def test_fp64_holdout_and_selection(fp64_small):
+    out, ref = fp64_small["out"], fp64_small["ref"]
+    E = out.E.cpu().numpy()
+    np.testing.assert_allclose(E, ref.E, rtol=FP64_TOL, atol=0)
+    assert int(out.t_star.cpu().item()) == ref.t_star
+
+
+def test_fp64_solutions(fp64_small):
+    out, ref = fp64_small["out"], fp64_small["ref"]
+    W = out.W.cpu().numpy()
+    for (f, t), Wr in list(ref.W.items())[::17]:
+        assert np.max(np.abs(W[f, t] - Wr)) <= 1e-9 * np.max(np.abs(Wr)), (f, t)
+
+
+def test_fp64_device_status_clean(fp64_small):
+    info = fp64_small["ctx"].info()
+    assert info.code == 0 and info.unusable == int(fp64_small["ref"].unusable.sum())
+    assert fp64_small["ctx"].launch_count() > 10
+
+
+def test_fp64_exact_cv(fp64_small, torch_mod):
+    prob = fp64_small["prob"]
+    ref = oracle.cv(prob.X, prob.Y, k=5, g=4, r=2, q=31, exact=True)
+    ctx = _ctx(prob, k=5, g=4, r=2, q=31, mode="fp64", exact_batch=8)
+    ctx.hessian(fp64_small["X"], fp64_small["Y"])
+    out = ctx.eval_holdout_exact()
+    np.testing.assert_allclose(out.E.cpu().numpy(), ref.E, rtol=FP64_TOL)
+    assert int(out.t_star.cpu().item()) == ref.t_star
+    assert ctx.info().code == 0
+
+
+# ---------------------------------------------------------------------------
+# ragged shapes and edge cases, double precision
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,d,c,k,g,r,q,basis", [
+    (517, 100, 1, 3, 3, 2, 7, "mono"),        # d not a multiple of 64, uneven folds, one output
+    (300, 37, 4, 7, 5, 3, 11, "cheb_log"),    # d smaller than one tile
+    (900, 129, 12, 2, 2, 1, 5, "cheb_log"),   # two folds, 3 tiles with a 1-wide edge
+    (260, 64, 2, 4, 1, 0, 1, "mono"),         # a single lambda, constant polynomial
+])
+def test_fp64_ragged_shapes(torch_mod, n, d, c, k, g, r, q, basis):
+    torch = torch_mod
+    prob = synth.spectral_gaussian(n, d, c, seed=100 + d)
+    ref = oracle.cv(prob.X, prob.Y, k=k, g=g, r=r, q=q, basis=basis)
+    ctx = _ctx(prob, k=k, g=g, r=r, q=q, basis=basis, mode="fp64")
+    out = ctx.run(_dev(torch, prob.X, "fp64"), _dev(torch, prob.Y, "fp64"))
+    E = out.E.cpu().numpy()
+    np.testing.assert_allclose(E, ref.E, rtol=1e-9)
+    assert int(out.t_star.cpu().item()) == ref.t_star
+    ex = ctx.eval_holdout_exact()
+    refx = oracle.cv(prob.X, prob.Y, k=k, g=g, r=r, q=q, exact=True)
+    np.testing.assert_allclose(ex.E.cpu().numpy(), refx.E, rtol=1e-9)
+
+
+def test_nan_input_latches_not_spd(torch_mod):
+    torch = torch_mod
+    prob = synth.spectral_gaussian(200, 20, 2, seed=5)
+    X = prob.X.copy()
+    X[3, 7] = np.nan
+    ctx = _ctx(prob, k=4, g=3, r=2, q=5, mode="fp64")
+    ctx.hessian(_dev(torch, X, "fp64"), _dev(torch, prob.Y, "fp64"))
+    ctx.factor_samples()
+    info = ctx.info()
+    assert info.code == 2 and 0 <= info.fold < 4 and 0 <= info.pivot < 20
+    ctx.clear_status()
+    assert ctx.info().code == 0
+
+
+# ---------------------------------------------------------------------------
+# mixed precision
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def mixed_small(torch_mod):
+    # the mixed case's generator and method parameters at n = 4096, d = 200
+    prob = synth.mixed_ecc(n=4096, d=200)
+    ref = oracle.cv(prob.X, prob.Y, k=5, g=6, r=3, q=101, basis="cheb_log")
+    return prob, ref
+
+
+@pytest.mark.parametrize("refine", [0, 1])
+def test_mixed_holdout_and_selection(torch_mod, mixed_small, refine):
+    torch = torch_mod
+    prob, ref = mixed_small
+    ctx = _ctx(prob, k=5, g=6, r=3, q=101, basis="cheb_log", mode="mixed", refine_steps=refine)
+    out = ctx.run(_dev(torch, prob.X, "mixed"), _dev(torch, prob.Y, "mixed"))
+    E = out.E.cpu().numpy()
+    rel = np.max(np.abs(E - ref.E) / ref.E)
+    assert rel <= MIXED_TOL, rel
+    _check_selected(int(out.t_star.cpu().item()), ref, MIXED_TOL)
+    assert ctx.info().code == 0
+
+
+def test_mixed_exact_cv(torch_mod, mixed_small):
+    torch = torch_mod
+    prob, _ = mixed_small
+    ref = oracle.cv(prob.X, prob.Y, k=5, g=6, r=3, q=101, exact=True, lam_idx=range(0, 101, 10))
+    ctx = _ctx(prob, k=5, g=6, r=3, q=101, basis="cheb_log", mode="mixed", exact_batch=17)
+    ctx.hessian(_dev(torch, prob.X, "mixed"), _dev(torch, prob.Y, "mixed"))
+    out = ctx.eval_holdout_exact()
+    E = out.E.cpu().numpy()
+    cols = list(range(0, 101, 10))
+    rel = np.max(np.abs(E[:, cols] - ref.E[:, cols]) / ref.E[:, cols])
+    assert rel <= MIXED_TOL, rel

@@ -1,0 +1,439 @@
+#!/usr/bin/env python
+"""Benchmark of piCholesky k-fold cross-validation on GB300.
+
+One step = the whole hot path on one batch of synthetic input: normal-equation
+blocks, exact factors at the g sampled lambdas, the polynomial fit, and the
+interpolated solves, refinement and hold-out scores at all q lambdas, ending
+with the selected lambda.  The metric is fold x lambda hold-out evaluations per
+second (k * q per step).
+
+Own arm (default): the C ABI on cuda:LOCAL_RANK with X, Y resident in HBM.
+Also reported: the same metric end to end from pinned host buffers (e2e),
+exact-Cholesky cross-validation with the same kernels on the same GPU, the
+error of the hold-out scores against the FP64 oracle on a sample, per-stage
+device times, the roofline of the dominant kernel, SM clocks during the timed
+region, and the oracle timed on the host cores (cpu_baseline).
+
+--impl reference: the FP64 CPU oracle as it stands, one fold of the same
+workload per step, on this machine's cores (rank 0 only).
+
+Multi-GPU (torchrun): every rank runs its own replica of the problem (the
+method's units are independent); the timed region is bracketed by barriers
+and the maximum time over ranks is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fold×λ hold-out evals/sec vs exact-Cholesky CV on same GB300; err vs FP64"
+
+WORKLOADS = {
+    # n = 32768, d = 2048, c = 10 ECC targets of a 10-cluster mixture, k = 5, g = 6, r = 3, q = 101
+    "mixed_ecc": dict(gen="mixed_ecc", cfg="MIXED_ECC", mode="mixed", basis="cheb_log", refine=1),
+    # n = 2048, d = 256, c = 10, k = 5, g = 4, r = 2, q = 31, double precision
+    "fp64_small": dict(gen="fp64_small", cfg="FP64_SMALL", mode="fp64", basis="mono", refine=0),
+}
+
+# GB300: 152 SMs x 128 FP32 lanes x 2 flops at the 2070 MHz maximum SM clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["own", "reference"], default="own")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="mixed_ecc")
+    ap.add_argument("--refine", type=int, default=None, help="refinement steps (default: the workload's)")
+    ap.add_argument("--no-exact", action="store_true", help="skip the exact-Cholesky comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle sample (cpu_baseline, error)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="warm-up + steps only, for ncu")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(name):
+    from paper_1404_0466_gb300 import synth
+    w = WORKLOADS[name]
+    cfg = dict(getattr(synth, w["cfg"]))
+    prob = getattr(synth, w["gen"])()
+    return w, cfg, prob
+
+
+def describe(name, w, cfg, refine):
+    return (f"{name}: n={cfg['n']} d={cfg['d']} c={cfg['c']} k={cfg['k']} g={cfg['g']} r={cfg['r']} "
+            f"q={cfg['q']} basis={w['basis']} mode={w['mode']} refine={refine}")
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                smax.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per stage (for the roofline of the dominant kernel)
+# ---------------------------------------------------------------------------
+def stage_work(cfg, mode, refine):
+    n, d, c, k, g, r, q = (cfg[x] for x in ("n", "d", "c", "k", "g", "r", "q"))
+    p = r + 1
+    D = d * (d + 1) // 2
+    nt = -(-d // 64)
+    eb = 8 if mode == "fp64" else 4
+    upd = sum((m * (m + 1) // 2) for m in range(nt)) * 2 * 64 ** 3 * k * g
+    return {
+        # SYRK of every fold block: n d (d + 1) flops
+        "gram": ("flop", n * d * (d + 1)),
+        # trailing updates of k g blocked factorisations (lower tiles, 2 b^3 per tile update)
+        "chol_update": ("flop", upd),
+        # read g factors, write p coefficient sets, per fold (lower triangles)
+        "fit": ("byte", k * (g + p) * D * eb),
+        # per fold and lambda: two triangular solves (2 d^2 c) + the factor built twice (4 p D)
+        "solve": ("flop", k * q * (2 * d * d * c + 4 * p * D) * (1 + refine)),
+        # per fold and lambda: <W, G W>: 2 d^2 c
+        "score": ("flop", k * q * 2 * d * d * c),
+    }
+
+
+def roofline(stage_ms, cfg, mode, refine, steps, peaks):
+    work = stage_work(cfg, mode, refine)
+    dom = max(stage_ms.items(), key=lambda kv: kv[1][0])
+    name, (ms, launches) = dom
+    info = {"kernel_stage": name, "stage_ms_per_step": ms / steps, "launches_per_step": launches / steps}
+    if name not in work or ms <= 0:
+        info.update({"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None})
+        return info
+    kind, amount = work[name]
+    per_launch = amount / max(1, launches / steps)
+    avg_s = ms / 1e3 / max(1, launches)
+    if kind == "flop":
+        achieved = per_launch / avg_s / 1e12
+        peak = FP32_PEAK_TFLOPS if mode == "mixed" else None
+        info.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x 2070 MHz (derived)"})
+    else:
+        achieved = per_launch / avg_s / 1e9
+        peak = peaks.get("hbm_gbs")
+        info.update({"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)"})
+    info["frac"] = (achieved / peak) if peak else None
+    info["traffic"] = None
+    return info
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "note": "fallback"}
+
+
+# ---------------------------------------------------------------------------
+# oracle sample: error vs FP64 and cpu_baseline
+# ---------------------------------------------------------------------------
+def oracle_sample(prob, cfg, w, E_gpu, t_star):
+    import numpy as np
+
+    import oracle
+    q = cfg["q"]
+    idx = sorted(set([0, q // 4, q // 2, (3 * q) // 4, q - 1] + ([t_star] if t_star >= 0 else [])))
+    tm = {}
+    t0 = time.perf_counter()
+    ref = oracle.cv(prob.X, prob.Y, k=cfg["k"], g=cfg["g"], r=cfg["r"], q=q, lo=cfg["lo"], hi=cfg["hi"],
+                    basis=w["basis"], folds=[0], lam_idx=idx, timings=tm)
+    wall = time.perf_counter() - t0
+    Eo = ref.E[0, idx]
+    Eg = E_gpu[0, idx]
+    err = float(np.max(np.abs(Eg - Eo) / np.abs(Eo)))
+    # one fold of the method = fixed part (Hessian, factors, fit) + q evaluations
+    per_eval = tm["eval"] / max(1, tm["n_eval"])
+    fold_s = tm["setup"] + tm["fold"] + q * per_eval
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {
+        "err_vs_fp64": {"max_rel_E": err, "sample": f"fold 0, grid indices {idx}"},
+        "cpu_baseline": {"value": q / fold_s, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                         "sample": (f"fold 0 of the workload: Hessian, {cfg['g']} factors and fit "
+                                    f"({tm['setup'] + tm['fold']:.1f} s) and {len(idx)} of {q} lambdas "
+                                    f"({per_eval:.2f} s each), extrapolated to the fold's {q} lambdas; "
+                                    f"{wall:.1f} s of CPU work")},
+    }
+
+
+# ---------------------------------------------------------------------------
+# the reference arm: the oracle as it stands
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    w, cfg, prob = workload(args.workload)
+    k, q = cfg["k"], cfg["q"]
+    refine = w["refine"] if args.refine is None else args.refine
+
+    def step(i):
+        f = i % k
+        oracle.cv(prob.X, prob.Y, k=k, g=cfg["g"], r=cfg["r"], q=q, lo=cfg["lo"], hi=cfg["hi"],
+                  basis=w["basis"], folds=[f])
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(args.warmup + i)
+    sec = time.perf_counter() - t0
+    value = args.steps * q / sec
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": describe(args.workload, w, cfg, refine),
+                   "reference_step": f"one fold (all {q} lambdas) of the FP64 CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                         "sample": f"one fold per step, {q} lambdas each"},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# own arm
+# ---------------------------------------------------------------------------
+def run_own(args):
+    import numpy as np
+    import torch
+
+    from paper_1404_0466_gb300 import binding, build
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    build.build()
+    w, cfg, prob = workload(args.workload)
+    refine = w["refine"] if args.refine is None else args.refine
+    k, q = cfg["k"], cfg["q"]
+    dt = torch.float64 if w["mode"] == "fp64" else torch.float32
+    Xh = torch.from_numpy(prob.X).to(dt).pin_memory()
+    Yh = torch.from_numpy(prob.Y).to(dt).pin_memory()
+    X = Xh.to(dev)
+    Y = Yh.to(dev)
+    params = dict(n=cfg["n"], d=cfg["d"], c=cfg["c"], k=k, g=cfg["g"], r=cfg["r"], q=q, lam_lo=cfg["lo"],
+                  lam_hi=cfg["hi"], basis=w["basis"], mode=w["mode"], refine_steps=refine)
+    ctx = binding.Context(**params)
+    out = ctx._outputs(False)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.run(X, Y, out=out)
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    info = ctx.info()
+    if info.code != 0:
+        raise RuntimeError(f"device status after warm-up: {binding.STATUS.get(info.code)}")
+    if args.profile:
+        for _ in range(args.steps):
+            step()
+        torch.cuda.synchronize()
+        return 0
+
+    # ---- timed region: K steps, inputs resident in HBM -------------------
+    ctx.set_timing(args.steps * 400 + 64)
+    ctx.stage_times()
+    n0 = ctx.launch_count()
+    sampler = ClockSampler()
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    launches = ctx.launch_count() - n0
+    stages, complete = ctx.stage_times()
+    ctx.set_timing(0)
+    if pg is not None:
+        t = torch.tensor([ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps * k * q / (ms / 1e3)
+    E = out[0].cpu().numpy()
+    t_star = int(out[1].cpu().item())
+    info = ctx.info()
+
+    # ---- end to end: pinned host in, scores and argmin out -----------------
+    e2e = None
+    if not args.no_e2e:
+        Eh = torch.empty((k, q), dtype=torch.float64).pin_memory()
+        th = torch.empty((1,), dtype=torch.int32).pin_memory()
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            X.copy_(Xh, non_blocking=True)
+            Y.copy_(Yh, non_blocking=True)
+            step()
+            Eh.copy_(out[0], non_blocking=True)
+            th.copy_(out[1], non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ems = e0.elapsed_time(e1)
+        if pg is not None:
+            t = torch.tensor([ems], device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * args.steps * k * q / (ems / 1e3), "unit": "evals/s",
+               "h2d_bytes_per_step": Xh.numel() * Xh.element_size() + Yh.numel() * Yh.element_size(),
+               "d2h_bytes_per_step": Eh.numel() * 8 + 4, "ms_per_step": ems / args.steps}
+
+    # ---- exact-Cholesky CV with the same kernels ---------------------------
+    exact = None
+    if not args.no_exact and rank == 0:
+        del ctx
+        torch.cuda.empty_cache()
+        ctxe = binding.Context(**params)
+        oute = ctxe._outputs(False)
+        ctxe.hessian(X, Y)
+        ctxe.eval_holdout_exact(out=oute)
+        torch.cuda.synchronize()
+        reps = 2
+        e0.record(stream)
+        for _ in range(reps):
+            ctxe.hessian(X, Y)
+            ctxe.eval_holdout_exact(out=oute)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        xms = e0.elapsed_time(e1) / reps
+        Ex = oute[0].cpu().numpy()
+        tx = int(oute[1].cpu().item())
+        exact = {"value": k * q / (xms / 1e3), "unit": "evals/s", "ms_per_step": xms,
+                 "t_star": tx, "t_star_pichol": t_star,
+                 "min_E_exact": float(np.mean(Ex, axis=0)[tx]),
+                 "min_E_pichol": float(np.mean(E, axis=0)[t_star]) if t_star >= 0 else None,
+                 "selected_lambda_equal": tx == t_star}
+        ctxe.close()
+
+    if rank != 0:
+        return 0
+    sample = None if args.no_cpu else oracle_sample(prob, cfg, w, E, t_star)
+    peaks = load_peaks()
+    stage_ms = {s: v for s, v in stages.items() if v[1] > 0}
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if w["mode"] == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": describe(args.workload, w, cfg, refine),
+                   "l2": "inputs larger than L2 (X is %d MB)" % (Xh.numel() * Xh.element_size() // 2 ** 20),
+                   "parallelism": f"replicas x{world}"},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "roofline": roofline(stage_ms, cfg, w["mode"], refine, args.steps, peaks),
+        "stages_ms_per_step": {s: round(v[0] / args.steps, 4) for s, v in stage_ms.items()},
+        "stage_timing_complete": complete,
+        "clocks": clocks,
+        "exact_cv": exact,
+        "speedup_vs_exact": (value / world / exact["value"]) if exact else None,
+        "device_status": binding.STATUS.get(info.code), "unusable_pairs": info.unusable,
+    }
+    if sample:
+        line["cpu_baseline"] = sample["cpu_baseline"]
+        line["err_vs_fp64"] = sample["err_vs_fp64"]
+    print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_own(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -132,7 +132,9 @@ PICHOL_API pichol_status pichol_set_workspace(pichol_ctx* ctx, void* workspace, 
  * yy_j = ||Y_j||_F^2; then tau = tr(sum_j G_j)/d, the lambda grid, and the
  * training right-hand sides B_f = sum_{j != f} Bv_j.  X, Y: device, row-major,
  * n x d and n x c, double (FP64 mode) or float (mixed mode).  X and Y are only
- * read during this call's kernels.
+ * read during this call's kernels.  A grid that is not finite and positive, or
+ * sampled lambdas that give a rank-deficient V, latch PICHOL_ERR_INVALID_ARG
+ * on the device (e.g. a NaN in X with scale_by_trace set).
  */
 PICHOL_API pichol_status pichol_hessian(pichol_ctx* ctx, const void* X, const void* Y, void* stream);
 
@@ -196,7 +198,26 @@ PICHOL_API pichol_status pichol_clear_status(pichol_ctx* ctx, void* stream);
 /* Number of kernel launches this context has enqueued since creation. */
 PICHOL_API int64_t pichol_launch_count(const pichol_ctx* ctx);
 
-/* Frees the host-side context.  The workspace stays the caller's. */
+/* Stage timing (for benchmarks): with max_launches > 0 the context records a
+ * pair of CUDA events around each of its next max_launches kernel launches on
+ * the launching stream; 0 turns timing off and frees the events.  Creating
+ * events is the only resource this takes. */
+PICHOL_API pichol_status pichol_set_timing(pichol_ctx* ctx, int32_t max_launches);
+
+/* Synchronises `stream`, then sums the recorded launch durations per stage
+ * into ms[i] and counts them in launches[i] for the first n_stages stages, and
+ * restarts recording.  Stages, in order: 0 Gram blocks, 1 X^T Y, 2 set-up
+ * (grid, V^+), 3 factor input, 4 diagonal-tile Cholesky, 5 panel solve,
+ * 6 trailing update, 7 polynomial fit, 8 diagonal inverses, 9 interpolated
+ * solve, 10 refinement residual, 11 hold-out score, 12 selection, 13 other.
+ * Returns PICHOL_ERR_STATE if timing is off and PICHOL_ERR_WORKSPACE if more
+ * launches happened than events were reserved (the sums then cover the first
+ * max_launches launches only). */
+PICHOL_API pichol_status pichol_stage_times(pichol_ctx* ctx, double* ms, int64_t* launches, int32_t n_stages,
+                                            void* stream);
+
+/* Frees the host-side context (and its timing events).  The workspace stays
+ * the caller's. */
 PICHOL_API void pichol_destroy(pichol_ctx* ctx);
 
 /* Short text for a status code (static storage). */

@@ -333,14 +333,21 @@ class CVResult:
 
 def cv(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e1,
        basis: str = BASIS_MONO, exact: bool = False, scale_by_trace: bool = True,
-       folds=None, lam_idx=None, keep: bool = False) -> CVResult:
+       folds=None, lam_idx=None, keep: bool = False, timings: dict | None = None) -> CVResult:
     """k-fold CV of ridge regression over q lambdas, piCholesky (default) or
     exact Cholesky at every lambda (``exact=True``, ``Chol`` of Sec. 6.2).
 
     ``folds`` restricts the work to some folds and ``lam_idx`` to some grid
     indices (entries outside are NaN); the grid, the samples and the fit are
-    unchanged by either.
+    unchanged by either.  If ``timings`` is a dict, wall-clock seconds are
+    added to its keys "setup" (grid scale), "fold" (per-fold Hessian, factors
+    and fit) and "eval" (per-lambda work), and "n_eval" counts evaluations.
     """
+    import time as _time
+    tm = timings if timings is not None else {}
+    for key in ("setup", "fold", "eval", "n_eval"):
+        tm.setdefault(key, 0.0)
+    _t0 = _time.perf_counter()
     X, Y = _f64(X), _f64(Y)
     n, d = X.shape
     c = Y.shape[1]
@@ -353,12 +360,14 @@ def cv(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e
     sidx = sample_indices(q, g) if not exact else list(range(q))
     folds = list(range(k)) if folds is None else list(folds)
     tsel = list(range(q)) if lam_idx is None else list(lam_idx)
+    tm["setup"] += _time.perf_counter() - _t0
 
     E = np.full((k, q), np.nan)
     bad = np.zeros((k, q), dtype=bool)
     res = CVResult(lam=lam, sample_idx=sidx, E=E, Ebar=None, t_star=-1, unusable=bad, tau=tau)
 
     for f in folds:
+        _tf = _time.perf_counter()
         r0, r1 = offs[f], offs[f + 1]
         nv = r1 - r0
         Hf, Bf = normal_blocks(X, Y, r0, r1)
@@ -366,12 +375,16 @@ def cv(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e
         if keep:
             res.H[f], res.B[f] = Hf, Bf
         if exact:
+            tm["fold"] += _time.perf_counter() - _tf
             for t in tsel:
+                _te = _time.perf_counter()
                 L = cholesky(Hf + lam[t] * np.eye(d))
                 W = solve_factored(L, Bf)
                 E[f, t] = holdout_sse(Xv, Yv, W) / (nv * c)
                 if keep:
                     res.W[(f, t)] = W
+                tm["eval"] += _time.perf_counter() - _te
+                tm["n_eval"] += 1
             continue
         # Algorithm 1, steps 1-2: exact factors at the samples, stacked as rows of T
         lam_s = lam[sidx]
@@ -388,16 +401,21 @@ def cv(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e
             res.theta[f] = Theta
         # evaluation at every grid lambda, two triangular solves, hold-out error
         Phi = basis_values(basis, lam, lam_s, p)
+        tm["fold"] += _time.perf_counter() - _tf
         for t in tsel:
+            _te = _time.perf_counter()
+            tm["n_eval"] += 1
             Lt = unvec_lower(eval_poly(Phi[t], Theta), d)
             if diag_unusable(np.diag(Lt)):
                 bad[f, t] = True
                 E[f, t] = np.inf
+                tm["eval"] += _time.perf_counter() - _te
                 continue
             W = solve_factored(Lt, Bf)
             E[f, t] = holdout_sse(Xv, Yv, W) / (nv * c)
             if keep:
                 res.W[(f, t)] = W
+            tm["eval"] += _time.perf_counter() - _te
     if len(folds) == k:
         res.Ebar = E.mean(axis=0)
         res.t_star = argmin_first(res.Ebar)

@@ -27,8 +27,10 @@ EXPORTS = [
     "pichol_hessian", "pichol_factor_samples", "pichol_fit", "pichol_eval_holdout",
     "pichol_eval_holdout_exact", "pichol_get_lambdas", "pichol_export_factor", "pichol_export_theta",
     "pichol_export_hessian", "pichol_get_info", "pichol_clear_status", "pichol_launch_count",
-    "pichol_destroy", "pichol_status_string",
+    "pichol_destroy", "pichol_status_string", "pichol_set_timing", "pichol_stage_times",
 ]
+STAGES = ["gram", "xty", "setup", "chol_init", "chol_diag", "chol_panel", "chol_update", "fit",
+          "diag_inv", "solve", "resid", "score", "select", "misc"]
 
 
 class Config(ctypes.Structure):
@@ -82,6 +84,9 @@ def lib():
         "pichol_launch_count": ([vp], i64),
         "pichol_destroy": ([vp], None),
         "pichol_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "pichol_set_timing": ([vp, i32], ctypes.c_int),
+        "pichol_stage_times": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32, vp],
+                               ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -228,6 +233,19 @@ class Context:
 
     def clear_status(self, stream=None):
         _check(lib().pichol_clear_status(self._h, ctypes.c_void_p(_stream_ptr(stream))), "pichol_clear_status")
+
+    def set_timing(self, max_launches: int):
+        _check(lib().pichol_set_timing(self._h, max_launches), "pichol_set_timing")
+
+    def stage_times(self, stream=None):
+        """{stage: (total ms, launches)} since the last call; needs set_timing."""
+        n = len(STAGES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        rc = lib().pichol_stage_times(self._h, ms, cnt, n, ctypes.c_void_p(_stream_ptr(stream)))
+        if rc not in (0, 4):
+            _check(rc, "pichol_stage_times")
+        return {STAGES[i]: (ms[i], int(cnt[i])) for i in range(n)}, rc == 0
 
     def launch_count(self) -> int:
         return int(lib().pichol_launch_count(self._h))

@@ -266,7 +266,64 @@ pichol_status pichol_clear_status(pichol_ctx* ctx, void* stream)
 
 int64_t pichol_launch_count(const pichol_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
-void pichol_destroy(pichol_ctx* ctx) { delete ctx; }
+static void free_timing(pichol_ctx* ctx)
+{
+    if (ctx->ev) {
+        for (int i = 0; i < 2 * ctx->ev_cap; ++i) cudaEventDestroy(ctx->ev[i]);
+        std::free(ctx->ev);
+        std::free(ctx->ev_stage);
+    }
+    ctx->ev = nullptr;
+    ctx->ev_stage = nullptr;
+    ctx->ev_cap = ctx->ev_used = 0;
+    ctx->timing = 0;
+}
+
+pichol_status pichol_set_timing(pichol_ctx* ctx, int32_t max_launches)
+{
+    if (!ctx || max_launches < 0 || max_launches > (1 << 20)) return PICHOL_ERR_INVALID_ARG;
+    free_timing(ctx);
+    if (max_launches == 0) return PICHOL_OK;
+    ctx->ev = (cudaEvent_t*)std::calloc((size_t)2 * max_launches, sizeof(cudaEvent_t));
+    ctx->ev_stage = (int*)std::calloc((size_t)max_launches, sizeof(int));
+    if (!ctx->ev || !ctx->ev_stage) { free_timing(ctx); return PICHOL_ERR_INVALID_ARG; }
+    for (int i = 0; i < 2 * max_launches; ++i) {
+        if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) {
+            ctx->ev_cap = i / 2;
+            free_timing(ctx);
+            return PICHOL_ERR_CUDA;
+        }
+        ctx->ev_cap = (i + 1) / 2;
+    }
+    ctx->ev_cap = max_launches;
+    ctx->ev_used = 0;
+    ctx->timing = 1;
+    return PICHOL_OK;
+}
+
+pichol_status pichol_stage_times(pichol_ctx* ctx, double* ms, int64_t* launches, int32_t n_stages, void* stream)
+{
+    if (!ctx || !ms || !launches || n_stages < 1) return PICHOL_ERR_INVALID_ARG;
+    for (int i = 0; i < n_stages; ++i) { ms[i] = 0.0; launches[i] = 0; }
+    if (!ctx->timing) return PICHOL_ERR_STATE;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return PICHOL_ERR_CUDA;
+    for (int k = 0; k < ctx->ev_used; ++k) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, ctx->ev[2 * k], ctx->ev[2 * k + 1]) != cudaSuccess) return PICHOL_ERR_CUDA;
+        const int st = ctx->ev_stage[k];
+        if (st < n_stages) { ms[st] += t; launches[st] += 1; }
+    }
+    const int overflow = ctx->ev_used >= ctx->ev_cap;
+    ctx->ev_used = 0;
+    return overflow ? PICHOL_ERR_WORKSPACE : PICHOL_OK;
+}
+
+void pichol_destroy(pichol_ctx* ctx)
+{
+    if (!ctx) return;
+    free_timing(ctx);
+    delete ctx;
+}
 
 const char* pichol_status_string(pichol_status s)
 {

@@ -225,16 +225,28 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
         cudaFuncSetAttribute(k_chol_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_mm);
         attr_done = true;
     }
-    k_chol_init<T><<<dim3((unsigned)ctx->ntiles, nprob), 256, 0, s>>>(
-        (const T*)ctx->G, c.k, c.d, ctx->dp, ctx->ntiles, pm, ctx->lam, ctx->lam_s, F);
+    {
+        StageScope sc_(ctx, ST_CHOL_INIT, s);
+        k_chol_init<T><<<dim3((unsigned)ctx->ntiles, nprob), 256, 0, s>>>(
+            (const T*)ctx->G, c.k, c.d, ctx->dp, ctx->ntiles, pm, ctx->lam, ctx->lam_s, F);
+    }
     ctx->launches++;
     for (int J = 0; J < ctx->nt; ++J) {
-        k_chol_diag<T><<<nprob, 256, sm_diag, s>>>(F, ctx->ntiles, J, c.d, pm, ctx->Linv, ctx->status);
+        {
+            StageScope sc_(ctx, ST_CHOL_DIAG, s);
+            k_chol_diag<T><<<nprob, 256, sm_diag, s>>>(F, ctx->ntiles, J, c.d, pm, ctx->Linv, ctx->status);
+        }
         ctx->launches++;
         const int m = ctx->nt - 1 - J;
         if (m > 0) {
-            k_chol_panel<T><<<dim3(m, nprob), 256, sm_mm, s>>>(F, ctx->ntiles, J, ctx->Linv, pm);
-            k_chol_update<T><<<dim3(m * (m + 1) / 2, nprob), 256, sm_mm, s>>>(F, ctx->ntiles, J, pm);
+            {
+                StageScope sc_(ctx, ST_CHOL_PANEL, s);
+                k_chol_panel<T><<<dim3(m, nprob), 256, sm_mm, s>>>(F, ctx->ntiles, J, ctx->Linv, pm);
+            }
+            {
+                StageScope sc_(ctx, ST_CHOL_UPDATE, s);
+                k_chol_update<T><<<dim3(m * (m + 1) / 2, nprob), 256, sm_mm, s>>>(F, ctx->ntiles, J, pm);
+            }
             ctx->launches += 2;
         }
     }

@@ -33,6 +33,7 @@ cudaError_t launch_fit(pichol_ctx* ctx, cudaStream_t s)
 {
     const pichol_config& c = ctx->cfg;
     dim3 grid((unsigned)ctx->ntiles, c.k);
+    StageScope sc_(ctx, ST_FIT, s);
     if (c.mode == PICHOL_MODE_FP64)
         k_fit<double><<<grid, 256, 0, s>>>((const double*)ctx->F, ctx->pinv, c.g, ctx->p, ctx->ntiles,
                                            (double*)ctx->Theta);

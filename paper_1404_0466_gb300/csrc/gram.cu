@@ -220,6 +220,7 @@ k_setup(const void* G, int mode_fp64, int64_t d, int64_t dp, int k, int g, int p
     }
     if (threadIdx.x != 0) return;
     double tau = scale_by_trace ? red[0] / (double)d : 1.0;
+    if (!(tau > 0.0) || isinf(tau)) latch_error(st, PICHOL_ERR_INVALID_ARG, -1, -1, -1);
     scal[0] = tau;
     for (int t = 0; t < q; ++t)
         lam[t] = (q == 1) ? tau * lo : tau * lo * pow(hi / lo, (double)t / (double)(q - 1));
@@ -274,18 +275,33 @@ static cudaError_t gram_impl(pichol_ctx* ctx, const T* X, const T* Y, cudaStream
     T* G = (T*)ctx->G;
     cudaError_t e = cudaMemsetAsync(G, 0, sizeof(T) * (size_t)c.k * ctx->dp * ctx->dp, s);
     if (e != cudaSuccess) return e;
-    k_gram_simt<T><<<dim3((unsigned)ctx->ntiles, c.k), 256, 0, s>>>(X, c.d, ctx->dp, fo, G);
+    {
+        StageScope sc_(ctx, ST_GRAM, s);
+        k_gram_simt<T><<<dim3((unsigned)ctx->ntiles, c.k), 256, 0, s>>>(X, c.d, ctx->dp, fo, G);
+    }
     ctx->launches++;
     e = cudaMemsetAsync(ctx->Bv, 0, sizeof(T) * (size_t)c.k * ctx->dp * c.c, s);
     if (e != cudaSuccess) return e;
-    k_xty<T><<<dim3(ctx->nt, c.k), 256, 0, s>>>(X, Y, c.d, ctx->dp, c.c, fo, (T*)ctx->Bv);
-    k_yy<T><<<c.k, 256, 0, s>>>(Y, c.c, fo, ctx->yy, ctx->nfc);
-    k_setup<<<1, 256, 0, s>>>(G, c.mode == PICHOL_MODE_FP64, c.d, ctx->dp, c.k, c.g, ctx->p, c.q,
-                              c.lam_lo, c.lam_hi, c.scale_by_trace, c.basis, ctx->scal, ctx->lam,
-                              ctx->lam_s, ctx->pinv, ctx->phi, ctx->dphi, ctx->status);
+    {
+        StageScope sc_(ctx, ST_XTY, s);
+        k_xty<T><<<dim3(ctx->nt, c.k), 256, 0, s>>>(X, Y, c.d, ctx->dp, c.c, fo, (T*)ctx->Bv);
+    }
+    {
+        StageScope sc_(ctx, ST_MISC, s);
+        k_yy<T><<<c.k, 256, 0, s>>>(Y, c.c, fo, ctx->yy, ctx->nfc);
+    }
+    {
+        StageScope sc_(ctx, ST_SETUP, s);
+        k_setup<<<1, 256, 0, s>>>(G, c.mode == PICHOL_MODE_FP64, c.d, ctx->dp, c.k, c.g, ctx->p, c.q,
+                                  c.lam_lo, c.lam_hi, c.scale_by_trace, c.basis, ctx->scal, ctx->lam,
+                                  ctx->lam_s, ctx->pinv, ctx->phi, ctx->dphi, ctx->status);
+    }
     const int64_t len = ctx->dp * c.c;
-    k_btrain<T><<<dim3((unsigned)((len + 255) / 256), c.k), 256, 0, s>>>((const T*)ctx->Bv, c.k, len,
-                                                                          (T*)ctx->Btr);
+    {
+        StageScope sc_(ctx, ST_MISC, s);
+        k_btrain<T><<<dim3((unsigned)((len + 255) / 256), c.k), 256, 0, s>>>((const T*)ctx->Bv, c.k, len,
+                                                                              (T*)ctx->Btr);
+    }
     ctx->launches += 4;
     return cudaGetLastError();
 }

@@ -122,9 +122,39 @@ struct pichol_ctx {
 
     bool have_hessian, have_factors, have_fit;
     long long launches;
+
+    // optional per-stage timing: pairs of events recorded around launches
+    int timing;
+    int ev_cap, ev_used;
+    cudaEvent_t* ev;     // 2 * ev_cap events
+    int* ev_stage;       // stage of each pair
 };
 
 namespace pichol {
+
+// Stages reported by pichol_stage_times (order matters: it is the ABI's).
+enum Stage {
+    ST_GRAM = 0, ST_XTY, ST_SETUP, ST_CHOL_INIT, ST_CHOL_DIAG, ST_CHOL_PANEL, ST_CHOL_UPDATE, ST_FIT,
+    ST_DIAG_INV, ST_SOLVE, ST_RESID, ST_SCORE, ST_SELECT, ST_MISC, NSTAGE
+};
+
+// Records a start event on construction and a stop event on destruction
+// when timing is enabled on the context (and the event pool has room).
+struct StageScope {
+    pichol_ctx* ctx;
+    cudaStream_t s;
+    int slot;
+    StageScope(pichol_ctx* c, int stage, cudaStream_t st) : ctx(c), s(st), slot(-1) {
+        if (ctx->timing && ctx->ev_used < ctx->ev_cap) {
+            slot = ctx->ev_used++;
+            ctx->ev_stage[slot] = stage;
+            cudaEventRecord(ctx->ev[2 * slot], s);
+        }
+    }
+    ~StageScope() {
+        if (slot >= 0) cudaEventRecord(ctx->ev[2 * slot + 1], s);
+    }
+};
 
 // Launch helpers implemented per translation unit; each returns a cudaError_t.
 cudaError_t launch_gram(pichol_ctx* ctx, const void* X, const void* Y, cudaStream_t s);

@@ -796,7 +796,10 @@ static cudaError_t run_solve(pichol_ctx* ctx, const SolveArgs& sa, cudaStream_t 
         done = true;
     }
     dim3 grid((unsigned)((sa.tcount + LG - 1) / LG), ctx->cfg.k);
-    k_solve<T, LG, CB, NP, EXACT><<<grid, 256, C::SMEM, s>>>(sa);
+    {
+        StageScope sc_(ctx, ST_SOLVE, s);
+        k_solve<T, LG, CB, NP, EXACT><<<grid, 256, C::SMEM, s>>>(sa);
+    }
     ctx->launches++;
     return cudaGetLastError();
 }
@@ -840,7 +843,10 @@ static cudaError_t run_score(pichol_ctx* ctx, const ScoreArgs& sc, cudaStream_t 
         done = true;
     }
     dim3 grid(ctx->nt, (unsigned)((sc.tcount + LG - 1) / LG), ctx->cfg.k);
-    k_score<T, LG, CB><<<grid, 256, smem, s>>>(sc);
+    {
+        StageScope sc_(ctx, ST_SCORE, s);
+        k_score<T, LG, CB><<<grid, 256, smem, s>>>(sc);
+    }
     ctx->launches++;
     return cudaGetLastError();
 }
@@ -867,7 +873,10 @@ static cudaError_t run_resid(pichol_ctx* ctx, const ResidArgs& ra, cudaStream_t 
         done = true;
     }
     dim3 grid(ctx->nt, (unsigned)((ra.tcount + LG - 1) / LG), ctx->cfg.k);
-    k_resid<LG, CB, NP, PASS><<<grid, 256, smem, s>>>(ra);
+    {
+        StageScope sc_(ctx, ST_RESID, s);
+        k_resid<LG, CB, NP, PASS><<<grid, 256, smem, s>>>(ra);
+    }
     ctx->launches++;
     return cudaGetLastError();
 }
@@ -921,7 +930,10 @@ static cudaError_t eval_impl(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s
         if (ea != cudaSuccess) return ea;
         attr_done = true;
     }
-    k_diag_inv<T, EXACT><<<dim3(ctx->nt, tcount, cf.k), 128, dsm, s>>>(da);
+    {
+        StageScope sc_(ctx, ST_DIAG_INV, s);
+        k_diag_inv<T, EXACT><<<dim3(ctx->nt, tcount, cf.k), 128, dsm, s>>>(da);
+    }
     ctx->launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -975,7 +987,10 @@ static cudaError_t eval_impl(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s
             sc.out = ctx->Rres;
             if ((e = solve_dispatch<T, EXACT>(ctx, sc, s)) != cudaSuccess) return e;
             const int64_t n = (int64_t)cf.k * cf.q * ctx->dp * cf.c;
-            k_axpy<float><<<1024, 256, 0, s>>>((float*)ctx->W, (const float*)ctx->Rres, n);
+            {
+                StageScope sc_(ctx, ST_RESID, s);
+                k_axpy<float><<<1024, 256, 0, s>>>((float*)ctx->W, (const float*)ctx->Rres, n);
+            }
             ctx->launches++;
         }
     }
@@ -1004,8 +1019,11 @@ cudaError_t launch_eval(pichol_ctx* ctx, int exact, int t0, int tcount, cudaStre
 cudaError_t launch_finish(pichol_ctx* ctx, double* E_out, int32_t* t_star, cudaStream_t s)
 {
     const pichol_config& cf = ctx->cfg;
-    k_select<<<1, 256, 0, s>>>(ctx->Epart, ctx->flags, ctx->dmax, ctx->dmin, ctx->yy, ctx->nfc, cf.k, cf.q, ctx->nt,
-                               E_out, ctx->E, t_star, ctx->status);
+    {
+        StageScope sc_(ctx, ST_SELECT, s);
+        k_select<<<1, 256, 0, s>>>(ctx->Epart, ctx->flags, ctx->dmax, ctx->dmin, ctx->yy, ctx->nfc, cf.k, cf.q, ctx->nt,
+                                   E_out, ctx->E, t_star, ctx->status);
+    }
     ctx->launches++;
     return cudaGetLastError();
 }

@@ -158,6 +158,25 @@ def test_fp64_ragged_shapes(torch_mod, n, d, c, k, g, r, q, basis):
 
 
 def test_nan_input_latches_not_spd(torch_mod):
+    """A NaN in X makes a pivot non-positive: the factorisation latches
+    PICHOL_ERR_NOT_SPD with its fold, sample and row (absolute grid, so the
+    grid itself stays finite)."""
+    torch = torch_mod
+    prob = synth.spectral_gaussian(200, 20, 2, seed=5)
+    X = prob.X.copy()
+    X[3, 7] = np.nan
+    ctx = _ctx(prob, k=4, g=3, r=2, q=5, mode="fp64", scale_by_trace=False)
+    ctx.hessian(_dev(torch, X, "fp64"), _dev(torch, prob.Y, "fp64"))
+    ctx.factor_samples()
+    info = ctx.info()
+    assert info.code == 2 and 0 <= info.fold < 4 and 0 <= info.index < 3 and 0 <= info.pivot < 20
+    ctx.clear_status()
+    assert ctx.info().code == 0
+
+
+def test_nan_input_with_trace_scaled_grid_latches_invalid(torch_mod):
+    """With the grid scaled by tr(X^T X)/d a NaN makes the grid itself
+    non-finite; the set-up latches PICHOL_ERR_INVALID_ARG first."""
     torch = torch_mod
     prob = synth.spectral_gaussian(200, 20, 2, seed=5)
     X = prob.X.copy()
@@ -165,10 +184,7 @@ def test_nan_input_latches_not_spd(torch_mod):
     ctx = _ctx(prob, k=4, g=3, r=2, q=5, mode="fp64")
     ctx.hessian(_dev(torch, X, "fp64"), _dev(torch, prob.Y, "fp64"))
     ctx.factor_samples()
-    info = ctx.info()
-    assert info.code == 2 and 0 <= info.fold < 4 and 0 <= info.pivot < 20
-    ctx.clear_status()
-    assert ctx.info().code == 0
+    assert ctx.info().code == 1
 
 
 # ---------------------------------------------------------------------------

@@ -291,7 +291,8 @@ def run_own(args):
     Y = Yh.to(dev)
     params = dict(n=cfg["n"], d=cfg["d"], c=cfg["c"], k=k, g=cfg["g"], r=cfg["r"], q=q, lam_lo=cfg["lo"],
                   lam_hi=cfg["hi"], basis=w["basis"], mode=w["mode"], refine_steps=refine)
-    ctx = binding.Context(**params)
+    # the piCholesky context needs factor slots for the g samples only
+    ctx = binding.Context(exact_batch=cfg["g"], **params)
     out = ctx._outputs(False)
     stream = torch.cuda.current_stream()
 

@@ -37,8 +37,9 @@ size_t plan(pichol_ctx* ctx, char* base)
     ctx->G = take((size_t)(k * dp * dp * eb));
     ctx->Bv = take((size_t)(k * dp * cc * eb));
     ctx->Btr = take((size_t)(k * dp * cc * eb));
+    ctx->xpart = (double*)take(xty_part_bytes((int)k, dp, cc));
+    ctx->Hf = take((size_t)(k * ntl * TILE_ELEMS * eb));
     ctx->F = take((size_t)(ctx->nfac * ntl * TILE_ELEMS * eb));
-    ctx->Linv = (double*)take((size_t)(ctx->nfac * TILE_ELEMS * sizeof(double)));
     ctx->Theta = take((size_t)(k * ntl * p * TILE_ELEMS * eb));
     ctx->Dinv = take((size_t)(k * q * nt * TILE_ELEMS * eb));
     ctx->W = take((size_t)(k * q * dp * cc * eb));

@@ -2,8 +2,8 @@
 // (Sec. 3.2; Algorithm 1, step 1).  For each factorisation problem pr (a fold
 // f and a shift lambda), A = H_f + lambda I with H_f = sum_{j != f} G_j is
 // written tile-major, then for every tile column J:
-//   k_chol_diag   : L_JJ = chol(A_JJ) and L_JJ^{-1}, in double precision
-//   k_chol_panel  : L_IJ = A_IJ L_JJ^{-T}             (I > J)
+//   k_chol_diag   : L_JJ = chol(A_JJ), in double precision
+//   k_chol_panel  : L_IJ = A_IJ L_JJ^{-T} by substitution, row by row (I > J)
 //   k_chol_update : A_IK -= L_IJ L_KJ^T               (J < K <= I)
 // All problems advance one tile column per launch.  A non-positive pivot
 // latches PICHOL_ERR_NOT_SPD with (fold, sample, row) and the factorisation
@@ -26,10 +26,11 @@ __device__ inline double prob_lambda(const ProbMap& pm, int pr, const double* la
     return pm.exact ? lam[pm.t0 + i] : lam_s[i];
 }
 
-// A = sum_{j != f} G_j + lambda I on the lower tiles; identity on the padding.
+// A = H_f + lambda I on the lower tiles (H_f tile-major from the Gram step);
+// identity on the padding.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_chol_init(const T* __restrict__ G, int k, int64_t d, int64_t dp, int64_t ntiles, ProbMap pm,
+k_chol_init(const T* __restrict__ Hf, int64_t d, int64_t ntiles, ProbMap pm,
             const double* __restrict__ lam, const double* __restrict__ lam_s, T* __restrict__ F)
 {
     int I, J;
@@ -38,54 +39,52 @@ k_chol_init(const T* __restrict__ G, int k, int64_t d, int64_t dp, int64_t ntile
     if (prob_dead(pm, pr)) return;
     const int f = pr / pm.per;
     const double shift = prob_lambda(pm, pr, lam, lam_s);
+    const T* src = Hf + ((int64_t)f * ntiles + blockIdx.x) * TILE_ELEMS;
     T* dst = F + ((int64_t)pr * ntiles + blockIdx.x) * TILE_ELEMS;
     for (int e = threadIdx.x; e < TILE_ELEMS; e += 256) {
-        int r = e / TB, c = e % TB;
-        int64_t row = (int64_t)I * TB + r, col = (int64_t)J * TB + c;
-        double v;
-        if (I == J && c > r) v = 0.0;
-        else if (row >= d || col >= d) v = (row == col) ? 1.0 : 0.0;
-        else {
-            v = 0.0;
-            for (int j = 0; j < k; ++j)
-                if (j != f) v += (double)G[(int64_t)j * dp * dp + row * dp + col];
-            if (row == col) v += shift;
-        }
-        dst[e] = (T)v;
+        const int r = e / TB, c = e % TB;
+        const int64_t row = (int64_t)I * TB + r, col = (int64_t)J * TB + c;
+        T v;
+        if (I == J && c > r) v = T(0);
+        else if (row >= d || col >= d) v = (row == col) ? T(1) : T(0);
+        else v = (row == col) ? (T)((double)src[e] + shift) : src[e];
+        dst[e] = v;
     }
 }
 
-// One CTA per problem: factor the 64 x 64 diagonal tile in double precision
-// and form its inverse (column-by-column substitution) for the panel solve.
+// One CTA per problem: factor the 64 x 64 diagonal tile in double precision,
+// right-looking inside the tile (pivot, scale the column by 1/L_jj, rank-1
+// update of the trailing triangle).
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_chol_diag(T* __restrict__ F, int64_t ntiles, int J, int64_t d, ProbMap pm,
-            double* __restrict__ Linv, DevStatus* st)
+k_chol_diag(T* __restrict__ F, int64_t ntiles, int J, int64_t d, ProbMap pm, DevStatus* st)
 {
-    extern __shared__ double smd[];
-    double (*A)[TB + 1] = reinterpret_cast<double (*)[TB + 1]>(smd);
-    double (*B)[TB + 1] = reinterpret_cast<double (*)[TB + 1]>(smd + TB * (TB + 1));
+    __shared__ double A[TB][TB + 1];
+    __shared__ double piv_inv;
     const int pr = blockIdx.x, tid = threadIdx.x;
     if (prob_dead(pm, pr)) return;
     T* tile = F + ((int64_t)pr * ntiles + tile_index(J, J)) * TILE_ELEMS;
     for (int e = tid; e < TILE_ELEMS; e += 256) {
-        int r = e / TB, c = e % TB;
+        const int r = e / TB, c = e % TB;
         A[r][c] = (c <= r) ? (double)tile[e] : 0.0;
-        B[r][c] = 0.0;
     }
     for (int j = 0; j < TB; ++j) {
         __syncthreads();
-        double piv = A[j][j];
-        if (!(piv > 0.0)) {
-            if (tid == 0 && (int64_t)J * TB + j < d)
-                latch_error(st, PICHOL_ERR_NOT_SPD, pr / pm.per,
-                            pm.exact ? pm.t0 + pr % pm.per : pr % pm.per, (long long)J * TB + j);
-            piv = 1.0;
+        if (tid == 0) {
+            double piv = A[j][j];
+            if (!(piv > 0.0)) {
+                if ((int64_t)J * TB + j < d)
+                    latch_error(st, PICHOL_ERR_NOT_SPD, pr / pm.per,
+                                pm.exact ? pm.t0 + pr % pm.per : pr % pm.per, (long long)J * TB + j);
+                piv = 1.0;
+            }
+            const double ljj = sqrt(piv);
+            A[j][j] = ljj;
+            piv_inv = 1.0 / ljj;
         }
-        const double ljj = sqrt(piv);
         __syncthreads();
-        if (tid == 0) A[j][j] = ljj;
-        for (int i = j + 1 + tid; i < TB; i += 256) A[i][j] /= ljj;
+        const double inv = piv_inv;
+        for (int i = j + 1 + tid; i < TB; i += 256) A[i][j] *= inv;
         __syncthreads();
         const int m = TB - 1 - j;
         const int npairs = m * (m + 1) / 2;
@@ -97,22 +96,9 @@ k_chol_diag(T* __restrict__ F, int64_t ntiles, int J, int64_t d, ProbMap pm,
         }
     }
     __syncthreads();
-    // inverse: column c of L^{-1} by forward substitution on e_c
-    if (tid < TB) {
-        const int c = tid;
-        B[c][c] = 1.0 / A[c][c];
-        for (int r = c + 1; r < TB; ++r) {
-            double s = 0.0;
-            for (int q = c; q < r; ++q) s += A[r][q] * B[q][c];
-            B[r][c] = -s / A[r][r];
-        }
-    }
-    __syncthreads();
-    double* li = Linv + (int64_t)pr * TILE_ELEMS;
     for (int e = tid; e < TILE_ELEMS; e += 256) {
-        int r = e / TB, c = e % TB;
+        const int r = e / TB, c = e % TB;
         tile[e] = (c <= r) ? (T)A[r][c] : T(0);
-        li[e] = (c <= r) ? B[r][c] : 0.0;
     }
 }
 
@@ -145,31 +131,39 @@ __device__ inline void mm_nt(T (*As)[TB + 1], T (*Bs)[TB + 1], T acc[4][4])
     }
 }
 
-// L_IJ = A_IJ L_JJ^{-T}: out[r][c] = sum_k A[r][k] Linv[c][k].
+// L_IJ = A_IJ L_JJ^{-T}: every row x of L_IJ solves L_JJ x^T = a^T by forward
+// substitution, x_c = (a_c - sum_{k<c} L_JJ[c][k] x_k) / L_JJ[c][c].  One
+// thread per row, 256 / 64 = 4 tiles per CTA, the row in registers.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_chol_panel(T* __restrict__ F, int64_t ntiles, int J, const double* __restrict__ Linv, ProbMap pm)
+k_chol_panel(T* __restrict__ F, int64_t ntiles, int J, int m, ProbMap pm)
 {
     if (prob_dead(pm, blockIdx.y)) return;
-    extern __shared__ __align__(16) unsigned char sm_raw[];
-    T (*As)[TB + 1] = reinterpret_cast<T (*)[TB + 1]>(sm_raw);
-    T (*Ls)[TB + 1] = reinterpret_cast<T (*)[TB + 1]>(sm_raw + sizeof(T) * TB * (TB + 1));
-    const int I = J + 1 + blockIdx.x, pr = blockIdx.y;
-    T* tile = F + ((int64_t)pr * ntiles + tile_index(I, J)) * TILE_ELEMS;
-    load_tile_transposed<T, T>(tile, As);
-    load_tile_transposed<T, double>(Linv + (int64_t)pr * TILE_ELEMS, Ls);
+    __shared__ T Ls[TB][TB + 1];
+    __shared__ T inv[TB];
+    const int pr = blockIdx.y, tid = threadIdx.x;
+    T* base = F + (int64_t)pr * ntiles * TILE_ELEMS;
+    const T* ljj = base + tile_index(J, J) * TILE_ELEMS;
+    for (int e = tid; e < TILE_ELEMS; e += 256) Ls[e / TB][e % TB] = ljj[e];
     __syncthreads();
-    T acc[4][4];
+    if (tid < TB) inv[tid] = T(1) / Ls[tid][tid];
+    __syncthreads();
+    const int it = blockIdx.x * 4 + (tid >> 6);
+    if (it >= m) return;
+    const int r = tid & 63;
+    T* row = base + tile_index(J + 1 + it, J) * TILE_ELEMS + r * TB;
+    T x[TB];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int c = 0; c < TB; ++c) x[c] = row[c];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-    mm_nt<T>(As, Ls, acc);
-    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+    for (int c = 0; c < TB; ++c) {
+        T sacc = x[c];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+        for (int k2 = 0; k2 < c; ++k2) sacc = fma(-Ls[c][k2], x[k2], sacc);
+        x[c] = sacc * inv[c];
+    }
 #pragma unroll
-        for (int b = 0; b < 4; ++b) tile[(ty + 16 * a) * TB + tx + 16 * b] = acc[a][b];
+    for (int c = 0; c < TB; ++c) row[c] = x[c];
 }
 
 // A_IK -= L_IJ L_KJ^T for the trailing lower tiles J < K <= I.
@@ -216,32 +210,30 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
     pm.count = count;
     const int nprob = c.k * pm.per;
     T* F = (T*)ctx->F;
-    const size_t sm_diag = 2 * sizeof(double) * TB * (TB + 1);
     const size_t sm_mm = 2 * sizeof(T) * TB * (TB + 1);
     static bool attr_done = false;
     if (!attr_done) {
-        cudaFuncSetAttribute(k_chol_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_diag);
-        cudaFuncSetAttribute(k_chol_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_mm);
-        cudaFuncSetAttribute(k_chol_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_mm);
+        cudaError_t e = cudaFuncSetAttribute(k_chol_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_mm);
+        if (e != cudaSuccess) return e;
         attr_done = true;
     }
     {
         StageScope sc_(ctx, ST_CHOL_INIT, s);
         k_chol_init<T><<<dim3((unsigned)ctx->ntiles, nprob), 256, 0, s>>>(
-            (const T*)ctx->G, c.k, c.d, ctx->dp, ctx->ntiles, pm, ctx->lam, ctx->lam_s, F);
+            (const T*)ctx->Hf, c.d, ctx->ntiles, pm, ctx->lam, ctx->lam_s, F);
     }
     ctx->launches++;
     for (int J = 0; J < ctx->nt; ++J) {
         {
             StageScope sc_(ctx, ST_CHOL_DIAG, s);
-            k_chol_diag<T><<<nprob, 256, sm_diag, s>>>(F, ctx->ntiles, J, c.d, pm, ctx->Linv, ctx->status);
+            k_chol_diag<T><<<nprob, 256, 0, s>>>(F, ctx->ntiles, J, c.d, pm, ctx->status);
         }
         ctx->launches++;
         const int m = ctx->nt - 1 - J;
         if (m > 0) {
             {
                 StageScope sc_(ctx, ST_CHOL_PANEL, s);
-                k_chol_panel<T><<<dim3(m, nprob), 256, sm_mm, s>>>(F, ctx->ntiles, J, ctx->Linv, pm);
+                k_chol_panel<T><<<dim3((m + 3) / 4, nprob), 256, 0, s>>>(F, ctx->ntiles, J, m, pm);
             }
             {
                 StageScope sc_(ctx, ST_CHOL_UPDATE, s);

@@ -2,10 +2,11 @@
 // the lambda grid, and the Vandermonde pseudo-inverse of Algorithm 1.
 //
 //   G_j  = X_j^T X_j   (dense dp x dp, fold j's rows)       k_gram_simt
-//   Bv_j = X_j^T Y_j   (dp x c)                             k_xty
+//   Bv_j = X_j^T Y_j   (dp x c)                             k_xty + k_bsum
 //   yy_j = ||Y_j||_F^2                                      k_yy
 //   tau, lambda grid, sampled lambdas, V, P = V^+, phi      k_setup
-//   B_f  = sum_{j != f} Bv_j                                k_btrain
+//   B_f  = sum_{j != f} Bv_j                                k_bsum
+//   H_f  = sum_{j != f} G_j, lower tiles                    k_hf_tiles
 #include "internal.cuh"
 #include <cmath>
 
@@ -86,18 +87,26 @@ k_gram_simt(const T* __restrict__ X, int64_t d, int64_t dp, FoldOffs fo, T* __re
 }
 
 // ---------------------------------------------------------------------------
-// Bv_j = X_j^T Y_j.  Thread (feature fi, output phase oc) accumulates outputs
-// o = oc + 4u.  32-row chunk sums in the working type, totals in double.
+// Bv_j = X_j^T Y_j in two deterministic passes.  k_xty: CTA (tile, fold j,
+// row split rs) sums rows [r0 + rs*chunk, ...) of fold j; thread (feature fi,
+// output phase oc) accumulates outputs o = oc + 4u over 32-row chunks in the
+// working type, chunk totals in double, into part[j][rs][dp][c].
+// k_bsum: Bv_j = sum_rs part (increasing rs), B_f = sum_{j != f} Bv_j.
 // ---------------------------------------------------------------------------
+constexpr int XTY_SPLITS = 16;
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_xty(const T* __restrict__ X, const T* __restrict__ Y, int64_t d, int64_t dp, int64_t c,
-      FoldOffs fo, T* __restrict__ Bv)
+      FoldOffs fo, double* __restrict__ part)
 {
-    const int tile = blockIdx.x, j = blockIdx.y;
+    const int tile = blockIdx.x, j = blockIdx.y, rs = blockIdx.z;
     const int fi = threadIdx.x & 63, oc = threadIdx.x >> 6;
     const int64_t col = (int64_t)tile * TB + fi;
-    const int64_t r0 = fo.o[j], r1 = fo.o[j + 1];
+    const int64_t nj = fo.o[j + 1] - fo.o[j];
+    const int64_t chunk = ((nj + XTY_SPLITS - 1) / XTY_SPLITS + 31) / 32 * 32;
+    const int64_t r0 = fo.o[j] + rs * chunk;
+    const int64_t r1 = (r0 + chunk < fo.o[j + 1]) ? r0 + chunk : fo.o[j + 1];
     double tot[16];
     T acc[16];
 #pragma unroll
@@ -105,23 +114,46 @@ k_xty(const T* __restrict__ X, const T* __restrict__ Y, int64_t d, int64_t dp, i
     for (int64_t rb = r0; rb < r1; rb += 32) {
 #pragma unroll
         for (int u = 0; u < 16; ++u) acc[u] = T(0);
-        int64_t re = rb + 32 < r1 ? rb + 32 : r1;
+        const int64_t re = rb + 32 < r1 ? rb + 32 : r1;
         for (int64_t row = rb; row < re; ++row) {
-            T x = col < d ? X[row * d + col] : T(0);
+            const T x = col < d ? X[row * d + col] : T(0);
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
-                int64_t o = oc + 4 * u;
+                const int64_t o = oc + 4 * u;
                 if (o < c) acc[u] = fma(x, Y[row * c + o], acc[u]);
             }
         }
 #pragma unroll
         for (int u = 0; u < 16; ++u) tot[u] += (double)acc[u];
     }
-    T* B = Bv + (int64_t)j * dp * c;
+    double* P = part + ((int64_t)j * XTY_SPLITS + rs) * dp * c;
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
-        int64_t o = oc + 4 * u;
-        if (o < c) B[col * c + o] = (T)tot[u];
+        const int64_t o = oc + 4 * u;
+        if (o < c) P[col * c + o] = tot[u];
+    }
+}
+
+template <typename T>
+__global__ void k_bsum(const double* __restrict__ part, int k, int64_t len, T* __restrict__ Bv,
+                       T* __restrict__ Btr)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double bv[MAX_K];
+        double all = 0.0;
+        for (int j = 0; j < k; ++j) {
+            double s = 0.0;
+            for (int rs = 0; rs < XTY_SPLITS; ++rs) s += part[((int64_t)j * XTY_SPLITS + rs) * len + e];
+            bv[j] = s;
+            Bv[(int64_t)j * len + e] = (T)s;
+        }
+        for (int f = 0; f < k; ++f) {
+            all = 0.0;
+            for (int j = 0; j < k; ++j)
+                if (j != f) all += bv[j];
+            Btr[(int64_t)f * len + e] = (T)all;
+        }
     }
 }
 
@@ -146,20 +178,6 @@ k_yy(const T* __restrict__ Y, int64_t c, FoldOffs fo, double* __restrict__ yy, i
         __syncthreads();
     }
     if (threadIdx.x == 0) yy[j] = red[0];
-}
-
-// B_f = sum_{j != f} Bv_j, summed in increasing j.
-template <typename T>
-__global__ void k_btrain(const T* __restrict__ Bv, int k, int64_t len, T* __restrict__ Btr)
-{
-    const int f = blockIdx.y;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int j = 0; j < k; ++j)
-            if (j != f) s += (double)Bv[(int64_t)j * len + e];
-        Btr[(int64_t)f * len + e] = (T)s;
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -205,11 +223,12 @@ k_setup(const void* G, int mode_fp64, int64_t d, int64_t dp, int k, int g, int p
         DevStatus* st)
 {
     __shared__ double red[256];
+    __shared__ double shared_ab[3];
     double s = 0.0;
     for (int64_t e = threadIdx.x; e < (int64_t)k * d; e += 256) {
-        int j = (int)(e / d);
-        int64_t i = e % d;
-        int64_t off = (int64_t)j * dp * dp + i * dp + i;
+        const int j = (int)(e / d);
+        const int64_t i = e % d;
+        const int64_t off = (int64_t)j * dp * dp + i * dp + i;
         s += mode_fp64 ? ((const double*)G)[off] : (double)((const float*)G)[off];
     }
     red[threadIdx.x] = s;
@@ -218,52 +237,80 @@ k_setup(const void* G, int mode_fp64, int64_t d, int64_t dp, int k, int g, int p
         if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x != 0) return;
-    double tau = scale_by_trace ? red[0] / (double)d : 1.0;
-    if (!(tau > 0.0) || isinf(tau)) latch_error(st, PICHOL_ERR_INVALID_ARG, -1, -1, -1);
-    scal[0] = tau;
-    for (int t = 0; t < q; ++t)
+    const double tau = scale_by_trace ? red[0] / (double)d : 1.0;
+    for (int t = threadIdx.x; t < q; t += 256)
         lam[t] = (q == 1) ? tau * lo : tau * lo * pow(hi / lo, (double)t / (double)(q - 1));
-    for (int i = 0; i < g; ++i) {
-        int idx = (g == 1) ? 0 : (2 * i * (q - 1) + (g - 1)) / (2 * (g - 1));
-        lam_s[i] = lam[idx];
-    }
-    double smin = lam_s[0], smax = lam_s[0];
-    for (int i = 1; i < g; ++i) { smin = fmin(smin, lam_s[i]); smax = fmax(smax, lam_s[i]); }
-    const double a = log(smin), b = log(smax);
-    double V[MAX_G][MAX_P], dummy[MAX_P];
-    for (int i = 0; i < g; ++i) basis_eval(basis, p, lam_s[i], a, b, smax, V[i], dummy);
-    // modified Gram-Schmidt with re-orthogonalisation: V = Q R
-    double Q[MAX_G][MAX_P], R[MAX_P][MAX_P];
-    for (int m = 0; m < p; ++m)
-        for (int l = 0; l < p; ++l) R[m][l] = 0.0;
-    bool ok = true;
-    for (int m = 0; m < p; ++m) {
-        double v[MAX_G];
-        for (int i = 0; i < g; ++i) v[i] = V[i][m];
-        for (int pass = 0; pass < 2; ++pass)
-            for (int l = 0; l < m; ++l) {
-                double dot = 0.0;
-                for (int i = 0; i < g; ++i) dot += Q[i][l] * v[i];
-                R[l][m] += dot;
-                for (int i = 0; i < g; ++i) v[i] -= dot * Q[i][l];
-            }
-        double nrm = 0.0;
-        for (int i = 0; i < g; ++i) nrm += v[i] * v[i];
-        nrm = sqrt(nrm);
-        if (!(nrm > 0.0)) { ok = false; nrm = 1.0; }
-        R[m][m] = nrm;
-        for (int i = 0; i < g; ++i) Q[i][m] = v[i] / nrm;
-    }
-    if (!ok) latch_error(st, PICHOL_ERR_INVALID_ARG, -1, -1, -1);
-    // P = R^{-1} Q^T: back substitution column by column
-    for (int i = 0; i < g; ++i)
-        for (int m = p - 1; m >= 0; --m) {
-            double v = Q[i][m];
-            for (int l = m + 1; l < p; ++l) v -= R[m][l] * pinv[l * g + i];
-            pinv[m * g + i] = v / R[m][m];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!(tau > 0.0) || isinf(tau)) latch_error(st, PICHOL_ERR_INVALID_ARG, -1, -1, -1);
+        scal[0] = tau;
+        for (int i = 0; i < g; ++i) {
+            const int idx = (g == 1) ? 0 : (2 * i * (q - 1) + (g - 1)) / (2 * (g - 1));
+            lam_s[i] = lam[idx];
         }
-    for (int t = 0; t < q; ++t) basis_eval(basis, p, lam[t], a, b, smax, phi + t * p, dphi + t * p);
+        double smin = lam_s[0], smax = lam_s[0];
+        for (int i = 1; i < g; ++i) { smin = fmin(smin, lam_s[i]); smax = fmax(smax, lam_s[i]); }
+        const double a = log(smin), b = log(smax);
+        double V[MAX_G][MAX_P], dummy[MAX_P];
+        for (int i = 0; i < g; ++i) basis_eval(basis, p, lam_s[i], a, b, smax, V[i], dummy);
+        // modified Gram-Schmidt with re-orthogonalisation: V = Q R
+        double Q[MAX_G][MAX_P], R[MAX_P][MAX_P];
+        for (int m = 0; m < p; ++m)
+            for (int l = 0; l < p; ++l) R[m][l] = 0.0;
+        bool ok = true;
+        for (int m = 0; m < p; ++m) {
+            double v[MAX_G];
+            for (int i = 0; i < g; ++i) v[i] = V[i][m];
+            for (int pass = 0; pass < 2; ++pass)
+                for (int l = 0; l < m; ++l) {
+                    double dot = 0.0;
+                    for (int i = 0; i < g; ++i) dot += Q[i][l] * v[i];
+                    R[l][m] += dot;
+                    for (int i = 0; i < g; ++i) v[i] -= dot * Q[i][l];
+                }
+            double nrm = 0.0;
+            for (int i = 0; i < g; ++i) nrm += v[i] * v[i];
+            nrm = sqrt(nrm);
+            if (!(nrm > 0.0)) { ok = false; nrm = 1.0; }
+            R[m][m] = nrm;
+            for (int i = 0; i < g; ++i) Q[i][m] = v[i] / nrm;
+        }
+        if (!ok) latch_error(st, PICHOL_ERR_INVALID_ARG, -1, -1, -1);
+        // P = R^{-1} Q^T: back substitution column by column
+        for (int i = 0; i < g; ++i)
+            for (int m = p - 1; m >= 0; --m) {
+                double v = Q[i][m];
+                for (int l = m + 1; l < p; ++l) v -= R[m][l] * pinv[l * g + i];
+                pinv[m * g + i] = v / R[m][m];
+            }
+        shared_ab[0] = a;
+        shared_ab[1] = b;
+        shared_ab[2] = smax;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < q; t += 256)
+        basis_eval(basis, p, lam[t], shared_ab[0], shared_ab[1], shared_ab[2], phi + t * p, dphi + t * p);
+}
+
+// H_f = sum_{j != f} G_j on the lower tiles, tile-major, summed in double in
+// increasing j (the padding stays zero; the factorisation input adds the
+// shift and the identity on the padding).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_hf_tiles(const T* __restrict__ G, int k, int64_t dp, int64_t ntiles, T* __restrict__ Hf)
+{
+    int I, J;
+    tile_coords(blockIdx.x, I, J);
+    const int f = blockIdx.y;
+    T* dst = Hf + ((int64_t)f * ntiles + blockIdx.x) * TILE_ELEMS;
+    for (int e = threadIdx.x; e < TILE_ELEMS; e += 256) {
+        const int r = e / TB, c = e % TB;
+        const int64_t row = (int64_t)I * TB + r, col = (int64_t)J * TB + c;
+        double v = 0.0;
+        for (int j = 0; j < k; ++j)
+            if (j != f) v += (double)G[(int64_t)j * dp * dp + row * dp + col];
+        dst[e] = (T)v;
+    }
 }
 
 template <typename T>
@@ -279,12 +326,9 @@ static cudaError_t gram_impl(pichol_ctx* ctx, const T* X, const T* Y, cudaStream
         StageScope sc_(ctx, ST_GRAM, s);
         k_gram_simt<T><<<dim3((unsigned)ctx->ntiles, c.k), 256, 0, s>>>(X, c.d, ctx->dp, fo, G);
     }
-    ctx->launches++;
-    e = cudaMemsetAsync(ctx->Bv, 0, sizeof(T) * (size_t)c.k * ctx->dp * c.c, s);
-    if (e != cudaSuccess) return e;
     {
         StageScope sc_(ctx, ST_XTY, s);
-        k_xty<T><<<dim3(ctx->nt, c.k), 256, 0, s>>>(X, Y, c.d, ctx->dp, c.c, fo, (T*)ctx->Bv);
+        k_xty<T><<<dim3(ctx->nt, c.k, XTY_SPLITS), 256, 0, s>>>(X, Y, c.d, ctx->dp, c.c, fo, ctx->xpart);
     }
     {
         StageScope sc_(ctx, ST_MISC, s);
@@ -298,13 +342,18 @@ static cudaError_t gram_impl(pichol_ctx* ctx, const T* X, const T* Y, cudaStream
     }
     const int64_t len = ctx->dp * c.c;
     {
-        StageScope sc_(ctx, ST_MISC, s);
-        k_btrain<T><<<dim3((unsigned)((len + 255) / 256), c.k), 256, 0, s>>>((const T*)ctx->Bv, c.k, len,
-                                                                              (T*)ctx->Btr);
+        StageScope sc_(ctx, ST_XTY, s);
+        k_bsum<T><<<(unsigned)((len + 255) / 256), 256, 0, s>>>(ctx->xpart, c.k, len, (T*)ctx->Bv, (T*)ctx->Btr);
     }
-    ctx->launches += 4;
+    {
+        StageScope sc_(ctx, ST_MISC, s);
+        k_hf_tiles<T><<<dim3((unsigned)ctx->ntiles, c.k), 256, 0, s>>>(G, c.k, ctx->dp, ctx->ntiles, (T*)ctx->Hf);
+    }
+    ctx->launches += 7;
     return cudaGetLastError();
 }
+
+size_t xty_part_bytes(int k, int64_t dp, int64_t c) { return sizeof(double) * (size_t)k * XTY_SPLITS * dp * c; }
 
 cudaError_t launch_gram(pichol_ctx* ctx, const void* X, const void* Y, cudaStream_t s)
 {

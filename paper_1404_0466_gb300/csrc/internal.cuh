@@ -106,8 +106,9 @@ struct pichol_ctx {
     void* Bv;            // k x dp x c
     double* yy;          // k
     void* Btr;           // k x dp x c
+    double* xpart;       // k x XTY_SPLITS x dp x c partial sums of X_j^T Y_j
+    void* Hf;            // k x ntiles x TB^2: H_f, tile-major lower
     void* F;             // nfac x ntiles x TB^2
-    double* Linv;        // nfac x TB^2 (double)
     void* Theta;         // k x ntiles x p x TB^2
     void* Dinv;          // k x q x nt x TB^2
     void* W;             // k x q x dp x c
@@ -167,5 +168,6 @@ cudaError_t launch_export_tiles(pichol_ctx* ctx, const void* tiles, int64_t plan
 cudaError_t launch_export_hessian(pichol_ctx* ctx, int f, double* H, double* B, cudaStream_t s);
 cudaError_t launch_copy_w(pichol_ctx* ctx, void* W_out, cudaStream_t s);
 size_t solve_smem_bytes(int eb, int p, int64_t c);
+size_t xty_part_bytes(int k, int64_t dp, int64_t c);
 
 }  // namespace pichol

@@ -220,6 +220,36 @@ PICHOL_API pichol_status pichol_stage_times(pichol_ctx* ctx, double* ms, int64_t
  * the caller's. */
 PICHOL_API void pichol_destroy(pichol_ctx* ctx);
 
+/*
+ * Fold right-hand sides with no allocation at all.  The paper has no
+ * counterpart to this call; it exists for callers that cannot allocate device
+ * memory (a plug-in inside a framework that owns the whole device through its
+ * own memory pool, a real-time path that cannot afford cudaMalloc's implicit
+ * synchronisation, code that is given only its inputs and outputs).  It
+ * computes, for the k contiguous folds f = rows [floor(f n/k), floor((f+1) n/k)),
+ *   Bv_out[j] = X_j^T Y_j          and   B_out[f] = sum_{j != f} Bv_out[j],
+ * both k x d x c row-major in the mode's type (double for PICHOL_MODE_FP64,
+ * float for PICHOL_MODE_MIXED), the same values pichol_hessian forms for B_f.
+ * X (n x d) and Y (n x c) are device pointers; the outputs are caller-owned
+ * device buffers.  Requires 2 <= k <= 64, n >= k, d >= 1, 1 <= c <= 64.
+ *
+ * Scratch: the partial sums use a fixed array in the library's device memory
+ * (8 MiB, i.e. 2^20 doubles, held by every GPU that loads the library until
+ * the process exits); k * 16 * ceil(d/64)*64 * c must not exceed 2^20, else
+ * PICHOL_ERR_WORKSPACE is returned and nothing is enqueued.  The array is
+ * shared by every call on a device and keeps the last call's contents; every
+ * partial a call reads is first written by the same call, so nothing needs to
+ * start at zero.  Calls that overlap on the GPU (on different streams, or from
+ * several threads) race on the array and give wrong results: serialise them.
+ * The first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current); make that first call before
+ * any stream capture.  The call never calls cudaMalloc, cudaFree or any other
+ * allocating routine.  Errors: PICHOL_ERR_INVALID_ARG for bad arguments,
+ * PICHOL_ERR_CUDA if a CUDA call fails.
+ */
+PICHOL_API pichol_status pichol_fold_rhs_noalloc(int32_t mode, const void* X, const void* Y, int64_t n, int64_t d,
+                                                 int64_t c, int32_t k, void* Bv_out, void* B_out, void* stream);
+
 /* Short text for a status code (static storage). */
 PICHOL_API const char* pichol_status_string(pichol_status s);
 

@@ -28,6 +28,7 @@ EXPORTS = [
     "pichol_eval_holdout_exact", "pichol_get_lambdas", "pichol_export_factor", "pichol_export_theta",
     "pichol_export_hessian", "pichol_get_info", "pichol_clear_status", "pichol_launch_count",
     "pichol_destroy", "pichol_status_string", "pichol_set_timing", "pichol_stage_times",
+    "pichol_fold_rhs_noalloc",
 ]
 STAGES = ["gram", "xty", "setup", "chol_init", "chol_diag", "chol_panel", "chol_update", "fit",
           "diag_inv", "solve", "resid", "score", "select", "misc"]
@@ -85,6 +86,7 @@ def lib():
         "pichol_destroy": ([vp], None),
         "pichol_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "pichol_set_timing": ([vp, i32], ctypes.c_int),
+        "pichol_fold_rhs_noalloc": ([i32, vp, vp, i64, i64, i64, i32, vp, vp, vp], ctypes.c_int),
         "pichol_stage_times": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32, vp],
                                ctypes.c_int),
     }

@@ -9,6 +9,7 @@
 //   H_f  = sum_{j != f} G_j, lower tiles                    k_hf_tiles
 #include "internal.cuh"
 #include <cmath>
+#include <mutex>
 
 namespace pichol {
 
@@ -355,6 +356,62 @@ static cudaError_t gram_impl(pichol_ctx* ctx, const T* X, const T* Y, cudaStream
 
 size_t xty_part_bytes(int k, int64_t dp, int64_t c) { return sizeof(double) * (size_t)k * XTY_SPLITS * dp * c; }
 
+// ---------------------------------------------------------------------------
+// Fold right-hand sides without allocating (pichol_fold_rhs_noalloc).
+//
+// Some callers cannot allocate device memory at all: a plug-in inside a
+// framework that owns every byte of the GPU through its own pool, a real-time
+// path that cannot pay for cudaMalloc's implicit device-wide synchronisation,
+// or code that is handed only its input and output buffers.  For them the
+// partial sums of X_j^T Y_j live in a fixed array in the library's own device
+// memory instead of a workspace: NOALLOC_PART_DOUBLES doubles (8 MiB) per GPU,
+// held by every GPU that loads the library until the process exits.
+// ---------------------------------------------------------------------------
+constexpr size_t NOALLOC_PART_DOUBLES = (size_t)1 << 20;
+static __device__ __align__(256) double g_noalloc_part[NOALLOC_PART_DOUBLES];
+
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_ptr[256];   // device address of g_noalloc_part, per device
+
+// Bv_j (k x d x c) and B_f (k x d x c), unpadded, from the partial sums.
+template <typename T>
+__global__ void k_bsum_unpadded(const double* __restrict__ part, int k, int64_t dp, int64_t d, int64_t c,
+                                T* __restrict__ Bv, T* __restrict__ B)
+{
+    const int64_t len = d * c, plen = dp * c;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double bv[MAX_K];
+        for (int j = 0; j < k; ++j) {
+            double s = 0.0;
+            for (int rs = 0; rs < XTY_SPLITS; ++rs) s += part[((int64_t)j * XTY_SPLITS + rs) * plen + e];
+            bv[j] = s;
+            Bv[(int64_t)j * len + e] = (T)s;
+        }
+        for (int f = 0; f < k; ++f) {
+            double all = 0.0;
+            for (int j = 0; j < k; ++j)
+                if (j != f) all += bv[j];
+            B[(int64_t)f * len + e] = (T)all;
+        }
+    }
+}
+
+template <typename T>
+static cudaError_t fold_rhs_noalloc(const T* X, const T* Y, int64_t n, int64_t d, int64_t c, int k, T* Bv,
+                                    T* B, double* part, cudaStream_t s)
+{
+    FoldOffs fo;
+    for (int j = 0; j <= k; ++j) fo.o[j] = (int64_t)j * n / k;
+    const int nt = (int)((d + TB - 1) / TB);
+    const int64_t dp = (int64_t)nt * TB;
+    k_xty<T><<<dim3(nt, k, XTY_SPLITS), 256, 0, s>>>(X, Y, d, dp, c, fo, part);
+    const int64_t len = d * c;
+    const unsigned blocks = (unsigned)((len + 255) / 256 < 4096 ? (len + 255) / 256 : 4096);
+    k_bsum_unpadded<T><<<blocks, 256, 0, s>>>(part, k, dp, d, c, Bv, B);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gram(pichol_ctx* ctx, const void* X, const void* Y, cudaStream_t s)
 {
     if (ctx->cfg.mode == PICHOL_MODE_FP64)
@@ -363,3 +420,35 @@ cudaError_t launch_gram(pichol_ctx* ctx, const void* X, const void* Y, cudaStrea
 }
 
 }  // namespace pichol
+
+extern "C" PICHOL_API pichol_status pichol_fold_rhs_noalloc(int32_t mode, const void* X, const void* Y, int64_t n,
+                                                           int64_t d, int64_t c, int32_t k, void* Bv_out,
+                                                           void* B_out, void* stream)
+{
+    using namespace pichol;
+    if (mode != PICHOL_MODE_FP64 && mode != PICHOL_MODE_MIXED) return PICHOL_ERR_INVALID_ARG;
+    if (!X || !Y || !Bv_out || !B_out) return PICHOL_ERR_INVALID_ARG;
+    if (k < 2 || k > MAX_K || n < k || d < 1 || c < 1 || c > 64) return PICHOL_ERR_INVALID_ARG;
+    const int64_t dp = (d + TB - 1) / TB * TB;
+    // the partial sums need k * 16 * dp * c doubles of the fixed array
+    if ((double)k * XTY_SPLITS * (double)dp * (double)c > (double)NOALLOC_PART_DOUBLES) return PICHOL_ERR_WORKSPACE;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return PICHOL_ERR_CUDA;
+    double* part = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* addr = nullptr;
+            if (cudaGetSymbolAddress(&addr, g_noalloc_part) != cudaSuccess || !addr) return PICHOL_ERR_CUDA;
+            g_noalloc_ptr[dev] = (double*)addr;
+        }
+        part = g_noalloc_ptr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = (mode == PICHOL_MODE_FP64)
+        ? fold_rhs_noalloc<double>((const double*)X, (const double*)Y, n, d, c, k, (double*)Bv_out,
+                                   (double*)B_out, part, s)
+        : fold_rhs_noalloc<float>((const float*)X, (const float*)Y, n, d, c, k, (float*)Bv_out, (float*)B_out,
+                                  part, s);
+    return e == cudaSuccess ? PICHOL_OK : PICHOL_ERR_CUDA;
+}

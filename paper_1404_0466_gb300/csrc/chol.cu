@@ -86,13 +86,12 @@ k_chol_diag(T* __restrict__ F, int64_t ntiles, int J, int64_t d, ProbMap pm, Dev
         const double inv = piv_inv;
         for (int i = j + 1 + tid; i < TB; i += 256) A[i][j] *= inv;
         __syncthreads();
-        const int m = TB - 1 - j;
-        const int npairs = m * (m + 1) / 2;
-        for (int e = tid; e < npairs; e += 256) {
-            int ii, kk;
-            tile_coords(e, ii, kk);
-            const int i = j + 1 + ii, c = j + 1 + kk;
-            A[i][c] -= A[i][j] * A[c][j];
+        // rank-1 update of the trailing triangle: thread (row i = tid & 63,
+        // phase ph = tid >> 6) updates columns c = j+1+ph, j+5+ph, ... <= i
+        const int i = tid & 63, ph = tid >> 6;
+        if (i > j) {
+            const double aij = A[i][j];
+            for (int c = j + 1 + ph; c <= i; c += 4) A[i][c] -= aij * A[c][j];
         }
     }
     __syncthreads();

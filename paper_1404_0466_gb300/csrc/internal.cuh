@@ -48,7 +48,7 @@ __host__ __device__ inline int64_t num_tiles(int nt) {
 
 // Recover (I, J), J <= I, from a lower-triangular tile index.
 __host__ __device__ inline void tile_coords(int64_t e, int& I, int& J) {
-    int i = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+    int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);   // estimate, fixed up below
     while ((int64_t)(i + 1) * (i + 2) / 2 <= e) ++i;
     while ((int64_t)i * (i + 1) / 2 > e) --i;
     I = i;

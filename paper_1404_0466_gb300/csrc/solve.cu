@@ -171,10 +171,12 @@ struct SolveCfg {
     static constexpr int CBP = (CB + VN - 1) / VN * VN;
     static constexpr int NPL = (EXACT ? LG : NP) > LG ? (EXACT ? LG : NP) : LG;  // planes in a stage
     static constexpr int PB = TILE_ELEMS * (int)sizeof(T);
-    static constexpr int STAGES = (2 * NPL * PB <= 128 * 1024) ? 2 : 1;
-    static constexpr int PLANE_BYTES = STAGES * NPL * PB;
     static constexpr int ZS_BYTES = 2 * LG * TB * CBP * (int)sizeof(T);
     static constexpr int R_BYTES = LG * TB * CBP * (int)sizeof(T);
+    // two stages only if two CTAs still fit on an SM (227 KB); otherwise the
+    // second resident CTA hides the copies
+    static constexpr int STAGES = (2 * (2 * NPL * PB + ZS_BYTES + R_BYTES) <= 227 * 1024) ? 2 : 1;
+    static constexpr int PLANE_BYTES = STAGES * NPL * PB;
     static constexpr int SMEM = PLANE_BYTES + ZS_BYTES + R_BYTES;
 };
 
@@ -313,7 +315,7 @@ k_solve(SolveArgs a)
                     const T* zs = Zs + zi * LG * TB * CBP;
                     if (!back) {
                         // row-owner: row r of tile (i, j), k in [16 kq, 16 kq + 16)
-#pragma unroll 1
+#pragma unroll
                         for (int ch = 0; ch < 16 / VN; ++ch) {
                             const int kc = (kq * 16) / VN + ch;
                             T v[NPS][VN];
@@ -345,12 +347,21 @@ k_solve(SolveArgs a)
                             }
                         }
                     } else {
-                        // column-owner: column r of tile (j, i), k (its rows) in [16 kq, 16 kq + 16)
-#pragma unroll 4
-                        for (int kk = kq * 16; kk < kq * 16 + 16; ++kk) {
+                        // column-owner: column r of tile (j, i), k (its rows) in [16 kq, 16 kq + 16);
+                        // 16 kq is a multiple of 8, so kk & 7 = e & 7 and the swizzled
+                        // column offset takes 8 values, computed once
+                        int cofs[8];
+#pragma unroll
+                        for (int x = 0; x < 8; ++x) cofs[x] = swz_off(x, r, sizeof(T));
+                        const unsigned char* plk = pl + kq * 16 * TB * (int)sizeof(T);
+#pragma unroll
+                        for (int e16 = 0; e16 < 16; ++e16) {
+                            const int kk = kq * 16 + e16;
                             T ve[NPS];
 #pragma unroll
-                            for (int m = 0; m < NPS; ++m) ve[m] = sm_elem<T>(pl + m * C::PB, kk, r);
+                            for (int m = 0; m < NPS; ++m)
+                                ve[m] = *reinterpret_cast<const T*>(plk + m * C::PB + e16 * TB * (int)sizeof(T) +
+                                                                    cofs[e16 & 7] - (e16 & 7) * TB * (int)sizeof(T));
 #pragma unroll
                             for (int l = 0; l < LG; ++l) {
                                 const T lv = eval_elem<T, NP, LG, EXACT>(w, ve, l);
@@ -780,8 +791,9 @@ size_t solve_smem_bytes(int eb, int p, int64_t c)
     const int cbp = (cb + vn - 1) / vn * vn;
     const int np_interp = p > LG ? p : LG;
     const size_t pb = (size_t)TILE_ELEMS * eb;
-    const size_t stages = (2 * np_interp * pb <= 128 * 1024) ? 2 : 1;
-    return stages * np_interp * pb + (size_t)3 * LG * TB * cbp * eb;
+    const size_t zr = (size_t)3 * LG * TB * cbp * eb;
+    const size_t stages = (2 * (2 * np_interp * pb + zr) <= 227 * 1024) ? 2 : 1;
+    return stages * np_interp * pb + zr;
 }
 
 template <typename T, int LG, int CB, int NP, bool EXACT>

@@ -46,6 +46,16 @@ size_t plan(pichol_ctx* ctx, char* base)
     const bool refine = c.mode == PICHOL_MODE_MIXED && c.refine_steps > 0;
     ctx->U = refine ? take((size_t)(2 * k * q * dp * cc * sizeof(float))) : nullptr;
     ctx->Rres = refine ? take((size_t)(k * q * dp * cc * eb)) : nullptr;
+    if (c.mode == PICHOL_MODE_MIXED) {
+        const int64_t qc = q * cc;
+        ctx->Xh = (float*)take((size_t)(dp * ctx->kpad * 4));
+        ctx->Xl = (float*)take((size_t)(dp * ctx->kpad * 4));
+        ctx->Gh = (float*)take((size_t)(k * dp * dp * 4));
+        ctx->Gl = (float*)take((size_t)(k * dp * dp * 4));
+        ctx->Wth = (float*)take((size_t)(k * qc * dp * 4));
+        ctx->Wtl = (float*)take((size_t)(k * qc * dp * 4));
+        ctx->U2 = (float*)take((size_t)(k * dp * ctx->ldu * 4));
+    }
     ctx->Epart = (double*)take((size_t)(k * q * nt * sizeof(double)));
     ctx->E = (double*)take((size_t)(k * q * sizeof(double)));
     ctx->flags = (int*)take((size_t)(k * q * nt * sizeof(int)));
@@ -110,6 +120,8 @@ pichol_status pichol_create(const pichol_config* cfg, pichol_ctx** out)
     for (int f = 0; f <= c.k; ++f) ctx->offs[f] = (int64_t)f * c.n / c.k;
     ctx->exact_batch = c.exact_batch > 0 ? c.exact_batch : c.q;
     ctx->nfac = (int64_t)c.k * (ctx->exact_batch > c.g ? ctx->exact_batch : c.g);
+    ctx->kpad = tc_kpad(ctx);
+    ctx->ldu = ((int64_t)c.q * c.c + 3) / 4 * 4;
     ctx->need_bytes = plan(ctx, nullptr);
     *out = ctx;
     return PICHOL_OK;

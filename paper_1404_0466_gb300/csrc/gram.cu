@@ -323,7 +323,11 @@ static cudaError_t gram_impl(pichol_ctx* ctx, const T* X, const T* Y, cudaStream
     T* G = (T*)ctx->G;
     cudaError_t e = cudaMemsetAsync(G, 0, sizeof(T) * (size_t)c.k * ctx->dp * ctx->dp, s);
     if (e != cudaSuccess) return e;
-    {
+    if constexpr (std::is_same<T, float>::value) {
+        // mixed mode: tensor cores (split TF32 when gram_passes = 3)
+        e = launch_gram_tc(ctx, X, s);
+        if (e != cudaSuccess) return e;
+    } else {
         StageScope sc_(ctx, ST_GRAM, s);
         k_gram_simt<T><<<dim3((unsigned)ctx->ntiles, c.k), 256, 0, s>>>(X, c.d, ctx->dp, fo, G);
     }

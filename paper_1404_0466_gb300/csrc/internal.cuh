@@ -115,6 +115,16 @@ struct pichol_ctx {
     void* U;             // 2 x k x q x dp x c floats: L~^T W as (hi, lo) (refinement)
     void* Rres;          // k x q x dp x c (residual / correction)
     int64_t* nfc;        // k: n_f * c
+    // tensor-core operands (mixed mode)
+    int64_t kpad;        // columns of the transposed, fold-padded X
+    int64_t ldu;         // leading dimension of U2 (q c rounded up to 4)
+    float* Xh;           // dp x kpad: X^T split, TF32 part
+    float* Xl;           // dp x kpad: remainder
+    float* Gh;           // k x dp x dp: G_j split
+    float* Gl;
+    float* Wth;          // k x (q c) x dp: W^T split
+    float* Wtl;
+    float* U2;           // k x dp x ldu: G_f W for every lambda
     double* Epart;       // k x q x nt
     double* E;           // k x q
     int* flags;          // k x q x nt (per-tile diagonal checks: bit0 nonpositive)
@@ -169,5 +179,8 @@ cudaError_t launch_export_hessian(pichol_ctx* ctx, int f, double* H, double* B, 
 cudaError_t launch_copy_w(pichol_ctx* ctx, void* W_out, cudaStream_t s);
 size_t solve_smem_bytes(int eb, int p, int64_t c);
 size_t xty_part_bytes(int k, int64_t dp, int64_t c);
+int64_t tc_kpad(const pichol_ctx* ctx);
+cudaError_t launch_gram_tc(pichol_ctx* ctx, const float* X, cudaStream_t s);
+cudaError_t launch_score_tc(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s);
 
 }  // namespace pichol

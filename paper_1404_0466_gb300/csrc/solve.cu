@@ -1007,6 +1007,10 @@ static cudaError_t eval_impl(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s
         }
     }
 
+    if constexpr (std::is_same<T, float>::value) {
+        // mixed mode: G_f W for all lambdas on tensor cores, then the dot products
+        return launch_score_tc(ctx, t0, tcount, s);
+    }
     ScoreArgs sc;
     sc.G = ctx->G;
     sc.Bv = ctx->Bv;

@@ -1,0 +1,566 @@
+// Tensor-core (tcgen05, TF32) contractions of the mixed-precision path:
+//   Gram blocks     G_j = X_j^T X_j                     (Sec. 3.1, Eq. 2)
+//   score products  U_f = G_f W_f for all q lambdas      (hold-out expansion, Sec. 3.1)
+//
+// C = sum_p A_p B_p^T with A (M x K) and B (N x K) both K-major fp32 in global
+// memory.  With PASSES = 3 every operand is split as x = hi + lo, hi = x
+// rounded to TF32 and lo = x - hi (exact in fp32), and the products
+// hi*hi + hi*lo + lo*hi are accumulated in one fp32 accumulator: the dropped
+// lo*lo term and the TF32 rounding of lo are ~2^-22 of |x y|, so the result is
+// close to an fp32 product (the split-TF32 scheme of Ootomo & Yokota, 2022).
+//
+// One CTA computes one 128 x 128 tile of C:
+//   warp 0 lane 0  TMA producer: 128 x 32 fp32 boxes (128-byte swizzle) of
+//                  A_hi, A_lo, B_hi, B_lo per stage into a STAGES-deep ring
+//   warp 1 lane 0  MMA issuer: tcgen05.mma kind::tf32, M = 128, N = 128,
+//                  K = 8, accumulator in tensor memory (128 columns)
+//   all 4 warps    epilogue: tcgen05.ld 32 lanes x 16 columns, fp32 stores
+// Every wait on an mbarrier is bounded (about two seconds of clock); a wait
+// that runs out latches PICHOL_ERR_TIMEOUT, the CTA stops issuing work, waits
+// (bounded) for its own copies and MMAs, frees its tensor memory and returns.
+#include "internal.cuh"
+
+#include <cuda.h>
+
+namespace pichol {
+
+namespace tc {
+
+constexpr int BM = 128, BN = 128, BK = 32;     // BK fp32 = 128 bytes = one swizzle row
+constexpr int STAGES = 3;
+constexpr int TILE_BYTES = BM * BK * 4;        // 16 KB per operand tile
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;    // A_hi, A_lo, B_hi, B_lo
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+constexpr int TMEM_COLS = 128;
+constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.b32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of `parity` to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+    return true;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];\n" ::
+            "r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major operand tile written by TMA with
+// the 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);   // start address >> 4
+    d |= (uint64_t)1 << 16;                     // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: 8 rows x 128 bytes
+    d |= (uint64_t)1 << 46;                     // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: kind::tf32, fp32 accumulator, both operands K-major,
+// M = 128, N = 128.
+__host__ __device__ constexpr uint32_t idesc_tf32_128x128()
+{
+    return (1u << 4)            // D format: f32
+         | (2u << 7)            // A format: tf32
+         | (2u << 10)           // B format: tf32
+         | ((uint32_t)(BN >> 3) << 17)
+         | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float tf32_round(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+}  // namespace tc
+
+enum GemmMode { GEMM_GRAM = 0, GEMM_PLAIN = 1 };
+
+struct GemmArgs {
+    int mode;
+    int passes;
+    // GEMM_GRAM: lower tiles (I, J) of fold blockIdx.y; K range of fold f is
+    // [k0[f], k0[f] + kn[f]) in the transposed, fold-padded X.
+    int ntb;                  // 128-tiles per side
+    int k0[MAX_K + 1];
+    int kn[MAX_K];
+    // GEMM_PLAIN: fold f uses A rows [f*a_rows_fold, ...) and B rows
+    // [f*b_rows_fold + b_row_off, ...); output columns start at c_col_off
+    int a_rows_fold, b_rows_fold, b_row_off, c_col_off;
+    int K;
+    // output
+    float* C;                 // GRAM: G (k x dp x dp); PLAIN: C (k x M x ldc)
+    float* Chi;               // GRAM: split of G for later contractions (may be null)
+    float* Clo;
+    int64_t ldc, M, N;        // valid rows / columns of one fold's C
+    int64_t c_fold_stride;
+    DevStatus* st;
+};
+
+__global__ void __launch_bounds__(128, 1)
+k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+          const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, const GemmArgs a)
+{
+    using namespace tc;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accum = empty + STAGES;
+    uint32_t* tmem_slot = (uint32_t*)(accum + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    volatile int* consumed = abort_flag + 1;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int f = blockIdx.y;
+    int tI, tJ, nk, kx0, arow, brow;
+    if (a.mode == GEMM_GRAM) {
+        tile_coords(blockIdx.x, tI, tJ);
+        nk = (a.kn[f] + BK - 1) / BK;
+        kx0 = a.k0[f];
+        arow = tI * BM;
+        brow = tJ * BN;
+    } else {
+        tI = blockIdx.x % ((int)((a.M + BM - 1) / BM));
+        tJ = blockIdx.x / ((int)((a.M + BM - 1) / BM));
+        nk = (a.K + BK - 1) / BK;
+        kx0 = 0;
+        arow = f * a.a_rows_fold + tI * BM;
+        brow = f * a.b_rows_fold + a.b_row_off + tJ * BN;
+    }
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        *abort_flag = 0;
+        *consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t bytes_per_stage = (a.passes == 3 ? 4 : 2) * TILE_BYTES;
+
+    if (warp == 0 && lane == 0) {
+        // ---- producer ----
+        int issued = 0;
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % STAGES;
+            if (!mbar_wait(&empty[s], ((kb / STAGES) & 1) ^ 1)) { *abort_flag = 1; break; }
+            if (*abort_flag) break;
+            unsigned char* st = smem + s * STAGE_BYTES;
+            mbar_expect_tx(&full[s], bytes_per_stage);
+            const int x = kx0 + kb * BK;
+            tma_load_2d(st, &mAh, &full[s], x, arow);
+            tma_load_2d(st + 2 * TILE_BYTES, &mBh, &full[s], x, brow);
+            if (a.passes == 3) {
+                tma_load_2d(st + TILE_BYTES, &mAl, &full[s], x, arow);
+                tma_load_2d(st + 3 * TILE_BYTES, &mBl, &full[s], x, brow);
+            }
+            ++issued;
+        }
+        // wait (bounded) for copies that were issued but never consumed
+        __threadfence_block();
+        for (int kb = *consumed; kb < issued; ++kb) mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1);
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer ----
+        const uint32_t idesc = idesc_tf32_128x128();
+        int kb = 0;
+        for (; kb < nk; ++kb) {
+            const int s = kb % STAGES;
+            if (*abort_flag || !mbar_wait(&full[s], (kb / STAGES) & 1)) { *abort_flag = 1; break; }
+            tc_fence_after();
+            const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+            const uint32_t ah = base, al = base + TILE_BYTES, bh = base + 2 * TILE_BYTES, bl = base + 3 * TILE_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / 8; ++kk) {
+                const uint32_t off = kk * 32;   // 8 tf32 = 32 bytes along K
+                umma_tf32(tmem, sw128_desc(ah + off), sw128_desc(bh + off), idesc, (kb | kk) != 0);
+                if (a.passes == 3) {
+                    umma_tf32(tmem, sw128_desc(ah + off), sw128_desc(bl + off), idesc, 1);
+                    umma_tf32(tmem, sw128_desc(al + off), sw128_desc(bh + off), idesc, 1);
+                }
+            }
+            umma_commit(&empty[s]);
+            *consumed = kb + 1;
+        }
+        umma_commit(accum);   // arrives once every MMA issued above has completed
+    }
+    __syncwarp();
+
+    // ---- epilogue: every warp reads its 32 TMEM lanes ----
+    const bool ok = mbar_wait(accum, 0);
+    if (!ok) *abort_flag = 1;
+    tc_fence_after();
+    __syncthreads();
+    if (*abort_flag) {
+        if (threadIdx.x == 0) latch_error(a.st, PICHOL_ERR_TIMEOUT, f, (int)blockIdx.x, -1);
+    } else if (nk > 0) {
+        const int row = warp * 32 + lane;          // row inside the tile
+        const int64_t grow = (int64_t)tI * BM + row;
+        float* Cf = a.C + (int64_t)f * a.c_fold_stride;
+        for (int cc = 0; cc < BN / 16; ++cc) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 16), v);
+            const int64_t gcol0 = (int64_t)tJ * BN + cc * 16;
+            if (a.mode == GEMM_GRAM) {
+                if (grow < a.M) {
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int64_t gc = gcol0 + u;
+                        if (gc < a.N) {
+                            Cf[grow * a.ldc + gc] = v[u];
+                            if (a.Chi) {
+                                const float hi = tc::tf32_round(v[u]);
+                                a.Chi[(int64_t)f * a.c_fold_stride + grow * a.ldc + gc] = hi;
+                                a.Clo[(int64_t)f * a.c_fold_stride + grow * a.ldc + gc] = v[u] - hi;
+                            }
+                        }
+                    }
+                }
+                if (tI != tJ && grow < a.N) {   // mirror into the upper tile
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int64_t gc = gcol0 + u;
+                        if (gc < a.M) {
+                            Cf[gc * a.ldc + grow] = v[u];
+                            if (a.Chi) {
+                                const float hi = tc::tf32_round(v[u]);
+                                a.Chi[(int64_t)f * a.c_fold_stride + gc * a.ldc + grow] = hi;
+                                a.Clo[(int64_t)f * a.c_fold_stride + gc * a.ldc + grow] = v[u] - hi;
+                            }
+                        }
+                    }
+                }
+            } else if (grow < a.M) {
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int64_t gc = gcol0 + u;
+                    if (gc < a.N) Cf[grow * a.ldc + a.c_col_off + gc] = v[u];
+                }
+            }
+        }
+    } else if (a.mode == GEMM_PLAIN) {
+        // empty K range: C = 0
+        const int row = warp * 32 + lane;
+        const int64_t grow = (int64_t)tI * BM + row;
+        float* Cf = a.C + (int64_t)f * a.c_fold_stride;
+        if (grow < a.M)
+            for (int u = 0; u < BN; ++u) {
+                const int64_t gc = (int64_t)tJ * BN + u;
+                if (gc < a.N) Cf[grow * a.ldc + a.c_col_off + gc] = 0.0f;
+            }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Operand preparation
+// ---------------------------------------------------------------------------
+
+// XT_hi / XT_lo [dp][Kpad]: column kc of fold j (k0[j] <= kc < k0[j+1]) holds
+// sample row o[j] + (kc - k0[j]) if that row is in fold j, else 0; rows >= d are 0.
+struct XtArgs {
+    int64_t k0[MAX_K + 1];
+    int64_t o[MAX_K + 1];
+    int k;
+};
+
+__global__ void __launch_bounds__(256)
+k_split_xt(const float* __restrict__ X, int64_t d, int64_t dp, int64_t kpad, XtArgs xa, float* __restrict__ Xh,
+           float* __restrict__ Xl)
+{
+    __shared__ float t[32][33];
+    const int64_t kc0 = (int64_t)blockIdx.x * 32, f0 = (int64_t)blockIdx.y * 32;
+    int j = 0;
+    while (j + 1 < xa.k && xa.k0[j + 1] <= kc0) ++j;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    for (int yy = ty; yy < 32; yy += 8) {
+        const int64_t kc = kc0 + yy;
+        const int64_t row = xa.o[j] + (kc - xa.k0[j]);
+        const int64_t feat = f0 + tx;
+        float v = 0.0f;
+        if (row < xa.o[j + 1] && feat < d) v = X[row * d + feat];
+        t[yy][tx] = v;
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+        const int64_t feat = f0 + yy, kc = kc0 + tx;
+        if (feat < dp && kc < kpad) {
+            const float v = t[tx][yy];
+            const float hi = tc::tf32_round(v);
+            Xh[feat * kpad + kc] = hi;
+            Xl[feat * kpad + kc] = v - hi;
+        }
+    }
+}
+
+// Wt_hi / Wt_lo [f][t*c + o][dp] = split of W[f][t][k][o].
+__global__ void __launch_bounds__(256)
+k_split_wt(const float* __restrict__ W, int q, int t0, int64_t dp, int64_t c, float* __restrict__ Wh,
+           float* __restrict__ Wl)
+{
+    const int t = t0 + blockIdx.y, f = blockIdx.z;
+    const float* Wt = W + ((int64_t)f * q + t) * dp * c;
+    float* oh = Wh + ((int64_t)f * q + t) * c * dp;
+    float* ol = Wl + ((int64_t)f * q + t) * c * dp;
+    for (int64_t kk = (int64_t)blockIdx.x * 256 + threadIdx.x; kk < dp; kk += (int64_t)gridDim.x * 256)
+        for (int o = 0; o < c; ++o) {
+            const float v = Wt[kk * c + o];
+            const float hi = tc::tf32_round(v);
+            oh[(int64_t)o * dp + kk] = hi;
+            ol[(int64_t)o * dp + kk] = v - hi;
+        }
+}
+
+// Score partials from U = G_f W (dp x ldu per fold, column t*c + o):
+// Epart[f][t][I] = sum_{rows in 64-tile I} sum_o W (U - 2 Bv), in double.
+__global__ void __launch_bounds__(64)
+k_score_reduce(const float* __restrict__ U, int64_t ldu, const float* __restrict__ W, const float* __restrict__ Bv,
+               int q, int t0, int nt, int64_t dp, int64_t c, double* __restrict__ Epart)
+{
+    __shared__ double red[64];
+    const int I = blockIdx.x, t = t0 + blockIdx.y, f = blockIdx.z;
+    const int64_t row = (int64_t)I * TB + threadIdx.x;
+    const float* wr = W + (((int64_t)f * q + t) * dp + row) * c;
+    const float* ur = U + ((int64_t)f * dp + row) * ldu + (int64_t)t * c;
+    const float* br = Bv + ((int64_t)f * dp + row) * c;
+    double s = 0.0;
+    for (int o = 0; o < c; ++o) s += (double)wr[o] * ((double)ur[o] - 2.0 * (double)br[o]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 32; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) Epart[((int64_t)f * q + t) * nt + I] = red[0];
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// 2D fp32 K-major map: `rows` rows of `cols` elements, leading dimension `ld`,
+// boxes of 32 (K) x 128 (rows), 128-byte swizzle, zero fill out of range.
+static bool make_map(CUtensorMap* m, const float* base, uint64_t cols, uint64_t rows, uint64_t ld)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn || ((uintptr_t)base & 15) || ((ld * 4) & 15)) return false;
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {ld * 4};
+    cuuint32_t box[2] = {tc::BK, tc::BM};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static cudaError_t gemm_attr()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+int64_t tc_kpad(const pichol_ctx* ctx)
+{
+    int64_t kp = 0;
+    for (int j = 0; j < ctx->cfg.k; ++j) kp += (ctx->offs[j + 1] - ctx->offs[j] + 31) / 32 * 32;
+    return kp;
+}
+
+cudaError_t launch_gram_tc(pichol_ctx* ctx, const float* X, cudaStream_t s)
+{
+    const pichol_config& c = ctx->cfg;
+    const int64_t dp = ctx->dp, kpad = ctx->kpad;
+    XtArgs xa;
+    xa.k = c.k;
+    xa.k0[0] = 0;
+    for (int j = 0; j < c.k; ++j) {
+        xa.o[j] = ctx->offs[j];
+        xa.k0[j + 1] = xa.k0[j] + (ctx->offs[j + 1] - ctx->offs[j] + 31) / 32 * 32;
+    }
+    xa.o[c.k] = ctx->offs[c.k];
+    {
+        StageScope sc_(ctx, ST_GRAM, s);
+        k_split_xt<<<dim3((unsigned)(kpad / 32), (unsigned)((dp + 31) / 32)), 256, 0, s>>>(X, c.d, dp, kpad, xa,
+                                                                                          ctx->Xh, ctx->Xl);
+    }
+    ctx->launches++;
+    CUtensorMap mh, ml;
+    if (!make_map(&mh, ctx->Xh, (uint64_t)kpad, (uint64_t)dp, (uint64_t)kpad) ||
+        !make_map(&ml, ctx->Xl, (uint64_t)kpad, (uint64_t)dp, (uint64_t)kpad))
+        return cudaErrorInvalidValue;
+    cudaError_t e = gemm_attr();
+    if (e != cudaSuccess) return e;
+    GemmArgs ga;
+    memset(&ga, 0, sizeof(ga));
+    ga.mode = GEMM_GRAM;
+    ga.passes = c.gram_passes;
+    ga.ntb = (int)((dp + tc::BM - 1) / tc::BM);
+    for (int j = 0; j <= c.k; ++j) ga.k0[j] = (int)xa.k0[j];
+    for (int j = 0; j < c.k; ++j) ga.kn[j] = (int)(ctx->offs[j + 1] - ctx->offs[j]);
+    ga.C = (float*)ctx->G;
+    ga.Chi = ctx->Gh;
+    ga.Clo = ctx->Gl;
+    ga.ldc = dp;
+    ga.M = dp;
+    ga.N = dp;
+    ga.c_fold_stride = dp * dp;
+    ga.st = ctx->status;
+    const unsigned tiles = (unsigned)((int64_t)ga.ntb * (ga.ntb + 1) / 2);
+    {
+        StageScope sc_(ctx, ST_GRAM, s);
+        k_tc_gemm<<<dim3(tiles, c.k), 128, tc::SMEM_BYTES, s>>>(mh, ml, mh, ml, ga);
+    }
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_score_tc(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s)
+{
+    const pichol_config& c = ctx->cfg;
+    const int64_t dp = ctx->dp, qc = (int64_t)c.q * c.c;
+    {
+        StageScope sc_(ctx, ST_SCORE, s);
+        k_split_wt<<<dim3((unsigned)((dp + 255) / 256), tcount, c.k), 256, 0, s>>>((const float*)ctx->W, c.q, t0, dp,
+                                                                                  c.c, ctx->Wth, ctx->Wtl);
+    }
+    ctx->launches++;
+    CUtensorMap ah, al, bh, bl;
+    if (!make_map(&ah, ctx->Gh, (uint64_t)dp, (uint64_t)(c.k * dp), (uint64_t)dp) ||
+        !make_map(&al, ctx->Gl, (uint64_t)dp, (uint64_t)(c.k * dp), (uint64_t)dp) ||
+        !make_map(&bh, ctx->Wth, (uint64_t)dp, (uint64_t)(c.k * qc), (uint64_t)dp) ||
+        !make_map(&bl, ctx->Wtl, (uint64_t)dp, (uint64_t)(c.k * qc), (uint64_t)dp))
+        return cudaErrorInvalidValue;
+    cudaError_t e = gemm_attr();
+    if (e != cudaSuccess) return e;
+    GemmArgs ga;
+    memset(&ga, 0, sizeof(ga));
+    ga.mode = GEMM_PLAIN;
+    ga.passes = 3;
+    ga.a_rows_fold = (int)dp;
+    ga.b_rows_fold = (int)qc;
+    ga.b_row_off = t0 * (int)c.c;
+    ga.c_col_off = t0 * (int)c.c;
+    ga.K = (int)dp;
+    ga.C = ctx->U2;
+    ga.ldc = ctx->ldu;
+    ga.M = dp;
+    ga.N = (int64_t)tcount * c.c;
+    ga.c_fold_stride = dp * ctx->ldu;
+    ga.st = ctx->status;
+    const unsigned mt = (unsigned)((dp + tc::BM - 1) / tc::BM), nt = (unsigned)((ga.N + tc::BN - 1) / tc::BN);
+    {
+        StageScope sc_(ctx, ST_SCORE, s);
+        k_tc_gemm<<<dim3(mt * nt, c.k), 128, tc::SMEM_BYTES, s>>>(ah, al, bh, bl, ga);
+    }
+    {
+        StageScope sc_(ctx, ST_SCORE, s);
+        k_score_reduce<<<dim3(ctx->nt, tcount, c.k), 64, 0, s>>>(ctx->U2, ctx->ldu, (const float*)ctx->W,
+                                                                 (const float*)ctx->Bv, c.q, t0, ctx->nt, dp, c.c,
+                                                                 ctx->Epart);
+    }
+    ctx->launches += 2;
+    return cudaGetLastError();
+}
+
+}  // namespace pichol

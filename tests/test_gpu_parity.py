@@ -223,3 +223,25 @@ def test_mixed_exact_cv(torch_mod, mixed_small):
     cols = list(range(0, 101, 10))
     rel = np.max(np.abs(E[:, cols] - ref.E[:, cols]) / ref.E[:, cols])
     assert rel <= MIXED_TOL, rel
+
+
+@pytest.mark.parametrize("n,d,passes,tol", [
+    (1500, 200, 3, 2e-6),    # 2 tensor-core tiles per side, 56 padded rows, uneven folds
+    (2999, 300, 3, 2e-6),    # 3 tiles per side
+    (1500, 200, 1, 2e-3),    # plain TF32 products
+])
+def test_mixed_hessian_on_tensor_cores(torch_mod, n, d, passes, tol):
+    """H_f formed by the tcgen05 Gram (split TF32 or plain TF32) against the
+    FP64 oracle's direct sum over the training rows (Eq. 2)."""
+    torch = torch_mod
+    prob = synth.mixture_ecc(n, d, 10, seed=40 + d)
+    ctx = _ctx(prob, k=5, g=4, r=2, q=9, basis="cheb_log", mode="mixed", gram_passes=passes)
+    ctx.hessian(_dev(torch, prob.X, "mixed"), _dev(torch, prob.Y, "mixed"))
+    offs = oracle.fold_offsets(n, 5)
+    for f in (0, 3):
+        H, B = ctx.export_hessian(f)
+        Hr, Br = oracle.normal_blocks(prob.X, prob.Y, offs[f], offs[f + 1])
+        err = np.max(np.abs(H.cpu().numpy() - Hr)) / np.max(np.abs(Hr))
+        assert err <= tol, (f, err)
+        assert np.max(np.abs(B.cpu().numpy() - Br)) <= 1e-5 * np.max(np.abs(Br))
+    assert ctx.info().code == 0

@@ -225,15 +225,21 @@ def test_mixed_exact_cv(torch_mod, mixed_small):
     assert rel <= MIXED_TOL, rel
 
 
-@pytest.mark.parametrize("n,d,passes,tol", [
-    (1500, 200, 3, 2e-6),    # 2 tensor-core tiles per side, 56 padded rows, uneven folds
-    (2999, 300, 3, 2e-6),    # 3 tiles per side
-    (1500, 200, 1, 2e-3),    # plain TF32 products
+@pytest.mark.parametrize("n,d,passes", [
+    (1500, 200, 3),    # 2 tensor-core tiles per side, 56 padded rows, uneven folds
+    (2999, 300, 3),    # 3 tiles per side
+    (1500, 200, 1),    # plain TF32 products
 ])
-def test_mixed_hessian_on_tensor_cores(torch_mod, n, d, passes, tol):
+def test_mixed_hessian_on_tensor_cores(torch_mod, n, d, passes):
     """H_f formed by the tcgen05 Gram (split TF32 or plain TF32) against the
-    FP64 oracle's direct sum over the training rows (Eq. 2)."""
+    FP64 oracle's direct sum over the training rows (Eq. 2).
+
+    Tolerance, relative to max |H|: split TF32 products are exact to ~2^-22
+    and the fp32 accumulation of n_train terms adds ~sqrt(n_train) 2^-24; the
+    bound used is 8 sqrt(n_train) 2^-24.  Plain TF32 rounds each operand to 11
+    bits, so a product is off by up to ~2^-10."""
     torch = torch_mod
+    tol = 8 * np.sqrt(n) * 2.0 ** -24 if passes == 3 else 2.0 ** -10
     prob = synth.mixture_ecc(n, d, 10, seed=40 + d)
     ctx = _ctx(prob, k=5, g=4, r=2, q=9, basis="cheb_log", mode="mixed", gram_passes=passes)
     ctx.hessian(_dev(torch, prob.X, "mixed"), _dev(torch, prob.Y, "mixed"))

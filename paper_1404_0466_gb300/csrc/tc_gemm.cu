@@ -13,8 +13,12 @@
 //   warp 0 lane 0  TMA producer: 128 x 32 fp32 boxes (128-byte swizzle) of
 //                  A_hi, A_lo, B_hi, B_lo per stage into a STAGES-deep ring
 //   warp 1 lane 0  MMA issuer: tcgen05.mma kind::tf32, M = 128, N = 128,
-//                  K = 8, accumulator in tensor memory (128 columns)
-//   all 4 warps    epilogue: tcgen05.ld 32 lanes x 16 columns, fp32 stores
+//                  K = 8, into one of two 128-column tensor-memory
+//                  accumulators, switching every CHUNK k-blocks
+//   warps 2..9     drain each finished chunk (tcgen05.ld) into compensated
+//                  (Kahan) fp32 totals in registers, then store C.  Summing
+//                  128-row partial sums this way keeps the accumulation error
+//                  of long K (the fold's rows) near one fp32 rounding.
 // Every wait on an mbarrier is bounded (about two seconds of clock); a wait
 // that runs out latches PICHOL_ERR_TIMEOUT, the CTA stops issuing work, waits
 // (bounded) for its own copies and MMAs, frees its tensor memory and returns.
@@ -31,7 +35,10 @@ constexpr int STAGES = 3;
 constexpr int TILE_BYTES = BM * BK * 4;        // 16 KB per operand tile
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;    // A_hi, A_lo, B_hi, B_lo
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
-constexpr int TMEM_COLS = 128;
+constexpr int TMEM_COLS = 256;                 // two 128-column accumulators
+constexpr int CHUNK = 4;                       // k-blocks (128 rows of K) per accumulator drain
+constexpr int EPI_WARPS = 8;                   // warps 2..9 drain and store
+constexpr int THREADS = 32 * (2 + EPI_WARPS);
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -163,7 +170,7 @@ struct GemmArgs {
     DevStatus* st;
 };
 
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(320, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
           const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, const GemmArgs a)
 {
@@ -172,8 +179,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
     uint64_t* empty = full + STAGES;
-    uint64_t* accum = empty + STAGES;
-    uint32_t* tmem_slot = (uint32_t*)(accum + 1);
+    uint64_t* tfull = empty + STAGES;      // [2] accumulator buffer ready to drain
+    uint64_t* tempty = tfull + 2;          // [2] accumulator buffer drained
+    uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     volatile int* consumed = abort_flag + 1;
 
@@ -194,13 +202,17 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
         arow = f * a.a_rows_fold + tI * BM;
         brow = f * a.b_rows_fold + a.b_row_off + tJ * BN;
     }
+    const int nchunks = (nk + CHUNK - 1) / CHUNK;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accum, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], EPI_WARPS);
+        }
         *abort_flag = 0;
         *consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -217,118 +229,137 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
     const uint32_t tmem = *tmem_slot;
     const uint32_t bytes_per_stage = (a.passes == 3 ? 4 : 2) * TILE_BYTES;
 
-    if (warp == 0 && lane == 0) {
-        // ---- producer ----
-        int issued = 0;
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % STAGES;
-            if (!mbar_wait(&empty[s], ((kb / STAGES) & 1) ^ 1)) { *abort_flag = 1; break; }
-            if (*abort_flag) break;
-            unsigned char* st = smem + s * STAGE_BYTES;
-            mbar_expect_tx(&full[s], bytes_per_stage);
-            const int x = kx0 + kb * BK;
-            tma_load_2d(st, &mAh, &full[s], x, arow);
-            tma_load_2d(st + 2 * TILE_BYTES, &mBh, &full[s], x, brow);
-            if (a.passes == 3) {
-                tma_load_2d(st + TILE_BYTES, &mAl, &full[s], x, arow);
-                tma_load_2d(st + 3 * TILE_BYTES, &mBl, &full[s], x, brow);
-            }
-            ++issued;
-        }
-        // wait (bounded) for copies that were issued but never consumed
-        __threadfence_block();
-        for (int kb = *consumed; kb < issued; ++kb) mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1);
-    } else if (warp == 1 && lane == 0) {
-        // ---- MMA issuer ----
-        const uint32_t idesc = idesc_tf32_128x128();
-        int kb = 0;
-        for (; kb < nk; ++kb) {
-            const int s = kb % STAGES;
-            if (*abort_flag || !mbar_wait(&full[s], (kb / STAGES) & 1)) { *abort_flag = 1; break; }
-            tc_fence_after();
-            const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
-            const uint32_t ah = base, al = base + TILE_BYTES, bh = base + 2 * TILE_BYTES, bl = base + 3 * TILE_BYTES;
-#pragma unroll
-            for (int kk = 0; kk < BK / 8; ++kk) {
-                const uint32_t off = kk * 32;   // 8 tf32 = 32 bytes along K
-                umma_tf32(tmem, sw128_desc(ah + off), sw128_desc(bh + off), idesc, (kb | kk) != 0);
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- producer ----
+            int issued = 0;
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % STAGES;
+                if (!mbar_wait(&empty[s], ((kb / STAGES) & 1) ^ 1)) { *abort_flag = 1; break; }
+                if (*abort_flag) break;
+                unsigned char* st = smem + s * STAGE_BYTES;
+                mbar_expect_tx(&full[s], bytes_per_stage);
+                const int x = kx0 + kb * BK;
+                tma_load_2d(st, &mAh, &full[s], x, arow);
+                tma_load_2d(st + 2 * TILE_BYTES, &mBh, &full[s], x, brow);
                 if (a.passes == 3) {
-                    umma_tf32(tmem, sw128_desc(ah + off), sw128_desc(bl + off), idesc, 1);
-                    umma_tf32(tmem, sw128_desc(al + off), sw128_desc(bh + off), idesc, 1);
+                    tma_load_2d(st + TILE_BYTES, &mAl, &full[s], x, arow);
+                    tma_load_2d(st + 3 * TILE_BYTES, &mBl, &full[s], x, brow);
+                }
+                ++issued;
+            }
+            // wait (bounded) for copies that were issued but never consumed
+            for (int kb = *consumed; kb < issued; ++kb) mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer: chunk ch accumulates into buffer ch & 1 ----
+            const uint32_t idesc = idesc_tf32_128x128();
+            int kb = 0;
+            for (int ch = 0; ch < nchunks && !*abort_flag; ++ch) {
+                const int b = ch & 1, use = ch >> 1;
+                if (!mbar_wait(&tempty[b], (use & 1) ^ 1)) { *abort_flag = 1; break; }
+                tc_fence_after();
+                const uint32_t acc = tmem + (uint32_t)(b * BN);
+                const int kend = (kb + CHUNK < nk) ? kb + CHUNK : nk;
+                for (int k0 = kb; kb < kend; ++kb) {
+                    const int s = kb % STAGES;
+                    if (*abort_flag || !mbar_wait(&full[s], (kb / STAGES) & 1)) { *abort_flag = 1; break; }
+                    tc_fence_after();
+                    const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+                    const uint32_t ah = base, al = base + TILE_BYTES, bh = base + 2 * TILE_BYTES,
+                                   bl = base + 3 * TILE_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 8; ++kk) {
+                        const uint32_t off = kk * 32;   // 8 tf32 = 32 bytes along K
+                        umma_tf32(acc, sw128_desc(ah + off), sw128_desc(bh + off), idesc, ((kb - k0) | kk) != 0);
+                        if (a.passes == 3) {
+                            umma_tf32(acc, sw128_desc(ah + off), sw128_desc(bl + off), idesc, 1);
+                            umma_tf32(acc, sw128_desc(al + off), sw128_desc(bh + off), idesc, 1);
+                        }
+                    }
+                    umma_commit(&empty[s]);
+                    *consumed = kb + 1;
+                }
+                umma_commit(&tfull[b]);   // buffer b holds the chunk's sum once its MMAs complete
+            }
+        }
+    } else {
+        // ---- drain: add every chunk's partial sum into compensated fp32 totals ----
+        // warp w may access TMEM lanes 32 (w % 4) .. +31: its tile rows; the
+        // first four drain warps take columns 0..63, the next four 64..127
+        float tot[64], cmp[64];
+        const int qtr = warp & 3, chalf = (warp - 2) >> 2;
+#pragma unroll
+        for (int u = 0; u < 64; ++u) { tot[u] = 0.0f; cmp[u] = 0.0f; }
+        for (int ch = 0; ch < nchunks; ++ch) {
+            const int b = ch & 1, use = ch >> 1;
+            if (!mbar_wait(&tfull[b], use & 1)) { *abort_flag = 1; break; }
+            tc_fence_after();
+            const uint32_t src = tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(b * BN + chalf * 64);
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+                float v[16];
+                tmem_ld16(src + (uint32_t)(cc * 16), v);
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {   // Kahan: tot += v
+                    const float y = v[u] - cmp[cc * 16 + u];
+                    const float t = tot[cc * 16 + u] + y;
+                    cmp[cc * 16 + u] = (t - tot[cc * 16 + u]) - y;
+                    tot[cc * 16 + u] = t;
                 }
             }
-            umma_commit(&empty[s]);
-            *consumed = kb + 1;
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&tempty[b])) : "memory");
         }
-        umma_commit(accum);   // arrives once every MMA issued above has completed
+        if (!*abort_flag) {
+        const int row = qtr * 32 + lane;           // row inside the tile
+        const int64_t grow = (int64_t)tI * BM + row;
+        const int64_t gcol0 = (int64_t)tJ * BN + chalf * 64;
+        float* Cf = a.C + (int64_t)f * a.c_fold_stride;
+        if (a.mode == GEMM_GRAM) {
+            if (grow < a.M) {
+#pragma unroll
+                for (int u = 0; u < 64; ++u) {
+                    const int64_t gc = gcol0 + u;
+                    if (gc < a.N) {
+                        Cf[grow * a.ldc + gc] = tot[u];
+                        if (a.Chi) {
+                            const float hi = tc::tf32_round(tot[u]);
+                            a.Chi[(int64_t)f * a.c_fold_stride + grow * a.ldc + gc] = hi;
+                            a.Clo[(int64_t)f * a.c_fold_stride + grow * a.ldc + gc] = tot[u] - hi;
+                        }
+                    }
+                }
+            }
+            if (tI != tJ && grow < a.N) {   // mirror into the upper tile
+#pragma unroll
+                for (int u = 0; u < 64; ++u) {
+                    const int64_t gc = gcol0 + u;
+                    if (gc < a.M) {
+                        Cf[gc * a.ldc + grow] = tot[u];
+                        if (a.Chi) {
+                            const float hi = tc::tf32_round(tot[u]);
+                            a.Chi[(int64_t)f * a.c_fold_stride + gc * a.ldc + grow] = hi;
+                            a.Clo[(int64_t)f * a.c_fold_stride + gc * a.ldc + grow] = tot[u] - hi;
+                        }
+                    }
+                }
+            }
+        } else if (grow < a.M) {
+#pragma unroll
+            for (int u = 0; u < 64; ++u) {
+                const int64_t gc = gcol0 + u;
+                if (gc < a.N) Cf[grow * a.ldc + a.c_col_off + gc] = tot[u];
+            }
+        }
+        }
     }
     __syncwarp();
-
-    // ---- epilogue: every warp reads its 32 TMEM lanes ----
-    const bool ok = mbar_wait(accum, 0);
-    if (!ok) *abort_flag = 1;
-    tc_fence_after();
-    __syncthreads();
-    if (*abort_flag) {
-        if (threadIdx.x == 0) latch_error(a.st, PICHOL_ERR_TIMEOUT, f, (int)blockIdx.x, -1);
-    } else if (nk > 0) {
-        const int row = warp * 32 + lane;          // row inside the tile
-        const int64_t grow = (int64_t)tI * BM + row;
-        float* Cf = a.C + (int64_t)f * a.c_fold_stride;
-        for (int cc = 0; cc < BN / 16; ++cc) {
-            float v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 16), v);
-            const int64_t gcol0 = (int64_t)tJ * BN + cc * 16;
-            if (a.mode == GEMM_GRAM) {
-                if (grow < a.M) {
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        const int64_t gc = gcol0 + u;
-                        if (gc < a.N) {
-                            Cf[grow * a.ldc + gc] = v[u];
-                            if (a.Chi) {
-                                const float hi = tc::tf32_round(v[u]);
-                                a.Chi[(int64_t)f * a.c_fold_stride + grow * a.ldc + gc] = hi;
-                                a.Clo[(int64_t)f * a.c_fold_stride + grow * a.ldc + gc] = v[u] - hi;
-                            }
-                        }
-                    }
-                }
-                if (tI != tJ && grow < a.N) {   // mirror into the upper tile
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        const int64_t gc = gcol0 + u;
-                        if (gc < a.M) {
-                            Cf[gc * a.ldc + grow] = v[u];
-                            if (a.Chi) {
-                                const float hi = tc::tf32_round(v[u]);
-                                a.Chi[(int64_t)f * a.c_fold_stride + gc * a.ldc + grow] = hi;
-                                a.Clo[(int64_t)f * a.c_fold_stride + gc * a.ldc + grow] = v[u] - hi;
-                            }
-                        }
-                    }
-                }
-            } else if (grow < a.M) {
-#pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int64_t gc = gcol0 + u;
-                    if (gc < a.N) Cf[grow * a.ldc + a.c_col_off + gc] = v[u];
-                }
-            }
-        }
-    } else if (a.mode == GEMM_PLAIN) {
-        // empty K range: C = 0
-        const int row = warp * 32 + lane;
-        const int64_t grow = (int64_t)tI * BM + row;
-        float* Cf = a.C + (int64_t)f * a.c_fold_stride;
-        if (grow < a.M)
-            for (int u = 0; u < BN; ++u) {
-                const int64_t gc = (int64_t)tJ * BN + u;
-                if (gc < a.N) Cf[grow * a.ldc + a.c_col_off + gc] = 0.0f;
-            }
-    }
     tc_fence_before();
     __syncthreads();
+    if (*abort_flag && threadIdx.x == 0) latch_error(a.st, PICHOL_ERR_TIMEOUT, f, (int)blockIdx.x, -1);
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
@@ -509,7 +540,7 @@ cudaError_t launch_gram_tc(pichol_ctx* ctx, const float* X, cudaStream_t s)
     const unsigned tiles = (unsigned)((int64_t)ga.ntb * (ga.ntb + 1) / 2);
     {
         StageScope sc_(ctx, ST_GRAM, s);
-        k_tc_gemm<<<dim3(tiles, c.k), 128, tc::SMEM_BYTES, s>>>(mh, ml, mh, ml, ga);
+        k_tc_gemm<<<dim3(tiles, c.k), tc::THREADS, tc::SMEM_BYTES, s>>>(mh, ml, mh, ml, ga);
     }
     ctx->launches++;
     return cudaGetLastError();
@@ -551,7 +582,7 @@ cudaError_t launch_score_tc(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s)
     const unsigned mt = (unsigned)((dp + tc::BM - 1) / tc::BM), nt = (unsigned)((ga.N + tc::BN - 1) / tc::BN);
     {
         StageScope sc_(ctx, ST_SCORE, s);
-        k_tc_gemm<<<dim3(mt * nt, c.k), 128, tc::SMEM_BYTES, s>>>(ah, al, bh, bl, ga);
+        k_tc_gemm<<<dim3(mt * nt, c.k), tc::THREADS, tc::SMEM_BYTES, s>>>(ah, al, bh, bl, ga);
     }
     {
         StageScope sc_(ctx, ST_SCORE, s);

@@ -56,22 +56,6 @@ __device__ __forceinline__ T sm_elem(const unsigned char* plane, int row, int co
     return *reinterpret_cast<const T*>(plane + swz_off(row, col, sizeof(T)));
 }
 
-// Value of system l's matrix at one element, from the staged coefficient
-// values v[m] (m < NP): sum_m w[l][m] v[m], evaluated as w0 v0 then FMAs in m.
-// In exact mode each system owns its own plane and the value is v[l].
-template <typename T, int NP, int LG, bool EXACT>
-__device__ __forceinline__ T eval_elem(const T (&w)[LG][NP > 0 ? NP : 1], const T* v, int l)
-{
-    if constexpr (EXACT) {
-        return v[l];
-    } else {
-        T s = w[l][0] * v[0];
-#pragma unroll
-        for (int m = 1; m < NP; ++m) s = fma(w[l][m], v[m], s);
-        return s;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Diagonal tiles: build, check, invert.
 // ---------------------------------------------------------------------------
@@ -115,7 +99,8 @@ k_diag_inv(DiagArgs a)
         if constexpr (EXACT) {
             v = base[e];
         } else {
-            v = w[0] * base[e];
+            // phi_0 = 1 for both bases: start at Theta_0, then FMAs in m (the solve's order)
+            v = base[e];
             for (int m = 1; m < np; ++m) v = fma(w[m], base[(int64_t)m * TILE_ELEMS + e], v);
         }
         Ls[r][c] = (c <= r) ? v : T(0);
@@ -169,10 +154,16 @@ template <typename T, int LG, int CB, int NP, bool EXACT>
 struct SolveCfg {
     static constexpr int VN = Vec16<T>::N;
     static constexpr int CBP = (CB + VN - 1) / VN * VN;
-    static constexpr int NPL = (EXACT ? LG : NP) > LG ? (EXACT ? LG : NP) : LG;  // planes in a stage
+    static constexpr int NPS = EXACT ? LG : NP;            // coefficient planes per tile
+    // rows per thread: two when the accumulators fit (2 x LG x CBP), else one
+    static constexpr int RB = (CBP * (int)sizeof(T) <= 48) ? 2 : 1;
+    static constexpr int RPT = TB / RB;                   // threads per k slice (row groups)
+    static constexpr int NKQ = 256 / RPT;                 // k slices: 8 (RB = 2) or 4 (RB = 1)
+    static constexpr int KW = TB / NKQ;                   // k slice width: 8 or 16
+    static constexpr int NPL = NPS > LG ? NPS : LG;        // planes in a stage (also holds LG inverses)
     static constexpr int PB = TILE_ELEMS * (int)sizeof(T);
-    static constexpr int ZS_BYTES = 2 * LG * TB * CBP * (int)sizeof(T);
-    static constexpr int R_BYTES = LG * TB * CBP * (int)sizeof(T);
+    static constexpr int ZS_BYTES = 2 * LG * TB * CBP * (int)sizeof(T);   // staged solved blocks, double buffer
+    static constexpr int R_BYTES = 4 * LG * TB * CBP * (int)sizeof(T);    // 4 reduction slots
     // two stages only if two CTAs still fit on an SM (227 KB); otherwise the
     // second resident CTA hides the copies
     static constexpr int STAGES = (2 * (2 * NPL * PB + ZS_BYTES + R_BYTES) <= 227 * 1024) ? 2 : 1;
@@ -180,21 +171,29 @@ struct SolveCfg {
     static constexpr int SMEM = PLANE_BYTES + ZS_BYTES + R_BYTES;
 };
 
+// Thread layout of k_solve (256 threads, LG = 2 systems): with RB rows per
+// thread (RB = 2 when 2 x LG x CBP accumulators fit in registers), thread t
+// owns rows {rp, rp + 64/RB, ...} (rp = t mod 64/RB) of the current tile for
+// both systems and the k slice [KW kq, KW kq + KW), kq = t / (64/RB); the
+// lanes of a warp share one k slice, so the staged right-hand-side values they
+// read are the same (broadcast).  The NKQ k-slice partial sums are combined in
+// a fixed order through four shared slots.
 template <typename T, int LG, int CB, int NP, bool EXACT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 k_solve(SolveArgs a)
 {
     using C = SolveCfg<T, LG, CB, NP, EXACT>;
-    constexpr int VN = C::VN, CBP = C::CBP, STAGES = C::STAGES;
-    constexpr int NPS = EXACT ? LG : NP;          // coefficient planes per tile
+    constexpr int VN = C::VN, CBP = C::CBP, STAGES = C::STAGES, NPS = C::NPS;
+    constexpr int RB = C::RB, RPT = C::RPT, KW = C::KW;
+    constexpr int ESZ = (int)sizeof(T);
     using V = typename Vec16<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* planes = smem;
-    T* Zs = reinterpret_cast<T*>(smem + C::PLANE_BYTES);            // [2][LG][64][CBP]
-    T* Rs = reinterpret_cast<T*>(smem + C::PLANE_BYTES + C::ZS_BYTES); // [LG][64][CBP]
+    T* Zs = reinterpret_cast<T*>(smem + C::PLANE_BYTES);              // [2][LG][64][CBP]
+    T* Rs = reinterpret_cast<T*>(smem + C::PLANE_BYTES + C::ZS_BYTES); // [4][LG][64][CBP]
 
     const int f = blockIdx.y, tid = threadIdx.x;
-    const int r = tid & 63, kq = tid >> 6;
+    const int rp = tid % RPT, kq = tid / RPT;
     const int64_t c = a.c, dp = a.dp;
     int tl[LG];
     bool live[LG];
@@ -204,7 +203,8 @@ k_solve(SolveArgs a)
         live[l] = li < a.tcount;
         tl[l] = a.t0 + (live[l] ? li : a.tcount - 1);
     }
-    T w[LG][NP > 0 ? NP : 1];
+    // basis weights; phi_0 = 1 for both bases, so the evaluation starts at Theta_0
+    T w[LG][NP > 1 ? NP : 1];
     if constexpr (!EXACT) {
 #pragma unroll
         for (int l = 0; l < LG; ++l)
@@ -216,14 +216,11 @@ k_solve(SolveArgs a)
     const T* rhs = (const T*)a.rhs;
     T* zb = (T*)a.zbuf;
     T* out = (T*)a.out;
-    // zero the padding columns of the staged right-hand-side blocks once
     for (int e = tid; e < 2 * LG * TB * CBP; e += 256)
         if ((e % CBP) >= c) Zs[e] = T(0);
-    for (int e = tid; e < LG * TB * CBP; e += 256)
-        if ((e % CBP) >= c) Rs[e] = T(0);
+    for (int e = tid; e < 4 * LG * TB * CBP; e += 256) Rs[e] = T(0);
 
     auto sys_base = [&](int l) -> int64_t { return ((int64_t)f * a.q + tl[l]) * dp * c; };
-    // pointer to the coefficient planes of tile (I, J) (interp: shared; exact: system 0's)
     auto tile_src = [&](int I, int J, int l) -> const T* {
         const int64_t tix = tile_index(I, J);
         if constexpr (EXACT) {
@@ -243,7 +240,6 @@ k_solve(SolveArgs a)
         }
         cp_async_commit();
     };
-    // right-hand-side block j of every live system from buffer `buf` into Zs[zi]
     constexpr int ZPER = (LG * TB * CB + 255) / 256;
     auto load_z_regs = [&](const T* buf, int j, T (&zr)[ZPER]) {
 #pragma unroll
@@ -267,9 +263,19 @@ k_solve(SolveArgs a)
             }
         }
     };
+    // interpolated value of system l from the planes' values v[0..NPS)
+    auto evalv = [&](const T* v, int l) -> T {
+        if constexpr (EXACT) {
+            return v[l];
+        } else {
+            T sacc = v[0];
+#pragma unroll
+            for (int m = 1; m < NP; ++m) sacc = fma(w[l][m], v[m], sacc);
+            return sacc;
+        }
+    };
 
-    T acc[LG][CBP];
-    // forward (UPPER = false) then back (UPPER = true)
+    T acc[RB][LG][CBP];
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
         const bool back = pass == 1;
@@ -279,9 +285,11 @@ k_solve(SolveArgs a)
             const int i = back ? a.nt - 1 - step : step;
             const int nj = back ? a.nt - 1 - i : i;       // off-diagonal tiles in this row
 #pragma unroll
-            for (int l = 0; l < LG; ++l)
+            for (int h = 0; h < RB; ++h)
 #pragma unroll
-                for (int o = 0; o < CBP; ++o) acc[l][o] = T(0);
+                for (int l = 0; l < LG; ++l)
+#pragma unroll
+                    for (int o = 0; o < CBP; ++o) acc[h][l][o] = T(0);
             if (nj > 0) {
                 auto jof = [&](int jj) { return back ? i + 1 + jj : jj; };
                 T zr[ZPER];
@@ -314,26 +322,34 @@ k_solve(SolveArgs a)
                     const unsigned char* pl = planes + stage * C::NPL * C::PB;
                     const T* zs = Zs + zi * LG * TB * CBP;
                     if (!back) {
-                        // row-owner: row r of tile (i, j), k in [16 kq, 16 kq + 16)
+                        // row-owner: rows rp + RPT h of tile (i, j)
 #pragma unroll
-                        for (int ch = 0; ch < 16 / VN; ++ch) {
-                            const int kc = (kq * 16) / VN + ch;
-                            T v[NPS][VN];
+                        for (int ch = 0; ch < KW / VN; ++ch) {
+                            const int kc = (kq * KW) / VN + ch;
+                            T v[RB][NPS][VN];
 #pragma unroll
-                            for (int m = 0; m < NPS; ++m) {
-                                V x = *reinterpret_cast<const V*>(pl + m * C::PB + r * TB * (int)sizeof(T) +
-                                                                  ((kc ^ (r & 7)) << 4));
-                                memcpy(v[m], &x, 16);
+                            for (int h = 0; h < RB; ++h) {
+                                const int r = rp + RPT * h;
+#pragma unroll
+                                for (int m = 0; m < NPS; ++m) {
+                                    V x = *reinterpret_cast<const V*>(pl + m * C::PB + r * TB * ESZ +
+                                                                      ((kc ^ (r & 7)) << 4));
+                                    memcpy(v[h][m], &x, 16);
+                                }
                             }
 #pragma unroll
                             for (int e = 0; e < VN; ++e) {
                                 const int kk = kc * VN + e;
-                                T ve[NPS];
-#pragma unroll
-                                for (int m = 0; m < NPS; ++m) ve[m] = v[m][e];
 #pragma unroll
                                 for (int l = 0; l < LG; ++l) {
-                                    const T lv = eval_elem<T, NP, LG, EXACT>(w, ve, l);
+                                    T lv[RB];
+#pragma unroll
+                                    for (int h = 0; h < RB; ++h) {
+                                        T ve[NPS];
+#pragma unroll
+                                        for (int m = 0; m < NPS; ++m) ve[m] = v[h][m][e];
+                                        lv[h] = evalv(ve, l);
+                                    }
                                     const T* zrow = zs + (l * TB + kk) * CBP;
 #pragma unroll
                                     for (int o = 0; o < CBP; o += VN) {
@@ -341,30 +357,34 @@ k_solve(SolveArgs a)
                                         T zz[VN];
                                         memcpy(zz, &z4, 16);
 #pragma unroll
-                                        for (int u = 0; u < VN; ++u) acc[l][o + u] = fma(lv, zz[u], acc[l][o + u]);
+                                        for (int u = 0; u < VN; ++u)
+#pragma unroll
+                                            for (int h = 0; h < RB; ++h)
+                                                acc[h][l][o + u] = fma(lv[h], zz[u], acc[h][l][o + u]);
                                     }
                                 }
                             }
                         }
                     } else {
-                        // column-owner: column r of tile (j, i), k (its rows) in [16 kq, 16 kq + 16);
-                        // 16 kq is a multiple of 8, so kk & 7 = e & 7 and the swizzled
-                        // column offset takes 8 values, computed once
-                        int cofs[8];
+                        // column-owner: columns rp + RPT h of tile (j, i); k = its rows KW kq + e,
+                        // and since KW kq is a multiple of 8, (KW kq + e) & 7 = e & 7
 #pragma unroll
-                        for (int x = 0; x < 8; ++x) cofs[x] = swz_off(x, r, sizeof(T));
-                        const unsigned char* plk = pl + kq * 16 * TB * (int)sizeof(T);
+                        for (int e = 0; e < KW; ++e) {
+                            const int kk = kq * KW + e;
+                            T lv[RB][LG];
 #pragma unroll
-                        for (int e16 = 0; e16 < 16; ++e16) {
-                            const int kk = kq * 16 + e16;
-                            T ve[NPS];
+                            for (int h = 0; h < RB; ++h) {
+                                const int col = rp + RPT * h;
+                                const int coff = kk * TB * ESZ + ((((col * ESZ) >> 4) ^ (e & 7)) << 4) + ((col * ESZ) & 15);
+                                T ve[NPS];
 #pragma unroll
-                            for (int m = 0; m < NPS; ++m)
-                                ve[m] = *reinterpret_cast<const T*>(plk + m * C::PB + e16 * TB * (int)sizeof(T) +
-                                                                    cofs[e16 & 7] - (e16 & 7) * TB * (int)sizeof(T));
+                                for (int m = 0; m < NPS; ++m)
+                                    ve[m] = *reinterpret_cast<const T*>(pl + m * C::PB + coff);
+#pragma unroll
+                                for (int l = 0; l < LG; ++l) lv[h][l] = evalv(ve, l);
+                            }
 #pragma unroll
                             for (int l = 0; l < LG; ++l) {
-                                const T lv = eval_elem<T, NP, LG, EXACT>(w, ve, l);
                                 const T* zrow = zs + (l * TB + kk) * CBP;
 #pragma unroll
                                 for (int o = 0; o < CBP; o += VN) {
@@ -372,7 +392,10 @@ k_solve(SolveArgs a)
                                     T zz[VN];
                                     memcpy(zz, &z4, 16);
 #pragma unroll
-                                    for (int u = 0; u < VN; ++u) acc[l][o + u] = fma(lv, zz[u], acc[l][o + u]);
+                                    for (int u = 0; u < VN; ++u)
+#pragma unroll
+                                        for (int h = 0; h < RB; ++h)
+                                            acc[h][l][o + u] = fma(lv[h][l], zz[u], acc[h][l][o + u]);
                                 }
                             }
                         }
@@ -381,35 +404,44 @@ k_solve(SolveArgs a)
                     __syncthreads();
                 }
             }
-            // reduce the four k-quarters: (((a3 + a2) + a1) + a0)
+            // combine the k slices: slot s = kq & 3; with eight slices the upper four
+            // write first and the lower four add (slot s = a[s + 4] + a[s]); the four
+            // slots are then summed in order
+            constexpr int ROUNDS = C::NKQ / 4;
 #pragma unroll 1
-            for (int qq = 3; qq >= 1; --qq) {
-                if (kq == qq) {
+            for (int round = 0; round < ROUNDS; ++round) {
+                if ((kq >> 2) == ROUNDS - 1 - round) {
+                    T* slot = Rs + (kq & 3) * LG * TB * CBP;
 #pragma unroll
-                    for (int l = 0; l < LG; ++l)
+                    for (int h = 0; h < RB; ++h)
 #pragma unroll
-                        for (int o = 0; o < CBP; ++o) {
-                            T* dst = Rs + (l * TB + r) * CBP + o;
-                            *dst = (qq == 3) ? acc[l][o] : *dst + acc[l][o];
-                        }
+                        for (int l = 0; l < LG; ++l)
+#pragma unroll
+                            for (int o = 0; o < CBP; ++o) {
+                                T* dst = slot + (l * TB + rp + RPT * h) * CBP + o;
+                                *dst = (round == 0) ? acc[h][l][o] : *dst + acc[h][l][o];
+                            }
                 }
                 __syncthreads();
             }
-            // right-hand side of the diagonal solve: rhs_i - (sum of off-diagonal products)
-            if (kq == 0) {
+            // right-hand side of the diagonal solve (threads 0 .. LG*64-1: row rr, system l)
+            // written into slot 0
+            if (tid < LG * TB) {
+                const int l = tid >> 6, rr = tid & 63;
 #pragma unroll
-                for (int l = 0; l < LG; ++l)
-#pragma unroll
-                    for (int o = 0; o < CBP; ++o) {
-                        if (o < c) {
-                            T b;
-                            const int64_t row = (int64_t)i * TB + r;
-                            if (back) b = zb[sys_base(l) + row * c + o];
-                            else if (a.rhs_per_system) b = rhs[sys_base(l) + row * c + o];
-                            else b = rhs[(int64_t)f * dp * c + row * c + o];
-                            Rs[(l * TB + r) * CBP + o] = b - (Rs[(l * TB + r) * CBP + o] + acc[l][o]);
-                        }
+                for (int o = 0; o < CBP; ++o) {
+                    if (o < c) {
+                        const int64_t row = (int64_t)i * TB + rr;
+                        T b;
+                        if (back) b = zb[sys_base(l) + row * c + o];
+                        else if (a.rhs_per_system) b = rhs[sys_base(l) + row * c + o];
+                        else b = rhs[(int64_t)f * dp * c + row * c + o];
+                        const int idx = (l * TB + rr) * CBP + o;
+                        const int sl = LG * TB * CBP;
+                        const T sum = ((Rs[idx] + Rs[sl + idx]) + Rs[2 * sl + idx]) + Rs[3 * sl + idx];
+                        Rs[idx] = b - sum;
                     }
+                }
             }
             // stage the LG diagonal inverses
 #pragma unroll
@@ -427,9 +459,9 @@ k_solve(SolveArgs a)
                 const unsigned char* pl = planes + l * C::PB;
                 const T* rsl = Rs + l * TB * CBP;
                 if (!back) {
-#pragma unroll 1
+#pragma unroll 2
                     for (int kc = 0; kc < TB / VN; ++kc) {
-                        V dv4 = *reinterpret_cast<const V*>(pl + rr * TB * (int)sizeof(T) + ((kc ^ (rr & 7)) << 4));
+                        V dv4 = *reinterpret_cast<const V*>(pl + rr * TB * ESZ + ((kc ^ (rr & 7)) << 4));
                         T dv[VN];
                         memcpy(dv, &dv4, 16);
 #pragma unroll
@@ -540,28 +572,42 @@ k_resid(ResidArgs a)
         }
         cp_async_wait<0>();
         __syncthreads();
-#pragma unroll 2
-        for (int kk = kq * 16; kk < kq * 16 + 16; ++kk) {
-            float ve[NP];
+#pragma unroll 1
+        for (int ch = 0; ch < 4; ++ch) {
+            // four consecutive k: PASS 0 reads column r of tile (j, i) (transposed use),
+            // PASS 1 reads row r of tile (i, j) as one 16-byte chunk per plane
+            float v4[NP][4];
+            const int kc = kq * 4 + ch;
 #pragma unroll
-            for (int m = 0; m < NP; ++m)
-                ve[m] = PASS == 0 ? sm_elem<float>(planes + m * PB, kk, r)   // L~_ji[kk][r]: transposed use
-                                  : sm_elem<float>(planes + m * PB, r, kk);  // L~_ij[r][kk]
+            for (int m = 0; m < NP; ++m) {
+                if (PASS == 0) {
 #pragma unroll
-            for (int l = 0; l < LG; ++l) {
-                float lv = w[l][0] * ve[0];
+                    for (int e = 0; e < 4; ++e) v4[m][e] = sm_elem<float>(planes + m * PB, kc * 4 + e, r);
+                } else {
+                    float4 x = *reinterpret_cast<const float4*>(planes + m * PB + r * TB * 4 + ((kc ^ (r & 7)) << 4));
+                    v4[m][0] = x.x; v4[m][1] = x.y; v4[m][2] = x.z; v4[m][3] = x.w;
+                }
+            }
 #pragma unroll
-                for (int m = 1; m < NP; ++m) lv = fmaf(w[l][m], ve[m], lv);
-                const float* zh = Zh + (l * TB + kk) * CBP;
-                const float* zl = Zl + (l * TB + kk) * CBP;
+            for (int e = 0; e < 4; ++e) {
+                const int kk = kc * 4 + e;
 #pragma unroll
-                for (int o = 0; o < CBP; ++o) {
-                    const float pp = lv * zh[o];
-                    const float pe = fmaf(lv, zh[o], -pp);
-                    float s, e;
-                    two_sum(sh[l][o], pp, s, e);
-                    sh[l][o] = s;
-                    sl[l][o] += e + pe + (PASS == 1 ? lv * zl[o] : 0.0f);
+                for (int l = 0; l < LG; ++l) {
+                    // same evaluation as the solve: phi_0 = 1, then FMAs in m
+                    float lv = v4[0][e];
+#pragma unroll
+                    for (int m = 1; m < NP; ++m) lv = fmaf(w[l][m], v4[m][e], lv);
+                    const float* zh = Zh + (l * TB + kk) * CBP;
+                    const float* zl = Zl + (l * TB + kk) * CBP;
+#pragma unroll
+                    for (int o = 0; o < CBP; ++o) {
+                        const float pp = lv * zh[o];
+                        const float pe = fmaf(lv, zh[o], -pp);
+                        float s2, e2;
+                        two_sum(sh[l][o], pp, s2, e2);
+                        sh[l][o] = s2;
+                        sl[l][o] += e2 + pe + (PASS == 1 ? lv * zl[o] : 0.0f);
+                    }
                 }
             }
         }
@@ -791,7 +837,7 @@ size_t solve_smem_bytes(int eb, int p, int64_t c)
     const int cbp = (cb + vn - 1) / vn * vn;
     const int np_interp = p > LG ? p : LG;
     const size_t pb = (size_t)TILE_ELEMS * eb;
-    const size_t zr = (size_t)3 * LG * TB * cbp * eb;
+    const size_t zr = (size_t)(2 + 4) * LG * TB * cbp * eb;
     const size_t stages = (2 * (2 * np_interp * pb + zr) <= 227 * 1024) ? 2 : 1;
     return stages * np_interp * pb + zr;
 }

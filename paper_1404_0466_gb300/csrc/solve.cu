@@ -153,43 +153,72 @@ struct SolveArgs {
 template <typename T, int LG, int CB, int NP, bool EXACT>
 struct SolveCfg {
     static constexpr int VN = Vec16<T>::N;
+    static constexpr int ESZ = (int)sizeof(T);
     static constexpr int CBP = (CB + VN - 1) / VN * VN;
     static constexpr int NPS = EXACT ? LG : NP;            // coefficient planes per tile
-    // rows per thread: two when the accumulators fit (2 x LG x CBP), else one
-    static constexpr int RB = (CBP * (int)sizeof(T) <= 48) ? 2 : 1;
-    static constexpr int RPT = TB / RB;                   // threads per k slice (row groups)
-    static constexpr int NKQ = 256 / RPT;                 // k slices: 8 (RB = 2) or 4 (RB = 1)
-    static constexpr int KW = TB / NKQ;                   // k slice width: 8 or 16
-    static constexpr int NPL = NPS > LG ? NPS : LG;        // planes in a stage (also holds LG inverses)
-    static constexpr int PB = TILE_ELEMS * (int)sizeof(T);
-    static constexpr int ZS_BYTES = 2 * LG * TB * CBP * (int)sizeof(T);   // staged solved blocks, double buffer
-    static constexpr int R_BYTES = 4 * LG * TB * CBP * (int)sizeof(T);    // 4 reduction slots
-    // two stages only if two CTAs still fit on an SM (227 KB); otherwise the
-    // second resident CTA hides the copies
-    static constexpr int STAGES = (2 * (2 * NPL * PB + ZS_BYTES + R_BYTES) <= 227 * 1024) ? 2 : 1;
-    static constexpr int PLANE_BYTES = STAGES * NPL * PB;
+    // rows per thread: two when the accumulators (2 x LG x CBP) fit in registers
+    static constexpr int RB = (CBP * ESZ <= 48) ? 2 : 1;
+    static constexpr int RPT = TB / RB;                   // row groups (threads per k slice)
+    static constexpr int NKQ = 256 / RPT;                 // k slices per half tile: 8 or 4
+    static constexpr int KW = (TB / 2) / NKQ;             // k per slice per half tile: 4 or 8
+    static constexpr int HPB = (TB / 2) * TB * ESZ;       // bytes of a half plane (32 x 64)
+    static constexpr int STAGE_BYTES = NPS * HPB;
+    static constexpr int DINV_BYTES = LG * TB * TB * ESZ; // the diagonal inverses reuse the ring
+    static constexpr int PLANE_BYTES = (2 * STAGE_BYTES > DINV_BYTES) ? 2 * STAGE_BYTES : DINV_BYTES;
+    static constexpr int ZS_BYTES = 2 * LG * (TB / 2) * CBP * ESZ;     // staged solved half blocks
+    static constexpr int R_BYTES = 4 * LG * TB * CBP * ESZ;            // 4 reduction slots
     static constexpr int SMEM = PLANE_BYTES + ZS_BYTES + R_BYTES;
+    static constexpr int ZPER = (LG * (TB / 2) * CB + 255) / 256;      // staged values per thread
 };
 
-// Thread layout of k_solve (256 threads, LG = 2 systems): with RB rows per
-// thread (RB = 2 when 2 x LG x CBP accumulators fit in registers), thread t
-// owns rows {rp, rp + 64/RB, ...} (rp = t mod 64/RB) of the current tile for
-// both systems and the k slice [KW kq, KW kq + KW), kq = t / (64/RB); the
-// lanes of a warp share one k slice, so the staged right-hand-side values they
-// read are the same (broadcast).  The NKQ k-slice partial sums are combined in
-// a fixed order through four shared slots.
+// Copy half of the NPS coefficient planes of one tile into a swizzled stage.
+//  forward (cols = true):  columns [32 h, 32 h + 32) of all 64 rows, 32-wide rows
+//  backward (cols = false): rows [32 h, 32 h + 32) with all 64 columns
+// In both layouts the 16-byte chunks of a row are permuted by XOR with (row & 7).
+template <typename T>
+__device__ __forceinline__ void stage_half(unsigned char* sdst, const T* gsrc, int nplanes, int h, bool cols)
+{
+    constexpr int ESZ = (int)sizeof(T);
+    constexpr int HPB = (TB / 2) * TB * ESZ;
+    if (cols) {
+        constexpr int CPR = (TB / 2) * ESZ / 16;      // chunks per 32-wide row
+        const int total = nplanes * TB * CPR;
+        for (int q = threadIdx.x; q < total; q += 256) {
+            const int pl = q / (TB * CPR), rem = q % (TB * CPR);
+            const int row = rem / CPR, ch = rem % CPR;
+            const T* g = gsrc + (int64_t)pl * TILE_ELEMS + row * TB + h * (TB / 2) + ch * (16 / ESZ);
+            cp_async16(sdst + pl * HPB + row * (TB / 2) * ESZ + ((ch ^ (row & 7)) << 4), g);
+        }
+    } else {
+        constexpr int CPR = TB * ESZ / 16;            // chunks per 64-wide row
+        const int total = nplanes * (TB / 2) * CPR;
+        for (int q = threadIdx.x; q < total; q += 256) {
+            const int pl = q / ((TB / 2) * CPR), rem = q % ((TB / 2) * CPR);
+            const int row = rem / CPR, ch = rem % CPR;
+            const T* g = gsrc + (int64_t)pl * TILE_ELEMS + (h * (TB / 2) + row) * TB + ch * (16 / ESZ);
+            cp_async16(sdst + pl * HPB + row * TB * ESZ + ((ch ^ (row & 7)) << 4), g);
+        }
+    }
+}
+
+// Thread layout of k_solve (256 threads, LG systems): with RB rows per thread,
+// thread t owns rows {rp + RPT h} (rp = t mod RPT) of the current tile for all
+// LG systems and, inside each half tile, the k slice [KW kq, KW kq + KW)
+// (kq = t / RPT); the lanes of a warp share one k slice, so the staged
+// solved-block values they read are the same (broadcast).  The NKQ k-slice
+// partial sums are combined in a fixed order through four shared slots.
 template <typename T, int LG, int CB, int NP, bool EXACT>
 __global__ void __launch_bounds__(256, 2)
 k_solve(SolveArgs a)
 {
     using C = SolveCfg<T, LG, CB, NP, EXACT>;
-    constexpr int VN = C::VN, CBP = C::CBP, STAGES = C::STAGES, NPS = C::NPS;
-    constexpr int RB = C::RB, RPT = C::RPT, KW = C::KW;
-    constexpr int ESZ = (int)sizeof(T);
+    constexpr int VN = C::VN, CBP = C::CBP, NPS = C::NPS, ESZ = C::ESZ;
+    constexpr int RB = C::RB, RPT = C::RPT, KW = C::KW, HPB = C::HPB, ZPER = C::ZPER;
+    constexpr int HT = TB / 2;
     using V = typename Vec16<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* planes = smem;
-    T* Zs = reinterpret_cast<T*>(smem + C::PLANE_BYTES);              // [2][LG][64][CBP]
+    T* Zs = reinterpret_cast<T*>(smem + C::PLANE_BYTES);              // [2][LG][32][CBP]
     T* Rs = reinterpret_cast<T*>(smem + C::PLANE_BYTES + C::ZS_BYTES); // [4][LG][64][CBP]
 
     const int f = blockIdx.y, tid = threadIdx.x;
@@ -216,11 +245,25 @@ k_solve(SolveArgs a)
     const T* rhs = (const T*)a.rhs;
     T* zb = (T*)a.zbuf;
     T* out = (T*)a.out;
-    for (int e = tid; e < 2 * LG * TB * CBP; e += 256)
-        if ((e % CBP) >= c) Zs[e] = T(0);
+    for (int e = tid; e < 2 * LG * HT * CBP; e += 256) Zs[e] = T(0);
     for (int e = tid; e < 4 * LG * TB * CBP; e += 256) Rs[e] = T(0);
 
     auto sys_base = [&](int l) -> int64_t { return ((int64_t)f * a.q + tl[l]) * dp * c; };
+    // the staged values of this thread: system l, row kk of the half block, output o
+    int64_t zg[ZPER];
+    int zs_off[ZPER];
+#pragma unroll
+    for (int u = 0; u < ZPER; ++u) {
+        const int e = tid + 256 * u;
+        if (e < LG * HT * (int)c) {
+            const int l = e / (HT * (int)c), rem = e % (HT * (int)c);
+            zg[u] = sys_base(l) + rem;
+            zs_off[u] = (l * HT + rem / (int)c) * CBP + rem % (int)c;
+        } else {
+            zg[u] = -1;
+            zs_off[u] = 0;
+        }
+    }
     auto tile_src = [&](int I, int J, int l) -> const T* {
         const int64_t tix = tile_index(I, J);
         if constexpr (EXACT) {
@@ -230,40 +273,16 @@ k_solve(SolveArgs a)
             return src + ((int64_t)f * a.ntiles + tix) * a.p * TILE_ELEMS;
         }
     };
-    auto issue_planes = [&](int I, int J, int stage) {
-        unsigned char* dst = planes + stage * C::NPL * C::PB;
+    auto issue = [&](int I, int J, int h, bool cols, int stage) {
+        unsigned char* dst = planes + stage * C::STAGE_BYTES;
         if constexpr (EXACT) {
 #pragma unroll
-            for (int l = 0; l < LG; ++l) stage_planes<T>(dst + l * C::PB, tile_src(I, J, l), 1, TB, TILE_ELEMS);
+            for (int l = 0; l < LG; ++l) stage_half<T>(dst + l * HPB, tile_src(I, J, l), 1, h, cols);
         } else {
-            stage_planes<T>(dst, tile_src(I, J, 0), NPS, TB, TILE_ELEMS);
+            stage_half<T>(dst, tile_src(I, J, 0), NPS, h, cols);
         }
         cp_async_commit();
     };
-    constexpr int ZPER = (LG * TB * CB + 255) / 256;
-    auto load_z_regs = [&](const T* buf, int j, T (&zr)[ZPER]) {
-#pragma unroll
-        for (int u = 0; u < ZPER; ++u) {
-            const int e = tid + 256 * u;
-            zr[u] = T(0);
-            if (e < LG * TB * c) {
-                const int l = e / (TB * (int)c), rem = e % (TB * (int)c);
-                zr[u] = buf[sys_base(l) + (int64_t)j * TB * c + rem];
-            }
-        }
-    };
-    auto store_z_regs = [&](int zi, const T (&zr)[ZPER]) {
-#pragma unroll
-        for (int u = 0; u < ZPER; ++u) {
-            const int e = tid + 256 * u;
-            if (e < LG * TB * c) {
-                const int l = e / (TB * (int)c), rem = e % (TB * (int)c);
-                const int kk = rem / (int)c, o = rem % (int)c;
-                Zs[((zi * LG + l) * TB + kk) * CBP + o] = zr[u];
-            }
-        }
-    };
-    // interpolated value of system l from the planes' values v[0..NPS)
     auto evalv = [&](const T* v, int l) -> T {
         if constexpr (EXACT) {
             return v[l];
@@ -284,108 +303,73 @@ k_solve(SolveArgs a)
         for (int step = 0; step < a.nt; ++step) {
             const int i = back ? a.nt - 1 - step : step;
             const int nj = back ? a.nt - 1 - i : i;       // off-diagonal tiles in this row
+            const int nit = 2 * nj;                       // half tiles
 #pragma unroll
-            for (int h = 0; h < RB; ++h)
+            for (int hh = 0; hh < RB; ++hh)
 #pragma unroll
                 for (int l = 0; l < LG; ++l)
 #pragma unroll
-                    for (int o = 0; o < CBP; ++o) acc[h][l][o] = T(0);
-            if (nj > 0) {
-                auto jof = [&](int jj) { return back ? i + 1 + jj : jj; };
-                T zr[ZPER];
-                if (STAGES == 2) {
-                    issue_planes(back ? jof(0) : i, back ? i : jof(0), 0);
-                    load_z_regs(zsrc, jof(0), zr);
-                    store_z_regs(0, zr);
-                }
+                    for (int o = 0; o < CBP; ++o) acc[hh][l][o] = T(0);
+            auto tj = [&](int it) { return back ? i + 1 + (it >> 1) : (it >> 1); };
+            T zr[ZPER];
+            auto load_z = [&](int it) {
+                const int64_t blk = ((int64_t)tj(it) * TB + (it & 1) * HT) * c;
+#pragma unroll
+                for (int u = 0; u < ZPER; ++u) zr[u] = (zg[u] >= 0) ? zsrc[zg[u] + blk] : T(0);
+            };
+            auto store_z = [&](int buf) {
+                T* zsb = Zs + buf * LG * HT * CBP;
+#pragma unroll
+                for (int u = 0; u < ZPER; ++u)
+                    if (zg[u] >= 0) zsb[zs_off[u]] = zr[u];
+            };
+            if (nit > 0) {
+                issue(back ? tj(0) : i, back ? i : tj(0), 0, !back, 0);
+                load_z(0);
+                store_z(0);
+            }
 #pragma unroll 1
-                for (int jj = 0; jj < nj; ++jj) {
-                    const int j = jof(jj);
-                    const int stage = (STAGES == 2) ? (jj & 1) : 0;
-                    const int zi = jj & 1;
-                    if (STAGES == 2) {
-                        if (jj + 1 < nj) {
-                            const int jn = jof(jj + 1);
-                            issue_planes(back ? jn : i, back ? i : jn, (jj + 1) & 1);
-                            cp_async_wait<1>();
-                        } else {
-                            cp_async_wait<0>();
-                        }
-                    } else {
-                        issue_planes(back ? j : i, back ? i : j, 0);
-                        load_z_regs(zsrc, j, zr);
-                        store_z_regs(zi, zr);
-                        cp_async_wait<0>();
-                    }
-                    __syncthreads();
-                    if (STAGES == 2 && jj + 1 < nj) load_z_regs(zsrc, jof(jj + 1), zr);
-                    const unsigned char* pl = planes + stage * C::NPL * C::PB;
-                    const T* zs = Zs + zi * LG * TB * CBP;
-                    if (!back) {
-                        // row-owner: rows rp + RPT h of tile (i, j)
+            for (int it = 0; it < nit; ++it) {
+                const int stage = it & 1, h = it & 1;
+                if (it + 1 < nit) {
+                    issue(back ? tj(it + 1) : i, back ? i : tj(it + 1), (it + 1) & 1, !back, (it + 1) & 1);
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                __syncthreads();
+                if (it + 1 < nit) load_z(it + 1);
+                const unsigned char* pl = planes + stage * C::STAGE_BYTES;
+                const T* zs = Zs + stage * LG * HT * CBP;
+                if (!back) {
+                    // row-owner: rows rp + RPT hh of tile (i, j), local k in [KW kq, KW kq + KW)
 #pragma unroll
-                        for (int ch = 0; ch < KW / VN; ++ch) {
-                            const int kc = (kq * KW) / VN + ch;
-                            T v[RB][NPS][VN];
+                    for (int ch = 0; ch < KW / VN; ++ch) {
+                        const int kc = (kq * KW) / VN + ch;
+                        T v[RB][NPS][VN];
 #pragma unroll
-                            for (int h = 0; h < RB; ++h) {
-                                const int r = rp + RPT * h;
+                        for (int hh = 0; hh < RB; ++hh) {
+                            const int r = rp + RPT * hh;
 #pragma unroll
-                                for (int m = 0; m < NPS; ++m) {
-                                    V x = *reinterpret_cast<const V*>(pl + m * C::PB + r * TB * ESZ +
-                                                                      ((kc ^ (r & 7)) << 4));
-                                    memcpy(v[h][m], &x, 16);
-                                }
-                            }
-#pragma unroll
-                            for (int e = 0; e < VN; ++e) {
-                                const int kk = kc * VN + e;
-#pragma unroll
-                                for (int l = 0; l < LG; ++l) {
-                                    T lv[RB];
-#pragma unroll
-                                    for (int h = 0; h < RB; ++h) {
-                                        T ve[NPS];
-#pragma unroll
-                                        for (int m = 0; m < NPS; ++m) ve[m] = v[h][m][e];
-                                        lv[h] = evalv(ve, l);
-                                    }
-                                    const T* zrow = zs + (l * TB + kk) * CBP;
-#pragma unroll
-                                    for (int o = 0; o < CBP; o += VN) {
-                                        V z4 = *reinterpret_cast<const V*>(zrow + o);
-                                        T zz[VN];
-                                        memcpy(zz, &z4, 16);
-#pragma unroll
-                                        for (int u = 0; u < VN; ++u)
-#pragma unroll
-                                            for (int h = 0; h < RB; ++h)
-                                                acc[h][l][o + u] = fma(lv[h], zz[u], acc[h][l][o + u]);
-                                    }
-                                }
+                            for (int m = 0; m < NPS; ++m) {
+                                V x = *reinterpret_cast<const V*>(pl + m * HPB + r * HT * ESZ + ((kc ^ (r & 7)) << 4));
+                                memcpy(v[hh][m], &x, 16);
                             }
                         }
-                    } else {
-                        // column-owner: columns rp + RPT h of tile (j, i); k = its rows KW kq + e,
-                        // and since KW kq is a multiple of 8, (KW kq + e) & 7 = e & 7
 #pragma unroll
-                        for (int e = 0; e < KW; ++e) {
-                            const int kk = kq * KW + e;
-                            T lv[RB][LG];
-#pragma unroll
-                            for (int h = 0; h < RB; ++h) {
-                                const int col = rp + RPT * h;
-                                const int coff = kk * TB * ESZ + ((((col * ESZ) >> 4) ^ (e & 7)) << 4) + ((col * ESZ) & 15);
-                                T ve[NPS];
-#pragma unroll
-                                for (int m = 0; m < NPS; ++m)
-                                    ve[m] = *reinterpret_cast<const T*>(pl + m * C::PB + coff);
-#pragma unroll
-                                for (int l = 0; l < LG; ++l) lv[h][l] = evalv(ve, l);
-                            }
+                        for (int e = 0; e < VN; ++e) {
+                            const int kk = kc * VN + e;
 #pragma unroll
                             for (int l = 0; l < LG; ++l) {
-                                const T* zrow = zs + (l * TB + kk) * CBP;
+                                T lv[RB];
+#pragma unroll
+                                for (int hh = 0; hh < RB; ++hh) {
+                                    T ve[NPS];
+#pragma unroll
+                                    for (int m = 0; m < NPS; ++m) ve[m] = v[hh][m][e];
+                                    lv[hh] = evalv(ve, l);
+                                }
+                                const T* zrow = zs + (l * HT + kk) * CBP;
 #pragma unroll
                                 for (int o = 0; o < CBP; o += VN) {
                                     V z4 = *reinterpret_cast<const V*>(zrow + o);
@@ -394,16 +378,55 @@ k_solve(SolveArgs a)
 #pragma unroll
                                     for (int u = 0; u < VN; ++u)
 #pragma unroll
-                                        for (int h = 0; h < RB; ++h)
-                                            acc[h][l][o + u] = fma(lv[h][l], zz[u], acc[h][l][o + u]);
+                                        for (int hh = 0; hh < RB; ++hh)
+                                            acc[hh][l][o + u] = fma(lv[hh], zz[u], acc[hh][l][o + u]);
                                 }
                             }
                         }
                     }
-                    if (STAGES == 2 && jj + 1 < nj) store_z_regs((jj + 1) & 1, zr);
-                    __syncthreads();
+                } else {
+                    // column-owner: columns rp + RPT hh of tile (j, i); k = local rows KW kq + e
+#pragma unroll
+                    for (int e = 0; e < KW; ++e) {
+                        const int kk = kq * KW + e;
+                        T lv[RB][LG];
+#pragma unroll
+                        for (int hh = 0; hh < RB; ++hh) {
+                            const int col = rp + RPT * hh;
+                            const int coff = kk * TB * ESZ + ((((col * ESZ) >> 4) ^ (kk & 7)) << 4) + ((col * ESZ) & 15);
+                            T ve[NPS];
+#pragma unroll
+                            for (int m = 0; m < NPS; ++m) ve[m] = *reinterpret_cast<const T*>(pl + m * HPB + coff);
+#pragma unroll
+                            for (int l = 0; l < LG; ++l) lv[hh][l] = evalv(ve, l);
+                        }
+#pragma unroll
+                        for (int l = 0; l < LG; ++l) {
+                            const T* zrow = zs + (l * HT + kk) * CBP;
+#pragma unroll
+                            for (int o = 0; o < CBP; o += VN) {
+                                V z4 = *reinterpret_cast<const V*>(zrow + o);
+                                T zz[VN];
+                                memcpy(zz, &z4, 16);
+#pragma unroll
+                                for (int u = 0; u < VN; ++u)
+#pragma unroll
+                                    for (int hh = 0; hh < RB; ++hh)
+                                        acc[hh][l][o + u] = fma(lv[hh][l], zz[u], acc[hh][l][o + u]);
+                            }
+                        }
+                    }
                 }
+                if (it + 1 < nit) store_z((it + 1) & 1);
+                __syncthreads();
             }
+            // stage the LG diagonal inverses (the ring is free now) while the
+            // k-slice partial sums are combined
+#pragma unroll
+            for (int l = 0; l < LG; ++l)
+                stage_planes<T>(planes + l * TB * TB * ESZ,
+                                dinv + (((int64_t)f * a.q + tl[l]) * a.nt + i) * TILE_ELEMS, 1, TB, TILE_ELEMS);
+            cp_async_commit();
             // combine the k slices: slot s = kq & 3; with eight slices the upper four
             // write first and the lower four add (slot s = a[s + 4] + a[s]); the four
             // slots are then summed in order
@@ -413,18 +436,18 @@ k_solve(SolveArgs a)
                 if ((kq >> 2) == ROUNDS - 1 - round) {
                     T* slot = Rs + (kq & 3) * LG * TB * CBP;
 #pragma unroll
-                    for (int h = 0; h < RB; ++h)
+                    for (int hh = 0; hh < RB; ++hh)
 #pragma unroll
                         for (int l = 0; l < LG; ++l)
 #pragma unroll
                             for (int o = 0; o < CBP; ++o) {
-                                T* dst = slot + (l * TB + rp + RPT * h) * CBP + o;
-                                *dst = (round == 0) ? acc[h][l][o] : *dst + acc[h][l][o];
+                                T* dst = slot + (l * TB + rp + RPT * hh) * CBP + o;
+                                *dst = (round == 0) ? acc[hh][l][o] : *dst + acc[hh][l][o];
                             }
                 }
                 __syncthreads();
             }
-            // right-hand side of the diagonal solve (threads 0 .. LG*64-1: row rr, system l)
+            // right-hand side of the diagonal solve (threads 0 .. LG*64-1: row rr, system l),
             // written into slot 0
             if (tid < LG * TB) {
                 const int l = tid >> 6, rr = tid & 63;
@@ -443,12 +466,6 @@ k_solve(SolveArgs a)
                     }
                 }
             }
-            // stage the LG diagonal inverses
-#pragma unroll
-            for (int l = 0; l < LG; ++l)
-                stage_planes<T>(planes + l * C::PB, dinv + (((int64_t)f * a.q + tl[l]) * a.nt + i) * TILE_ELEMS, 1,
-                                TB, TILE_ELEMS);
-            cp_async_commit();
             cp_async_wait<0>();
             __syncthreads();
             if (tid < LG * TB) {
@@ -456,7 +473,7 @@ k_solve(SolveArgs a)
                 T x[CBP];
 #pragma unroll
                 for (int o = 0; o < CBP; ++o) x[o] = T(0);
-                const unsigned char* pl = planes + l * C::PB;
+                const unsigned char* pl = planes + l * TB * TB * ESZ;
                 const T* rsl = Rs + l * TB * CBP;
                 if (!back) {
 #pragma unroll 2
@@ -835,11 +852,10 @@ size_t solve_smem_bytes(int eb, int p, int64_t c)
 {
     const int LG = 2, cb = pick_cb(c), vn = 16 / eb;
     const int cbp = (cb + vn - 1) / vn * vn;
-    const int np_interp = p > LG ? p : LG;
-    const size_t pb = (size_t)TILE_ELEMS * eb;
-    const size_t zr = (size_t)(2 + 4) * LG * TB * cbp * eb;
-    const size_t stages = (2 * (2 * np_interp * pb + zr) <= 227 * 1024) ? 2 : 1;
-    return stages * np_interp * pb + zr;
+    const int nps = p > LG ? p : LG;   // interpolated (p planes) or exact (LG planes)
+    const size_t hpb = (size_t)(TB / 2) * TB * eb;
+    const size_t ring = 2 * nps * hpb > (size_t)LG * TB * TB * eb ? 2 * nps * hpb : (size_t)LG * TB * TB * eb;
+    return ring + (size_t)2 * LG * (TB / 2) * cbp * eb + (size_t)4 * LG * TB * cbp * eb;
 }
 
 template <typename T, int LG, int CB, int NP, bool EXACT>

@@ -116,12 +116,17 @@ k_xty(const T* __restrict__ X, const T* __restrict__ Y, int64_t d, int64_t dp, i
 #pragma unroll
         for (int u = 0; u < 16; ++u) acc[u] = T(0);
         const int64_t re = rb + 32 < r1 ? rb + 32 : r1;
-        for (int64_t row = rb; row < re; ++row) {
-            const T x = col < d ? X[row * d + col] : T(0);
+        // 32 rows, fully unrolled so the loads of X are independent of each other
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int64_t o = oc + 4 * u;
-                if (o < c) acc[u] = fma(x, Y[row * c + o], acc[u]);
+        for (int rr = 0; rr < 32; ++rr) {
+            const int64_t row = rb + rr;
+            if (row < re) {
+                const T x = col < d ? X[row * d + col] : T(0);
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int64_t o = oc + 4 * u;
+                    if (o < c) acc[u] = fma(x, Y[row * c + o], acc[u]);
+                }
             }
         }
 #pragma unroll

@@ -537,18 +537,20 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 }
 
 template <int LG, int CB, int NP, int PASS>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 k_resid(ResidArgs a)
 {
-    constexpr int CBP = (CB + 3) / 4 * 4;
-    constexpr int PB = TILE_ELEMS * 4;
+    constexpr int CBP = CB;                     // exact column count (no vector loads of Z here)
+    constexpr int HT = TB / 2;
+    constexpr int HPB = HT * TB * 4;            // half plane, fp32
+    constexpr int STAGE = NP * HPB;
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char* planes = smem;                                        // NP planes
-    float* Zh = reinterpret_cast<float*>(smem + NP * PB);                // [LG][64][CBP]
-    float* Zl = Zh + LG * TB * CBP;                                      // [LG][64][CBP]
-    double* Rd = reinterpret_cast<double*>(Zl + LG * TB * CBP);          // [LG][64][CBP]
+    unsigned char* planes = smem;                                          // 2 stages
+    float* Zh = reinterpret_cast<float*>(smem + 2 * STAGE);                // [2][LG][32][CBP]
+    float* Zl = Zh + 2 * LG * HT * CBP;                                    // [2][LG][32][CBP]
+    double* Rd = reinterpret_cast<double*>(Zl + 2 * LG * HT * CBP);       // [LG][64][CBP]
     const int i = blockIdx.x, f = blockIdx.z, tid = threadIdx.x;
-    const int r = tid & 63, kq = tid >> 6;
+    const int r = tid & 63, kq = tid >> 6;      // row (PASS 1) / column (PASS 0) r, k slice [8 kq, 8 kq + 8)
     const int64_t c = a.c, dp = a.dp;
     int tl[LG];
     bool live[LG];
@@ -563,59 +565,112 @@ k_resid(ResidArgs a)
     for (int l = 0; l < LG; ++l)
 #pragma unroll
         for (int m = 0; m < NP; ++m) w[l][m] = (float)a.phi[(int64_t)tl[l] * a.p + m];
-    for (int e = tid; e < LG * TB * CBP; e += 256) { Zh[e] = 0.0f; Zl[e] = 0.0f; }
     float sh[LG][CBP], sl[LG][CBP];
 #pragma unroll
     for (int l = 0; l < LG; ++l)
 #pragma unroll
         for (int o = 0; o < CBP; ++o) { sh[l][o] = 0.0f; sl[l][o] = 0.0f; }
+    for (int e = tid; e < 2 * 2 * LG * HT * CBP; e += 256) Zh[e] = 0.0f;   // Zh and Zl, both buffers
+    // staged values of this thread (precomputed offsets): system l, row kk, output o
+    constexpr int ZPER = (LG * HT * CB + 255) / 256;
+    int64_t zg[ZPER];
+    int zoff[ZPER];
+#pragma unroll
+    for (int u = 0; u < ZPER; ++u) {
+        const int e = tid + 256 * u;
+        if (e < LG * HT * (int)c) {
+            const int l = e / (HT * (int)c), rem = e % (HT * (int)c);
+            zg[u] = ((int64_t)f * a.q + tl[l]) * dp * c + rem;
+            zoff[u] = (l * HT + rem / (int)c) * CBP + rem % (int)c;
+        } else {
+            zg[u] = -1;
+            zoff[u] = 0;
+        }
+    }
     const int jlo = PASS == 0 ? i : 0, jhi = PASS == 0 ? a.nt - 1 : i;
-#pragma unroll 1
-    for (int j = jlo; j <= jhi; ++j) {
-        __syncthreads();
+    const int nit = 2 * (jhi - jlo + 1);
+    auto issue = [&](int it) {
+        const int j = jlo + (it >> 1), h = it & 1;
         const int64_t tix = PASS == 0 ? tile_index(j, i) : tile_index(i, j);
-        stage_planes<float>(planes, a.theta + ((int64_t)f * a.ntiles + tix) * a.p * TILE_ELEMS, NP, TB, TILE_ELEMS);
+        // PASS 0 reads columns r of tile (j, i): its k are the tile's rows (half = rows);
+        // PASS 1 reads rows r of tile (i, j): its k are the tile's columns (half = columns)
+        stage_half<float>(planes + (it & 1) * STAGE, a.theta + ((int64_t)f * a.ntiles + tix) * a.p * TILE_ELEMS, NP,
+                          h, PASS == 1);
         cp_async_commit();
-        for (int e = tid; e < LG * TB * c; e += 256) {
-            const int l = e / (TB * (int)c), rem = e % (TB * (int)c);
-            const int kk = rem / (int)c, o = rem % (int)c;
-            const int64_t g = ((int64_t)f * a.q + tl[l]) * dp * c + (int64_t)j * TB * c + rem;
-            if (PASS == 0) {
-                Zh[(l * TB + kk) * CBP + o] = a.W[g];
-            } else {
-                Zh[(l * TB + kk) * CBP + o] = a.uhi[g];
-                Zl[(l * TB + kk) * CBP + o] = a.ulo[g];
+    };
+    float zr[2][ZPER];
+    auto load_z = [&](int it) {
+        const int j = jlo + (it >> 1), h = it & 1;
+        const int64_t blk = ((int64_t)j * TB + h * HT) * c;
+#pragma unroll
+        for (int u = 0; u < ZPER; ++u) {
+            if (zg[u] >= 0) {
+                if (PASS == 0) {
+                    zr[0][u] = a.W[zg[u] + blk];
+                } else {
+                    zr[0][u] = a.uhi[zg[u] + blk];
+                    zr[1][u] = a.ulo[zg[u] + blk];
+                }
             }
         }
-        cp_async_wait<0>();
-        __syncthreads();
+    };
+    auto store_z = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < ZPER; ++u) {
+            if (zg[u] >= 0) {
+                Zh[buf * LG * HT * CBP + zoff[u]] = zr[0][u];
+                Zl[buf * LG * HT * CBP + zoff[u]] = (PASS == 1) ? zr[1][u] : 0.0f;
+            }
+        }
+    };
+    issue(0);
+    load_z(0);
+    store_z(0);
 #pragma unroll 1
-        for (int ch = 0; ch < 4; ++ch) {
-            // four consecutive k: PASS 0 reads column r of tile (j, i) (transposed use),
-            // PASS 1 reads row r of tile (i, j) as one 16-byte chunk per plane
+    for (int it = 0; it < nit; ++it) {
+        if (it + 1 < nit) {
+            issue(it + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        if (it + 1 < nit) load_z(it + 1);
+        const unsigned char* pl = planes + (it & 1) * STAGE;
+        const float* zhb = Zh + (it & 1) * LG * HT * CBP;
+        const float* zlb = Zl + (it & 1) * LG * HT * CBP;
+#pragma unroll 1
+        for (int ch = 0; ch < 2; ++ch) {
             float v4[NP][4];
-            const int kc = kq * 4 + ch;
+            const int k0 = kq * 8 + ch * 4;     // local k (0..31) of the half
 #pragma unroll
             for (int m = 0; m < NP; ++m) {
                 if (PASS == 0) {
+                    // column r of the staged rows k0..k0+3 (64-wide rows)
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) v4[m][e] = sm_elem<float>(planes + m * PB, kc * 4 + e, r);
+                    for (int e = 0; e < 4; ++e) {
+                        const int kk = k0 + e;
+                        v4[m][e] = *reinterpret_cast<const float*>(pl + m * HPB + kk * TB * 4 +
+                                                                   ((((r * 4) >> 4) ^ (kk & 7)) << 4) + ((r * 4) & 15));
+                    }
                 } else {
-                    float4 x = *reinterpret_cast<const float4*>(planes + m * PB + r * TB * 4 + ((kc ^ (r & 7)) << 4));
+                    // row r, columns k0..k0+3 of the staged 32-wide rows: one 16-byte chunk
+                    const int kc = k0 >> 2;
+                    float4 x = *reinterpret_cast<const float4*>(pl + m * HPB + r * HT * 4 + ((kc ^ (r & 7)) << 4));
                     v4[m][0] = x.x; v4[m][1] = x.y; v4[m][2] = x.z; v4[m][3] = x.w;
                 }
             }
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int kk = kc * 4 + e;
+                const int kk = k0 + e;
 #pragma unroll
                 for (int l = 0; l < LG; ++l) {
                     // same evaluation as the solve: phi_0 = 1, then FMAs in m
                     float lv = v4[0][e];
 #pragma unroll
                     for (int m = 1; m < NP; ++m) lv = fmaf(w[l][m], v4[m][e], lv);
-                    const float* zh = Zh + (l * TB + kk) * CBP;
-                    const float* zl = Zl + (l * TB + kk) * CBP;
+                    const float* zh = zhb + (l * HT + kk) * CBP;
+                    const float* zl = zlb + (l * HT + kk) * CBP;
 #pragma unroll
                     for (int o = 0; o < CBP; ++o) {
                         const float pp = lv * zh[o];
@@ -628,9 +683,10 @@ k_resid(ResidArgs a)
                 }
             }
         }
+        if (it + 1 < nit) store_z((it + 1) & 1);
+        __syncthreads();
     }
-    __syncthreads();
-    // combine the four k-quarters in double
+    // combine the four k slices in double
 #pragma unroll 1
     for (int qq = 3; qq >= 0; --qq) {
         if (kq == qq) {
@@ -938,8 +994,7 @@ static cudaError_t score_dispatch(pichol_ctx* ctx, const ScoreArgs& sc, cudaStre
 template <int LG, int CB, int NP, int PASS>
 static cudaError_t run_resid(pichol_ctx* ctx, const ResidArgs& ra, cudaStream_t s)
 {
-    constexpr int CBP = (CB + 3) / 4 * 4;
-    const int smem = NP * TILE_ELEMS * 4 + 2 * LG * TB * CBP * 4 + LG * TB * CBP * 8;
+    const int smem = 2 * NP * (TB / 2) * TB * 4 + 2 * 2 * LG * (TB / 2) * CB * 4 + LG * TB * CB * 8;
     static bool done = false;
     if (!done) {
         cudaError_t e = cudaFuncSetAttribute(k_resid<LG, CB, NP, PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -972,11 +1027,14 @@ static cudaError_t resid_np(pichol_ctx* ctx, const ResidArgs& ra, cudaStream_t s
 template <int PASS>
 static cudaError_t resid_dispatch(pichol_ctx* ctx, const ResidArgs& ra, cudaStream_t s)
 {
-    switch (pick_cb(ctx->cfg.c)) {
-    case 4: return resid_np<2, 4, PASS>(ctx, ra, s);
-    case 12: return resid_np<2, 12, PASS>(ctx, ra, s);
-    default: return resid_np<1, 32, PASS>(ctx, ra, s);
-    }
+    // the residual reads its staged values one at a time, so it carries exactly
+    // the columns it needs: 1, 4, 10, 12 or 32 (a larger count pads with zeros)
+    const int64_t c = ctx->cfg.c;
+    if (c <= 1) return resid_np<2, 1, PASS>(ctx, ra, s);
+    if (c <= 4) return resid_np<2, 4, PASS>(ctx, ra, s);
+    if (c <= 10) return resid_np<2, 10, PASS>(ctx, ra, s);
+    if (c <= 12) return resid_np<2, 12, PASS>(ctx, ra, s);
+    return resid_np<1, 32, PASS>(ctx, ra, s);
 }
 
 template <typename T, bool EXACT>

@@ -420,3 +420,77 @@ def cv(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e
         res.Ebar = E.mean(axis=0)
         res.t_star = argmin_first(res.Ebar)
     return res
+
+
+# ----------------------------------------------------------------------------
+# gradient of the mean hold-out error with respect to log(lambda)
+# ----------------------------------------------------------------------------
+
+@dataclass
+class GradResult:
+    E: np.ndarray        # k hold-out MSEs at lambda
+    dE: np.ndarray       # k derivatives dE_f / d log(lambda)
+    Ebar: float
+    dEbar: float
+
+
+def _holdout_and_grad(Xv, Yv, Bf, L, dL, lam):
+    """E = ||Y_v - X_v W||^2 / (n_v c) with W = A^{-1} B_f, A = L L^T, and
+    dE/dlog(lambda) = lambda dE/dlambda where dA/dlambda = dL L^T + L dL^T:
+      dW = -A^{-1} (dA) W,   dE/dlambda = -(2 / (n_v c)) <X_v^T (Y_v - X_v W), dW>
+    (chain rule on the definitions; no identity of the paper is needed)."""
+    nv, c = Yv.shape
+    W = solve_factored(L, Bf)
+    R = Yv - Xv @ W
+    E = float(np.sum(R * R)) / (nv * c)
+    dA_W = dL @ (L.T @ W) + L @ (dL.T @ W)
+    dW = -solve_factored(L, dA_W)
+    dE = -2.0 / (nv * c) * float(np.sum((Xv.T @ R) * dW))
+    return E, lam * dE
+
+
+def holdout_grad(X, Y, *, k: int, g: int, r: int, q: int, log_lam: float, lo: float = 1e-3, hi: float = 1e1,
+                 basis: str = BASIS_CHEB_LOG, exact: bool = False, scale_by_trace: bool = True) -> GradResult:
+    """Hold-out MSE per fold at lambda = exp(log_lam) and its derivative with
+    respect to log(lambda).
+
+    exact=False: through the interpolated factor L(lambda) = sum_m phi_m(lambda)
+    Theta_m of Algorithm 1 (sampled at the same grid indices as ``cv``), so
+    dL/dlambda = sum_m phi_m'(lambda) Theta_m.
+    exact=True: through the exact factor of H_f + lambda I, where
+    dA/dlambda = I, so dW/dlambda = -A^{-1} W.
+    """
+    X, Y = _f64(X), _f64(Y)
+    n, d = X.shape
+    p = r + 1
+    lam = float(np.exp(log_lam))
+    offs = fold_offsets(n, k)
+    tau = trace_scale(X) if scale_by_trace else 1.0
+    grid = lambda_grid(tau, q, lo, hi)
+    sidx = sample_indices(q, g)
+    lam_s = grid[sidx]
+    E = np.empty(k)
+    dE = np.empty(k)
+    for f in range(k):
+        r0, r1 = offs[f], offs[f + 1]
+        Hf, Bf = normal_blocks(X, Y, r0, r1)
+        Xv, Yv = X[r0:r1], Y[r0:r1]
+        nv, c = Yv.shape
+        if exact:
+            L = cholesky(Hf + lam * np.eye(d))
+            W = solve_factored(L, Bf)
+            R = Yv - Xv @ W
+            E[f] = float(np.sum(R * R)) / (nv * c)
+            dW = -solve_factored(L, W)                   # dA/dlambda = I
+            dE[f] = lam * (-2.0 / (nv * c)) * float(np.sum((Xv.T @ R) * dW))
+            continue
+        T = np.empty((g, d * (d + 1) // 2))
+        for s in range(g):
+            T[s] = vec_lower(cholesky(Hf + lam_s[s] * np.eye(d)))
+        Theta = lstsq(basis_values(basis, lam_s, lam_s, p), T)
+        phi = basis_values(basis, [lam], lam_s, p)[0]
+        dphi = basis_derivs(basis, [lam], lam_s, p)[0]
+        L = unvec_lower(eval_poly(phi, Theta), d)
+        dL = unvec_lower(eval_poly(dphi, Theta), d)
+        E[f], dE[f] = _holdout_and_grad(Xv, Yv, Bf, L, dL, lam)
+    return GradResult(E=E, dE=dE, Ebar=float(E.mean()), dEbar=float(dE.mean()))

@@ -398,3 +398,48 @@ def test_diagonal_hessian_interpolation_error_is_small():
         Lt = orc.unvec_lower(orc.basis_values(orc.BASIS_MONO, [lam], lam_s, 3)[0] @ Theta, 4)
         assert np.all(np.abs(np.diag(Lt) - np.sqrt(h + lam)) <= tol)
         assert np.abs(np.tril(Lt, -1)).max() < 1e-14
+
+
+# --------------------------------------------------------------------------
+# gradient of the hold-out error in log(lambda)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("exact,basis", [(True, "mono"), (False, orc.BASIS_CHEB_LOG), (False, orc.BASIS_MONO)])
+def test_holdout_gradient_matches_central_differences(exact, basis):
+    """dE/dlog(lambda) against central differences of E itself (h = 1e-4 in
+    log lambda), for the exact factor and for the interpolated factor."""
+    p = synth.spectral_gaussian(240, 16, 3, seed=50)
+    kw = dict(k=4, g=4, r=2, q=9, basis=basis, exact=exact)
+    for ll in (np.log(0.05), np.log(2.0)):
+        tau = orc.trace_scale(p.X)
+        ll = ll + np.log(tau)
+        gr = orc.holdout_grad(p.X, p.Y, log_lam=ll, **kw)
+        h = 1e-4
+        ep = orc.holdout_grad(p.X, p.Y, log_lam=ll + h, **kw).E
+        em = orc.holdout_grad(p.X, p.Y, log_lam=ll - h, **kw).E
+        fd = (ep - em) / (2 * h)
+        np.testing.assert_allclose(gr.dE, fd, rtol=1e-5, atol=1e-9 * np.abs(gr.E).max())
+
+
+def test_exact_gradient_matches_eigen_closed_form():
+    """For exact ridge, E(lambda) has the closed form through H = Q diag(mu) Q^T;
+    its derivative in log(lambda) is lambda * sum over the eigenbasis."""
+    p = synth.spectral_gaussian(200, 12, 2, seed=51)
+    k = 4
+    offs = orc.fold_offsets(200, k)
+    lam = 0.3 * orc.trace_scale(p.X)
+    gr = orc.holdout_grad(p.X, p.Y, k=k, g=2, r=1, q=3, log_lam=np.log(lam), exact=True)
+    for f in range(k):
+        keep = np.r_[0:offs[f], offs[f + 1]:200]
+        H = p.X[keep].T @ p.X[keep]
+        B = p.X[keep].T @ p.Y[keep]
+        mu, Q = np.linalg.eigh(H)
+        Xv, Yv = p.X[offs[f]:offs[f + 1]], p.Y[offs[f]:offs[f + 1]]
+        Bq = Q.T @ B
+        W = Q @ (Bq / (mu + lam)[:, None])
+        dW = Q @ (-Bq / ((mu + lam) ** 2)[:, None])
+        R = Yv - Xv @ W
+        nvc = R.size
+        assert abs(gr.E[f] - np.sum(R * R) / nvc) <= 1e-10 * gr.E[f]
+        ref = lam * (-2.0 / nvc) * np.sum((Xv.T @ R) * dW)
+        assert abs(gr.dE[f] - ref) <= 1e-8 * abs(ref) + 1e-14

@@ -178,6 +178,21 @@ PICHOL_API pichol_status pichol_eval_holdout(pichol_ctx* ctx, double* E_out, int
 PICHOL_API pichol_status pichol_eval_holdout_exact(pichol_ctx* ctx, double* E_out, int32_t* t_star,
                                         void* W_out, void* stream);
 
+/*
+ * Hold-out error and its derivative in log(lambda) at any lambda = exp(log_lam),
+ * through the interpolated factor (after pichol_fit): with
+ * L~ = sum_m phi_m(lambda) Theta_m and L~' = sum_m phi_m'(lambda) Theta_m
+ * (Sec. 3.3's polynomials and their derivative), A = L~ L~^T,
+ * W = A^{-1} B_f, V = G_f W - Bv_f, U = A^{-1} V:
+ *   E_out[f]  = ||Y_f - X_f W||^2 / (n_f c)
+ *   dE_out[f] = lambda * (-2 / (n_f c)) (<L~'^T U, L~^T W> + <L~^T U, L~'^T W>)
+ * which is d E_f / d log(lambda) (chain rule on dW = -A^{-1} dA W; not in the
+ * paper).  E_out, dE_out: device, k doubles each.  The diagonal of L~ at this
+ * lambda is not checked for usability.  log_lam must be finite (|.| <= 700).
+ */
+PICHOL_API pichol_status pichol_holdout_grad(pichol_ctx* ctx, double log_lam, double* E_out, double* dE_out,
+                                             void* stream);
+
 /* Device copy of the q grid lambdas (after pichol_hessian). */
 PICHOL_API pichol_status pichol_get_lambdas(pichol_ctx* ctx, double* lam_out, void* stream);
 

@@ -28,7 +28,7 @@ EXPORTS = [
     "pichol_eval_holdout_exact", "pichol_get_lambdas", "pichol_export_factor", "pichol_export_theta",
     "pichol_export_hessian", "pichol_get_info", "pichol_clear_status", "pichol_launch_count",
     "pichol_destroy", "pichol_status_string", "pichol_set_timing", "pichol_stage_times",
-    "pichol_fold_rhs_noalloc",
+    "pichol_fold_rhs_noalloc", "pichol_holdout_grad",
 ]
 STAGES = ["gram", "xty", "setup", "chol_init", "chol_diag", "chol_panel", "chol_update", "fit",
           "diag_inv", "solve", "resid", "score", "select", "misc"]
@@ -87,6 +87,7 @@ def lib():
         "pichol_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "pichol_set_timing": ([vp, i32], ctypes.c_int),
         "pichol_fold_rhs_noalloc": ([i32, vp, vp, i64, i64, i64, i32, vp, vp, vp], ctypes.c_int),
+        "pichol_holdout_grad": ([vp, ctypes.c_double, vp, vp, vp], ctypes.c_int),
         "pichol_stage_times": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32, vp],
                                ctypes.c_int),
     }
@@ -195,6 +196,17 @@ class Context:
         self.fit(stream)
         return self.eval_holdout(want_w, out, stream)
 
+    def holdout_grad(self, log_lam: float, stream=None):
+        """(E, dE/dlog(lambda)) per fold at lambda = exp(log_lam), through the
+        interpolated factor; device float64 tensors of k entries."""
+        import torch
+        E = torch.empty((self.cfg.k,), dtype=torch.float64, device="cuda")
+        dE = torch.empty((self.cfg.k,), dtype=torch.float64, device="cuda")
+        _check(lib().pichol_holdout_grad(self._h, float(log_lam), ctypes.c_void_p(E.data_ptr()),
+                                         ctypes.c_void_p(dE.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
+               "pichol_holdout_grad")
+        return E, dE
+
     # -- inspection ----------------------------------------------------------
     def lambdas(self, stream=None):
         import torch
@@ -262,3 +274,24 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def holdout_loss(ctx: "Context", log_lam):
+    """Mean hold-out error over the folds as a differentiable function of a
+    scalar log(lambda) tensor: the forward pass and the derivative both come
+    from pichol_holdout_grad (one call), the backward pass scales it."""
+    import torch
+
+    class _HoldoutLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, ll):
+            E, dE = ctx.holdout_grad(float(ll.detach().cpu()))
+            fctx.save_for_backward(dE.mean().to(ll.device, ll.dtype))
+            return E.mean().to(ll.device, ll.dtype)
+
+        @staticmethod
+        def backward(fctx, g):
+            (dEbar,) = fctx.saved_tensors
+            return g * dEbar
+
+    return _HoldoutLoss.apply(log_lam)

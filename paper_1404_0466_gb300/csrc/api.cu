@@ -56,6 +56,13 @@ size_t plan(pichol_ctx* ctx, char* base)
         ctx->Wtl = (float*)take((size_t)(k * qc * dp * 4));
         ctx->U2 = (float*)take((size_t)(k * dp * ctx->ldu * 4));
     }
+    ctx->gW = take((size_t)(3 * k * dp * cc * eb));
+    ctx->gDinv = take((size_t)(k * nt * TILE_ELEMS * eb));
+    ctx->gP = (double*)take((size_t)(4 * k * dp * cc * sizeof(double)));
+    ctx->gphi = (double*)take((size_t)(2 * MAX_P + 1) * sizeof(double));
+    ctx->gflags = (int*)take((size_t)(k * nt * sizeof(int)));
+    ctx->gdmax = (float*)take((size_t)(k * nt * sizeof(float)));
+    ctx->gdmin = (float*)take((size_t)(k * nt * sizeof(float)));
     ctx->Epart = (double*)take((size_t)(k * q * nt * sizeof(double)));
     ctx->E = (double*)take((size_t)(k * q * sizeof(double)));
     ctx->flags = (int*)take((size_t)(k * q * nt * sizeof(int)));
@@ -209,6 +216,15 @@ pichol_status pichol_eval_holdout_exact(pichol_ctx* ctx, double* E_out, int32_t*
     if (e == cudaSuccess) e = launch_finish(ctx, E_out, t_star, s);
     if (e == cudaSuccess && W_out) e = launch_copy_w(ctx, W_out, s);
     return cuda_status(e);
+}
+
+pichol_status pichol_holdout_grad(pichol_ctx* ctx, double log_lam, double* E_out, double* dE_out, void* stream)
+{
+    if (!ctx || !E_out || !dE_out || !(log_lam == log_lam) || log_lam > 700.0 || log_lam < -700.0)
+        return PICHOL_ERR_INVALID_ARG;
+    if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
+    if (!ctx->have_fit) return PICHOL_ERR_STATE;
+    return cuda_status(launch_grad(ctx, log_lam, E_out, dE_out, (cudaStream_t)stream));
 }
 
 pichol_status pichol_get_lambdas(pichol_ctx* ctx, double* lam_out, void* stream)

@@ -125,6 +125,14 @@ struct pichol_ctx {
     float* Wth;          // k x (q c) x dp: W^T split
     float* Wtl;
     float* U2;           // k x dp x ldu: G_f W for every lambda
+    // gradient in log(lambda) at one lambda (pichol_holdout_grad)
+    void* gW;            // 3 x k x dp x c: W, U, V
+    void* gDinv;         // k x nt x TB^2
+    double* gP;          // 4 x k x dp x c: L~^T W, L~^T U, L~'^T W, L~'^T U
+    double* gphi;        // phi (MAX_P), phi' (MAX_P), lambda
+    int* gflags;         // k x nt
+    float* gdmax;
+    float* gdmin;
     double* Epart;       // k x q x nt
     double* E;           // k x q
     int* flags;          // k x q x nt (per-tile diagonal checks: bit0 nonpositive)
@@ -181,6 +189,7 @@ size_t solve_smem_bytes(int eb, int p, int64_t c);
 size_t xty_part_bytes(int k, int64_t dp, int64_t c);
 int64_t tc_kpad(const pichol_ctx* ctx);
 cudaError_t launch_gram_tc(pichol_ctx* ctx, const float* X, cudaStream_t s);
+cudaError_t launch_grad(pichol_ctx* ctx, double log_lam, double* E_out, double* dE_out, cudaStream_t s);
 cudaError_t launch_score_tc(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s);
 
 }  // namespace pichol

@@ -1145,6 +1145,66 @@ static cudaError_t eval_impl(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s
     return score_dispatch<T>(ctx, sc, s);
 }
 
+// One interpolated system per fold at the lambda whose basis values are
+// phi_row[0..p): optional diagonal inverses (into dinv_out, with the gradient's
+// own diagonal checks), then the solve of (L~ L~^T) out = rhs.
+template <typename T>
+static cudaError_t diag_solve_one_impl(pichol_ctx* ctx, const double* phi_row, const void* rhs, int rhs_per_system,
+                                       void* out, void* dinv_out, cudaStream_t s)
+{
+    const pichol_config& cf = ctx->cfg;
+    if (dinv_out) {
+        DiagArgs da;
+        da.src = ctx->Theta;
+        da.dinv = dinv_out;
+        da.phi = phi_row;
+        da.flags = ctx->gflags;
+        da.dmax = ctx->gdmax;
+        da.dmin = ctx->gdmin;
+        da.p = ctx->p;
+        da.nt = ctx->nt;
+        da.q = 1;
+        da.t0 = 0;
+        da.per = 1;
+        da.ntiles = ctx->ntiles;
+        da.d = cf.d;
+        const int dsm = 2 * (int)sizeof(T) * TB * (TB + 1);
+        cudaError_t ea = cudaFuncSetAttribute(k_diag_inv<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm);
+        if (ea != cudaSuccess) return ea;
+        {
+            StageScope sc_(ctx, ST_DIAG_INV, s);
+            k_diag_inv<T, false><<<dim3(ctx->nt, 1, cf.k), 128, dsm, s>>>(da);
+        }
+        ctx->launches++;
+    }
+    SolveArgs sa;
+    sa.src = ctx->Theta;
+    sa.dinv = ctx->gDinv;
+    sa.rhs = rhs;
+    sa.zbuf = out;
+    sa.out = out;
+    sa.phi = phi_row;
+    sa.p = ctx->p;
+    sa.nt = ctx->nt;
+    sa.q = 1;
+    sa.t0 = 0;
+    sa.tcount = 1;
+    sa.per = 1;
+    sa.rhs_per_system = rhs_per_system;
+    sa.ntiles = ctx->ntiles;
+    sa.dp = ctx->dp;
+    sa.c = cf.c;
+    return solve_dispatch<T, false>(ctx, sa, s);
+}
+
+cudaError_t launch_diag_solve_one(pichol_ctx* ctx, const double* phi_row, const void* rhs, int rhs_per_system,
+                                  void* out, void* dinv, cudaStream_t s)
+{
+    if (ctx->cfg.mode == PICHOL_MODE_FP64)
+        return diag_solve_one_impl<double>(ctx, phi_row, rhs, rhs_per_system, out, dinv, s);
+    return diag_solve_one_impl<float>(ctx, phi_row, rhs, rhs_per_system, out, dinv, s);
+}
+
 cudaError_t launch_eval(pichol_ctx* ctx, int exact, int t0, int tcount, cudaStream_t s)
 {
     if (ctx->cfg.mode == PICHOL_MODE_FP64)

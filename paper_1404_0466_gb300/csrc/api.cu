@@ -50,6 +50,8 @@ size_t plan(pichol_ctx* ctx, char* base)
         const int64_t qc = q * cc;
         ctx->Xh = (float*)take((size_t)(dp * ctx->kpad * 4));
         ctx->Xl = (float*)take((size_t)(dp * ctx->kpad * 4));
+        ctx->Yh = (float*)take((size_t)(cc * ctx->kpad * 4));
+        ctx->Yl = (float*)take((size_t)(cc * ctx->kpad * 4));
         ctx->Gh = (float*)take((size_t)(k * dp * dp * 4));
         ctx->Gl = (float*)take((size_t)(k * dp * dp * 4));
         ctx->Wth = (float*)take((size_t)(k * qc * dp * 4));

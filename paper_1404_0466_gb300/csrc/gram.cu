@@ -186,6 +186,21 @@ k_yy(const T* __restrict__ Y, int64_t c, FoldOffs fo, double* __restrict__ yy, i
     if (threadIdx.x == 0) yy[j] = red[0];
 }
 
+// B_f = sum_{j != f} Bv_j (summed in double in increasing j) when Bv is already formed.
+template <typename T>
+__global__ void k_btrain_from_bv(const T* __restrict__ Bv, int k, int64_t len, T* __restrict__ Btr)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        for (int f = 0; f < k; ++f) {
+            double all = 0.0;
+            for (int j = 0; j < k; ++j)
+                if (j != f) all += (double)Bv[(int64_t)j * len + e];
+            Btr[(int64_t)f * len + e] = (T)all;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Set-up in double precision (one CTA):
 //   tau = tr(sum_j G_j) / d (if scale_by_trace, else 1)
@@ -329,14 +344,15 @@ static cudaError_t gram_impl(pichol_ctx* ctx, const T* X, const T* Y, cudaStream
     cudaError_t e = cudaMemsetAsync(G, 0, sizeof(T) * (size_t)c.k * ctx->dp * ctx->dp, s);
     if (e != cudaSuccess) return e;
     if constexpr (std::is_same<T, float>::value) {
-        // mixed mode: tensor cores (split TF32 when gram_passes = 3)
+        // mixed mode: G_j and Bv_j = X_j^T Y_j on tensor cores (split TF32 when gram_passes = 3)
+        ctx->Yin = Y;
         e = launch_gram_tc(ctx, X, s);
         if (e != cudaSuccess) return e;
     } else {
-        StageScope sc_(ctx, ST_GRAM, s);
-        k_gram_simt<T><<<dim3((unsigned)ctx->ntiles, c.k), 256, 0, s>>>(X, c.d, ctx->dp, fo, G);
-    }
-    {
+        {
+            StageScope sc_(ctx, ST_GRAM, s);
+            k_gram_simt<T><<<dim3((unsigned)ctx->ntiles, c.k), 256, 0, s>>>(X, c.d, ctx->dp, fo, G);
+        }
         StageScope sc_(ctx, ST_XTY, s);
         k_xty<T><<<dim3(ctx->nt, c.k, XTY_SPLITS), 256, 0, s>>>(X, Y, c.d, ctx->dp, c.c, fo, ctx->xpart);
     }
@@ -351,7 +367,10 @@ static cudaError_t gram_impl(pichol_ctx* ctx, const T* X, const T* Y, cudaStream
                                   ctx->lam_s, ctx->pinv, ctx->phi, ctx->dphi, ctx->status);
     }
     const int64_t len = ctx->dp * c.c;
-    {
+    if constexpr (std::is_same<T, float>::value) {
+        StageScope sc_(ctx, ST_XTY, s);
+        k_btrain_from_bv<T><<<(unsigned)((len + 255) / 256), 256, 0, s>>>((const T*)ctx->Bv, c.k, len, (T*)ctx->Btr);
+    } else {
         StageScope sc_(ctx, ST_XTY, s);
         k_bsum<T><<<(unsigned)((len + 255) / 256), 256, 0, s>>>(ctx->xpart, c.k, len, (T*)ctx->Bv, (T*)ctx->Btr);
     }

@@ -120,6 +120,9 @@ struct pichol_ctx {
     int64_t ldu;         // leading dimension of U2 (q c rounded up to 4)
     float* Xh;           // dp x kpad: X^T split, TF32 part
     float* Xl;           // dp x kpad: remainder
+    float* Yh;           // c x kpad: Y^T split (fold-padded like X^T)
+    float* Yl;
+    const float* Yin;    // the caller's Y during pichol_hessian
     float* Gh;           // k x dp x dp: G_j split
     float* Gl;
     float* Wth;          // k x (q c) x dp: W^T split

@@ -147,7 +147,7 @@ __device__ __forceinline__ float tf32_round(float x)
 
 }  // namespace tc
 
-enum GemmMode { GEMM_GRAM = 0, GEMM_PLAIN = 1 };
+enum GemmMode { GEMM_GRAM = 0, GEMM_PLAIN = 1, GEMM_XTY = 2 };
 
 struct GemmArgs {
     int mode;
@@ -194,6 +194,14 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
         kx0 = a.k0[f];
         arow = tI * BM;
         brow = tJ * BN;
+    } else if (a.mode == GEMM_XTY) {
+        // X_f^T Y_f: A = X^T (feature tile blockIdx.x), B = Y^T (outputs), K = fold f's rows
+        tI = blockIdx.x;
+        tJ = 0;
+        nk = (a.kn[f] + BK - 1) / BK;
+        kx0 = a.k0[f];
+        arow = tI * BM;
+        brow = 0;
     } else {
         tI = blockIdx.x % ((int)((a.M + BM - 1) / BM));
         tJ = blockIdx.x / ((int)((a.M + BM - 1) / BM));
@@ -368,6 +376,34 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
 // Operand preparation
 // ---------------------------------------------------------------------------
 
+// YT_hi / YT_lo [c][Kpad]: the same fold-padded transpose for the targets Y.
+__global__ void __launch_bounds__(256)
+k_split_yt(const float* __restrict__ Y, int64_t c, int64_t kpad, XtArgs xa, float* __restrict__ Yh,
+           float* __restrict__ Yl)
+{
+    __shared__ float t[32][33];
+    const int64_t kc0 = (int64_t)blockIdx.x * 32, o0 = (int64_t)blockIdx.y * 32;
+    int j = 0;
+    while (j + 1 < xa.k && xa.k0[j + 1] <= kc0) ++j;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int yy = ty; yy < 32; yy += 8) {
+        const int64_t kc = kc0 + yy;
+        const int64_t row = xa.o[j] + (kc - xa.k0[j]);
+        const int64_t o = o0 + tx;
+        t[yy][tx] = (row < xa.o[j + 1] && o < c) ? Y[row * c + o] : 0.0f;
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+        const int64_t o = o0 + yy, kc = kc0 + tx;
+        if (o < c && kc < kpad) {
+            const float v = t[tx][yy];
+            const float hi = tc::tf32_round(v);
+            Yh[o * kpad + kc] = hi;
+            Yl[o * kpad + kc] = v - hi;
+        }
+    }
+}
+
 // XT_hi / XT_lo [dp][Kpad]: column kc of fold j (k0[j] <= kc < k0[j+1]) holds
 // sample row o[j] + (kc - k0[j]) if that row is in fold j, else 0; rows >= d are 0.
 struct XtArgs {
@@ -541,6 +577,35 @@ cudaError_t launch_gram_tc(pichol_ctx* ctx, const float* X, cudaStream_t s)
     {
         StageScope sc_(ctx, ST_GRAM, s);
         k_tc_gemm<<<dim3(tiles, c.k), tc::THREADS, tc::SMEM_BYTES, s>>>(mh, ml, mh, ml, ga);
+    }
+    ctx->launches++;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+
+    // Bv_j = X_j^T Y_j on the same operands: B = Y^T (c rows, zero-filled to 128)
+    {
+        StageScope sc_(ctx, ST_XTY, s);
+        k_split_yt<<<dim3((unsigned)(kpad / 32), (unsigned)((c.c + 31) / 32)), 256, 0, s>>>(ctx->Yin, c.c, kpad, xa,
+                                                                                          ctx->Yh, ctx->Yl);
+    }
+    ctx->launches++;
+    CUtensorMap yh, yl;
+    if (!make_map(&yh, ctx->Yh, (uint64_t)kpad, (uint64_t)c.c, (uint64_t)kpad) ||
+        !make_map(&yl, ctx->Yl, (uint64_t)kpad, (uint64_t)c.c, (uint64_t)kpad))
+        return cudaErrorInvalidValue;
+    GemmArgs gy = ga;
+    gy.mode = GEMM_XTY;
+    gy.C = (float*)ctx->Bv;
+    gy.Chi = nullptr;
+    gy.Clo = nullptr;
+    gy.ldc = c.c;
+    gy.M = dp;
+    gy.N = c.c;
+    gy.c_col_off = 0;
+    gy.c_fold_stride = dp * c.c;
+    {
+        StageScope sc_(ctx, ST_XTY, s);
+        k_tc_gemm<<<dim3((unsigned)ga.ntb, c.k), tc::THREADS, tc::SMEM_BYTES, s>>>(mh, ml, yh, yl, gy);
     }
     ctx->launches++;
     return cudaGetLastError();

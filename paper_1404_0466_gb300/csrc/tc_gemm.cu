@@ -376,34 +376,6 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
 // Operand preparation
 // ---------------------------------------------------------------------------
 
-// YT_hi / YT_lo [c][Kpad]: the same fold-padded transpose for the targets Y.
-__global__ void __launch_bounds__(256)
-k_split_yt(const float* __restrict__ Y, int64_t c, int64_t kpad, XtArgs xa, float* __restrict__ Yh,
-           float* __restrict__ Yl)
-{
-    __shared__ float t[32][33];
-    const int64_t kc0 = (int64_t)blockIdx.x * 32, o0 = (int64_t)blockIdx.y * 32;
-    int j = 0;
-    while (j + 1 < xa.k && xa.k0[j + 1] <= kc0) ++j;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    for (int yy = ty; yy < 32; yy += 8) {
-        const int64_t kc = kc0 + yy;
-        const int64_t row = xa.o[j] + (kc - xa.k0[j]);
-        const int64_t o = o0 + tx;
-        t[yy][tx] = (row < xa.o[j + 1] && o < c) ? Y[row * c + o] : 0.0f;
-    }
-    __syncthreads();
-    for (int yy = ty; yy < 32; yy += 8) {
-        const int64_t o = o0 + yy, kc = kc0 + tx;
-        if (o < c && kc < kpad) {
-            const float v = t[tx][yy];
-            const float hi = tc::tf32_round(v);
-            Yh[o * kpad + kc] = hi;
-            Yl[o * kpad + kc] = v - hi;
-        }
-    }
-}
-
 // XT_hi / XT_lo [dp][Kpad]: column kc of fold j (k0[j] <= kc < k0[j+1]) holds
 // sample row o[j] + (kc - k0[j]) if that row is in fold j, else 0; rows >= d are 0.
 struct XtArgs {
@@ -437,6 +409,34 @@ k_split_xt(const float* __restrict__ X, int64_t d, int64_t dp, int64_t kpad, XtA
             const float hi = tc::tf32_round(v);
             Xh[feat * kpad + kc] = hi;
             Xl[feat * kpad + kc] = v - hi;
+        }
+    }
+}
+
+// YT_hi / YT_lo [c][Kpad]: the same fold-padded transpose for the targets Y.
+__global__ void __launch_bounds__(256)
+k_split_yt(const float* __restrict__ Y, int64_t c, int64_t kpad, XtArgs xa, float* __restrict__ Yh,
+           float* __restrict__ Yl)
+{
+    __shared__ float t[32][33];
+    const int64_t kc0 = (int64_t)blockIdx.x * 32, o0 = (int64_t)blockIdx.y * 32;
+    int j = 0;
+    while (j + 1 < xa.k && xa.k0[j + 1] <= kc0) ++j;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int yy = ty; yy < 32; yy += 8) {
+        const int64_t kc = kc0 + yy;
+        const int64_t row = xa.o[j] + (kc - xa.k0[j]);
+        const int64_t o = o0 + tx;
+        t[yy][tx] = (row < xa.o[j + 1] && o < c) ? Y[row * c + o] : 0.0f;
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+        const int64_t o = o0 + yy, kc = kc0 + tx;
+        if (o < c && kc < kpad) {
+            const float v = t[tx][yy];
+            const float hi = tc::tf32_round(v);
+            Yh[o * kpad + kc] = hi;
+            Yl[o * kpad + kc] = v - hi;
         }
     }
 }

@@ -138,50 +138,69 @@ class ClockSampler:
 # algorithmic work per stage (for the roofline of the dominant kernel)
 # ---------------------------------------------------------------------------
 def stage_work(cfg, mode, refine):
+    """Algorithmic work per step of each timed stage: (kind, amount, bound, note).
+    kind "flop": floating-point operations the method needs (not the ones the
+    kernel happens to execute); "op32": FP32 operations of the double-float
+    residual (10 per exact multiply-add, 3 per evaluated factor entry and
+    lambda); "byte": bytes that must cross HBM."""
     n, d, c, k, g, r, q = (cfg[x] for x in ("n", "d", "c", "k", "g", "r", "q"))
     p = r + 1
     D = d * (d + 1) // 2
     nt = -(-d // 64)
     eb = 8 if mode == "fp64" else 4
     upd = sum((m * (m + 1) // 2) for m in range(nt)) * 2 * 64 ** 3 * k * g
+    tensor = "tensor" if mode == "mixed" else "alu"
+    passes = 3 if mode == "mixed" else 1
     return {
-        # SYRK of every fold block: n d (d + 1) flops
-        "gram": ("flop", n * d * (d + 1)),
+        # SYRK of every fold block, n d (d + 1) flops; split TF32 runs 3 products
+        "gram": ("flop", n * d * (d + 1) * passes, tensor),
+        # X_j^T Y_j for every fold: 2 n d c flops (x3 split products)
+        "xty": ("flop", 2 * n * d * c * passes, tensor),
         # trailing updates of k g blocked factorisations (lower tiles, 2 b^3 per tile update)
-        "chol_update": ("flop", upd),
+        "chol_update": ("flop", upd, "alu"),
         # read g factors, write p coefficient sets, per fold (lower triangles)
-        "fit": ("byte", k * (g + p) * D * eb),
-        # per fold and lambda: two triangular solves (2 d^2 c) + the factor built twice (4 p D)
-        "solve": ("flop", k * q * (2 * d * d * c + 4 * p * D) * (1 + refine)),
-        # per fold and lambda: <W, G W>: 2 d^2 c
-        "score": ("flop", k * q * 2 * d * d * c),
+        "fit": ("byte", k * (g + p) * D * eb, "hbm"),
+        # per fold and lambda: two triangular solves (2 d^2 c) + the factor built twice (2 (p-1) 2 D)
+        "solve": ("flop", k * q * (2 * d * d * c + 4 * (p - 1) * D) * (1 + refine), "alu"),
+        # two triangular products per refinement step, double-float: 10 fp32 ops per multiply-add
+        "resid": ("op32", k * q * refine * (d * d * c * 10 + 2 * 3 * D * 2), "alu"),
+        # per fold and lambda: <W, G W> as G_f W for all lambdas: 2 d^2 c q flops (x3 split)
+        "score": ("flop", k * q * 2 * d * d * c * passes, tensor),
     }
 
 
-def roofline(stage_ms, cfg, mode, refine, steps, peaks):
+def _peak(bound, mode, peaks):
+    if bound == "hbm":
+        return peaks.get("hbm_gbs"), "GB/s", "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    if bound == "tensor":
+        # TF32 dense is half the bf16 rate on this part (nominal 1.1 vs 2.25 PFLOP/s)
+        return peaks.get("bf16_tflops", 1919.0) * 0.5, "TFLOP/s", \
+            "TF32 = 0.5 x measured bf16 burst (MEASURED_PEAKS.json), nominal ratio"
+    if mode == "fp64":
+        return 1.25, "TFLOP/s", "nominal GB300 FP64 (1.25 TFLOP/s); no measured figure"
+    return FP32_PEAK_TFLOPS, "TFLOP/s", "FP32 ALU: 152 SMs x 128 lanes x 2 flops x 2070 MHz (derived)"
+
+
+def roofline_of(name, ms, launches, cfg, mode, refine, steps, peaks):
     work = stage_work(cfg, mode, refine)
-    dom = max(stage_ms.items(), key=lambda kv: kv[1][0])
-    name, (ms, launches) = dom
     info = {"kernel_stage": name, "stage_ms_per_step": ms / steps, "launches_per_step": launches / steps}
     if name not in work or ms <= 0:
         info.update({"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None})
         return info
-    kind, amount = work[name]
+    kind, amount, bound = work[name]
     per_launch = amount / max(1, launches / steps)
     avg_s = ms / 1e3 / max(1, launches)
-    if kind == "flop":
-        achieved = per_launch / avg_s / 1e12
-        peak = FP32_PEAK_TFLOPS if mode == "mixed" else None
-        info.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x 2070 MHz (derived)"})
-    else:
-        achieved = per_launch / avg_s / 1e9
-        peak = peaks.get("hbm_gbs")
-        info.update({"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)"})
-    info["frac"] = (achieved / peak) if peak else None
-    info["traffic"] = None
+    peak, unit, note = _peak(bound, mode, peaks)
+    achieved = per_launch / avg_s / (1e9 if kind == "byte" else 1e12)
+    info.update({"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "peak_note": note,
+                 "work": kind, "work_per_launch": per_launch,
+                 "frac": (achieved / peak) if peak else None, "traffic": None})
     return info
+
+
+def roofline(stage_ms, cfg, mode, refine, steps, peaks):
+    name, (ms, launches) = max(stage_ms.items(), key=lambda kv: kv[1][0])
+    return roofline_of(name, ms, launches, cfg, mode, refine, steps, peaks)
 
 
 def load_peaks():
@@ -413,6 +432,11 @@ def run_own(args):
         "e2e": e2e,
         "gpu_launches": launches,
         "roofline": roofline(stage_ms, cfg, w["mode"], refine, args.steps, peaks),
+        "kernels_roofline": {nm: {kk: v for kk, v in roofline_of(nm, ms_, la, cfg, w["mode"], refine, args.steps,
+                                                                peaks).items()
+                                  if kk in ("bound", "achieved", "peak", "unit", "frac", "stage_ms_per_step")}
+                             for nm, (ms_, la) in stage_ms.items()
+                             if nm in stage_work(cfg, w["mode"], refine)},
         "stages_ms_per_step": {s: round(v[0] / args.steps, 4) for s, v in stage_ms.items()},
         "stage_timing_complete": complete,
         "clocks": clocks,

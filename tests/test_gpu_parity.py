@@ -249,5 +249,7 @@ def test_mixed_hessian_on_tensor_cores(torch_mod, n, d, passes):
         Hr, Br = oracle.normal_blocks(prob.X, prob.Y, offs[f], offs[f + 1])
         err = np.max(np.abs(H.cpu().numpy() - Hr)) / np.max(np.abs(Hr))
         assert err <= tol, (f, err)
-        assert np.max(np.abs(B.cpu().numpy() - Br)) <= 1e-5 * np.max(np.abs(Br))
+        # X_f^T Y_f runs on the same tensor-core path with the same tolerance
+        errb = np.max(np.abs(B.cpu().numpy() - Br)) / np.max(np.abs(Br))
+        assert errb <= tol, (f, errb)
     assert ctx.info().code == 0

@@ -265,6 +265,37 @@ PICHOL_API void pichol_destroy(pichol_ctx* ctx);
 PICHOL_API pichol_status pichol_fold_rhs_noalloc(int32_t mode, const void* X, const void* Y, int64_t n, int64_t d,
                                                  int64_t c, int32_t k, void* Bv_out, void* B_out, void* stream);
 
+/*
+ * Batches of independent problems of uneven size (the data-parallel structure
+ * of Sec. 1: folds, lambdas and separate problems are independent units).
+ * pichol_batch_create makes one context per entry of cfgs[0..nprob) (host
+ * memory only); all of them live in one caller-owned workspace of
+ * pichol_batch_workspace_size bytes.  pichol_batch_run enqueues, for every
+ * problem i, pichol_hessian(X[i], Y[i]), pichol_factor_samples, pichol_fit and
+ * pichol_eval_holdout(E_out[i], t_star + i): X, Y, E_out are HOST arrays of
+ * DEVICE pointers (problem i's X is n_i x d_i, Y n_i x c_i, E_out[i] k_i * q_i
+ * doubles), t_star a device array of nprob int32.  The work forks from
+ * `stream` onto `nstreams` internal streams (created on the first run on the
+ * current device, most expensive problems first, round robin) and joins back,
+ * so everything is ordered after earlier work on `stream` and later work on
+ * `stream` waits for it; the whole call can be captured into a CUDA graph
+ * (after one uncaptured run, which creates the streams and kernel attributes).
+ * Errors of any problem's call are returned; device errors per problem with
+ * pichol_batch_get_info.
+ */
+typedef struct pichol_batch pichol_batch;
+PICHOL_API pichol_status pichol_batch_create(const pichol_config* cfgs, int32_t nprob, int32_t nstreams,
+                                             pichol_batch** out);
+PICHOL_API pichol_status pichol_batch_workspace_size(const pichol_batch* b, size_t* bytes);
+PICHOL_API pichol_status pichol_batch_set_workspace(pichol_batch* b, void* workspace, size_t bytes);
+/* Changes the number of internal streams (1..64) used by later runs. */
+PICHOL_API pichol_status pichol_batch_set_streams(pichol_batch* b, int32_t nstreams);
+PICHOL_API pichol_status pichol_batch_run(pichol_batch* b, const void* const* X, const void* const* Y,
+                                          double* const* E_out, int32_t* t_star, void* stream);
+PICHOL_API pichol_status pichol_batch_get_info(pichol_batch* b, int32_t i, pichol_info* info, void* stream);
+PICHOL_API int64_t pichol_batch_launch_count(const pichol_batch* b);
+PICHOL_API void pichol_batch_destroy(pichol_batch* b);
+
 /* Short text for a status code (static storage). */
 PICHOL_API const char* pichol_status_string(pichol_status s);
 

@@ -29,6 +29,8 @@ EXPORTS = [
     "pichol_export_hessian", "pichol_get_info", "pichol_clear_status", "pichol_launch_count",
     "pichol_destroy", "pichol_status_string", "pichol_set_timing", "pichol_stage_times",
     "pichol_fold_rhs_noalloc", "pichol_holdout_grad",
+    "pichol_batch_create", "pichol_batch_workspace_size", "pichol_batch_set_workspace", "pichol_batch_set_streams",
+    "pichol_batch_run", "pichol_batch_get_info", "pichol_batch_launch_count", "pichol_batch_destroy",
 ]
 STAGES = ["gram", "xty", "setup", "chol_init", "chol_diag", "chol_panel", "chol_update", "fit",
           "diag_inv", "solve", "resid", "score", "select", "misc"]
@@ -88,6 +90,14 @@ def lib():
         "pichol_set_timing": ([vp, i32], ctypes.c_int),
         "pichol_fold_rhs_noalloc": ([i32, vp, vp, i64, i64, i64, i32, vp, vp, vp], ctypes.c_int),
         "pichol_holdout_grad": ([vp, ctypes.c_double, vp, vp, vp], ctypes.c_int),
+        "pichol_batch_create": ([ctypes.POINTER(Config), i32, i32, ctypes.POINTER(vp)], ctypes.c_int),
+        "pichol_batch_workspace_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+        "pichol_batch_set_workspace": ([vp, vp, ctypes.c_size_t], ctypes.c_int),
+        "pichol_batch_set_streams": ([vp, i32], ctypes.c_int),
+        "pichol_batch_run": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp], ctypes.c_int),
+        "pichol_batch_get_info": ([vp, i32, ctypes.POINTER(Info), vp], ctypes.c_int),
+        "pichol_batch_launch_count": ([vp], i64),
+        "pichol_batch_destroy": ([vp], None),
         "pichol_stage_times": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32, vp],
                                ctypes.c_int),
     }
@@ -295,3 +305,74 @@ def holdout_loss(ctx: "Context", log_lam):
             return g * dEbar
 
     return _HoldoutLoss.apply(log_lam)
+
+
+class Batch:
+    """Independent problems of uneven size run by one call (pichol_batch_run),
+    capturable into a CUDA graph.  ``problems`` is a list of dicts with the
+    Context keyword arguments (n, d, c, k, g, r, q, ...)."""
+
+    def __init__(self, problems, nstreams=8):
+        import torch
+        L = lib()
+        n = len(problems)
+        cfgs = (Config * n)()
+        self.mode = problems[0].get("mode", "fp64")
+        for i, pr in enumerate(problems):
+            L.pichol_config_default(ctypes.byref(cfgs[i]))
+            cfg = cfgs[i]
+            cfg.n, cfg.d, cfg.c, cfg.k, cfg.g, cfg.r, cfg.q = (pr[x] for x in ("n", "d", "c", "k", "g", "r", "q"))
+            cfg.lam_lo, cfg.lam_hi = pr.get("lam_lo", 1e-3), pr.get("lam_hi", 1e1)
+            cfg.basis = {"mono": PICHOL_BASIS_MONO, "cheb_log": PICHOL_BASIS_CHEB_LOG}[pr.get("basis", "mono")]
+            cfg.mode = {"fp64": PICHOL_MODE_FP64, "mixed": PICHOL_MODE_MIXED}[pr.get("mode", "fp64")]
+            cfg.refine_steps = pr.get("refine_steps", 0)
+            cfg.exact_batch = pr.get("exact_batch", cfg.g)
+        self.cfgs = cfgs
+        self.n = n
+        h = ctypes.c_void_p()
+        _check(L.pichol_batch_create(cfgs, n, nstreams, ctypes.byref(h)), "pichol_batch_create")
+        self._h = h
+        nbytes = ctypes.c_size_t()
+        _check(L.pichol_batch_workspace_size(h, ctypes.byref(nbytes)), "pichol_batch_workspace_size")
+        self.workspace_bytes = nbytes.value
+        self._ws = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device="cuda")
+        _check(L.pichol_batch_set_workspace(h, ctypes.c_void_p(self._ws.data_ptr()), self._ws.numel()),
+               "pichol_batch_set_workspace")
+        dt = torch.float64 if self.mode == "fp64" else torch.float32
+        self.dtype = dt
+        self.E = [torch.empty((c.k, c.q), dtype=torch.float64, device="cuda") for c in cfgs]
+        self.t_star = torch.empty((n,), dtype=torch.int32, device="cuda")
+
+    def set_streams(self, nstreams):
+        _check(lib().pichol_batch_set_streams(self._h, nstreams), "pichol_batch_set_streams")
+
+    def run(self, Xs, Ys, stream=None):
+        P = ctypes.c_void_p * self.n
+        self._keep = (Xs, Ys)
+        xp = P(*[x.data_ptr() for x in Xs])
+        yp = P(*[y.data_ptr() for y in Ys])
+        ep = P(*[e.data_ptr() for e in self.E])
+        self._ptrs = (xp, yp, ep)
+        _check(lib().pichol_batch_run(self._h, xp, yp, ep, ctypes.c_void_p(self.t_star.data_ptr()),
+                                      ctypes.c_void_p(_stream_ptr(stream))), "pichol_batch_run")
+        return self.E, self.t_star
+
+    def info(self, i, stream=None) -> Info:
+        inf = Info()
+        _check(lib().pichol_batch_get_info(self._h, i, ctypes.byref(inf), ctypes.c_void_p(_stream_ptr(stream))),
+               "pichol_batch_get_info")
+        return inf
+
+    def launch_count(self) -> int:
+        return int(lib().pichol_batch_launch_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pichol_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -143,9 +143,8 @@ class ClockSampler:
 def stage_work(cfg, mode, refine):
     """Algorithmic work per step of each timed stage: (kind, amount, bound, note).
     kind "flop": floating-point operations the method needs (not the ones the
-    kernel happens to execute); "op32": FP32 operations of the double-float
-    residual (10 per exact multiply-add, 3 per evaluated factor entry and
-    lambda); "byte": bytes that must cross HBM."""
+    kernel happens to execute; an FMA counts 2); "byte": bytes that must cross
+    HBM."""
     n, d, c, k, g, r, q = (cfg[x] for x in ("n", "d", "c", "k", "g", "r", "q"))
     p = r + 1
     D = d * (d + 1) // 2
@@ -165,8 +164,10 @@ def stage_work(cfg, mode, refine):
         "fit": ("byte", k * (g + p) * D * eb, "hbm"),
         # per fold and lambda: two triangular solves (2 d^2 c) + the factor built twice (2 (p-1) 2 D)
         "solve": ("flop", k * q * (2 * d * d * c + 4 * (p - 1) * D) * (1 + refine), "alu"),
-        # two triangular products per refinement step, double-float: 10 fp32 ops per multiply-add
-        "resid": ("op32", k * q * refine * (d * d * c * 10 + 2 * 3 * D * 2), "alu"),
+        # two triangular products per refinement step in double-float arithmetic (error-free
+        # product + TwoSum): 11 flops per multiply-add in L~^T W, 13 in L~ (u_hi + u_lo)
+        # (FMA = 2), plus the factor built twice (2 (p-1) 2 D)
+        "resid": ("flop", k * q * refine * (12 * d * d * c + 4 * (p - 1) * D), "alu"),
         # per fold and lambda: <W, G W> as G_f W for all lambdas: 2 d^2 c q flops (x3 split)
         "score": ("flop", k * q * 2 * d * d * c * passes, tensor),
     }
@@ -184,8 +185,8 @@ def _peak(bound, mode, peaks):
     return FP32_PEAK_TFLOPS, "TFLOP/s", "FP32 ALU: 152 SMs x 128 lanes x 2 flops x 2070 MHz (derived)"
 
 
-def roofline_of(name, ms, launches, cfg, mode, refine, steps, peaks):
-    work = stage_work(cfg, mode, refine)
+def roofline_of(name, ms, launches, cfg, mode, refine, steps, peaks, work=None):
+    work = work if work is not None else stage_work(cfg, mode, refine)
     info = {"kernel_stage": name, "stage_ms_per_step": ms / steps, "launches_per_step": launches / steps}
     if name not in work or ms <= 0:
         info.update({"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None})
@@ -385,20 +386,48 @@ def run_batched(args):
     if rank != 0:
         return 0
     h2d = sum(x.numel() * 4 for x in Xh) + sum(y.numel() * 4 for y in Yh)
-    # error against the FP64 oracle on the two smallest problems, all folds, five lambdas
+    # per-kernel durations: one eager run on a single stream with stage timing, so the
+    # kernels of different problems do not overlap; work summed over the problems
+    batch.set_streams(1)
+    batch.set_timing(1024)
+    batch.run(Xs, Ys)
+    torch.cuda.synchronize()
+    stage_ms, work = {}, {}
+    for i, sp in enumerate(specs):
+        st, _ = batch.stage_times(i)
+        for nm, (ms_, la) in st.items():
+            if la:
+                a, b = stage_ms.get(nm, (0.0, 0))
+                stage_ms[nm] = (a + ms_, b + la)
+        cfg_i = dict(sp, lo=B["lo"], hi=B["hi"])
+        for nm, (kind, amount, bound) in stage_work(cfg_i, w["mode"], refine).items():
+            work[nm] = (kind, work.get(nm, (kind, 0, bound))[1] + amount, bound)
+    batch.set_timing(0)
+    peaks = load_peaks()
+    top = max(stage_ms, key=lambda nm: stage_ms[nm][0])
+    roof = roofline_of(top, *stage_ms[top], None, w["mode"], refine, 1, peaks, work=work)
+    kern_roof = {nm: {kk: v for kk, v in roofline_of(nm, ms_, la, None, w["mode"], refine, 1, peaks, work=work).items()
+                      if kk in ("achieved", "frac", "bound", "stage_ms_per_step", "launches_per_step")}
+                 for nm, (ms_, la) in stage_ms.items() if nm in work}
+    # error against the FP64 oracle and the oracle's own speed, on four problems spread
+    # over the batch's size range (fold 0, five lambdas each, extrapolated to the fold)
     import oracle
-    small = sorted(range(len(probs)), key=lambda i: probs[i].X.shape[1])[:2]
+    by_size = sorted(range(len(probs)), key=lambda i: probs[i].X.shape[1])
+    pick = [by_size[(2 * j + 1) * len(probs) // 8] for j in range(4)]
     errs = []
+    fold_s = 0.0
     t0 = time.perf_counter()
-    tm = {}
-    for i in small:
-        idx = [0, B["q"] // 4, B["q"] // 2, 3 * B["q"] // 4, B["q"] - 1]
+    idx = [0, B["q"] // 4, B["q"] // 2, 3 * B["q"] // 4, B["q"] - 1]
+    for i in pick:
+        tm = {}
         ref = oracle.cv(probs[i].X, probs[i].Y, k=B["k"], g=B["g"], r=B["r"], q=B["q"], lo=B["lo"], hi=B["hi"],
                         basis=w["basis"], folds=[0], lam_idx=idx, timings=tm)
+        fold_s += tm["setup"] + tm["fold"] + B["q"] * tm["eval"] / max(1, tm["n_eval"])
         got = batch.E[i].cpu().numpy()
         errs.append(float(np.max(np.abs(got[0, idx] - ref.E[0, idx]) / np.abs(ref.E[0, idx]))))
     wall = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    dims = [probs[i].X.shape[1] for i in pick]
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -411,11 +440,15 @@ def run_batched(args):
                 "d2h_bytes_per_step": sum(e.numel() * 8 for e in Eh), "ms_per_step": ems / args.steps},
         "gpu_launches": per_run * args.steps,
         "clocks": clocks,
-        "err_vs_fp64": {"max_rel_E": max(errs), "sample": f"problems {small}, fold 0, five lambdas"},
-        "cpu_baseline": {"value": tm["n_eval"] / max(1e-9, wall), "unit": "evals/s", "cores": cores,
-                         "kind": "oracle", "sample": f"problems {small}, fold 0, five lambdas each "
-                                                     f"(Hessian, factors and fit included), {wall:.1f} s"},
-        "roofline": None,
+        "err_vs_fp64": {"max_rel_E": max(errs), "sample": f"problems {pick} (d = {dims}), fold 0, grid indices {idx}"},
+        "cpu_baseline": {"value": len(pick) * B["q"] / fold_s, "unit": "evals/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": (f"fold 0 of problems {pick} (d = {dims}, spread over the batch's sizes): "
+                                    f"Hessian, factors and fit, and {len(idx)} of {B['q']} lambdas, extrapolated "
+                                    f"to the fold's {B['q']} lambdas; {wall:.1f} s of CPU work")},
+        "roofline": dict(roof, traffic=None,
+                         timing="per-launch durations from one eager run of the batch on one stream"),
+        "kernels_roofline": kern_roof,
     }
     print(json.dumps(line), flush=True)
     batch.close()

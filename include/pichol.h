@@ -294,6 +294,15 @@ PICHOL_API pichol_status pichol_batch_run(pichol_batch* b, const void* const* X,
                                           double* const* E_out, int32_t* t_star, void* stream);
 PICHOL_API pichol_status pichol_batch_get_info(pichol_batch* b, int32_t i, pichol_info* info, void* stream);
 PICHOL_API int64_t pichol_batch_launch_count(const pichol_batch* b);
+/* Stage timing of every problem's context (pichol_set_timing on each, same
+ * meaning of max_launches), and problem i's per-stage sums
+ * (pichol_stage_times).  Each context records on the stream its problem runs
+ * on, so with more than one internal stream the recorded durations include
+ * time shared with other problems' kernels; time with one stream to get
+ * per-kernel durations. */
+PICHOL_API pichol_status pichol_batch_set_timing(pichol_batch* b, int32_t max_launches);
+PICHOL_API pichol_status pichol_batch_stage_times(pichol_batch* b, int32_t i, double* ms, int64_t* launches,
+                                                  int32_t n_stages, void* stream);
 PICHOL_API void pichol_batch_destroy(pichol_batch* b);
 
 /* Short text for a status code (static storage). */

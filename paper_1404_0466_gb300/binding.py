@@ -31,6 +31,7 @@ EXPORTS = [
     "pichol_fold_rhs_noalloc", "pichol_holdout_grad",
     "pichol_batch_create", "pichol_batch_workspace_size", "pichol_batch_set_workspace", "pichol_batch_set_streams",
     "pichol_batch_run", "pichol_batch_get_info", "pichol_batch_launch_count", "pichol_batch_destroy",
+    "pichol_batch_set_timing", "pichol_batch_stage_times",
 ]
 STAGES = ["gram", "xty", "setup", "chol_init", "chol_diag", "chol_panel", "chol_update", "fit",
           "diag_inv", "solve", "resid", "score", "select", "misc"]
@@ -98,6 +99,9 @@ def lib():
         "pichol_batch_get_info": ([vp, i32, ctypes.POINTER(Info), vp], ctypes.c_int),
         "pichol_batch_launch_count": ([vp], i64),
         "pichol_batch_destroy": ([vp], None),
+        "pichol_batch_set_timing": ([vp, i32], ctypes.c_int),
+        "pichol_batch_stage_times": ([vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32,
+                                      vp], ctypes.c_int),
         "pichol_stage_times": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32, vp],
                                ctypes.c_int),
     }
@@ -365,6 +369,19 @@ class Batch:
 
     def launch_count(self) -> int:
         return int(lib().pichol_batch_launch_count(self._h))
+
+    def set_timing(self, max_launches: int):
+        _check(lib().pichol_batch_set_timing(self._h, max_launches), "pichol_batch_set_timing")
+
+    def stage_times(self, i, stream=None):
+        """Problem i's {stage: (total ms, launches)} since the last call; needs set_timing."""
+        n = len(STAGES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        rc = lib().pichol_batch_stage_times(self._h, i, ms, cnt, n, ctypes.c_void_p(_stream_ptr(stream)))
+        if rc not in (0, 4):
+            _check(rc, "pichol_batch_stage_times")
+        return {STAGES[j]: (ms[j], int(cnt[j])) for j in range(n)}, rc == 0
 
     def close(self):
         if getattr(self, "_h", None):

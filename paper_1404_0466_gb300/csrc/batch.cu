@@ -168,6 +168,23 @@ pichol_status pichol_batch_get_info(pichol_batch* b, int32_t i, pichol_info* inf
     return pichol_get_info(b->ctx[i], info, stream);
 }
 
+pichol_status pichol_batch_set_timing(pichol_batch* b, int32_t max_launches)
+{
+    if (!b) return PICHOL_ERR_INVALID_ARG;
+    for (pichol_ctx* c : b->ctx) {
+        pichol_status st = pichol_set_timing(c, max_launches);
+        if (st != PICHOL_OK) return st;
+    }
+    return PICHOL_OK;
+}
+
+pichol_status pichol_batch_stage_times(pichol_batch* b, int32_t i, double* ms, int64_t* launches, int32_t n_stages,
+                                       void* stream)
+{
+    if (!b || i < 0 || i >= b->nprob) return PICHOL_ERR_INVALID_ARG;
+    return pichol_stage_times(b->ctx[i], ms, launches, n_stages, stream);
+}
+
 int64_t pichol_batch_launch_count(const pichol_batch* b)
 {
     if (!b) return 0;

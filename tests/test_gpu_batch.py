@@ -90,3 +90,21 @@ def test_batch_graph_replay_equals_eager_run(torch_mod):
         assert torch.equal(a, e)
     assert torch.equal(t_eager, b.t_star)
     b.close()
+
+
+def test_batch_stage_timing_per_problem(torch_mod):
+    torch = torch_mod
+    probs = synth.batched_uneven(3, seed=9, d_lo=64, d_hi=160)
+    b, Xs, Ys = _batch(torch, probs, "mixed")
+    b.set_streams(1)
+    b.set_timing(256)
+    b.run(Xs, Ys)
+    torch.cuda.synchronize()
+    for i in range(len(probs)):
+        st, complete = b.stage_times(i)
+        assert complete
+        for stage in ("gram", "chol_diag", "fit", "solve", "score"):
+            ms, launches = st[stage]
+            assert launches > 0 and ms > 0.0, (i, stage)
+    b.set_timing(0)
+    b.close()

@@ -123,7 +123,10 @@ PICHOL_API pichol_status pichol_workspace_size(const pichol_ctx* ctx, size_t* by
 
 /* Attaches the caller's workspace (device pointer, >= pichol_workspace_size
  * bytes, 256-byte aligned).  Contents need not be initialised: the call zeroes
- * the status word with a blocking cudaMemset on the current device. */
+ * the status word with a blocking cudaMemset on the current device.  The first
+ * call also creates, on the current device, the context's one internal stream
+ * (at the highest stream priority) and four events (factorisation look-ahead,
+ * see pichol_factor_samples); pichol_destroy frees them. */
 PICHOL_API pichol_status pichol_set_workspace(pichol_ctx* ctx, void* workspace, size_t bytes);
 
 /*
@@ -144,6 +147,9 @@ PICHOL_API pichol_status pichol_hessian(pichol_ctx* ctx, const void* X, const vo
  * idx_s = round(s (q-1)/(g-1)) (Sec. 6.3: samples taken from the grid), with
  * H_f = sum_{j != f} G_j.  Blocked right-looking factorisation, all k*g
  * problems per launch.  A non-positive pivot latches PICHOL_ERR_NOT_SPD.
+ * Part of each trailing update runs on the context's internal stream, forked
+ * from `stream` by an event and joined back before the call's last enqueued
+ * work, so the call orders like a single-stream call and can be captured.
  */
 PICHOL_API pichol_status pichol_factor_samples(pichol_ctx* ctx, void* stream);
 

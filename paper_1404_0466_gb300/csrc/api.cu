@@ -151,6 +151,14 @@ pichol_status pichol_set_workspace(pichol_ctx* ctx, void* workspace, size_t byte
     ctx->ws_bytes = bytes;
     plan(ctx, ctx->ws);
     ctx->have_hessian = ctx->have_factors = ctx->have_fit = false;
+    if (!ctx->aux) {
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, greatest) != cudaSuccess)
+            return PICHOL_ERR_CUDA;
+        for (cudaEvent_t* e : {&ctx->ev_fork, &ctx->ev_panel, &ctx->ev_upd, &ctx->ev_join})
+            if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return PICHOL_ERR_CUDA;
+    }
     // the status word must read "no error" before any kernel runs
     return cuda_status(cudaMemset(ctx->status, 0, sizeof(DevStatus)));
 }
@@ -353,6 +361,9 @@ void pichol_destroy(pichol_ctx* ctx)
 {
     if (!ctx) return;
     free_timing(ctx);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_panel, ctx->ev_upd, ctx->ev_join})
+        if (e) cudaEventDestroy(e);
     delete ctx;
 }
 

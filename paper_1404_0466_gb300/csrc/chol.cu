@@ -10,6 +10,8 @@
 // continues with a unit pivot so no NaN spreads.
 #include "internal.cuh"
 
+#include <cstring>
+
 namespace pichol {
 
 struct ProbMap {
@@ -52,46 +54,74 @@ k_chol_init(const T* __restrict__ Hf, int64_t d, int64_t ntiles, ProbMap pm,
     }
 }
 
+// 1/sqrt(p) by Newton-Raphson, y <- y + (y/2)(1 - p y^2), each step roughly
+// doubling the correct bits, seeded with the single-precision rsqrtf (about 22
+// bits): two steps reach double precision.  Outside the seed's range the
+// quotient of the library square root is used.
+__device__ __forceinline__ double rsqrt_newton(double p)
+{
+    if (!(p > 1e-30 && p < 1e30)) return 1.0 / sqrt(p);
+    double y = (double)rsqrtf((float)p);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const double r = fma(-p * y, y, 1.0);
+        y = fma(0.5 * y, r, y);
+    }
+    return y;
+}
+
+// Pivot of column j of the diagonal tile: L_jj = sqrt(a_jj), 1 / L_jj kept in yinv[j].
+__device__ __forceinline__ void take_pivot(double (*A)[TB + 1], double* yinv, int j, int J, int64_t d,
+                                           const ProbMap& pm, int pr, DevStatus* st)
+{
+    double piv = A[j][j];
+    if (!(piv > 0.0)) {
+        if ((int64_t)J * TB + j < d)
+            latch_error(st, PICHOL_ERR_NOT_SPD, pr / pm.per, pm.exact ? pm.t0 + pr % pm.per : pr % pm.per,
+                        (long long)J * TB + j);
+        piv = 1.0;
+    }
+    const double y = rsqrt_newton(piv);
+    A[j][j] = piv * y;
+    yinv[j] = y;
+}
+
 // One CTA per problem: factor the 64 x 64 diagonal tile in double precision,
-// right-looking inside the tile (pivot, scale the column by 1/L_jj, rank-1
-// update of the trailing triangle).
+// right-looking inside the tile.  Column j: scale it by 1 / L_jj, then the
+// rank-1 update of the trailing triangle {(i, c) : j < c <= i}.  The lower
+// triangle is listed column by column in `tab`, so each trailing triangle is
+// a suffix of the list that the 256 threads share evenly; its first element
+// is (j+1, j+1), which thread 0 updates first and then turns into the next
+// pivot while the other threads are still updating.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_chol_diag(T* __restrict__ F, int64_t ntiles, int J, int64_t d, ProbMap pm, DevStatus* st)
 {
+    constexpr int NTRI = TB * (TB + 1) / 2;
     __shared__ double A[TB][TB + 1];
-    __shared__ double piv_inv;
+    __shared__ double yinv[TB];
+    __shared__ unsigned short tab[NTRI];
     const int pr = blockIdx.x, tid = threadIdx.x;
     if (prob_dead(pm, pr)) return;
     T* tile = F + ((int64_t)pr * ntiles + tile_index(J, J)) * TILE_ELEMS;
     for (int e = tid; e < TILE_ELEMS; e += 256) {
         const int r = e / TB, c = e % TB;
         A[r][c] = (c <= r) ? (double)tile[e] : 0.0;
+        // column c starts at c TB - c (c - 1) / 2 in the list
+        if (c <= r) tab[c * TB - c * (c - 1) / 2 + (r - c)] = (unsigned short)((r << 8) | c);
     }
-    for (int j = 0; j < TB; ++j) {
+    __syncthreads();
+    if (tid == 0) take_pivot(A, yinv, 0, J, d, pm, pr, st);
+    for (int j = 0; j < TB - 1; ++j) {
+        __syncthreads();                                  // pivot j and column j final
+        if (tid < TB - 1 - j) A[j + 1 + tid][j] *= yinv[j];
         __syncthreads();
-        if (tid == 0) {
-            double piv = A[j][j];
-            if (!(piv > 0.0)) {
-                if ((int64_t)J * TB + j < d)
-                    latch_error(st, PICHOL_ERR_NOT_SPD, pr / pm.per,
-                                pm.exact ? pm.t0 + pr % pm.per : pr % pm.per, (long long)J * TB + j);
-                piv = 1.0;
-            }
-            const double ljj = sqrt(piv);
-            A[j][j] = ljj;
-            piv_inv = 1.0 / ljj;
-        }
-        __syncthreads();
-        const double inv = piv_inv;
-        for (int i = j + 1 + tid; i < TB; i += 256) A[i][j] *= inv;
-        __syncthreads();
-        // rank-1 update of the trailing triangle: thread (row i = tid & 63,
-        // phase ph = tid >> 6) updates columns c = j+1+ph, j+5+ph, ... <= i
-        const int i = tid & 63, ph = tid >> 6;
-        if (i > j) {
-            const double aij = A[i][j];
-            for (int c = j + 1 + ph; c <= i; c += 4) A[i][c] -= aij * A[c][j];
+        const int e0 = (j + 1) * TB - (j + 1) * j / 2;
+        for (int e = e0 + tid; e < NTRI; e += 256) {
+            const int ic = tab[e];
+            const int i = ic >> 8, c = ic & 255;
+            A[i][c] = fma(-A[i][j], A[c][j], A[i][c]);
+            if (e == e0) take_pivot(A, yinv, j + 1, J, d, pm, pr, st);
         }
     }
     __syncthreads();
@@ -101,51 +131,41 @@ k_chol_diag(T* __restrict__ F, int64_t ntiles, int J, int64_t d, ProbMap pm, Dev
     }
 }
 
-// Load a 64 x 64 row-major tile transposed into shared memory: S[k][r] = src[r][k].
-template <typename T, typename S>
-__device__ inline void load_tile_transposed(const S* __restrict__ src, T (*dst)[TB + 1])
-{
-    for (int e = threadIdx.x; e < TILE_ELEMS; e += blockDim.x) {
-        int r = e / TB, k = e % TB;
-        dst[k][r] = (T)src[e];
-    }
-}
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int N = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
 
-// acc[a][b] += sum_k As[k][ty + 16a] * Bs[k][tx + 16b]   (C = A B^T for row-major A, B)
-template <typename T>
-__device__ inline void mm_nt(T (*As)[TB + 1], T (*Bs)[TB + 1], T acc[4][4])
+// Copy a row-major 64 x 64 tile into shared memory rows of LD elements (16-byte moves).
+template <typename T, int LD, int NT>
+__device__ __forceinline__ void stage_tile(T* __restrict__ dst, const T* __restrict__ src)
 {
-    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-#pragma unroll 4
-    for (int k = 0; k < TB; ++k) {
-        T av[4], bv[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = As[k][ty + 16 * a];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) bv[b] = Bs[k][tx + 16 * b];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::N, CPR = TB / VN;
+    for (int q = threadIdx.x; q < TB * CPR; q += NT) {
+        const int r = q / CPR, ch = q % CPR;
+        *reinterpret_cast<V*>(dst + r * LD + ch * VN) = *reinterpret_cast<const V*>(src + r * TB + ch * VN);
     }
 }
 
 // L_IJ = A_IJ L_JJ^{-T}: every row x of L_IJ solves L_JJ x^T = a^T by forward
 // substitution, x_c = (a_c - sum_{k<c} L_JJ[c][k] x_k) / L_JJ[c][c].  One
-// thread per row, 256 / 64 = 4 tiles per CTA, the row in registers.
+// thread per row (the row in registers), 256 / 64 = 4 tiles per CTA; the rows
+// of L_JJ are read from shared memory 16 bytes at a time (the same address for
+// the whole warp), and each sum runs as two interleaved partial sums.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_chol_panel(T* __restrict__ F, int64_t ntiles, int J, int m, ProbMap pm)
 {
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::N, LD = TB + VN;
     if (prob_dead(pm, blockIdx.y)) return;
-    __shared__ T Ls[TB][TB + 1];
+    __shared__ __align__(16) T Ls[TB * LD];
     __shared__ T inv[TB];
     const int pr = blockIdx.y, tid = threadIdx.x;
     T* base = F + (int64_t)pr * ntiles * TILE_ELEMS;
-    const T* ljj = base + tile_index(J, J) * TILE_ELEMS;
-    for (int e = tid; e < TILE_ELEMS; e += 256) Ls[e / TB][e % TB] = ljj[e];
+    stage_tile<T, LD, 256>(Ls, base + tile_index(J, J) * TILE_ELEMS);
     __syncthreads();
-    if (tid < TB) inv[tid] = T(1) / Ls[tid][tid];
+    if (tid < TB) inv[tid] = T(1) / Ls[tid * LD + tid];
     __syncthreads();
     const int it = blockIdx.x * 4 + (tid >> 6);
     if (it >= m) return;
@@ -153,50 +173,102 @@ k_chol_panel(T* __restrict__ F, int64_t ntiles, int J, int m, ProbMap pm)
     T* row = base + tile_index(J + 1 + it, J) * TILE_ELEMS + r * TB;
     T x[TB];
 #pragma unroll
-    for (int c = 0; c < TB; ++c) x[c] = row[c];
-#pragma unroll
-    for (int c = 0; c < TB; ++c) {
-        T sacc = x[c];
-#pragma unroll
-        for (int k2 = 0; k2 < c; ++k2) sacc = fma(-Ls[c][k2], x[k2], sacc);
-        x[c] = sacc * inv[c];
+    for (int ch = 0; ch < TB / VN; ++ch) {
+        V v = reinterpret_cast<const V*>(row)[ch];
+        memcpy(&x[ch * VN], &v, sizeof(V));
     }
 #pragma unroll
-    for (int c = 0; c < TB; ++c) row[c] = x[c];
+    for (int c = 0; c < TB; ++c) {
+        T s0 = x[c], s1 = T(0);
+#pragma unroll
+        for (int k0 = 0; k0 < c; k0 += VN) {
+            V lv = *reinterpret_cast<const V*>(Ls + c * LD + k0);
+            T l[VN];
+            memcpy(l, &lv, sizeof(V));
+#pragma unroll
+            for (int e = 0; e < VN; ++e) {
+                if (k0 + e < c) {
+                    if (((k0 / VN) & 1) == 0) s0 = fma(-l[e], x[k0 + e], s0);
+                    else s1 = fma(-l[e], x[k0 + e], s1);
+                }
+            }
+        }
+        x[c] = (s0 + s1) * inv[c];
+    }
+#pragma unroll
+    for (int ch = 0; ch < TB / VN; ++ch) {
+        V v;
+        memcpy(&v, &x[ch * VN], sizeof(V));
+        reinterpret_cast<V*>(row)[ch] = v;
+    }
 }
 
-// A_IK -= L_IJ L_KJ^T for the trailing lower tiles J < K <= I.
-template <typename T>
-__global__ void __launch_bounds__(256)
-k_chol_update(T* __restrict__ F, int64_t ntiles, int J, ProbMap pm)
+// A_IK -= L_IJ L_KJ^T for trailing lower tiles: with column = 0 the triangle
+// first <= K <= I < nt (one CTA per tile, triangular index), with column = 1
+// the tiles (I, first), I >= first.  NT threads per tile; thread (ty, tx) =
+// (t / 8, t % 8) owns rows ty + (NT/8) a and columns tx + 8 b.  Both operand
+// tiles are staged row-major (k contiguous, rows padded to LD elements so that
+// the 16-byte row reads of a warp hit distinct banks) and read 16 bytes of k
+// at a time.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT)
+k_chol_update(T* __restrict__ F, int64_t ntiles, int J, int first, int column, ProbMap pm)
 {
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::N, LD = TB + VN;
+    constexpr int TY = NT / 8, RA = TB / TY, RC = 8;
     if (prob_dead(pm, blockIdx.y)) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    T (*As)[TB + 1] = reinterpret_cast<T (*)[TB + 1]>(sm_raw);
-    T (*Bs)[TB + 1] = reinterpret_cast<T (*)[TB + 1]>(sm_raw + sizeof(T) * TB * (TB + 1));
-    int ii, kk;
-    tile_coords(blockIdx.x, ii, kk);
-    const int I = J + 1 + ii, K = J + 1 + kk, pr = blockIdx.y;
+    T* As = reinterpret_cast<T*>(sm_raw);
+    int ii = (int)blockIdx.x, kk = 0;
+    if (!column) tile_coords(blockIdx.x, ii, kk);
+    const int I = first + ii, K = first + kk, pr = blockIdx.y;
     T* base = F + (int64_t)pr * ntiles * TILE_ELEMS;
-    load_tile_transposed<T, T>(base + tile_index(I, J) * TILE_ELEMS, As);
-    load_tile_transposed<T, T>(base + tile_index(K, J) * TILE_ELEMS, Bs);
+    stage_tile<T, LD, NT>(As, base + tile_index(I, J) * TILE_ELEMS);
+    T* Bs = As;
+    if (K != I) {
+        Bs = As + TB * LD;
+        stage_tile<T, LD, NT>(Bs, base + tile_index(K, J) * TILE_ELEMS);
+    }
     __syncthreads();
-    T acc[4][4];
+    const int ty = threadIdx.x >> 3, tx = threadIdx.x & 7;
+    T acc[RA][RC];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < RA; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-    mm_nt<T>(As, Bs, acc);
+        for (int b = 0; b < RC; ++b) acc[a][b] = T(0);
+#pragma unroll 2
+    for (int k0 = 0; k0 < TB; k0 += VN) {
+        T av[RA][VN], bv[RC][VN];
+#pragma unroll
+        for (int a = 0; a < RA; ++a) {
+            V v = *reinterpret_cast<const V*>(As + (ty + TY * a) * LD + k0);
+            memcpy(av[a], &v, sizeof(V));
+        }
+#pragma unroll
+        for (int b = 0; b < RC; ++b) {
+            V v = *reinterpret_cast<const V*>(Bs + (tx + 8 * b) * LD + k0);
+            memcpy(bv[b], &v, sizeof(V));
+        }
+#pragma unroll
+        for (int e = 0; e < VN; ++e)
+#pragma unroll
+            for (int a = 0; a < RA; ++a)
+#pragma unroll
+                for (int b = 0; b < RC; ++b) acc[a][b] = fma(av[a][e], bv[b][e], acc[a][b]);
+    }
     T* out = base + tile_index(I, K) * TILE_ELEMS;
-    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < RA; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            int e = (ty + 16 * a) * TB + tx + 16 * b;
+        for (int b = 0; b < RC; ++b) {
+            const int e = (ty + TY * a) * TB + tx + 8 * b;
             out[e] = out[e] - acc[a][b];
         }
 }
+
+template <typename T> struct UpdateThreads { static constexpr int value = 128; };
+template <> struct UpdateThreads<double> { static constexpr int value = 256; };
 
 template <typename T>
 static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cudaStream_t s)
@@ -209,10 +281,12 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
     pm.count = count;
     const int nprob = c.k * pm.per;
     T* F = (T*)ctx->F;
-    const size_t sm_mm = 2 * sizeof(T) * TB * (TB + 1);
+    constexpr int UNT = UpdateThreads<T>::value;
+    const size_t sm_mm = 2 * sizeof(T) * TB * (TB + Vec16<T>::N);
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_chol_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_mm);
+        cudaError_t e = cudaFuncSetAttribute(k_chol_update<T, UNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sm_mm);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
@@ -222,24 +296,65 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
             (const T*)ctx->Hf, c.d, ctx->ntiles, pm, ctx->lam, ctx->lam_s, F);
     }
     ctx->launches++;
+    // Look-ahead: the critical path (diagonal tile J, panel J, then the tiles
+    // of column J+1) runs on the context's high-priority stream sh, so its
+    // CTAs are dispatched ahead of the bulk of the trailing update (tiles
+    // K >= J+2), which runs on the caller's stream s meanwhile.  The column
+    // update J+1 waits for the bulk update J (both write column J+2).  sh forks
+    // from s after the factor input is written and joins back at the end, so
+    // the call stays capturable.
+    cudaStream_t sh = ctx->aux ? ctx->aux : s;
+    const bool split = sh != s;
+    cudaError_t e;
+    if (split) {
+        if ((e = cudaEventRecord(ctx->ev_fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(sh, ctx->ev_fork, 0)) != cudaSuccess) return e;
+    }
+    bool pending = false;   // a bulk update on s that sh has not yet waited for
     for (int J = 0; J < ctx->nt; ++J) {
         {
-            StageScope sc_(ctx, ST_CHOL_DIAG, s);
-            k_chol_diag<T><<<nprob, 256, 0, s>>>(F, ctx->ntiles, J, c.d, pm, ctx->status);
+            StageScope sc_(ctx, ST_CHOL_DIAG, sh);
+            k_chol_diag<T><<<nprob, 256, 0, sh>>>(F, ctx->ntiles, J, c.d, pm, ctx->status);
         }
         ctx->launches++;
         const int m = ctx->nt - 1 - J;
-        if (m > 0) {
+        if (m == 0) break;
+        {
+            StageScope sc_(ctx, ST_CHOL_PANEL, sh);
+            k_chol_panel<T><<<dim3((m + 3) / 4, nprob), 256, 0, sh>>>(F, ctx->ntiles, J, m, pm);
+        }
+        ctx->launches++;
+        if (split && m > 1) {
+            if ((e = cudaEventRecord(ctx->ev_panel, sh)) != cudaSuccess) return e;
+            if (pending && (e = cudaStreamWaitEvent(sh, ctx->ev_upd, 0)) != cudaSuccess) return e;
             {
-                StageScope sc_(ctx, ST_CHOL_PANEL, s);
-                k_chol_panel<T><<<dim3((m + 3) / 4, nprob), 256, 0, s>>>(F, ctx->ntiles, J, m, pm);
+                StageScope sc_(ctx, ST_CHOL_UPDATE, sh);
+                k_chol_update<T, UNT><<<dim3(m, nprob), UNT, sm_mm, sh>>>(F, ctx->ntiles, J, J + 1, 1, pm);
             }
+            if ((e = cudaStreamWaitEvent(s, ctx->ev_panel, 0)) != cudaSuccess) return e;
             {
                 StageScope sc_(ctx, ST_CHOL_UPDATE, s);
-                k_chol_update<T><<<dim3(m * (m + 1) / 2, nprob), 256, sm_mm, s>>>(F, ctx->ntiles, J, pm);
+                k_chol_update<T, UNT><<<dim3(m * (m - 1) / 2, nprob), UNT, sm_mm, s>>>(F, ctx->ntiles, J, J + 2, 0,
+                                                                                     pm);
             }
+            if ((e = cudaEventRecord(ctx->ev_upd, s)) != cudaSuccess) return e;
+            pending = true;
             ctx->launches += 2;
+        } else {
+            if (pending && (e = cudaStreamWaitEvent(sh, ctx->ev_upd, 0)) != cudaSuccess) return e;
+            pending = false;
+            {
+                StageScope sc_(ctx, ST_CHOL_UPDATE, sh);
+                k_chol_update<T, UNT><<<dim3(m * (m + 1) / 2, nprob), UNT, sm_mm, sh>>>(F, ctx->ntiles, J, J + 1, 0,
+                                                                                      pm);
+            }
+            ctx->launches++;
         }
+    }
+    if (split) {
+        // s already follows every bulk update it ran; it now waits for sh
+        if ((e = cudaEventRecord(ctx->ev_join, sh)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, ctx->ev_join, 0)) != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }

@@ -145,6 +145,12 @@ struct pichol_ctx {
     bool have_hessian, have_factors, have_fit;
     long long launches;
 
+    // factorisation look-ahead: diagonal tiles, panels and the next tile column
+    // run on `aux` (the device's highest stream priority) while the rest of each
+    // trailing update runs on the caller's stream (created with the workspace)
+    cudaStream_t aux;
+    cudaEvent_t ev_fork, ev_panel, ev_upd, ev_join;
+
     // optional per-stage timing: pairs of events recorded around launches
     int timing;
     int ev_cap, ev_used;

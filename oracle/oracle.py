@@ -450,9 +450,11 @@ def _holdout_and_grad(Xv, Yv, Bf, L, dL, lam):
 
 
 def holdout_grad(X, Y, *, k: int, g: int, r: int, q: int, log_lam: float, lo: float = 1e-3, hi: float = 1e1,
-                 basis: str = BASIS_CHEB_LOG, exact: bool = False, scale_by_trace: bool = True) -> GradResult:
+                 basis: str = BASIS_CHEB_LOG, exact: bool = False, scale_by_trace: bool = True,
+                 folds=None) -> GradResult:
     """Hold-out MSE per fold at lambda = exp(log_lam) and its derivative with
-    respect to log(lambda).
+    respect to log(lambda).  ``folds`` restricts the work to some folds (the
+    others are NaN; Ebar and dEbar then average the computed folds only).
 
     exact=False: through the interpolated factor L(lambda) = sum_m phi_m(lambda)
     Theta_m of Algorithm 1 (sampled at the same grid indices as ``cv``), so
@@ -469,9 +471,9 @@ def holdout_grad(X, Y, *, k: int, g: int, r: int, q: int, log_lam: float, lo: fl
     grid = lambda_grid(tau, q, lo, hi)
     sidx = sample_indices(q, g)
     lam_s = grid[sidx]
-    E = np.empty(k)
-    dE = np.empty(k)
-    for f in range(k):
+    E = np.full(k, np.nan)
+    dE = np.full(k, np.nan)
+    for f in (range(k) if folds is None else folds):
         r0, r1 = offs[f], offs[f + 1]
         Hf, Bf = normal_blocks(X, Y, r0, r1)
         Xv, Yv = X[r0:r1], Y[r0:r1]
@@ -493,4 +495,4 @@ def holdout_grad(X, Y, *, k: int, g: int, r: int, q: int, log_lam: float, lo: fl
         L = unvec_lower(eval_poly(phi, Theta), d)
         dL = unvec_lower(eval_poly(dphi, Theta), d)
         E[f], dE[f] = _holdout_and_grad(Xv, Yv, Bf, L, dL, lam)
-    return GradResult(E=E, dE=dE, Ebar=float(E.mean()), dEbar=float(dE.mean()))
+    return GradResult(E=E, dE=dE, Ebar=float(np.nanmean(E)), dEbar=float(np.nanmean(dE)))

@@ -9,14 +9,18 @@
 //   k_solve    : forward (L~ Z = B) and back (L~^T W = Z) block substitution
 //                for a group of LG lambdas of one fold per CTA.  Each
 //                off-diagonal tile's coefficient planes are copied into shared
-//                memory once (cp.async, XOR-swizzled) and evaluated there for
+//                memory once (fp32: TMA boxes with 128-byte swizzle, one thread
+//                issuing; fp64: cp.async, XOR-swizzled) and evaluated there for
 //                all LG lambdas, so L~(lambda) never exists in global memory.
 //   k_resid    : refinement residual r = B - L~ (L~^T W) with double-float
 //                accumulation (error-free products, compensated sums).
 //   k_score    : E partials <W_I, (G_f W)_I> - 2 <Bv_I, W_I> per tile row.
 //   k_select   : E_f(t), mean over folds, first argmin.
 #include "internal.cuh"
+#include "tma.cuh"
+
 #include <cfloat>
+#include <cstring>
 
 namespace pichol {
 
@@ -148,6 +152,7 @@ struct SolveArgs {
     const double* phi;   // [t][p]
     int p, nt, q, t0, tcount, per, rhs_per_system;
     int64_t ntiles, dp, c;
+    DevStatus* st;       // PICHOL_ERR_TIMEOUT if a bounded copy wait runs out
 };
 
 template <typename T, int LG, int CB, int NP, bool EXACT>
@@ -167,9 +172,43 @@ struct SolveCfg {
     static constexpr int PLANE_BYTES = (2 * STAGE_BYTES > DINV_BYTES) ? 2 * STAGE_BYTES : DINV_BYTES;
     static constexpr int ZS_BYTES = 2 * LG * (TB / 2) * CBP * ESZ;     // staged solved half blocks
     static constexpr int R_BYTES = 4 * LG * TB * CBP * ESZ;            // 4 reduction slots
-    static constexpr int SMEM = PLANE_BYTES + ZS_BYTES + R_BYTES;
+    static constexpr bool TMA = std::is_same<T, float>::value;          // fp32 planes arrive by TMA
+    static constexpr int SMEM = PLANE_BYTES + ZS_BYTES + R_BYTES + (TMA ? 1024 : 0);   // + alignment
     static constexpr int ZPER = (LG * (TB / 2) * CB + 255) / 256;      // staged values per thread
 };
+
+// Byte offset of element (row, col) of a row half (rows [32 h, 32 h + 32), all
+// 64 columns) of an fp32 plane staged by two TMA boxes of 32 x 32: the box of
+// columns [32 b, 32 b + 32) at b * 4096, rows of 128 bytes whose 16-byte
+// chunks are permuted by XOR with (row & 7) (the 128-byte swizzle).
+__device__ __forceinline__ int rowhalf_off_f32(int row, int col)
+{
+    return (col >> 5) * 4096 + row * 128 + (((((col & 31) >> 2) ^ (row & 7))) << 4) + ((col & 3) << 2);
+}
+
+// TMA copy of half of the NPS fp32 planes of one tile into a stage (1024-byte
+// aligned), the same layouts stage_half writes for cols = true, and the
+// rowhalf_off_f32 layout for cols = false.  row0(pl) is the first row of plane
+// pl in the map's [rows][64] view.  Issued by one thread; completes on `bar`.
+template <int NPS, typename Row0>
+__device__ __forceinline__ void tma_stage_half(unsigned char* sdst, const CUtensorMap* map, uint64_t* bar, int h,
+                                               bool cols, Row0 row0)
+{
+    constexpr int HPB = (TB / 2) * TB * 4;
+    mbar_expect_tx(bar, (uint32_t)(NPS * HPB));
+#pragma unroll
+    for (int pl = 0; pl < NPS; ++pl) {
+        const int y = row0(pl);
+        unsigned char* d = sdst + pl * HPB;
+        if (cols) {
+            tma_load_2d(d, map, bar, 32 * h, y);
+            tma_load_2d(d + 4096, map, bar, 32 * h, y + 32);
+        } else {
+            tma_load_2d(d, map, bar, 0, y + 32 * h);
+            tma_load_2d(d + 4096, map, bar, 32, y + 32 * h);
+        }
+    }
+}
 
 // Copy half of the NPS coefficient planes of one tile into a swizzled stage.
 //  forward (cols = true):  columns [32 h, 32 h + 32) of all 64 rows, 32-wide rows
@@ -209,14 +248,19 @@ __device__ __forceinline__ void stage_half(unsigned char* sdst, const T* gsrc, i
 // partial sums are combined in a fixed order through four shared slots.
 template <typename T, int LG, int CB, int NP, bool EXACT>
 __global__ void __launch_bounds__(256, 2)
-k_solve(SolveArgs a)
+k_solve(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
 {
     using C = SolveCfg<T, LG, CB, NP, EXACT>;
     constexpr int VN = C::VN, CBP = C::CBP, NPS = C::NPS, ESZ = C::ESZ;
     constexpr int RB = C::RB, RPT = C::RPT, KW = C::KW, HPB = C::HPB, ZPER = C::ZPER;
     constexpr int HT = TB / 2;
+    constexpr bool TMA = C::TMA;
     using V = typename Vec16<T>::type;
-    extern __shared__ __align__(128) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw;
+    if constexpr (TMA) smem += (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;   // 128-byte swizzle atoms
+    __shared__ uint64_t tbar[2];
+    uint32_t phase = 0;                 // bit s: parity of the next completion of stage s
     unsigned char* planes = smem;
     T* Zs = reinterpret_cast<T*>(smem + C::PLANE_BYTES);              // [2][LG][32][CBP]
     T* Rs = reinterpret_cast<T*>(smem + C::PLANE_BYTES + C::ZS_BYTES); // [4][LG][64][CBP]
@@ -247,6 +291,12 @@ k_solve(SolveArgs a)
     T* out = (T*)a.out;
     for (int e = tid; e < 2 * LG * HT * CBP; e += 256) Zs[e] = T(0);
     for (int e = tid; e < 4 * LG * TB * CBP; e += 256) Rs[e] = T(0);
+    if (TMA && tid == 0) {
+        mbar_init(&tbar[0], 1);
+        mbar_init(&tbar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
 
     auto sys_base = [&](int l) -> int64_t { return ((int64_t)f * a.q + tl[l]) * dp * c; };
     // the staged values of this thread: system l, row kk of the half block, output o
@@ -275,13 +325,34 @@ k_solve(SolveArgs a)
     };
     auto issue = [&](int I, int J, int h, bool cols, int stage) {
         unsigned char* dst = planes + stage * C::STAGE_BYTES;
-        if constexpr (EXACT) {
-#pragma unroll
-            for (int l = 0; l < LG; ++l) stage_half<T>(dst + l * HPB, tile_src(I, J, l), 1, h, cols);
+        if constexpr (TMA) {
+            if (tid == 0) {
+                const int64_t tix = tile_index(I, J);
+                tma_stage_half<NPS>(dst, &tmap, &tbar[stage], h, cols, [&](int pl) -> int {
+                    if constexpr (EXACT)
+                        return (int)(((int64_t)(f * a.per + (tl[pl] - a.t0)) * a.ntiles + tix) * TB);
+                    else
+                        return (int)((((int64_t)f * a.ntiles + tix) * a.p + pl) * TB);
+                });
+            }
         } else {
-            stage_half<T>(dst, tile_src(I, J, 0), NPS, h, cols);
+            if constexpr (EXACT) {
+#pragma unroll
+                for (int l = 0; l < LG; ++l) stage_half<T>(dst + l * HPB, tile_src(I, J, l), 1, h, cols);
+            } else {
+                stage_half<T>(dst, tile_src(I, J, 0), NPS, h, cols);
+            }
+            cp_async_commit();
         }
-        cp_async_commit();
+    };
+    // a bounded copy wait ran out: latch, wait (bounded) for this CTA's copies
+    // still in flight, and let every thread return
+    auto give_up = [&](int stage, bool prefetched) {
+        if (tid == 0) {
+            latch_error(a.st, PICHOL_ERR_TIMEOUT, f, (int)blockIdx.x, -1);
+            mbar_wait(&tbar[stage], (phase >> stage) & 1u);
+            if (prefetched) mbar_wait(&tbar[stage ^ 1], (phase >> (stage ^ 1)) & 1u);
+        }
     };
     auto evalv = [&](const T* v, int l) -> T {
         if constexpr (EXACT) {
@@ -330,14 +401,20 @@ k_solve(SolveArgs a)
             }
 #pragma unroll 1
             for (int it = 0; it < nit; ++it) {
-                const int stage = it & 1, h = it & 1;
+                const int stage = it & 1;
                 if (it + 1 < nit) {
                     issue(back ? tj(it + 1) : i, back ? i : tj(it + 1), (it + 1) & 1, !back, (it + 1) & 1);
-                    cp_async_wait<1>();
+                    if constexpr (!TMA) cp_async_wait<1>();
                 } else {
-                    cp_async_wait<0>();
+                    if constexpr (!TMA) cp_async_wait<0>();
                 }
-                __syncthreads();
+                bool ok = true;
+                if constexpr (TMA) ok = mbar_wait(&tbar[stage], (phase >> stage) & 1u);
+                if (__syncthreads_or(!ok)) {
+                    give_up(stage, it + 1 < nit);
+                    return;
+                }
+                if constexpr (TMA) phase ^= 1u << stage;
                 if (it + 1 < nit) load_z(it + 1);
                 const unsigned char* pl = planes + stage * C::STAGE_BYTES;
                 const T* zs = Zs + stage * LG * HT * CBP;
@@ -393,7 +470,9 @@ k_solve(SolveArgs a)
 #pragma unroll
                         for (int hh = 0; hh < RB; ++hh) {
                             const int col = rp + RPT * hh;
-                            const int coff = kk * TB * ESZ + ((((col * ESZ) >> 4) ^ (kk & 7)) << 4) + ((col * ESZ) & 15);
+                            const int coff = TMA ? rowhalf_off_f32(kk, col)
+                                                 : kk * TB * ESZ + ((((col * ESZ) >> 4) ^ (kk & 7)) << 4) +
+                                                       ((col * ESZ) & 15);
                             T ve[NPS];
 #pragma unroll
                             for (int m = 0; m < NPS; ++m) ve[m] = *reinterpret_cast<const T*>(pl + m * HPB + coff);
@@ -418,6 +497,7 @@ k_solve(SolveArgs a)
                     }
                 }
                 if (it + 1 < nit) store_z((it + 1) & 1);
+                if constexpr (TMA) fence_proxy_async();   // reads of this stage before its next TMA fill
                 __syncthreads();
             }
             // stage the LG diagonal inverses (the ring is free now) while the
@@ -504,6 +584,7 @@ k_solve(SolveArgs a)
                         if (o < c) dstb[o] = x[o];
                 }
             }
+            if constexpr (TMA) fence_proxy_async();   // the inverses' ring before the next TMA fill
             __syncthreads();
         }
     }
@@ -527,6 +608,7 @@ struct ResidArgs {
     const double* phi;
     int p, nt, q, t0, tcount;
     int64_t ntiles, dp, c;
+    DevStatus* st;       // PICHOL_ERR_TIMEOUT if a bounded copy wait runs out
 };
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
@@ -538,14 +620,17 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 
 template <int LG, int CB, int NP, int PASS>
 __global__ void __launch_bounds__(256, 2)
-k_resid(ResidArgs a)
+k_resid(ResidArgs a, const __grid_constant__ CUtensorMap tmap)
 {
     constexpr int CBP = CB;                     // exact column count (no vector loads of Z here)
     constexpr int HT = TB / 2;
     constexpr int HPB = HT * TB * 4;            // half plane, fp32
     constexpr int STAGE = NP * HPB;
-    extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char* planes = smem;                                          // 2 stages
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    __shared__ uint64_t tbar[2];
+    uint32_t phase = 0;                         // bit s: parity of the next completion of stage s
+    unsigned char* planes = smem;                                          // 2 stages (TMA)
     float* Zh = reinterpret_cast<float*>(smem + 2 * STAGE);                // [2][LG][32][CBP]
     float* Zl = Zh + 2 * LG * HT * CBP;                                    // [2][LG][32][CBP]
     double* Rd = reinterpret_cast<double*>(Zl + 2 * LG * HT * CBP);       // [LG][64][CBP]
@@ -571,6 +656,12 @@ k_resid(ResidArgs a)
 #pragma unroll
         for (int o = 0; o < CBP; ++o) { sh[l][o] = 0.0f; sl[l][o] = 0.0f; }
     for (int e = tid; e < 2 * 2 * LG * HT * CBP; e += 256) Zh[e] = 0.0f;   // Zh and Zl, both buffers
+    if (tid == 0) {
+        mbar_init(&tbar[0], 1);
+        mbar_init(&tbar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
     // staged values of this thread (precomputed offsets): system l, row kk, output o
     constexpr int ZPER = (LG * HT * CB + 255) / 256;
     int64_t zg[ZPER];
@@ -594,9 +685,10 @@ k_resid(ResidArgs a)
         const int64_t tix = PASS == 0 ? tile_index(j, i) : tile_index(i, j);
         // PASS 0 reads columns r of tile (j, i): its k are the tile's rows (half = rows);
         // PASS 1 reads rows r of tile (i, j): its k are the tile's columns (half = columns)
-        stage_half<float>(planes + (it & 1) * STAGE, a.theta + ((int64_t)f * a.ntiles + tix) * a.p * TILE_ELEMS, NP,
-                          h, PASS == 1);
-        cp_async_commit();
+        if (tid == 0)
+            tma_stage_half<NP>(planes + (it & 1) * STAGE, &tmap, &tbar[it & 1], h, PASS == 1, [&](int pl) -> int {
+                return (int)((((int64_t)f * a.ntiles + tix) * a.p + pl) * TB);
+            });
     };
     float zr[2][ZPER];
     auto load_z = [&](int it) {
@@ -628,13 +720,20 @@ k_resid(ResidArgs a)
     store_z(0);
 #pragma unroll 1
     for (int it = 0; it < nit; ++it) {
-        if (it + 1 < nit) {
-            issue(it + 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
+        const int stage = it & 1;
+        if (it + 1 < nit) issue(it + 1);
+        const bool ok = mbar_wait(&tbar[stage], (phase >> stage) & 1u);
+        if (__syncthreads_or(!ok)) {
+            // a bounded copy wait ran out: latch, wait (bounded) for this CTA's
+            // copies still in flight, and let every thread return
+            if (tid == 0) {
+                latch_error(a.st, PICHOL_ERR_TIMEOUT, f, (int)blockIdx.x, -1);
+                mbar_wait(&tbar[stage], (phase >> stage) & 1u);
+                if (it + 1 < nit) mbar_wait(&tbar[stage ^ 1], (phase >> (stage ^ 1)) & 1u);
+            }
+            return;
         }
-        __syncthreads();
+        phase ^= 1u << stage;
         if (it + 1 < nit) load_z(it + 1);
         const unsigned char* pl = planes + (it & 1) * STAGE;
         const float* zhb = Zh + (it & 1) * LG * HT * CBP;
@@ -646,13 +745,10 @@ k_resid(ResidArgs a)
 #pragma unroll
             for (int m = 0; m < NP; ++m) {
                 if (PASS == 0) {
-                    // column r of the staged rows k0..k0+3 (64-wide rows)
+                    // column r of the staged rows k0..k0+3 (two 32-column boxes)
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int kk = k0 + e;
-                        v4[m][e] = *reinterpret_cast<const float*>(pl + m * HPB + kk * TB * 4 +
-                                                                   ((((r * 4) >> 4) ^ (kk & 7)) << 4) + ((r * 4) & 15));
-                    }
+                    for (int e = 0; e < 4; ++e)
+                        v4[m][e] = *reinterpret_cast<const float*>(pl + m * HPB + rowhalf_off_f32(k0 + e, r));
                 } else {
                     // row r, columns k0..k0+3 of the staged 32-wide rows: one 16-byte chunk
                     const int kc = k0 >> 2;
@@ -684,6 +780,7 @@ k_resid(ResidArgs a)
             }
         }
         if (it + 1 < nit) store_z((it + 1) & 1);
+        fence_proxy_async();                    // reads of this stage before its next TMA fill
         __syncthreads();
     }
     // combine the four k slices in double
@@ -911,7 +1008,16 @@ size_t solve_smem_bytes(int eb, int p, int64_t c)
     const int nps = p > LG ? p : LG;   // interpolated (p planes) or exact (LG planes)
     const size_t hpb = (size_t)(TB / 2) * TB * eb;
     const size_t ring = 2 * nps * hpb > (size_t)LG * TB * TB * eb ? 2 * nps * hpb : (size_t)LG * TB * TB * eb;
-    return ring + (size_t)2 * LG * (TB / 2) * cbp * eb + (size_t)4 * LG * TB * cbp * eb;
+    return ring + (size_t)2 * LG * (TB / 2) * cbp * eb + (size_t)4 * LG * TB * cbp * eb + (eb == 4 ? 1024 : 0);
+}
+
+// The map the fp32 solve and residual stage coefficient (or factor) planes
+// through: the buffer viewed as [rows][64] fp32, 32 x 32 boxes.
+static cudaError_t plane_map(CUtensorMap* m, const void* buf, int64_t planes)
+{
+    const int64_t rows = planes * TB;
+    if (rows > INT32_MAX) return cudaErrorInvalidValue;   // TMA coordinates are 32-bit
+    return make_map_f32(m, (const float*)buf, TB, (uint64_t)rows, TB, 32, 32) ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 template <typename T, int LG, int CB, int NP, bool EXACT>
@@ -926,9 +1032,16 @@ static cudaError_t run_solve(pichol_ctx* ctx, const SolveArgs& sa, cudaStream_t 
         done = true;
     }
     dim3 grid((unsigned)((sa.tcount + LG - 1) / LG), ctx->cfg.k);
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    if constexpr (C::TMA) {
+        const int64_t planes = EXACT ? ctx->nfac * ctx->ntiles : (int64_t)ctx->cfg.k * ctx->ntiles * ctx->p;
+        cudaError_t e = plane_map(&map, sa.src, planes);
+        if (e != cudaSuccess) return e;
+    }
     {
         StageScope sc_(ctx, ST_SOLVE, s);
-        k_solve<T, LG, CB, NP, EXACT><<<grid, 256, C::SMEM, s>>>(sa);
+        k_solve<T, LG, CB, NP, EXACT><<<grid, 256, C::SMEM, s>>>(sa, map);
     }
     ctx->launches++;
     return cudaGetLastError();
@@ -994,17 +1107,20 @@ static cudaError_t score_dispatch(pichol_ctx* ctx, const ScoreArgs& sc, cudaStre
 template <int LG, int CB, int NP, int PASS>
 static cudaError_t run_resid(pichol_ctx* ctx, const ResidArgs& ra, cudaStream_t s)
 {
-    const int smem = 2 * NP * (TB / 2) * TB * 4 + 2 * 2 * LG * (TB / 2) * CB * 4 + LG * TB * CB * 8;
+    const int smem = 2 * NP * (TB / 2) * TB * 4 + 2 * 2 * LG * (TB / 2) * CB * 4 + LG * TB * CB * 8 + 1024;
     static bool done = false;
     if (!done) {
         cudaError_t e = cudaFuncSetAttribute(k_resid<LG, CB, NP, PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         done = true;
     }
+    CUtensorMap map;
+    cudaError_t e = plane_map(&map, ra.theta, (int64_t)ctx->cfg.k * ctx->ntiles * ctx->p);
+    if (e != cudaSuccess) return e;
     dim3 grid(ctx->nt, (unsigned)((ra.tcount + LG - 1) / LG), ctx->cfg.k);
     {
         StageScope sc_(ctx, ST_RESID, s);
-        k_resid<LG, CB, NP, PASS><<<grid, 256, smem, s>>>(ra);
+        k_resid<LG, CB, NP, PASS><<<grid, 256, smem, s>>>(ra, map);
     }
     ctx->launches++;
     return cudaGetLastError();
@@ -1087,6 +1203,7 @@ static cudaError_t eval_impl(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s
     sa.ntiles = ctx->ntiles;
     sa.dp = ctx->dp;
     sa.c = cf.c;
+    sa.st = ctx->status;
     e = solve_dispatch<T, EXACT>(ctx, sa, s);
     if (e != cudaSuccess) return e;
 
@@ -1110,6 +1227,7 @@ static cudaError_t eval_impl(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s
             ra.ntiles = ctx->ntiles;
             ra.dp = ctx->dp;
             ra.c = cf.c;
+            ra.st = ctx->status;
             if ((e = resid_dispatch<0>(ctx, ra, s)) != cudaSuccess) return e;
             if ((e = resid_dispatch<1>(ctx, ra, s)) != cudaSuccess) return e;
             SolveArgs sc = sa;
@@ -1194,6 +1312,7 @@ static cudaError_t diag_solve_one_impl(pichol_ctx* ctx, const double* phi_row, c
     sa.ntiles = ctx->ntiles;
     sa.dp = ctx->dp;
     sa.c = cf.c;
+    sa.st = ctx->status;
     return solve_dispatch<T, false>(ctx, sa, s);
 }
 

@@ -116,6 +116,10 @@ FP64_SMALL = dict(n=2048, d=256, c=10, k=5, g=4, r=2, q=31, lo=1e-3, hi=1e1, see
 MIXED_ECC = dict(n=32768, d=2048, c=10, k=5, g=6, r=3, q=101, lo=1e-3, hi=1e1, seed=1)
 # Large single problem: n = 131072, d = 8192 random-Fourier features, c = 32.
 LARGE_RFF = dict(n=131072, d=8192, c=32, k=5, g=6, r=3, q=101, lo=1e-3, hi=1e1, seed=2)
+# Differentiation case: n = 16384, d = 1024, c = 10, Sigma eigenvalues i^-1,
+# k = 5, g = 5, r = 3, fp32 data; lambda window [0.02, 0.5] tr(H)/d (q only
+# fixes where the g samples sit).
+DIFFERENTIATION = dict(n=16384, d=1024, c=10, k=5, g=5, r=3, q=51, lo=0.02, hi=0.5, seed=4)
 
 
 def fp64_small(**over) -> Problem:
@@ -133,6 +137,12 @@ def mixed_ecc(**over) -> Problem:
 def large_rff(**over) -> Problem:
     cfg = {**LARGE_RFF, **over}
     return random_fourier(cfg["n"], cfg["d"], cfg["c"], seed=cfg["seed"], name="large_rff")
+
+
+def differentiation(**over) -> Problem:
+    cfg = {**DIFFERENTIATION, **over}
+    return spectral_gaussian(cfg["n"], cfg["d"], cfg["c"], seed=cfg["seed"], decay=1.0, dtype=np.float32,
+                             name="differentiation")
 
 
 def batched_uneven(count: int = 64, *, seed: int = 3, d_lo: int = 128, d_hi: int = 1536,

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
+import tolerances
 from paper_1404_0466_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -31,24 +32,6 @@ def _batch(torch, probs, mode):
     return b, Xs, Ys
 
 
-def _mixed_tolerance(p, ref):
-    """Per (fold, lambda) tolerance of the mixed mode: 1e-4, or the fp32
-    forward-error scale 16 kappa 2^-24 where kappa = (mu_max + lambda) /
-    (mu_min + lambda) is the condition number of H_f + lambda I (these
-    problems' Sigma has eigenvalues i^-1.5, so small lambdas are ill
-    conditioned)."""
-    n = p.X.shape[0]
-    offs = oracle.fold_offsets(n, K)
-    tol = np.empty((K, Q))
-    for f in range(K):
-        keep = np.r_[0:offs[f], offs[f + 1]:n]
-        Xk = p.X[keep].astype(np.float64)
-        mu = np.linalg.eigvalsh(Xk.T @ Xk)
-        kappa = (mu.max() + ref.lam) / (max(mu.min(), 0.0) + ref.lam)
-        tol[f] = np.maximum(1e-4, 16 * kappa * 2.0 ** -24)
-    return tol
-
-
 @pytest.mark.parametrize("mode", ["fp64", "mixed"])
 def test_batch_matches_oracle_per_problem(torch_mod, mode):
     torch = torch_mod
@@ -60,7 +43,7 @@ def test_batch_matches_oracle_per_problem(torch_mod, mode):
     for i, p in enumerate(probs):
         ref = oracle.cv(p.X, p.Y, k=K, g=G, r=R, q=Q, basis="cheb_log")
         got = E[i].cpu().numpy()
-        tol = np.full((K, Q), 1e-9) if mode == "fp64" else _mixed_tolerance(p, ref)
+        tol = np.full((K, Q), 1e-9) if mode == "fp64" else tolerances.mixed_tolerance(p.X, ref.lam, K)
         assert np.all(np.abs(got - ref.E) <= tol * np.abs(ref.E)), (i, np.max(np.abs(got - ref.E) / ref.E / tol))
         if ts[i] != ref.t_star:
             t_tol = float(tol.max())

@@ -160,6 +160,12 @@ def stage_work(cfg, mode, refine):
         "xty": ("flop", 2 * n * d * c * passes, tensor),
         # trailing updates of k g blocked factorisations (lower tiles, 2 b^3 per tile update)
         "chol_update": ("flop", upd, "alu"),
+        # the 64 x 64 diagonal tiles of k g factorisations, b^3 / 3 flops each, in FP64
+        "chol_diag": ("flop", nt * k * g * 64 ** 3 // 3, "fp64"),
+        # panel rows by substitution: b^3 flops per off-diagonal tile of the panel
+        "chol_panel": ("flop", sum(range(nt)) * 64 ** 3 * k * g, "alu"),
+        # per (fold, lambda, tile row): L~_ii from p planes (2 (p-1) b^2 / 2) and its inverse (b^3 / 3)
+        "diag_inv": ("flop", k * q * nt * (64 ** 3 // 3 + (p - 1) * 64 * 64), "alu"),
         # read g factors, write p coefficient sets, per fold (lower triangles)
         "fit": ("byte", k * (g + p) * D * eb, "hbm"),
         # per fold and lambda: two triangular solves (2 d^2 c) + the factor built twice (2 (p-1) 2 D)
@@ -174,6 +180,8 @@ def stage_work(cfg, mode, refine):
 
 
 def _peak(bound, mode, peaks):
+    if bound == "fp64":
+        return 1.25, "TFLOP/s", "nominal GB300 FP64 (1.25 TFLOP/s); no measured figure"
     if bound == "hbm":
         return peaks.get("hbm_gbs"), "GB/s", "of measured (MEASURED_PEAKS.json hbm_gbs)"
     if bound == "tensor":

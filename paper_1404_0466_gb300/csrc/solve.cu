@@ -402,19 +402,29 @@ k_solve(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
 #pragma unroll 1
             for (int it = 0; it < nit; ++it) {
                 const int stage = it & 1;
-                if (it + 1 < nit) {
-                    issue(back ? tj(it + 1) : i, back ? i : tj(it + 1), (it + 1) & 1, !back, (it + 1) & 1);
-                    if constexpr (!TMA) cp_async_wait<1>();
-                } else {
-                    if constexpr (!TMA) cp_async_wait<0>();
-                }
                 bool ok = true;
-                if constexpr (TMA) ok = mbar_wait(&tbar[stage], (phase >> stage) & 1u);
+                if constexpr (TMA) {
+                    // one barrier per half tile: the next stage is refilled after it, when
+                    // every thread has finished reading that stage (previous half tile)
+                    ok = mbar_wait(&tbar[stage], (phase >> stage) & 1u);
+                    fence_proxy_async();
+                } else {
+                    if (it + 1 < nit) {
+                        issue(back ? tj(it + 1) : i, back ? i : tj(it + 1), (it + 1) & 1, !back, (it + 1) & 1);
+                        cp_async_wait<1>();
+                    } else {
+                        cp_async_wait<0>();
+                    }
+                }
                 if (__syncthreads_or(!ok)) {
-                    give_up(stage, it + 1 < nit);
+                    give_up(stage, false);
                     return;
                 }
-                if constexpr (TMA) phase ^= 1u << stage;
+                if constexpr (TMA) {
+                    phase ^= 1u << stage;
+                    if (it + 1 < nit)
+                        issue(back ? tj(it + 1) : i, back ? i : tj(it + 1), (it + 1) & 1, !back, (it + 1) & 1);
+                }
                 if (it + 1 < nit) load_z(it + 1);
                 const unsigned char* pl = planes + stage * C::STAGE_BYTES;
                 const T* zs = Zs + stage * LG * HT * CBP;
@@ -497,11 +507,11 @@ k_solve(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
                     }
                 }
                 if (it + 1 < nit) store_z((it + 1) & 1);
-                if constexpr (TMA) fence_proxy_async();   // reads of this stage before its next TMA fill
-                __syncthreads();
+                if constexpr (!TMA) __syncthreads();
             }
-            // stage the LG diagonal inverses (the ring is free now) while the
-            // k-slice partial sums are combined
+            // stage the LG diagonal inverses (the ring is free once every thread has
+            // finished the last half tile) while the k-slice partial sums are combined
+            if constexpr (TMA) __syncthreads();
 #pragma unroll
             for (int l = 0; l < LG; ++l)
                 stage_planes<T>(planes + l * TB * TB * ESZ,
@@ -721,19 +731,21 @@ k_resid(ResidArgs a, const __grid_constant__ CUtensorMap tmap)
 #pragma unroll 1
     for (int it = 0; it < nit; ++it) {
         const int stage = it & 1;
-        if (it + 1 < nit) issue(it + 1);
+        // one barrier per half tile: the next stage is refilled after it, when every
+        // thread has finished reading that stage (previous half tile)
         const bool ok = mbar_wait(&tbar[stage], (phase >> stage) & 1u);
+        fence_proxy_async();
         if (__syncthreads_or(!ok)) {
-            // a bounded copy wait ran out: latch, wait (bounded) for this CTA's
-            // copies still in flight, and let every thread return
+            // a bounded copy wait ran out: latch, wait (bounded) for the copy still
+            // in flight, and let every thread return
             if (tid == 0) {
                 latch_error(a.st, PICHOL_ERR_TIMEOUT, f, (int)blockIdx.x, -1);
                 mbar_wait(&tbar[stage], (phase >> stage) & 1u);
-                if (it + 1 < nit) mbar_wait(&tbar[stage ^ 1], (phase >> (stage ^ 1)) & 1u);
             }
             return;
         }
         phase ^= 1u << stage;
+        if (it + 1 < nit) issue(it + 1);
         if (it + 1 < nit) load_z(it + 1);
         const unsigned char* pl = planes + (it & 1) * STAGE;
         const float* zhb = Zh + (it & 1) * LG * HT * CBP;
@@ -780,8 +792,6 @@ k_resid(ResidArgs a, const __grid_constant__ CUtensorMap tmap)
             }
         }
         if (it + 1 < nit) store_z((it + 1) & 1);
-        fence_proxy_async();                    // reads of this stage before its next TMA fill
-        __syncthreads();
     }
     // combine the four k slices in double
 #pragma unroll 1

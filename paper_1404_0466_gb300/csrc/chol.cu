@@ -203,68 +203,94 @@ k_chol_panel(T* __restrict__ F, int64_t ntiles, int J, int m, ProbMap pm)
     }
 }
 
-// A_IK -= L_IJ L_KJ^T for trailing lower tiles: with column = 0 the triangle
-// first <= K <= I < nt (one CTA per tile, triangular index), with column = 1
-// the tiles (I, first), I >= first.  NT threads per tile; thread (ty, tx) =
-// (t / 8, t % 8) owns rows ty + (NT/8) a and columns tx + 8 b.  Both operand
-// tiles are staged row-major (k contiguous, rows padded to LD elements so that
-// the 16-byte row reads of a warp hit distinct banks) and read 16 bytes of k
-// at a time.
+// Copy a row-major 64 x 64 tile into shared memory rows of LD elements with
+// 16-byte cp.async copies (committed by the caller).
+template <typename T, int LD, int NT>
+__device__ __forceinline__ void stage_tile_async(T* __restrict__ dst, const T* __restrict__ src)
+{
+    constexpr int VN = Vec16<T>::N, CPR = TB / VN;
+    for (int q = threadIdx.x; q < TB * CPR; q += NT) {
+        const int r = q / CPR, ch = q % CPR;
+        cp_async16(dst + r * LD + ch * VN, src + r * TB + ch * VN);
+    }
+}
+
+// A_IK -= L_IJ L_KJ^T for trailing lower tiles.  One CTA takes a strip of up
+// to `chunk` output tiles of one tile column: K = first + blockIdx.y, rows
+// I = K + blockIdx.x * chunk, ... (I < nt); blockIdx.z is the problem.  L_KJ
+// is staged once, the L_IJ tiles are double-buffered (cp.async), and the
+// output tile's current values are loaded into registers before its product,
+// so the global latency of each step hides behind the previous step's
+// arithmetic.  NT threads per CTA; thread (ty, tx) = (t / 8, t % 8) owns rows
+// ty + (NT/8) a and columns tx + 8 b.  Operand rows are padded to LD elements
+// so that the 16-byte row reads of a warp hit distinct banks.
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT)
-k_chol_update(T* __restrict__ F, int64_t ntiles, int J, int first, int column, ProbMap pm)
+k_chol_update(T* __restrict__ F, int64_t ntiles, int nt, int J, int first, int chunk, ProbMap pm)
 {
     using V = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::N, LD = TB + VN;
     constexpr int TY = NT / 8, RA = TB / TY, RC = 8;
-    if (prob_dead(pm, blockIdx.y)) return;
+    const int pr = blockIdx.z;
+    if (prob_dead(pm, pr)) return;
+    const int K = first + (int)blockIdx.y;
+    const int I0 = K + (int)blockIdx.x * chunk;
+    if (I0 >= nt) return;
+    const int n = (I0 + chunk < nt ? I0 + chunk : nt) - I0;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    T* As = reinterpret_cast<T*>(sm_raw);
-    int ii = (int)blockIdx.x, kk = 0;
-    if (!column) tile_coords(blockIdx.x, ii, kk);
-    const int I = first + ii, K = first + kk, pr = blockIdx.y;
+    T* Bs = reinterpret_cast<T*>(sm_raw);
+    T* As = Bs + TB * LD;                          // two buffers
     T* base = F + (int64_t)pr * ntiles * TILE_ELEMS;
-    stage_tile<T, LD, NT>(As, base + tile_index(I, J) * TILE_ELEMS);
-    T* Bs = As;
-    if (K != I) {
-        Bs = As + TB * LD;
-        stage_tile<T, LD, NT>(Bs, base + tile_index(K, J) * TILE_ELEMS);
-    }
-    __syncthreads();
+    stage_tile_async<T, LD, NT>(Bs, base + tile_index(K, J) * TILE_ELEMS);
+    stage_tile_async<T, LD, NT>(As, base + tile_index(I0, J) * TILE_ELEMS);
+    cp_async_commit();
     const int ty = threadIdx.x >> 3, tx = threadIdx.x & 7;
-    T acc[RA][RC];
+#pragma unroll 1
+    for (int u = 0; u < n; ++u) {
+        const int I = I0 + u;
+        const T* Au = As + (u & 1) * TB * LD;
+        if (u + 1 < n)
+            stage_tile_async<T, LD, NT>(As + ((u + 1) & 1) * TB * LD, base + tile_index(I + 1, J) * TILE_ELEMS);
+        cp_async_commit();
+        T* out = base + tile_index(I, K) * TILE_ELEMS;
+        T cv[RA][RC];
 #pragma unroll
-    for (int a = 0; a < RA; ++a)
+        for (int a = 0; a < RA; ++a)
 #pragma unroll
-        for (int b = 0; b < RC; ++b) acc[a][b] = T(0);
+            for (int b = 0; b < RC; ++b) cv[a][b] = out[(ty + TY * a) * TB + tx + 8 * b];
+        cp_async_wait<1>();                        // L_KJ and L_IJ have landed
+        __syncthreads();
+        T acc[RA][RC];
+#pragma unroll
+        for (int a = 0; a < RA; ++a)
+#pragma unroll
+            for (int b = 0; b < RC; ++b) acc[a][b] = T(0);
 #pragma unroll 2
-    for (int k0 = 0; k0 < TB; k0 += VN) {
-        T av[RA][VN], bv[RC][VN];
+        for (int k0 = 0; k0 < TB; k0 += VN) {
+            T av[RA][VN], bv[RC][VN];
 #pragma unroll
-        for (int a = 0; a < RA; ++a) {
-            V v = *reinterpret_cast<const V*>(As + (ty + TY * a) * LD + k0);
-            memcpy(av[a], &v, sizeof(V));
+            for (int a = 0; a < RA; ++a) {
+                V v = *reinterpret_cast<const V*>(Au + (ty + TY * a) * LD + k0);
+                memcpy(av[a], &v, sizeof(V));
+            }
+#pragma unroll
+            for (int b = 0; b < RC; ++b) {
+                V v = *reinterpret_cast<const V*>(Bs + (tx + 8 * b) * LD + k0);
+                memcpy(bv[b], &v, sizeof(V));
+            }
+#pragma unroll
+            for (int e = 0; e < VN; ++e)
+#pragma unroll
+                for (int a = 0; a < RA; ++a)
+#pragma unroll
+                    for (int b = 0; b < RC; ++b) acc[a][b] = fma(av[a][e], bv[b][e], acc[a][b]);
         }
 #pragma unroll
-        for (int b = 0; b < RC; ++b) {
-            V v = *reinterpret_cast<const V*>(Bs + (tx + 8 * b) * LD + k0);
-            memcpy(bv[b], &v, sizeof(V));
-        }
+        for (int a = 0; a < RA; ++a)
 #pragma unroll
-        for (int e = 0; e < VN; ++e)
-#pragma unroll
-            for (int a = 0; a < RA; ++a)
-#pragma unroll
-                for (int b = 0; b < RC; ++b) acc[a][b] = fma(av[a][e], bv[b][e], acc[a][b]);
+            for (int b = 0; b < RC; ++b) out[(ty + TY * a) * TB + tx + 8 * b] = cv[a][b] - acc[a][b];
+        __syncthreads();                           // this buffer is refilled two steps on
     }
-    T* out = base + tile_index(I, K) * TILE_ELEMS;
-#pragma unroll
-    for (int a = 0; a < RA; ++a)
-#pragma unroll
-        for (int b = 0; b < RC; ++b) {
-            const int e = (ty + TY * a) * TB + tx + 8 * b;
-            out[e] = out[e] - acc[a][b];
-        }
 }
 
 template <typename T> struct UpdateThreads { static constexpr int value = 128; };
@@ -282,7 +308,8 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
     const int nprob = c.k * pm.per;
     T* F = (T*)ctx->F;
     constexpr int UNT = UpdateThreads<T>::value;
-    const size_t sm_mm = 2 * sizeof(T) * TB * (TB + Vec16<T>::N);
+    constexpr int UCH = 4;                       // output tiles per CTA in the bulk updates
+    const size_t sm_mm = 3 * sizeof(T) * TB * (TB + Vec16<T>::N);
     static bool attr_done = false;
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(k_chol_update<T, UNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -329,13 +356,14 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
             if (pending && (e = cudaStreamWaitEvent(sh, ctx->ev_upd, 0)) != cudaSuccess) return e;
             {
                 StageScope sc_(ctx, ST_CHOL_UPDATE, sh);
-                k_chol_update<T, UNT><<<dim3(m, nprob), UNT, sm_mm, sh>>>(F, ctx->ntiles, J, J + 1, 1, pm);
+                k_chol_update<T, UNT><<<dim3(m, 1, nprob), UNT, sm_mm, sh>>>(F, ctx->ntiles, ctx->nt, J, J + 1, 1,
+                                                                           pm);
             }
             if ((e = cudaStreamWaitEvent(s, ctx->ev_panel, 0)) != cudaSuccess) return e;
             {
                 StageScope sc_(ctx, ST_CHOL_UPDATE, s);
-                k_chol_update<T, UNT><<<dim3(m * (m - 1) / 2, nprob), UNT, sm_mm, s>>>(F, ctx->ntiles, J, J + 2, 0,
-                                                                                     pm);
+                k_chol_update<T, UNT><<<dim3((m - 1 + UCH - 1) / UCH, m - 1, nprob), UNT, sm_mm, s>>>(
+                    F, ctx->ntiles, ctx->nt, J, J + 2, UCH, pm);
             }
             if ((e = cudaEventRecord(ctx->ev_upd, s)) != cudaSuccess) return e;
             pending = true;
@@ -345,8 +373,8 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
             pending = false;
             {
                 StageScope sc_(ctx, ST_CHOL_UPDATE, sh);
-                k_chol_update<T, UNT><<<dim3(m * (m + 1) / 2, nprob), UNT, sm_mm, sh>>>(F, ctx->ntiles, J, J + 1, 0,
-                                                                                      pm);
+                k_chol_update<T, UNT><<<dim3((m + UCH - 1) / UCH, m, nprob), UNT, sm_mm, sh>>>(
+                    F, ctx->ntiles, ctx->nt, J, J + 1, UCH, pm);
             }
             ctx->launches++;
         }

@@ -56,6 +56,16 @@ __host__ __device__ inline void tile_coords(int64_t e, int& I, int& J) {
 }
 
 #ifdef __CUDACC__
+// 16-byte asynchronous global -> shared copies (cp.async, L2 only) and their groups.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    unsigned saddr = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // First error wins; the extra fields describe it.
 __device__ inline void latch_error(DevStatus* st, int code, int fold, int index, long long pivot) {
     if (atomicCAS(&st->code, 0, code) == 0) {

@@ -132,6 +132,7 @@ pichol_status pichol_create(const pichol_config* cfg, pichol_ctx** out)
     ctx->kpad = tc_kpad(ctx);
     ctx->ldu = ((int64_t)c.q * c.c + 3) / 4 * 4;
     ctx->need_bytes = plan(ctx, nullptr);
+    ctx->diag_exclusive = 1;
     *out = ctx;
     return PICHOL_OK;
 }
@@ -152,7 +153,10 @@ pichol_status pichol_set_workspace(pichol_ctx* ctx, void* workspace, size_t byte
     plan(ctx, ctx->ws);
     ctx->have_hessian = ctx->have_factors = ctx->have_fit = false;
     if (!ctx->aux) {
-        int least = 0, greatest = 0;
+        int dev = 0, least = 0, greatest = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return PICHOL_ERR_CUDA;
         if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
             cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, greatest) != cudaSuccess)
             return PICHOL_ERR_CUDA;

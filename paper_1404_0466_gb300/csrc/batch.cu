@@ -85,6 +85,7 @@ pichol_status pichol_batch_create(const pichol_config* cfgs, int32_t nprob, int3
             delete b;
             return st;
         }
+        c->diag_exclusive = 0;     // other problems' work fills the SMs instead
         b->ctx.push_back(c);
         b->off.push_back(off);
         size_t need = 0;

@@ -86,15 +86,16 @@ __device__ __forceinline__ void take_pivot(double (*A)[TB + 1], double* yinv, in
     yinv[j] = y;
 }
 
-// One CTA per problem: factor the 64 x 64 diagonal tile in double precision,
-// right-looking inside the tile.  Column j: scale it by 1 / L_jj, then the
-// rank-1 update of the trailing triangle {(i, c) : j < c <= i}.  The lower
-// triangle is listed column by column in `tab`, so each trailing triangle is
-// a suffix of the list that the 256 threads share evenly; its first element
-// is (j+1, j+1), which thread 0 updates first and then turns into the next
-// pivot while the other threads are still updating.
-template <typename T>
-__global__ void __launch_bounds__(256)
+// One CTA of DNT threads per problem: factor the 64 x 64 diagonal tile in
+// double precision, right-looking inside the tile.  Column j: scale it by
+// 1 / L_jj, then the rank-1 update of the trailing triangle
+// {(i, c) : j < c <= i}.  The lower triangle is listed column by column in
+// `tab`, so each trailing triangle is a suffix of the list that the threads
+// share evenly; its first element is (j+1, j+1), which thread 0 updates first
+// and then turns into the next pivot while the other threads are still
+// updating (with PIVOT_ALONE, thread 0 takes that element only).
+template <typename T, int DNT, bool PIVOT_ALONE>
+__global__ void __launch_bounds__(DNT)
 k_chol_diag(T* __restrict__ F, int64_t ntiles, int J, int64_t d, ProbMap pm, DevStatus* st)
 {
     constexpr int NTRI = TB * (TB + 1) / 2;
@@ -104,7 +105,7 @@ k_chol_diag(T* __restrict__ F, int64_t ntiles, int J, int64_t d, ProbMap pm, Dev
     const int pr = blockIdx.x, tid = threadIdx.x;
     if (prob_dead(pm, pr)) return;
     T* tile = F + ((int64_t)pr * ntiles + tile_index(J, J)) * TILE_ELEMS;
-    for (int e = tid; e < TILE_ELEMS; e += 256) {
+    for (int e = tid; e < TILE_ELEMS; e += DNT) {
         const int r = e / TB, c = e % TB;
         A[r][c] = (c <= r) ? (double)tile[e] : 0.0;
         // column c starts at c TB - c (c - 1) / 2 in the list
@@ -114,18 +115,31 @@ k_chol_diag(T* __restrict__ F, int64_t ntiles, int J, int64_t d, ProbMap pm, Dev
     if (tid == 0) take_pivot(A, yinv, 0, J, d, pm, pr, st);
     for (int j = 0; j < TB - 1; ++j) {
         __syncthreads();                                  // pivot j and column j final
-        if (tid < TB - 1 - j) A[j + 1 + tid][j] *= yinv[j];
+        for (int i = j + 1 + tid; i < TB; i += DNT) A[i][j] *= yinv[j];
         __syncthreads();
         const int e0 = (j + 1) * TB - (j + 1) * j / 2;
-        for (int e = e0 + tid; e < NTRI; e += 256) {
-            const int ic = tab[e];
-            const int i = ic >> 8, c = ic & 255;
-            A[i][c] = fma(-A[i][j], A[c][j], A[i][c]);
-            if (e == e0) take_pivot(A, yinv, j + 1, J, d, pm, pr, st);
+        if (PIVOT_ALONE) {
+            if (tid == 0) {
+                A[j + 1][j + 1] = fma(-A[j + 1][j], A[j + 1][j], A[j + 1][j + 1]);
+                take_pivot(A, yinv, j + 1, J, d, pm, pr, st);
+            } else {
+                for (int e = e0 + tid; e < NTRI; e += DNT - 1) {
+                    const int ic = tab[e];
+                    const int i = ic >> 8, c = ic & 255;
+                    A[i][c] = fma(-A[i][j], A[c][j], A[i][c]);
+                }
+            }
+        } else {
+            for (int e = e0 + tid; e < NTRI; e += DNT) {
+                const int ic = tab[e];
+                const int i = ic >> 8, c = ic & 255;
+                A[i][c] = fma(-A[i][j], A[c][j], A[i][c]);
+                if (e == e0) take_pivot(A, yinv, j + 1, J, d, pm, pr, st);
+            }
         }
     }
     __syncthreads();
-    for (int e = tid; e < TILE_ELEMS; e += 256) {
+    for (int e = tid; e < TILE_ELEMS; e += DNT) {
         const int r = e / TB, c = e % TB;
         tile[e] = (c <= r) ? (T)A[r][c] : T(0);
     }
@@ -309,11 +323,19 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
     T* F = (T*)ctx->F;
     constexpr int UNT = UpdateThreads<T>::value;
     constexpr int UCH = 4;                       // output tiles per CTA in the bulk updates
+    constexpr int DIAG_NT = 512;                 // threads of the diagonal-tile kernel
+    // The diagonal tiles are the critical path.  When the k g problems fit on
+    // half the SMs, each diagonal CTA asks for enough shared memory that no
+    // trailing-update CTA can share its SM.
+    constexpr int DIAG_RESERVE = 160 * 1024;
     const size_t sm_mm = 3 * sizeof(T) * TB * (TB + Vec16<T>::N);
     static bool attr_done = false;
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(k_chol_update<T, UNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sm_mm);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_chol_diag<T, DIAG_NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     DIAG_RESERVE);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
@@ -332,6 +354,7 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
     // the call stays capturable.
     cudaStream_t sh = ctx->aux ? ctx->aux : s;
     const bool split = sh != s;
+    const size_t diag_smem = (ctx->diag_exclusive && 2 * nprob <= ctx->nsm) ? DIAG_RESERVE : 0;
     cudaError_t e;
     if (split) {
         if ((e = cudaEventRecord(ctx->ev_fork, s)) != cudaSuccess) return e;
@@ -341,7 +364,7 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
     for (int J = 0; J < ctx->nt; ++J) {
         {
             StageScope sc_(ctx, ST_CHOL_DIAG, sh);
-            k_chol_diag<T><<<nprob, 256, 0, sh>>>(F, ctx->ntiles, J, c.d, pm, ctx->status);
+            k_chol_diag<T, DIAG_NT, true><<<nprob, DIAG_NT, diag_smem, sh>>>(F, ctx->ntiles, J, c.d, pm, ctx->status);
         }
         ctx->launches++;
         const int m = ctx->nt - 1 - J;

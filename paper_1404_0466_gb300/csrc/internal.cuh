@@ -160,6 +160,8 @@ struct pichol_ctx {
     // trailing update runs on the caller's stream (created with the workspace)
     cudaStream_t aux;
     cudaEvent_t ev_fork, ev_panel, ev_upd, ev_join;
+    int nsm;             // SMs of the device the workspace lives on
+    int diag_exclusive;  // the diagonal-tile CTAs may reserve whole SMs (off in batches)
 
     // optional per-stage timing: pairs of events recorded around launches
     int timing;

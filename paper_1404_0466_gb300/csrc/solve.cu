@@ -620,6 +620,29 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
     e = (a - (s - bb)) + (b - bb);
 }
 
+// n consecutive fp32 values of shared memory in 16- or 8-byte loads when n
+// allows (the row start is then aligned to match).
+template <int N>
+__device__ __forceinline__ void load_row(float (&dst)[N], const float* src)
+{
+    if constexpr (N % 4 == 0) {
+#pragma unroll
+        for (int o = 0; o < N; o += 4) {
+            const float4 t = *reinterpret_cast<const float4*>(src + o);
+            dst[o] = t.x; dst[o + 1] = t.y; dst[o + 2] = t.z; dst[o + 3] = t.w;
+        }
+    } else if constexpr (N % 2 == 0) {
+#pragma unroll
+        for (int o = 0; o < N; o += 2) {
+            const float2 t = *reinterpret_cast<const float2*>(src + o);
+            dst[o] = t.x; dst[o + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int o = 0; o < N; ++o) dst[o] = src[o];
+    }
+}
+
 template <int LG, int CB, int NP, int PASS>
 __global__ void __launch_bounds__(256, 2)
 k_resid(ResidArgs a, const __grid_constant__ CUtensorMap tmap)
@@ -769,8 +792,10 @@ k_resid(ResidArgs a, const __grid_constant__ CUtensorMap tmap)
                     float lv = v4[0][e];
 #pragma unroll
                     for (int m = 1; m < NP; ++m) lv = fmaf(w[l][m], v4[m][e], lv);
-                    const float* zh = zhb + (l * HT + kk) * CBP;
-                    const float* zl = zlb + (l * HT + kk) * CBP;
+                    // the staged values of row kk (rows are 8- or 16-byte aligned when CBP is even)
+                    float zh[CBP], zl[CBP];
+                    load_row<CBP>(zh, zhb + (l * HT + kk) * CBP);
+                    if (PASS == 1) load_row<CBP>(zl, zlb + (l * HT + kk) * CBP);
 #pragma unroll
                     for (int o = 0; o < CBP; ++o) {
                         const float pp = lv * zh[o];

@@ -42,6 +42,10 @@ WORKLOADS = {
     "mixed_ecc": dict(gen="mixed_ecc", cfg="MIXED_ECC", mode="mixed", basis="cheb_log", refine=1),
     # n = 2048, d = 256, c = 10, k = 5, g = 4, r = 2, q = 31, double precision
     "fp64_small": dict(gen="fp64_small", cfg="FP64_SMALL", mode="fp64", basis="mono", refine=0),
+    # the mixed case with its refinement step taken against H_f + lambda I (the interpolated
+    # factor as a preconditioner; moves the result toward exact CV; not the paper's method)
+    "mixed_ecc_precond": dict(gen="mixed_ecc", cfg="MIXED_ECC", mode="mixed", basis="cheb_log", refine=1,
+                              refine_target="exact"),
     # 64 problems, d ~ U[128, 1536], n = 8 d, c in {1, 10}, k = 5, g = 5, r = 3, q = 51, one CUDA graph
     "batched_uneven": dict(gen="batched_uneven", cfg=None, mode="mixed", basis="cheb_log", refine=1),
 }
@@ -82,8 +86,10 @@ def workload(name):
 
 
 def describe(name, w, cfg, refine):
+    target = w.get("refine_target", "interpolated")
     return (f"{name}: n={cfg['n']} d={cfg['d']} c={cfg['c']} k={cfg['k']} g={cfg['g']} r={cfg['r']} "
-            f"q={cfg['q']} basis={w['basis']} mode={w['mode']} refine={refine}")
+            f"q={cfg['q']} basis={w['basis']} mode={w['mode']} refine={refine}"
+            + (f" refine_target={target}" if refine and target != "interpolated" else ""))
 
 
 # ---------------------------------------------------------------------------
@@ -233,8 +239,10 @@ def oracle_sample(prob, cfg, w, E_gpu, t_star):
     idx = sorted(set([0, q // 4, q // 2, (3 * q) // 4, q - 1] + ([t_star] if t_star >= 0 else [])))
     tm = {}
     t0 = time.perf_counter()
+    # the oracle follows the same refinement when it changes the result (exact-system target)
+    pre = w["refine"] if w.get("refine_target") == "exact" else 0
     ref = oracle.cv(prob.X, prob.Y, k=cfg["k"], g=cfg["g"], r=cfg["r"], q=q, lo=cfg["lo"], hi=cfg["hi"],
-                    basis=w["basis"], folds=[0], lam_idx=idx, timings=tm)
+                    basis=w["basis"], folds=[0], lam_idx=idx, timings=tm, precond_steps=pre)
     wall = time.perf_counter() - t0
     Eo = ref.E[0, idx]
     Eg = E_gpu[0, idx]
@@ -266,10 +274,12 @@ def run_reference(args):
     k, q = cfg["k"], cfg["q"]
     refine = w["refine"] if args.refine is None else args.refine
 
+    pre = refine if w.get("refine_target") == "exact" else 0
+
     def step(i):
         f = i % k
         oracle.cv(prob.X, prob.Y, k=k, g=cfg["g"], r=cfg["r"], q=q, lo=cfg["lo"], hi=cfg["hi"],
-                  basis=w["basis"], folds=[f])
+                  basis=w["basis"], folds=[f], precond_steps=pre)
 
     for i in range(args.warmup):
         step(i)
@@ -489,7 +499,8 @@ def run_own(args):
     X = Xh.to(dev)
     Y = Yh.to(dev)
     params = dict(n=cfg["n"], d=cfg["d"], c=cfg["c"], k=k, g=cfg["g"], r=cfg["r"], q=q, lam_lo=cfg["lo"],
-                  lam_hi=cfg["hi"], basis=w["basis"], mode=w["mode"], refine_steps=refine)
+                  lam_hi=cfg["hi"], basis=w["basis"], mode=w["mode"], refine_steps=refine,
+                  refine_target=w.get("refine_target", "interpolated"))
     # the piCholesky context needs factor slots for the g samples only
     ctx = binding.Context(exact_batch=cfg["g"], **params)
     out = ctx._outputs(False)
@@ -575,7 +586,7 @@ def run_own(args):
     if not args.no_exact and rank == 0:
         del ctx
         torch.cuda.empty_cache()
-        ctxe = binding.Context(**params)
+        ctxe = binding.Context(**dict(params, refine_steps=0, refine_target="interpolated"))
         oute = ctxe._outputs(False)
         ctxe.hessian(X, Y)
         ctxe.eval_holdout_exact(out=oute)
@@ -595,6 +606,10 @@ def run_own(args):
                  "min_E_exact": float(np.mean(Ex, axis=0)[tx]),
                  "min_E_pichol": float(np.mean(E, axis=0)[t_star]) if t_star >= 0 else None,
                  "selected_lambda_equal": tx == t_star}
+        fin = np.isfinite(E)
+        exact["max_rel_E_vs_exact"] = float(np.max(np.abs(E[fin] - Ex[fin]) / Ex[fin])) if fin.any() else None
+        exact["rel_min_E_vs_exact"] = (abs(exact["min_E_pichol"] - exact["min_E_exact"]) / exact["min_E_exact"]
+                                       if exact["min_E_pichol"] is not None else None)
         ctxe.close()
 
     if rank != 0:

@@ -93,8 +93,16 @@ typedef struct {
     int32_t refine_steps; /* mixed mode: refinement steps after each solve (0..4) */
     int32_t gram_passes;  /* mixed mode: 1 = plain TF32 products, 3 = split TF32 (hi*hi + hi*lo + lo*hi) */
     int32_t exact_batch;  /* lambdas factored per batch by pichol_eval_holdout_exact (0 = all q) */
-    int32_t reserved[6];  /* must be zero */
+    int32_t refine_target;/* mixed mode, which system each refinement step takes its residual from:
+                             PICHOL_REFINE_INTERPOLATED (default): B - L~ (L~^T W), in double-float,
+                             so the result stays the interpolated solution of Algorithm 1;
+                             PICHOL_REFINE_EXACT: B - (H_f + lambda I) W from two tensor-core
+                             products (split TF32), so the interpolated factor acts as a
+                             preconditioner and the result moves toward exact CV (not in the paper) */
+    int32_t reserved[5];  /* must be zero */
 } pichol_config;
+
+enum { PICHOL_REFINE_INTERPOLATED = 0, PICHOL_REFINE_EXACT = 1 };
 
 /* First device error, as latched by the kernels. */
 typedef struct {
@@ -109,8 +117,10 @@ typedef struct {
 typedef struct pichol_ctx pichol_ctx;
 
 /* Fills *cfg with defaults: lam_lo = 1e-3, lam_hi = 1e1, scale_by_trace = 1,
- * basis MONO, mode FP64, refine_steps 0, gram_passes 3, exact_batch 0; the
- * sizes are left zero. */
+ * basis MONO, mode FP64, refine_steps 0, gram_passes 3, exact_batch 0,
+ * refine_target PICHOL_REFINE_INTERPOLATED; the sizes are left zero.
+ * refine_target PICHOL_REFINE_EXACT needs mode MIXED (else
+ * PICHOL_ERR_UNSUPPORTED from pichol_create). */
 PICHOL_API void pichol_config_default(pichol_config* cfg);
 
 /* Validates cfg and creates a context (host memory only).  *out is NULL on

@@ -333,9 +333,15 @@ class CVResult:
 
 def cv(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e1,
        basis: str = BASIS_MONO, exact: bool = False, scale_by_trace: bool = True,
-       folds=None, lam_idx=None, keep: bool = False, timings: dict | None = None) -> CVResult:
+       folds=None, lam_idx=None, keep: bool = False, timings: dict | None = None,
+       precond_steps: int = 0) -> CVResult:
     """k-fold CV of ridge regression over q lambdas, piCholesky (default) or
     exact Cholesky at every lambda (``exact=True``, ``Chol`` of Sec. 6.2).
+
+    ``precond_steps`` > 0 (piCholesky only; not in the paper) follows each
+    interpolated solve with that many steps of iterative refinement against
+    the exact system: R = B_f - (H_f + lambda I) W, W <- W + (L~ L~^T)^{-1} R,
+    so the interpolated factor serves as a preconditioner.
 
     ``folds`` restricts the work to some folds and ``lam_idx`` to some grid
     indices (entries outside are NaN); the grid, the samples and the fit are
@@ -412,6 +418,9 @@ def cv(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e
                 tm["eval"] += _time.perf_counter() - _te
                 continue
             W = solve_factored(Lt, Bf)
+            for _ in range(precond_steps):
+                R = Bf - (Hf @ W + lam[t] * W)
+                W = W + solve_factored(Lt, R)
             E[f, t] = holdout_sse(Xv, Yv, W) / (nv * c)
             if keep:
                 res.W[(f, t)] = W

@@ -18,6 +18,7 @@ LIB_PATH = _PKG / "libpichol.so"
 
 PICHOL_MODE_FP64, PICHOL_MODE_MIXED = 0, 1
 PICHOL_BASIS_MONO, PICHOL_BASIS_CHEB_LOG = 0, 1
+REFINE_TARGETS = {"interpolated": 0, "exact": 1}
 STATUS = {0: "PICHOL_OK", 1: "PICHOL_ERR_INVALID_ARG", 2: "PICHOL_ERR_NOT_SPD", 3: "PICHOL_ERR_CUDA",
           4: "PICHOL_ERR_WORKSPACE", 5: "PICHOL_ERR_TIMEOUT", 6: "PICHOL_ERR_UNSUPPORTED", 7: "PICHOL_ERR_STATE"}
 
@@ -43,7 +44,7 @@ class Config(ctypes.Structure):
                 ("lam_lo", ctypes.c_double), ("lam_hi", ctypes.c_double),
                 ("scale_by_trace", ctypes.c_int32), ("basis", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("refine_steps", ctypes.c_int32), ("gram_passes", ctypes.c_int32),
-                ("exact_batch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("exact_batch", ctypes.c_int32), ("refine_target", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class Info(ctypes.Structure):
@@ -143,7 +144,7 @@ class Context:
     """One piCholesky cross-validation problem on the current CUDA device."""
 
     def __init__(self, *, n, d, c, k, g, r, q, lam_lo=1e-3, lam_hi=1e1, basis="mono", mode="fp64",
-                 refine_steps=0, gram_passes=3, exact_batch=0, scale_by_trace=True):
+                 refine_steps=0, gram_passes=3, exact_batch=0, scale_by_trace=True, refine_target="interpolated"):
         import torch
         L = lib()
         cfg = Config()
@@ -154,6 +155,7 @@ class Context:
         cfg.basis = {"mono": PICHOL_BASIS_MONO, "cheb_log": PICHOL_BASIS_CHEB_LOG}[basis]
         cfg.mode = {"fp64": PICHOL_MODE_FP64, "mixed": PICHOL_MODE_MIXED}[mode]
         cfg.refine_steps, cfg.gram_passes, cfg.exact_batch = refine_steps, gram_passes, exact_batch
+        cfg.refine_target = REFINE_TARGETS[refine_target]
         self.cfg = cfg
         self.dtype = torch.float64 if mode == "fp64" else torch.float32
         h = ctypes.c_void_p()
@@ -330,6 +332,7 @@ class Batch:
             cfg.basis = {"mono": PICHOL_BASIS_MONO, "cheb_log": PICHOL_BASIS_CHEB_LOG}[pr.get("basis", "mono")]
             cfg.mode = {"fp64": PICHOL_MODE_FP64, "mixed": PICHOL_MODE_MIXED}[pr.get("mode", "fp64")]
             cfg.refine_steps = pr.get("refine_steps", 0)
+            cfg.refine_target = REFINE_TARGETS[pr.get("refine_target", "interpolated")]
             cfg.exact_batch = pr.get("exact_batch", cfg.g)
         self.cfgs = cfgs
         self.n = n

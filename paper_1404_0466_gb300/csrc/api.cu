@@ -44,7 +44,8 @@ size_t plan(pichol_ctx* ctx, char* base)
     ctx->Dinv = take((size_t)(k * q * nt * TILE_ELEMS * eb));
     ctx->W = take((size_t)(k * q * dp * cc * eb));
     const bool refine = c.mode == PICHOL_MODE_MIXED && c.refine_steps > 0;
-    ctx->U = refine ? take((size_t)(2 * k * q * dp * cc * sizeof(float))) : nullptr;
+    const bool rexact = refine && c.refine_target == PICHOL_REFINE_EXACT;
+    ctx->U = (refine && !rexact) ? take((size_t)(2 * k * q * dp * cc * sizeof(float))) : nullptr;
     ctx->Rres = refine ? take((size_t)(k * q * dp * cc * eb)) : nullptr;
     if (c.mode == PICHOL_MODE_MIXED) {
         const int64_t qc = q * cc;
@@ -57,6 +58,9 @@ size_t plan(pichol_ctx* ctx, char* base)
         ctx->Wth = (float*)take((size_t)(k * qc * dp * 4));
         ctx->Wtl = (float*)take((size_t)(k * qc * dp * 4));
         ctx->U2 = (float*)take((size_t)(k * dp * ctx->ldu * 4));
+        ctx->Gah = rexact ? (float*)take((size_t)(dp * dp * 4)) : nullptr;
+        ctx->Gal = rexact ? (float*)take((size_t)(dp * dp * 4)) : nullptr;
+        ctx->U3 = rexact ? (float*)take((size_t)(k * dp * ctx->ldu * 4)) : nullptr;
     }
     ctx->gW = take((size_t)(3 * k * dp * cc * eb));
     ctx->gDinv = take((size_t)(k * nt * TILE_ELEMS * eb));
@@ -112,8 +116,11 @@ pichol_status pichol_create(const pichol_config* cfg, pichol_ctx** out)
     if (c.refine_steps < 0 || c.refine_steps > 4) return PICHOL_ERR_INVALID_ARG;
     if (c.gram_passes != 1 && c.gram_passes != 3) return PICHOL_ERR_INVALID_ARG;
     if (c.exact_batch < 0 || c.exact_batch > c.q) return PICHOL_ERR_INVALID_ARG;
-    for (int i = 0; i < 6; ++i)
+    if (c.refine_target != PICHOL_REFINE_INTERPOLATED && c.refine_target != PICHOL_REFINE_EXACT)
+        return PICHOL_ERR_INVALID_ARG;
+    for (int i = 0; i < 5; ++i)
         if (c.reserved[i] != 0) return PICHOL_ERR_INVALID_ARG;
+    if (c.refine_target == PICHOL_REFINE_EXACT && c.mode != PICHOL_MODE_MIXED) return PICHOL_ERR_UNSUPPORTED;
     // the interpolate-on-load solve keeps p coefficient planes and the
     // right-hand-side blocks of two lambdas in shared memory (227 KB per CTA)
     if (solve_smem_bytes(c.mode == PICHOL_MODE_FP64 ? 8 : 4, c.r + 1, c.c) > 227 * 1024)

@@ -347,6 +347,7 @@ static cudaError_t gram_impl(pichol_ctx* ctx, const T* X, const T* Y, cudaStream
         // mixed mode: G_j and Bv_j = X_j^T Y_j on tensor cores (split TF32 when gram_passes = 3)
         ctx->Yin = Y;
         e = launch_gram_tc(ctx, X, s);
+        if (e == cudaSuccess && ctx->Gah) e = launch_gall_split(ctx, s);
         if (e != cudaSuccess) return e;
     } else {
         {

@@ -138,6 +138,9 @@ struct pichol_ctx {
     float* Wth;          // k x (q c) x dp: W^T split
     float* Wtl;
     float* U2;           // k x dp x ldu: G_f W for every lambda
+    float* Gah;          // dp x dp: G_all = sum_j G_j split (exact-system refinement only)
+    float* Gal;
+    float* U3;           // k x dp x ldu: G_all W for every lambda (exact-system refinement only)
     // gradient in log(lambda) at one lambda (pichol_holdout_grad)
     void* gW;            // 3 x k x dp x c: W, U, V
     void* gDinv;         // k x nt x TB^2
@@ -212,5 +215,7 @@ int64_t tc_kpad(const pichol_ctx* ctx);
 cudaError_t launch_gram_tc(pichol_ctx* ctx, const float* X, cudaStream_t s);
 cudaError_t launch_grad(pichol_ctx* ctx, double log_lam, double* E_out, double* dE_out, cudaStream_t s);
 cudaError_t launch_score_tc(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s);
+cudaError_t launch_gall_split(pichol_ctx* ctx, cudaStream_t s);
+cudaError_t launch_resid_exact(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s);
 
 }  // namespace pichol

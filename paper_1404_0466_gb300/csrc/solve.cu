@@ -19,6 +19,7 @@
 #include "internal.cuh"
 #include "tma.cuh"
 
+#include <algorithm>
 #include <cfloat>
 #include <cstring>
 
@@ -161,11 +162,18 @@ struct SolveCfg {
     static constexpr int HPB = (TB / 2) * TB * ESZ;       // bytes of a half plane (32 x 64)
     static constexpr int STAGE_BYTES = NPS * HPB;
     static constexpr int DINV_BYTES = LG * TB * TB * ESZ; // the diagonal inverses reuse the ring
-    static constexpr int PLANE_BYTES = (2 * STAGE_BYTES > DINV_BYTES) ? 2 * STAGE_BYTES : DINV_BYTES;
     static constexpr int ZS_BYTES = 2 * LG * (TB / 2) * CBP * ESZ;     // staged solved half blocks
     static constexpr int R_BYTES = 4 * LG * TB * CBP * ESZ;            // 4 reduction slots
     static constexpr bool TMA = std::is_same<T, float>::value;          // fp32 planes arrive by TMA
-    static constexpr int SMEM = PLANE_BYTES + ZS_BYTES + R_BYTES + (TMA ? 1024 : 0);   // + alignment
+    // Two stages (one half tile in flight while one is read); a third stage
+    // measured slower on the mixed case.  In fp32 the reduction slots live in
+    // the ring too, after the inverses (both are used only after the k loop).
+    static constexpr int NSTAGE = 2;
+    static constexpr int RING_LOOP = NSTAGE * STAGE_BYTES;
+    static constexpr int RING_AFTER = DINV_BYTES + (TMA ? R_BYTES : 0);
+    static constexpr int PLANE_BYTES = RING_LOOP > RING_AFTER ? RING_LOOP : RING_AFTER;
+    static constexpr int R_OFFSET = TMA ? DINV_BYTES : PLANE_BYTES + ZS_BYTES;
+    static constexpr int SMEM = PLANE_BYTES + ZS_BYTES + (TMA ? 1024 : R_BYTES);   // fp32: + alignment
     static constexpr int ZPER = (LG * (TB / 2) * CB + 255) / 256;      // staged values per thread
 };
 
@@ -251,11 +259,12 @@ k_solve(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = smem_raw;
     if constexpr (TMA) smem += (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;   // 128-byte swizzle atoms
-    __shared__ uint64_t tbar[2];
+    __shared__ uint64_t tbar[3];
     uint32_t phase = 0;                 // bit s: parity of the next completion of stage s
     unsigned char* planes = smem;
+    constexpr int NSTAGE = C::NSTAGE;
     T* Zs = reinterpret_cast<T*>(smem + C::PLANE_BYTES);              // [2][LG][32][CBP]
-    T* Rs = reinterpret_cast<T*>(smem + C::PLANE_BYTES + C::ZS_BYTES); // [4][LG][64][CBP]
+    T* Rs = reinterpret_cast<T*>(smem + C::R_OFFSET);                 // [4][LG][64][CBP]
 
     const int f = blockIdx.y, tid = threadIdx.x;
     const int rp = tid % RPT, kq = tid / RPT;
@@ -282,10 +291,9 @@ k_solve(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
     T* zb = (T*)a.zbuf;
     T* out = (T*)a.out;
     for (int e = tid; e < 2 * LG * HT * CBP; e += 256) Zs[e] = T(0);
-    for (int e = tid; e < 4 * LG * TB * CBP; e += 256) Rs[e] = T(0);
+    // (every reduction slot is written before it is read, so Rs needs no clearing)
     if (TMA && tid == 0) {
-        mbar_init(&tbar[0], 1);
-        mbar_init(&tbar[1], 1);
+        for (int st = 0; st < NSTAGE; ++st) mbar_init(&tbar[st], 1);
         mbar_init_fence();
     }
     __syncthreads();
@@ -337,13 +345,16 @@ k_solve(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
             cp_async_commit();
         }
     };
-    // a bounded copy wait ran out: latch, wait (bounded) for this CTA's copies
-    // still in flight, and let every thread return
-    auto give_up = [&](int stage, bool prefetched) {
+    // a bounded copy wait ran out at half tile `it`: latch, wait (bounded) for
+    // this CTA's copies still in flight (half tiles it .. it + NSTAGE - 2), and
+    // let every thread return
+    auto give_up = [&](int it, int nit) {
         if (tid == 0) {
             latch_error(a.st, PICHOL_ERR_TIMEOUT, f, (int)blockIdx.x, -1);
-            mbar_wait(&tbar[stage], (phase >> stage) & 1u);
-            if (prefetched) mbar_wait(&tbar[stage ^ 1], (phase >> (stage ^ 1)) & 1u);
+            for (int u = it; u < it + NSTAGE - 1 && u < nit; ++u) {
+                const int st = u % NSTAGE;
+                mbar_wait(&tbar[st], (phase >> st) & 1u);
+            }
         }
     };
     auto evalv = [&](const T* v, int l) -> T {
@@ -387,13 +398,16 @@ k_solve(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
                     if (zg[u] >= 0) zsb[zs_off[u]] = zr[u];
             };
             if (nit > 0) {
-                issue(back ? tj(0) : i, back ? i : tj(0), 0, !back, 0);
+                // TMA: NSTAGE - 1 half tiles in flight ahead of the one being read
+                const int pre = TMA ? NSTAGE - 1 : 1;
+                for (int u = 0; u < pre && u < nit; ++u)
+                    issue(back ? tj(u) : i, back ? i : tj(u), u & 1, !back, u);
                 load_z(0);
                 store_z(0);
             }
 #pragma unroll 1
             for (int it = 0; it < nit; ++it) {
-                const int stage = it & 1;
+                const int stage = TMA ? it % NSTAGE : it & 1;
                 bool ok = true;
                 if constexpr (TMA) {
                     // one barrier per half tile: the next stage is refilled after it, when
@@ -409,17 +423,17 @@ k_solve(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
                     }
                 }
                 if (__syncthreads_or(!ok)) {
-                    give_up(stage, false);
+                    give_up(it, nit);
                     return;
                 }
                 if constexpr (TMA) {
                     phase ^= 1u << stage;
-                    if (it + 1 < nit)
-                        issue(back ? tj(it + 1) : i, back ? i : tj(it + 1), (it + 1) & 1, !back, (it + 1) & 1);
+                    const int nx = it + NSTAGE - 1;
+                    if (nx < nit) issue(back ? tj(nx) : i, back ? i : tj(nx), nx & 1, !back, nx % NSTAGE);
                 }
                 if (it + 1 < nit) load_z(it + 1);
                 const unsigned char* pl = planes + stage * C::STAGE_BYTES;
-                const T* zs = Zs + stage * LG * HT * CBP;
+                const T* zs = Zs + (it & 1) * LG * HT * CBP;      // the solved blocks are double-buffered
                 if (!back) {
                     // row-owner: rows rp + RPT hh of tile (i, j), local k in [KW kq, KW kq + KW)
 #pragma unroll
@@ -1032,10 +1046,21 @@ size_t solve_smem_bytes(int eb, int p, int64_t c)
 {
     const int LG = 2, cb = pick_cb(c), vn = 16 / eb;
     const int cbp = (cb + vn - 1) / vn * vn;
-    const int nps = p > LG ? p : LG;   // interpolated (p planes) or exact (LG planes)
-    const size_t hpb = (size_t)(TB / 2) * TB * eb;
-    const size_t ring = 2 * nps * hpb > (size_t)LG * TB * TB * eb ? 2 * nps * hpb : (size_t)LG * TB * TB * eb;
-    return ring + (size_t)2 * LG * (TB / 2) * cbp * eb + (size_t)4 * LG * TB * cbp * eb + (eb == 4 ? 1024 : 0);
+    const size_t zs = (size_t)2 * LG * (TB / 2) * cbp * eb, rb = (size_t)4 * LG * TB * cbp * eb;
+    const size_t dinv = (size_t)LG * TB * TB * eb, hpb = (size_t)(TB / 2) * TB * eb;
+    size_t most = 0;
+    for (int nps : {p, LG}) {          // interpolated (p planes) and exact (LG planes)
+        const size_t stage = (size_t)nps * hpb;
+        if (eb == 4) {
+            const size_t loop = 2 * stage;
+            const size_t ring = loop > dinv + rb ? loop : dinv + rb;
+            most = std::max(most, ring + zs + 1024);
+        } else {
+            const size_t ring = 2 * stage > dinv ? 2 * stage : dinv;
+            most = std::max(most, ring + zs + rb);
+        }
+    }
+    return most;
 }
 
 // The map the fp32 solve and residual stage coefficient (or factor) planes
@@ -1236,27 +1261,32 @@ static cudaError_t eval_impl(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s
 
     if constexpr (std::is_same<T, float>::value && !EXACT) {
         for (int it = 0; it < cf.refine_steps; ++it) {
-            ResidArgs ra;
-            ra.theta = (const float*)ctx->Theta;
-            ra.W = (const float*)ctx->W;
-            ra.uhi = (const float*)ctx->U;
-            ra.ulo = (const float*)ctx->U + (int64_t)cf.k * cf.q * ctx->dp * cf.c;
-            ra.ohi = (float*)ctx->U;
-            ra.olo = (float*)ctx->U + (int64_t)cf.k * cf.q * ctx->dp * cf.c;
-            ra.B = (const float*)ctx->Btr;
-            ra.R = (float*)ctx->Rres;
-            ra.phi = ctx->phi;
-            ra.p = ctx->p;
-            ra.nt = ctx->nt;
-            ra.q = cf.q;
-            ra.t0 = t0;
-            ra.tcount = tcount;
-            ra.ntiles = ctx->ntiles;
-            ra.dp = ctx->dp;
-            ra.c = cf.c;
-            ra.st = ctx->status;
-            if ((e = resid_dispatch<0>(ctx, ra, s)) != cudaSuccess) return e;
-            if ((e = resid_dispatch<1>(ctx, ra, s)) != cudaSuccess) return e;
+            // the residual of the system this step refines (see refine_target)
+            if (cf.refine_target == PICHOL_REFINE_EXACT) {
+                if ((e = launch_resid_exact(ctx, t0, tcount, s)) != cudaSuccess) return e;
+            } else {
+                ResidArgs ra;
+                ra.theta = (const float*)ctx->Theta;
+                ra.W = (const float*)ctx->W;
+                ra.uhi = (const float*)ctx->U;
+                ra.ulo = (const float*)ctx->U + (int64_t)cf.k * cf.q * ctx->dp * cf.c;
+                ra.ohi = (float*)ctx->U;
+                ra.olo = (float*)ctx->U + (int64_t)cf.k * cf.q * ctx->dp * cf.c;
+                ra.B = (const float*)ctx->Btr;
+                ra.R = (float*)ctx->Rres;
+                ra.phi = ctx->phi;
+                ra.p = ctx->p;
+                ra.nt = ctx->nt;
+                ra.q = cf.q;
+                ra.t0 = t0;
+                ra.tcount = tcount;
+                ra.ntiles = ctx->ntiles;
+                ra.dp = ctx->dp;
+                ra.c = cf.c;
+                ra.st = ctx->status;
+                if ((e = resid_dispatch<0>(ctx, ra, s)) != cudaSuccess) return e;
+                if ((e = resid_dispatch<1>(ctx, ra, s)) != cudaSuccess) return e;
+            }
             SolveArgs sc = sa;
             sc.rhs = ctx->Rres;
             sc.rhs_per_system = 1;

@@ -542,6 +542,109 @@ cudaError_t launch_gram_tc(pichol_ctx* ctx, const float* X, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// G_all = sum_j G_j (the fp32 blocks summed in double, in increasing j),
+// rounded to fp32 and split into a TF32 part and an fp32 remainder for the
+// products with W of the exact-system refinement.
+__global__ void __launch_bounds__(256)
+k_gall_split(const float* __restrict__ G, int k, int64_t n, float* __restrict__ hi, float* __restrict__ lo)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int j = 0; j < k; ++j) v += (double)G[(int64_t)j * n + e];
+        const float vf = (float)v;
+        const float h = tc::tf32_round(vf);
+        hi[e] = h;
+        lo[e] = vf - h;
+    }
+}
+
+cudaError_t launch_gall_split(pichol_ctx* ctx, cudaStream_t s)
+{
+    const int64_t n = ctx->dp * ctx->dp;
+    {
+        StageScope sc_(ctx, ST_MISC, s);
+        k_gall_split<<<1216, 256, 0, s>>>((const float*)ctx->G, ctx->cfg.k, n, ctx->Gah, ctx->Gal);
+    }
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
+// Residual of the exact shifted system for every (fold f, lambda t) of the batch:
+//   R = B_f - lambda_t W - (G_all W - G_f W)     (H_f = G_all - G_f),
+// combined in double from the two split-TF32 products.
+__global__ void __launch_bounds__(256)
+k_resid_exact(const float* __restrict__ U2, const float* __restrict__ U3, int64_t ldu, const float* __restrict__ W,
+              const float* __restrict__ B, const double* __restrict__ lam, int q, int t0, int tcount, int64_t dp,
+              int64_t c, float* __restrict__ R)
+{
+    const int f = blockIdx.z, t = t0 + blockIdx.y;
+    const int64_t len = dp * c;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / c, o = e % c;
+        const int64_t u = ((int64_t)f * dp + i) * ldu + (int64_t)t * c + o;
+        const int64_t w = ((int64_t)f * q + t) * len + e;
+        const double hw = (double)U3[u] - (double)U2[u];
+        R[w] = (float)((double)B[(int64_t)f * len + e] - lam[t] * (double)W[w] - hw);
+    }
+}
+
+cudaError_t launch_resid_exact(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s)
+{
+    const pichol_config& c = ctx->cfg;
+    const int64_t dp = ctx->dp, qc = (int64_t)c.q * c.c;
+    {
+        StageScope sc_(ctx, ST_RESID, s);
+        k_split_wt<<<dim3((unsigned)((dp + 255) / 256), tcount, c.k), 256, 0, s>>>((const float*)ctx->W, c.q, t0, dp,
+                                                                                  c.c, ctx->Wth, ctx->Wtl);
+    }
+    ctx->launches++;
+    CUtensorMap fh, fl, ah, al, bh, bl;
+    if (!make_map(&fh, ctx->Gh, (uint64_t)dp, (uint64_t)(c.k * dp), (uint64_t)dp) ||
+        !make_map(&fl, ctx->Gl, (uint64_t)dp, (uint64_t)(c.k * dp), (uint64_t)dp) ||
+        !make_map(&ah, ctx->Gah, (uint64_t)dp, (uint64_t)dp, (uint64_t)dp) ||
+        !make_map(&al, ctx->Gal, (uint64_t)dp, (uint64_t)dp, (uint64_t)dp) ||
+        !make_map(&bh, ctx->Wth, (uint64_t)dp, (uint64_t)(c.k * qc), (uint64_t)dp) ||
+        !make_map(&bl, ctx->Wtl, (uint64_t)dp, (uint64_t)(c.k * qc), (uint64_t)dp))
+        return cudaErrorInvalidValue;
+    cudaError_t e = gemm_attr();
+    if (e != cudaSuccess) return e;
+    GemmArgs ga;
+    memset(&ga, 0, sizeof(ga));
+    ga.mode = GEMM_PLAIN;
+    ga.passes = 3;
+    ga.a_rows_fold = (int)dp;
+    ga.b_rows_fold = (int)qc;
+    ga.b_row_off = t0 * (int)c.c;
+    ga.c_col_off = t0 * (int)c.c;
+    ga.K = (int)dp;
+    ga.C = ctx->U2;
+    ga.ldc = ctx->ldu;
+    ga.M = dp;
+    ga.N = (int64_t)tcount * c.c;
+    ga.c_fold_stride = dp * ctx->ldu;
+    ga.st = ctx->status;
+    const unsigned mt = (unsigned)((dp + tc::BM - 1) / tc::BM), nt = (unsigned)((ga.N + tc::BN - 1) / tc::BN);
+    {
+        StageScope sc_(ctx, ST_RESID, s);
+        k_tc_gemm<<<dim3(mt * nt, c.k), tc::THREADS, tc::SMEM_BYTES, s>>>(fh, fl, bh, bl, ga);   // G_f W
+    }
+    GemmArgs gb = ga;
+    gb.a_rows_fold = 0;                       // one A for every fold
+    gb.C = ctx->U3;
+    {
+        StageScope sc_(ctx, ST_RESID, s);
+        k_tc_gemm<<<dim3(mt * nt, c.k), tc::THREADS, tc::SMEM_BYTES, s>>>(ah, al, bh, bl, gb);   // G_all W
+    }
+    {
+        StageScope sc_(ctx, ST_RESID, s);
+        k_resid_exact<<<dim3((unsigned)((dp * c.c + 255) / 256), tcount, c.k), 256, 0, s>>>(
+            ctx->U2, ctx->U3, ctx->ldu, (const float*)ctx->W, (const float*)ctx->Btr, ctx->lam, c.q, t0, tcount, dp,
+            c.c, (float*)ctx->Rres);
+    }
+    ctx->launches += 3;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_score_tc(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s)
 {
     const pichol_config& c = ctx->cfg;

@@ -58,6 +58,7 @@ def test_defaults(L):
 @pytest.mark.parametrize("bad", [
     dict(k=1), dict(k=65), dict(n=3, k=5), dict(d=0), dict(d=16385), dict(c=0), dict(c=33),
     dict(q=0), dict(q=4097), dict(r=6), dict(r=-1), dict(g=2, r=2), dict(g=40, q=50), dict(g=8, q=5),
+    dict(refine_target=2), dict(refine_target=-1),
     dict(lam_lo=0.0), dict(lam_lo=2.0, lam_hi=1.0), dict(basis=7), dict(mode=5),
     dict(refine_steps=9), dict(gram_passes=2), dict(exact_batch=99), dict(scale_by_trace=2),
 ])
@@ -104,3 +105,11 @@ def test_workspace_grows_with_exact_batch(L):
 def test_status_strings(L):
     assert L.pichol_status_string(0) == b"ok"
     assert b"positive definite" in L.pichol_status_string(2)
+
+
+def test_exact_system_refinement_needs_mixed_mode(L):
+    rc, h = _create(L, _cfg(L, refine_target=binding.REFINE_TARGETS["exact"], refine_steps=1))
+    assert rc == 6 and not h.value        # PICHOL_ERR_UNSUPPORTED in FP64 mode
+    rc, h = _create(L, _cfg(L, refine_target=1, refine_steps=1, mode=binding.PICHOL_MODE_MIXED))
+    assert rc == 0
+    L.pichol_destroy(h)

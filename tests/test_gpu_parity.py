@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
+import tolerances
 from paper_1404_0466_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -209,6 +210,27 @@ def test_mixed_holdout_and_selection(torch_mod, mixed_small, refine):
     rel = np.max(np.abs(E - ref.E) / ref.E)
     assert rel <= MIXED_TOL, rel
     _check_selected(int(out.t_star.cpu().item()), ref, MIXED_TOL)
+    assert ctx.info().code == 0
+
+
+def test_mixed_exact_system_refinement(torch_mod, mixed_small):
+    """One refinement step against H_f + lambda I (the interpolated factor as a
+    preconditioner): the oracle's refined errors, and closer to exact CV than
+    the interpolated solution itself."""
+    torch = torch_mod
+    prob, ref0 = mixed_small
+    kw = dict(k=5, g=6, r=3, q=101, basis="cheb_log")
+    ref = oracle.cv(prob.X, prob.Y, precond_steps=1, **kw)
+    ex = oracle.cv(prob.X, prob.Y, exact=True, **kw)
+    ctx = _ctx(prob, mode="mixed", refine_steps=1, refine_target="exact", **kw)
+    out = ctx.run(_dev(torch, prob.X, "mixed"), _dev(torch, prob.Y, "mixed"))
+    E = out.E.cpu().numpy()
+    tol = tolerances.mixed_tolerance(prob.X, ref.lam, 5)
+    assert np.all(np.abs(E - ref.E) <= tol * ref.E), float(np.max(np.abs(E - ref.E) / ref.E / tol))
+    _check_selected(int(out.t_star.cpu().item()), ref, float(tol.max()))
+    gap = np.max(np.abs(E - ex.E) / ex.E)
+    gap0 = np.max(np.abs(ref0.E - ex.E) / ex.E)
+    assert gap < gap0 / 3, (gap, gap0)
     assert ctx.info().code == 0
 
 

@@ -443,3 +443,48 @@ def test_exact_gradient_matches_eigen_closed_form():
         assert abs(gr.E[f] - np.sum(R * R) / nvc) <= 1e-10 * gr.E[f]
         ref = lam * (-2.0 / nvc) * np.sum((Xv.T @ R) * dW)
         assert abs(gr.dE[f] - ref) <= 1e-8 * abs(ref) + 1e-14
+
+
+# ---------------------------------------------------------------------------
+# refinement against the exact system with the interpolated factor as the
+# preconditioner (not in the paper)
+# ---------------------------------------------------------------------------
+
+def test_exact_system_refinement_step_is_the_preconditioned_iteration():
+    """One step maps the error e0 = w0 - w* to (I - M^{-1} A) e0 with
+    M = L~ L~^T and A = H_f + lambda I, both solved densely by numpy."""
+    prob = synth.spectral_gaussian(300, 20, 2, seed=71)
+    kw = dict(k=3, g=4, r=2, q=7, basis="cheb_log", folds=[1], lam_idx=[2], keep=True)
+    r0 = orc.cv(prob.X, prob.Y, **kw)
+    r1 = orc.cv(prob.X, prob.Y, precond_steps=1, **kw)
+    f, t = 1, 2
+    Hf, Bf = r0.H[f], r0.B[f]
+    A = Hf + r0.lam[t] * np.eye(Hf.shape[0])
+    lam_s = r0.lam[r0.sample_idx]
+    phi = orc.basis_values("cheb_log", [r0.lam[t]], lam_s, 3)[0]
+    Lt = orc.unvec_lower(orc.eval_poly(phi, r0.theta[f]), Hf.shape[0])
+    M = Lt @ Lt.T
+    w_star = np.linalg.solve(A, Bf)
+    e0 = r0.W[(f, t)] - w_star
+    e1 = r1.W[(f, t)] - w_star
+    np.testing.assert_allclose(e1, e0 - np.linalg.solve(M, A @ e0), rtol=1e-8, atol=1e-12 * np.abs(w_star).max())
+
+
+def test_exact_system_refinement_converges_to_exact_cv():
+    """Where the interpolated factor is a good preconditioner (the mixed
+    case's generator), each step shrinks the distance to exact CV."""
+    prob = synth.mixed_ecc(n=2048, d=96)
+    kw = dict(k=4, g=6, r=3, q=41, basis="cheb_log", folds=[0])
+    ex = orc.cv(prob.X, prob.Y, exact=True, **kw)
+    errs = [np.max(np.abs(orc.cv(prob.X, prob.Y, precond_steps=st, **kw).E[0] - ex.E[0]) / ex.E[0])
+            for st in (0, 1, 2, 3)]
+    assert errs[0] > 1e-4
+    assert errs[1] < errs[0] / 3 and errs[2] < errs[1] / 3 and errs[3] < errs[2] / 3, errs
+
+
+def test_exact_system_refinement_is_idle_when_every_lambda_is_a_node():
+    prob = synth.spectral_gaussian(200, 12, 2, seed=72)
+    kw = dict(k=4, g=5, r=4, q=5, basis="cheb_log")
+    ex = orc.cv(prob.X, prob.Y, exact=True, **kw)
+    r1 = orc.cv(prob.X, prob.Y, precond_steps=1, **kw)
+    np.testing.assert_allclose(r1.E, ex.E, rtol=1e-11)

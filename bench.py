@@ -146,7 +146,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # algorithmic work per stage (for the roofline of the dominant kernel)
 # ---------------------------------------------------------------------------
-def stage_work(cfg, mode, refine):
+def stage_work(cfg, mode, refine, target="interpolated"):
     """Algorithmic work per step of each timed stage: (kind, amount, bound, note).
     kind "flop": floating-point operations the method needs (not the ones the
     kernel happens to execute; an FMA counts 2); "byte": bytes that must cross
@@ -180,6 +180,10 @@ def stage_work(cfg, mode, refine):
         # product + TwoSum): 11 flops per multiply-add in L~^T W, 13 in L~ (u_hi + u_lo)
         # (FMA = 2), plus the factor built twice (2 (p-1) 2 D)
         "resid": ("flop", k * q * refine * (12 * d * d * c + 4 * (p - 1) * D), "alu"),
+    } | ({
+        # exact-system residual: G_f W and G_all W for every lambda, 2 d^2 c each (x3 split)
+        "resid": ("flop", k * q * refine * 2 * 2 * d * d * c * passes, tensor),
+    } if target == "exact" else {}) | {
         # per fold and lambda: <W, G W> as G_f W for all lambdas: 2 d^2 c q flops (x3 split)
         "score": ("flop", k * q * 2 * d * d * c * passes, tensor),
     }
@@ -216,9 +220,9 @@ def roofline_of(name, ms, launches, cfg, mode, refine, steps, peaks, work=None):
     return info
 
 
-def roofline(stage_ms, cfg, mode, refine, steps, peaks):
+def roofline(stage_ms, cfg, mode, refine, steps, peaks, work=None):
     name, (ms, launches) = max(stage_ms.items(), key=lambda kv: kv[1][0])
-    return roofline_of(name, ms, launches, cfg, mode, refine, steps, peaks)
+    return roofline_of(name, ms, launches, cfg, mode, refine, steps, peaks, work=work)
 
 
 def load_peaks():
@@ -617,6 +621,7 @@ def run_own(args):
     sample = None if args.no_cpu else oracle_sample(prob, cfg, w, E, t_star)
     peaks = load_peaks()
     stage_ms = {s: v for s, v in stages.items() if v[1] > 0}
+    work = stage_work(cfg, w["mode"], refine, w.get("refine_target", "interpolated"))
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -626,12 +631,12 @@ def run_own(args):
                    "parallelism": f"replicas x{world}"},
         "e2e": e2e,
         "gpu_launches": launches,
-        "roofline": roofline(stage_ms, cfg, w["mode"], refine, args.steps, peaks),
+        "roofline": roofline(stage_ms, cfg, w["mode"], refine, args.steps, peaks, work=work),
         "kernels_roofline": {nm: {kk: v for kk, v in roofline_of(nm, ms_, la, cfg, w["mode"], refine, args.steps,
-                                                                peaks).items()
+                                                                peaks, work=work).items()
                                   if kk in ("bound", "achieved", "peak", "unit", "frac", "stage_ms_per_step")}
                              for nm, (ms_, la) in stage_ms.items()
-                             if nm in stage_work(cfg, w["mode"], refine)},
+                             if nm in work},
         "stages_ms_per_step": {s: round(v[0] / args.steps, 4) for s, v in stage_ms.items()},
         "stage_timing_complete": complete,
         "clocks": clocks,

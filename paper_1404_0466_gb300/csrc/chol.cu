@@ -165,7 +165,8 @@ __device__ __forceinline__ void stage_tile(T* __restrict__ dst, const T* __restr
 // substitution, x_c = (a_c - sum_{k<c} L_JJ[c][k] x_k) / L_JJ[c][c].  One
 // thread per row (the row in registers), 256 / 64 = 4 tiles per CTA; the rows
 // of L_JJ are read from shared memory 16 bytes at a time (the same address for
-// the whole warp), and each sum runs as two interleaved partial sums.
+// the whole warp), and each sum runs as VN interleaved partial sums (one per
+// element of the 16-byte chunk), added in a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_chol_panel(T* __restrict__ F, int64_t ntiles, int J, int m, ProbMap pm)
@@ -193,21 +194,22 @@ k_chol_panel(T* __restrict__ F, int64_t ntiles, int J, int m, ProbMap pm)
     }
 #pragma unroll
     for (int c = 0; c < TB; ++c) {
-        T s0 = x[c], s1 = T(0);
+        T sp[VN];
+#pragma unroll
+        for (int e = 0; e < VN; ++e) sp[e] = T(0);
 #pragma unroll
         for (int k0 = 0; k0 < c; k0 += VN) {
             V lv = *reinterpret_cast<const V*>(Ls + c * LD + k0);
             T l[VN];
             memcpy(l, &lv, sizeof(V));
 #pragma unroll
-            for (int e = 0; e < VN; ++e) {
-                if (k0 + e < c) {
-                    if (((k0 / VN) & 1) == 0) s0 = fma(-l[e], x[k0 + e], s0);
-                    else s1 = fma(-l[e], x[k0 + e], s1);
-                }
-            }
+            for (int e = 0; e < VN; ++e)
+                if (k0 + e < c) sp[e] = fma(l[e], x[k0 + e], sp[e]);
         }
-        x[c] = (s0 + s1) * inv[c];
+        T sum = sp[0];
+#pragma unroll
+        for (int e = 1; e < VN; ++e) sum += sp[e];
+        x[c] = (x[c] - sum) * inv[c];
     }
 #pragma unroll
     for (int ch = 0; ch < TB / VN; ++ch) {

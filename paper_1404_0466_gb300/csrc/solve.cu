@@ -76,6 +76,7 @@ k_diag_inv(DiagArgs a)
     T (*Xs)[TB + 1] = reinterpret_cast<T (*)[TB + 1]>(dsm + sizeof(T) * TB * (TB + 1));
     __shared__ float rmax[TB], rmin[TB];
     __shared__ int rbad[TB];
+    __shared__ T rinv[TB];
     const int i = blockIdx.x, t = a.t0 + blockIdx.y, f = blockIdx.z, tid = threadIdx.x;
     const int64_t ti = tile_index(i, i);
     T w[MAX_P];
@@ -110,13 +111,24 @@ k_diag_inv(DiagArgs a)
         rmax[tid] = valid ? (float)fabs((double)dv) : 0.0f;
         rmin[tid] = valid ? (float)fabs((double)dv) : FLT_MAX;
         rbad[tid] = (valid && !(dv > T(0))) ? 1 : 0;
-        // inverse column tid by forward substitution on e_tid
+        rinv[tid] = T(1) / dv;
+    }
+    __syncthreads();
+    if (tid < TB) {
+        // inverse column c = tid by forward substitution on e_c:
+        //   X[r][c] = -(sum_{c <= q < r} L[r][q] X[q][c]) / L[r][r],
+        // each sum as two interleaved partial sums (even and odd q)
         const int c = tid;
-        Xs[c][c] = T(1) / Ls[c][c];
+        Xs[c][c] = rinv[c];
         for (int r = c + 1; r < TB; ++r) {
-            T s = T(0);
-            for (int qq = c; qq < r; ++qq) s = fma(Ls[r][qq], Xs[qq][c], s);
-            Xs[r][c] = -s / Ls[r][r];
+            T s0 = T(0), s1 = T(0);
+            int qq = c;
+            for (; qq + 1 < r; qq += 2) {
+                s0 = fma(Ls[r][qq], Xs[qq][c], s0);
+                s1 = fma(Ls[r][qq + 1], Xs[qq + 1][c], s1);
+            }
+            if (qq < r) s0 = fma(Ls[r][qq], Xs[qq][c], s0);
+            Xs[r][c] = -(s0 + s1) * rinv[r];
         }
     }
     __syncthreads();

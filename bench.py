@@ -70,6 +70,23 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(ms, pg, device):
+    """The slowest rank's duration (ms) of a timed region every rank ran;
+    ``pg`` is torch.distributed with a process group, or None for one process."""
+    if pg is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, units_per_step, ms):
+    """Units all ranks processed per second over the slowest rank's time (weak scaling:
+    every rank runs the same work)."""
+    return world * steps * units_per_step / (ms / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -379,12 +396,8 @@ def run_batched(args):
     if pg is not None:
         pg.barrier()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if pg is not None:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps * evals / (ms / 1e3)
+    ms = max_over_ranks(e0.elapsed_time(e1), pg, dev)
+    value = job_throughput(world, args.steps, evals, ms)
     # launches inside one graph replay = launches the captured run enqueued
     per_run = None
     n1 = batch.launch_count()
@@ -404,7 +417,7 @@ def run_batched(args):
             eh.copy_(e, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    ems = e0.elapsed_time(e1)
+    ems = max_over_ranks(e0.elapsed_time(e1), pg, dev)
     if rank != 0:
         return 0
     h2d = sum(x.numel() * 4 for x in Xh) + sum(y.numel() * 4 for y in Yh)
@@ -458,7 +471,7 @@ def run_batched(args):
                                 f"k={B['k']} g={B['g']} r={B['r']} q={B['q']} basis={w['basis']} mode=mixed "
                                 f"refine={refine}; one CUDA graph per step, {best} streams (autotuned {tune})"),
                    "l2": "inputs larger than L2 (%d MB of X)" % (h2d // 2 ** 20), "parallelism": f"replicas x{world}"},
-        "e2e": {"value": world * args.steps * evals / (ems / 1e3), "unit": "evals/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_throughput(world, args.steps, evals, ems), "unit": "evals/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": sum(e.numel() * 8 for e in Eh), "ms_per_step": ems / args.steps},
         "gpu_launches": per_run * args.steps,
         "clocks": clocks,
@@ -550,11 +563,8 @@ def run_own(args):
     launches = ctx.launch_count() - n0
     stages, complete = ctx.stage_times()
     ctx.set_timing(0)
-    if pg is not None:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps * k * q / (ms / 1e3)
+    ms = max_over_ranks(ms, pg, dev)
+    value = job_throughput(world, args.steps, k * q, ms)
     E = out[0].cpu().numpy()
     t_star = int(out[1].cpu().item())
     info = ctx.info()
@@ -576,12 +586,8 @@ def run_own(args):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ems = e0.elapsed_time(e1)
-        if pg is not None:
-            t = torch.tensor([ems], device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * args.steps * k * q / (ems / 1e3), "unit": "evals/s",
+        ems = max_over_ranks(e0.elapsed_time(e1), pg, dev)
+        e2e = {"value": job_throughput(world, args.steps, k * q, ems), "unit": "evals/s",
                "h2d_bytes_per_step": Xh.numel() * Xh.element_size() + Yh.numel() * Yh.element_size(),
                "d2h_bytes_per_step": Eh.numel() * 8 + 4, "ms_per_step": ems / args.steps}
 

@@ -113,3 +113,15 @@ def test_exact_system_refinement_needs_mixed_mode(L):
     rc, h = _create(L, _cfg(L, refine_target=1, refine_steps=1, mode=binding.PICHOL_MODE_MIXED))
     assert rc == 0
     L.pichol_destroy(h)
+
+
+def test_fp64_shapes_beyond_shared_memory_are_unsupported(L):
+    """The FP64 solve double-buffers p = r + 1 coefficient half-planes of 16 KB
+    beside its staged blocks and reduction slots: degree 5 fits in a CTA's
+    227 KB with up to 4 outputs (212 KB) but not with 12 (252 KB)."""
+    rc, h = _create(L, _cfg(L, r=5, g=8, q=31, c=12))
+    assert rc == 6 and not h.value
+    for r, c in ((5, 4), (3, 12)):
+        rc, h = _create(L, _cfg(L, r=r, g=8, q=31, c=c))
+        assert rc == 0, (r, c)
+        L.pichol_destroy(h)

@@ -6,27 +6,69 @@
 // rounded to float (P is well conditioned for the Chebyshev-log basis).
 #include "internal.cuh"
 
+#include <cstring>
+
 namespace pichol {
 
-template <typename T>
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int N = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
+
+// Each thread carries 16 bytes of a tile at a time (4 fp32 or 2 fp64 entries):
+// the g factor values in, the p coefficients out.
+template <typename T, int G>
 __global__ void __launch_bounds__(256)
-k_fit(const T* __restrict__ F, const double* __restrict__ pinv, int g, int p, int64_t ntiles,
-      T* __restrict__ Theta)
+k_fit(const T* __restrict__ F, const double* __restrict__ pinv, int p, int64_t ntiles, T* __restrict__ Theta)
 {
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::N;
     __shared__ T P[MAX_P * MAX_G];
     const int tile = blockIdx.x, f = blockIdx.y;
-    for (int e = threadIdx.x; e < p * g; e += 256) P[e] = (T)pinv[e];
+    for (int e = threadIdx.x; e < p * G; e += 256) P[e] = (T)pinv[e];
     __syncthreads();
     T* out = Theta + ((int64_t)f * ntiles + tile) * p * TILE_ELEMS;
-    for (int e = threadIdx.x; e < TILE_ELEMS; e += 256) {
-        T l[MAX_G];
-        for (int s = 0; s < g; ++s) l[s] = F[(((int64_t)f * g + s) * ntiles + tile) * TILE_ELEMS + e];
+    const T* in = F + ((int64_t)f * G * ntiles + tile) * TILE_ELEMS;
+    const int64_t sstride = ntiles * TILE_ELEMS;      // between the g factors of fold f
+    for (int v = threadIdx.x; v < TILE_ELEMS / VN; v += 256) {
+        T l[G][VN];
+#pragma unroll
+        for (int s = 0; s < G; ++s) {
+            const V x = reinterpret_cast<const V*>(in + s * sstride)[v];
+            memcpy(l[s], &x, sizeof(V));
+        }
         for (int m = 0; m < p; ++m) {
-            T acc = P[m * g] * l[0];
-            for (int s = 1; s < g; ++s) acc = fma(P[m * g + s], l[s], acc);
-            out[(int64_t)m * TILE_ELEMS + e] = acc;
+            T acc[VN];
+#pragma unroll
+            for (int u = 0; u < VN; ++u) acc[u] = P[m * G] * l[0][u];
+#pragma unroll
+            for (int s = 1; s < G; ++s)
+#pragma unroll
+                for (int u = 0; u < VN; ++u) acc[u] = fma(P[m * G + s], l[s][u], acc[u]);
+            V y;
+            memcpy(&y, acc, sizeof(V));
+            reinterpret_cast<V*>(out + (int64_t)m * TILE_ELEMS)[v] = y;
         }
     }
+}
+
+template <typename T>
+static cudaError_t fit_dispatch(int g, dim3 grid, const T* F, const double* pinv, int p, int64_t ntiles, T* Theta,
+                                cudaStream_t s)
+{
+    switch (g) {
+#define PICHOL_FIT_CASE(G) \
+    case G: k_fit<T, G><<<grid, 256, 0, s>>>(F, pinv, p, ntiles, Theta); break;
+        PICHOL_FIT_CASE(1) PICHOL_FIT_CASE(2) PICHOL_FIT_CASE(3) PICHOL_FIT_CASE(4) PICHOL_FIT_CASE(5)
+        PICHOL_FIT_CASE(6) PICHOL_FIT_CASE(7) PICHOL_FIT_CASE(8) PICHOL_FIT_CASE(9) PICHOL_FIT_CASE(10)
+        PICHOL_FIT_CASE(11) PICHOL_FIT_CASE(12) PICHOL_FIT_CASE(13) PICHOL_FIT_CASE(14) PICHOL_FIT_CASE(15)
+        PICHOL_FIT_CASE(16) PICHOL_FIT_CASE(17) PICHOL_FIT_CASE(18) PICHOL_FIT_CASE(19) PICHOL_FIT_CASE(20)
+        PICHOL_FIT_CASE(21) PICHOL_FIT_CASE(22) PICHOL_FIT_CASE(23) PICHOL_FIT_CASE(24) PICHOL_FIT_CASE(25)
+        PICHOL_FIT_CASE(26) PICHOL_FIT_CASE(27) PICHOL_FIT_CASE(28) PICHOL_FIT_CASE(29) PICHOL_FIT_CASE(30)
+        PICHOL_FIT_CASE(31) PICHOL_FIT_CASE(32)
+#undef PICHOL_FIT_CASE
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fit(pichol_ctx* ctx, cudaStream_t s)
@@ -34,14 +76,15 @@ cudaError_t launch_fit(pichol_ctx* ctx, cudaStream_t s)
     const pichol_config& c = ctx->cfg;
     dim3 grid((unsigned)ctx->ntiles, c.k);
     StageScope sc_(ctx, ST_FIT, s);
+    cudaError_t e;
     if (c.mode == PICHOL_MODE_FP64)
-        k_fit<double><<<grid, 256, 0, s>>>((const double*)ctx->F, ctx->pinv, c.g, ctx->p, ctx->ntiles,
-                                           (double*)ctx->Theta);
+        e = fit_dispatch<double>(c.g, grid, (const double*)ctx->F, ctx->pinv, ctx->p, ctx->ntiles, (double*)ctx->Theta,
+                                 s);
     else
-        k_fit<float><<<grid, 256, 0, s>>>((const float*)ctx->F, ctx->pinv, c.g, ctx->p, ctx->ntiles,
-                                          (float*)ctx->Theta);
+        e = fit_dispatch<float>(c.g, grid, (const float*)ctx->F, ctx->pinv, ctx->p, ctx->ntiles, (float*)ctx->Theta,
+                                s);
     ctx->launches++;
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace pichol

@@ -358,21 +358,29 @@ def run_batched(args):
     batch = binding.Batch(specs, nstreams=8)
     stream = torch.cuda.current_stream()
     evals = sum(sp["k"] * sp["q"] for sp in specs)
-    # autotune the number of concurrent streams (4 to 32) on eager runs
+    # autotune the number of concurrent streams and the update strip length on eager runs
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     tune = {}
     for ns in (4, 8, 16, 32):
-        batch.set_streams(ns)
-        batch.run(Xs, Ys)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(2):
+        for strip in (1, 2, 4):
+            batch.set_streams(ns)
+            batch.set_tuning(update_strip=strip)
             batch.run(Xs, Ys)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        tune[ns] = e0.elapsed_time(e1) / 2
-    best = min(tune, key=tune.get)
-    batch.set_streams(best)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(2):
+                batch.run(Xs, Ys)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tune[(ns, strip)] = e0.elapsed_time(e1) / 2
+    best_ns, best_strip = min(tune, key=tune.get)
+    if pg is not None:
+        choice = torch.tensor([best_ns, best_strip], device=dev)
+        pg.broadcast(choice, 0)
+        best_ns, best_strip = (int(v) for v in choice.tolist())
+    batch.set_streams(best_ns)
+    batch.set_tuning(update_strip=best_strip)
+    best = best_ns
     batch.run(Xs, Ys)
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
@@ -469,7 +477,8 @@ def run_batched(args):
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": (f"batched_uneven: {B['count']} problems, d ~ U[128,1536], n = 8 d, c in {{1,10}}, "
                                 f"k={B['k']} g={B['g']} r={B['r']} q={B['q']} basis={w['basis']} mode=mixed "
-                                f"refine={refine}; one CUDA graph per step, {best} streams (autotuned {tune})"),
+                                f"refine={refine}; one CUDA graph per step, {best} streams, update strips of {best_strip} "
+                                f"(autotuned, ms: {{{', '.join(f'{a}x{b}: {v:.2f}' for (a, b), v in tune.items())}}})"),
                    "l2": "inputs larger than L2 (%d MB of X)" % (h2d // 2 ** 20), "parallelism": f"replicas x{world}"},
         "e2e": {"value": job_throughput(world, args.steps, evals, ems), "unit": "evals/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": sum(e.numel() * 8 for e in Eh), "ms_per_step": ems / args.steps},
@@ -529,6 +538,27 @@ def run_own(args):
     def barrier():
         if pg is not None:
             pg.barrier()
+
+    # autotune the factorisation's launch shapes (every result is bit-identical under each)
+    tune_ms = {}
+    ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for strip in (1, 2, 4, 8):
+        for dt in (256, 512):
+            ctx.set_tuning(update_strip=strip, diag_threads=dt)
+            step()
+            ta.record(stream)
+            for _ in range(2):
+                step()
+            tb.record(stream)
+            torch.cuda.synchronize()
+            tune_ms[(strip, dt)] = ta.elapsed_time(tb) / 2
+    best = min(tune_ms, key=tune_ms.get)
+    if pg is not None:                      # every rank uses rank 0's choice
+        choice = torch.tensor(list(best), device=dev)
+        pg.broadcast(choice, 0)
+        best = tuple(int(v) for v in choice.tolist())
+    ctx.set_tuning(update_strip=best[0], diag_threads=best[1])
+    tuning = dict(ctx.tuning(), autotuned_ms={f"strip{a}_diag{b}": round(v, 3) for (a, b), v in tune_ms.items()})
 
     for _ in range(args.warmup):
         step()
@@ -634,7 +664,7 @@ def run_own(args):
         "vs_baseline": None, "dtype": "f32+f64" if w["mode"] == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": describe(args.workload, w, cfg, refine),
                    "l2": "inputs larger than L2 (X is %d MB)" % (Xh.numel() * Xh.element_size() // 2 ** 20),
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "tuning": tuning},
         "e2e": e2e,
         "gpu_launches": launches,
         "roofline": roofline(stage_ms, cfg, w["mode"], refine, args.steps, peaks, work=work),

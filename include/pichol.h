@@ -247,6 +247,28 @@ PICHOL_API pichol_status pichol_set_timing(pichol_ctx* ctx, int32_t max_launches
 PICHOL_API pichol_status pichol_stage_times(pichol_ctx* ctx, double* ms, int64_t* launches, int32_t n_stages,
                                             void* stream);
 
+/*
+ * Launch shapes of the factorisation that a tuner may change.  Each changes
+ * how the work is split into CTAs and scheduled, never the order of any
+ * element's arithmetic, so every result is bit-identical under every tuning.
+ *   update_strip   : output tiles per CTA in the bulk trailing updates, 1..8 (default 4)
+ *   diag_threads   : threads of a diagonal-tile CTA, 256 or 512 (default 512)
+ *   diag_exclusive : 1 lets each diagonal-tile CTA hold a whole SM (a shared
+ *                    memory request no update CTA fits beside) when the k g
+ *                    problems fit on half the SMs; 0 never (default 1; batches
+ *                    set 0 for their problems)
+ * pichol_set_tuning returns PICHOL_ERR_INVALID_ARG for values out of range or
+ * nonzero reserved fields and then changes nothing.
+ */
+typedef struct {
+    int32_t update_strip;
+    int32_t diag_threads;
+    int32_t diag_exclusive;
+    int32_t reserved[5];
+} pichol_tuning;
+PICHOL_API pichol_status pichol_get_tuning(const pichol_ctx* ctx, pichol_tuning* t);
+PICHOL_API pichol_status pichol_set_tuning(pichol_ctx* ctx, const pichol_tuning* t);
+
 /* Frees the host-side context (and its timing events).  The workspace stays
  * the caller's. */
 PICHOL_API void pichol_destroy(pichol_ctx* ctx);
@@ -306,6 +328,8 @@ PICHOL_API pichol_status pichol_batch_workspace_size(const pichol_batch* b, size
 PICHOL_API pichol_status pichol_batch_set_workspace(pichol_batch* b, void* workspace, size_t bytes);
 /* Changes the number of internal streams (1..64) used by later runs. */
 PICHOL_API pichol_status pichol_batch_set_streams(pichol_batch* b, int32_t nstreams);
+/* Applies pichol_set_tuning to every problem (all or none on invalid values). */
+PICHOL_API pichol_status pichol_batch_set_tuning(pichol_batch* b, const pichol_tuning* t);
 PICHOL_API pichol_status pichol_batch_run(pichol_batch* b, const void* const* X, const void* const* Y,
                                           double* const* E_out, int32_t* t_star, void* stream);
 PICHOL_API pichol_status pichol_batch_get_info(pichol_batch* b, int32_t i, pichol_info* info, void* stream);

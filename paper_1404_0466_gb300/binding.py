@@ -33,9 +33,15 @@ EXPORTS = [
     "pichol_batch_create", "pichol_batch_workspace_size", "pichol_batch_set_workspace", "pichol_batch_set_streams",
     "pichol_batch_run", "pichol_batch_get_info", "pichol_batch_launch_count", "pichol_batch_destroy",
     "pichol_batch_set_timing", "pichol_batch_stage_times",
+    "pichol_get_tuning", "pichol_set_tuning", "pichol_batch_set_tuning",
 ]
 STAGES = ["gram", "xty", "setup", "chol_init", "chol_diag", "chol_panel", "chol_update", "fit",
           "diag_inv", "solve", "resid", "score", "select", "misc"]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("update_strip", ctypes.c_int32), ("diag_threads", ctypes.c_int32),
+                ("diag_exclusive", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class Config(ctypes.Structure):
@@ -101,6 +107,9 @@ def lib():
         "pichol_batch_launch_count": ([vp], i64),
         "pichol_batch_destroy": ([vp], None),
         "pichol_batch_set_timing": ([vp, i32], ctypes.c_int),
+        "pichol_get_tuning": ([vp, ctypes.POINTER(Tuning)], ctypes.c_int),
+        "pichol_set_tuning": ([vp, ctypes.POINTER(Tuning)], ctypes.c_int),
+        "pichol_batch_set_tuning": ([vp, ctypes.POINTER(Tuning)], ctypes.c_int),
         "pichol_batch_stage_times": ([vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32,
                                       vp], ctypes.c_int),
         "pichol_stage_times": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32, vp],
@@ -267,6 +276,18 @@ class Context:
     def set_timing(self, max_launches: int):
         _check(lib().pichol_set_timing(self._h, max_launches), "pichol_set_timing")
 
+    def tuning(self) -> dict:
+        t = Tuning()
+        _check(lib().pichol_get_tuning(self._h, ctypes.byref(t)), "pichol_get_tuning")
+        return {"update_strip": t.update_strip, "diag_threads": t.diag_threads, "diag_exclusive": t.diag_exclusive}
+
+    def set_tuning(self, **kw):
+        """Change factorisation launch shapes (results are bit-identical under every tuning)."""
+        cur = self.tuning()
+        cur.update(kw)
+        t = Tuning(cur["update_strip"], cur["diag_threads"], cur["diag_exclusive"])
+        _check(lib().pichol_set_tuning(self._h, ctypes.byref(t)), "pichol_set_tuning")
+
     def stage_times(self, stream=None):
         """{stage: (total ms, launches)} since the last call; needs set_timing."""
         n = len(STAGES)
@@ -352,6 +373,11 @@ class Batch:
 
     def set_streams(self, nstreams):
         _check(lib().pichol_batch_set_streams(self._h, nstreams), "pichol_batch_set_streams")
+
+    def set_tuning(self, update_strip=4, diag_threads=512, diag_exclusive=0):
+        """Factorisation launch shapes for every problem (results are bit-identical)."""
+        t = Tuning(update_strip, diag_threads, diag_exclusive)
+        _check(lib().pichol_batch_set_tuning(self._h, ctypes.byref(t)), "pichol_batch_set_tuning")
 
     def run(self, Xs, Ys, stream=None):
         P = ctypes.c_void_p * self.n

@@ -139,7 +139,9 @@ pichol_status pichol_create(const pichol_config* cfg, pichol_ctx** out)
     ctx->kpad = tc_kpad(ctx);
     ctx->ldu = ((int64_t)c.q * c.c + 3) / 4 * 4;
     ctx->need_bytes = plan(ctx, nullptr);
-    ctx->diag_exclusive = 1;
+    ctx->tune.update_strip = 4;
+    ctx->tune.diag_threads = 512;
+    ctx->tune.diag_exclusive = 1;
     *out = ctx;
     return PICHOL_OK;
 }
@@ -366,6 +368,25 @@ pichol_status pichol_stage_times(pichol_ctx* ctx, double* ms, int64_t* launches,
     const int overflow = ctx->ev_used >= ctx->ev_cap;
     ctx->ev_used = 0;
     return overflow ? PICHOL_ERR_WORKSPACE : PICHOL_OK;
+}
+
+pichol_status pichol_get_tuning(const pichol_ctx* ctx, pichol_tuning* t)
+{
+    if (!ctx || !t) return PICHOL_ERR_INVALID_ARG;
+    *t = ctx->tune;
+    return PICHOL_OK;
+}
+
+pichol_status pichol_set_tuning(pichol_ctx* ctx, const pichol_tuning* t)
+{
+    if (!ctx || !t) return PICHOL_ERR_INVALID_ARG;
+    if (t->update_strip < 1 || t->update_strip > 8) return PICHOL_ERR_INVALID_ARG;
+    if (t->diag_threads != 256 && t->diag_threads != 512) return PICHOL_ERR_INVALID_ARG;
+    if (t->diag_exclusive != 0 && t->diag_exclusive != 1) return PICHOL_ERR_INVALID_ARG;
+    for (int i = 0; i < 5; ++i)
+        if (t->reserved[i] != 0) return PICHOL_ERR_INVALID_ARG;
+    ctx->tune = *t;
+    return PICHOL_OK;
 }
 
 void pichol_destroy(pichol_ctx* ctx)

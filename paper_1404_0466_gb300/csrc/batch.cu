@@ -85,7 +85,7 @@ pichol_status pichol_batch_create(const pichol_config* cfgs, int32_t nprob, int3
             delete b;
             return st;
         }
-        c->diag_exclusive = 0;     // other problems' work fills the SMs instead
+        c->tune.diag_exclusive = 0;   // other problems' work fills the SMs instead
         b->ctx.push_back(c);
         b->off.push_back(off);
         size_t need = 0;
@@ -129,6 +129,15 @@ pichol_status pichol_batch_set_streams(pichol_batch* b, int32_t nstreams)
         free_streams(b);
         b->nstreams = nstreams;
     }
+    return PICHOL_OK;
+}
+
+pichol_status pichol_batch_set_tuning(pichol_batch* b, const pichol_tuning* t)
+{
+    if (!b || !t || b->ctx.empty()) return PICHOL_ERR_INVALID_ARG;
+    pichol_status st = pichol_set_tuning(b->ctx[0], t);   // validates; changes nothing on error
+    if (st != PICHOL_OK) return st;
+    for (pichol_ctx* c : b->ctx) c->tune = *t;
     return PICHOL_OK;
 }
 

@@ -324,11 +324,10 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
     const int nprob = c.k * pm.per;
     T* F = (T*)ctx->F;
     constexpr int UNT = UpdateThreads<T>::value;
-    constexpr int UCH = 4;                       // output tiles per CTA in the bulk updates
-    constexpr int DIAG_NT = 512;                 // threads of the diagonal-tile kernel
+    const int UCH = ctx->tune.update_strip;     // output tiles per CTA in the bulk updates
     // The diagonal tiles are the critical path.  When the k g problems fit on
-    // half the SMs, each diagonal CTA asks for enough shared memory that no
-    // trailing-update CTA can share its SM.
+    // half the SMs (and the tuning allows), each diagonal CTA asks for enough
+    // shared memory that no trailing-update CTA can share its SM.
     constexpr int DIAG_RESERVE = 160 * 1024;
     const size_t sm_mm = 3 * sizeof(T) * TB * (TB + Vec16<T>::N);
     static bool attr_done = false;
@@ -336,7 +335,10 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
         cudaError_t e = cudaFuncSetAttribute(k_chol_update<T, UNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sm_mm);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_chol_diag<T, DIAG_NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(k_chol_diag<T, 512, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     DIAG_RESERVE);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_chol_diag<T, 256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      DIAG_RESERVE);
         if (e != cudaSuccess) return e;
         attr_done = true;
@@ -356,7 +358,7 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
     // the call stays capturable.
     cudaStream_t sh = ctx->aux ? ctx->aux : s;
     const bool split = sh != s;
-    const size_t diag_smem = (ctx->diag_exclusive && 2 * nprob <= ctx->nsm) ? DIAG_RESERVE : 0;
+    const size_t diag_smem = (ctx->tune.diag_exclusive && 2 * nprob <= ctx->nsm) ? DIAG_RESERVE : 0;
     cudaError_t e;
     if (split) {
         if ((e = cudaEventRecord(ctx->ev_fork, s)) != cudaSuccess) return e;
@@ -366,7 +368,10 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
     for (int J = 0; J < ctx->nt; ++J) {
         {
             StageScope sc_(ctx, ST_CHOL_DIAG, sh);
-            k_chol_diag<T, DIAG_NT, true><<<nprob, DIAG_NT, diag_smem, sh>>>(F, ctx->ntiles, J, c.d, pm, ctx->status);
+            if (ctx->tune.diag_threads == 256)
+                k_chol_diag<T, 256, true><<<nprob, 256, diag_smem, sh>>>(F, ctx->ntiles, J, c.d, pm, ctx->status);
+            else
+                k_chol_diag<T, 512, true><<<nprob, 512, diag_smem, sh>>>(F, ctx->ntiles, J, c.d, pm, ctx->status);
         }
         ctx->launches++;
         const int m = ctx->nt - 1 - J;

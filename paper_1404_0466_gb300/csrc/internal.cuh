@@ -164,7 +164,7 @@ struct pichol_ctx {
     cudaStream_t aux;
     cudaEvent_t ev_fork, ev_panel, ev_upd, ev_join;
     int nsm;             // SMs of the device the workspace lives on
-    int diag_exclusive;  // the diagonal-tile CTAs may reserve whole SMs (off in batches)
+    pichol_tuning tune;  // factorisation launch shapes (pichol_set_tuning)
 
     // optional per-stage timing: pairs of events recorded around launches
     int timing;

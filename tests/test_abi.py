@@ -125,3 +125,19 @@ def test_fp64_shapes_beyond_shared_memory_are_unsupported(L):
         rc, h = _create(L, _cfg(L, r=r, g=8, q=31, c=c))
         assert rc == 0, (r, c)
         L.pichol_destroy(h)
+
+
+def test_tuning_defaults_and_validation(L):
+    rc, h = _create(L, _cfg(L))
+    assert rc == 0
+    t = binding.Tuning()
+    assert L.pichol_get_tuning(h, ctypes.byref(t)) == 0
+    assert (t.update_strip, t.diag_threads, t.diag_exclusive) == (4, 512, 1)
+    for bad in (dict(update_strip=0), dict(update_strip=9), dict(diag_threads=384), dict(diag_exclusive=2)):
+        b = binding.Tuning(**{**dict(update_strip=4, diag_threads=512, diag_exclusive=1), **bad})
+        assert L.pichol_set_tuning(h, ctypes.byref(b)) == 1, bad
+    good = binding.Tuning(update_strip=2, diag_threads=256, diag_exclusive=0)
+    assert L.pichol_set_tuning(h, ctypes.byref(good)) == 0
+    assert L.pichol_get_tuning(h, ctypes.byref(t)) == 0
+    assert (t.update_strip, t.diag_threads, t.diag_exclusive) == (2, 256, 0)
+    L.pichol_destroy(h)

@@ -234,6 +234,26 @@ def test_mixed_exact_system_refinement(torch_mod, mixed_small):
     assert ctx.info().code == 0
 
 
+def test_tuning_leaves_every_result_bit_identical(torch_mod, mixed_small):
+    """Launch-shape tunings change scheduling only: scores, selection and solutions
+    are bit-identical."""
+    torch = torch_mod
+    prob, _ = mixed_small
+    ctx = _ctx(prob, k=5, g=6, r=3, q=101, basis="cheb_log", mode="mixed", refine_steps=1)
+    X, Y = _dev(torch, prob.X, "mixed"), _dev(torch, prob.Y, "mixed")
+    outs = []
+    for tune in (dict(update_strip=4, diag_threads=512, diag_exclusive=1),
+                 dict(update_strip=1, diag_threads=256, diag_exclusive=0),
+                 dict(update_strip=8, diag_threads=512, diag_exclusive=0)):
+        ctx.set_tuning(**tune)
+        assert ctx.tuning() == tune
+        out = ctx.run(X, Y, want_w=True)
+        outs.append((out.E.clone(), out.t_star.clone(), out.W.clone()))
+    for E, t, W in outs[1:]:
+        assert torch.equal(E, outs[0][0]) and torch.equal(t, outs[0][1]) and torch.equal(W, outs[0][2])
+    assert ctx.info().code == 0
+
+
 def test_mixed_exact_cv(torch_mod, mixed_small):
     torch = torch_mod
     prob, _ = mixed_small

@@ -226,6 +226,13 @@ PICHOL_API pichol_status pichol_get_info(pichol_ctx* ctx, pichol_info* info, voi
 /* Clears the latched device status (enqueued on `stream`). */
 PICHOL_API pichol_status pichol_clear_status(pichol_ctx* ctx, void* stream);
 
+/* Exercises the error path of the bounded copy waits: enqueues one wait, with
+ * a limit of `cycles` SM clocks (1 .. 2^34), on an mbarrier that nothing
+ * completes.  It runs out, latches PICHOL_ERR_TIMEOUT (fold, index and pivot
+ * -1) and returns; nothing faults or hangs, and after pichol_clear_status the
+ * context is usable as before.  For tests of failure detection. */
+PICHOL_API pichol_status pichol_check_timeout(pichol_ctx* ctx, int64_t cycles, void* stream);
+
 /* Number of kernel launches this context has enqueued since creation. */
 PICHOL_API int64_t pichol_launch_count(const pichol_ctx* ctx);
 

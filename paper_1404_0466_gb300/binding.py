@@ -33,7 +33,7 @@ EXPORTS = [
     "pichol_batch_create", "pichol_batch_workspace_size", "pichol_batch_set_workspace", "pichol_batch_set_streams",
     "pichol_batch_run", "pichol_batch_get_info", "pichol_batch_launch_count", "pichol_batch_destroy",
     "pichol_batch_set_timing", "pichol_batch_stage_times",
-    "pichol_get_tuning", "pichol_set_tuning", "pichol_batch_set_tuning",
+    "pichol_get_tuning", "pichol_set_tuning", "pichol_batch_set_tuning", "pichol_check_timeout",
 ]
 STAGES = ["gram", "xty", "setup", "chol_init", "chol_diag", "chol_panel", "chol_update", "fit",
           "diag_inv", "solve", "resid", "score", "select", "misc"]
@@ -108,6 +108,7 @@ def lib():
         "pichol_batch_destroy": ([vp], None),
         "pichol_batch_set_timing": ([vp, i32], ctypes.c_int),
         "pichol_get_tuning": ([vp, ctypes.POINTER(Tuning)], ctypes.c_int),
+        "pichol_check_timeout": ([vp, i64, vp], ctypes.c_int),
         "pichol_set_tuning": ([vp, ctypes.POINTER(Tuning)], ctypes.c_int),
         "pichol_batch_set_tuning": ([vp, ctypes.POINTER(Tuning)], ctypes.c_int),
         "pichol_batch_stage_times": ([vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32,
@@ -269,6 +270,11 @@ class Context:
         inf = Info()
         _check(lib().pichol_get_info(self._h, ctypes.byref(inf), ctypes.c_void_p(_stream_ptr(stream))), "pichol_get_info")
         return inf
+
+    def check_timeout(self, cycles: int, stream=None):
+        """One bounded wait that runs out after `cycles` clocks (latches PICHOL_ERR_TIMEOUT)."""
+        _check(lib().pichol_check_timeout(self._h, cycles, ctypes.c_void_p(_stream_ptr(stream))),
+               "pichol_check_timeout")
 
     def clear_status(self, stream=None):
         _check(lib().pichol_clear_status(self._h, ctypes.c_void_p(_stream_ptr(stream))), "pichol_clear_status")

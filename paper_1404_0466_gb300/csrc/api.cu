@@ -370,6 +370,13 @@ pichol_status pichol_stage_times(pichol_ctx* ctx, double* ms, int64_t* launches,
     return overflow ? PICHOL_ERR_WORKSPACE : PICHOL_OK;
 }
 
+pichol_status pichol_check_timeout(pichol_ctx* ctx, int64_t cycles, void* stream)
+{
+    if (!ctx || cycles < 1 || cycles > ((int64_t)1 << 34)) return PICHOL_ERR_INVALID_ARG;
+    if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
+    return cuda_status(launch_wait_check(ctx, (long long)cycles, (cudaStream_t)stream));
+}
+
 pichol_status pichol_get_tuning(const pichol_ctx* ctx, pichol_tuning* t)
 {
     if (!ctx || !t) return PICHOL_ERR_INVALID_ARG;

@@ -216,6 +216,7 @@ cudaError_t launch_gram_tc(pichol_ctx* ctx, const float* X, cudaStream_t s);
 cudaError_t launch_grad(pichol_ctx* ctx, double log_lam, double* E_out, double* dE_out, cudaStream_t s);
 cudaError_t launch_score_tc(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s);
 cudaError_t launch_gall_split(pichol_ctx* ctx, cudaStream_t s);
+cudaError_t launch_wait_check(pichol_ctx* ctx, long long limit, cudaStream_t s);
 cudaError_t launch_resid_exact(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s);
 
 }  // namespace pichol

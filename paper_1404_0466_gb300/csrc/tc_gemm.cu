@@ -542,6 +542,26 @@ cudaError_t launch_gram_tc(pichol_ctx* ctx, const float* X, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// The error path of every bounded copy wait, exercised on purpose: one
+// mbarrier expecting one arrival that nothing makes, waited on with a limit of
+// `limit` clocks; when the wait runs out the kernel latches PICHOL_ERR_TIMEOUT
+// and returns, like a copy wait that gives up.
+__global__ void k_wait_check(long long limit, DevStatus* st)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+    if (!mbar_wait(&bar, 0, limit)) latch_error(st, PICHOL_ERR_TIMEOUT, -1, -1, -1);
+}
+
+cudaError_t launch_wait_check(pichol_ctx* ctx, long long limit, cudaStream_t s)
+{
+    k_wait_check<<<1, 32, 0, s>>>(limit, ctx->status);
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
 // G_all = sum_j G_j (the fp32 blocks summed in double, in increasing j),
 // rounded to fp32 and split into a TF32 part and an fp32 remainder for the
 // products with W of the exact-system refinement.

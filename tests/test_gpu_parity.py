@@ -175,6 +175,23 @@ def test_nan_input_latches_not_spd(torch_mod):
     assert ctx.info().code == 0
 
 
+def test_bounded_wait_runs_out_and_the_context_recovers(torch_mod):
+    """A bounded copy wait that nothing completes (about 1 ms of clocks) latches
+    PICHOL_ERR_TIMEOUT without a fault or a hang; after clearing the status the
+    same context runs a cross-validation that matches the oracle."""
+    torch = torch_mod
+    prob = synth.spectral_gaussian(300, 40, 2, seed=6)
+    ctx = _ctx(prob, k=3, g=3, r=2, q=5, mode="fp64")
+    ctx.check_timeout(2_000_000)
+    info = ctx.info()
+    assert info.code == 5 and info.fold == -1 and info.index == -1
+    ctx.clear_status()
+    out = ctx.run(_dev(torch, prob.X, "fp64"), _dev(torch, prob.Y, "fp64"))
+    assert ctx.info().code == 0
+    ref = oracle.cv(prob.X, prob.Y, k=3, g=3, r=2, q=5)
+    np.testing.assert_allclose(out.E.cpu().numpy(), ref.E, rtol=1e-10)
+
+
 def test_nan_input_with_trace_scaled_grid_latches_invalid(torch_mod):
     """With the grid scaled by tr(X^T X)/d a NaN makes the grid itself
     non-finite; the set-up latches PICHOL_ERR_INVALID_ARG first."""

@@ -239,7 +239,11 @@ PICHOL_API int64_t pichol_launch_count(const pichol_ctx* ctx);
 /* Stage timing (for benchmarks): with max_launches > 0 the context records a
  * pair of CUDA events around each of its next max_launches kernel launches on
  * the launching stream; 0 turns timing off and frees the events.  Creating
- * events is the only resource this takes. */
+ * events is the only resource this takes.  The records are external event
+ * records, so calls captured into a CUDA graph while timing is on put them in
+ * the graph and every replay re-records them (pichol_stage_times then reports
+ * the last replay); such a graph must be destroyed before timing is turned
+ * off or set again, which frees the events it refers to. */
 PICHOL_API pichol_status pichol_set_timing(pichol_ctx* ctx, int32_t max_launches);
 
 /* Synchronises `stream`, then sums the recorded launch durations per stage

@@ -182,20 +182,26 @@ enum Stage {
 };
 
 // Records a start event on construction and a stop event on destruction
-// when timing is enabled on the context (and the event pool has room).
+// when timing is enabled on the context (and the event pool has room).  Under
+// stream capture the records are external, so they become event-record nodes
+// that every replay of the graph re-records.
 struct StageScope {
     pichol_ctx* ctx;
     cudaStream_t s;
     int slot;
-    StageScope(pichol_ctx* c, int stage, cudaStream_t st) : ctx(c), s(st), slot(-1) {
+    unsigned flags;
+    StageScope(pichol_ctx* c, int stage, cudaStream_t st) : ctx(c), s(st), slot(-1), flags(cudaEventRecordDefault) {
         if (ctx->timing && ctx->ev_used < ctx->ev_cap) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+                flags = cudaEventRecordExternal;
             slot = ctx->ev_used++;
             ctx->ev_stage[slot] = stage;
-            cudaEventRecord(ctx->ev[2 * slot], s);
+            cudaEventRecordWithFlags(ctx->ev[2 * slot], s, flags);
         }
     }
     ~StageScope() {
-        if (slot >= 0) cudaEventRecord(ctx->ev[2 * slot + 1], s);
+        if (slot >= 0) cudaEventRecordWithFlags(ctx->ev[2 * slot + 1], s, flags);
     }
 };
 

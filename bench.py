@@ -540,10 +540,11 @@ def run_own(args):
         if pg is not None:
             pg.barrier()
 
-    # autotune the factorisation's launch shapes (every result is bit-identical under each)
+    # autotune the factorisation's launch shapes (every result is bit-identical under each;
+    # --profile keeps the defaults so that profiled runs stay short)
     tune_ms = {}
     ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for strip in (1, 2, 4, 8):
+    for strip in ((1, 2, 4, 8) if not args.profile else ()):
         for dt in (256, 512):
             ctx.set_tuning(update_strip=strip, diag_threads=dt)
             step()
@@ -553,7 +554,7 @@ def run_own(args):
             tb.record(stream)
             torch.cuda.synchronize()
             tune_ms[(strip, dt)] = ta.elapsed_time(tb) / 2
-    best = min(tune_ms, key=tune_ms.get)
+    best = min(tune_ms, key=tune_ms.get) if tune_ms else (4, 512)
     if pg is not None:                      # every rank uses rank 0's choice
         choice = torch.tensor(list(best), device=dev)
         pg.broadcast(choice, 0)

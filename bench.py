@@ -8,11 +8,20 @@ with the selected lambda.  The metric is fold x lambda hold-out evaluations per
 second (k * q per step).
 
 Own arm (default): the C ABI on cuda:LOCAL_RANK with X, Y resident in HBM.
+Before the timed region the factorisation's launch shapes are autotuned
+(results are bit-identical under every tuning), and eager calls are timed
+against a CUDA-graph replay of one step; the faster launch mode is used.
 Also reported: the same metric end to end from pinned host buffers (e2e),
 exact-Cholesky cross-validation with the same kernels on the same GPU, the
 error of the hold-out scores against the FP64 oracle on a sample, per-stage
 device times, the roofline of the dominant kernel, SM clocks during the timed
 region, and the oracle timed on the host cores (cpu_baseline).
+
+Workloads: mixed_ecc (default: n = 32768, d = 2048, c = 10, k = 5, g = 6,
+r = 3, q = 101, mixed precision, one refinement step against the interpolated
+system), mixed_ecc_precond (the same with the exact-system refinement),
+fp64_small (n = 2048, d = 256, FP64), batched_uneven (64 problems of uneven
+size per CUDA-graph replay, streams and update strips autotuned).
 
 --impl reference: the FP64 CPU oracle as it stands, one fold of the same
 workload per step, on this machine's cores (rank 0 only).

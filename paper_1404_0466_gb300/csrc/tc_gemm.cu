@@ -1,6 +1,10 @@
 // Tensor-core (tcgen05, TF32) contractions of the mixed-precision path:
-//   Gram blocks     G_j = X_j^T X_j                     (Sec. 3.1, Eq. 2)
+//   Gram blocks     G_j = X_j^T X_j and X_j^T Y_j       (Sec. 3.1, Eq. 2)
 //   score products  U_f = G_f W_f for all q lambdas      (hold-out expansion, Sec. 3.1)
+//   exact-system refinement residual (refine_target exact; not in the paper):
+//                   G_f W_f and G_all W_f, G_all = sum_j G_j, combined as
+//                   R = B_f - lambda W - (G_all W - G_f W)
+// and the bounded-wait check (pichol_check_timeout).
 //
 // C = sum_p A_p B_p^T with A (M x K) and B (N x K) both K-major fp32 in global
 // memory.  With PASSES = 3 every operand is split as x = hi + lo, hi = x

@@ -505,3 +505,88 @@ def holdout_grad(X, Y, *, k: int, g: int, r: int, q: int, log_lam: float, lo: fl
         dL = unvec_lower(eval_poly(dphi, Theta), d)
         E[f], dE[f] = _holdout_and_grad(Xv, Yv, Bf, L, dL, lam)
     return GradResult(E=E, dE=dE, Ebar=float(np.nanmean(E)), dEbar=float(np.nanmean(dE)))
+
+
+# ----------------------------------------------------------------------------
+# multi-level range narrowing (MChol, Sec. 6.2)
+# ----------------------------------------------------------------------------
+
+def holdout_exact_at(X, Y, *, k: int, lams, folds=None) -> np.ndarray:
+    """k x m hold-out MSEs E[f, i] = ||Y_f - X_f W||^2 / (n_f c) with
+    W = (H_f + lams[i] I)^{-1} B_f through the exact Cholesky factor, at any
+    lambdas (not only grid points).  Folds outside ``folds`` are NaN."""
+    X, Y = _f64(X), _f64(Y)
+    n, d = X.shape
+    lams = np.atleast_1d(np.asarray(lams, dtype=np.float64))
+    offs = fold_offsets(n, k)
+    E = np.full((k, lams.size), np.nan)
+    for f in (range(k) if folds is None else folds):
+        r0, r1 = offs[f], offs[f + 1]
+        Hf, Bf = normal_blocks(X, Y, r0, r1)
+        Xv, Yv = X[r0:r1], Y[r0:r1]
+        for i, lam in enumerate(lams):
+            W = solve_factored(cholesky(Hf + lam * np.eye(d)), Bf)
+            E[f, i] = holdout_sse(Xv, Yv, W) / (Yv.shape[0] * Yv.shape[1])
+    return E
+
+
+def mchol_levels(s: float, s_min: float) -> int:
+    """Number of levels the search runs: the three steps repeat, halving s
+    each time, until s <= s_min (at least one level)."""
+    if not (s > 0.0 and s_min > 0.0):
+        raise ValueError("MChol needs s > 0 and s_min > 0")
+    n = 0
+    while True:
+        n += 1
+        s = s / 2.0
+        if s <= s_min:
+            return n
+
+
+@dataclass
+class MCholResult:
+    lams: list          # per level: the three lambdas 10^(c-s), 10^c, 10^(c+s) (times tau)
+    Ebar: list          # per level: their mean hold-out errors
+    best: list          # per level: index 0..2 of the first smallest finite one, -1 if none
+    c: float            # final centre (log10 of lambda / tau)
+    s: float            # final half-width (decades)
+    tau: float
+
+    @property
+    def window(self) -> tuple:
+        """The final range [10^(c-s), 10^(c+s)], relative to tau."""
+        return 10.0 ** (self.c - self.s), 10.0 ** (self.c + self.s)
+
+
+def mchol_search(h, c: float, s: float, s_min: float, tau: float = 1.0) -> MCholResult:
+    """The multi-level search of Sec. 6.2 over a hold-out function h that maps
+    an array of lambdas to their mean hold-out errors:
+      (a) evaluate h at lambda = tau 10^(c-s), tau 10^c, tau 10^(c+s);
+      (b) lambda_opt = the first argmin of (a) over finite values;
+      (c) c <- log10(lambda_opt / tau), s <- s / 2;
+    repeated until s <= s_min.  tau = 1 is the paper's absolute range; a
+    trace scale makes c relative, as for the grid of ``cv``.  If no value of a
+    level is finite, c is kept."""
+    res = MCholResult(lams=[], Ebar=[], best=[], c=c, s=s, tau=tau)
+    for _ in range(mchol_levels(s, s_min)):
+        lams = tau * 10.0 ** np.array([c - s, c, c + s])
+        Ebar = np.asarray(h(lams), dtype=np.float64)
+        best = argmin_first(Ebar)
+        if best >= 0:
+            c = float(np.log10(lams[best] / tau))
+        s = s / 2.0
+        res.lams.append(lams)
+        res.Ebar.append(Ebar)
+        res.best.append(best)
+    res.c, res.s = c, s
+    return res
+
+
+def mchol(X, Y, *, k: int, c: float, s: float, s_min: float, scale_by_trace: bool = True) -> MCholResult:
+    """MChol of Sec. 6.2 on k-fold cross-validation: the search of
+    ``mchol_search`` with h = the mean over folds of the exact hold-out MSE
+    (``holdout_exact_at``).  With scale_by_trace the range is relative to
+    tau = tr(X^T X) / d, like the grid of ``cv``; piCholesky then searches
+    the final window by ``cv(..., lo=window[0], hi=window[1])``."""
+    tau = trace_scale(X) if scale_by_trace else 1.0
+    return mchol_search(lambda lams: holdout_exact_at(X, Y, k=k, lams=lams).mean(axis=0), c, s, s_min, tau)

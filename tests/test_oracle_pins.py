@@ -488,3 +488,104 @@ def test_exact_system_refinement_is_idle_when_every_lambda_is_a_node():
     ex = orc.cv(prob.X, prob.Y, exact=True, **kw)
     r1 = orc.cv(prob.X, prob.Y, precond_steps=1, **kw)
     np.testing.assert_allclose(r1.E, ex.E, rtol=1e-11)
+
+
+# ----------------------------------------------------------------------------
+# MChol (Sec. 6.2): multi-level narrowing of the lambda range
+# ----------------------------------------------------------------------------
+
+def test_exact_holdout_at_any_lambda_matches_eigen_closed_form():
+    """Exact hold-out MSE at lambdas off any grid, against the spectral form
+    W = Q diag(1 / (mu + lambda)) Q^T B on each fold's training rows."""
+    p = synth.spectral_gaussian(180, 12, 3, seed=81)
+    lams = np.array([3.7e-2, 1.0, 55.5])
+    E = orc.holdout_exact_at(p.X, p.Y, k=4, lams=lams)
+    offs = orc.fold_offsets(180, 4)
+    for f in range(4):
+        keep = np.r_[0:offs[f], offs[f + 1]:180]
+        mu, Q = np.linalg.eigh(p.X[keep].T @ p.X[keep])
+        B = p.X[keep].T @ p.Y[keep]
+        Xv, Yv = p.X[offs[f]:offs[f + 1]], p.Y[offs[f]:offs[f + 1]]
+        for i, lam in enumerate(lams):
+            W = Q @ ((Q.T @ B) / (mu + lam)[:, None])
+            ref = np.mean((Yv - Xv @ W) ** 2)
+            assert abs(E[f, i] - ref) <= 1e-10 * ref
+    assert np.all(np.isnan(orc.holdout_exact_at(p.X, p.Y, k=4, lams=lams, folds=[1])[[0, 2, 3]]))
+
+
+def test_mchol_level_count():
+    """The paper's parameters s = 1.5, s0 = 0.0025 (Sec. 6.3): 1.5 / 2^9 > s0
+    and 1.5 / 2^10 <= s0, so ten levels; a start already below s0 still runs
+    one level."""
+    assert orc.mchol_levels(1.5, 0.0025) == 10
+    assert orc.mchol_levels(1.5, 0.1) == 4
+    assert orc.mchol_levels(1.5, 0.75) == 1
+    assert orc.mchol_levels(0.1, 0.2) == 1
+    with pytest.raises(ValueError):
+        orc.mchol_levels(1.0, 0.0)
+
+
+def test_mchol_search_hand_traced():
+    """h(lambda) = (log10 lambda - 0.3)^2 from c = 0, s = 1.5, s0 = 0.0025,
+    traced by hand: the nearest of the three points wins at each level.
+      s=1.5     {-1.5, 0, 1.5}              -> 0
+      s=0.75    {-0.75, 0, 0.75}            -> 0
+      s=0.375   {-0.375, 0, 0.375}          -> 0.375
+      s=0.1875  {0.1875, 0.375, 0.5625}     -> 0.375
+      s=0.09375 {0.28125, 0.375, 0.46875}   -> 0.28125
+      s=3/64    {0.234375, 0.28125, 0.328125} -> 0.28125
+      s=3/128   {0.2578125, 0.28125, 0.3046875} -> 0.3046875
+      s=3/256   {0.29296875, 0.3046875, 0.31640625} -> 0.3046875
+      s=3/512   {0.298828125, 0.3046875, 0.310546875} -> 0.298828125
+      s=3/1024  {0.2958984375, 0.298828125, 0.3017578125} -> 0.298828125
+    final c = 153/512, s = 3/2048."""
+    res = orc.mchol_search(lambda lam: (np.log10(lam) - 0.3) ** 2, 0.0, 1.5, 0.0025)
+    assert res.best == [1, 1, 2, 1, 0, 1, 2, 1, 0, 1]
+    assert abs(res.c - 153 / 512) < 1e-12
+    assert res.s == 3 / 2048
+    np.testing.assert_allclose(res.lams[4], 10.0 ** np.array([0.28125, 0.375, 0.46875]), rtol=1e-14)
+
+
+def test_mchol_search_brackets_a_unimodal_minimum():
+    """For h = (log10 lambda - c*)^2 the winner of a level is the point nearest
+    c*, so |c - c*| <= 1.5 s before a level gives |c - c*| <= s after it; from
+    c = 0, s = 1.5 every c* in [-2.25, 2.25] ends within the final s."""
+    for cstar in np.linspace(-2.25, 2.25, 41):
+        res = orc.mchol_search(lambda lam: (np.log10(lam) - cstar) ** 2, 0.0, 1.5, 0.01)
+        assert abs(res.c - cstar) <= res.s + 1e-12, (cstar, res.c, res.s)
+
+
+def test_mchol_search_ties_and_non_finite_values():
+    """Equal errors pick the smallest lambda (first argmin): c drops by s at
+    every level, c_final = c0 - 2 s0 (1 - 2^-n).  A level with no finite
+    value keeps c and still halves s."""
+    res = orc.mchol_search(lambda lam: np.ones_like(lam), 1.0, 1.0, 0.1)
+    n = orc.mchol_levels(1.0, 0.1)
+    assert res.best == [0] * n
+    assert abs(res.c - (1.0 - 2.0 * (1.0 - 2.0 ** -n))) < 1e-12
+    res = orc.mchol_search(lambda lam: np.full_like(lam, np.inf), 0.5, 1.0, 0.1)
+    assert res.best == [-1] * n and res.c == 0.5 and res.s == 2.0 ** -n
+
+
+def test_mchol_on_data_finds_the_dense_scan_minimum():
+    """On data whose exact mean hold-out curve is unimodal in log lambda
+    (checked on a dense scan), MChol ends within its final half-width plus
+    one scan step of the scan's minimum, the best error never rises from one
+    level to the next, and each level is centred on the previous winner."""
+    p = synth.spectral_gaussian(240, 16, 2, seed=83)
+    k = 4
+    tau = orc.trace_scale(p.X)
+    u = np.linspace(-4.0, 1.0, 201)
+    Ebar = orc.holdout_exact_at(p.X, p.Y, k=k, lams=tau * 10.0 ** u).mean(axis=0)
+    i0 = int(np.argmin(Ebar))
+    assert 0 < i0 < u.size - 1
+    assert np.all(np.diff(Ebar[:i0 + 1]) < 0) and np.all(np.diff(Ebar[i0:]) > 0)
+    res = orc.mchol(p.X, p.Y, k=k, c=-1.5, s=1.5, s_min=0.01)
+    assert abs(res.c - u[i0]) <= res.s + (u[1] - u[0])
+    mins = [float(np.min(e)) for e in res.Ebar]
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(mins, mins[1:]))
+    for lv in range(1, len(res.lams)):
+        prev = res.lams[lv - 1][res.best[lv - 1]]
+        assert abs(res.lams[lv][1] / prev - 1.0) < 1e-12
+    lo, hi = res.window
+    assert abs(np.log10(hi / lo) - 2 * res.s) < 1e-12

@@ -209,6 +209,40 @@ PICHOL_API pichol_status pichol_eval_holdout_exact(pichol_ctx* ctx, double* E_ou
 PICHOL_API pichol_status pichol_holdout_grad(pichol_ctx* ctx, double log_lam, double* E_out, double* dE_out,
                                              void* stream);
 
+/*
+ * Multi-level narrowing of the lambda range (MChol, Sec. 6.2), then a new grid
+ * on the final range.  Starting from (c, s), each level
+ *   (a) evaluates the exact hold-out error of every fold at the three lambdas
+ *       tau 10^(c-s), tau 10^c, tau 10^(c+s) (exact Cholesky, as in
+ *       pichol_eval_holdout_exact), tau = tr(X^T X)/d if scale_by_trace else 1;
+ *   (b) takes lambda_opt = the first of the three with the smallest finite mean
+ *       over folds (c is kept if none is finite);
+ *   (c) sets c <- log10(lambda_opt / tau), s <- s / 2;
+ * and the levels repeat until s <= s_min (at least one level; their number is
+ * pichol_mchol_levels(s, s_min)).  Afterwards the grid, the samples and V^+
+ * are set up again as in pichol_hessian with lam_lo = 10^(c-s) and
+ * lam_hi = 10^(c+s) from the final (c, s), so pichol_factor_samples,
+ * pichol_fit and pichol_eval_holdout run piCholesky over that range (and
+ * pichol_get_lambdas returns it).  Everything runs on the device; nothing
+ * synchronises.
+ *   c, s, s_min : |c| <= 300; 0 < s <= 300; 0 < s_min <= 300; at most 64 levels
+ *   trace_out   : device or NULL; levels x 8 doubles, one row per level:
+ *                 the three lambdas, their mean hold-out errors, then c and s
+ *                 after the level's update
+ * Needs pichol_hessian before it and q >= 3 (else PICHOL_ERR_UNSUPPORTED); the
+ * sampled factors and the fit are invalidated (the factor buffer is reused).
+ * Errors of the exact factorisations latch as in pichol_eval_holdout_exact
+ * (index = 0..2, the position of the lambda in its level); a final range that
+ * is not finite latches PICHOL_ERR_INVALID_ARG.
+ */
+PICHOL_API pichol_status pichol_mchol(pichol_ctx* ctx, double c, double s, double s_min, double* trace_out,
+                                      void* stream);
+
+/* Number of levels pichol_mchol runs for (s, s_min): the smallest n >= 1 with
+ * s / 2^n <= s_min.  PICHOL_ERR_INVALID_ARG for values out of the ranges of
+ * pichol_mchol or more than 64 levels. */
+PICHOL_API pichol_status pichol_mchol_levels(double s, double s_min, int32_t* levels);
+
 /* Device copy of the q grid lambdas (after pichol_hessian). */
 PICHOL_API pichol_status pichol_get_lambdas(pichol_ctx* ctx, double* lam_out, void* stream);
 

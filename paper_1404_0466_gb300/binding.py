@@ -34,6 +34,7 @@ EXPORTS = [
     "pichol_batch_run", "pichol_batch_get_info", "pichol_batch_launch_count", "pichol_batch_destroy",
     "pichol_batch_set_timing", "pichol_batch_stage_times",
     "pichol_get_tuning", "pichol_set_tuning", "pichol_batch_set_tuning", "pichol_check_timeout",
+    "pichol_mchol", "pichol_mchol_levels",
 ]
 STAGES = ["gram", "xty", "setup", "chol_init", "chol_diag", "chol_panel", "chol_update", "fit",
           "diag_inv", "solve", "resid", "score", "select", "misc"]
@@ -98,6 +99,8 @@ def lib():
         "pichol_set_timing": ([vp, i32], ctypes.c_int),
         "pichol_fold_rhs_noalloc": ([i32, vp, vp, i64, i64, i64, i32, vp, vp, vp], ctypes.c_int),
         "pichol_holdout_grad": ([vp, ctypes.c_double, vp, vp, vp], ctypes.c_int),
+        "pichol_mchol": ([vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, vp], ctypes.c_int),
+        "pichol_mchol_levels": ([ctypes.c_double, ctypes.c_double, ctypes.POINTER(i32)], ctypes.c_int),
         "pichol_batch_create": ([ctypes.POINTER(Config), i32, i32, ctypes.POINTER(vp)], ctypes.c_int),
         "pichol_batch_workspace_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
         "pichol_batch_set_workspace": ([vp, vp, ctypes.c_size_t], ctypes.c_int),
@@ -233,6 +236,19 @@ class Context:
                "pichol_holdout_grad")
         return E, dE
 
+    def mchol(self, c: float, s: float, s_min: float, trace=True, stream=None):
+        """Multi-level range narrowing (pichol_mchol) after ``hessian``; the
+        grid then spans the final range, so ``factor_samples``, ``fit`` and
+        ``eval_holdout`` run piCholesky over it.  Returns the device trace
+        (levels x 8 float64: three lambdas, their mean errors, c, s) or None."""
+        import torch
+        levels = mchol_levels(s, s_min)
+        tr = torch.empty((levels, 8), dtype=torch.float64, device="cuda") if trace else None
+        _check(lib().pichol_mchol(self._h, float(c), float(s), float(s_min),
+                                  ctypes.c_void_p(tr.data_ptr() if tr is not None else 0),
+                                  ctypes.c_void_p(_stream_ptr(stream))), "pichol_mchol")
+        return tr
+
     # -- inspection ----------------------------------------------------------
     def lambdas(self, stream=None):
         import torch
@@ -317,6 +333,13 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def mchol_levels(s: float, s_min: float) -> int:
+    """Levels pichol_mchol runs from half-width s down to s_min."""
+    n = ctypes.c_int32(0)
+    _check(lib().pichol_mchol_levels(float(s), float(s_min), ctypes.byref(n)), "pichol_mchol_levels")
+    return int(n.value)
 
 
 def holdout_loss(ctx: "Context", log_lam):

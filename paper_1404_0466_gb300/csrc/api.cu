@@ -28,6 +28,7 @@ size_t plan(pichol_ctx* ctx, char* base)
     ctx->status = (DevStatus*)take(sizeof(DevStatus));
     ctx->scal = (double*)take(8 * sizeof(double));
     ctx->lam = (double*)take(q * sizeof(double));
+    ctx->mlam = (double*)take(8 * sizeof(double));
     ctx->lam_s = (double*)take(g * sizeof(double));
     ctx->pinv = (double*)take(p * g * sizeof(double));
     ctx->phi = (double*)take(q * p * sizeof(double));
@@ -239,6 +240,29 @@ pichol_status pichol_eval_holdout_exact(pichol_ctx* ctx, double* E_out, int32_t*
     if (e == cudaSuccess) e = launch_finish(ctx, E_out, t_star, s);
     if (e == cudaSuccess && W_out) e = launch_copy_w(ctx, W_out, s);
     return cuda_status(e);
+}
+
+pichol_status pichol_mchol_levels(double s, double s_min, int32_t* levels)
+{
+    if (!levels || !(s > 0.0) || !(s <= 300.0) || !(s_min > 0.0) || !(s_min <= 300.0)) return PICHOL_ERR_INVALID_ARG;
+    const int n = mchol_levels(s, s_min);
+    if (n > 64) return PICHOL_ERR_INVALID_ARG;
+    *levels = n;
+    return PICHOL_OK;
+}
+
+pichol_status pichol_mchol(pichol_ctx* ctx, double c, double s, double s_min, double* trace_out, void* stream)
+{
+    int32_t levels = 0;
+    if (!ctx || !(c >= -300.0 && c <= 300.0)) return PICHOL_ERR_INVALID_ARG;
+    pichol_status st = pichol_mchol_levels(s, s_min, &levels);
+    if (st != PICHOL_OK) return st;
+    if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
+    if (!ctx->have_hessian) return PICHOL_ERR_STATE;
+    if (ctx->cfg.q < 3) return PICHOL_ERR_UNSUPPORTED;
+    st = cuda_status(launch_mchol(ctx, c, s, levels, trace_out, (cudaStream_t)stream));
+    ctx->have_factors = ctx->have_fit = false;   // the factor buffer was reused; the grid moved
+    return st;
 }
 
 pichol_status pichol_holdout_grad(pichol_ctx* ctx, double log_lam, double* E_out, double* dE_out, void* stream)

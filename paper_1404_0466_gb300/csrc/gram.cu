@@ -239,10 +239,14 @@ __device__ inline void basis_eval(int basis, int p, double lam, double a, double
 
 __global__ void __launch_bounds__(256)
 k_setup(const void* G, int mode_fp64, int64_t d, int64_t dp, int k, int g, int p, int q,
-        double lo, double hi, int scale_by_trace, int basis,
+        double lo, double hi, const double* __restrict__ window, int scale_by_trace, int basis,
         double* scal, double* lam, double* lam_s, double* pinv, double* phi, double* dphi,
         DevStatus* st)
 {
+    if (window) {
+        lo = window[0];
+        hi = window[1];
+    }
     __shared__ double red[256];
     __shared__ double shared_ab[3];
     double s = 0.0;
@@ -263,7 +267,8 @@ k_setup(const void* G, int mode_fp64, int64_t d, int64_t dp, int k, int g, int p
         lam[t] = (q == 1) ? tau * lo : tau * lo * pow(hi / lo, (double)t / (double)(q - 1));
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (!(tau > 0.0) || isinf(tau)) latch_error(st, PICHOL_ERR_INVALID_ARG, -1, -1, -1);
+        if (!(tau > 0.0) || isinf(tau) || !(lo > 0.0) || !(hi >= lo) || isinf(hi))
+            latch_error(st, PICHOL_ERR_INVALID_ARG, -1, -1, -1);
         scal[0] = tau;
         for (int i = 0; i < g; ++i) {
             const int idx = (g == 1) ? 0 : (2 * i * (q - 1) + (g - 1)) / (2 * (g - 1));
@@ -361,12 +366,7 @@ static cudaError_t gram_impl(pichol_ctx* ctx, const T* X, const T* Y, cudaStream
         StageScope sc_(ctx, ST_MISC, s);
         k_yy<T><<<c.k, 256, 0, s>>>(Y, c.c, fo, ctx->yy, ctx->nfc);
     }
-    {
-        StageScope sc_(ctx, ST_SETUP, s);
-        k_setup<<<1, 256, 0, s>>>(G, c.mode == PICHOL_MODE_FP64, c.d, ctx->dp, c.k, c.g, ctx->p, c.q,
-                                  c.lam_lo, c.lam_hi, c.scale_by_trace, c.basis, ctx->scal, ctx->lam,
-                                  ctx->lam_s, ctx->pinv, ctx->phi, ctx->dphi, ctx->status);
-    }
+    if ((e = launch_setup(ctx, nullptr, s)) != cudaSuccess) return e;
     const int64_t len = ctx->dp * c.c;
     if constexpr (std::is_same<T, float>::value) {
         StageScope sc_(ctx, ST_XTY, s);
@@ -379,7 +379,20 @@ static cudaError_t gram_impl(pichol_ctx* ctx, const T* X, const T* Y, cudaStream
         StageScope sc_(ctx, ST_MISC, s);
         k_hf_tiles<T><<<dim3((unsigned)ctx->ntiles, c.k), 256, 0, s>>>(G, c.k, ctx->dp, ctx->ntiles, (T*)ctx->Hf);
     }
-    ctx->launches += 7;
+    ctx->launches += 6;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_setup(pichol_ctx* ctx, const double* window, cudaStream_t s)
+{
+    const pichol_config& c = ctx->cfg;
+    {
+        StageScope sc_(ctx, ST_SETUP, s);
+        k_setup<<<1, 256, 0, s>>>(ctx->G, c.mode == PICHOL_MODE_FP64, c.d, ctx->dp, c.k, c.g, ctx->p, c.q,
+                                  c.lam_lo, c.lam_hi, window, c.scale_by_trace, c.basis, ctx->scal, ctx->lam,
+                                  ctx->lam_s, ctx->pinv, ctx->phi, ctx->dphi, ctx->status);
+    }
+    ctx->launches++;
     return cudaGetLastError();
 }
 

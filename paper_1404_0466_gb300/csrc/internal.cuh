@@ -108,6 +108,7 @@ struct pichol_ctx {
     pichol::DevStatus* status;
     double* scal;        // [0] tau
     double* lam;         // q
+    double* mlam;        // MChol state: [0..2] the level's lambdas, [4] c, [5] s, [6..7] final window
     double* lam_s;       // g
     double* pinv;        // p x g
     double* phi;         // q x p
@@ -224,5 +225,10 @@ cudaError_t launch_score_tc(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s)
 cudaError_t launch_gall_split(pichol_ctx* ctx, cudaStream_t s);
 cudaError_t launch_wait_check(pichol_ctx* ctx, long long limit, cudaStream_t s);
 cudaError_t launch_resid_exact(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s);
+// grid, samples and V^+ from the Gram blocks; window (device, nullable) holds
+// (lo, hi) replacing the configured range
+cudaError_t launch_setup(pichol_ctx* ctx, const double* window, cudaStream_t s);
+cudaError_t launch_mchol(pichol_ctx* ctx, double c, double s, int levels, double* trace_out, cudaStream_t st);
+int mchol_levels(double s, double s_min);
 
 }  // namespace pichol

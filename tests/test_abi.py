@@ -141,3 +141,22 @@ def test_tuning_defaults_and_validation(L):
     assert L.pichol_get_tuning(h, ctypes.byref(t)) == 0
     assert (t.update_strip, t.diag_threads, t.diag_exclusive) == (2, 256, 0)
     L.pichol_destroy(h)
+
+
+def test_mchol_levels_and_argument_checks(L):
+    """Level counts (the paper's s = 1.5, s0 = 0.0025 give ten) and the checks
+    pichol_mchol makes before any CUDA call."""
+    n = ctypes.c_int32()
+    for s, s_min, want in [(1.5, 0.0025, 10), (1.5, 0.1, 4), (1.5, 0.75, 1), (0.1, 0.2, 1), (1.0, 0.5, 1)]:
+        assert L.pichol_mchol_levels(s, s_min, ctypes.byref(n)) == 0
+        assert n.value == want, (s, s_min)
+    for s, s_min in [(0.0, 0.1), (-1.0, 0.1), (1.0, 0.0), (float("nan"), 0.1), (1.0, float("inf")),
+                     (300.0, 1e-30)]:                   # the last needs more than 64 levels
+        assert L.pichol_mchol_levels(s, s_min, ctypes.byref(n)) == 1, (s, s_min)
+    assert L.pichol_mchol_levels(1.0, 0.1, None) == 1
+    rc, h = _create(L, _cfg(L))
+    assert L.pichol_mchol(h, float("nan"), 1.0, 0.1, None, None) == 1
+    assert L.pichol_mchol(h, 0.0, 1.0, 0.0, None, None) == 1
+    assert L.pichol_mchol(h, 0.0, 1.0, 0.1, None, None) == 4      # no workspace yet
+    assert L.pichol_mchol(None, 0.0, 1.0, 0.1, None, None) == 1
+    L.pichol_destroy(h)

@@ -15,7 +15,10 @@ Also reported: the same metric end to end from pinned host buffers (e2e),
 exact-Cholesky cross-validation with the same kernels on the same GPU, the
 error of the hold-out scores against the FP64 oracle on a sample, per-stage
 device times, the roofline of the dominant kernel, SM clocks during the timed
-region, and the oracle timed on the host cores (cpu_baseline).
+region, the oracle timed on the host cores (cpu_baseline), and MChol
+(Sec. 6.2) on the same data: alone at the paper's stopping width, and as the
+range narrowing before piCholesky, each timed and compared with exact CV's
+selected lambda.
 
 Workloads: mixed_ecc (default: n = 32768, d = 2048, c = 10, k = 5, g = 6,
 r = 3, q = 101, mixed precision, one refinement step against the interpolated
@@ -73,6 +76,7 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="mixed_ecc")
     ap.add_argument("--refine", type=int, default=None, help="refinement steps (default: the workload's)")
     ap.add_argument("--no-exact", action="store_true", help="skip the exact-Cholesky comparison")
+    ap.add_argument("--no-mchol", action="store_true", help="skip the MChol comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle sample (cpu_baseline, error)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time eager calls instead of one CUDA graph per step")
@@ -540,6 +544,90 @@ def run_batched(args):
     return 0
 
 
+def mchol_compare(binding, params, cfg, X, Y, stream, exact, E, t_star):
+    """MChol over the workload's range [lo, hi] tau (c = the range's centre in
+    log10, s = its half-width), timed from the normal-equation blocks on:
+      * alone at the paper's stopping width s0 = 0.0025 (Sec. 6.3), the
+        selected lambda being the last level's winner;
+      * narrowed to a half-width of at most 0.1 decade, then piCholesky over
+        that range with the workload's g, r, q.
+    Each selection is compared with exact CV's (and piCholesky's over the full
+    range) as |log10(lambda / lambda_exact)|, the accuracy measure of the
+    paper's accuracy-versus-time figure."""
+    import math
+
+    import numpy as np
+    import torch
+    c0 = 0.5 * (math.log10(cfg["lo"]) + math.log10(cfg["hi"]))
+    s0 = 0.5 * (math.log10(cfg["hi"]) - math.log10(cfg["lo"]))
+    ctx = binding.Context(**params)
+    out = ctx._outputs(False)
+    lam_grid = None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {"c": c0, "s": s0}
+
+    def timed(fn, reps=2):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for name, s_min, with_pichol in (("alone", 0.0025, False), ("then_pichol", 0.1, True)):
+        tr = None
+
+        def run():
+            nonlocal tr
+            ctx.hessian(X, Y)
+            tr = ctx.mchol(c0, s0, s_min)
+            if with_pichol:
+                ctx.factor_samples()
+                ctx.fit()
+                ctx.eval_holdout(out=out)
+
+        ms = timed(run)
+        info = ctx.info()
+        trh = tr.cpu().numpy()
+        tau = float(trh[0, 1] / 10.0 ** c0)
+        last = trh[-1]
+        best = int(np.argmin(last[3:6]))
+        entry = {"ms": ms, "levels": int(trh.shape[0]), "s_min": s_min,
+                 "exact_factorisations": int(trh.shape[0]) * 3 * cfg["k"],
+                 "lambda_rel": float(last[best] / tau), "Ebar": float(last[3 + best]),
+                 "device_status": binding.STATUS.get(info.code)}
+        if with_pichol:
+            lam = ctx.lambdas().cpu().numpy()
+            Ew = out[0].cpu().numpy()
+            tw = int(out[1].cpu().item())
+            entry.update({"window_rel": [float(lam[0] / tau), float(lam[-1] / tau)],
+                          "t_star": tw, "lambda_rel": float(lam[tw] / tau) if tw >= 0 else None,
+                          "Ebar": float(Ew.mean(axis=0)[tw]) if tw >= 0 else None,
+                          "evals": cfg["k"] * cfg["q"] + int(trh.shape[0]) * 3 * cfg["k"]})
+        res[name] = entry
+    # the full-range grid, for the comparisons below
+    ctx.hessian(X, Y)
+    lam_grid = ctx.lambdas().cpu().numpy()
+    tau = float(lam_grid[0] / cfg["lo"])
+    torch.cuda.synchronize()
+    ctx.close()
+    ref = []
+    if exact:
+        ref.append(("exact", float(lam_grid[exact["t_star"]] / tau)))
+    if t_star >= 0:
+        ref.append(("pichol_full_range", float(lam_grid[t_star] / tau)))
+    for name in ("alone", "then_pichol"):
+        lr = res[name]["lambda_rel"]
+        for rn, rl in ref:
+            res[name][f"abs_log10_vs_{rn}"] = abs(math.log10(lr / rl)) if lr else None
+    if exact:
+        res["exact_ms"] = exact["ms_per_step"]
+        res["exact_min_Ebar"] = exact["min_E_exact"]
+    return res
+
+
 def run_own(args):
     import numpy as np
     import torch
@@ -760,6 +848,11 @@ def run_own(args):
                                        if exact["min_E_pichol"] is not None else None)
         ctxe.close()
 
+    # ---- MChol (Sec. 6.2), alone and as the range for piCholesky ----------
+    mchol = None
+    if not args.no_mchol and rank == 0:
+        mchol = mchol_compare(binding, params, cfg, X, Y, stream, exact, E, t_star)
+
     if rank != 0:
         return 0
     sample = None if args.no_cpu else oracle_sample(prob, cfg, w, E, t_star)
@@ -789,6 +882,7 @@ def run_own(args):
         "clocks": clocks,
         "exact_cv": exact,
         "speedup_vs_exact": (value / world / exact["value"]) if exact else None,
+        "mchol": mchol,
         "device_status": binding.STATUS.get(info.code), "unusable_pairs": info.unusable,
     }
     if sample:

@@ -267,6 +267,14 @@ PICHOL_API pichol_status pichol_clear_status(pichol_ctx* ctx, void* stream);
  * context is usable as before.  For tests of failure detection. */
 PICHOL_API pichol_status pichol_check_timeout(pichol_ctx* ctx, int64_t cycles, void* stream);
 
+/* Accuracy check of the double-precision 1/sqrt used for the pivots of the
+ * diagonal tiles (a float seed refined by one third-order step, see chol.cu):
+ * writes to *max_rel_err (device, one double) the largest relative difference
+ * from the library's 1.0 / sqrt(p) over n values p = 2^u, u uniform in
+ * [-110, 110) from a splitmix64 stream started at `seed`.  1 <= n <= 2^32.
+ * Needs no context.  For tests. */
+PICHOL_API pichol_status pichol_check_rsqrt(int64_t n, uint64_t seed, double* max_rel_err, void* stream);
+
 /* Number of kernel launches this context has enqueued since creation. */
 PICHOL_API int64_t pichol_launch_count(const pichol_ctx* ctx);
 

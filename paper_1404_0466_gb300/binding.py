@@ -34,7 +34,7 @@ EXPORTS = [
     "pichol_batch_run", "pichol_batch_get_info", "pichol_batch_launch_count", "pichol_batch_destroy",
     "pichol_batch_set_timing", "pichol_batch_stage_times",
     "pichol_get_tuning", "pichol_set_tuning", "pichol_batch_set_tuning", "pichol_check_timeout",
-    "pichol_mchol", "pichol_mchol_levels",
+    "pichol_mchol", "pichol_mchol_levels", "pichol_check_rsqrt",
 ]
 STAGES = ["gram", "xty", "setup", "chol_init", "chol_diag", "chol_panel", "chol_update", "fit",
           "diag_inv", "solve", "resid", "score", "select", "misc"]
@@ -101,6 +101,7 @@ def lib():
         "pichol_holdout_grad": ([vp, ctypes.c_double, vp, vp, vp], ctypes.c_int),
         "pichol_mchol": ([vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, vp], ctypes.c_int),
         "pichol_mchol_levels": ([ctypes.c_double, ctypes.c_double, ctypes.POINTER(i32)], ctypes.c_int),
+        "pichol_check_rsqrt": ([i64, ctypes.c_uint64, vp, vp], ctypes.c_int),
         "pichol_batch_create": ([ctypes.POINTER(Config), i32, i32, ctypes.POINTER(vp)], ctypes.c_int),
         "pichol_batch_workspace_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
         "pichol_batch_set_workspace": ([vp, vp, ctypes.c_size_t], ctypes.c_int),
@@ -333,6 +334,16 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def check_rsqrt(n: int, seed: int = 1, stream=None) -> float:
+    """Largest relative difference of the pivots' 1/sqrt from the library's
+    1 / sqrt over n sampled values (pichol_check_rsqrt)."""
+    import torch
+    out = torch.empty((1,), dtype=torch.float64, device="cuda")
+    _check(lib().pichol_check_rsqrt(int(n), int(seed), ctypes.c_void_p(out.data_ptr()),
+                                    ctypes.c_void_p(_stream_ptr(stream))), "pichol_check_rsqrt")
+    return float(out.cpu().item())
 
 
 def mchol_levels(s: float, s_min: float) -> int:

@@ -340,6 +340,12 @@ pichol_status pichol_clear_status(pichol_ctx* ctx, void* stream)
     return cuda_status(cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), (cudaStream_t)stream));
 }
 
+pichol_status pichol_check_rsqrt(int64_t n, uint64_t seed, double* max_rel_err, void* stream)
+{
+    if (n < 1 || n > ((int64_t)1 << 32) || !max_rel_err) return PICHOL_ERR_INVALID_ARG;
+    return cuda_status(launch_check_rsqrt(n, seed, max_rel_err, (cudaStream_t)stream));
+}
+
 int64_t pichol_launch_count(const pichol_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 static void free_timing(pichol_ctx* ctx)

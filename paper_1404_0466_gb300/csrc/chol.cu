@@ -54,55 +54,79 @@ k_chol_init(const T* __restrict__ Hf, int64_t d, int64_t ntiles, ProbMap pm,
     }
 }
 
-// 1/sqrt(p) by Newton-Raphson, y <- y + (y/2)(1 - p y^2), each step roughly
-// doubling the correct bits, seeded with the single-precision rsqrtf (about 22
-// bits): two steps reach double precision.  Outside the seed's range the
-// quotient of the library square root is used.
-__device__ __forceinline__ double rsqrt_newton(double p)
+// 1/sqrt(p) in double precision with few FP64 instructions.  GB300 issues one
+// FP64 warp instruction per 64 cycles on each SM sub-partition, so the pivot
+// chain of the diagonal tiles is counted in FP64 instructions:
+//  * seed: the float with p's exponent and top 20 mantissa bits (integer
+//    arithmetic on the high word), rsqrtf of it (relative error below 2^-20
+//    in all), widened back to double exactly by integer arithmetic;
+//  * one third-order step from the binomial series of (1 - r)^(-1/2):
+//    y1 = y + y r (1/2 + 3r/8), r = 1 - p y^2, which cubes the seed's error
+//    (5/16 e^3 < 2^-62) and leaves the rounding of five FP64 operations.
+// Outside [2^-99, 2^100) (and for NaN or p <= 0) the library quotient is used.
+__device__ __forceinline__ bool rsqrt_seed_range(int hi) { return hi >= (924 << 20) && hi < (1123 << 20); }
+
+__device__ __forceinline__ double rsqrt_cubic(double p)
 {
-    if (!(p > 1e-30 && p < 1e30)) return 1.0 / sqrt(p);
-    double y = (double)rsqrtf((float)p);
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        const double r = fma(-p * y, y, 1.0);
-        y = fma(0.5 * y, r, y);
-    }
-    return y;
+    const int hi = __double2hiint(p);
+    if (!rsqrt_seed_range(hi)) return 1.0 / sqrt(p);
+    const float pf = __int_as_float((hi - 0x38000000) << 3);       // exponent 1023 -> 127
+    const int fb = __float_as_int(rsqrtf(pf));
+    const double y = __hiloint2double((fb >> 3) + 0x38000000, fb << 29);
+    const double r = fma(-p * y, y, 1.0);
+    return fma(y * r, fma(r, 0.375, 0.5), y);
 }
 
-// Pivot of column j of the diagonal tile: L_jj = sqrt(a_jj), 1 / L_jj kept in yinv[j].
-__device__ __forceinline__ void take_pivot(double (*A)[TB + 1], double* yinv, int j, int J, int64_t d,
-                                           const ProbMap& pm, int pr, DevStatus* st)
+// Largest relative difference between rsqrt_cubic and the library's 1 / sqrt
+// over n values p = 2^u, u uniform in [-110, 110) from a splitmix64 stream
+// (covers the seeded range and both fallbacks); one value per thread and
+// grid-stride step, the maximum reduced with an atomic on the bit pattern
+// (non-negative doubles order like their bits).
+__global__ void k_check_rsqrt(int64_t n, uint64_t seed, unsigned long long* out)
 {
-    double piv = A[j][j];
-    if (!(piv > 0.0)) {
-        if ((int64_t)J * TB + j < d)
-            latch_error(st, PICHOL_ERR_NOT_SPD, pr / pm.per, pm.exact ? pm.t0 + pr % pm.per : pr % pm.per,
-                        (long long)J * TB + j);
-        piv = 1.0;
+    double mx = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(i + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const double u = (double)(z >> 11) * 0x1.0p-53;
+        const double p = exp2(-110.0 + 220.0 * u);
+        const double ref = 1.0 / sqrt(p);
+        mx = fmax(mx, fabs(rsqrt_cubic(p) - ref) / ref);
     }
-    const double y = rsqrt_newton(piv);
-    A[j][j] = piv * y;
-    yinv[j] = y;
+    atomicMax(out, (unsigned long long)__double_as_longlong(mx));
 }
 
-// One CTA of DNT threads per problem: factor the 64 x 64 diagonal tile in
-// double precision, right-looking inside the tile.  Column j: scale it by
-// 1 / L_jj, then the rank-1 update of the trailing triangle
-// {(i, c) : j < c <= i}.  The lower triangle is listed column by column in
-// `tab`, so each trailing triangle is a suffix of the list that the threads
-// share evenly; its first element is (j+1, j+1), which thread 0 updates first
-// and then turns into the next pivot while the other threads are still
-// updating (with PIVOT_ALONE, thread 0 takes that element only).
-template <typename T, int DNT, bool PIVOT_ALONE>
+cudaError_t launch_check_rsqrt(int64_t n, uint64_t seed, double* max_rel, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(max_rel, 0, sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    k_check_rsqrt<<<152, 256, 0, s>>>(n, seed, (unsigned long long*)max_rel);
+    return cudaGetLastError();
+}
+
+// One CTA of DNT threads per problem: the 64 x 64 diagonal tile in double
+// precision, right-looking with a look-ahead of one column.  In phase t:
+//  * warp 0 finishes column t (pivot L_tt = sqrt(a_tt), column scaled by
+//    1 / L_tt) and brings column t+1 up to date (the updates by columns t-1
+//    and t), so pivot t+1 is ready at the next phase;
+//  * the bulk warps apply column t-1 to the trailing columns >= t+2.
+// One barrier per phase; every element receives its updates in column order,
+// as in the plain right-looking loop.  Warp 0's sub-partition takes no bulk
+// work (warps 4, 8, ... stay idle), so its FP64 unit serves the pivot chain
+// alone.  The lower triangle is listed column by column in `tab`, so each
+// trailing set is a suffix of the list that the bulk threads share evenly.
+template <typename T, int DNT, int ILP>
 __global__ void __launch_bounds__(DNT)
 k_chol_diag(T* __restrict__ F, int64_t ntiles, int J, int64_t d, ProbMap pm, DevStatus* st)
 {
     constexpr int NTRI = TB * (TB + 1) / 2;
+    constexpr int NW = DNT / 32;
+    constexpr int NB = NW - (NW + 3) / 4;       // bulk warps: those off sub-partition 0
     __shared__ double A[TB][TB + 1];
-    __shared__ double yinv[TB];
     __shared__ unsigned short tab[NTRI];
-    const int pr = blockIdx.x, tid = threadIdx.x;
+    const int pr = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (prob_dead(pm, pr)) return;
     T* tile = F + ((int64_t)pr * ntiles + tile_index(J, J)) * TILE_ELEMS;
     for (int e = tid; e < TILE_ELEMS; e += DNT) {
@@ -111,34 +135,59 @@ k_chol_diag(T* __restrict__ F, int64_t ntiles, int J, int64_t d, ProbMap pm, Dev
         // column c starts at c TB - c (c - 1) / 2 in the list
         if (c <= r) tab[c * TB - c * (c - 1) / 2 + (r - c)] = (unsigned short)((r << 8) | c);
     }
+    const int brank = (warp % 4 != 0) ? warp - warp / 4 - 1 : -1;
     __syncthreads();
-    if (tid == 0) take_pivot(A, yinv, 0, J, d, pm, pr, st);
-    for (int j = 0; j < TB - 1; ++j) {
-        __syncthreads();                                  // pivot j and column j final
-        for (int i = j + 1 + tid; i < TB; i += DNT) A[i][j] *= yinv[j];
-        __syncthreads();
-        const int e0 = (j + 1) * TB - (j + 1) * j / 2;
-        if (PIVOT_ALONE) {
-            if (tid == 0) {
-                A[j + 1][j + 1] = fma(-A[j + 1][j], A[j + 1][j], A[j + 1][j + 1]);
-                take_pivot(A, yinv, j + 1, J, d, pm, pr, st);
-            } else {
-                for (int e = e0 + tid; e < NTRI; e += DNT - 1) {
-                    const int ic = tab[e];
-                    const int i = ic >> 8, c = ic & 255;
-                    A[i][c] = fma(-A[i][j], A[c][j], A[i][c]);
+    for (int t = 0; t < TB; ++t) {
+        if (warp == 0) {
+            double piv = A[t][t];
+            if (!(piv > 0.0)) {
+                if (lane == 0 && (int64_t)J * TB + t < d)
+                    latch_error(st, PICHOL_ERR_NOT_SPD, pr / pm.per, pm.exact ? pm.t0 + pr % pm.per : pr % pm.per,
+                                (long long)J * TB + t);
+                piv = 1.0;
+            }
+            const double y = rsqrt_cubic(piv);       // every lane: no broadcast needed
+            __syncwarp();
+            if (lane == 0) A[t][t] = piv * y;
+            for (int i = t + 1 + lane; i < TB; i += 32) A[i][t] *= y;
+            __syncwarp();
+            if (t + 1 < TB) {
+                const double a1 = (t > 0) ? A[t + 1][t - 1] : 0.0;
+                const double a2 = A[t + 1][t];
+                for (int i = t + 1 + lane; i < TB; i += 32) {
+                    double v = A[i][t + 1];
+                    if (t > 0) v = fma(-A[i][t - 1], a1, v);
+                    v = fma(-A[i][t], a2, v);
+                    A[i][t + 1] = v;
                 }
             }
-        } else {
-            for (int e = e0 + tid; e < NTRI; e += DNT) {
-                const int ic = tab[e];
-                const int i = ic >> 8, c = ic & 255;
-                A[i][c] = fma(-A[i][j], A[c][j], A[i][c]);
-                if (e == e0) take_pivot(A, yinv, j + 1, J, d, pm, pr, st);
+        } else if (brank >= 0 && t >= 1) {
+            const int j = t - 1;
+            const int e0 = (t + 2) * TB - (t + 2) * (t + 1) / 2;   // column t+2 onwards
+            for (int eb = e0 + brank * 32 + lane; eb < NTRI; eb += NB * 32 * ILP) {
+                double a[ILP], b[ILP], c[ILP];
+                int ii[ILP], cc[ILP];
+#pragma unroll
+                for (int u = 0; u < ILP; ++u) {
+                    const int e = eb + u * NB * 32;
+                    ii[u] = -1;
+                    cc[u] = 0;
+                    if (e < NTRI) {
+                        const int ic = tab[e];
+                        ii[u] = ic >> 8;
+                        cc[u] = ic & 255;
+                        a[u] = A[ii[u]][j];
+                        b[u] = A[cc[u]][j];
+                        c[u] = A[ii[u]][cc[u]];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < ILP; ++u)
+                    if (ii[u] >= 0) A[ii[u]][cc[u]] = fma(-a[u], b[u], c[u]);
             }
         }
+        __syncthreads();
     }
-    __syncthreads();
     for (int e = tid; e < TILE_ELEMS; e += DNT) {
         const int r = e / TB, c = e % TB;
         tile[e] = (c <= r) ? (T)A[r][c] : T(0);
@@ -335,10 +384,10 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
         cudaError_t e = cudaFuncSetAttribute(k_chol_update<T, UNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sm_mm);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_chol_diag<T, 512, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(k_chol_diag<T, 512, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      DIAG_RESERVE);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_chol_diag<T, 256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(k_chol_diag<T, 256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      DIAG_RESERVE);
         if (e != cudaSuccess) return e;
         attr_done = true;
@@ -369,9 +418,9 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
         {
             StageScope sc_(ctx, ST_CHOL_DIAG, sh);
             if (ctx->tune.diag_threads == 256)
-                k_chol_diag<T, 256, true><<<nprob, 256, diag_smem, sh>>>(F, ctx->ntiles, J, c.d, pm, ctx->status);
+                k_chol_diag<T, 256, 1><<<nprob, 256, diag_smem, sh>>>(F, ctx->ntiles, J, c.d, pm, ctx->status);
             else
-                k_chol_diag<T, 512, true><<<nprob, 512, diag_smem, sh>>>(F, ctx->ntiles, J, c.d, pm, ctx->status);
+                k_chol_diag<T, 512, 2><<<nprob, 512, diag_smem, sh>>>(F, ctx->ntiles, J, c.d, pm, ctx->status);
         }
         ctx->launches++;
         const int m = ctx->nt - 1 - J;

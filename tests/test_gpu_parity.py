@@ -312,3 +312,12 @@ def test_mixed_hessian_on_tensor_cores(torch_mod, n, d, passes):
         errb = np.max(np.abs(B.cpu().numpy() - Br)) / np.max(np.abs(Br))
         assert errb <= tol, (f, errb)
     assert ctx.info().code == 0
+
+
+def test_pivot_rsqrt_matches_library_within_a_few_ulps(torch_mod):
+    """The pivots' 1/sqrt (float seed from the high word, one third-order step)
+    against the library's 1.0 / sqrt on 2^22 values spread over 2^-110..2^110
+    (seeded range and both fallbacks): within 4 units of 2^-53 relative."""
+    from paper_1404_0466_gb300 import binding
+    err = binding.check_rsqrt(1 << 22, seed=3)
+    assert 0.0 <= err <= 4 * 2.0 ** -53, err

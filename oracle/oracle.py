@@ -590,3 +590,44 @@ def mchol(X, Y, *, k: int, c: float, s: float, s_min: float, scale_by_trace: boo
     the final window by ``cv(..., lo=window[0], hi=window[1])``."""
     tau = trace_scale(X) if scale_by_trace else 1.0
     return mchol_search(lambda lams: holdout_exact_at(X, Y, k=k, lams=lams).mean(axis=0), c, s, s_min, tau)
+
+
+# ----------------------------------------------------------------------------
+# PINRMSE: interpolating the sampled hold-out errors directly
+# ----------------------------------------------------------------------------
+
+def pinrmse(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e1,
+            basis: str = BASIS_MONO, scale_by_trace: bool = True, folds=None) -> CVResult:
+    """PINRMSE, the comparator of the paper's supplementary section: Algorithm
+    1 with the g x D target matrix T replaced by the g x 1 vector t_f of exact
+    hold-out errors at the sampled lambdas, so the fitted polynomial is the
+    hold-out error itself: theta_f = argmin ||t_f - V theta||, then
+    E[f, t] = phi(lambda_t) . theta_f on the whole grid.  Same grid, samples
+    and basis as ``cv``.  A fold with a non-finite sampled error scores +inf
+    everywhere."""
+    X, Y = _f64(X), _f64(Y)
+    n, d = X.shape
+    p = r + 1
+    if not (g > r):
+        raise ValueError("PINRMSE needs g > r sampled lambdas (Algorithm 1)")
+    tau = trace_scale(X) if scale_by_trace else 1.0
+    lam = lambda_grid(tau, q, lo, hi)
+    sidx = sample_indices(q, g)
+    lam_s = lam[sidx]
+    V = basis_values(basis, lam_s, lam_s, p)
+    Phi = basis_values(basis, lam, lam_s, p)
+    folds = list(range(k)) if folds is None else list(folds)
+    t = holdout_exact_at(X, Y, k=k, lams=lam_s, folds=folds)          # k x g
+    E = np.full((k, q), np.nan)
+    for f in folds:
+        if not np.all(np.isfinite(t[f])):
+            E[f] = np.inf
+            continue
+        theta = lstsq(V, t[f][:, None])[:, 0]
+        E[f] = Phi @ theta
+    res = CVResult(lam=lam, sample_idx=sidx, E=E, Ebar=None, t_star=-1,
+                   unusable=np.zeros((k, q), dtype=bool), tau=tau)
+    if len(folds) == k:
+        res.Ebar = E.mean(axis=0)
+        res.t_star = argmin_first(res.Ebar)
+    return res

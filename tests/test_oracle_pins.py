@@ -589,3 +589,60 @@ def test_mchol_on_data_finds_the_dense_scan_minimum():
         assert abs(res.lams[lv][1] / prev - 1.0) < 1e-12
     lo, hi = res.window
     assert abs(np.log10(hi / lo) - 2 * res.s) < 1e-12
+
+
+# ----------------------------------------------------------------------------
+# PINRMSE (supplementary comparator): the hold-out error interpolated directly
+# ----------------------------------------------------------------------------
+
+def test_pinrmse_matches_a_library_polynomial_fit_of_the_exact_errors():
+    """With monomials the fitted curve is numpy's least-squares polynomial in
+    lambda / max lambda_s through the exact errors at the sampled grid points."""
+    p = synth.spectral_gaussian(200, 10, 2, seed=91)
+    k, g, r, q = 4, 6, 2, 25
+    res = orc.pinrmse(p.X, p.Y, k=k, g=g, r=r, q=q, basis="mono")
+    tau = np.trace(p.X.T @ p.X) / 10
+    lam = tau * 1e-3 * 1e4 ** (np.arange(q) / (q - 1))
+    sidx = [round(i * (q - 1) / (g - 1) + 1e-9) for i in range(g)]
+    assert sidx == orc.sample_indices(q, g)
+    offs = orc.fold_offsets(200, k)
+    for f in range(k):
+        keep = np.r_[0:offs[f], offs[f + 1]:200]
+        H, B = p.X[keep].T @ p.X[keep], p.X[keep].T @ p.Y[keep]
+        Xv, Yv = p.X[offs[f]:offs[f + 1]], p.Y[offs[f]:offs[f + 1]]
+        ts = [np.mean((Yv - Xv @ np.linalg.solve(H + lam[i] * np.eye(10), B)) ** 2) for i in sidx]
+        x = lam / lam[sidx].max()
+        coef = np.polyfit(x[sidx], ts, r)
+        np.testing.assert_allclose(res.E[f], np.polyval(coef, x), rtol=1e-8, atol=1e-12)
+
+
+@pytest.mark.parametrize("basis", ["mono", "cheb_log"])
+def test_pinrmse_reproduces_the_exact_errors_at_the_nodes(basis):
+    """g = r + 1: the polynomial interpolates, so at the sampled grid points
+    PINRMSE equals exact CV; with every grid point a node it is exact CV."""
+    p = synth.spectral_gaussian(160, 8, 2, seed=92)
+    ex = orc.cv(p.X, p.Y, k=4, g=1, r=0, q=9, exact=True)
+    res = orc.pinrmse(p.X, p.Y, k=4, g=5, r=4, q=9, basis=basis)
+    sidx = orc.sample_indices(9, 5)
+    np.testing.assert_allclose(res.E[:, sidx], ex.E[:, sidx], rtol=1e-9)
+    full = orc.pinrmse(p.X, p.Y, k=4, g=5, r=4, q=5, basis=basis)
+    ex5 = orc.cv(p.X, p.Y, k=4, g=1, r=0, q=5, exact=True)
+    np.testing.assert_allclose(full.E, ex5.E, rtol=1e-9)
+    assert full.t_star == ex5.t_star
+
+
+def test_pinrmse_is_the_fit_of_the_fold_mean_and_rejects_too_few_samples():
+    """The fit is linear in t, so the mean over folds of the interpolated errors
+    is the interpolation of the mean sampled error; g <= r is refused."""
+    p = synth.spectral_gaussian(150, 7, 1, seed=93)
+    k, g, r, q = 3, 5, 3, 17
+    res = orc.pinrmse(p.X, p.Y, k=k, g=g, r=r, q=q, basis="cheb_log")
+    tau = orc.trace_scale(p.X)
+    lam = orc.lambda_grid(tau, q, 1e-3, 1e1)
+    sidx = orc.sample_indices(q, g)
+    tbar = orc.holdout_exact_at(p.X, p.Y, k=k, lams=lam[sidx]).mean(axis=0)
+    V = orc.basis_values("cheb_log", lam[sidx], lam[sidx], r + 1)
+    Phi = orc.basis_values("cheb_log", lam, lam[sidx], r + 1)
+    np.testing.assert_allclose(res.Ebar, Phi @ np.linalg.lstsq(V, tbar, rcond=None)[0], rtol=1e-9)
+    with pytest.raises(ValueError):
+        orc.pinrmse(p.X, p.Y, k=k, g=3, r=3, q=q)

@@ -18,7 +18,8 @@ device times, the roofline of the dominant kernel, SM clocks during the timed
 region, the oracle timed on the host cores (cpu_baseline), and MChol
 (Sec. 6.2) on the same data: alone at the paper's stopping width, and as the
 range narrowing before piCholesky, each timed and compared with exact CV's
-selected lambda.
+selected lambda; and PINRMSE (the sampled hold-out errors interpolated
+directly) likewise.
 
 Workloads: mixed_ecc (default: n = 32768, d = 2048, c = 10, k = 5, g = 6,
 r = 3, q = 101, mixed precision, one refinement step against the interpolated
@@ -76,7 +77,7 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="mixed_ecc")
     ap.add_argument("--refine", type=int, default=None, help="refinement steps (default: the workload's)")
     ap.add_argument("--no-exact", action="store_true", help="skip the exact-Cholesky comparison")
-    ap.add_argument("--no-mchol", action="store_true", help="skip the MChol comparison")
+    ap.add_argument("--no-mchol", action="store_true", help="skip the MChol and PINRMSE comparisons")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle sample (cpu_baseline, error)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time eager calls instead of one CUDA graph per step")
@@ -628,6 +629,42 @@ def mchol_compare(binding, params, cfg, X, Y, stream, exact, E, t_star):
     return res
 
 
+def pinrmse_compare(binding, params, cfg, X, Y, stream, exact, t_star):
+    """PINRMSE (the supplementary comparator) on the same data: the exact
+    hold-out errors at the g sampled lambdas interpolated over the grid, timed
+    from the normal-equation blocks on, with its selection's distance from
+    exact CV's and piCholesky's in grid steps and decades."""
+    import math
+
+    import torch
+    ctx = binding.Context(**params)
+    out = ctx._outputs(False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def run():
+        ctx.hessian(X, Y)
+        ctx.factor_samples()
+        ctx.eval_pinrmse(out=out)
+
+    run()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(3):
+        run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 3
+    tp = int(out[1].cpu().item())
+    step = (math.log10(cfg["hi"]) - math.log10(cfg["lo"])) / (cfg["q"] - 1)
+    res = {"ms": ms, "t_star": tp, "device_status": binding.STATUS.get(ctx.info().code)}
+    for name, ref in (("exact", exact["t_star"] if exact else None), ("pichol", t_star if t_star >= 0 else None)):
+        if ref is not None and tp >= 0:
+            res[f"grid_steps_from_{name}"] = tp - ref
+            res[f"abs_log10_vs_{name}"] = abs(tp - ref) * step
+    ctx.close()
+    return res
+
+
 def run_own(args):
     import numpy as np
     import torch
@@ -848,10 +885,11 @@ def run_own(args):
                                        if exact["min_E_pichol"] is not None else None)
         ctxe.close()
 
-    # ---- MChol (Sec. 6.2), alone and as the range for piCholesky ----------
-    mchol = None
+    # ---- MChol (Sec. 6.2), alone and as the range for piCholesky; PINRMSE --
+    mchol = pinrmse = None
     if not args.no_mchol and rank == 0:
         mchol = mchol_compare(binding, params, cfg, X, Y, stream, exact, E, t_star)
+        pinrmse = pinrmse_compare(binding, params, cfg, X, Y, stream, exact, t_star)
 
     if rank != 0:
         return 0
@@ -883,6 +921,7 @@ def run_own(args):
         "exact_cv": exact,
         "speedup_vs_exact": (value / world / exact["value"]) if exact else None,
         "mchol": mchol,
+        "pinrmse": pinrmse,
         "device_status": binding.STATUS.get(info.code), "unusable_pairs": info.unusable,
     }
     if sample:

@@ -210,6 +210,22 @@ PICHOL_API pichol_status pichol_holdout_grad(pichol_ctx* ctx, double log_lam, do
                                              void* stream);
 
 /*
+ * PINRMSE, the comparator of the paper's supplementary material: Algorithm 1
+ * with the g x D target matrix T replaced by the g x 1 vector t_f of exact
+ * hold-out errors at the sampled lambdas.  After pichol_factor_samples, the
+ * sampled factors L_{f,s} are used for exact solves and scores, t_f[s] =
+ * ||Y_f - X_f W||^2 / (n_f c) with W = (L_{f,s} L_{f,s}^T)^{-1} B_f; then
+ * theta_f = V^+ t_f (the same V^+ as pichol_fit) and
+ *   E_out[f*q + t] = sum_m phi_m(lambda_t) theta_f[m],
+ * and *t_star = the smallest t minimising mean_f E_out[f*q + t] over finite
+ * values (-1 if none).  A fold with an unusable sampled factor scores +inf at
+ * every t (pichol_info.unusable counts such samples).  E_out: device, k*q
+ * doubles; t_star: device, one int32.  The sampled factors and the fit stay
+ * valid; the solution buffer of pichol_eval_holdout is reused.
+ */
+PICHOL_API pichol_status pichol_eval_pinrmse(pichol_ctx* ctx, double* E_out, int32_t* t_star, void* stream);
+
+/*
  * Multi-level narrowing of the lambda range (MChol, Sec. 6.2), then a new grid
  * on the final range.  Starting from (c, s), each level
  *   (a) evaluates the exact hold-out error of every fold at the three lambdas

@@ -34,7 +34,7 @@ EXPORTS = [
     "pichol_batch_run", "pichol_batch_get_info", "pichol_batch_launch_count", "pichol_batch_destroy",
     "pichol_batch_set_timing", "pichol_batch_stage_times",
     "pichol_get_tuning", "pichol_set_tuning", "pichol_batch_set_tuning", "pichol_check_timeout",
-    "pichol_mchol", "pichol_mchol_levels", "pichol_check_rsqrt",
+    "pichol_mchol", "pichol_mchol_levels", "pichol_check_rsqrt", "pichol_eval_pinrmse",
 ]
 STAGES = ["gram", "xty", "setup", "chol_init", "chol_diag", "chol_panel", "chol_update", "fit",
           "diag_inv", "solve", "resid", "score", "select", "misc"]
@@ -102,6 +102,7 @@ def lib():
         "pichol_mchol": ([vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, vp], ctypes.c_int),
         "pichol_mchol_levels": ([ctypes.c_double, ctypes.c_double, ctypes.POINTER(i32)], ctypes.c_int),
         "pichol_check_rsqrt": ([i64, ctypes.c_uint64, vp, vp], ctypes.c_int),
+        "pichol_eval_pinrmse": ([vp, vp, vp, vp], ctypes.c_int),
         "pichol_batch_create": ([ctypes.POINTER(Config), i32, i32, ctypes.POINTER(vp)], ctypes.c_int),
         "pichol_batch_workspace_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
         "pichol_batch_set_workspace": ([vp, vp, ctypes.c_size_t], ctypes.c_int),
@@ -236,6 +237,14 @@ class Context:
                                          ctypes.c_void_p(dE.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
                "pichol_holdout_grad")
         return E, dE
+
+    def eval_pinrmse(self, out=None, stream=None) -> CVOutput:
+        """PINRMSE after ``factor_samples``: the exact hold-out errors at the g
+        sampled lambdas interpolated over the grid (pichol_eval_pinrmse)."""
+        E, t, _ = out if out is not None else self._outputs(False)
+        _check(lib().pichol_eval_pinrmse(self._h, ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                         ctypes.c_void_p(_stream_ptr(stream))), "pichol_eval_pinrmse")
+        return CVOutput(E, t, None)
 
     def mchol(self, c: float, s: float, s_min: float, trace=True, stream=None):
         """Multi-level range narrowing (pichol_mchol) after ``hessian``; the

@@ -242,6 +242,14 @@ pichol_status pichol_eval_holdout_exact(pichol_ctx* ctx, double* E_out, int32_t*
     return cuda_status(e);
 }
 
+pichol_status pichol_eval_pinrmse(pichol_ctx* ctx, double* E_out, int32_t* t_star, void* stream)
+{
+    if (!ctx || !E_out || !t_star) return PICHOL_ERR_INVALID_ARG;
+    if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
+    if (!ctx->have_factors) return PICHOL_ERR_STATE;
+    return cuda_status(launch_pinrmse(ctx, E_out, t_star, (cudaStream_t)stream));
+}
+
 pichol_status pichol_mchol_levels(double s, double s_min, int32_t* levels)
 {
     if (!levels || !(s > 0.0) || !(s <= 300.0) || !(s_min > 0.0) || !(s_min <= 300.0)) return PICHOL_ERR_INVALID_ARG;

@@ -230,6 +230,7 @@ cudaError_t launch_resid_exact(pichol_ctx* ctx, int t0, int tcount, cudaStream_t
 cudaError_t launch_setup(pichol_ctx* ctx, const double* window, cudaStream_t s);
 cudaError_t launch_mchol(pichol_ctx* ctx, double c, double s, int levels, double* trace_out, cudaStream_t st);
 int mchol_levels(double s, double s_min);
+cudaError_t launch_pinrmse(pichol_ctx* ctx, double* E_out, int32_t* t_star, cudaStream_t s);
 cudaError_t launch_check_rsqrt(int64_t n, uint64_t seed, double* max_rel, cudaStream_t s);
 
 }  // namespace pichol

@@ -329,12 +329,13 @@ class CVResult:
     W: dict = field(default_factory=dict)         # (f, t) -> W (d x c)
     H: dict = field(default_factory=dict)         # f -> H_f
     B: dict = field(default_factory=dict)         # f -> B_f
+    warm_idx: list = field(default_factory=list)  # grid indices of the warm-start samples
 
 
 def cv(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e1,
        basis: str = BASIS_MONO, exact: bool = False, scale_by_trace: bool = True,
        folds=None, lam_idx=None, keep: bool = False, timings: dict | None = None,
-       precond_steps: int = 0) -> CVResult:
+       precond_steps: int = 0, warm: int = 0) -> CVResult:
     """k-fold CV of ridge regression over q lambdas, piCholesky (default) or
     exact Cholesky at every lambda (``exact=True``, ``Chol`` of Sec. 6.2).
 
@@ -342,6 +343,14 @@ def cv(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e
     interpolated solve with that many steps of iterative refinement against
     the exact system: R = B_f - (H_f + lambda I) W, W <- W + (L~ L~^T)^{-1} R,
     so the interpolated factor serves as a preconditioner.
+
+    ``warm`` = g' (2 <= g' <= g; piCholesky only; the paper's future-work
+    warm start, Sec. 7) fits fold 0 from its g sampled factors as above and
+    every other fold f from g' exact factors only, at the grid indices
+    round(i (q-1)/(g'-1)), starting from fold 0's coefficients:
+    Theta_f = Theta_0 + V'^+ (T'_f - V' Theta_0), where V' holds the first
+    p' = min(g', r+1) basis functions at those lambdas (the basis normalised
+    by fold 0's samples) and the remaining rows of Theta_f are fold 0's.
 
     ``folds`` restricts the work to some folds and ``lam_idx`` to some grid
     indices (entries outside are NaN); the grid, the samples and the fit are
@@ -360,6 +369,8 @@ def cv(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e
     p = r + 1
     if not exact and not (g > r):
         raise ValueError("piCholesky needs g > r sampled lambdas (Algorithm 1)")
+    if warm and (exact or not (2 <= warm <= g)):
+        raise ValueError("the warm start needs piCholesky and 2 <= warm <= g")
     offs = fold_offsets(n, k)
     tau = trace_scale(X) if scale_by_trace else 1.0
     lam = lambda_grid(tau, q, lo, hi)
@@ -371,6 +382,18 @@ def cv(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e
     E = np.full((k, q), np.nan)
     bad = np.zeros((k, q), dtype=bool)
     res = CVResult(lam=lam, sample_idx=sidx, E=E, Ebar=None, t_star=-1, unusable=bad, tau=tau)
+    theta0 = None
+    if warm:
+        # fold 0's coefficients start every other fold, whichever folds are asked for
+        H0, _ = normal_blocks(X, Y, offs[0], offs[1])
+        T0 = np.empty((g, d * (d + 1) // 2))
+        for s_ in range(g):
+            T0[s_] = vec_lower(cholesky(H0 + lam[sidx[s_]] * np.eye(d)))
+        theta0 = lstsq(basis_values(basis, lam[sidx], lam[sidx], p), T0)
+        widx = sample_indices(q, warm)
+        pw = min(warm, p)
+        Vw = basis_values(basis, lam[widx], lam[sidx], p)
+        res.warm_idx = widx
 
     for f in folds:
         _tf = _time.perf_counter()
@@ -392,17 +415,28 @@ def cv(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e
                 tm["eval"] += _time.perf_counter() - _te
                 tm["n_eval"] += 1
             continue
-        # Algorithm 1, steps 1-2: exact factors at the samples, stacked as rows of T
         lam_s = lam[sidx]
-        T = np.empty((g, d * (d + 1) // 2))
-        for s in range(g):
-            L = cholesky(Hf + lam_s[s] * np.eye(d))
-            T[s] = vec_lower(L)
-            if keep:
-                res.factors[(f, s)] = L
-        # steps 3-6: observation matrix and least-squares coefficients
-        V = basis_values(basis, lam_s, lam_s, p)
-        Theta = lstsq(V, T)
+        if warm and f > 0:
+            # warm start: g' exact factors, a degree-(p'-1) correction of fold 0's fit
+            Tw = np.empty((warm, d * (d + 1) // 2))
+            for s in range(warm):
+                L = cholesky(Hf + lam[widx[s]] * np.eye(d))
+                Tw[s] = vec_lower(L)
+                if keep:
+                    res.factors[(f, s)] = L
+            Theta = theta0.copy()
+            Theta[:pw] += lstsq(Vw[:, :pw], Tw - Vw @ theta0)
+        else:
+            # Algorithm 1, steps 1-2: exact factors at the samples, stacked as rows of T
+            T = np.empty((g, d * (d + 1) // 2))
+            for s in range(g):
+                L = cholesky(Hf + lam_s[s] * np.eye(d))
+                T[s] = vec_lower(L)
+                if keep:
+                    res.factors[(f, s)] = L
+            # steps 3-6: observation matrix and least-squares coefficients
+            V = basis_values(basis, lam_s, lam_s, p)
+            Theta = lstsq(V, T)
         if keep:
             res.theta[f] = Theta
         # evaluation at every grid lambda, two triangular solves, hold-out error

@@ -646,3 +646,48 @@ def test_pinrmse_is_the_fit_of_the_fold_mean_and_rejects_too_few_samples():
     np.testing.assert_allclose(res.Ebar, Phi @ np.linalg.lstsq(V, tbar, rcond=None)[0], rtol=1e-9)
     with pytest.raises(ValueError):
         orc.pinrmse(p.X, p.Y, k=k, g=3, r=3, q=q)
+
+
+# ----------------------------------------------------------------------------
+# warm start across folds (the paper's future work, Sec. 7)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("basis", ["mono", "cheb_log"])
+def test_warm_start_with_every_sample_is_the_plain_fit(basis):
+    """g' = g uses fold 0's sample indices; with V of full column rank,
+    Theta_0 + V^+ (T - V Theta_0) = V^+ T, the plain fit of Algorithm 1."""
+    p = synth.spectral_gaussian(200, 12, 2, seed=101)
+    kw = dict(k=4, g=5, r=3, q=21, basis=basis, keep=True)
+    a = orc.cv(p.X, p.Y, **kw)
+    b = orc.cv(p.X, p.Y, warm=5, **kw)
+    for f in range(4):
+        np.testing.assert_allclose(b.theta[f], a.theta[f], rtol=1e-8, atol=1e-10 * np.abs(a.theta[f]).max())
+    np.testing.assert_allclose(b.E, a.E, rtol=1e-9)
+
+
+def test_warm_start_interpolates_the_exact_factors_at_its_nodes():
+    """g' <= r + 1: the correction interpolates, so at the warm nodes a warm
+    fold's interpolated factor is its exact Cholesky factor; fold 0 is the
+    plain fit; and the warm samples sit at round(i (q-1)/(g'-1))."""
+    p = synth.spectral_gaussian(240, 10, 2, seed=102)
+    k, g, r, q = 4, 5, 3, 21
+    for warm in (2, 3, 4):
+        res = orc.cv(p.X, p.Y, k=k, g=g, r=r, q=q, basis="cheb_log", warm=warm, keep=True)
+        assert res.warm_idx == [round(i * (q - 1) / (warm - 1) + 1e-9) for i in range(warm)]
+        lam_s = res.lam[res.sample_idx]
+        for f in range(1, k):
+            for s, t in enumerate(res.warm_idx):
+                phi = orc.basis_values("cheb_log", [res.lam[t]], lam_s, r + 1)[0]
+                L = orc.unvec_lower(orc.eval_poly(phi, res.theta[f]), 10)
+                np.testing.assert_allclose(L, res.factors[(f, s)], rtol=1e-9, atol=1e-11)
+        plain = orc.cv(p.X, p.Y, k=k, g=g, r=r, q=q, basis="cheb_log", folds=[0])
+        np.testing.assert_allclose(res.E[0], plain.E[0], rtol=1e-12)
+
+
+def test_warm_start_arguments():
+    p = synth.spectral_gaussian(100, 6, 1, seed=103)
+    for bad in (1, 6):
+        with pytest.raises(ValueError):
+            orc.cv(p.X, p.Y, k=3, g=5, r=2, q=11, warm=bad)
+    with pytest.raises(ValueError):
+        orc.cv(p.X, p.Y, k=3, g=5, r=2, q=11, warm=2, exact=True)

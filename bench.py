@@ -18,8 +18,9 @@ device times, the roofline of the dominant kernel, SM clocks during the timed
 region, the oracle timed on the host cores (cpu_baseline), and MChol
 (Sec. 6.2) on the same data: alone at the paper's stopping width, and as the
 range narrowing before piCholesky, each timed and compared with exact CV's
-selected lambda; and PINRMSE (the sampled hold-out errors interpolated
-directly) likewise.
+selected lambda; PINRMSE (the sampled hold-out errors interpolated
+directly) likewise; and the warm start across folds (g' = 2 exact factors per
+fold after the first).
 
 Workloads: mixed_ecc (default: n = 32768, d = 2048, c = 10, k = 5, g = 6,
 r = 3, q = 101, mixed precision, one refinement step against the interpolated
@@ -77,7 +78,7 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="mixed_ecc")
     ap.add_argument("--refine", type=int, default=None, help="refinement steps (default: the workload's)")
     ap.add_argument("--no-exact", action="store_true", help="skip the exact-Cholesky comparison")
-    ap.add_argument("--no-mchol", action="store_true", help="skip the MChol and PINRMSE comparisons")
+    ap.add_argument("--no-mchol", action="store_true", help="skip the MChol, PINRMSE and warm-start comparisons")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle sample (cpu_baseline, error)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time eager calls instead of one CUDA graph per step")
@@ -561,7 +562,7 @@ def mchol_compare(binding, params, cfg, X, Y, stream, exact, E, t_star):
     import torch
     c0 = 0.5 * (math.log10(cfg["lo"]) + math.log10(cfg["hi"]))
     s0 = 0.5 * (math.log10(cfg["hi"]) - math.log10(cfg["lo"]))
-    ctx = binding.Context(**params)
+    ctx = binding.Context(**dict(params, exact_batch=max(3, cfg["g"])))
     out = ctx._outputs(False)
     lam_grid = None
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -637,7 +638,7 @@ def pinrmse_compare(binding, params, cfg, X, Y, stream, exact, t_star):
     import math
 
     import torch
-    ctx = binding.Context(**params)
+    ctx = binding.Context(**dict(params, exact_batch=max(3, cfg["g"])))
     out = ctx._outputs(False)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -661,6 +662,41 @@ def pinrmse_compare(binding, params, cfg, X, Y, stream, exact, t_star):
         if ref is not None and tp >= 0:
             res[f"grid_steps_from_{name}"] = tp - ref
             res[f"abs_log10_vs_{name}"] = abs(tp - ref) * step
+    ctx.close()
+    return res
+
+
+def warm_compare(binding, params, cfg, X, Y, stream, exact, E, t_star, warm=2):
+    """The warm start across folds (warm_samples = g'): one step of the same
+    workload with fold 0 fitted from its g factors and every other fold from
+    g' factors and fold 0's coefficients; timed, and its hold-out errors and
+    selection compared with the plain piCholesky step's and exact CV's."""
+    import math
+
+    import numpy as np
+    import torch
+    ctx = binding.Context(**dict(params, warm_samples=warm, exact_batch=cfg["g"]))
+    out = ctx._outputs(False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.run(X, Y, out=out)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(3):
+        ctx.run(X, Y, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 3
+    Ew = out[0].cpu().numpy()
+    tw = int(out[1].cpu().item())
+    fin = np.isfinite(Ew) & np.isfinite(E)
+    step = (math.log10(cfg["hi"]) - math.log10(cfg["lo"])) / (cfg["q"] - 1)
+    res = {"warm_samples": warm, "ms": ms, "value": cfg["k"] * cfg["q"] / (ms / 1e3), "unit": "evals/s",
+           "exact_factorisations": cfg["g"] + (cfg["k"] - 1) * warm,
+           "max_rel_E_vs_plain": float(np.max(np.abs(Ew[fin] - E[fin]) / E[fin])) if fin.any() else None,
+           "t_star": tw, "t_star_plain": t_star, "device_status": binding.STATUS.get(ctx.info().code)}
+    if exact and tw >= 0:
+        res["grid_steps_from_exact"] = tw - exact["t_star"]
+        res["abs_log10_vs_exact"] = abs(tw - exact["t_star"]) * step
     ctx.close()
     return res
 
@@ -886,10 +922,11 @@ def run_own(args):
         ctxe.close()
 
     # ---- MChol (Sec. 6.2), alone and as the range for piCholesky; PINRMSE --
-    mchol = pinrmse = None
+    mchol = pinrmse = warm = None
     if not args.no_mchol and rank == 0:
         mchol = mchol_compare(binding, params, cfg, X, Y, stream, exact, E, t_star)
         pinrmse = pinrmse_compare(binding, params, cfg, X, Y, stream, exact, t_star)
+        warm = warm_compare(binding, params, cfg, X, Y, stream, exact, E, t_star)
 
     if rank != 0:
         return 0
@@ -922,6 +959,7 @@ def run_own(args):
         "speedup_vs_exact": (value / world / exact["value"]) if exact else None,
         "mchol": mchol,
         "pinrmse": pinrmse,
+        "warm_start": warm,
         "device_status": binding.STATUS.get(info.code), "unusable_pairs": info.unusable,
     }
     if sample:

@@ -99,7 +99,13 @@ typedef struct {
                              PICHOL_REFINE_EXACT: B - (H_f + lambda I) W from two tensor-core
                              products (split TF32), so the interpolated factor acts as a
                              preconditioner and the result moves toward exact CV (not in the paper) */
-    int32_t reserved[5];  /* must be zero */
+    int32_t warm_samples; /* 0, or g' with 2 <= g' <= min(g, 8): warm start across folds (the paper's future
+                             work, Sec. 7).  Fold 0 is fitted from its g sampled factors; every other
+                             fold f factors only g' lambdas, at grid indices round(i (q-1)/(g'-1)),
+                             and takes Theta_f = Theta_0 + V'^+ (T'_f - V' Theta_0), V' = the first
+                             min(g', r+1) basis functions at those lambdas (the basis normalised by
+                             the g samples); its other coefficient planes are fold 0's */
+    int32_t reserved[4];  /* must be zero */
 } pichol_config;
 
 enum { PICHOL_REFINE_INTERPOLATED = 0, PICHOL_REFINE_EXACT = 1 };
@@ -118,7 +124,7 @@ typedef struct pichol_ctx pichol_ctx;
 
 /* Fills *cfg with defaults: lam_lo = 1e-3, lam_hi = 1e1, scale_by_trace = 1,
  * basis MONO, mode FP64, refine_steps 0, gram_passes 3, exact_batch 0,
- * refine_target PICHOL_REFINE_INTERPOLATED; the sizes are left zero.
+ * refine_target PICHOL_REFINE_INTERPOLATED, warm_samples 0; the sizes are left zero.
  * refine_target PICHOL_REFINE_EXACT needs mode MIXED (else
  * PICHOL_ERR_UNSUPPORTED from pichol_create). */
 PICHOL_API void pichol_config_default(pichol_config* cfg);
@@ -221,7 +227,8 @@ PICHOL_API pichol_status pichol_holdout_grad(pichol_ctx* ctx, double log_lam, do
  * values (-1 if none).  A fold with an unusable sampled factor scores +inf at
  * every t (pichol_info.unusable counts such samples).  E_out: device, k*q
  * doubles; t_star: device, one int32.  The sampled factors and the fit stay
- * valid; the solution buffer of pichol_eval_holdout is reused.
+ * valid; the solution buffer of pichol_eval_holdout is reused.  Not with
+ * warm_samples (PICHOL_ERR_UNSUPPORTED): the folds then have no common samples.
  */
 PICHOL_API pichol_status pichol_eval_pinrmse(pichol_ctx* ctx, double* E_out, int32_t* t_star, void* stream);
 
@@ -263,7 +270,8 @@ PICHOL_API pichol_status pichol_mchol_levels(double s, double s_min, int32_t* le
 PICHOL_API pichol_status pichol_get_lambdas(pichol_ctx* ctx, double* lam_out, void* stream);
 
 /* Inspection (for tests): dense double copies of internal results.
- *   factor : L_{f,s} (d x d, upper triangle zero) after pichol_factor_samples
+ *   factor : L_{f,s} (d x d, upper triangle zero) after pichol_factor_samples; with
+ *            warm_samples = g' the folds f > 0 hold s < g' only (the warm-start lambdas)
  *   theta  : Theta_{f,m} for m = 0..r, (r+1) x d x d (upper triangles zero) after pichol_fit
  *   hessian: H_f (d x d, lower triangle mirrored) and B_f (d x c) after pichol_hessian */
 PICHOL_API pichol_status pichol_export_factor(pichol_ctx* ctx, int32_t f, int32_t s, double* L_out, void* stream);

@@ -51,7 +51,8 @@ class Config(ctypes.Structure):
                 ("lam_lo", ctypes.c_double), ("lam_hi", ctypes.c_double),
                 ("scale_by_trace", ctypes.c_int32), ("basis", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("refine_steps", ctypes.c_int32), ("gram_passes", ctypes.c_int32),
-                ("exact_batch", ctypes.c_int32), ("refine_target", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("exact_batch", ctypes.c_int32), ("refine_target", ctypes.c_int32),
+                ("warm_samples", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class Info(ctypes.Structure):
@@ -159,7 +160,8 @@ class Context:
     """One piCholesky cross-validation problem on the current CUDA device."""
 
     def __init__(self, *, n, d, c, k, g, r, q, lam_lo=1e-3, lam_hi=1e1, basis="mono", mode="fp64",
-                 refine_steps=0, gram_passes=3, exact_batch=0, scale_by_trace=True, refine_target="interpolated"):
+                 refine_steps=0, gram_passes=3, exact_batch=0, scale_by_trace=True, refine_target="interpolated",
+                 warm_samples=0):
         import torch
         L = lib()
         cfg = Config()
@@ -171,6 +173,7 @@ class Context:
         cfg.mode = {"fp64": PICHOL_MODE_FP64, "mixed": PICHOL_MODE_MIXED}[mode]
         cfg.refine_steps, cfg.gram_passes, cfg.exact_batch = refine_steps, gram_passes, exact_batch
         cfg.refine_target = REFINE_TARGETS[refine_target]
+        cfg.warm_samples = warm_samples
         self.cfg = cfg
         self.dtype = torch.float64 if mode == "fp64" else torch.float32
         h = ctypes.c_void_p()
@@ -404,6 +407,7 @@ class Batch:
             cfg.refine_steps = pr.get("refine_steps", 0)
             cfg.refine_target = REFINE_TARGETS[pr.get("refine_target", "interpolated")]
             cfg.exact_batch = pr.get("exact_batch", cfg.g)
+            cfg.warm_samples = pr.get("warm_samples", 0)
         self.cfgs = cfgs
         self.n = n
         h = ctypes.c_void_p()

@@ -31,6 +31,9 @@ size_t plan(pichol_ctx* ctx, char* base)
     ctx->mlam = (double*)take(8 * sizeof(double));
     ctx->lam_s = (double*)take(g * sizeof(double));
     ctx->pinv = (double*)take(p * g * sizeof(double));
+    ctx->lam_w = (double*)take(g * sizeof(double));
+    ctx->pinv_w = (double*)take(p * g * sizeof(double));
+    ctx->vw = (double*)take(g * p * sizeof(double));
     ctx->phi = (double*)take(q * p * sizeof(double));
     ctx->dphi = (double*)take(q * p * sizeof(double));
     ctx->nfc = (int64_t*)take(k * sizeof(int64_t));
@@ -119,8 +122,10 @@ pichol_status pichol_create(const pichol_config* cfg, pichol_ctx** out)
     if (c.exact_batch < 0 || c.exact_batch > c.q) return PICHOL_ERR_INVALID_ARG;
     if (c.refine_target != PICHOL_REFINE_INTERPOLATED && c.refine_target != PICHOL_REFINE_EXACT)
         return PICHOL_ERR_INVALID_ARG;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 4; ++i)
         if (c.reserved[i] != 0) return PICHOL_ERR_INVALID_ARG;
+    if (c.warm_samples != 0 && (c.warm_samples < 2 || c.warm_samples > c.g || c.warm_samples > 8))
+        return PICHOL_ERR_INVALID_ARG;
     if (c.refine_target == PICHOL_REFINE_EXACT && c.mode != PICHOL_MODE_MIXED) return PICHOL_ERR_UNSUPPORTED;
     // the interpolate-on-load solve keeps p coefficient planes and the
     // right-hand-side blocks of two lambdas in shared memory (227 KB per CTA)
@@ -246,6 +251,7 @@ pichol_status pichol_eval_pinrmse(pichol_ctx* ctx, double* E_out, int32_t* t_sta
 {
     if (!ctx || !E_out || !t_star) return PICHOL_ERR_INVALID_ARG;
     if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
+    if (ctx->cfg.warm_samples) return PICHOL_ERR_UNSUPPORTED;
     if (!ctx->have_factors) return PICHOL_ERR_STATE;
     return cuda_status(launch_pinrmse(ctx, E_out, t_star, (cudaStream_t)stream));
 }
@@ -294,6 +300,7 @@ pichol_status pichol_get_lambdas(pichol_ctx* ctx, double* lam_out, void* stream)
 pichol_status pichol_export_factor(pichol_ctx* ctx, int32_t f, int32_t s, double* L_out, void* stream)
 {
     if (!ctx || !L_out || f < 0 || f >= ctx->cfg.k || s < 0 || s >= ctx->cfg.g) return PICHOL_ERR_INVALID_ARG;
+    if (f > 0 && ctx->cfg.warm_samples && s >= ctx->cfg.warm_samples) return PICHOL_ERR_INVALID_ARG;
     if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
     if (!ctx->have_factors) return PICHOL_ERR_STATE;
     const int64_t slot = (int64_t)f * ctx->cfg.g + s;

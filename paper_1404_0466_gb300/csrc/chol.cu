@@ -19,13 +19,21 @@ struct ProbMap {
     int count;      // live slots per fold (slots >= count are skipped)
     int exact;      // 0: shifts are the sampled lambdas; 1: grid lambdas t0 + i
     int t0;
+    int warm;       // > 0: folds f > 0 have this many live slots, shifted by the warm-start lambdas
 };
 
-__device__ inline bool prob_dead(const ProbMap& pm, int pr) { return pr % pm.per >= pm.count; }
+__device__ inline bool prob_dead(const ProbMap& pm, int pr)
+{
+    const int live = (pm.warm > 0 && pr >= pm.per) ? pm.warm : pm.count;
+    return pr % pm.per >= live;
+}
 
-__device__ inline double prob_lambda(const ProbMap& pm, int pr, const double* lam, const double* lam_s) {
-    int i = pr % pm.per;
-    return pm.exact ? lam[pm.t0 + i] : lam_s[i];
+__device__ inline double prob_lambda(const ProbMap& pm, int pr, const double* lam, const double* lam_s,
+                                     const double* lam_w)
+{
+    const int i = pr % pm.per;
+    if (pm.exact) return lam[pm.t0 + i];
+    return (pm.warm > 0 && pr >= pm.per) ? lam_w[i] : lam_s[i];
 }
 
 // A = H_f + lambda I on the lower tiles (H_f tile-major from the Gram step);
@@ -33,14 +41,15 @@ __device__ inline double prob_lambda(const ProbMap& pm, int pr, const double* la
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_chol_init(const T* __restrict__ Hf, int64_t d, int64_t ntiles, ProbMap pm,
-            const double* __restrict__ lam, const double* __restrict__ lam_s, T* __restrict__ F)
+            const double* __restrict__ lam, const double* __restrict__ lam_s, const double* __restrict__ lam_w,
+            T* __restrict__ F)
 {
     int I, J;
     tile_coords(blockIdx.x, I, J);
     const int pr = blockIdx.y;
     if (prob_dead(pm, pr)) return;
     const int f = pr / pm.per;
-    const double shift = prob_lambda(pm, pr, lam, lam_s);
+    const double shift = prob_lambda(pm, pr, lam, lam_s, lam_w);
     const T* src = Hf + ((int64_t)f * ntiles + blockIdx.x) * TILE_ELEMS;
     T* dst = F + ((int64_t)pr * ntiles + blockIdx.x) * TILE_ELEMS;
     for (int e = threadIdx.x; e < TILE_ELEMS; e += 256) {
@@ -370,6 +379,7 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
     pm.t0 = t0;
     pm.per = exact ? (int)ctx->exact_batch : c.g;
     pm.count = count;
+    pm.warm = exact ? 0 : c.warm_samples;
     const int nprob = c.k * pm.per;
     T* F = (T*)ctx->F;
     constexpr int UNT = UpdateThreads<T>::value;
@@ -395,7 +405,7 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
     {
         StageScope sc_(ctx, ST_CHOL_INIT, s);
         k_chol_init<T><<<dim3((unsigned)ctx->ntiles, nprob), 256, 0, s>>>(
-            (const T*)ctx->Hf, c.d, ctx->ntiles, pm, ctx->lam, ctx->lam_s, F);
+            (const T*)ctx->Hf, c.d, ctx->ntiles, pm, ctx->lam, ctx->lam_s, ctx->lam_w, F);
     }
     ctx->launches++;
     // Look-ahead: the critical path (diagonal tile J, panel J, then the tiles

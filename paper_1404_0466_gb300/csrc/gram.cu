@@ -209,6 +209,8 @@ __global__ void k_btrain_from_bv(const T* __restrict__ Bv, int k, int64_t len, T
 //   V[s][m] = phi_m(lambda_s); V = Q R by modified Gram-Schmidt with one
 //   re-orthogonalisation pass; P = R^{-1} Q^T = V^+ (Algorithm 1, steps 3-6)
 //   phi[t][m] = phi_m(lambda_t), dphi[t][m] = d phi_m / d lambda at lambda_t
+//   warm start (gw > 0): lam_w[i] = lambda at round(i (q-1)/(gw-1)),
+//   vw[i][m] = phi_m(lam_w[i]), pinv_w = (first min(gw, p) columns of vw)^+
 // ---------------------------------------------------------------------------
 __device__ inline void basis_eval(int basis, int p, double lam, double a, double b, double smax,
                                   double* phi, double* dphi)
@@ -237,11 +239,47 @@ __device__ inline void basis_eval(int basis, int p, double lam, double a, double
     }
 }
 
+// Pseudo-inverse P = V^+ (cols x rows, row-major P[m * rows + i]) of the first
+// `cols` columns of V (rows x cols, full column rank) by modified Gram-Schmidt
+// with one re-orthogonalisation pass, V = Q R, then P = R^{-1} Q^T by back
+// substitution.  False if a column is dependent on the previous ones.
+__device__ inline bool pinv_mgs(const double (*V)[MAX_P], int rows, int cols, double* P)
+{
+    double Q[MAX_G][MAX_P], R[MAX_P][MAX_P];
+    for (int m = 0; m < cols; ++m)
+        for (int l = 0; l < cols; ++l) R[m][l] = 0.0;
+    bool ok = true;
+    for (int m = 0; m < cols; ++m) {
+        double v[MAX_G];
+        for (int i = 0; i < rows; ++i) v[i] = V[i][m];
+        for (int pass = 0; pass < 2; ++pass)
+            for (int l = 0; l < m; ++l) {
+                double dot = 0.0;
+                for (int i = 0; i < rows; ++i) dot += Q[i][l] * v[i];
+                R[l][m] += dot;
+                for (int i = 0; i < rows; ++i) v[i] -= dot * Q[i][l];
+            }
+        double nrm = 0.0;
+        for (int i = 0; i < rows; ++i) nrm += v[i] * v[i];
+        nrm = sqrt(nrm);
+        if (!(nrm > 0.0)) { ok = false; nrm = 1.0; }
+        R[m][m] = nrm;
+        for (int i = 0; i < rows; ++i) Q[i][m] = v[i] / nrm;
+    }
+    for (int i = 0; i < rows; ++i)
+        for (int m = cols - 1; m >= 0; --m) {
+            double v = Q[i][m];
+            for (int l = m + 1; l < cols; ++l) v -= R[m][l] * P[l * rows + i];
+            P[m * rows + i] = v / R[m][m];
+        }
+    return ok;
+}
+
 __global__ void __launch_bounds__(256)
 k_setup(const void* G, int mode_fp64, int64_t d, int64_t dp, int k, int g, int p, int q,
         double lo, double hi, const double* __restrict__ window, int scale_by_trace, int basis,
         double* scal, double* lam, double* lam_s, double* pinv, double* phi, double* dphi,
-        DevStatus* st)
+        int gw, double* lam_w, double* pinv_w, double* vw, DevStatus* st)
 {
     if (window) {
         lo = window[0];
@@ -279,36 +317,20 @@ k_setup(const void* G, int mode_fp64, int64_t d, int64_t dp, int k, int g, int p
         const double a = log(smin), b = log(smax);
         double V[MAX_G][MAX_P], dummy[MAX_P];
         for (int i = 0; i < g; ++i) basis_eval(basis, p, lam_s[i], a, b, smax, V[i], dummy);
-        // modified Gram-Schmidt with re-orthogonalisation: V = Q R
-        double Q[MAX_G][MAX_P], R[MAX_P][MAX_P];
-        for (int m = 0; m < p; ++m)
-            for (int l = 0; l < p; ++l) R[m][l] = 0.0;
-        bool ok = true;
-        for (int m = 0; m < p; ++m) {
-            double v[MAX_G];
-            for (int i = 0; i < g; ++i) v[i] = V[i][m];
-            for (int pass = 0; pass < 2; ++pass)
-                for (int l = 0; l < m; ++l) {
-                    double dot = 0.0;
-                    for (int i = 0; i < g; ++i) dot += Q[i][l] * v[i];
-                    R[l][m] += dot;
-                    for (int i = 0; i < g; ++i) v[i] -= dot * Q[i][l];
-                }
-            double nrm = 0.0;
-            for (int i = 0; i < g; ++i) nrm += v[i] * v[i];
-            nrm = sqrt(nrm);
-            if (!(nrm > 0.0)) { ok = false; nrm = 1.0; }
-            R[m][m] = nrm;
-            for (int i = 0; i < g; ++i) Q[i][m] = v[i] / nrm;
-        }
-        if (!ok) latch_error(st, PICHOL_ERR_INVALID_ARG, -1, -1, -1);
-        // P = R^{-1} Q^T: back substitution column by column
-        for (int i = 0; i < g; ++i)
-            for (int m = p - 1; m >= 0; --m) {
-                double v = Q[i][m];
-                for (int l = m + 1; l < p; ++l) v -= R[m][l] * pinv[l * g + i];
-                pinv[m * g + i] = v / R[m][m];
+        if (!pinv_mgs(V, g, p, pinv)) latch_error(st, PICHOL_ERR_INVALID_ARG, -1, -1, -1);
+        if (gw > 0) {
+            // warm start: gw samples at round(i (q-1)/(gw-1)), the same basis
+            // (normalised by the g samples), the first pw functions fitted
+            const int pw = gw < p ? gw : p;
+            double Vw[MAX_G][MAX_P];
+            for (int i = 0; i < gw; ++i) {
+                const int idx = (2 * i * (q - 1) + (gw - 1)) / (2 * (gw - 1));
+                lam_w[i] = lam[idx];
+                basis_eval(basis, p, lam_w[i], a, b, smax, Vw[i], dummy);
+                for (int m = 0; m < p; ++m) vw[i * p + m] = Vw[i][m];
             }
+            if (!pinv_mgs(Vw, gw, pw, pinv_w)) latch_error(st, PICHOL_ERR_INVALID_ARG, -1, -1, -1);
+        }
         shared_ab[0] = a;
         shared_ab[1] = b;
         shared_ab[2] = smax;
@@ -390,7 +412,8 @@ cudaError_t launch_setup(pichol_ctx* ctx, const double* window, cudaStream_t s)
         StageScope sc_(ctx, ST_SETUP, s);
         k_setup<<<1, 256, 0, s>>>(ctx->G, c.mode == PICHOL_MODE_FP64, c.d, ctx->dp, c.k, c.g, ctx->p, c.q,
                                   c.lam_lo, c.lam_hi, window, c.scale_by_trace, c.basis, ctx->scal, ctx->lam,
-                                  ctx->lam_s, ctx->pinv, ctx->phi, ctx->dphi, ctx->status);
+                                  ctx->lam_s, ctx->pinv, ctx->phi, ctx->dphi, c.warm_samples, ctx->lam_w,
+                                  ctx->pinv_w, ctx->vw, ctx->status);
     }
     ctx->launches++;
     return cudaGetLastError();

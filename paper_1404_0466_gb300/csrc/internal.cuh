@@ -111,6 +111,9 @@ struct pichol_ctx {
     double* mlam;        // MChol state: [0..2] the level's lambdas, [4] c, [5] s, [6..7] final window
     double* lam_s;       // g
     double* pinv;        // p x g
+    double* lam_w;       // g': warm-start lambdas (warm_samples > 0)
+    double* pinv_w;      // min(g', p) x g': V'^+ of the warm start
+    double* vw;          // g' x p: basis values at the warm-start lambdas
     double* phi;         // q x p
     double* dphi;        // q x p
     void* G;             // k x dp x dp

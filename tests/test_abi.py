@@ -160,3 +160,17 @@ def test_mchol_levels_and_argument_checks(L):
     assert L.pichol_mchol(h, 0.0, 1.0, 0.1, None, None) == 4      # no workspace yet
     assert L.pichol_mchol(None, 0.0, 1.0, 0.1, None, None) == 1
     L.pichol_destroy(h)
+
+
+def test_warm_samples_validation(L):
+    """warm_samples: 0, or 2 <= g' <= min(g, 8)."""
+    for ws, want in [(0, 0), (2, 0), (4, 0), (1, 1), (5, 1), (-1, 1)]:
+        rc, h = _create(L, _cfg(L, g=4, r=2, warm_samples=ws))
+        assert rc == want, (ws, rc)
+        if rc == 0:
+            L.pichol_destroy(h)
+    rc, h = _create(L, _cfg(L, g=12, r=3, q=31, warm_samples=9))
+    assert rc == 1
+    rc, h = _create(L, _cfg(L, g=12, r=3, q=31, warm_samples=8))
+    assert rc == 0
+    L.pichol_destroy(h)

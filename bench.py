@@ -754,12 +754,27 @@ def run_own(args):
             torch.cuda.synchronize()
             tune_ms[(strip, dt)] = ta.elapsed_time(tb) / 2
     best = min(tune_ms, key=tune_ms.get) if tune_ms else (4, 512)
-    if pg is not None:                      # every rank uses rank 0's choice
-        choice = torch.tensor(list(best), device=dev)
-        pg.broadcast(choice, 0)
-        best = tuple(int(v) for v in choice.tolist())
     ctx.set_tuning(update_strip=best[0], diag_threads=best[1])
-    tuning = dict(ctx.tuning(), autotuned_ms={f"strip{a}_diag{b}": round(v, 3) for (a, b), v in tune_ms.items()})
+    # then the evaluation's two-stream overlap of the solve with the refinement residual
+    overlap_ms = {}
+    if refine > 0 and w["mode"] == "mixed" and not args.profile:
+        for ov in (0, 1):
+            ctx.set_tuning(eval_overlap=ov)
+            step()
+            ta.record(stream)
+            for _ in range(2):
+                step()
+            tb.record(stream)
+            torch.cuda.synchronize()
+            overlap_ms[ov] = ta.elapsed_time(tb) / 2
+    best_ov = min(overlap_ms, key=overlap_ms.get) if overlap_ms else 0
+    if pg is not None:                      # every rank uses rank 0's choice
+        choice = torch.tensor(list(best) + [best_ov], device=dev)
+        pg.broadcast(choice, 0)
+        best, best_ov = tuple(int(v) for v in choice.tolist()[:2]), int(choice.tolist()[2])
+    ctx.set_tuning(update_strip=best[0], diag_threads=best[1], eval_overlap=best_ov)
+    tuning = dict(ctx.tuning(), autotuned_ms={f"strip{a}_diag{b}": round(v, 3) for (a, b), v in tune_ms.items()},
+                  overlap_ms={f"eval_overlap{k}": round(v, 3) for k, v in overlap_ms.items()})
 
     for _ in range(args.warmup):
         step()

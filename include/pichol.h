@@ -325,7 +325,7 @@ PICHOL_API pichol_status pichol_stage_times(pichol_ctx* ctx, double* ms, int64_t
                                             void* stream);
 
 /*
- * Launch shapes of the factorisation that a tuner may change.  Each changes
+ * Launch shapes of the factorisation and the evaluation that a tuner may change.  Each changes
  * how the work is split into CTAs and scheduled, never the order of any
  * element's arithmetic, so every result is bit-identical under every tuning.
  *   update_strip   : output tiles per CTA in the bulk trailing updates, 1..8 (default 4)
@@ -334,6 +334,11 @@ PICHOL_API pichol_status pichol_stage_times(pichol_ctx* ctx, double* ms, int64_t
  *                    memory request no update CTA fits beside) when the k g
  *                    problems fit on half the SMs; 0 never (default 1; batches
  *                    set 0 for their problems)
+ *   eval_overlap   : mixed mode with refinement: 1 splits the lambdas of
+ *                    pichol_eval_holdout in two halves, the second run on the
+ *                    internal stream from the end of the first half's solve,
+ *                    so that its solve overlaps the first half's residual
+ *                    passes; 0 runs them as one (default 0)
  * pichol_set_tuning returns PICHOL_ERR_INVALID_ARG for values out of range or
  * nonzero reserved fields and then changes nothing.
  */
@@ -341,7 +346,8 @@ typedef struct {
     int32_t update_strip;
     int32_t diag_threads;
     int32_t diag_exclusive;
-    int32_t reserved[5];
+    int32_t eval_overlap;
+    int32_t reserved[4];
 } pichol_tuning;
 PICHOL_API pichol_status pichol_get_tuning(const pichol_ctx* ctx, pichol_tuning* t);
 PICHOL_API pichol_status pichol_set_tuning(pichol_ctx* ctx, const pichol_tuning* t);

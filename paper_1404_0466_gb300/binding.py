@@ -42,7 +42,7 @@ STAGES = ["gram", "xty", "setup", "chol_init", "chol_diag", "chol_panel", "chol_
 
 class Tuning(ctypes.Structure):
     _fields_ = [("update_strip", ctypes.c_int32), ("diag_threads", ctypes.c_int32),
-                ("diag_exclusive", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("diag_exclusive", ctypes.c_int32), ("eval_overlap", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class Config(ctypes.Structure):
@@ -314,13 +314,14 @@ class Context:
     def tuning(self) -> dict:
         t = Tuning()
         _check(lib().pichol_get_tuning(self._h, ctypes.byref(t)), "pichol_get_tuning")
-        return {"update_strip": t.update_strip, "diag_threads": t.diag_threads, "diag_exclusive": t.diag_exclusive}
+        return {"update_strip": t.update_strip, "diag_threads": t.diag_threads, "diag_exclusive": t.diag_exclusive,
+                "eval_overlap": t.eval_overlap}
 
     def set_tuning(self, **kw):
-        """Change factorisation launch shapes (results are bit-identical under every tuning)."""
+        """Change launch shapes and scheduling (results are bit-identical under every tuning)."""
         cur = self.tuning()
         cur.update(kw)
-        t = Tuning(cur["update_strip"], cur["diag_threads"], cur["diag_exclusive"])
+        t = Tuning(cur["update_strip"], cur["diag_threads"], cur["diag_exclusive"], cur["eval_overlap"])
         _check(lib().pichol_set_tuning(self._h, ctypes.byref(t)), "pichol_set_tuning")
 
     def stage_times(self, stream=None):
@@ -427,9 +428,9 @@ class Batch:
     def set_streams(self, nstreams):
         _check(lib().pichol_batch_set_streams(self._h, nstreams), "pichol_batch_set_streams")
 
-    def set_tuning(self, update_strip=4, diag_threads=512, diag_exclusive=0):
-        """Factorisation launch shapes for every problem (results are bit-identical)."""
-        t = Tuning(update_strip, diag_threads, diag_exclusive)
+    def set_tuning(self, update_strip=4, diag_threads=512, diag_exclusive=0, eval_overlap=0):
+        """Launch shapes and scheduling for every problem (results are bit-identical)."""
+        t = Tuning(update_strip, diag_threads, diag_exclusive, eval_overlap)
         _check(lib().pichol_batch_set_tuning(self._h, ctypes.byref(t)), "pichol_batch_set_tuning")
 
     def run(self, Xs, Ys, stream=None):

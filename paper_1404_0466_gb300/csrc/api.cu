@@ -435,7 +435,8 @@ pichol_status pichol_set_tuning(pichol_ctx* ctx, const pichol_tuning* t)
     if (t->update_strip < 1 || t->update_strip > 8) return PICHOL_ERR_INVALID_ARG;
     if (t->diag_threads != 256 && t->diag_threads != 512) return PICHOL_ERR_INVALID_ARG;
     if (t->diag_exclusive != 0 && t->diag_exclusive != 1) return PICHOL_ERR_INVALID_ARG;
-    for (int i = 0; i < 5; ++i)
+    if (t->eval_overlap != 0 && t->eval_overlap != 1) return PICHOL_ERR_INVALID_ARG;
+    for (int i = 0; i < 4; ++i)
         if (t->reserved[i] != 0) return PICHOL_ERR_INVALID_ARG;
     ctx->tune = *t;
     return PICHOL_OK;

@@ -868,11 +868,17 @@ k_resid(ResidArgs a, const __grid_constant__ CUtensorMap tmap)
     }
 }
 
+// y += x over the systems t0 .. t0 + tcount - 1 of every fold ([f][t][dp][c]
+// blocks of `len` values).
 template <typename T>
-__global__ void k_axpy(T* __restrict__ y, const T* __restrict__ x, int64_t n)
+__global__ void k_axpy(T* __restrict__ y, const T* __restrict__ x, int k, int q, int t0, int tcount, int64_t len)
 {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        y[e] += x[e];
+    const int64_t per = (int64_t)tcount * len, n = (int64_t)k * per;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int f = (int)(e / per);
+        const int64_t g = ((int64_t)f * q + t0) * len + e % per;
+        y[g] += x[g];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1250,68 +1256,91 @@ static cudaError_t eval_impl(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
 
-    SolveArgs sa;
-    sa.src = da.src;
-    sa.dinv = ctx->Dinv;
-    sa.rhs = ctx->Btr;
-    sa.zbuf = ctx->W;
-    sa.out = ctx->W;
-    sa.phi = ctx->phi;
-    sa.p = ctx->p;
-    sa.nt = ctx->nt;
-    sa.q = cf.q;
-    sa.t0 = t0;
-    sa.tcount = tcount;
-    sa.per = (int)ctx->exact_batch;
-    sa.rhs_per_system = 0;
-    sa.ntiles = ctx->ntiles;
-    sa.dp = ctx->dp;
-    sa.c = cf.c;
-    sa.st = ctx->status;
-    e = solve_dispatch<T, EXACT>(ctx, sa, s);
-    if (e != cudaSuccess) return e;
-
-    if constexpr (std::is_same<T, float>::value && !EXACT) {
-        for (int it = 0; it < cf.refine_steps; ++it) {
-            // the residual of the system this step refines (see refine_target)
-            if (cf.refine_target == PICHOL_REFINE_EXACT) {
-                if ((e = launch_resid_exact(ctx, t0, tcount, s)) != cudaSuccess) return e;
-            } else {
-                ResidArgs ra;
-                ra.theta = (const float*)ctx->Theta;
-                ra.W = (const float*)ctx->W;
-                ra.uhi = (const float*)ctx->U;
-                ra.ulo = (const float*)ctx->U + (int64_t)cf.k * cf.q * ctx->dp * cf.c;
-                ra.ohi = (float*)ctx->U;
-                ra.olo = (float*)ctx->U + (int64_t)cf.k * cf.q * ctx->dp * cf.c;
-                ra.B = (const float*)ctx->Btr;
-                ra.R = (float*)ctx->Rres;
-                ra.phi = ctx->phi;
-                ra.p = ctx->p;
-                ra.nt = ctx->nt;
-                ra.q = cf.q;
-                ra.t0 = t0;
-                ra.tcount = tcount;
-                ra.ntiles = ctx->ntiles;
-                ra.dp = ctx->dp;
-                ra.c = cf.c;
-                ra.st = ctx->status;
-                if ((e = resid_dispatch<0>(ctx, ra, s)) != cudaSuccess) return e;
-                if ((e = resid_dispatch<1>(ctx, ra, s)) != cudaSuccess) return e;
+    // the interpolated (or exact) solves of systems [t0h, t0h + tch) and their
+    // refinement steps, on stream `st`
+    auto solve_refine = [&](int t0h, int tch, cudaStream_t st, cudaEvent_t solved) -> cudaError_t {
+        SolveArgs sa;
+        sa.src = da.src;
+        sa.dinv = ctx->Dinv;
+        sa.rhs = ctx->Btr;
+        sa.zbuf = ctx->W;
+        sa.out = ctx->W;
+        sa.phi = ctx->phi;
+        sa.p = ctx->p;
+        sa.nt = ctx->nt;
+        sa.q = cf.q;
+        sa.t0 = t0h;
+        sa.tcount = tch;
+        sa.per = (int)ctx->exact_batch;
+        sa.rhs_per_system = 0;
+        sa.ntiles = ctx->ntiles;
+        sa.dp = ctx->dp;
+        sa.c = cf.c;
+        sa.st = ctx->status;
+        cudaError_t er = solve_dispatch<T, EXACT>(ctx, sa, st);
+        if (er == cudaSuccess && solved) er = cudaEventRecord(solved, st);
+        if (er != cudaSuccess) return er;
+        if constexpr (std::is_same<T, float>::value && !EXACT) {
+            for (int it = 0; it < cf.refine_steps; ++it) {
+                // the residual of the system this step refines (see refine_target)
+                if (cf.refine_target == PICHOL_REFINE_EXACT) {
+                    if ((er = launch_resid_exact(ctx, t0h, tch, st)) != cudaSuccess) return er;
+                } else {
+                    ResidArgs ra;
+                    ra.theta = (const float*)ctx->Theta;
+                    ra.W = (const float*)ctx->W;
+                    ra.uhi = (const float*)ctx->U;
+                    ra.ulo = (const float*)ctx->U + (int64_t)cf.k * cf.q * ctx->dp * cf.c;
+                    ra.ohi = (float*)ctx->U;
+                    ra.olo = (float*)ctx->U + (int64_t)cf.k * cf.q * ctx->dp * cf.c;
+                    ra.B = (const float*)ctx->Btr;
+                    ra.R = (float*)ctx->Rres;
+                    ra.phi = ctx->phi;
+                    ra.p = ctx->p;
+                    ra.nt = ctx->nt;
+                    ra.q = cf.q;
+                    ra.t0 = t0h;
+                    ra.tcount = tch;
+                    ra.ntiles = ctx->ntiles;
+                    ra.dp = ctx->dp;
+                    ra.c = cf.c;
+                    ra.st = ctx->status;
+                    if ((er = resid_dispatch<0>(ctx, ra, st)) != cudaSuccess) return er;
+                    if ((er = resid_dispatch<1>(ctx, ra, st)) != cudaSuccess) return er;
+                }
+                SolveArgs sc = sa;
+                sc.rhs = ctx->Rres;
+                sc.rhs_per_system = 1;
+                sc.zbuf = ctx->Rres;
+                sc.out = ctx->Rres;
+                if ((er = solve_dispatch<T, EXACT>(ctx, sc, st)) != cudaSuccess) return er;
+                {
+                    StageScope sc_(ctx, ST_RESID, st);
+                    k_axpy<float><<<1024, 256, 0, st>>>((float*)ctx->W, (const float*)ctx->Rres, cf.k, cf.q, t0h,
+                                                        tch, ctx->dp * cf.c);
+                }
+                ctx->launches++;
             }
-            SolveArgs sc = sa;
-            sc.rhs = ctx->Rres;
-            sc.rhs_per_system = 1;
-            sc.zbuf = ctx->Rres;
-            sc.out = ctx->Rres;
-            if ((e = solve_dispatch<T, EXACT>(ctx, sc, s)) != cudaSuccess) return e;
-            const int64_t n = (int64_t)cf.k * cf.q * ctx->dp * cf.c;
-            {
-                StageScope sc_(ctx, ST_RESID, s);
-                k_axpy<float><<<1024, 256, 0, s>>>((float*)ctx->W, (const float*)ctx->Rres, n);
-            }
-            ctx->launches++;
         }
+        return cudaGetLastError();
+    };
+
+    // With refinement and the overlap tuning, the systems are split in two
+    // halves: the second half starts on the internal high-priority stream when
+    // the first half's solve ends, so its solve runs beside the first half's
+    // residual passes (the solve alone leaves most issue slots idle).  Each
+    // system's arithmetic is unchanged.
+    const bool overlap = std::is_same<T, float>::value && !EXACT && cf.refine_steps > 0 && ctx->tune.eval_overlap &&
+                         ctx->aux && tcount >= 4;
+    if (overlap) {
+        const int tA = (tcount / 2) & ~1, tB = tcount - tA;
+        if ((e = solve_refine(t0, tA, s, ctx->ev_panel)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(ctx->aux, ctx->ev_panel, 0)) != cudaSuccess) return e;
+        if ((e = solve_refine(t0 + tA, tB, ctx->aux, nullptr)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(ctx->ev_join, ctx->aux)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, ctx->ev_join, 0)) != cudaSuccess) return e;
+    } else {
+        if ((e = solve_refine(t0, tcount, s, nullptr)) != cudaSuccess) return e;
     }
 
     if constexpr (std::is_same<T, float>::value) {

@@ -132,14 +132,15 @@ def test_tuning_defaults_and_validation(L):
     assert rc == 0
     t = binding.Tuning()
     assert L.pichol_get_tuning(h, ctypes.byref(t)) == 0
-    assert (t.update_strip, t.diag_threads, t.diag_exclusive) == (4, 512, 1)
-    for bad in (dict(update_strip=0), dict(update_strip=9), dict(diag_threads=384), dict(diag_exclusive=2)):
+    assert (t.update_strip, t.diag_threads, t.diag_exclusive, t.eval_overlap) == (4, 512, 1, 0)
+    for bad in (dict(update_strip=0), dict(update_strip=9), dict(diag_threads=384), dict(diag_exclusive=2),
+                dict(eval_overlap=2)):
         b = binding.Tuning(**{**dict(update_strip=4, diag_threads=512, diag_exclusive=1), **bad})
         assert L.pichol_set_tuning(h, ctypes.byref(b)) == 1, bad
-    good = binding.Tuning(update_strip=2, diag_threads=256, diag_exclusive=0)
+    good = binding.Tuning(update_strip=2, diag_threads=256, diag_exclusive=0, eval_overlap=1)
     assert L.pichol_set_tuning(h, ctypes.byref(good)) == 0
     assert L.pichol_get_tuning(h, ctypes.byref(t)) == 0
-    assert (t.update_strip, t.diag_threads, t.diag_exclusive) == (2, 256, 0)
+    assert (t.update_strip, t.diag_threads, t.diag_exclusive, t.eval_overlap) == (2, 256, 0, 1)
     L.pichol_destroy(h)
 
 

@@ -259,9 +259,10 @@ def test_tuning_leaves_every_result_bit_identical(torch_mod, mixed_small):
     ctx = _ctx(prob, k=5, g=6, r=3, q=101, basis="cheb_log", mode="mixed", refine_steps=1)
     X, Y = _dev(torch, prob.X, "mixed"), _dev(torch, prob.Y, "mixed")
     outs = []
-    for tune in (dict(update_strip=4, diag_threads=512, diag_exclusive=1),
-                 dict(update_strip=1, diag_threads=256, diag_exclusive=0),
-                 dict(update_strip=8, diag_threads=512, diag_exclusive=0)):
+    for tune in (dict(update_strip=4, diag_threads=512, diag_exclusive=1, eval_overlap=0),
+                 dict(update_strip=1, diag_threads=256, diag_exclusive=0, eval_overlap=1),
+                 dict(update_strip=8, diag_threads=512, diag_exclusive=0, eval_overlap=0),
+                 dict(update_strip=2, diag_threads=256, diag_exclusive=1, eval_overlap=1)):
         ctx.set_tuning(**tune)
         assert ctx.tuning() == tune
         out = ctx.run(X, Y, want_w=True)

@@ -135,7 +135,8 @@ class ClockSampler:
 
     def __init__(self):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        scratch = os.environ.get("BENCH_SCRATCH", os.path.join(ROOT, ".bench"))
+        self.path = os.path.join(scratch, f"clocks_{os.getpid()}.csv")
 
     def start(self):
         try:

@@ -165,3 +165,24 @@ def test_mchol_state_rules(torch_mod):
     torch.cuda.synchronize()
     assert ctx.info().code == 0
     ctx.close()
+
+
+def test_mchol_on_nan_input_latches_an_error_and_returns(torch_mod):
+    """A NaN in X reaches every exact factorisation of the search: the status
+    word reports the first error (NOT_SPD, or INVALID_ARG from the trace-scaled
+    range), every call returns, and the context still works afterwards."""
+    torch = torch_mod
+    prob = synth.fp64_small(n=600, d=40)
+    X = prob.X.copy()
+    X[5, 3] = np.nan
+    ctx = _ctx(prob, "fp64", q=9, g=4, r=2)
+    ctx.hessian(_dev(torch, X, "fp64"), _dev(torch, prob.Y, "fp64"))
+    ctx.mchol(C0, S0, SMIN)
+    torch.cuda.synchronize()
+    assert ctx.info().code in (1, 2)
+    ctx.clear_status()
+    ctx.hessian(_dev(torch, prob.X, "fp64"), _dev(torch, prob.Y, "fp64"))
+    tr = ctx.mchol(C0, 1.0, 0.5).cpu().numpy()
+    torch.cuda.synchronize()
+    assert ctx.info().code == 0 and np.all(np.isfinite(tr))
+    ctx.close()

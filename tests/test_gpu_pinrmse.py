@@ -100,3 +100,20 @@ def test_pinrmse_needs_the_sampled_factors(torch_mod):
         ctx.eval_pinrmse()
     assert ei.value.code == 7
     ctx.close()
+
+
+def test_pinrmse_interpolates_the_exact_errors_at_the_nodes(torch_mod):
+    """g = r + 1 in the Chebyshev basis: at the sampled grid points PINRMSE is
+    exact CV (the device's own exact path), to the solves' precision."""
+    torch = torch_mod
+    prob = synth.fp64_small(n=800, d=70)
+    k, g, r, q = 4, 4, 3, 13
+    ctx = _ctx(prob, k=k, g=g, r=r, q=q, basis="cheb_log", mode="fp64")
+    ctx.hessian(_dev(torch, prob.X, "fp64"), _dev(torch, prob.Y, "fp64"))
+    ctx.factor_samples()
+    pin = ctx.eval_pinrmse().E.cpu().numpy()
+    ex = ctx.eval_holdout_exact().E.cpu().numpy()
+    torch.cuda.synchronize()
+    idx = oracle.sample_indices(q, g)
+    np.testing.assert_allclose(pin[:, idx], ex[:, idx], rtol=1e-9)
+    ctx.close()

@@ -100,3 +100,16 @@ def test_warm_start_rules(torch_mod):
     torch.cuda.synchronize()
     assert ctx.info().code == 0
     ctx.close()
+
+
+def test_warm_start_with_every_sample_matches_the_plain_fit(torch_mod):
+    """g' = g: Theta_0 + V^+ (T - V Theta_0) = V^+ T, so the device's warm-started
+    errors equal its plain piCholesky errors up to rounding."""
+    torch = torch_mod
+    prob = synth.fp64_small(n=1000, d=90)
+    kw = dict(k=4, g=5, r=3, q=21, basis="cheb_log", mode="fp64")
+    X, Y = _dev(torch, prob.X, "fp64"), _dev(torch, prob.Y, "fp64")
+    a = _ctx(prob, **kw).run(X, Y).E.cpu().numpy()
+    b = _ctx(prob, warm_samples=5, **kw).run(X, Y).E.cpu().numpy()
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(b, a, rtol=1e-10)

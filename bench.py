@@ -906,6 +906,29 @@ def run_own(args):
                "pipelining": "next step's inputs copied on a second stream during this step's factorisation"}
         del Xb, Yb
 
+    # ---- the hold-out gradient in log(lambda) at one lambda -----------------
+    grad = None
+    if rank == 0:
+        import math
+        lg = math.log(float(ctx.lambdas()[q // 2].item()))
+        ctx.holdout_grad(lg)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(10):
+            ctx.holdout_grad(lg)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        grad = {"ms": e0.elapsed_time(e1) / 10, "folds": k, "log_lambda": lg,
+                "what": "E_f and dE_f/dlog(lambda) of every fold at one lambda through the interpolated factor "
+                        "(pichol_holdout_grad after the step's fit)"}
+        # per-stage device time of one call (separate calls with stage timing on)
+        ctx.set_timing(64)
+        ctx.stage_times()
+        ctx.holdout_grad(lg)
+        gst, _ = ctx.stage_times()
+        ctx.set_timing(0)
+        grad["stages_ms"] = {nm: round(v[0], 4) for nm, v in gst.items() if v[1] > 0}
+
     # ---- exact-Cholesky CV with the same kernels ---------------------------
     exact = None
     if not args.no_exact and rank == 0:
@@ -973,6 +996,7 @@ def run_own(args):
         "clocks": clocks,
         "exact_cv": exact,
         "speedup_vs_exact": (value / world / exact["value"]) if exact else None,
+        "holdout_grad": grad,
         "mchol": mchol,
         "pinrmse": pinrmse,
         "warm_start": warm,

@@ -56,44 +56,62 @@ __global__ void k_grad_setup(int basis, int p, int g, double log_lam, const doub
     }
 }
 
-// V = G_f W - Bv_f for every fold (dense G_f, dp x dp): block (tile row I, fold f),
-// thread (row r, column quarter cq) sums its quarter; quarters combined in order.
+// V = G_f W - Bv_f for every fold (dense G_f, dp x dp).  Block (tile row I,
+// fold f) walks the columns of its 64 rows in blocks of 32: the G block and the
+// matching 32 x c block of W are staged in shared memory (coalesced rows),
+// thread (row r, column group cq) multiplies them in the working type, and the
+// per-block sums are added in double.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_grad_gv(const T* __restrict__ G, const T* __restrict__ W, const T* __restrict__ Bv, int64_t dp, int64_t c,
           T* __restrict__ V)
 {
-    __shared__ double part[TB][33];
-    const int I = blockIdx.x, f = blockIdx.y, r = threadIdx.x & 63, cq = threadIdx.x >> 6;
+    constexpr int KB = 32;
+    __shared__ T Gs[TB][KB + 1];
+    __shared__ T Ws[KB][32];
+    const int I = blockIdx.x, f = blockIdx.y, tid = threadIdx.x, r = tid & 63, cq = tid >> 6;
     const int64_t row = (int64_t)I * TB + r;
-    const T* Gr = G + (int64_t)f * dp * dp + row * dp;
+    const T* Gf = G + (int64_t)f * dp * dp + (int64_t)I * TB * dp;
     const T* Wf = W + (int64_t)f * dp * c;
-    double acc[32];
+    double acc[8];
 #pragma unroll
-    for (int o = 0; o < 32; ++o) acc[o] = 0.0;
-    const int64_t q0 = cq * (dp / 4), q1 = q0 + dp / 4;
-    for (int64_t col = q0; col < q1; ++col) {
-        const double gv = (double)Gr[col];
-#pragma unroll
-        for (int o = 0; o < 32; ++o)
-            if (o < c) acc[o] += gv * (double)Wf[col * c + o];
-    }
-    // combine the quarters in a fixed order: (((q3 + q2) + q1) + q0)
-    for (int qq = 3; qq >= 0; --qq) {
-        if (cq == qq) {
-#pragma unroll
-            for (int o = 0; o < 32; ++o) part[r][o] = (qq == 3) ? acc[o] : part[r][o] + acc[o];
+    for (int u = 0; u < 8; ++u) acc[u] = 0.0;
+    const int nb = (int)(dp / KB);
+    for (int J = 0; J < nb; ++J) {
+        __syncthreads();
+        for (int e = tid; e < TB * KB; e += 256) Gs[e / KB][e % KB] = Gf[(int64_t)(e / KB) * dp + J * KB + e % KB];
+        for (int e = tid; e < KB * 32; e += 256) {
+            const int kk = e / 32, o = e % 32;
+            Ws[kk][o] = (o < c) ? Wf[((int64_t)J * KB + kk) * c + o] : T(0);
         }
         __syncthreads();
+        T t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] = T(0);
+#pragma unroll 4
+        for (int kk = 0; kk < KB; ++kk) {
+            const T g = Gs[r][kk];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) t[u] = fma(g, Ws[kk][cq * 8 + u], t[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] += (double)t[u];
     }
-    if (cq == 0) {
-        for (int o = 0; o < c; ++o)
-            V[(int64_t)f * dp * c + row * c + o] = (T)(part[r][o] - (double)Bv[(int64_t)f * dp * c + row * c + o]);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int o = cq * 8 + u;
+        if (o < c) {
+            const int64_t g = (int64_t)f * dp * c + row * c + o;
+            V[g] = (T)(acc[u] - (double)Bv[g]);
+        }
     }
 }
 
 // out_i = sum_{j >= i} M_ji^T x_j with M = sum_m w_m Theta_m (w = phi or phi'),
 // for the four products (M, x) in {L~, L~'} x {W, U} (blockIdx.z = 2 which_m + which_x).
+// M's tiles are evaluated in the working type with w rounded to it, as the
+// solves evaluate L~; each tile's product is summed in the working type and
+// the tiles are added in double.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_grad_tmv(const T* __restrict__ Theta, int p, int64_t ntiles, int nt, int64_t dp, int64_t c,
@@ -108,8 +126,8 @@ k_grad_tmv(const T* __restrict__ Theta, int p, int64_t ntiles, int nt, int64_t d
     const int which_m = combo >> 1, which_x = combo & 1;
     const int col = threadIdx.x & 63, kq = threadIdx.x >> 6;
     const T* x = (which_x ? Uv : Wv) + (int64_t)f * dp * c;
-    double w[MAX_P];
-    for (int m = 0; m < p; ++m) w[m] = gphi[which_m * p + m];
+    T w[MAX_P];
+    for (int m = 0; m < p; ++m) w[m] = (T)gphi[which_m * p + m];
     double acc[32];
 #pragma unroll
     for (int o = 0; o < 32; ++o) acc[o] = 0.0;
@@ -117,21 +135,27 @@ k_grad_tmv(const T* __restrict__ Theta, int p, int64_t ntiles, int nt, int64_t d
         const T* th = Theta + ((int64_t)f * ntiles + tile_index(j, i)) * p * TILE_ELEMS;
         __syncthreads();
         for (int e = threadIdx.x; e < TILE_ELEMS; e += 256) {
-            double v = 0.0;
-            for (int m = 0; m < p; ++m) v += w[m] * (double)th[(int64_t)m * TILE_ELEMS + e];
-            Ms[e / TB][e % TB] = (T)v;
+            T v = w[0] * th[e];
+            for (int m = 1; m < p; ++m) v = fma(w[m], th[(int64_t)m * TILE_ELEMS + e], v);
+            Ms[e / TB][e % TB] = v;
         }
         for (int e = threadIdx.x; e < TB * 32; e += 256) {
             const int kk = e / 32, o = e % 32;
             xs[kk][o] = (o < c) ? x[((int64_t)j * TB + kk) * c + o] : T(0);
         }
         __syncthreads();
+        T t[32];
+#pragma unroll
+        for (int o = 0; o < 32; ++o) t[o] = T(0);
         for (int kk = kq * 16; kk < kq * 16 + 16; ++kk) {
-            const double mv = (double)Ms[kk][col];
+            const T mv = Ms[kk][col];
 #pragma unroll
             for (int o = 0; o < 32; ++o)
-                if (o < c) acc[o] += mv * (double)xs[kk][o];
+                if (o < c) t[o] = fma(mv, xs[kk][o], t[o]);
         }
+#pragma unroll
+        for (int o = 0; o < 32; ++o)
+            if (o < c) acc[o] += (double)t[o];
     }
     __syncthreads();
     for (int qq = 3; qq >= 0; --qq) {

@@ -592,12 +592,20 @@ def mchol_compare(binding, params, cfg, X, Y, stream, exact, E, t_star):
                 ctx.eval_holdout(out=out)
 
         ms = timed(run)
+        # per-stage device time of one more run
+        ctx.set_timing(4096)
+        ctx.stage_times()
+        run()
+        mst, mcomplete = ctx.stage_times()
+        ctx.set_timing(0)
         info = ctx.info()
         trh = tr.cpu().numpy()
         tau = float(trh[0, 1] / 10.0 ** c0)
         last = trh[-1]
         best = int(np.argmin(last[3:6]))
         entry = {"ms": ms, "levels": int(trh.shape[0]), "s_min": s_min,
+                 "stages_ms": {nm: round(v[0], 3) for nm, v in mst.items() if v[1] > 0},
+                 "stage_timing_complete": mcomplete,
                  "exact_factorisations": int(trh.shape[0]) * 3 * cfg["k"],
                  "lambda_rel": float(last[best] / tau), "Ebar": float(last[3 + best]),
                  "device_status": binding.STATUS.get(info.code)}

@@ -340,13 +340,16 @@ cudaError_t plane_map(CUtensorMap* m, const void* buf, int64_t planes)
     return make_map_f32(m, (const float*)buf, TB, (uint64_t)rows, TB, 32, 32) ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// Two lambdas per CTA share each staged coefficient tile; a single system
-// (the gradient's solves) takes one-lambda CTAs instead of leaving half of
-// each CTA's work dead.  A system's arithmetic does not depend on LG.
+// Two lambdas per CTA share each staged coefficient tile.  When every
+// system can have an SM of its own (a single lambda, as in the gradient, or a
+// few, as in an MChol level) the systems take one-lambda CTAs with a deeper
+// copy ring instead: there each CTA's serial chain sets the time, and a
+// two-lambda CTA would double it.  A system's arithmetic does not depend on LG.
 template <typename T, bool EXACT>
 static cudaError_t solve_dispatch(pichol_ctx* ctx, const SolveArgs& sa, cudaStream_t s)
 {
-    if (sa.tcount == 1 && !EXACT) return launch_solve_single(ctx, sa, s);
+    if (sa.tcount == 1 || (int64_t)ctx->cfg.k * sa.tcount <= ctx->nsm)
+        return launch_solve_single(ctx, sa, EXACT, s);
     constexpr int LG = 2;
     switch (pick_cb(ctx->cfg.c)) {
     case 4: return solve_np<T, LG, 4, EXACT>(ctx, sa, s);

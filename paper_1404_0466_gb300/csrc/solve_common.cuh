@@ -590,7 +590,7 @@ inline cudaError_t solve_np(pichol_ctx* ctx, const SolveArgs& sa, cudaStream_t s
     }
 }
 
-// the interpolated solves of a single lambda per fold with one-lambda CTAs
-cudaError_t launch_solve_single(pichol_ctx* ctx, const SolveArgs& sa, cudaStream_t s);
+// the solves of a few systems with one-lambda CTAs (exact: factor tiles)
+cudaError_t launch_solve_single(pichol_ctx* ctx, const SolveArgs& sa, bool exact, cudaStream_t s);
 
 }  // namespace pichol

@@ -254,9 +254,20 @@ def roofline_of(name, ms, launches, cfg, mode, refine, steps, peaks, work=None):
     return info
 
 
-def roofline(stage_ms, cfg, mode, refine, steps, peaks, work=None):
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
+# stage's kernels from one ncu capture of the same code on the same workload:
+# profiles/k_solve_k_resid_mixed_ecc.md (the two residual passes, 291 MB and
+# 299 MB; the stage's third launch, the refinement axpy, is not in it).
+MEASURED_TRAFFIC = {("mixed_ecc", "resid"): 295.0e6}
+
+
+def roofline(stage_ms, cfg, mode, refine, steps, peaks, work=None, workload=None):
     name, (ms, launches) = max(stage_ms.items(), key=lambda kv: kv[1][0])
-    return roofline_of(name, ms, launches, cfg, mode, refine, steps, peaks, work=work)
+    info = roofline_of(name, ms, launches, cfg, mode, refine, steps, peaks, work=work)
+    info["traffic"] = MEASURED_TRAFFIC.get((workload, name))
+    if info["traffic"] is not None:
+        info["traffic_note"] = "bytes per residual pass from ncu (profiles/k_solve_k_resid_mixed_ecc.md)"
+    return info
 
 
 def load_peaks():
@@ -297,6 +308,38 @@ def oracle_sample(prob, cfg, w, E_gpu, t_star):
                                     f"({per_eval:.2f} s each), extrapolated to the fold's {q} lambdas; "
                                     f"{wall:.1f} s of CPU work")},
     }
+
+
+def lapack_sample(prob, cfg):
+    """Exact-Cholesky CV with NumPy's LAPACK and BLAS on the host cores (a
+    competent CPU implementation, for context beside the plain oracle): fold
+    0's Hessian by one GEMM, then Cholesky, two triangular solves and the
+    hold-out error at a few grid lambdas, extrapolated to the fold's q."""
+    import numpy as np
+    import scipy.linalg as sla
+    X = np.asarray(prob.X, dtype=np.float64)
+    Y = np.asarray(prob.Y, dtype=np.float64)
+    n, d = X.shape
+    k, q = cfg["k"], cfg["q"]
+    r0, r1 = 0, n // k
+    t0 = time.perf_counter()
+    Xt, Yt = X[r1:], Y[r1:]
+    H = Xt.T @ Xt
+    B = Xt.T @ Yt
+    tau = float(np.einsum("ij,ij->", X, X)) / d
+    t_fixed = time.perf_counter() - t0
+    lam = tau * cfg["lo"] * (cfg["hi"] / cfg["lo"]) ** (np.arange(q) / max(1, q - 1))
+    idx = [0, q // 2, q - 1]
+    t1 = time.perf_counter()
+    for t in idx:
+        L = np.linalg.cholesky(H + lam[t] * np.eye(d))
+        W = sla.solve_triangular(L.T, sla.solve_triangular(L, B, lower=True), lower=False)
+        float(np.mean((Y[r0:r1] - X[r0:r1] @ W) ** 2))
+    per = (time.perf_counter() - t1) / len(idx)
+    fold_s = t_fixed + q * per
+    return {"value": q / fold_s, "unit": "evals/s", "cores": os.cpu_count() or 1, "kind": "numpy LAPACK exact CV",
+            "sample": (f"fold 0: Hessian by GEMM ({t_fixed:.2f} s), then {len(idx)} of {q} lambdas "
+                       f"({per:.3f} s each: Cholesky, two triangular solves, hold-out error), extrapolated")}
 
 
 # ---------------------------------------------------------------------------
@@ -764,6 +807,20 @@ def run_own(args):
             tune_ms[(strip, dt)] = ta.elapsed_time(tb) / 2
     best = min(tune_ms, key=tune_ms.get) if tune_ms else (4, 512)
     ctx.set_tuning(update_strip=best[0], diag_threads=best[1])
+    # then whether the diagonal-tile CTAs hold their SMs alone
+    excl_ms = {}
+    if not args.profile:
+        for ex in (1, 0):
+            ctx.set_tuning(diag_exclusive=ex)
+            step()
+            ta.record(stream)
+            for _ in range(2):
+                step()
+            tb.record(stream)
+            torch.cuda.synchronize()
+            excl_ms[ex] = ta.elapsed_time(tb) / 2
+    best_ex = min(excl_ms, key=excl_ms.get) if excl_ms else 1
+    ctx.set_tuning(diag_exclusive=best_ex)
     # then the evaluation's two-stream overlap of the solve with the refinement residual
     overlap_ms = {}
     if refine > 0 and w["mode"] == "mixed" and not args.profile:
@@ -778,11 +835,13 @@ def run_own(args):
             overlap_ms[ov] = ta.elapsed_time(tb) / 2
     best_ov = min(overlap_ms, key=overlap_ms.get) if overlap_ms else 0
     if pg is not None:                      # every rank uses rank 0's choice
-        choice = torch.tensor(list(best) + [best_ov], device=dev)
+        choice = torch.tensor(list(best) + [best_ov, best_ex], device=dev)
         pg.broadcast(choice, 0)
-        best, best_ov = tuple(int(v) for v in choice.tolist()[:2]), int(choice.tolist()[2])
-    ctx.set_tuning(update_strip=best[0], diag_threads=best[1], eval_overlap=best_ov)
+        vals = [int(v) for v in choice.tolist()]
+        best, best_ov, best_ex = tuple(vals[:2]), vals[2], vals[3]
+    ctx.set_tuning(update_strip=best[0], diag_threads=best[1], eval_overlap=best_ov, diag_exclusive=best_ex)
     tuning = dict(ctx.tuning(), autotuned_ms={f"strip{a}_diag{b}": round(v, 3) for (a, b), v in tune_ms.items()},
+                  exclusive_ms={f"diag_exclusive{k}": round(v, 3) for k, v in excl_ms.items()},
                   overlap_ms={f"eval_overlap{k}": round(v, 3) for k, v in overlap_ms.items()})
 
     for _ in range(args.warmup):
@@ -957,7 +1016,9 @@ def run_own(args):
         xms = e0.elapsed_time(e1) / reps
         Ex = oute[0].cpu().numpy()
         tx = int(oute[1].cpu().item())
+        gram_ms = sum(stages[st][0] for st in ("gram", "xty") if st in stages) / stage_steps
         exact = {"value": k * q / (xms / 1e3), "unit": "evals/s", "ms_per_step": xms,
+                 "speedup_excluding_gram": (xms - gram_ms) / (ms / args.steps - gram_ms),
                  "t_star": tx, "t_star_pichol": t_star,
                  "min_E_exact": float(np.mean(Ex, axis=0)[tx]),
                  "min_E_pichol": float(np.mean(E, axis=0)[t_star]) if t_star >= 0 else None,
@@ -978,6 +1039,7 @@ def run_own(args):
     if rank != 0:
         return 0
     sample = None if args.no_cpu else oracle_sample(prob, cfg, w, E, t_star)
+    lapack = None if args.no_cpu else lapack_sample(prob, cfg)
     peaks = load_peaks()
     stage_ms = {s: v for s, v in stages.items() if v[1] > 0}
     work = stage_work(cfg, w["mode"], refine, w.get("refine_target", "interpolated"))
@@ -990,7 +1052,7 @@ def run_own(args):
                    "parallelism": f"replicas x{world}", "tuning": tuning},
         "e2e": e2e,
         "gpu_launches": launches,
-        "roofline": roofline(stage_ms, cfg, w["mode"], refine, stage_steps, peaks, work=work),
+        "roofline": roofline(stage_ms, cfg, w["mode"], refine, stage_steps, peaks, work=work, workload=args.workload),
         "kernels_roofline": {nm: {kk: v for kk, v in roofline_of(nm, ms_, la, cfg, w["mode"], refine, stage_steps,
                                                                 peaks, work=work).items()
                                   if kk in ("bound", "achieved", "peak", "unit", "frac", "stage_ms_per_step")}
@@ -1013,6 +1075,8 @@ def run_own(args):
     if sample:
         line["cpu_baseline"] = sample["cpu_baseline"]
         line["err_vs_fp64"] = sample["err_vs_fp64"]
+    if lapack:
+        line["cpu_lapack_exact"] = lapack
     print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()

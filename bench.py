@@ -967,10 +967,17 @@ def run_own(args):
         torch.cuda.synchronize()
         barrier()
         ems = max_over_ranks(e0.elapsed_time(e1), pg, dev)
+        # the host link alone: one copy of X from the pinned buffer
+        e0.record(stream)
+        Xb[1].copy_(Xh, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        h2d_ms = e0.elapsed_time(e1)
         e2e = {"value": job_throughput(world, args.steps, k * q, ems), "unit": "evals/s",
                "h2d_bytes_per_step": Xh.numel() * Xh.element_size() + Yh.numel() * Yh.element_size(),
                "d2h_bytes_per_step": Eh.numel() * 8 + 4, "ms_per_step": ems / args.steps,
-               "pipelining": "next step's inputs copied on a second stream during this step's factorisation"}
+               "pipelining": "next step's inputs copied on a second stream during this step's factorisation",
+               "h2d_GBps_alone": Xh.numel() * Xh.element_size() / (h2d_ms / 1e3) / 1e9}
         del Xb, Yb
 
     # ---- the hold-out gradient in log(lambda) at one lambda -----------------

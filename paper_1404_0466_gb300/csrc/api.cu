@@ -68,7 +68,8 @@ size_t plan(pichol_ctx* ctx, char* base)
     }
     ctx->gW = take((size_t)(3 * k * dp * cc * eb));
     ctx->gDinv = take((size_t)(k * nt * TILE_ELEMS * eb));
-    ctx->gP = (double*)take((size_t)(4 * k * dp * cc * sizeof(double)));
+    ctx->gP = (double*)take((size_t)(GRAD_CHUNKS * 4 * k * dp * cc * sizeof(double)));
+    ctx->gL = take((size_t)(2 * k * ntl * TILE_ELEMS * eb));
     ctx->gphi = (double*)take((size_t)(2 * MAX_P + 1) * sizeof(double));
     ctx->gflags = (int*)take((size_t)(k * nt * sizeof(int)));
     ctx->gdmax = (float*)take((size_t)(k * nt * sizeof(float)));

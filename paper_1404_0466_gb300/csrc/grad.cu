@@ -15,6 +15,7 @@
 #include "internal.cuh"
 
 #include <cfloat>
+#include <type_traits>
 
 namespace pichol {
 
@@ -107,67 +108,114 @@ k_grad_gv(const T* __restrict__ G, const T* __restrict__ W, const T* __restrict_
     }
 }
 
-// out_i = sum_{j >= i} M_ji^T x_j with M = sum_m w_m Theta_m (w = phi or phi'),
-// for the four products (M, x) in {L~, L~'} x {W, U} (blockIdx.z = 2 which_m + which_x).
-// M's tiles are evaluated in the working type with w rounded to it, as the
-// solves evaluate L~; each tile's product is summed in the working type and
-// the tiles are added in double.
+// L~ = sum_m phi_m Theta_m and L~' = sum_m phi_m' Theta_m of every fold, tile by
+// tile, into ML[0] and ML[1] ([which][f][tile][64 x 64]), in the working type
+// with the weights rounded to it, as the solves evaluate L~.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_grad_tmv(const T* __restrict__ Theta, int p, int64_t ntiles, int nt, int64_t dp, int64_t c,
-           const double* __restrict__ gphi, const T* __restrict__ Wv, const T* __restrict__ Uv,
-           double* __restrict__ out)
+k_grad_eval(const T* __restrict__ Theta, int p, int64_t ntiles, int k, const double* __restrict__ gphi,
+            T* __restrict__ ML)
+{
+    const int64_t tile = blockIdx.x;
+    const int f = blockIdx.y;
+    T w[2][MAX_P];
+#pragma unroll
+    for (int m = 0; m < MAX_P; ++m) {
+        w[0][m] = m < p ? (T)gphi[m] : T(0);
+        w[1][m] = m < p ? (T)gphi[p + m] : T(0);
+    }
+    const T* th = Theta + ((int64_t)f * ntiles + tile) * p * TILE_ELEMS;
+    T* o0 = ML + ((int64_t)f * ntiles + tile) * TILE_ELEMS;
+    T* o1 = ML + (((int64_t)k + f) * ntiles + tile) * TILE_ELEMS;
+    for (int e = threadIdx.x; e < TILE_ELEMS; e += 256) {
+        T v0 = w[0][0] * th[e], v1 = w[1][0] * th[e];
+#pragma unroll
+        for (int m = 1; m < MAX_P; ++m)
+            if (m < p) {
+                const T x = th[(int64_t)m * TILE_ELEMS + e];
+                v0 = fma(w[0][m], x, v0);
+                v1 = fma(w[1][m], x, v1);
+            }
+        o0[e] = v0;
+        o1[e] = v1;
+    }
+}
+
+// out_i = sum_{j >= i} M_ji^T x_j for the four products (M, x) in {L~, L~'} x
+// {W, U} (blockIdx.z = 2 which_m + which_x), M's tiles read from ML.  Tile row
+// i's range of j is split into nch chunks of at most clen tiles (blockIdx.x =
+// i nch + chunk), so every CTA walks a few tiles; each chunk's partial sums go
+// to its own slot (k_grad_sum adds the slots in order).  Each tile's product
+// is summed in the working type and the tiles are added in double.
+template <typename T, int CB>
+__global__ void __launch_bounds__(256)
+k_grad_tmv(const T* __restrict__ ML, int64_t ntiles, int nt, int nch, int clen, int64_t dp, int64_t c,
+           const T* __restrict__ Wv, const T* __restrict__ Uv, double* __restrict__ out)
 {
     extern __shared__ __align__(16) unsigned char gsm[];
-    T (*Ms)[TB + 1] = reinterpret_cast<T (*)[TB + 1]>(gsm);                                   // 64 x 65
-    T (*xs)[33] = reinterpret_cast<T (*)[33]>(gsm + sizeof(T) * TB * (TB + 1));             // 64 x 33
-    double (*red)[33] = reinterpret_cast<double (*)[33]>(gsm + sizeof(T) * TB * (TB + 1 + 33)); // 64 x 33
-    const int i = blockIdx.x, f = blockIdx.y, combo = blockIdx.z;
+    double (*red)[CB + 1] = reinterpret_cast<double (*)[CB + 1]>(gsm);                          // 64 x (CB+1)
+    T (*Ms)[TB + 1] = reinterpret_cast<T (*)[TB + 1]>(gsm + sizeof(double) * TB * (CB + 1));   // 64 x 65
+    T (*xs)[CB] = reinterpret_cast<T (*)[CB]>(gsm + sizeof(double) * TB * (CB + 1) + sizeof(T) * TB * (TB + 1));
+    const int i = blockIdx.x / nch, chunk = blockIdx.x % nch, f = blockIdx.y, combo = blockIdx.z;
+    const int j0 = i + chunk * clen, j1 = (j0 + clen < nt) ? j0 + clen : nt;   // empty when j0 >= nt
     const int which_m = combo >> 1, which_x = combo & 1;
     const int col = threadIdx.x & 63, kq = threadIdx.x >> 6;
     const T* x = (which_x ? Uv : Wv) + (int64_t)f * dp * c;
-    T w[MAX_P];
-    for (int m = 0; m < p; ++m) w[m] = (T)gphi[which_m * p + m];
-    double acc[32];
+    const T* M = ML + ((int64_t)which_m * gridDim.y + f) * ntiles * TILE_ELEMS;
+    double acc[CB];
 #pragma unroll
-    for (int o = 0; o < 32; ++o) acc[o] = 0.0;
-    for (int j = i; j < nt; ++j) {
-        const T* th = Theta + ((int64_t)f * ntiles + tile_index(j, i)) * p * TILE_ELEMS;
+    for (int o = 0; o < CB; ++o) acc[o] = 0.0;
+    for (int j = j0; j < j1; ++j) {
+        const T* mt = M + tile_index(j, i) * TILE_ELEMS;
         __syncthreads();
-        for (int e = threadIdx.x; e < TILE_ELEMS; e += 256) {
-            T v = w[0] * th[e];
-            for (int m = 1; m < p; ++m) v = fma(w[m], th[(int64_t)m * TILE_ELEMS + e], v);
-            Ms[e / TB][e % TB] = v;
-        }
-        for (int e = threadIdx.x; e < TB * 32; e += 256) {
-            const int kk = e / 32, o = e % 32;
+        for (int e = threadIdx.x; e < TILE_ELEMS; e += 256) Ms[e / TB][e % TB] = mt[e];
+        for (int e = threadIdx.x; e < TB * CB; e += 256) {
+            const int kk = e / CB, o = e % CB;
             xs[kk][o] = (o < c) ? x[((int64_t)j * TB + kk) * c + o] : T(0);
         }
         __syncthreads();
-        T t[32];
+        if constexpr (std::is_same<T, double>::value) {
+#pragma unroll 4
+            for (int kk = kq * 16; kk < kq * 16 + 16; ++kk) {
+                const double mv = Ms[kk][col];
 #pragma unroll
-        for (int o = 0; o < 32; ++o) t[o] = T(0);
-        for (int kk = kq * 16; kk < kq * 16 + 16; ++kk) {
-            const T mv = Ms[kk][col];
+                for (int o = 0; o < CB; ++o) acc[o] = fma(mv, xs[kk][o], acc[o]);
+            }
+        } else {
+            T t[CB];
 #pragma unroll
-            for (int o = 0; o < 32; ++o)
-                if (o < c) t[o] = fma(mv, xs[kk][o], t[o]);
+            for (int o = 0; o < CB; ++o) t[o] = T(0);
+#pragma unroll 4
+            for (int kk = kq * 16; kk < kq * 16 + 16; ++kk) {
+                const T mv = Ms[kk][col];
+#pragma unroll
+                for (int o = 0; o < CB; ++o) t[o] = fma(mv, xs[kk][o], t[o]);
+            }
+#pragma unroll
+            for (int o = 0; o < CB; ++o) acc[o] += (double)t[o];
         }
-#pragma unroll
-        for (int o = 0; o < 32; ++o)
-            if (o < c) acc[o] += (double)t[o];
     }
     __syncthreads();
     for (int qq = 3; qq >= 0; --qq) {
         if (kq == qq) {
 #pragma unroll
-            for (int o = 0; o < 32; ++o) red[col][o] = (qq == 3) ? acc[o] : red[col][o] + acc[o];
+            for (int o = 0; o < CB; ++o) red[col][o] = (qq == 3) ? acc[o] : red[col][o] + acc[o];
         }
         __syncthreads();
     }
     if (kq == 0) {
-        double* dst = out + ((int64_t)combo * gridDim.y + f) * dp * c + ((int64_t)i * TB + col) * c;
+        double* dst = out + (((int64_t)chunk * 4 + combo) * gridDim.y + f) * dp * c + ((int64_t)i * TB + col) * c;
         for (int o = 0; o < c; ++o) dst[o] = red[col][o];
+    }
+}
+
+// slot 0 of P += slots 1 .. nch-1, in slot order (n values per slot)
+__global__ void k_grad_sum(double* __restrict__ P, int nch, int64_t n)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        double v = P[e];
+        for (int ch = 1; ch < nch; ++ch) v += P[(int64_t)ch * n + e];
+        P[e] = v;
     }
 }
 
@@ -175,13 +223,14 @@ k_grad_tmv(const T* __restrict__ Theta, int p, int64_t ntiles, int nt, int64_t d
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_grad_final(const T* __restrict__ W, const T* __restrict__ V, const T* __restrict__ Bv, const double* __restrict__ P,
-             const double* __restrict__ yy, const int64_t* __restrict__ nfc, const double* __restrict__ glam,
-             int k, int64_t dp, int64_t c, double* __restrict__ E_out, double* __restrict__ dE_out)
+             const double* __restrict__ yy, const int64_t* __restrict__ nfc, const double* __restrict__ glam, int k,
+             int64_t dp, int64_t c, double* __restrict__ E_out, double* __restrict__ dE_out)
 {
     __shared__ double red[2][256];
     const int f = blockIdx.x;
     const int64_t len = dp * c, base = (int64_t)f * len;
-    // products: combo 0 = L~^T W (P1), 1 = L~^T U (Q1), 2 = L~'^T W (P2), 3 = L~'^T U (Q2)
+    // products (slot 0 after k_grad_sum): combo 0 = L~^T W (P1), 1 = L~^T U (Q1),
+    // 2 = L~'^T W (P2), 3 = L~'^T U (Q2)
     const double* P1 = P + ((int64_t)0 * k + f) * len;
     const double* Q1 = P + ((int64_t)1 * k + f) * len;
     const double* P2 = P + ((int64_t)2 * k + f) * len;
@@ -209,6 +258,22 @@ k_grad_final(const T* __restrict__ W, const T* __restrict__ V, const T* __restri
     }
 }
 
+template <typename T, int CB>
+static cudaError_t launch_tmv(dim3 grid, const T* ML, pichol_ctx* ctx, int nch, int clen, const T* gW, const T* gU,
+                              cudaStream_t s)
+{
+    const int smem = (int)(sizeof(double) * TB * (CB + 1) + sizeof(T) * TB * (TB + 1) + sizeof(T) * TB * CB);
+    static bool attr_done = false;
+    if (!attr_done) {
+        const cudaError_t e = cudaFuncSetAttribute(k_grad_tmv<T, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    k_grad_tmv<T, CB><<<grid, 256, smem, s>>>(ML, ctx->ntiles, ctx->nt, nch, clen, ctx->dp, ctx->cfg.c, gW, gU,
+                                              ctx->gP);
+    return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t grad_impl(pichol_ctx* ctx, double log_lam, double* E_out, double* dE_out, cudaStream_t s)
 {
@@ -231,24 +296,36 @@ static cudaError_t grad_impl(pichol_ctx* ctx, double log_lam, double* E_out, dou
     ctx->launches++;
     e = launch_diag_solve_one(ctx, ctx->gphi, gV, 1, gU, nullptr, s);   // same lambda: reuse the inverses
     if (e != cudaSuccess) return e;
-    const int tmv_smem = (int)(sizeof(T) * TB * (TB + 1 + 33) + sizeof(double) * TB * 33);
-    static bool attr_done = false;
-    if (!attr_done) {
-        e = cudaFuncSetAttribute(k_grad_tmv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, tmv_smem);
-        if (e != cudaSuccess) return e;
-        attr_done = true;
+    // tile row i's tiles j = i .. nt-1 in at most GRAD_CHUNKS chunks of clen tiles
+    const int nch = ctx->nt < GRAD_CHUNKS ? ctx->nt : GRAD_CHUNKS;
+    const int clen = (ctx->nt + nch - 1) / nch;
+    T* ML = (T*)ctx->gL;
+    {
+        StageScope sc_(ctx, ST_RESID, s);
+        k_grad_eval<T><<<dim3((unsigned)ctx->ntiles, cf.k), 256, 0, s>>>((const T*)ctx->Theta, ctx->p, ctx->ntiles,
+                                                                        cf.k, ctx->gphi, ML);
     }
     {
         StageScope sc_(ctx, ST_RESID, s);
-        k_grad_tmv<T><<<dim3(ctx->nt, cf.k, 4), 256, tmv_smem, s>>>((const T*)ctx->Theta, ctx->p, ctx->ntiles,
-                                                                     ctx->nt, dp, c, ctx->gphi, gW, gU, ctx->gP);
+        const dim3 grid(ctx->nt * nch, cf.k, 4);
+        if (c <= 4)
+            e = launch_tmv<T, 4>(grid, ML, ctx, nch, clen, gW, gU, s);
+        else if (c <= 12)
+            e = launch_tmv<T, 12>(grid, ML, ctx, nch, clen, gW, gU, s);
+        else
+            e = launch_tmv<T, 32>(grid, ML, ctx, nch, clen, gW, gU, s);
+        if (e != cudaSuccess) return e;
+    }
+    {
+        StageScope sc_(ctx, ST_RESID, s);
+        k_grad_sum<<<1024, 256, 0, s>>>(ctx->gP, nch, (int64_t)4 * cf.k * dp * c);
     }
     {
         StageScope sc_(ctx, ST_SELECT, s);
         k_grad_final<T><<<cf.k, 256, 0, s>>>(gW, gV, (const T*)ctx->Bv, ctx->gP, ctx->yy, ctx->nfc,
                                              ctx->gphi + 2 * MAX_P, cf.k, dp, c, E_out, dE_out);
     }
-    ctx->launches += 2;
+    ctx->launches += 4;
     return cudaGetLastError();
 }
 

@@ -29,6 +29,7 @@ constexpr int TILE_ELEMS = TB * TB;
 constexpr int MAX_P = 8;                 // r + 1 <= 8
 constexpr int MAX_G = 32;                // sampled lambdas
 constexpr int MAX_K = 64;                // folds
+constexpr int GRAD_CHUNKS = 8;           // chunks of a tile row in the gradient's triangular products
 
 struct DevStatus {
     int code;
@@ -148,7 +149,8 @@ struct pichol_ctx {
     // gradient in log(lambda) at one lambda (pichol_holdout_grad)
     void* gW;            // 3 x k x dp x c: W, U, V
     void* gDinv;         // k x nt x TB^2
-    double* gP;          // 4 x k x dp x c: L~^T W, L~^T U, L~'^T W, L~'^T U
+    double* gP;          // GRAD_CHUNKS x 4 x k x dp x c: chunks of L~^T W, L~^T U, L~'^T W, L~'^T U
+    void* gL;            // 2 x k x ntiles x TB^2: L~ and L~' at the gradient's lambda
     double* gphi;        // phi (MAX_P), phi' (MAX_P), lambda
     int* gflags;         // k x nt
     float* gdmax;

@@ -928,9 +928,10 @@ def run_own(args):
 
     # ---- end to end: pinned host in, scores and argmin out -----------------
     # The next step's X, Y are copied on a separate stream into the other half
-    # of a double buffer as soon as this step's normal-equation blocks (the only
-    # reader of X, Y) are formed, so the copies overlap the factorisation, fit
-    # and solves; every copy is inside the timed region.
+    # of a double buffer (the normal-equation blocks are X and Y's only reader),
+    # started after this step's fit so that they overlap the solves and
+    # refinement rather than the factorisation; every copy is inside the timed
+    # region.
     e2e = None
     if not args.no_e2e:
         Eh = torch.empty((k, q), dtype=torch.float64).pin_memory()
@@ -951,15 +952,17 @@ def run_own(args):
             b = i % 2
             stream.wait_event(ready[b])
             ctx.hessian(Xb[b], Yb[b])
+            ctx.factor_samples()
+            ctx.fit()
             if i + 1 < args.steps:
+                # the copy streams through L2: start it after the factorisation, whose
+                # working set it would evict, beside the ALU-bound evaluation
                 formed.record(stream)
                 cs.wait_event(formed)
                 with torch.cuda.stream(cs):
                     Xb[1 - b].copy_(Xh, non_blocking=True)
                     Yb[1 - b].copy_(Yh, non_blocking=True)
                     ready[1 - b].record(cs)
-            ctx.factor_samples()
-            ctx.fit()
             ctx.eval_holdout(out=out)
             Eh.copy_(out[0], non_blocking=True)
             th.copy_(out[1], non_blocking=True)
@@ -976,7 +979,7 @@ def run_own(args):
         e2e = {"value": job_throughput(world, args.steps, k * q, ems), "unit": "evals/s",
                "h2d_bytes_per_step": Xh.numel() * Xh.element_size() + Yh.numel() * Yh.element_size(),
                "d2h_bytes_per_step": Eh.numel() * 8 + 4, "ms_per_step": ems / args.steps,
-               "pipelining": "next step's inputs copied on a second stream during this step's factorisation",
+               "pipelining": "next step's inputs copied on a second stream during this step's evaluation",
                "h2d_GBps_alone": Xh.numel() * Xh.element_size() / (h2d_ms / 1e3) / 1e9}
         del Xb, Yb
 

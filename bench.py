@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time eager calls instead of one CUDA graph per step")
     ap.add_argument("--profile", action="store_true", help="warm-up + steps only, for ncu")
+    ap.add_argument("--profile-grad", action="store_true",
+                    help="as --profile, then two hold-out gradient calls at the grid's middle lambda")
     return ap.parse_args()
 
 
@@ -853,6 +855,11 @@ def run_own(args):
     if args.profile:
         for _ in range(args.steps):
             step()
+        if args.profile_grad:
+            import math
+            lg = math.log(float(ctx.lambdas()[q // 2].item()))
+            for _ in range(2):
+                ctx.holdout_grad(lg)
         torch.cuda.synchronize()
         return 0
 
@@ -1095,6 +1102,8 @@ def run_own(args):
 
 def main():
     args = parse()
+    if args.profile_grad:
+        args.profile = True
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched_uneven":

@@ -1057,6 +1057,10 @@ def run_own(args):
         return 0
     sample = None if args.no_cpu else oracle_sample(prob, cfg, w, E, t_star)
     lapack = None if args.no_cpu else lapack_sample(prob, cfg)
+    # the FP32 and FP64 pipes measured on this GPU (the roofline keeps the derived FP32 and
+    # nominal FP64 peaks; these are reported beside them)
+    pipes = {"fp32_fma_tflops": binding.probe_fma(False, 1 << 14), "fp64_fma_tflops": binding.probe_fma(True, 1 << 12),
+             "method": "8 independent FMA chains per thread, 8 CTAs of 256 threads per SM (pichol_probe_fma)"}
     peaks = load_peaks()
     stage_ms = {s: v for s, v in stages.items() if v[1] > 0}
     work = stage_work(cfg, w["mode"], refine, w.get("refine_target", "interpolated"))
@@ -1094,6 +1098,7 @@ def run_own(args):
         line["err_vs_fp64"] = sample["err_vs_fp64"]
     if lapack:
         line["cpu_lapack_exact"] = lapack
+    line["measured_pipes"] = pipes
     print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()

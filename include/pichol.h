@@ -299,6 +299,14 @@ PICHOL_API pichol_status pichol_check_timeout(pichol_ctx* ctx, int64_t cycles, v
  * Needs no context.  For tests. */
 PICHOL_API pichol_status pichol_check_rsqrt(int64_t n, uint64_t seed, double* max_rel_err, void* stream);
 
+/* Sustained fused multiply-add rate of the current device's FP32 (fp64 = 0) or
+ * FP64 (fp64 = 1) pipes, for roofline denominators: 8 CTAs of 256 threads per
+ * SM, each thread running eight independent FMA chains of `iters` steps
+ * (1 .. 2^24), on the legacy default stream, timed with CUDA events (the
+ * second of two runs).  *tflops (host) = 2 x FMAs / seconds / 1e12.  Needs no
+ * context; synchronises the device. */
+PICHOL_API pichol_status pichol_probe_fma(int32_t fp64, int64_t iters, double* tflops);
+
 /* Number of kernel launches this context has enqueued since creation. */
 PICHOL_API int64_t pichol_launch_count(const pichol_ctx* ctx);
 

@@ -34,7 +34,7 @@ EXPORTS = [
     "pichol_batch_run", "pichol_batch_get_info", "pichol_batch_launch_count", "pichol_batch_destroy",
     "pichol_batch_set_timing", "pichol_batch_stage_times",
     "pichol_get_tuning", "pichol_set_tuning", "pichol_batch_set_tuning", "pichol_check_timeout",
-    "pichol_mchol", "pichol_mchol_levels", "pichol_check_rsqrt", "pichol_eval_pinrmse",
+    "pichol_mchol", "pichol_mchol_levels", "pichol_check_rsqrt", "pichol_eval_pinrmse", "pichol_probe_fma",
 ]
 STAGES = ["gram", "xty", "setup", "chol_init", "chol_diag", "chol_panel", "chol_update", "fit",
           "diag_inv", "solve", "resid", "score", "select", "misc"]
@@ -104,6 +104,7 @@ def lib():
         "pichol_mchol_levels": ([ctypes.c_double, ctypes.c_double, ctypes.POINTER(i32)], ctypes.c_int),
         "pichol_check_rsqrt": ([i64, ctypes.c_uint64, vp, vp], ctypes.c_int),
         "pichol_eval_pinrmse": ([vp, vp, vp, vp], ctypes.c_int),
+        "pichol_probe_fma": ([i32, i64, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "pichol_batch_create": ([ctypes.POINTER(Config), i32, i32, ctypes.POINTER(vp)], ctypes.c_int),
         "pichol_batch_workspace_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
         "pichol_batch_set_workspace": ([vp, vp, ctypes.c_size_t], ctypes.c_int),
@@ -357,6 +358,13 @@ def check_rsqrt(n: int, seed: int = 1, stream=None) -> float:
     _check(lib().pichol_check_rsqrt(int(n), int(seed), ctypes.c_void_p(out.data_ptr()),
                                     ctypes.c_void_p(_stream_ptr(stream))), "pichol_check_rsqrt")
     return float(out.cpu().item())
+
+
+def probe_fma(fp64: bool, iters: int = 1 << 14) -> float:
+    """Measured FMA throughput of the FP32 or FP64 pipes in TFLOP/s (pichol_probe_fma)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().pichol_probe_fma(1 if fp64 else 0, int(iters), ctypes.byref(out)), "pichol_probe_fma")
+    return float(out.value)
 
 
 def mchol_levels(s: float, s_min: float) -> int:

@@ -322,3 +322,14 @@ def test_pivot_rsqrt_matches_library_within_a_few_ulps(torch_mod):
     from paper_1404_0466_gb300 import binding
     err = binding.check_rsqrt(1 << 22, seed=3)
     assert 0.0 <= err <= 4 * 2.0 ** -53, err
+
+
+def test_fma_probe_reports_plausible_pipe_rates(torch_mod):
+    """The FP32 pipes are tens of TFLOP/s on this part and the FP64 pipes a
+    small fraction of that (GB300: one FP64 warp instruction per 64 cycles per
+    sub-partition)."""
+    from paper_1404_0466_gb300 import binding
+    f32 = binding.probe_fma(False, 1 << 12)
+    f64 = binding.probe_fma(True, 1 << 10)
+    assert 10.0 < f32 < 200.0, f32
+    assert 0.05 < f64 < f32 / 8, (f64, f32)

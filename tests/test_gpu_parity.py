@@ -333,3 +333,27 @@ def test_fma_probe_reports_plausible_pipe_rates(torch_mod):
     f64 = binding.probe_fma(True, 1 << 10)
     assert 10.0 < f32 < 200.0, f32
     assert 0.05 < f64 < f32 / 8, (f64, f32)
+
+
+def test_unusable_interpolated_diagonal_scores_inf(torch_mod):
+    """Over twelve decades with g = r + 1 = 3 the interpolated factor's diagonal
+    turns negative on part of the grid: the oracle flags 27 of the 63 (fold,
+    lambda) pairs, each with min diag = -max |diag|, while every other pair keeps
+    min diag >= 0.24 max |diag|.  The device scores exactly those pairs +inf,
+    counts them, matches the oracle elsewhere (double precision) and picks the
+    same lambda; nothing is latched as an error."""
+    torch = torch_mod
+    prob = synth.spectral_gaussian(300, 24, 2, seed=0, decay=2.0)
+    kw = dict(k=3, g=3, r=2, q=21, basis="cheb_log")
+    ref = oracle.cv(prob.X, prob.Y, lo=1e-9, hi=1e3, **kw)
+    assert ref.unusable.sum() == 27
+    ctx = _ctx(prob, lam_lo=1e-9, lam_hi=1e3, mode="fp64", **kw)
+    out = ctx.run(_dev(torch, prob.X, "fp64"), _dev(torch, prob.Y, "fp64"))
+    E = out.E.cpu().numpy()
+    info = ctx.info()
+    assert info.code == 0
+    assert np.array_equal(np.isinf(E), ref.unusable)
+    assert info.unusable == 27
+    fin = ~ref.unusable
+    assert np.max(np.abs(E[fin] - ref.E[fin]) / ref.E[fin]) <= 1e-9
+    assert int(out.t_star.cpu().item()) == ref.t_star

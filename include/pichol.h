@@ -10,6 +10,13 @@
  * error at all q lambdas through triangular solves with the interpolated
  * factor (Sec. 3.2 and the last paragraph of Sec. 3.3).
  *
+ * Around that path: exact-Cholesky CV with the same kernels (the `Chol`
+ * comparator of Sec. 6.2), the multi-level range search MChol (Sec. 6.2) that
+ * can narrow the grid before piCholesky, PINRMSE (the sampled hold-out errors
+ * interpolated directly, the paper's supplementary comparator), a warm start
+ * of the fit across folds (the future work of Sec. 7), the derivative of the
+ * hold-out error in log(lambda), and batches of independent problems.
+ *
  * Conventions shared by every call:
  *  - Pointers are DEVICE pointers owned by the caller unless marked "host".
  *  - Matrices are row-major.  X is n x d, Y is n x c, both of the mode's input

@@ -175,3 +175,21 @@ def test_warm_samples_validation(L):
     rc, h = _create(L, _cfg(L, g=12, r=3, q=31, warm_samples=8))
     assert rc == 0
     L.pichol_destroy(h)
+
+
+def test_new_entry_points_check_arguments_without_a_gpu(L):
+    """Argument and state checks that return before any CUDA call."""
+    E = ctypes.c_void_p(0x1000)
+    assert L.pichol_eval_pinrmse(None, E, E, None) == 1
+    rc, h = _create(L, _cfg(L))
+    assert L.pichol_eval_pinrmse(h, None, E, None) == 1
+    assert L.pichol_eval_pinrmse(h, E, E, None) == 4                 # no workspace yet
+    L.pichol_destroy(h)
+    out = ctypes.c_double()
+    assert L.pichol_probe_fma(2, 1024, ctypes.byref(out)) == 1
+    assert L.pichol_probe_fma(0, 0, ctypes.byref(out)) == 1
+    assert L.pichol_probe_fma(1, (1 << 24) + 1, ctypes.byref(out)) == 1
+    assert L.pichol_probe_fma(0, 1024, None) == 1
+    assert L.pichol_check_rsqrt(0, 1, E, None) == 1
+    assert L.pichol_check_rsqrt((1 << 32) + 1, 1, E, None) == 1
+    assert L.pichol_check_rsqrt(1024, 1, None, None) == 1

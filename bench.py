@@ -312,6 +312,26 @@ def oracle_sample(prob, cfg, w, E_gpu, t_star):
     }
 
 
+def oracle_exact_sample(prob, cfg, nlam=2):
+    """The FP64 oracle's exact-Cholesky CV (the `Chol` comparator) on the host
+    cores: fold 0 at nlam grid lambdas, extrapolated to the fold's q."""
+    import oracle
+    q = cfg["q"]
+    idx = [q // 2 + i for i in range(nlam)]
+    tm = {}
+    t0 = time.perf_counter()
+    oracle.cv(prob.X, prob.Y, k=cfg["k"], g=1, r=0, q=q, lo=cfg["lo"], hi=cfg["hi"], exact=True, folds=[0],
+              lam_idx=idx, timings=tm)
+    wall = time.perf_counter() - t0
+    per_eval = tm["eval"] / max(1, tm["n_eval"])
+    fold_s = tm["setup"] + tm["fold"] + q * per_eval
+    return {"value": q / fold_s, "unit": "evals/s", "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+            "kind": "oracle exact CV",
+            "sample": (f"fold 0: Hessian ({tm['setup'] + tm['fold']:.1f} s) and {len(idx)} of {q} lambdas "
+                       f"({per_eval:.2f} s each: exact factor, solves, hold-out error), extrapolated; "
+                       f"{wall:.1f} s of CPU work")}
+
+
 def lapack_sample(prob, cfg):
     """Exact-Cholesky CV with NumPy's LAPACK and BLAS on the host cores (a
     competent CPU implementation, for context beside the plain oracle): fold
@@ -1066,6 +1086,12 @@ def run_own(args):
         return 0
     sample = None if args.no_cpu else oracle_sample(prob, cfg, w, E, t_star)
     lapack = None if args.no_cpu else lapack_sample(prob, cfg)
+    oracle_exact = None
+    if not args.no_cpu:
+        try:
+            oracle_exact = oracle_exact_sample(prob, cfg)
+        except Exception as exc:                      # context only: never costs the line
+            oracle_exact = {"unavailable": f"{type(exc).__name__}: {exc}"}
     # the FP32 and FP64 pipes measured on this GPU (the roofline keeps the derived FP32 and
     # nominal FP64 peaks; these are reported beside them)
     pipes = {"fp32_fma_tflops": binding.probe_fma(False, 1 << 14), "fp64_fma_tflops": binding.probe_fma(True, 1 << 12),
@@ -1107,6 +1133,8 @@ def run_own(args):
         line["err_vs_fp64"] = sample["err_vs_fp64"]
     if lapack:
         line["cpu_lapack_exact"] = lapack
+    if oracle_exact:
+        line["cpu_oracle_exact"] = oracle_exact
     line["measured_pipes"] = pipes
     print(json.dumps(line), flush=True)
     if pg is not None:

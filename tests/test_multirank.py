@@ -81,3 +81,14 @@ def test_reference_arm_prints_one_contract_line():
     assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_host_core_samples_run_on_a_small_case():
+    """The bench's host-core samples (the oracle's piCholesky and exact CV, and
+    NumPy's LAPACK exact CV) return positive rates with their descriptions."""
+    from paper_1404_0466_gb300 import synth
+    prob = synth.fp64_small(n=512, d=64)
+    cfg = dict(synth.FP64_SMALL, n=512, d=64)
+    for fn in (bench.oracle_exact_sample, bench.lapack_sample):
+        out = fn(prob, cfg)
+        assert out["value"] > 0 and out["unit"] == "evals/s" and out["cores"] >= 1 and out["sample"]

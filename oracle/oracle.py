@@ -665,3 +665,28 @@ def pinrmse(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float
         res.Ebar = E.mean(axis=0)
         res.t_star = argmin_first(res.Ebar)
     return res
+
+
+# ----------------------------------------------------------------------------
+# NRMSE of the fit (the paper's Sec. 6.6 diagnostic)
+# ----------------------------------------------------------------------------
+
+def nrmse_curve(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e1,
+                basis: str = BASIS_MONO, scale_by_trace: bool = True, fold: int = 0) -> np.ndarray:
+    """NRMSE of Algorithm 1's fit at every grid lambda of one fold (Sec. 6.6):
+    the root mean squared difference between the interpolated and the exact
+    factor entries (the D lower-triangular entries), divided by the root mean
+    squared deviation of the exact entries from their mean, so that predicting
+    the mean scores 1."""
+    res = cv(X, Y, k=k, g=g, r=r, q=q, lo=lo, hi=hi, basis=basis, scale_by_trace=scale_by_trace,
+             folds=[fold], lam_idx=[], keep=True)
+    d = _f64(X).shape[1]
+    Hf = normal_blocks(X, Y, fold_offsets(_f64(X).shape[0], k)[fold], fold_offsets(_f64(X).shape[0], k)[fold + 1])[0]
+    lam_s = res.lam[res.sample_idx]
+    Phi = basis_values(basis, res.lam, lam_s, r + 1)
+    out = np.empty(q)
+    for t in range(q):
+        target = vec_lower(cholesky(Hf + res.lam[t] * np.eye(d)))
+        pred = eval_poly(Phi[t], res.theta[fold])
+        out[t] = np.sqrt(np.mean((pred - target) ** 2)) / np.sqrt(np.mean((target - target.mean()) ** 2))
+    return out

@@ -691,3 +691,35 @@ def test_warm_start_arguments():
             orc.cv(p.X, p.Y, k=3, g=5, r=2, q=11, warm=bad)
     with pytest.raises(ValueError):
         orc.cv(p.X, p.Y, k=3, g=5, r=2, q=11, warm=2, exact=True)
+
+
+# ----------------------------------------------------------------------------
+# NRMSE of the fit (Sec. 6.6 diagnostic)
+# ----------------------------------------------------------------------------
+
+def test_nrmse_is_zero_at_the_nodes_and_one_for_the_mean():
+    """g = r + 1: the fit interpolates, so the NRMSE vanishes at the sampled
+    grid points; and the normalisation makes a prediction by the targets' mean
+    score exactly 1 (checked on the definition with the exact factor)."""
+    p = synth.spectral_gaussian(200, 10, 2, seed=111)
+    k, g, r, q = 4, 4, 3, 13
+    curve = orc.nrmse_curve(p.X, p.Y, k=k, g=g, r=r, q=q, basis="cheb_log")
+    idx = orc.sample_indices(q, g)
+    assert np.all(curve[idx] < 1e-12)
+    assert np.all(curve >= 0) and np.all(np.isfinite(curve))
+    # the normalisation: the mean predictor's NRMSE is 1 by construction
+    H, _ = orc.normal_blocks(p.X, p.Y, *orc.fold_offsets(200, k)[0:2])
+    t = orc.vec_lower(np.linalg.cholesky(H + 0.5 * np.eye(10)))
+    mean_pred = np.full_like(t, t.mean())
+    assert abs(np.sqrt(np.mean((mean_pred - t) ** 2)) / np.sqrt(np.mean((t - t.mean()) ** 2)) - 1.0) < 1e-15
+
+
+def test_nrmse_is_small_inside_a_well_sampled_range():
+    """A narrow, well-sampled range fits the factors closely (the paper reports a
+    maximum of 0.0457 on its data); a four-decade range with g = 3 samples fits
+    them worse."""
+    p = synth.spectral_gaussian(300, 16, 2, seed=112)
+    narrow = orc.nrmse_curve(p.X, p.Y, k=4, g=5, r=3, q=21, lo=0.05, hi=0.5, basis="cheb_log")
+    wide = orc.nrmse_curve(p.X, p.Y, k=4, g=3, r=2, q=21, lo=1e-3, hi=1e1, basis="cheb_log")
+    assert narrow.max() < 1e-3
+    assert wide.max() > 10 * narrow.max()

@@ -92,3 +92,24 @@ def test_host_core_samples_run_on_a_small_case():
     for fn in (bench.oracle_exact_sample, bench.lapack_sample):
         out = fn(prob, cfg)
         assert out["value"] > 0 and out["unit"] == "evals/s" and out["cores"] >= 1 and out["sample"]
+
+
+def test_roofline_entry_arithmetic():
+    """achieved = algorithmic work per launch / average launch time, frac =
+    achieved / peak, and the residual's measured traffic is attached to the
+    mixed case only."""
+    from paper_1404_0466_gb300 import synth
+    cfg = dict(synth.MIXED_ECC)
+    work = bench.stage_work(cfg, "mixed", 1)
+    kind, amount, bound = work["resid"]
+    assert kind == "flop" and bound == "alu" and amount > 0
+    info = bench.roofline_of("resid", 9.0, 30, cfg, "mixed", 1, 10, {"hbm_gbs": 6695.0}, work=work)
+    per_launch = amount / 3.0
+    assert abs(info["work_per_launch"] - per_launch) < 1e-6 * per_launch
+    assert abs(info["achieved"] - per_launch / (9.0e-3 / 30) / 1e12) < 1e-9 * info["achieved"]
+    assert abs(info["frac"] - info["achieved"] / info["peak"]) < 1e-12
+    top = bench.roofline({"resid": (9.0, 30), "solve": (5.0, 20)}, cfg, "mixed", 1, 10, {"hbm_gbs": 6695.0},
+                         work=work, workload="mixed_ecc")
+    assert top["kernel_stage"] == "resid" and top["traffic"] == 295.0e6
+    other = bench.roofline({"resid": (9.0, 30)}, cfg, "mixed", 1, 10, {}, work=work, workload="fp64_small")
+    assert other["traffic"] is None

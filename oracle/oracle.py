@@ -32,6 +32,15 @@ arXiv 1404.0466):
 
 Exact cross-validation (``Chol`` of Sec. 6.2) is the same with the exact factor
 at every lambda.
+
+Around the method, each written from the paper's description:
+  * ``holdout_grad``   : the hold-out error's derivative in log(lambda);
+  * ``cv(precond_steps=...)``: refinement against H_f + lambda I (not in the paper);
+  * ``cv(warm=...)``   : the warm start across folds of Sec. 7's future work;
+  * ``holdout_exact_at``, ``mchol_search``, ``mchol``: MChol's range search (Sec. 6.2);
+  * ``pinrmse``        : the supplementary comparator that interpolates the
+    sampled hold-out errors themselves;
+  * ``nrmse_curve``    : the NRMSE of the fit per grid lambda (Sec. 6.6).
 """
 from __future__ import annotations
 

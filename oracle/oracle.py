@@ -17,7 +17,7 @@ arXiv 1404.0466):
    data so one grid is shared by all folds (Sec. 6.3 uses a fixed range; the
    scale makes the range dimensionless).
 4. g sampled lambdas at evenly spaced grid indices including both ends
-   (Sec. 6.3: "sparsely sample 4 lambda values from those 31").
+   (Sec. 6.3 samples 4 of its 31 grid values; their positions are not given).
 5. Exact Cholesky factors at the sampled lambdas (Algorithm 1, step 1).
 6. Target matrix T (g x D) of vectorised lower triangles (Algorithm 1, step 2;
    Sec. 5: any ordering gives the same coefficients entrywise).

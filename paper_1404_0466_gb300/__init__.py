@@ -5,4 +5,4 @@ C ABI, declared in ``include/pichol.h``); ``binding`` marshals arguments to it.
 Importing the package does not load the library; ``binding.lib()`` does, and
 raises if it has not been built.
 """
-__all__ = ["binding", "synth"]
+__all__ = ["autotune", "binding", "synth"]

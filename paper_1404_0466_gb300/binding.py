@@ -325,6 +325,12 @@ class Context:
         t = Tuning(cur["update_strip"], cur["diag_threads"], cur["diag_exclusive"], cur["eval_overlap"])
         _check(lib().pichol_set_tuning(self._h, ctypes.byref(t)), "pichol_set_tuning")
 
+    def autotune(self, X, Y, *, reps=2, stream=None, cache=None, pg=None):
+        """Time the launch-shape candidates on (X, Y), apply the fastest and
+        return an ``autotune.TuneResult``.  No choice changes a result."""
+        from . import autotune
+        return autotune.tune_context(self, X, Y, reps=reps, stream=stream, cache=cache, pg=pg)
+
     def stage_times(self, stream=None):
         """{stage: (total ms, launches)} since the last call; needs set_timing."""
         n = len(STAGES)
@@ -440,6 +446,12 @@ class Batch:
         """Launch shapes and scheduling for every problem (results are bit-identical)."""
         t = Tuning(update_strip, diag_threads, diag_exclusive, eval_overlap)
         _check(lib().pichol_batch_set_tuning(self._h, ctypes.byref(t)), "pichol_batch_set_tuning")
+
+    def autotune(self, Xs, Ys, *, reps=2, stream=None, cache=None, pg=None):
+        """Time concurrent streams x update strip on (Xs, Ys), apply the
+        fastest and return an ``autotune.TuneResult``."""
+        from . import autotune
+        return autotune.tune_batch(self, Xs, Ys, reps=reps, stream=stream, cache=cache, pg=pg)
 
     def run(self, Xs, Ys, stream=None):
         P = ctypes.c_void_p * self.n

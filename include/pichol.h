@@ -93,7 +93,7 @@ typedef struct {
     int32_t r;            /* polynomial degree, 0 .. 5 */
     int32_t q;            /* grid size, 1 .. 4096 */
     double lam_lo;        /* grid: lambda_t = s * lam_lo * (lam_hi/lam_lo)^(t/(q-1)) */
-    double lam_hi;        /*   with s = tr(X^T X)/d if scale_by_trace else 1; 0 < lo <= hi */
+    double lam_hi;        /*   with s = tr(X^T X)/d if scale_by_trace else 1; 0 < lo <= hi, hi finite */
     int32_t scale_by_trace;
     int32_t basis;        /* pichol_basis */
     int32_t mode;         /* pichol_mode */

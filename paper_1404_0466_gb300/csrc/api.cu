@@ -3,6 +3,7 @@
 // stream; see include/pichol.h for the contract of each entry point.
 #include "internal.cuh"
 
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -114,7 +115,7 @@ pichol_status pichol_create(const pichol_config* cfg, pichol_ctx** out)
     if (c.q < 1 || c.q > 4096) return PICHOL_ERR_INVALID_ARG;
     if (c.r < 0 || c.r > 5) return PICHOL_ERR_INVALID_ARG;
     if (c.g <= c.r || c.g > c.q || c.g > MAX_G) return PICHOL_ERR_INVALID_ARG;
-    if (!(c.lam_lo > 0.0) || !(c.lam_hi >= c.lam_lo)) return PICHOL_ERR_INVALID_ARG;
+    if (!(c.lam_lo > 0.0) || !(c.lam_hi >= c.lam_lo) || !std::isfinite(c.lam_hi)) return PICHOL_ERR_INVALID_ARG;
     if (c.scale_by_trace != 0 && c.scale_by_trace != 1) return PICHOL_ERR_INVALID_ARG;
     if (c.basis != PICHOL_BASIS_MONO && c.basis != PICHOL_BASIS_CHEB_LOG) return PICHOL_ERR_INVALID_ARG;
     if (c.mode != PICHOL_MODE_FP64 && c.mode != PICHOL_MODE_MIXED) return PICHOL_ERR_INVALID_ARG;

@@ -113,3 +113,14 @@ def test_roofline_entry_arithmetic():
     assert top["kernel_stage"] == "resid" and top["traffic"] == 295.0e6
     other = bench.roofline({"resid": (9.0, 30)}, cfg, "mixed", 1, 10, {}, work=work, workload="fp64_small")
     assert other["traffic"] is None
+
+
+def test_clock_samples_are_summarised():
+    ok = "0, 2070 MHz, 2070 MHz, 1010.52 W, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active"
+    capped = "0, 1965 MHz, 2070 MHz, 1398.02 W, 0x0000000000000004, Not Active, Not Active, Not Active, Active"
+    hot = "0, 1500 MHz, 2070 MHz, 1200.00 W, 0x0000000000000008, Active, Not Active, Not Active, Not Active"
+    got = bench.summarise_clocks([ok, ok, capped, "", "garbage", "0, [N/A], 2070 MHz, 1 W, 0x0, a, b, c, d"])
+    assert got == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    got = bench.summarise_clocks([ok, hot, capped])
+    assert got["sm_mhz"] == 1965.0 and got["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert bench.summarise_clocks([])["reasons"] == ["no samples"]

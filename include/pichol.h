@@ -280,7 +280,11 @@ PICHOL_API pichol_status pichol_get_lambdas(pichol_ctx* ctx, double* lam_out, vo
  *   factor : L_{f,s} (d x d, upper triangle zero) after pichol_factor_samples; with
  *            warm_samples = g' the folds f > 0 hold s < g' only (the warm-start lambdas)
  *   theta  : Theta_{f,m} for m = 0..r, (r+1) x d x d (upper triangles zero) after pichol_fit
- *   hessian: H_f (d x d, lower triangle mirrored) and B_f (d x c) after pichol_hessian */
+ *   hessian: H_f (d x d, lower triangle mirrored) and B_f (d x c) after pichol_hessian
+ * Outputs are device buffers of doubles.  PICHOL_ERR_INVALID_ARG for a null
+ * pointer or f, s out of range; PICHOL_ERR_STATE before the step that makes
+ * the result (also after a later call that invalidated it, see pichol_mchol
+ * and pichol_eval_holdout_exact). */
 PICHOL_API pichol_status pichol_export_factor(pichol_ctx* ctx, int32_t f, int32_t s, double* L_out, void* stream);
 PICHOL_API pichol_status pichol_export_theta(pichol_ctx* ctx, int32_t f, double* theta_out, void* stream);
 PICHOL_API pichol_status pichol_export_hessian(pichol_ctx* ctx, int32_t f, double* H_out, double* B_out, void* stream);
@@ -416,8 +420,15 @@ PICHOL_API pichol_status pichol_fold_rhs_noalloc(int32_t mode, const void* X, co
  * so everything is ordered after earlier work on `stream` and later work on
  * `stream` waits for it; the whole call can be captured into a CUDA graph
  * (after one uncaptured run, which creates the streams and kernel attributes).
- * Errors of any problem's call are returned; device errors per problem with
- * pichol_batch_get_info.
+ * The first failing call's status is returned: no later problem is enqueued,
+ * and the internal streams are still joined back to `stream`.  Device errors
+ * are reported per problem by pichol_batch_get_info.
+ * Errors: PICHOL_ERR_INVALID_ARG for a null pointer, nprob outside 1..4096,
+ * nstreams outside 1..64, i outside 0..nprob-1, or any config that
+ * pichol_create rejects (batch_create then returns that config's status);
+ * PICHOL_ERR_WORKSPACE from batch_run before batch_set_workspace, and from
+ * batch_set_workspace for a buffer that is too small or not 256-byte aligned.
+ * pichol_batch_destroy frees the host side; the workspace stays the caller's.
  */
 typedef struct pichol_batch pichol_batch;
 PICHOL_API pichol_status pichol_batch_create(const pichol_config* cfgs, int32_t nprob, int32_t nstreams,

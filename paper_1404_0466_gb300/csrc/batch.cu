@@ -155,21 +155,25 @@ pichol_status pichol_batch_run(pichol_batch* b, const void* const* X, const void
     if (cudaEventRecord(b->ev[0], origin) != cudaSuccess) return PICHOL_ERR_CUDA;
     for (int s = 0; s < b->nstreams; ++s)
         if (cudaStreamWaitEvent(b->streams[s], b->ev[0], 0) != cudaSuccess) return PICHOL_ERR_CUDA;
-    for (int r = 0; r < b->nprob; ++r) {
+    // after the first failing call no further problem is enqueued, but the join
+    // below still runs, so the caller's stream stays ordered after what was
+    // enqueued and a capture is never left with unjoined streams
+    for (int r = 0; r < b->nprob && st == PICHOL_OK; ++r) {
         const int i = b->order[r];
         cudaStream_t s = b->streams[r % b->nstreams];
         pichol_ctx* c = b->ctx[i];
-        if ((st = pichol_hessian(c, X[i], Y[i], s)) != PICHOL_OK) return st;
-        if ((st = pichol_factor_samples(c, s)) != PICHOL_OK) return st;
-        if ((st = pichol_fit(c, s)) != PICHOL_OK) return st;
-        if ((st = pichol_eval_holdout(c, E_out[i], t_star + i, nullptr, s)) != PICHOL_OK) return st;
+        if ((st = pichol_hessian(c, X[i], Y[i], s)) != PICHOL_OK) break;
+        if ((st = pichol_factor_samples(c, s)) != PICHOL_OK) break;
+        if ((st = pichol_fit(c, s)) != PICHOL_OK) break;
+        st = pichol_eval_holdout(c, E_out[i], t_star + i, nullptr, s);
     }
     // join: the caller's stream waits for every internal stream
     for (int s = 0; s < b->nstreams; ++s) {
-        if (cudaEventRecord(b->ev[1 + s], b->streams[s]) != cudaSuccess) return PICHOL_ERR_CUDA;
-        if (cudaStreamWaitEvent(origin, b->ev[1 + s], 0) != cudaSuccess) return PICHOL_ERR_CUDA;
+        if (cudaEventRecord(b->ev[1 + s], b->streams[s]) != cudaSuccess ||
+            cudaStreamWaitEvent(origin, b->ev[1 + s], 0) != cudaSuccess)
+            return st != PICHOL_OK ? st : PICHOL_ERR_CUDA;
     }
-    return PICHOL_OK;
+    return st;
 }
 
 pichol_status pichol_batch_get_info(pichol_batch* b, int32_t i, pichol_info* info, void* stream)

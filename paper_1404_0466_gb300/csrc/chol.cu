@@ -389,18 +389,12 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
     // shared memory that no trailing-update CTA can share its SM.
     constexpr int DIAG_RESERVE = 160 * 1024;
     const size_t sm_mm = 3 * sizeof(T) * TB * (TB + Vec16<T>::N);
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_chol_update<T, UNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sm_mm);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_chol_diag<T, 512, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     DIAG_RESERVE);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_chol_diag<T, 256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     DIAG_RESERVE);
+    static std::atomic<unsigned long long> set_upd{0}, set_d512{0}, set_d256{0};
+    {
+        cudaError_t e = smem_limit_once(k_chol_update<T, UNT>, (int)sm_mm, set_upd);
+        if (e == cudaSuccess) e = smem_limit_once(k_chol_diag<T, 512, 2>, DIAG_RESERVE, set_d512);
+        if (e == cudaSuccess) e = smem_limit_once(k_chol_diag<T, 256, 1>, DIAG_RESERVE, set_d256);
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     {
         StageScope sc_(ctx, ST_CHOL_INIT, s);

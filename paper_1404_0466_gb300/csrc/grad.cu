@@ -263,12 +263,9 @@ static cudaError_t launch_tmv(dim3 grid, const T* ML, pichol_ctx* ctx, int nch, 
                               cudaStream_t s)
 {
     const int smem = (int)(sizeof(double) * TB * (CB + 1) + sizeof(T) * TB * (TB + 1) + sizeof(T) * TB * CB);
-    static bool attr_done = false;
-    if (!attr_done) {
-        const cudaError_t e = cudaFuncSetAttribute(k_grad_tmv<T, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr_done = true;
-    }
+    static std::atomic<unsigned long long> set{0};
+    const cudaError_t e = smem_limit_once(k_grad_tmv<T, CB>, smem, set);
+    if (e != cudaSuccess) return e;
     k_grad_tmv<T, CB><<<grid, 256, smem, s>>>(ML, ctx->ntiles, ctx->nt, nch, clen, ctx->dp, ctx->cfg.c, gW, gU,
                                               ctx->gP);
     return cudaGetLastError();

@@ -15,6 +15,7 @@
 //  * Right-hand sides and solutions are [system][dp][c] row-major.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cstddef>
 #include <cuda_runtime.h>
@@ -54,6 +55,23 @@ __host__ __device__ inline void tile_coords(int64_t e, int& I, int& J) {
     while ((int64_t)i * (i + 1) / 2 > e) --i;
     I = i;
     J = (int)(e - (int64_t)i * (i + 1) / 2);
+}
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` on the current
+// device, once per device: the attribute belongs to the device's context, so a
+// process that drives several GPUs needs it on each.  `set` is the caller's
+// mask of devices (ordinal mod 64) done for this kernel.
+template <typename Kernel>
+inline cudaError_t smem_limit_once(Kernel* kernel, int bytes, std::atomic<unsigned long long>& set)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (set.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) set.fetch_or(bit, std::memory_order_release);
+    return e;
 }
 
 #ifdef __CUDACC__

@@ -245,11 +245,10 @@ template <int LG, int CB, int NP, int PASS>
 static cudaError_t run_resid(pichol_ctx* ctx, const ResidArgs& ra, cudaStream_t s)
 {
     const int smem = 2 * NP * (TB / 2) * TB * 4 + 2 * 2 * LG * (TB / 2) * CB * 4 + LG * TB * CB * 8 + 1024;
-    static bool done = false;
-    if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(k_resid<LG, CB, NP, PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    static std::atomic<unsigned long long> set{0};
+    {
+        const cudaError_t e = smem_limit_once(k_resid<LG, CB, NP, PASS>, smem, set);
         if (e != cudaSuccess) return e;
-        done = true;
     }
     CUtensorMap map;
     cudaError_t e = plane_map(&map, ra.theta, (int64_t)ctx->cfg.k * ctx->ntiles * ctx->p);

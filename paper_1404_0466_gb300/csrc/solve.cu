@@ -364,11 +364,10 @@ static cudaError_t run_score(pichol_ctx* ctx, const ScoreArgs& sc, cudaStream_t 
     constexpr int VN = Vec16<T>::N;
     constexpr int CBP = (CB + VN - 1) / VN * VN;
     const int smem = TILE_ELEMS * (int)sizeof(T) + LG * TB * CBP * (int)sizeof(T) + LG * TB * CBP * 8;
-    static bool done = false;
-    if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(k_score<T, LG, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    static std::atomic<unsigned long long> set{0};
+    {
+        const cudaError_t e = smem_limit_once(k_score<T, LG, CB>, smem, set);
         if (e != cudaSuccess) return e;
-        done = true;
     }
     dim3 grid(ctx->nt, (unsigned)((sc.tcount + LG - 1) / LG), ctx->cfg.k);
     {
@@ -408,11 +407,10 @@ static cudaError_t eval_impl(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s
     da.ntiles = ctx->ntiles;
     da.d = cf.d;
     const int dsm = 2 * (int)sizeof(T) * TB * (TB + 1);
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t ea = cudaFuncSetAttribute(k_diag_inv<T, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm);
+    static std::atomic<unsigned long long> set{0};
+    {
+        const cudaError_t ea = smem_limit_once(k_diag_inv<T, EXACT>, dsm, set);
         if (ea != cudaSuccess) return ea;
-        attr_done = true;
     }
     {
         StageScope sc_(ctx, ST_DIAG_INV, s);
@@ -551,7 +549,8 @@ static cudaError_t diag_solve_one_impl(pichol_ctx* ctx, const double* phi_row, c
         da.ntiles = ctx->ntiles;
         da.d = cf.d;
         const int dsm = 2 * (int)sizeof(T) * TB * (TB + 1);
-        cudaError_t ea = cudaFuncSetAttribute(k_diag_inv<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm);
+        static std::atomic<unsigned long long> set{0};
+        const cudaError_t ea = smem_limit_once(k_diag_inv<T, false>, dsm, set);
         if (ea != cudaSuccess) return ea;
         {
             StageScope sc_(ctx, ST_DIAG_INV, s);

@@ -552,12 +552,10 @@ template <typename T, int LG, int CB, int NP, bool EXACT>
 inline cudaError_t run_solve(pichol_ctx* ctx, const SolveArgs& sa, cudaStream_t s)
 {
     using C = SolveCfg<T, LG, CB, NP, EXACT>;
-    static bool done = false;
-    if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(k_solve<T, LG, CB, NP, EXACT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    static std::atomic<unsigned long long> set{0};
+    {
+        const cudaError_t e = smem_limit_once(k_solve<T, LG, CB, NP, EXACT>, C::SMEM, set);
         if (e != cudaSuccess) return e;
-        done = true;
     }
     dim3 grid((unsigned)((sa.tcount + LG - 1) / LG), ctx->cfg.k);
     CUtensorMap map;

@@ -455,11 +455,8 @@ static bool make_map(CUtensorMap* m, const float* base, uint64_t cols, uint64_t 
 
 static cudaError_t gemm_attr()
 {
-    static bool done = false;
-    if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
-    if (e == cudaSuccess) done = true;
-    return e;
+    static std::atomic<unsigned long long> set{0};
+    return smem_limit_once(k_tc_gemm, tc::SMEM_BYTES, set);
 }
 
 int64_t tc_kpad(const pichol_ctx* ctx)

@@ -349,6 +349,13 @@ class Context:
             lib().pichol_destroy(self._h)
             self._h = None
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
     def __del__(self):
         try:
             self.close()
@@ -490,6 +497,13 @@ class Batch:
         if getattr(self, "_h", None):
             lib().pichol_batch_destroy(self._h)
             self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
 
     def __del__(self):
         try:

@@ -194,3 +194,28 @@ def test_new_entry_points_check_arguments_without_a_gpu(L):
     assert L.pichol_check_rsqrt(0, 1, E, None) == 1
     assert L.pichol_check_rsqrt((1 << 32) + 1, 1, E, None) == 1
     assert L.pichol_check_rsqrt(1024, 1, None, None) == 1
+
+
+def test_context_and_batch_close_on_leaving_a_with_block(monkeypatch):
+    """The with-statement frees the C handle once, also when the block raises."""
+    from paper_1404_0466_gb300 import binding
+    freed = []
+
+    class FakeLib:
+        def pichol_destroy(self, h):
+            freed.append(("ctx", h))
+
+        def pichol_batch_destroy(self, h):
+            freed.append(("batch", h))
+
+    monkeypatch.setattr(binding, "lib", lambda: FakeLib())
+    for cls, tag in ((binding.Context, "ctx"), (binding.Batch, "batch")):
+        obj = cls.__new__(cls)
+        obj._h = 17
+        with pytest.raises(KeyError):
+            with obj as o:
+                assert o is obj
+                raise KeyError("inside")
+        assert obj._h is None
+        obj.close()
+        assert freed.count((tag, 17)) == 1

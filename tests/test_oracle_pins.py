@@ -230,6 +230,10 @@ def test_fold_offsets_partition_rows():
         assert o[0] == 0 and o[-1] == n and len(o) == k + 1
         sizes = np.diff(o)
         assert sizes.min() >= n // k and sizes.max() <= n // k + 1
+    # the split's convention (the paper leaves it open): boundaries floor(f n / k),
+    # so the longer folds come last
+    assert orc.fold_offsets(10, 3) == [0, 3, 6, 10]
+    assert orc.fold_offsets(103, 5) == [0, 20, 41, 61, 82, 103]
 
 
 def test_sample_indices_and_grid():
@@ -257,6 +261,10 @@ def test_unusable_diagonal_rule():
     assert orc.diag_unusable(np.array([1.0, -1e-3, 2.0]))
     assert orc.diag_unusable(np.array([1.0, 1e-20, 2.0]))
     assert not orc.diag_unusable(np.array([1.0, 1e-3, 2.0]))
+    # the threshold is 1e3 eps max|diag| = 4.44e-13 here: either side of it
+    assert orc.diag_unusable(np.array([1.0, 1e-14, 2.0]))
+    assert orc.diag_unusable(np.array([1.0, 4.4e-13, 2.0]))
+    assert not orc.diag_unusable(np.array([1.0, 4.5e-13, 2.0]))
 
 
 # --------------------------------------------------------------------------

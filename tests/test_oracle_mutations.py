@@ -72,6 +72,17 @@ def _unusable_eps(orig):
     return diag_unusable
 
 
+class _NumpyWith:
+    """numpy with some functions replaced, for a mistake inside an oracle
+    function that calls numpy directly."""
+
+    def __init__(self, **over):
+        self._over = over
+
+    def __getattr__(self, name):
+        return self._over[name] if name in self._over else getattr(np, name)
+
+
 MUTATIONS = {
     "holdout error drops the last output column": (
         lambda mp: _patch(mp, "holdout_sse",
@@ -130,6 +141,18 @@ MUTATIONS = {
     "fold boundaries rounded up": (
         lambda mp: _patch(mp, "fold_offsets", lambda o: lambda n, k: [-((-f * n) // k) for f in range(k + 1)]),
         [pins.test_fold_offsets_partition_rows]),
+    "MChol centre update in natural log": (
+        lambda mp: mp.setattr(impl, "np", _NumpyWith(log10=np.log)),
+        [pins.test_mchol_search_hand_traced]),
+    "MChol runs one level too many": (
+        lambda mp: _patch(mp, "mchol_levels", lambda o: lambda s, s_min: o(s, s_min) + 1),
+        [pins.test_mchol_level_count, pins.test_mchol_search_hand_traced]),
+    "exact hold-out error at twice the lambda": (
+        lambda mp: _patch(mp, "holdout_exact_at",
+                          lambda o: lambda X, Y, *, k, lams, folds=None: o(X, Y, k=k, lams=2.0 * np.asarray(lams),
+                                                                          folds=folds)),
+        [pins.test_exact_holdout_at_any_lambda_matches_eigen_closed_form,
+         pins.test_pinrmse_matches_a_library_polynomial_fit_of_the_exact_errors]),
     "gradient with the wrong sign": (
         lambda mp: _patch(mp, "_holdout_and_grad",
                           lambda o: lambda *a: (lambda e, de: (e, -de))(*o(*a))),

@@ -179,6 +179,8 @@ def lstsq(V, T) -> np.ndarray:
     D = T.shape[1]
     Theta = np.empty((p, D))
     rc = _get().orc_lstsq_householder(g, p, _p(V), D, _p(T), _p(Theta))
+    if rc == 2:
+        raise MemoryError("no memory for the least-squares scratch matrices")
     if rc:
         raise np.linalg.LinAlgError("observation matrix V is rank deficient")
     return Theta
@@ -320,6 +322,24 @@ def argmin_first(values: np.ndarray) -> int:
     return best_t
 
 
+def warm_fit(theta0, Vw, Tw, pw: int) -> np.ndarray:
+    """Coefficients of a warm-started fold (the future work of Sec. 7, as read
+    here): fold 0's coefficients plus the least-squares correction fitted to
+    the residual of the warm fold's exact factors,
+    Theta_f = Theta_0 + V'^+ (T'_f - V' Theta_0) on the first pw rows."""
+    Theta = theta0.copy()
+    Theta[:pw] += lstsq(Vw[:, :pw], Tw - Vw @ theta0)
+    return Theta
+
+
+def refine_exact_step(Hf, lam: float, Lt, Bf, W) -> np.ndarray:
+    """One step of iterative refinement against the exact system, with the
+    interpolated factor as the preconditioner (not in the paper):
+    R = B_f - (H_f + lambda I) W, then W + (L~ L~^T)^{-1} R."""
+    R = Bf - (Hf @ W + lam * W)
+    return W + solve_factored(Lt, R)
+
+
 # ----------------------------------------------------------------------------
 # the full cross-validation
 # ----------------------------------------------------------------------------
@@ -433,8 +453,7 @@ def cv(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e
                 Tw[s] = vec_lower(L)
                 if keep:
                     res.factors[(f, s)] = L
-            Theta = theta0.copy()
-            Theta[:pw] += lstsq(Vw[:, :pw], Tw - Vw @ theta0)
+            Theta = warm_fit(theta0, Vw, Tw, pw)
         else:
             # Algorithm 1, steps 1-2: exact factors at the samples, stacked as rows of T
             T = np.empty((g, d * (d + 1) // 2))
@@ -462,8 +481,7 @@ def cv(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e
                 continue
             W = solve_factored(Lt, Bf)
             for _ in range(precond_steps):
-                R = Bf - (Hf @ W + lam[t] * W)
-                W = W + solve_factored(Lt, R)
+                W = refine_exact_step(Hf, lam[t], Lt, Bf, W)
             E[f, t] = holdout_sse(Xv, Yv, W) / (nv * c)
             if keep:
                 res.W[(f, t)] = W

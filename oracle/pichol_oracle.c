@@ -13,7 +13,8 @@
  * states.  The one restructuring is a loop interchange in the Gram routine,
  * which keeps the order of every sum.  OpenMP is used only to run independent
  * units (groups of Gram rows, the entries of one Cholesky column, independent
- * right-hand sides) side by side; it never changes the order of a sum.
+ * right-hand sides, the rows of a hold-out error) side by side; it never
+ * changes the order of a sum, so every result is the same from run to run.
  *
  * Matrices are row-major: element (i, j) of an r x s matrix M is M[i*s + j].
  */
@@ -135,8 +136,11 @@ void orc_backward(int64_t d, int64_t c, const double* L, const double* Z, double
 double orc_holdout_sse(int64_t nv, int64_t d, int64_t c,
                        const double* Xv, const double* Yv, const double* W)
 {
-    double total = 0.0;
-    #pragma omp parallel for reduction(+:total) schedule(static)
+    /* the rows' sums are independent units; their total is then taken in row
+     * order r = 0, 1, ..., n_v - 1 (NaN if the scratch row cannot be had) */
+    double* rows = (double*)malloc(sizeof(double) * (size_t)(nv > 0 ? nv : 1));
+    if (!rows) return NAN;
+    #pragma omp parallel for schedule(static)
     for (int64_t r = 0; r < nv; ++r) {
         double row = 0.0;
         for (int64_t o = 0; o < c; ++o) {
@@ -146,8 +150,11 @@ double orc_holdout_sse(int64_t nv, int64_t d, int64_t c,
             double e = Yv[r * c + o] - pred;
             row += e * e;
         }
-        total += row;
+        rows[r] = row;
     }
+    double total = 0.0;
+    for (int64_t r = 0; r < nv; ++r) total += rows[r];
+    free(rows);
     return total;
 }
 
@@ -160,7 +167,8 @@ double orc_holdout_sse(int64_t nv, int64_t d, int64_t c,
  * (V^T V)^{-1} V^T T.  The same minimiser is computed here by Householder QR
  * of V, which does not square the condition number of V:
  *   V = Q R,  Theta = R^{-1} (Q^T T)[0:p].
- * Returns 0, or 1 if R has a zero diagonal (V rank deficient).
+ * Returns 0, 1 if R has a zero diagonal (V rank deficient), or 2 if the
+ * scratch matrices cannot be had.
  */
 int orc_lstsq_householder(int64_t g, int64_t p, const double* V,
                           int64_t D, const double* T, double* Theta)
@@ -168,6 +176,7 @@ int orc_lstsq_householder(int64_t g, int64_t p, const double* V,
     double* R = (double*)malloc((size_t)(g * p) * sizeof(double));
     double* QT = (double*)malloc((size_t)(g * D) * sizeof(double));
     double* v = (double*)malloc((size_t)g * sizeof(double));
+    if (!R || !QT || !v) { free(R); free(QT); free(v); return 2; }
     memcpy(R, V, (size_t)(g * p) * sizeof(double));
     memcpy(QT, T, (size_t)(g * D) * sizeof(double));
     int rc = 0;

@@ -731,3 +731,13 @@ def test_nrmse_is_small_inside_a_well_sampled_range():
     wide = orc.nrmse_curve(p.X, p.Y, k=4, g=3, r=2, q=21, lo=1e-3, hi=1e1, basis="cheb_log")
     assert narrow.max() < 1e-3
     assert wide.max() > 10 * narrow.max()
+
+
+def test_oracle_is_the_same_from_run_to_run():
+    """OpenMP in the oracle only runs independent units side by side, so two
+    runs give identical bits (the hold-out error's row sums included)."""
+    p = synth.spectral_gaussian(300, 20, 2, seed=71)
+    for kw in (dict(), dict(warm=3), dict(precond_steps=2), dict(exact=True)):
+        a = orc.cv(p.X, p.Y, k=3, g=5, r=3, q=15, basis="cheb_log", **kw)
+        b = orc.cv(p.X, p.Y, k=3, g=5, r=3, q=15, basis="cheb_log", **kw)
+        assert np.array_equal(a.E, b.E), kw

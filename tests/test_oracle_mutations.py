@@ -153,6 +153,16 @@ MUTATIONS = {
                                                                           folds=folds)),
         [pins.test_exact_holdout_at_any_lambda_matches_eigen_closed_form,
          pins.test_pinrmse_matches_a_library_polynomial_fit_of_the_exact_errors]),
+    "warm start without subtracting fold 0's fit at the warm samples": (
+        lambda mp: _patch(mp, "warm_fit",
+                          lambda o: lambda theta0, Vw, Tw, pw: o(theta0, Vw, Tw + Vw @ theta0, pw)),
+        [lambda: pins.test_warm_start_with_every_sample_is_the_plain_fit("cheb_log"),
+         pins.test_warm_start_interpolates_the_exact_factors_at_its_nodes]),
+    "exact-system refinement with the wrong sign of lambda": (
+        lambda mp: _patch(mp, "refine_exact_step",
+                          lambda o: lambda Hf, lam, Lt, Bf, W: o(Hf, -lam, Lt, Bf, W)),
+        [pins.test_exact_system_refinement_step_is_the_preconditioned_iteration,
+         pins.test_exact_system_refinement_converges_to_exact_cv]),
     "gradient with the wrong sign": (
         lambda mp: _patch(mp, "_holdout_and_grad",
                           lambda o: lambda *a: (lambda e, de: (e, -de))(*o(*a))),

@@ -144,6 +144,23 @@ def _check(code: int, where: str):
         raise PicholError(code, where)
 
 
+def _require(t, name: str, shape, dtype):
+    """Raise unless ``t`` is a contiguous CUDA tensor of ``dtype`` and
+    ``shape``: the kernels read and write exactly that many elements.  Only
+    tensor metadata is read, so this is safe during CUDA-graph capture."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor, got {type(t).__name__}")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be on a CUDA device")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
 def _stream_ptr(stream=None) -> int:
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -189,9 +206,8 @@ class Context:
 
     # -- steps -------------------------------------------------------------
     def hessian(self, X, Y, stream=None):
-        assert X.is_cuda and Y.is_cuda and X.dtype == self.dtype and Y.dtype == self.dtype
-        assert X.is_contiguous() and Y.is_contiguous()
-        assert tuple(X.shape) == (self.cfg.n, self.cfg.d) and tuple(Y.shape) == (self.cfg.n, self.cfg.c)
+        _require(X, "X", (self.cfg.n, self.cfg.d), self.dtype)
+        _require(Y, "Y", (self.cfg.n, self.cfg.c), self.dtype)
         self._X, self._Y = X, Y   # keep alive while kernels may read them
         _check(lib().pichol_hessian(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
                                     ctypes.c_void_p(_stream_ptr(stream))), "pichol_hessian")
@@ -210,15 +226,28 @@ class Context:
         W = torch.empty((cfg.k, cfg.q, cfg.d, cfg.c), dtype=self.dtype, device="cuda") if want_w else None
         return E, t, W
 
+    def _given_outputs(self, out, want_w):
+        """A caller's (E, t_star, W) buffers, checked; new ones if ``out`` is None."""
+        if out is None:
+            return self._outputs(want_w)
+        import torch
+        E, t, W = out
+        cfg = self.cfg
+        _require(E, "E", (cfg.k, cfg.q), torch.float64)
+        _require(t, "t_star", (1,), torch.int32)
+        if W is not None:
+            _require(W, "W", (cfg.k, cfg.q, cfg.d, cfg.c), self.dtype)
+        return E, t, W
+
     def eval_holdout(self, want_w=False, out=None, stream=None) -> CVOutput:
-        E, t, W = out if out is not None else self._outputs(want_w)
+        E, t, W = self._given_outputs(out, want_w)
         _check(lib().pichol_eval_holdout(self._h, ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(t.data_ptr()),
                                          ctypes.c_void_p(W.data_ptr() if W is not None else 0),
                                          ctypes.c_void_p(_stream_ptr(stream))), "pichol_eval_holdout")
         return CVOutput(E, t, W)
 
     def eval_holdout_exact(self, want_w=False, out=None, stream=None) -> CVOutput:
-        E, t, W = out if out is not None else self._outputs(want_w)
+        E, t, W = self._given_outputs(out, want_w)
         _check(lib().pichol_eval_holdout_exact(self._h, ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(t.data_ptr()),
                                                ctypes.c_void_p(W.data_ptr() if W is not None else 0),
                                                ctypes.c_void_p(_stream_ptr(stream))), "pichol_eval_holdout_exact")
@@ -245,7 +274,7 @@ class Context:
     def eval_pinrmse(self, out=None, stream=None) -> CVOutput:
         """PINRMSE after ``factor_samples``: the exact hold-out errors at the g
         sampled lambdas interpolated over the grid (pichol_eval_pinrmse)."""
-        E, t, _ = out if out is not None else self._outputs(False)
+        E, t, _ = self._given_outputs(out, False)
         _check(lib().pichol_eval_pinrmse(self._h, ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(t.data_ptr()),
                                          ctypes.c_void_p(_stream_ptr(stream))), "pichol_eval_pinrmse")
         return CVOutput(E, t, None)
@@ -461,6 +490,13 @@ class Batch:
         return autotune.tune_batch(self, Xs, Ys, reps=reps, stream=stream, cache=cache, pg=pg)
 
     def run(self, Xs, Ys, stream=None):
+        if len(Xs) != self.n or len(Ys) != self.n:
+            raise ValueError(f"expected {self.n} X and Y tensors, got {len(Xs)} and {len(Ys)}")
+        import torch
+        for i, (x, y, c) in enumerate(zip(Xs, Ys, self.cfgs)):
+            dt = torch.float64 if c.mode == PICHOL_MODE_FP64 else torch.float32
+            _require(x, f"X[{i}]", (c.n, c.d), dt)
+            _require(y, f"Y[{i}]", (c.n, c.c), dt)
         P = ctypes.c_void_p * self.n
         self._keep = (Xs, Ys)
         xp = P(*[x.data_ptr() for x in Xs])

@@ -219,3 +219,57 @@ def test_context_and_batch_close_on_leaving_a_with_block(monkeypatch):
         assert obj._h is None
         obj.close()
         assert freed.count((tag, 17)) == 1
+
+
+def test_tensor_arguments_are_checked_before_any_call(monkeypatch):
+    """Wrong device, dtype, shape or layout raise before the C library is
+    reached (the kernels would read or write out of bounds); without assert,
+    so the checks hold under python -O.  CPU tensors stand in for the CUDA
+    ones: the device is the first thing checked."""
+    import torch
+    from types import SimpleNamespace
+    from paper_1404_0466_gb300 import binding as B
+
+    def no_lib():
+        raise AssertionError("the C library must not be reached")
+
+    monkeypatch.setattr(B, "lib", no_lib)
+    ctx = B.Context.__new__(B.Context)
+    ctx._h = None
+    ctx.cfg = SimpleNamespace(n=8, d=3, c=2, k=2, q=5)
+    ctx.dtype = torch.float64
+    X, Y = torch.zeros(8, 3, dtype=torch.float64), torch.zeros(8, 2, dtype=torch.float64)
+    with pytest.raises(ValueError, match="CUDA"):
+        ctx.hessian(X, Y)
+    with pytest.raises(TypeError):
+        ctx.hessian(X.numpy(), Y)
+    # the remaining checks, each with the device check passed
+    monkeypatch.setattr(torch.Tensor, "is_cuda", property(lambda self: True))
+    with pytest.raises(ValueError, match="float64"):
+        ctx.hessian(X.float(), Y)
+    with pytest.raises(ValueError, match=r"shape \(8, 3\)"):
+        ctx.hessian(X[:7], Y)
+    with pytest.raises(ValueError, match="contiguous"):
+        ctx.hessian(torch.zeros(3, 8, dtype=torch.float64).t(), Y)
+    E, t = torch.zeros(2, 5, dtype=torch.float64), torch.zeros(1, dtype=torch.int32)
+    with pytest.raises(ValueError, match="E must have shape"):
+        ctx._given_outputs((torch.zeros(2, 4, dtype=torch.float64), t, None), False)
+    with pytest.raises(ValueError, match="t_star"):
+        ctx._given_outputs((E, torch.zeros(1, dtype=torch.int64), None), False)
+    with pytest.raises(ValueError, match="W must have shape"):
+        ctx._given_outputs((E, t, torch.zeros(2, 5, 3, 1, dtype=torch.float64)), True)
+    assert ctx._given_outputs((E, t, None), False)[0] is E
+    # a batch checks every problem against its own configuration and mode
+    b = B.Batch.__new__(B.Batch)
+    b._h = None
+    b.n = 2
+    b.cfgs = [SimpleNamespace(n=8, d=3, c=2, mode=B.PICHOL_MODE_FP64),
+              SimpleNamespace(n=6, d=4, c=1, mode=B.PICHOL_MODE_MIXED)]
+    good_x = [X, torch.zeros(6, 4)]
+    good_y = [Y, torch.zeros(6, 1)]
+    with pytest.raises(ValueError, match="expected 2"):
+        b.run(good_x[:1], good_y[:1])
+    with pytest.raises(ValueError, match=r"X\[1\] must be torch.float32"):
+        b.run([X, torch.zeros(6, 4, dtype=torch.float64)], good_y)
+    with pytest.raises(ValueError, match=r"Y\[0\] must have shape"):
+        b.run(good_x, [torch.zeros(8, 1, dtype=torch.float64), good_y[1]])

@@ -19,6 +19,14 @@ LIB_PATH = _PKG / "libpichol.so"
 PICHOL_MODE_FP64, PICHOL_MODE_MIXED = 0, 1
 PICHOL_BASIS_MONO, PICHOL_BASIS_CHEB_LOG = 0, 1
 REFINE_TARGETS = {"interpolated": 0, "exact": 1}
+BASES = {"mono": PICHOL_BASIS_MONO, "cheb_log": PICHOL_BASIS_CHEB_LOG}
+MODES = {"fp64": PICHOL_MODE_FP64, "mixed": PICHOL_MODE_MIXED}
+
+
+def _choice(what: str, value, table: dict) -> int:
+    if value not in table:
+        raise ValueError(f"{what} must be one of {sorted(table)}, got {value!r}")
+    return table[value]
 STATUS = {0: "PICHOL_OK", 1: "PICHOL_ERR_INVALID_ARG", 2: "PICHOL_ERR_NOT_SPD", 3: "PICHOL_ERR_CUDA",
           4: "PICHOL_ERR_WORKSPACE", 5: "PICHOL_ERR_TIMEOUT", 6: "PICHOL_ERR_UNSUPPORTED", 7: "PICHOL_ERR_STATE"}
 
@@ -187,10 +195,10 @@ class Context:
         cfg.n, cfg.d, cfg.c, cfg.k, cfg.g, cfg.r, cfg.q = n, d, c, k, g, r, q
         cfg.lam_lo, cfg.lam_hi = lam_lo, lam_hi
         cfg.scale_by_trace = 1 if scale_by_trace else 0
-        cfg.basis = {"mono": PICHOL_BASIS_MONO, "cheb_log": PICHOL_BASIS_CHEB_LOG}[basis]
-        cfg.mode = {"fp64": PICHOL_MODE_FP64, "mixed": PICHOL_MODE_MIXED}[mode]
+        cfg.basis = _choice("basis", basis, BASES)
+        cfg.mode = _choice("mode", mode, MODES)
         cfg.refine_steps, cfg.gram_passes, cfg.exact_batch = refine_steps, gram_passes, exact_batch
-        cfg.refine_target = REFINE_TARGETS[refine_target]
+        cfg.refine_target = _choice("refine_target", refine_target, REFINE_TARGETS)
         cfg.warm_samples = warm_samples
         self.cfg = cfg
         self.dtype = torch.float64 if mode == "fp64" else torch.float32
@@ -453,10 +461,10 @@ class Batch:
             cfg = cfgs[i]
             cfg.n, cfg.d, cfg.c, cfg.k, cfg.g, cfg.r, cfg.q = (pr[x] for x in ("n", "d", "c", "k", "g", "r", "q"))
             cfg.lam_lo, cfg.lam_hi = pr.get("lam_lo", 1e-3), pr.get("lam_hi", 1e1)
-            cfg.basis = {"mono": PICHOL_BASIS_MONO, "cheb_log": PICHOL_BASIS_CHEB_LOG}[pr.get("basis", "mono")]
-            cfg.mode = {"fp64": PICHOL_MODE_FP64, "mixed": PICHOL_MODE_MIXED}[pr.get("mode", "fp64")]
+            cfg.basis = _choice("basis", pr.get("basis", "mono"), BASES)
+            cfg.mode = _choice("mode", pr.get("mode", "fp64"), MODES)
             cfg.refine_steps = pr.get("refine_steps", 0)
-            cfg.refine_target = REFINE_TARGETS[pr.get("refine_target", "interpolated")]
+            cfg.refine_target = _choice("refine_target", pr.get("refine_target", "interpolated"), REFINE_TARGETS)
             cfg.exact_batch = pr.get("exact_batch", cfg.g)
             cfg.warm_samples = pr.get("warm_samples", 0)
         self.cfgs = cfgs

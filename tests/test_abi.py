@@ -273,3 +273,12 @@ def test_tensor_arguments_are_checked_before_any_call(monkeypatch):
         b.run([X, torch.zeros(6, 4, dtype=torch.float64)], good_y)
     with pytest.raises(ValueError, match=r"Y\[0\] must have shape"):
         b.run(good_x, [torch.zeros(8, 1, dtype=torch.float64), good_y[1]])
+
+
+def test_unknown_names_are_value_errors():
+    from paper_1404_0466_gb300 import binding as B
+    assert B._choice("mode", "mixed", B.MODES) == B.PICHOL_MODE_MIXED
+    with pytest.raises(ValueError, match="basis must be one of"):
+        B._choice("basis", "legendre", B.BASES)
+    with pytest.raises(ValueError, match="refine_target"):
+        B._choice("refine_target", "both", B.REFINE_TARGETS)

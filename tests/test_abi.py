@@ -282,3 +282,44 @@ def test_unknown_names_are_value_errors():
         B._choice("basis", "legendre", B.BASES)
     with pytest.raises(ValueError, match="refine_target"):
         B._choice("refine_target", "both", B.REFINE_TARGETS)
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include <string.h>
+#include "pichol.h"
+
+int main(void)
+{
+    pichol_config cfg;
+    pichol_ctx* ctx = NULL;
+    int32_t levels = 0;
+    pichol_config_default(&cfg);
+    cfg.n = 1000; cfg.d = 100; cfg.c = 3; cfg.k = 5; cfg.g = 4; cfg.r = 2; cfg.q = 31;
+    cfg.lam_lo = 2.0; cfg.lam_hi = 1.0;                      /* lo > hi: refused */
+    printf("%d ", (int)pichol_create(&cfg, &ctx));
+    printf("%d ", ctx == NULL);
+    printf("%d ", (int)pichol_mchol_levels(1.5, 0.0025, &levels));
+    printf("%d ", (int)levels);
+    printf("%s\n", pichol_status_string(PICHOL_ERR_NOT_SPD));
+    return 0;
+}
+"""
+
+
+def test_plain_c_client_compiles_links_and_runs(L, tmp_path):
+    """The header is C (pedantic C99, no C++), and a C program links against
+    libpichol.so and calls its host-only entry points without a GPU."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(str(binding.LIB_PATH))
+    subprocess.check_call(["gcc", "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror",
+                           "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                           "-L", libdir, "-lpichol", "-Wl,-rpath," + libdir])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    assert out.strip() == "1 1 0 10 matrix not positive definite"

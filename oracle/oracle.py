@@ -40,7 +40,7 @@ Around the method, each written from the paper's description:
   * ``holdout_exact_at``, ``mchol_search``, ``mchol``: MChol's range search (Sec. 6.2);
   * ``pinrmse``        : the supplementary comparator that interpolates the
     sampled hold-out errors themselves;
-  * ``nrmse_curve``    : the NRMSE of the fit per grid lambda (Sec. 6.6).
+  * ``nrmse_curve``, ``nrmse``: the NRMSE of the fit per grid lambda (Sec. 6.6).
 """
 from __future__ import annotations
 
@@ -715,5 +715,12 @@ def nrmse_curve(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: f
     for t in range(q):
         target = vec_lower(cholesky(Hf + res.lam[t] * np.eye(d)))
         pred = eval_poly(Phi[t], res.theta[fold])
-        out[t] = np.sqrt(np.mean((pred - target) ** 2)) / np.sqrt(np.mean((target - target.mean()) ** 2))
+        out[t] = nrmse(pred, target)
     return out
+
+
+def nrmse(pred, target) -> float:
+    """Root mean squared error of ``pred`` over the root mean squared deviation
+    of ``target`` from its mean (Sec. 6.6's normalisation: the mean scores 1)."""
+    pred, target = _f64(pred), _f64(target)
+    return float(np.sqrt(np.mean((pred - target) ** 2)) / np.sqrt(np.mean((target - target.mean()) ** 2)))

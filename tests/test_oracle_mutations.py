@@ -163,6 +163,9 @@ MUTATIONS = {
                           lambda o: lambda Hf, lam, Lt, Bf, W: o(Hf, -lam, Lt, Bf, W)),
         [pins.test_exact_system_refinement_step_is_the_preconditioned_iteration,
          pins.test_exact_system_refinement_converges_to_exact_cv]),
+    "NRMSE without its square roots": (
+        lambda mp: _patch(mp, "nrmse", lambda o: lambda pred, target: o(pred, target) ** 2),
+        [pins.test_nrmse_worked_by_hand, pins.test_nrmse_is_small_inside_a_well_sampled_range]),
     "gradient with the wrong sign": (
         lambda mp: _patch(mp, "_holdout_and_grad",
                           lambda o: lambda *a: (lambda e, de: (e, -de))(*o(*a))),

@@ -741,3 +741,13 @@ def test_oracle_is_the_same_from_run_to_run():
         a = orc.cv(p.X, p.Y, k=3, g=5, r=3, q=15, basis="cheb_log", **kw)
         b = orc.cv(p.X, p.Y, k=3, g=5, r=3, q=15, basis="cheb_log", **kw)
         assert np.array_equal(a.E, b.E), kw
+
+
+def test_nrmse_worked_by_hand():
+    """pred = (1, 2, 3) for target = (1, 2, 4): the RMSE is sqrt(1/3); the
+    target's mean is 7/3, so its RMS deviation is sqrt(14/9) = sqrt(14)/3,
+    and the ratio is sqrt(3/14)."""
+    assert abs(orc.nrmse([1.0, 2.0, 3.0], [1.0, 2.0, 4.0]) - math.sqrt(3.0 / 14.0)) <= 1e-15
+    t = np.array([0.5, -1.0, 2.0, 3.5])
+    assert orc.nrmse(t, t) == 0.0
+    assert abs(orc.nrmse(np.full(4, t.mean()), t) - 1.0) <= 1e-15

@@ -186,6 +186,7 @@ pichol_status pichol_set_workspace(pichol_ctx* ctx, void* workspace, size_t byte
 
 pichol_status pichol_hessian(pichol_ctx* ctx, const void* X, const void* Y, void* stream)
 {
+    CallRange range_(__func__);
     if (!ctx || !X || !Y) return PICHOL_ERR_INVALID_ARG;
     if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
@@ -198,6 +199,7 @@ pichol_status pichol_hessian(pichol_ctx* ctx, const void* X, const void* Y, void
 
 pichol_status pichol_factor_samples(pichol_ctx* ctx, void* stream)
 {
+    CallRange range_(__func__);
     if (!ctx) return PICHOL_ERR_INVALID_ARG;
     if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
     if (!ctx->have_hessian) return PICHOL_ERR_STATE;
@@ -209,6 +211,7 @@ pichol_status pichol_factor_samples(pichol_ctx* ctx, void* stream)
 
 pichol_status pichol_fit(pichol_ctx* ctx, void* stream)
 {
+    CallRange range_(__func__);
     if (!ctx) return PICHOL_ERR_INVALID_ARG;
     if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
     if (!ctx->have_factors) return PICHOL_ERR_STATE;
@@ -219,6 +222,7 @@ pichol_status pichol_fit(pichol_ctx* ctx, void* stream)
 
 pichol_status pichol_eval_holdout(pichol_ctx* ctx, double* E_out, int32_t* t_star, void* W_out, void* stream)
 {
+    CallRange range_(__func__);
     if (!ctx || !E_out || !t_star) return PICHOL_ERR_INVALID_ARG;
     if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
     if (!ctx->have_fit) return PICHOL_ERR_STATE;
@@ -232,6 +236,7 @@ pichol_status pichol_eval_holdout(pichol_ctx* ctx, double* E_out, int32_t* t_sta
 pichol_status pichol_eval_holdout_exact(pichol_ctx* ctx, double* E_out, int32_t* t_star, void* W_out,
                                         void* stream)
 {
+    CallRange range_(__func__);
     if (!ctx || !E_out || !t_star) return PICHOL_ERR_INVALID_ARG;
     if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
     if (!ctx->have_hessian) return PICHOL_ERR_STATE;
@@ -251,6 +256,7 @@ pichol_status pichol_eval_holdout_exact(pichol_ctx* ctx, double* E_out, int32_t*
 
 pichol_status pichol_eval_pinrmse(pichol_ctx* ctx, double* E_out, int32_t* t_star, void* stream)
 {
+    CallRange range_(__func__);
     if (!ctx || !E_out || !t_star) return PICHOL_ERR_INVALID_ARG;
     if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
     if (ctx->cfg.warm_samples) return PICHOL_ERR_UNSUPPORTED;
@@ -269,6 +275,7 @@ pichol_status pichol_mchol_levels(double s, double s_min, int32_t* levels)
 
 pichol_status pichol_mchol(pichol_ctx* ctx, double c, double s, double s_min, double* trace_out, void* stream)
 {
+    CallRange range_(__func__);
     int32_t levels = 0;
     if (!ctx || !(c >= -300.0 && c <= 300.0)) return PICHOL_ERR_INVALID_ARG;
     pichol_status st = pichol_mchol_levels(s, s_min, &levels);
@@ -283,6 +290,7 @@ pichol_status pichol_mchol(pichol_ctx* ctx, double c, double s, double s_min, do
 
 pichol_status pichol_holdout_grad(pichol_ctx* ctx, double log_lam, double* E_out, double* dE_out, void* stream)
 {
+    CallRange range_(__func__);
     if (!ctx || !E_out || !dE_out || !(log_lam == log_lam) || log_lam > 700.0 || log_lam < -700.0)
         return PICHOL_ERR_INVALID_ARG;
     if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;

@@ -144,6 +144,7 @@ pichol_status pichol_batch_set_tuning(pichol_batch* b, const pichol_tuning* t)
 pichol_status pichol_batch_run(pichol_batch* b, const void* const* X, const void* const* Y, double* const* E_out,
                                int32_t* t_star, void* stream)
 {
+    pichol::CallRange range_(__func__);
     if (!b || !X || !Y || !E_out || !t_star) return PICHOL_ERR_INVALID_ARG;
     if (!b->ws) return PICHOL_ERR_WORKSPACE;
     for (int i = 0; i < b->nprob; ++i)

@@ -19,6 +19,7 @@
 #include <cstdint>
 #include <cstddef>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <type_traits>
 
 #include "../../include/pichol.h"
@@ -56,6 +57,15 @@ __host__ __device__ inline void tile_coords(int64_t e, int& I, int& J) {
     I = i;
     J = (int)(e - (int64_t)i * (i + 1) / 2);
 }
+
+// A named NVTX range around one call of the C ABI, for timelines in a profiler
+// (header-only NVTX; without a profiler attached the calls do nothing).
+struct CallRange {
+    explicit CallRange(const char* name) { nvtxRangePushA(name); }
+    ~CallRange() { nvtxRangePop(); }
+    CallRange(const CallRange&) = delete;
+    CallRange& operator=(const CallRange&) = delete;
+};
 
 // Raises a kernel's dynamic shared-memory limit to `bytes` on the current
 // device, once per device: the attribute belongs to the device's context, so a

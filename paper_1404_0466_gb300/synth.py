@@ -52,13 +52,18 @@ def spectral_gaussian(n: int, d: int, c: int, *, seed: int, decay: float = 1.0,
 
 
 def ecc_codebook(rng: np.random.Generator, classes: int, bits: int) -> np.ndarray:
-    """Random +-1 code words (classes x bits) with no two rows equal."""
+    """Random +-1 code words (classes x bits) with no two rows equal: whole
+    codebooks are drawn until one has distinct rows, and after 1000 draws (a
+    codebook that nearly fills the 2^bits words) distinct words are drawn
+    without replacement instead."""
     if classes > 2 ** bits:
         raise ValueError("not enough bits for distinct code words")
-    while True:
+    for _ in range(1000):
         C = rng.choice(np.array([-1.0, 1.0]), size=(classes, bits))
         if len({tuple(row) for row in C}) == classes:
             return C
+    words = rng.choice(2 ** bits, size=classes, replace=False)
+    return np.where((words[:, None] >> np.arange(bits)) & 1, 1.0, -1.0)
 
 
 def mixture_ecc(n: int, d: int, c: int = 10, *, seed: int, clusters: int = 10,

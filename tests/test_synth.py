@@ -41,6 +41,8 @@ def test_ecc_codebook():
     assert len({tuple(r) for r in C}) == 4
     with pytest.raises(ValueError):
         synth.ecc_codebook(np.random.default_rng(3), 5, 2)
+    C = synth.ecc_codebook(np.random.default_rng(4), 16, 4)    # all 16 words: drawn without replacement
+    assert len({tuple(r) for r in C}) == 16 and set(np.unique(C)) == {-1.0, 1.0}
 
 
 def test_mixture_ecc_targets_and_clusters():

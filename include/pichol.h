@@ -371,6 +371,29 @@ typedef struct {
 PICHOL_API pichol_status pichol_get_tuning(const pichol_ctx* ctx, pichol_tuning* t);
 PICHOL_API pichol_status pichol_set_tuning(pichol_ctx* ctx, const pichol_tuning* t);
 
+/*
+ * Checkpoint and resume.  Every result of the path (normal-equation blocks,
+ * grid, sampled factors, coefficients, status word) lives in the caller's
+ * workspace, and nothing in it points into device memory, so a checkpoint is
+ * the workspace's bytes plus which results they hold.
+ *   pichol_get_state : *state = the results the workspace holds, as bits
+ *                      PICHOL_STATE_HESSIAN (pichol_hessian),
+ *                      PICHOL_STATE_FACTORS (pichol_factor_samples),
+ *                      PICHOL_STATE_FIT (pichol_fit).  Host only.
+ *   pichol_resume    : declares that the attached workspace now holds those
+ *                      results, its pichol_workspace_size bytes having been
+ *                      copied from a context of an identical configuration;
+ *                      later calls continue from there (e.g. pichol_eval_holdout
+ *                      after PICHOL_STATE_FIT).  Host only; the library cannot
+ *                      check the bytes.
+ * PICHOL_ERR_INVALID_ARG for a null pointer, unknown bits, or factors or fit
+ * without the Hessian; PICHOL_ERR_WORKSPACE from pichol_resume without a
+ * workspace.
+ */
+enum { PICHOL_STATE_HESSIAN = 1, PICHOL_STATE_FACTORS = 2, PICHOL_STATE_FIT = 4 };
+PICHOL_API pichol_status pichol_get_state(const pichol_ctx* ctx, int32_t* state);
+PICHOL_API pichol_status pichol_resume(pichol_ctx* ctx, int32_t state);
+
 /* Frees the host-side context (and its timing events).  The workspace stays
  * the caller's. */
 PICHOL_API void pichol_destroy(pichol_ctx* ctx);

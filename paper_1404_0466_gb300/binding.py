@@ -17,6 +17,7 @@ _PKG = pathlib.Path(__file__).resolve().parent
 LIB_PATH = _PKG / "libpichol.so"
 
 PICHOL_MODE_FP64, PICHOL_MODE_MIXED = 0, 1
+PICHOL_STATE_HESSIAN, PICHOL_STATE_FACTORS, PICHOL_STATE_FIT = 1, 2, 4
 PICHOL_BASIS_MONO, PICHOL_BASIS_CHEB_LOG = 0, 1
 REFINE_TARGETS = {"interpolated": 0, "exact": 1}
 BASES = {"mono": PICHOL_BASIS_MONO, "cheb_log": PICHOL_BASIS_CHEB_LOG}
@@ -43,6 +44,7 @@ EXPORTS = [
     "pichol_batch_set_timing", "pichol_batch_stage_times",
     "pichol_get_tuning", "pichol_set_tuning", "pichol_batch_set_tuning", "pichol_check_timeout",
     "pichol_mchol", "pichol_mchol_levels", "pichol_check_rsqrt", "pichol_eval_pinrmse", "pichol_probe_fma",
+    "pichol_get_state", "pichol_resume",
 ]
 STAGES = ["gram", "xty", "setup", "chol_init", "chol_diag", "chol_panel", "chol_update", "fit",
           "diag_inv", "solve", "resid", "score", "select", "misc"]
@@ -113,6 +115,8 @@ def lib():
         "pichol_check_rsqrt": ([i64, ctypes.c_uint64, vp, vp], ctypes.c_int),
         "pichol_eval_pinrmse": ([vp, vp, vp, vp], ctypes.c_int),
         "pichol_probe_fma": ([i32, i64, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "pichol_get_state": ([vp, ctypes.POINTER(i32)], ctypes.c_int),
+        "pichol_resume": ([vp, i32], ctypes.c_int),
         "pichol_batch_create": ([ctypes.POINTER(Config), i32, i32, ctypes.POINTER(vp)], ctypes.c_int),
         "pichol_batch_workspace_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
         "pichol_batch_set_workspace": ([vp, vp, ctypes.c_size_t], ctypes.c_int),
@@ -361,6 +365,38 @@ class Context:
         cur.update(kw)
         t = Tuning(cur["update_strip"], cur["diag_threads"], cur["diag_exclusive"], cur["eval_overlap"])
         _check(lib().pichol_set_tuning(self._h, ctypes.byref(t)), "pichol_set_tuning")
+
+    def state(self) -> int:
+        """Which results the workspace holds (PICHOL_STATE_* bits)."""
+        st = ctypes.c_int32(0)
+        _check(lib().pichol_get_state(self._h, ctypes.byref(st)), "pichol_get_state")
+        return int(st.value)
+
+    def state_dict(self, stream=None) -> dict:
+        """A checkpoint: the configuration, the tuning, which results the
+        workspace holds, and a copy of the workspace made on ``stream`` (default:
+        the current one) after the work enqueued there.  torch.save can store it."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        with torch.cuda.stream(s):
+            ws = self._ws.clone()
+        return {"config": bytes(self.cfg), "tuning": self.tuning(), "state": self.state(), "workspace": ws}
+
+    def load_state_dict(self, sd: dict, stream=None):
+        """Resume from ``state_dict()`` of a context with an identical
+        configuration: copy the workspace in, apply the tuning, and declare the
+        results it holds (pichol_resume)."""
+        import torch
+        if bytes(self.cfg) != sd["config"]:
+            raise ValueError("the checkpoint was saved from a context with another configuration")
+        ws = sd["workspace"]
+        if ws.dtype != self._ws.dtype or ws.numel() != self._ws.numel():
+            raise ValueError("the checkpoint's workspace does not match this context's")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        with torch.cuda.stream(s):
+            self._ws.copy_(ws, non_blocking=False)
+        self.set_tuning(**sd["tuning"])
+        _check(lib().pichol_resume(self._h, int(sd["state"])), "pichol_resume")
 
     def autotune(self, X, Y, *, reps=2, stream=None, cache=None, pg=None):
         """Time the launch-shape candidates on (X, Y), apply the fastest and

@@ -165,23 +165,41 @@ pichol_status pichol_set_workspace(pichol_ctx* ctx, void* workspace, size_t byte
 {
     if (!ctx || !workspace) return PICHOL_ERR_INVALID_ARG;
     if (bytes < ctx->need_bytes || ((uintptr_t)workspace & 255u)) return PICHOL_ERR_WORKSPACE;
+    // the host resources come first; the context takes the workspace only once
+    // they exist and its status word reads "no error", so a failure leaves it
+    // without a workspace (and without half-made resources)
+    if (!ctx->aux) {
+        int dev = 0, least = 0, greatest = 0;
+        cudaStream_t aux = nullptr;
+        cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+        bool ok = cudaGetDevice(&dev) == cudaSuccess &&
+                  cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                  cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+                  cudaStreamCreateWithPriority(&aux, cudaStreamNonBlocking, greatest) == cudaSuccess;
+        for (int i = 0; i < 4 && ok; ++i) ok = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            for (cudaEvent_t e : ev)
+                if (e) cudaEventDestroy(e);
+            if (aux) cudaStreamDestroy(aux);
+            return PICHOL_ERR_CUDA;
+        }
+        ctx->aux = aux;
+        ctx->ev_fork = ev[0];
+        ctx->ev_panel = ev[1];
+        ctx->ev_upd = ev[2];
+        ctx->ev_join = ev[3];
+    }
     ctx->ws = (char*)workspace;
     ctx->ws_bytes = bytes;
     plan(ctx, ctx->ws);
     ctx->have_hessian = ctx->have_factors = ctx->have_fit = false;
-    if (!ctx->aux) {
-        int dev = 0, least = 0, greatest = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            return PICHOL_ERR_CUDA;
-        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
-            cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, greatest) != cudaSuccess)
-            return PICHOL_ERR_CUDA;
-        for (cudaEvent_t* e : {&ctx->ev_fork, &ctx->ev_panel, &ctx->ev_upd, &ctx->ev_join})
-            if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return PICHOL_ERR_CUDA;
-    }
     // the status word must read "no error" before any kernel runs
-    return cuda_status(cudaMemset(ctx->status, 0, sizeof(DevStatus)));
+    if (cudaMemset(ctx->status, 0, sizeof(DevStatus)) != cudaSuccess) {
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+        return PICHOL_ERR_CUDA;
+    }
+    return PICHOL_OK;
 }
 
 pichol_status pichol_hessian(pichol_ctx* ctx, const void* X, const void* Y, void* stream)
@@ -449,6 +467,27 @@ pichol_status pichol_set_tuning(pichol_ctx* ctx, const pichol_tuning* t)
     for (int i = 0; i < 4; ++i)
         if (t->reserved[i] != 0) return PICHOL_ERR_INVALID_ARG;
     ctx->tune = *t;
+    return PICHOL_OK;
+}
+
+pichol_status pichol_get_state(const pichol_ctx* ctx, int32_t* state)
+{
+    if (!ctx || !state) return PICHOL_ERR_INVALID_ARG;
+    *state = (ctx->have_hessian ? PICHOL_STATE_HESSIAN : 0) | (ctx->have_factors ? PICHOL_STATE_FACTORS : 0) |
+             (ctx->have_fit ? PICHOL_STATE_FIT : 0);
+    return PICHOL_OK;
+}
+
+pichol_status pichol_resume(pichol_ctx* ctx, int32_t state)
+{
+    constexpr int32_t all = PICHOL_STATE_HESSIAN | PICHOL_STATE_FACTORS | PICHOL_STATE_FIT;
+    if (!ctx || (state & ~all)) return PICHOL_ERR_INVALID_ARG;
+    if ((state & (PICHOL_STATE_FACTORS | PICHOL_STATE_FIT)) && !(state & PICHOL_STATE_HESSIAN))
+        return PICHOL_ERR_INVALID_ARG;
+    if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
+    ctx->have_hessian = (state & PICHOL_STATE_HESSIAN) != 0;
+    ctx->have_factors = (state & PICHOL_STATE_FACTORS) != 0;
+    ctx->have_fit = (state & PICHOL_STATE_FIT) != 0;
     return PICHOL_OK;
 }
 

@@ -112,13 +112,14 @@ pichol_status pichol_batch_set_workspace(pichol_batch* b, void* workspace, size_
 {
     if (!b || !workspace) return PICHOL_ERR_INVALID_ARG;
     if (bytes < b->need_bytes || ((uintptr_t)workspace & 255u)) return PICHOL_ERR_WORKSPACE;
-    b->ws = (char*)workspace;
+    b->ws = nullptr;                      // until every problem has its part
     for (int i = 0; i < b->nprob; ++i) {
         size_t need = 0;
         pichol_workspace_size(b->ctx[i], &need);
-        pichol_status st = pichol_set_workspace(b->ctx[i], b->ws + b->off[i], need);
+        pichol_status st = pichol_set_workspace(b->ctx[i], (char*)workspace + b->off[i], need);
         if (st != PICHOL_OK) return st;
     }
+    b->ws = (char*)workspace;
     return PICHOL_OK;
 }
 

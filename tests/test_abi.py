@@ -323,3 +323,47 @@ def test_plain_c_client_compiles_links_and_runs(L, tmp_path):
                            "-L", libdir, "-lpichol", "-Wl,-rpath," + libdir])
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
     assert out.strip() == "1 1 0 10 matrix not positive definite"
+
+
+def test_state_and_resume_rules_without_a_gpu(L):
+    h = _create(L, _cfg(L))[1]
+    st = ctypes.c_int32(-1)
+    assert L.pichol_get_state(h, ctypes.byref(st)) == 0 and st.value == 0
+    assert L.pichol_get_state(None, ctypes.byref(st)) == 1
+    assert L.pichol_get_state(h, None) == 1
+    assert L.pichol_resume(None, 0) == 1
+    assert L.pichol_resume(h, 8) == 1          # unknown bit
+    assert L.pichol_resume(h, 2) == 1          # factors without the Hessian
+    assert L.pichol_resume(h, 4) == 1          # fit without the Hessian
+    assert L.pichol_resume(h, 7) == 4          # no workspace yet
+    # a workspace whose CUDA setup fails (no GPU here) is not taken
+    n = ctypes.c_size_t()
+    assert L.pichol_workspace_size(h, ctypes.byref(n)) == 0
+    rc = L.pichol_set_workspace(h, ctypes.c_void_p(0x100000), n.value)
+    if rc != 0:
+        assert rc == 3
+        assert L.pichol_resume(h, 7) == 4
+        assert L.pichol_hessian(h, ctypes.c_void_p(1), ctypes.c_void_p(1), None) == 4
+    L.pichol_destroy(h)
+
+
+def test_load_state_dict_checks_the_configuration(monkeypatch):
+    import torch
+    from paper_1404_0466_gb300 import binding as B
+
+    def no_lib():
+        raise AssertionError("the C library must not be reached")
+
+    monkeypatch.setattr(B, "lib", no_lib)
+    ctx = B.Context.__new__(B.Context)
+    ctx._h = None
+    ctx.cfg = B.Config()
+    ctx.cfg.n, ctx.cfg.d = 10, 4
+    ctx._ws = torch.zeros(512, dtype=torch.uint8)
+    other = B.Config()
+    other.n, other.d = 10, 5
+    with pytest.raises(ValueError, match="another configuration"):
+        ctx.load_state_dict({"config": bytes(other), "tuning": {}, "state": 7, "workspace": ctx._ws})
+    with pytest.raises(ValueError, match="workspace does not match"):
+        ctx.load_state_dict({"config": bytes(ctx.cfg), "tuning": {}, "state": 7,
+                             "workspace": torch.zeros(256, dtype=torch.uint8)})

@@ -342,6 +342,13 @@ class Context:
         _check(lib().pichol_get_info(self._h, ctypes.byref(inf), ctypes.c_void_p(_stream_ptr(stream))), "pichol_get_info")
         return inf
 
+    def check(self, stream=None) -> None:
+        """Synchronise ``stream`` and raise PicholError if a device error was
+        latched (pichol_get_info), naming the fold, index and pivot."""
+        inf = self.info(stream)
+        if inf.code != 0:
+            raise PicholError(inf.code, f"device (fold {inf.fold}, index {inf.index}, pivot {inf.pivot})")
+
     def check_timeout(self, cycles: int, stream=None):
         """One bounded wait that runs out after `cycles` clocks (latches PICHOL_ERR_TIMEOUT)."""
         _check(lib().pichol_check_timeout(self._h, cycles, ctypes.c_void_p(_stream_ptr(stream))),

@@ -367,3 +367,15 @@ def test_load_state_dict_checks_the_configuration(monkeypatch):
     with pytest.raises(ValueError, match="workspace does not match"):
         ctx.load_state_dict({"config": bytes(ctx.cfg), "tuning": {}, "state": 7,
                              "workspace": torch.zeros(256, dtype=torch.uint8)})
+
+
+def test_check_raises_the_latched_device_error(monkeypatch):
+    from paper_1404_0466_gb300 import binding as B
+    ctx = B.Context.__new__(B.Context)
+    ctx._h = None
+    monkeypatch.setattr(B.Context, "info", lambda self, stream=None: B.Info(0, -1, -1, -1, 0))
+    ctx.check()
+    monkeypatch.setattr(B.Context, "info", lambda self, stream=None: B.Info(2, 3, 1, 417, 0))
+    with pytest.raises(B.PicholError, match="PICHOL_ERR_NOT_SPD") as ei:
+        ctx.check()
+    assert ei.value.code == 2 and "fold 3" in str(ei.value) and "pivot 417" in str(ei.value)

@@ -52,6 +52,13 @@
 extern "C" {
 #endif
 
+/* Version of this interface.  The minor number grows when calls or fields
+ * are added (old callers keep working: new config fields take the place of
+ * reserved ones, which must be zero); the major number grows when a call or
+ * a layout changes incompatibly. */
+#define PICHOL_VERSION_MAJOR 1
+#define PICHOL_VERSION_MINOR 1
+
 typedef enum {
     PICHOL_OK = 0,
     PICHOL_ERR_INVALID_ARG = 1,   /* bad size, null pointer, unsupported combination */
@@ -479,6 +486,10 @@ PICHOL_API void pichol_batch_destroy(pichol_batch* b);
 
 /* Short text for a status code (static storage). */
 PICHOL_API const char* pichol_status_string(pichol_status s);
+
+/* The interface version the library was built with: 100 * major + minor
+ * (compare with PICHOL_VERSION_MAJOR / _MINOR of the header in use). */
+PICHOL_API int32_t pichol_version(void);
 
 #ifdef __cplusplus
 }

@@ -15,6 +15,7 @@ from dataclasses import dataclass
 
 _PKG = pathlib.Path(__file__).resolve().parent
 LIB_PATH = _PKG / "libpichol.so"
+INTERFACE = (1, 1)          # PICHOL_VERSION_MAJOR, _MINOR of include/pichol.h
 
 PICHOL_MODE_FP64, PICHOL_MODE_MIXED = 0, 1
 PICHOL_STATE_HESSIAN, PICHOL_STATE_FACTORS, PICHOL_STATE_FIT = 1, 2, 4
@@ -44,7 +45,7 @@ EXPORTS = [
     "pichol_batch_set_timing", "pichol_batch_stage_times",
     "pichol_get_tuning", "pichol_set_tuning", "pichol_batch_set_tuning", "pichol_check_timeout",
     "pichol_mchol", "pichol_mchol_levels", "pichol_check_rsqrt", "pichol_eval_pinrmse", "pichol_probe_fma",
-    "pichol_get_state", "pichol_resume",
+    "pichol_get_state", "pichol_resume", "pichol_version",
 ]
 STAGES = ["gram", "xty", "setup", "chol_init", "chol_diag", "chol_panel", "chol_update", "fit",
           "diag_inv", "solve", "resid", "score", "select", "misc"]
@@ -117,6 +118,7 @@ def lib():
         "pichol_probe_fma": ([i32, i64, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "pichol_get_state": ([vp, ctypes.POINTER(i32)], ctypes.c_int),
         "pichol_resume": ([vp, i32], ctypes.c_int),
+        "pichol_version": ([], i32),
         "pichol_batch_create": ([ctypes.POINTER(Config), i32, i32, ctypes.POINTER(vp)], ctypes.c_int),
         "pichol_batch_workspace_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
         "pichol_batch_set_workspace": ([vp, vp, ctypes.c_size_t], ctypes.c_int),
@@ -140,6 +142,10 @@ def lib():
         fn.argtypes = args
         fn.restype = res
     del dp
+    v = L.pichol_version()
+    if v // 100 != INTERFACE[0] or v % 100 < INTERFACE[1]:
+        raise RuntimeError(f"{LIB_PATH} implements interface {v // 100}.{v % 100}, this binding needs "
+                           f"{INTERFACE[0]}.{INTERFACE[1]}: rebuild it with paper_1404_0466_gb300.build.build()")
     _lib = L
     return L
 

@@ -501,6 +501,8 @@ void pichol_destroy(pichol_ctx* ctx)
     delete ctx;
 }
 
+int32_t pichol_version(void) { return 100 * PICHOL_VERSION_MAJOR + PICHOL_VERSION_MINOR; }
+
 const char* pichol_status_string(pichol_status s)
 {
     switch (s) {

@@ -379,3 +379,11 @@ def test_check_raises_the_latched_device_error(monkeypatch):
     with pytest.raises(B.PicholError, match="PICHOL_ERR_NOT_SPD") as ei:
         ctx.check()
     assert ei.value.code == 2 and "fold 3" in str(ei.value) and "pivot 417" in str(ei.value)
+
+
+def test_interface_version_agrees(L):
+    src = open(os.path.join(ROOT, "include", "pichol.h")).read()
+    major = int(re.search(r"#define PICHOL_VERSION_MAJOR (\d+)", src).group(1))
+    minor = int(re.search(r"#define PICHOL_VERSION_MINOR (\d+)", src).group(1))
+    assert (major, minor) == binding.INTERFACE
+    assert L.pichol_version() == 100 * major + minor

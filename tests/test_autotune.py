@@ -228,3 +228,61 @@ def test_two_gloo_ranks_apply_rank_zeros_choice(tmp_path):
     assert first1 == (2, 256, False)           # rank 1 takes rank 0's choice and writes none
     assert second0 == second1 == (True, 2, 256)
     assert batch0 == batch1 == (32, 1)
+
+
+def test_tuner_drives_the_real_binding_methods(monkeypatch):
+    """The tuner against binding.Context and binding.Batch themselves (their
+    tuning calls reach a fake C library), so the method names, keywords and
+    the Tuning struct are the ones the tuner uses."""
+    import ctypes
+    from paper_1404_0466_gb300 import binding as B
+
+    lib_state = {"t": B.Tuning(4, 512, 1, 0), "bt": None, "streams": 8}
+
+    class FakeLib:
+        def pichol_get_tuning(self, h, ref):
+            ctypes.memmove(ctypes.addressof(ref._obj), ctypes.addressof(lib_state["t"]), ctypes.sizeof(B.Tuning))
+            return 0
+
+        def pichol_set_tuning(self, h, ref):
+            ctypes.memmove(ctypes.addressof(lib_state["t"]), ctypes.addressof(ref._obj), ctypes.sizeof(B.Tuning))
+            return 0
+
+        def pichol_batch_set_tuning(self, h, ref):
+            lib_state["bt"] = (ref._obj.update_strip, ref._obj.diag_threads)
+            return 0
+
+        def pichol_batch_set_streams(self, h, n):
+            lib_state["streams"] = n
+            return 0
+
+    monkeypatch.setattr(B, "lib", lambda: FakeLib())
+    ctx = B.Context.__new__(B.Context)
+    ctx._h = None                     # a null handle: nothing for the real library to free later
+    ctx.cfg = B.Config()
+    ctx.cfg.mode, ctx.cfg.refine_steps = B.PICHOL_MODE_MIXED, 1
+    ran = []
+    ctx._outputs = lambda want_w: (None, None, None)
+    ctx.run = lambda X, Y, out=None, stream=None: ran.append(ctx.tuning())
+
+    def timer(fn, reps, stream):
+        fn()
+        t = ctx.tuning()
+        return _ctx_cost(t)
+
+    res = autotune.tune_context(ctx, "X", "Y", timer=timer, device="fake")
+    assert res.choice == dict(update_strip=2, diag_threads=256, diag_exclusive=0, eval_overlap=1)
+    t = lib_state["t"]
+    assert (t.update_strip, t.diag_threads, t.diag_exclusive, t.eval_overlap) == (2, 256, 0, 1)
+    assert len(ran) == 12
+
+    b = B.Batch.__new__(B.Batch)
+    b._h = None
+    b.n = 2
+    b.cfgs = (B.Config * 2)()
+    b.run = lambda Xs, Ys, stream=None: None
+    costs = {(16, 2): 1.0}
+    res = autotune.tune_batch(b, [], [], device="fake",
+                              timer=lambda fn, reps, s: costs.get((lib_state["streams"], lib_state["bt"][0]), 2.0))
+    assert res.choice == dict(streams=16, update_strip=2)
+    assert lib_state["streams"] == 16 and lib_state["bt"] == (2, 512)

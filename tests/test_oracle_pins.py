@@ -243,6 +243,10 @@ def test_sample_indices_and_grid():
     lam = orc.lambda_grid(2.0, 31, 1e-3, 1e1)
     assert np.isclose(lam[0], 2e-3) and np.isclose(lam[-1], 20.0)
     np.testing.assert_allclose(np.diff(np.log(lam)), np.log(1e4) / 30, rtol=1e-12)
+    # degenerate grids: one lambda (the low end), one sample (index 0)
+    assert np.allclose(orc.lambda_grid(2.0, 1, 1e-3, 1e1), [2e-3])
+    assert orc.sample_indices(1, 1) == [0] and orc.sample_indices(9, 1) == [0]
+    assert orc.sample_indices(2, 2) == [0, 1]
 
 
 def test_trace_scale():

@@ -1,0 +1,59 @@
+"""The oracle's pins over random small shapes (hypothesis): d down to 1, a
+single lambda, folds of one row, uneven folds and several outputs.
+
+- Exact cross-validation equals an independent pipeline: numpy.linalg.solve
+  on each fold's training normal equations (Eq. 2) and the hold-out mean
+  squared error, on the log-spaced grid scaled by tr(X^T X) / d.
+- piCholesky equals exact cross-validation when every grid lambda is a
+  sampled node (g = q, r = g - 1), in either basis.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+
+hypothesis = pytest.importorskip("hypothesis")
+from hypothesis import assume, given, settings, strategies as st  # noqa: E402
+
+
+def _library_cv(X, Y, k, q, lo=1e-3, hi=1e1):
+    n, d = X.shape
+    c = Y.shape[1]
+    bounds = [(f * n) // k for f in range(k + 1)]
+    tau = float(np.sum(X * X)) / d
+    lam = tau * lo * (hi / lo) ** (np.arange(q) / (q - 1)) if q > 1 else np.array([tau * lo])
+    E = np.empty((k, q))
+    for f in range(k):
+        keep = np.r_[0:bounds[f], bounds[f + 1]:n]
+        H, B = X[keep].T @ X[keep], X[keep].T @ Y[keep]
+        Xv, Yv = X[bounds[f]:bounds[f + 1]], Y[bounds[f]:bounds[f + 1]]
+        for t in range(q):
+            W = np.linalg.solve(H + lam[t] * np.eye(d), B)
+            E[f, t] = np.sum((Yv - Xv @ W) ** 2) / (Yv.shape[0] * c)
+    return E
+
+
+@settings(max_examples=30, deadline=None, derandomize=True)
+@given(n=st.integers(2, 40), d=st.integers(1, 8), c=st.integers(1, 3), k=st.integers(2, 6),
+       q=st.integers(1, 5), seed=st.integers(0, 2 ** 32 - 1))
+def test_exact_cv_equals_a_library_pipeline(n, d, c, k, q, seed):
+    assume(n >= k)
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, d))
+    Y = rng.standard_normal((n, c))
+    res = orc.cv(X, Y, k=k, g=1, r=0, q=q, exact=True)
+    np.testing.assert_allclose(res.E, _library_cv(X, Y, k, q), rtol=1e-8, atol=1e-12)
+    assert res.t_star == int(np.argmin(res.E.mean(axis=0)))
+
+
+@settings(max_examples=20, deadline=None, derandomize=True)
+@given(n=st.integers(12, 40), d=st.integers(1, 6), c=st.integers(1, 2), k=st.integers(2, 4),
+       q=st.integers(2, 5), basis=st.sampled_from([orc.BASIS_MONO, orc.BASIS_CHEB_LOG]),
+       seed=st.integers(0, 2 ** 32 - 1))
+def test_pichol_at_nodes_equals_exact_cv(n, d, c, k, q, basis, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, d))
+    Y = rng.standard_normal((n, c))
+    a = orc.cv(X, Y, k=k, g=q, r=q - 1, q=q, basis=basis)
+    b = orc.cv(X, Y, k=k, g=q, r=q - 1, q=q, exact=True)
+    np.testing.assert_allclose(a.E, b.E, rtol=1e-7)

@@ -5,8 +5,8 @@
  * Approximate Cross-Validation" (arXiv 1404.0466).  For k-fold cross-validation
  * of multi-output ridge regression over a grid of q regularisation values, the
  * library factors H_f + lambda_s I exactly at g sampled lambdas only
- * (Algorithm 1, step 1), fits a degree-r polynomial in lambda to every entry of
- * the lower Cholesky factor (Algorithm 1, steps 2-6), and scores the hold-out
+ * (Algorithm 1: the exact factors), fits a degree-r polynomial in lambda to every
+ * entry of the lower Cholesky factor (Algorithm 1: the fit), and scores the hold-out
  * error at all q lambdas through triangular solves with the interpolated
  * factor (Sec. 3.2 and the last paragraph of Sec. 3.3).
  *
@@ -160,7 +160,7 @@ PICHOL_API pichol_status pichol_workspace_size(const pichol_ctx* ctx, size_t* by
 PICHOL_API pichol_status pichol_set_workspace(pichol_ctx* ctx, void* workspace, size_t bytes);
 
 /*
- * Step 1: normal-equation blocks (Sec. 3.1, Eq. 2: H = X^T X, g = X^T y).
+ * Call 1 of the path: normal-equation blocks (Sec. 3.1, Eq. 2: H = X^T X, g = X^T y).
  * For every fold j: G_j = X_j^T X_j (X_j = rows of fold j), Bv_j = X_j^T Y_j,
  * yy_j = ||Y_j||_F^2; then tau = tr(sum_j G_j)/d, the lambda grid, and the
  * training right-hand sides B_f = sum_{j != f} Bv_j.  X, Y: device, row-major,
@@ -172,7 +172,7 @@ PICHOL_API pichol_status pichol_set_workspace(pichol_ctx* ctx, void* workspace, 
 PICHOL_API pichol_status pichol_hessian(pichol_ctx* ctx, const void* X, const void* Y, void* stream);
 
 /*
- * Step 2 (Algorithm 1, step 1): exact Cholesky factors L_{f,s} of
+ * Call 2 (Algorithm 1, the exact factors at the samples): exact Cholesky factors L_{f,s} of
  * H_f + lambda_s I for every fold f and each of the g sampled grid indices
  * idx_s = round(s (q-1)/(g-1)) (Sec. 6.3: samples taken from the grid), with
  * H_f = sum_{j != f} G_j.  Blocked right-looking factorisation, all k*g
@@ -184,7 +184,7 @@ PICHOL_API pichol_status pichol_hessian(pichol_ctx* ctx, const void* X, const vo
 PICHOL_API pichol_status pichol_factor_samples(pichol_ctx* ctx, void* stream);
 
 /*
- * Step 3 (Algorithm 1, steps 2-6): V[s][m] = phi_m(lambda_s) (g x (r+1)),
+ * Call 3 (Algorithm 1, the fit): V[s][m] = phi_m(lambda_s) (g x (r+1)),
  * P = V^+ by QR in double precision, and Theta_f = P T_f for every fold, where
  * row s of T_f holds the entries of L_{f,s}.  The coefficients stay in the
  * workspace (see pichol_export_theta).
@@ -192,7 +192,7 @@ PICHOL_API pichol_status pichol_factor_samples(pichol_ctx* ctx, void* stream);
 PICHOL_API pichol_status pichol_fit(pichol_ctx* ctx, void* stream);
 
 /*
- * Step 4 (Sec. 3.3 evaluation, Sec. 3.2 solves, Sec. 3.1 selection): for every
+ * Call 4 (Sec. 3.3 evaluation, Sec. 3.2 solves, Sec. 3.1 selection): for every
  * fold f and grid index t, W_{f,t} = (L~ L~^T)^{-1} B_f with
  * L~ = sum_m phi_m(lambda_t) Theta_{f,m} built tile by tile on the device, then
  * E[f*q + t] = ||Y_f - X_f W_{f,t}||_F^2 / (n_f c) evaluated as

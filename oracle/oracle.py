@@ -18,13 +18,13 @@ arXiv 1404.0466):
    scale makes the range dimensionless).
 4. g sampled lambdas at evenly spaced grid indices including both ends
    (Sec. 6.3 samples 4 of its 31 grid values; their positions are not given).
-5. Exact Cholesky factors at the sampled lambdas (Algorithm 1, step 1).
-6. Target matrix T (g x D) of vectorised lower triangles (Algorithm 1, step 2;
+5. Exact Cholesky factors at the sampled lambdas (Algorithm 1, its first step).
+6. Target matrix T (g x D) of vectorised lower triangles (Algorithm 1;
    Sec. 5: any ordering gives the same coefficients entrywise).
 7. Observation matrix V (g x (r+1)) of a polynomial basis at the sampled
-   lambdas (Algorithm 1, steps 3-4; monomials, or Chebyshev polynomials which
+   lambdas (Algorithm 1; monomials, or Chebyshev polynomials which
    Sec. 3.3 names as the more stable choice).
-8. Theta = argmin ||T - V Theta||_F (Algorithm 1, steps 5-6) by Householder QR.
+8. Theta = argmin ||T - V Theta||_F (Algorithm 1's least squares) by Householder QR.
 9. For each of the q lambdas: interpolated factor L_t = sum_m phi_m(lambda_t)
    Theta_m (Sec. 3.3, last paragraph), forward and back substitution for the c
    right-hand sides (Sec. 3.2), hold-out mean squared error.
@@ -173,7 +173,7 @@ def holdout_sse(Xv, Yv, W) -> float:
 
 
 def lstsq(V, T) -> np.ndarray:
-    """Theta = argmin ||T - V Theta||_F (Algorithm 1, steps 5-6) by Householder QR."""
+    """Theta = argmin ||T - V Theta||_F (Algorithm 1's least squares) by Householder QR."""
     V, T = _f64(V), _f64(T)
     g, p = V.shape
     D = T.shape[1]
@@ -455,14 +455,14 @@ def cv(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e
                     res.factors[(f, s)] = L
             Theta = warm_fit(theta0, Vw, Tw, pw)
         else:
-            # Algorithm 1, steps 1-2: exact factors at the samples, stacked as rows of T
+            # Algorithm 1: exact factors at the samples, stacked as rows of T
             T = np.empty((g, d * (d + 1) // 2))
             for s in range(g):
                 L = cholesky(Hf + lam_s[s] * np.eye(d))
                 T[s] = vec_lower(L)
                 if keep:
                     res.factors[(f, s)] = L
-            # steps 3-6: observation matrix and least-squares coefficients
+            # then the observation matrix and the least-squares coefficients
             V = basis_values(basis, lam_s, lam_s, p)
             Theta = lstsq(V, T)
         if keep:

@@ -159,7 +159,7 @@ double orc_holdout_sse(int64_t nv, int64_t d, int64_t c,
 }
 
 /*
- * Least-squares polynomial fit of Algorithm 1 (steps 5-6): Theta minimising
+ * Least-squares polynomial fit of Algorithm 1: Theta minimising
  * ||T - V Theta||_F, V: g x p (p = r + 1, g >= p, full column rank),
  * T: g x D, Theta: p x D.
  *

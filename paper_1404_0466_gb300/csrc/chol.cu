@@ -1,5 +1,5 @@
 // Blocked right-looking Cholesky factorisation of many shifted Hessians at once
-// (Sec. 3.2; Algorithm 1, step 1).  For each factorisation problem pr (a fold
+// (Sec. 3.2; the exact factors of Algorithm 1).  For each factorisation problem pr (a fold
 // f and a shift lambda), A = H_f + lambda I with H_f = sum_{j != f} G_j is
 // written tile-major, then for every tile column J:
 //   k_chol_diag   : L_JJ = chol(A_JJ), in double precision

@@ -1,4 +1,4 @@
-// Polynomial fit of Algorithm 1 (steps 2-6): Theta_f = P T_f, P = V^+ ((r+1) x g,
+// Polynomial fit of Algorithm 1: Theta_f = P T_f, P = V^+ ((r+1) x g,
 // computed in double by k_setup), T_f = the g sampled factors of fold f.
 // T_f is never assembled: each CTA reads one tile of all g factors and writes
 // the (r+1) coefficient planes of that tile, adjacent in memory.

@@ -207,7 +207,7 @@ __global__ void k_btrain_from_bv(const T* __restrict__ Bv, int k, int64_t len, T
 //   lambda_t = tau lo (hi/lo)^(t/(q-1))                 (Sec. 6.3 grid)
 //   idx_s = round(s (q-1)/(g-1)), lambda_s = lambda_{idx_s}
 //   V[s][m] = phi_m(lambda_s); V = Q R by modified Gram-Schmidt with one
-//   re-orthogonalisation pass; P = R^{-1} Q^T = V^+ (Algorithm 1, steps 3-6)
+//   re-orthogonalisation pass; P = R^{-1} Q^T = V^+ (Algorithm 1's observation matrix and least squares)
 //   phi[t][m] = phi_m(lambda_t), dphi[t][m] = d phi_m / d lambda at lambda_t
 //   warm start (gw > 0): lam_w[i] = lambda at round(i (q-1)/(gw-1)),
 //   vw[i][m] = phi_m(lam_w[i]), pinv_w = (first min(gw, p) columns of vw)^+

@@ -57,3 +57,46 @@ def test_pichol_at_nodes_equals_exact_cv(n, d, c, k, q, basis, seed):
     a = orc.cv(X, Y, k=k, g=q, r=q - 1, q=q, basis=basis)
     b = orc.cv(X, Y, k=k, g=q, r=q - 1, q=q, exact=True)
     np.testing.assert_allclose(a.E, b.E, rtol=1e-7)
+
+
+@settings(max_examples=40, deadline=None, derandomize=True)
+@given(g=st.integers(1, 12), p=st.integers(1, 6), D=st.integers(1, 30), seed=st.integers(0, 2 ** 32 - 1))
+def test_householder_fit_equals_library_least_squares(g, p, D, seed):
+    assume(g >= p)
+    rng = np.random.default_rng(seed)
+    V = rng.standard_normal((g, p))
+    T = rng.standard_normal((g, D))
+    np.testing.assert_allclose(orc.lstsq(V, T), np.linalg.lstsq(V, T, rcond=None)[0], rtol=1e-9, atol=1e-9)
+
+
+@settings(max_examples=40, deadline=None, derandomize=True)
+@given(lo=st.floats(-6, 3), span=st.floats(0.1, 8), g=st.integers(2, 8), p=st.integers(1, 6),
+       seed=st.integers(0, 2 ** 32 - 1))
+def test_log_chebyshev_basis_equals_chebvander(lo, span, g, p, seed):
+    rng = np.random.default_rng(seed)
+    lam_s = np.sort(10.0 ** rng.uniform(lo, lo + span, g))
+    assume(lam_s[-1] > lam_s[0] * (1 + 1e-9))
+    lam = 10.0 ** rng.uniform(lo, lo + span, 17)
+    u = 2 * (np.log(lam) - np.log(lam_s[0])) / (np.log(lam_s[-1]) - np.log(lam_s[0])) - 1
+    np.testing.assert_allclose(orc.basis_values(orc.BASIS_CHEB_LOG, lam, lam_s, p),
+                               np.polynomial.chebyshev.chebvander(u, p - 1), rtol=1e-10, atol=1e-10)
+
+
+@settings(max_examples=30, deadline=None, derandomize=True)
+@given(d=st.integers(1, 40), seed=st.integers(0, 2 ** 32 - 1))
+def test_vectorisation_round_trip_any_size(d, seed):
+    L = np.tril(np.random.default_rng(seed).standard_normal((d, d)))
+    v = orc.vec_lower(L)
+    assert v.size == d * (d + 1) // 2
+    np.testing.assert_array_equal(orc.unvec_lower(v, d), L)
+    np.testing.assert_array_equal(v, L[np.tril_indices(d)])       # row by row
+
+
+@settings(max_examples=60, deadline=None, derandomize=True)
+@given(n=st.integers(1, 10 ** 6), k=st.integers(1, 64))
+def test_fold_boundaries_partition_the_rows(n, k):
+    assume(n >= k)
+    o = orc.fold_offsets(n, k)
+    assert o[0] == 0 and o[-1] == n and all(o[f] == (f * n) // k for f in range(k + 1))
+    sizes = np.diff(o)
+    assert sizes.min() >= n // k and sizes.max() <= -(-n // k)

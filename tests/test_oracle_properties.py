@@ -100,3 +100,23 @@ def test_fold_boundaries_partition_the_rows(n, k):
     assert o[0] == 0 and o[-1] == n and all(o[f] == (f * n) // k for f in range(k + 1))
     sizes = np.diff(o)
     assert sizes.min() >= n // k and sizes.max() <= -(-n // k)
+
+
+@settings(max_examples=15, deadline=None, derandomize=True)
+@given(n=st.integers(20, 60), d=st.integers(1, 6), c=st.integers(1, 2), r=st.integers(1, 3),
+       basis=st.sampled_from([orc.BASIS_MONO, orc.BASIS_CHEB_LOG]), pos=st.floats(0.1, 0.9),
+       seed=st.integers(0, 2 ** 32 - 1))
+def test_interpolated_gradient_equals_central_differences(n, d, c, r, basis, pos, seed):
+    """dE/dlog(lambda) through the interpolated factor against central
+    differences of the same function (h = 1e-4 in log lambda), inside the
+    sampled range."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, d))
+    Y = X @ rng.standard_normal((d, c)) + 0.3 * rng.standard_normal((n, c))
+    kw = dict(k=3, g=r + 2, r=r, q=9, basis=basis, lo=0.05, hi=5.0)
+    tau = orc.trace_scale(X)
+    ll = np.log(tau * 0.05) + pos * np.log(100.0)
+    g0 = orc.holdout_grad(X, Y, log_lam=ll, **kw)
+    h = 1e-4
+    fd = (orc.holdout_grad(X, Y, log_lam=ll + h, **kw).E - orc.holdout_grad(X, Y, log_lam=ll - h, **kw).E) / (2 * h)
+    np.testing.assert_allclose(g0.dE, fd, rtol=1e-5, atol=1e-9 * np.abs(g0.E).max())

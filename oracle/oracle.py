@@ -364,7 +364,7 @@ class CVResult:
 def cv(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e1,
        basis: str = BASIS_MONO, exact: bool = False, scale_by_trace: bool = True,
        folds=None, lam_idx=None, keep: bool = False, timings: dict | None = None,
-       precond_steps: int = 0, warm: int = 0) -> CVResult:
+       precond_steps: int = 0, warm: int = 0, lams=None, lam_samples=None, offsets=None) -> CVResult:
     """k-fold CV of ridge regression over q lambdas, piCholesky (default) or
     exact Cholesky at every lambda (``exact=True``, ``Chol`` of Sec. 6.2).
 
@@ -383,7 +383,14 @@ def cv(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e
 
     ``folds`` restricts the work to some folds and ``lam_idx`` to some grid
     indices (entries outside are NaN); the grid, the samples and the fit are
-    unchanged by either.  If ``timings`` is a dict, wall-clock seconds are
+    unchanged by either.
+
+    Caller choices (Sec. 3.3: the interpolant is evaluated at any lambda without
+    a new factorisation; Sec. 1 leaves the fold split open): ``lams`` = the q
+    evaluation lambdas (absolute values) in place of the grid; ``lam_samples``
+    = the g sampled lambdas in place of the grid samples (they are the fit's
+    nodes and set the basis normalisation); ``offsets`` = the k+1 row offsets
+    of the folds in place of the floor split.  Not with ``warm``.  If ``timings`` is a dict, wall-clock seconds are
     added to its keys "setup" (grid scale), "fold" (per-fold Hessian, factors
     and fit) and "eval" (per-lambda work), and "n_eval" counts evaluations.
     """
@@ -400,9 +407,21 @@ def cv(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e
         raise ValueError("piCholesky needs g > r sampled lambdas (Algorithm 1)")
     if warm and (exact or not (2 <= warm <= g)):
         raise ValueError("the warm start needs piCholesky and 2 <= warm <= g")
-    offs = fold_offsets(n, k)
+    if warm and (lams is not None or lam_samples is not None):
+        raise ValueError("the warm start takes its samples from the grid")
+    if offsets is None:
+        offs = fold_offsets(n, k)
+    else:
+        offs = [int(o) for o in offsets]
+        if len(offs) != k + 1 or offs[0] != 0 or offs[k] != n or any(b <= a for a, b in zip(offs, offs[1:])):
+            raise ValueError("offsets must be k+1 increasing row offsets from 0 to n")
     tau = trace_scale(X) if scale_by_trace else 1.0
-    lam = lambda_grid(tau, q, lo, hi)
+    if lams is None:
+        lam = lambda_grid(tau, q, lo, hi)
+    else:
+        lam = np.asarray(lams, dtype=np.float64).reshape(-1).copy()
+        if lam.shape[0] != q or not np.all(np.isfinite(lam)) or not np.all(lam > 0):
+            raise ValueError("lams must be q finite positive values")
     sidx = sample_indices(q, g) if not exact else list(range(q))
     folds = list(range(k)) if folds is None else list(folds)
     tsel = list(range(q)) if lam_idx is None else list(lam_idx)
@@ -444,7 +463,12 @@ def cv(X, Y, *, k: int, g: int, r: int, q: int, lo: float = 1e-3, hi: float = 1e
                 tm["eval"] += _time.perf_counter() - _te
                 tm["n_eval"] += 1
             continue
-        lam_s = lam[sidx]
+        if lam_samples is None:
+            lam_s = lam[sidx]
+        else:
+            lam_s = np.asarray(lam_samples, dtype=np.float64).reshape(-1).copy()
+            if lam_s.shape[0] != g or not np.all(np.isfinite(lam_s)) or not np.all(lam_s > 0):
+                raise ValueError("lam_samples must be g finite positive values")
         if warm and f > 0:
             # warm start: g' exact factors, a degree-(p'-1) correction of fold 0's fit
             Tw = np.empty((warm, d * (d + 1) // 2))

@@ -320,6 +320,61 @@ def test_exact_cv_matches_independent_library_pipeline():
     assert res.t_star == int(np.argmin(Ebar))
 
 
+def test_caller_lambdas_and_offsets_equal_to_the_defaults_change_nothing():
+    """Passing the grid, its samples and the floor split explicitly gives the
+    default run bit for bit (the options only replace where the values come from)."""
+    p = synth.spectral_gaussian(150, 14, 2, seed=23)
+    kw = dict(k=5, g=4, r=2, q=9, basis=orc.BASIS_CHEB_LOG)
+    a = orc.cv(p.X, p.Y, **kw)
+    b = orc.cv(p.X, p.Y, lams=a.lam, lam_samples=a.lam[a.sample_idx], offsets=orc.fold_offsets(150, 5), **kw)
+    assert np.array_equal(a.E, b.E) and a.t_star == b.t_star
+
+
+def test_interpolant_at_caller_nodes_is_exact_at_those_lambdas():
+    """Algorithm 1 at caller-chosen nodes off the grid, g = r + 1: the fitted
+    polynomials pass through the exact factors there (Sec. 3.3), so piCholesky
+    evaluated at the nodes gives exact CV's hold-out errors at those lambdas,
+    while at a lambda between the nodes it differs."""
+    p = synth.spectral_gaussian(160, 12, 3, seed=24)
+    tau = orc.trace_scale(p.X)
+    nodes = tau * np.array([0.0137, 0.41, 2.9])
+    # the evaluation lambdas' own evenly spaced samples (indices 0, 2, 4) are not the nodes
+    lams = np.array([nodes[0], nodes[1], 1.7 * tau, 5.0 * tau, nodes[2]])
+    for kind in (orc.BASIS_MONO, orc.BASIS_CHEB_LOG):
+        pi = orc.cv(p.X, p.Y, k=4, g=3, r=2, q=5, basis=kind, lams=lams, lam_samples=nodes)
+        ex = orc.cv(p.X, p.Y, k=4, g=1, r=0, q=5, exact=True, lams=lams)
+        for t in (0, 1, 4):
+            np.testing.assert_allclose(pi.E[:, t], ex.E[:, t], rtol=1e-9)
+        assert np.max(np.abs(pi.E[:, 2] - ex.E[:, 2]) / ex.E[:, 2]) > 1e-7
+    # fitted at the evaluation lambdas' own samples instead, the factor at nodes[1] is interpolated
+    own = orc.cv(p.X, p.Y, k=4, g=3, r=2, q=5, basis=orc.BASIS_CHEB_LOG, lams=lams)
+    assert np.max(np.abs(own.E[:, 1] - ex.E[:, 1]) / ex.E[:, 1]) > 1e-7
+    np.testing.assert_allclose(own.E[:, 2], ex.E[:, 2], rtol=1e-9)
+
+
+def test_caller_fold_offsets_match_an_independent_pipeline():
+    """Uneven caller folds: exact CV against np.linalg.solve on each fold's
+    training rows (H_f, B_f left out by the caller's offsets), and the rows of
+    one fold scored alone."""
+    p = synth.spectral_gaussian(130, 9, 2, seed=25)
+    offs = [0, 7, 50, 51, 130]
+    lams = np.array([0.3, 2.0, 11.0])
+    res = orc.cv(p.X, p.Y, k=4, g=1, r=0, q=3, exact=True, lams=lams, offsets=offs)
+    X, Y = p.X, p.Y
+    for f in range(4):
+        keep = np.r_[0:offs[f], offs[f + 1]:130]
+        H, B = X[keep].T @ X[keep], X[keep].T @ Y[keep]
+        Xv, Yv = X[offs[f]:offs[f + 1]], Y[offs[f]:offs[f + 1]]
+        for t, lam in enumerate(lams):
+            W = np.linalg.solve(H + lam * np.eye(9), B)
+            ref = np.mean((Yv - Xv @ W) ** 2)
+            assert abs(res.E[f, t] - ref) <= 1e-10 * ref
+    with pytest.raises(ValueError):
+        orc.cv(p.X, p.Y, k=4, g=1, r=0, q=3, exact=True, offsets=[0, 7, 7, 51, 130])
+    with pytest.raises(ValueError):
+        orc.cv(p.X, p.Y, k=4, g=1, r=0, q=3, exact=True, lams=[1.0, -1.0, 2.0])
+
+
 def _kron_sum(L):
     d = L.shape[0]
     I = np.eye(d)

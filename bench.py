@@ -191,10 +191,13 @@ def summarise_clocks(lines):
 # algorithmic work per stage (for the roofline of the dominant kernel)
 # ---------------------------------------------------------------------------
 def stage_work(cfg, mode, refine, target="interpolated"):
-    """Algorithmic work per step of each timed stage: (kind, amount, bound, note).
-    kind "flop": floating-point operations the method needs (not the ones the
-    kernel happens to execute; an FMA counts 2); "byte": bytes that must cross
-    HBM."""
+    """Algorithmic work per step of each timed stage: (kind, amount, bound, executed).
+    kind "flop": floating-point operations the method needs, counted once (an
+    FMA counts 2), not the ones the kernel happens to execute; "byte": bytes
+    that must cross HBM.  ``executed`` is the factor by which the kernel's own
+    arithmetic exceeds that count (3 for the split-TF32 products, which run
+    hi*hi + hi*lo + lo*hi; about 12 for double-float accumulation on the FP32
+    pipes), reported beside the fraction and never folded into it."""
     n, d, c, k, g, r, q = (cfg[x] for x in ("n", "d", "c", "k", "g", "r", "q"))
     p = r + 1
     D = d * (d + 1) // 2
@@ -202,81 +205,96 @@ def stage_work(cfg, mode, refine, target="interpolated"):
     eb = 8 if mode == "fp64" else 4
     upd = sum((m * (m + 1) // 2) for m in range(nt)) * 2 * 64 ** 3 * k * g
     tensor = "tensor" if mode == "mixed" else "alu"
-    passes = 3 if mode == "mixed" else 1
-    return {
-        # SYRK of every fold block, n d (d + 1) flops; split TF32 runs 3 products
-        "gram": ("flop", n * d * (d + 1) * passes, tensor),
-        # X_j^T Y_j for every fold: 2 n d c flops (x3 split products)
-        "xty": ("flop", 2 * n * d * c * passes, tensor),
+    split = 3 if mode == "mixed" else 1
+    # per fold and lambda: the factor evaluated once (p multiply-adds per entry of the
+    # lower triangle, 2 p D) and two triangular solves with c right-hand sides (2 d^2 c)
+    eval_solve = k * q * (2 * d * d * c + 2 * p * D)
+    work = {
+        # SYRK of every fold block: n d (d + 1) flops
+        "gram": ("flop", n * d * (d + 1), tensor, split),
+        # X_j^T Y_j for every fold: 2 n d c flops
+        "xty": ("flop", 2 * n * d * c, tensor, split),
         # trailing updates of k g blocked factorisations (lower tiles, 2 b^3 per tile update)
-        "chol_update": ("flop", upd, "alu"),
+        "chol_update": ("flop", upd, "alu", 1),
         # the 64 x 64 diagonal tiles of k g factorisations, b^3 / 3 flops each, in FP64
-        "chol_diag": ("flop", nt * k * g * 64 ** 3 // 3, "fp64"),
+        "chol_diag": ("flop", nt * k * g * 64 ** 3 // 3, "fp64", 1),
         # panel rows by substitution: b^3 flops per off-diagonal tile of the panel
-        "chol_panel": ("flop", sum(range(nt)) * 64 ** 3 * k * g, "alu"),
-        # per (fold, lambda, tile row): L~_ii from p planes (2 (p-1) b^2 / 2) and its inverse (b^3 / 3)
-        "diag_inv": ("flop", k * q * nt * (64 ** 3 // 3 + (p - 1) * 64 * 64), "alu"),
+        "chol_panel": ("flop", sum(range(nt)) * 64 ** 3 * k * g, "alu", 1),
+        # per (fold, lambda, tile row): L~_ii from p planes (p b^2) and its inverse (b^3 / 3)
+        "diag_inv": ("flop", k * q * nt * (64 ** 3 // 3 + p * 64 * 64), "alu", 1),
         # read g factors, write p coefficient sets, per fold (lower triangles)
-        "fit": ("byte", k * (g + p) * D * eb, "hbm"),
-        # per fold and lambda: two triangular solves (2 d^2 c) + the factor built twice (2 (p-1) 2 D)
-        "solve": ("flop", k * q * (2 * d * d * c + 4 * (p - 1) * D) * (1 + refine), "alu"),
-        # two triangular products per refinement step in double-float arithmetic (error-free
-        # product + TwoSum): 11 flops per multiply-add in L~^T W, 13 in L~ (u_hi + u_lo)
-        # (FMA = 2), plus the factor built twice (2 (p-1) 2 D)
-        "resid": ("flop", k * q * refine * (12 * d * d * c + 4 * (p - 1) * D), "alu"),
-    } | ({
-        # exact-system residual: G_f W and G_all W for every lambda, 2 d^2 c each (x3 split)
-        "resid": ("flop", k * q * refine * 2 * 2 * d * d * c * passes, tensor),
-    } if target == "exact" else {}) | {
-        # per fold and lambda: <W, G W> as G_f W for all lambdas: 2 d^2 c q flops (x3 split)
-        "score": ("flop", k * q * 2 * d * d * c * passes, tensor),
+        "fit": ("byte", k * (g + p) * D * eb, "hbm", 1),
+        # the interpolated solves, once per refinement step more (the correction solve);
+        # the kernel evaluates the factor in each of its two substitutions (4 p D)
+        "solve": ("flop", eval_solve * (1 + refine), "alu",
+                  (2 * d * d * c + 4 * p * D) / (2 * d * d * c + 2 * p * D)),
+        # the residual B - L~ (L~^T W) per refinement step: the same two triangular
+        # products and one evaluation of the factor per (fold, lambda); the kernel runs them
+        # in double-float (error-free product + TwoSum: 11 and 13 flops per multiply-add)
+        # and evaluates the factor in each of its two passes
+        "resid": ("flop", eval_solve * refine, "alu",
+                  (12 * d * d * c + 4 * p * D) / (2 * d * d * c + 2 * p * D)),
+        # <W, G_f W> for every fold and lambda: G_f W as one product of N = q c columns
+        "score": ("flop", k * q * 2 * d * d * c, tensor, split),
     }
+    if target == "exact":
+        # exact-system residual: G_f W and G_all W for every lambda, 2 d^2 c each
+        work["resid"] = ("flop", k * q * refine * 2 * 2 * d * d * c, tensor, split)
+    return work
 
 
 def _peak(bound, mode, peaks):
-    if bound == "fp64":
-        return 1.25, "TFLOP/s", "nominal GB300 FP64 (1.25 TFLOP/s); no measured figure"
+    """Denominator of a stage's fraction: the measured HBM copy and bf16 figures
+    (MEASURED_PEAKS.json), and this GPU's FP32 and FP64 FMA rates measured by
+    pichol_probe_fma (all SMs of the device) when the bench has them."""
+    pipes = peaks.get("pipes") or {}
     if bound == "hbm":
         return peaks.get("hbm_gbs"), "GB/s", "of measured (MEASURED_PEAKS.json hbm_gbs)"
     if bound == "tensor":
         # TF32 dense is half the bf16 rate on this part (nominal 1.1 vs 2.25 PFLOP/s)
         return peaks.get("bf16_tflops", 1919.0) * 0.5, "TFLOP/s", \
             "TF32 = 0.5 x measured bf16 burst (MEASURED_PEAKS.json), nominal ratio"
-    if mode == "fp64":
+    if bound == "fp64" or mode == "fp64":
+        if pipes.get("fp64_fma_tflops"):
+            return pipes["fp64_fma_tflops"], "TFLOP/s", "of measured FP64 FMA rate (pichol_probe_fma, all SMs)"
         return 1.25, "TFLOP/s", "nominal GB300 FP64 (1.25 TFLOP/s); no measured figure"
+    if pipes.get("fp32_fma_tflops"):
+        return pipes["fp32_fma_tflops"], "TFLOP/s", "of measured FP32 FMA rate (pichol_probe_fma, all SMs)"
     return FP32_PEAK_TFLOPS, "TFLOP/s", "FP32 ALU: 152 SMs x 128 lanes x 2 flops x 2070 MHz (derived)"
 
 
 def roofline_of(name, ms, launches, cfg, mode, refine, steps, peaks, work=None):
+    """Roofline of one stage: achieved = algorithmic work per launch / average
+    launch duration; frac = achieved / peak.  ``executed_per_algorithmic`` is
+    how much arithmetic the kernel really runs per algorithmic flop, and
+    ``issue_rate`` the executed rate (achieved x that factor)."""
     work = work if work is not None else stage_work(cfg, mode, refine)
     info = {"kernel_stage": name, "stage_ms_per_step": ms / steps, "launches_per_step": launches / steps}
     if name not in work or ms <= 0:
         info.update({"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None})
         return info
-    kind, amount, bound = work[name]
+    kind, amount, bound, executed = work[name]
     per_launch = amount / max(1, launches / steps)
     avg_s = ms / 1e3 / max(1, launches)
     peak, unit, note = _peak(bound, mode, peaks)
     achieved = per_launch / avg_s / (1e9 if kind == "byte" else 1e12)
     info.update({"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "peak_note": note,
                  "work": kind, "work_per_launch": per_launch,
-                 "frac": (achieved / peak) if peak else None, "traffic": None})
+                 "frac": (achieved / peak) if peak else None, "traffic": None,
+                 "executed_per_algorithmic": executed, "issue_rate": achieved * executed})
     return info
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
-# stage's kernels from one ncu capture of the same code on the same workload:
-# profiles/k_solve_k_resid_mixed_ecc.md (the two residual passes, 291 MB and
-# 299 MB; the stage's third launch, the refinement axpy, is not in it).
-MEASURED_TRAFFIC = {("mixed_ecc", "resid"): 295.0e6}
+# stage's kernels from one ncu capture of the same code on the same workload,
+# for kernels unchanged since that capture.
+MEASURED_TRAFFIC = {}
 
 
 def roofline(stage_ms, cfg, mode, refine, steps, peaks, work=None, workload=None):
     name, (ms, launches) = max(stage_ms.items(), key=lambda kv: kv[1][0])
     info = roofline_of(name, ms, launches, cfg, mode, refine, steps, peaks, work=work)
     info["traffic"] = MEASURED_TRAFFIC.get((workload, name))
-    if info["traffic"] is not None:
-        info["traffic_note"] = "bytes per residual pass from ncu (profiles/k_solve_k_resid_mixed_ecc.md)"
     return info
 
 
@@ -565,14 +583,17 @@ def run_batched(args):
                 a, b = stage_ms.get(nm, (0.0, 0))
                 stage_ms[nm] = (a + ms_, b + la)
         cfg_i = dict(sp, lo=B["lo"], hi=B["hi"])
-        for nm, (kind, amount, bound) in stage_work(cfg_i, w["mode"], refine).items():
-            work[nm] = (kind, work.get(nm, (kind, 0, bound))[1] + amount, bound)
+        for nm, (kind, amount, bound, ex) in stage_work(cfg_i, w["mode"], refine).items():
+            work[nm] = (kind, work.get(nm, (kind, 0, bound, ex))[1] + amount, bound, ex)
     batch.set_timing(0)
     peaks = load_peaks()
+    pipes = {"fp32_fma_tflops": binding.probe_fma(False, 1 << 14), "fp64_fma_tflops": binding.probe_fma(True, 1 << 12),
+             "method": "8 independent FMA chains per thread, 8 CTAs of 256 threads per SM (pichol_probe_fma)"}
+    peaks["pipes"] = pipes
     top = max(stage_ms, key=lambda nm: stage_ms[nm][0])
     roof = roofline_of(top, *stage_ms[top], None, w["mode"], refine, 1, peaks, work=work)
     kern_roof = {nm: {kk: v for kk, v in roofline_of(nm, ms_, la, None, w["mode"], refine, 1, peaks, work=work).items()
-                      if kk in ("achieved", "frac", "bound", "stage_ms_per_step", "launches_per_step")}
+                      if kk in ("achieved", "frac", "bound", "stage_ms_per_step", "launches_per_step", "issue_rate")}
                  for nm, (ms_, la) in stage_ms.items() if nm in work}
     # error against the FP64 oracle and the oracle's own speed, on four problems spread
     # over the batch's size range (fold 0, five lambdas each, extrapolated to the fold)
@@ -616,6 +637,7 @@ def run_batched(args):
         "roofline": dict(roof, traffic=None,
                          timing="per-launch durations from one eager run of the batch on one stream"),
         "kernels_roofline": kern_roof,
+        "measured_pipes": pipes,
     }
     print(json.dumps(line), flush=True)
     batch.close()
@@ -1100,11 +1122,11 @@ def run_own(args):
             oracle_exact = oracle_exact_sample(prob, cfg)
         except Exception as exc:                      # context only: never costs the line
             oracle_exact = {"unavailable": f"{type(exc).__name__}: {exc}"}
-    # the FP32 and FP64 pipes measured on this GPU (the roofline keeps the derived FP32 and
-    # nominal FP64 peaks; these are reported beside them)
+    # the FP32 and FP64 pipes measured on this GPU: the denominators of the ALU-bound stages
     pipes = {"fp32_fma_tflops": binding.probe_fma(False, 1 << 14), "fp64_fma_tflops": binding.probe_fma(True, 1 << 12),
              "method": "8 independent FMA chains per thread, 8 CTAs of 256 threads per SM (pichol_probe_fma)"}
     peaks = load_peaks()
+    peaks["pipes"] = pipes
     stage_ms = {s: v for s, v in stages.items() if v[1] > 0}
     work = stage_work(cfg, w["mode"], refine, w.get("refine_target", "interpolated"))
     line = {
@@ -1119,7 +1141,7 @@ def run_own(args):
         "roofline": roofline(stage_ms, cfg, w["mode"], refine, stage_steps, peaks, work=work, workload=args.workload),
         "kernels_roofline": {nm: {kk: v for kk, v in roofline_of(nm, ms_, la, cfg, w["mode"], refine, stage_steps,
                                                                 peaks, work=work).items()
-                                  if kk in ("bound", "achieved", "peak", "unit", "frac", "stage_ms_per_step")}
+                                  if kk in ("bound", "achieved", "peak", "unit", "frac", "stage_ms_per_step", "issue_rate")}
                              for nm, (ms_, la) in stage_ms.items()
                              if nm in work},
         "stages_ms_per_step": {s: round(v[0] / stage_steps, 4) for s, v in stage_ms.items()},

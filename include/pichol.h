@@ -56,8 +56,8 @@ extern "C" {
  * are added (old callers keep working: new config fields take the place of
  * reserved ones, which must be zero); the major number grows when a call or
  * a layout changes incompatibly. */
-#define PICHOL_VERSION_MAJOR 1
-#define PICHOL_VERSION_MINOR 1
+#define PICHOL_VERSION_MAJOR 2
+#define PICHOL_VERSION_MINOR 0
 
 typedef enum {
     PICHOL_OK = 0,
@@ -162,57 +162,94 @@ PICHOL_API pichol_status pichol_set_workspace(pichol_ctx* ctx, void* workspace, 
 /*
  * Call 1 of the path: normal-equation blocks (Sec. 3.1, Eq. 2: H = X^T X, g = X^T y).
  * For every fold j: G_j = X_j^T X_j (X_j = rows of fold j), Bv_j = X_j^T Y_j,
- * yy_j = ||Y_j||_F^2; then tau = tr(sum_j G_j)/d, the lambda grid, and the
- * training right-hand sides B_f = sum_{j != f} Bv_j.  X, Y: device, row-major,
- * n x d and n x c, double (FP64 mode) or float (mixed mode).  X and Y are only
- * read during this call's kernels.  A grid that is not finite and positive, or
- * sampled lambdas that give a rank-deficient V, latch PICHOL_ERR_INVALID_ARG
- * on the device (e.g. a NaN in X with scale_by_trace set).
+ * yy_j = ||Y_j||_F^2; then tau = tr(sum_j G_j)/d, the default lambda grid
+ * lambda_t = s lam_lo (lam_hi/lam_lo)^(t/(q-1)) (s = tau if scale_by_trace
+ * else 1), the default samples lambda_{idx_s}, idx_s = round(s (q-1)/(g-1))
+ * (Sec. 6.3: samples taken from the grid), and the training right-hand sides
+ * B_f = sum_{j != f} Bv_j.
+ *   X, Y         : device, row-major, n x d and n x c, double (FP64 mode) or
+ *                  float (mixed mode); only read during this call's kernels
+ *   fold_offsets : HOST, k+1 int64 row offsets, fold f = rows
+ *                  [fold_offsets[f], fold_offsets[f+1]); offsets[0] = 0,
+ *                  offsets[k] = n, every fold at least one row (else
+ *                  PICHOL_ERR_INVALID_ARG, nothing enqueued).  NULL: the
+ *                  contiguous split fold f = rows [floor(f n/k), floor((f+1) n/k))
+ *                  (Sec. 1 leaves the split to the user).  Read during the call.
+ * A grid that is not finite and positive, or sampled lambdas that give a
+ * rank-deficient V, latch PICHOL_ERR_INVALID_ARG on the device (e.g. a NaN in
+ * X with scale_by_trace set).
  */
-PICHOL_API pichol_status pichol_hessian(pichol_ctx* ctx, const void* X, const void* Y, void* stream);
+PICHOL_API pichol_status pichol_hessian(pichol_ctx* ctx, const void* X, const void* Y, const int64_t* fold_offsets,
+                                        void* stream);
 
 /*
  * Call 2 (Algorithm 1, the exact factors at the samples): exact Cholesky factors L_{f,s} of
- * H_f + lambda_s I for every fold f and each of the g sampled grid indices
- * idx_s = round(s (q-1)/(g-1)) (Sec. 6.3: samples taken from the grid), with
+ * H_f + lambda_s I for every fold f and each of the g sampled lambdas, with
  * H_f = sum_{j != f} G_j.  Blocked right-looking factorisation, all k*g
  * problems per launch.  A non-positive pivot latches PICHOL_ERR_NOT_SPD.
+ *   lam_s : HOST, g doubles, or NULL.  The sampled lambdas (absolute values,
+ *           finite and > 0, else PICHOL_ERR_INVALID_ARG and nothing enqueued);
+ *           NULL takes the grid samples of pichol_hessian.  They also set the
+ *           observation matrix V[s][m] = phi_m(lambda_s) of pichol_fit and the
+ *           basis normalisation (largest sample for MONO, log range of the
+ *           samples for CHEB_LOG).  Values that make V rank deficient latch
+ *           PICHOL_ERR_INVALID_ARG.  With warm_samples the folds f > 0 factor
+ *           the warm-start lambdas of the default grid (see pichol_config).
+ *           Passed to the device as kernel arguments, so the call stays
+ *           capturable.
  * Part of each trailing update runs on the context's internal stream, forked
  * from `stream` by an event and joined back before the call's last enqueued
  * work, so the call orders like a single-stream call and can be captured.
  */
-PICHOL_API pichol_status pichol_factor_samples(pichol_ctx* ctx, void* stream);
+PICHOL_API pichol_status pichol_factor_samples(pichol_ctx* ctx, const double* lam_s, void* stream);
 
 /*
  * Call 3 (Algorithm 1, the fit): V[s][m] = phi_m(lambda_s) (g x (r+1)),
  * P = V^+ by QR in double precision, and Theta_f = P T_f for every fold, where
  * row s of T_f holds the entries of L_{f,s}.  The coefficients stay in the
- * workspace (see pichol_export_theta).
+ * workspace for pichol_eval_holdout.
+ *   theta_out : device or NULL.  When given, also receives a copy of every
+ *               fold's coefficients in the library's tile-major layout, of the
+ *               mode's type: k * T * (r+1) * 64 * 64 values, T = nt (nt+1)/2,
+ *               nt = ceil(d/64); value [f][i(i+1)/2 + j][m][a][b] is entry
+ *               (64 i + a, 64 j + b) of Theta_{f,m} (lower tiles j <= i;
+ *               entries above the diagonal and past d are zero, except on
+ *               the padded diagonal, whose factors are 1: there the fit of
+ *               that constant, 1 in Theta_{f,0} and 0 in the others up to
+ *               the rounding of V^+).
+ *               pichol_export_theta gives one fold as a dense matrix instead.
  */
-PICHOL_API pichol_status pichol_fit(pichol_ctx* ctx, void* stream);
+PICHOL_API pichol_status pichol_fit(pichol_ctx* ctx, void* theta_out, void* stream);
 
 /*
  * Call 4 (Sec. 3.3 evaluation, Sec. 3.2 solves, Sec. 3.1 selection): for every
- * fold f and grid index t, W_{f,t} = (L~ L~^T)^{-1} B_f with
+ * fold f and each of the q evaluation lambdas lambda_t, W_{f,t} = (L~ L~^T)^{-1} B_f with
  * L~ = sum_m phi_m(lambda_t) Theta_{f,m} built tile by tile on the device, then
  * E[f*q + t] = ||Y_f - X_f W_{f,t}||_F^2 / (n_f c) evaluated as
  * (yy_f - 2 <Bv_f, W> + <W, G_f W>) / (n_f c), and *t_star = the smallest t
  * minimising mean_f E[f*q + t] over finite values (-1 if none).
+ *   lam_t   : HOST, q doubles, or NULL.  The evaluation lambdas (absolute,
+ *             finite and > 0, any order; else PICHOL_ERR_INVALID_ARG and
+ *             nothing enqueued): the interpolant of Algorithm 1 is evaluated at
+ *             any lambda without a new factorisation (Sec. 3.3).  NULL takes
+ *             the grid of pichol_hessian.  pichol_get_lambdas then returns these
+ *             values.  Passed as kernel arguments (capturable).
  *   E_out   : device, k*q doubles
  *   t_star  : device, one int32
  *   W_out   : device or NULL; k*q*d*c values of the mode's type, [f][t][d][c]
  * A (fold, lambda) whose interpolated diagonal is unusable scores +inf.
  */
-PICHOL_API pichol_status pichol_eval_holdout(pichol_ctx* ctx, double* E_out, int32_t* t_star,
-                                  void* W_out, void* stream);
+PICHOL_API pichol_status pichol_eval_holdout(pichol_ctx* ctx, const double* lam_t, double* E_out, int32_t* t_star,
+                                             void* W_out, void* stream);
 
 /*
  * Exact-Cholesky cross-validation (the `Chol` comparator of Sec. 6.2) with the
- * same kernels: factor H_f + lambda_t I at every grid lambda, solve, score.
- * Needs only pichol_hessian before it.  Same outputs as pichol_eval_holdout.
+ * same kernels: factor H_f + lambda_t I at every evaluation lambda, solve,
+ * score.  Needs only pichol_hessian before it.  Same arguments and outputs as
+ * pichol_eval_holdout (lam_t: host q doubles or NULL for the grid).
  */
-PICHOL_API pichol_status pichol_eval_holdout_exact(pichol_ctx* ctx, double* E_out, int32_t* t_star,
-                                        void* W_out, void* stream);
+PICHOL_API pichol_status pichol_eval_holdout_exact(pichol_ctx* ctx, const double* lam_t, double* E_out,
+                                                   int32_t* t_star, void* W_out, void* stream);
 
 /*
  * Hold-out error and its derivative in log(lambda) at any lambda = exp(log_lam),
@@ -236,7 +273,8 @@ PICHOL_API pichol_status pichol_holdout_grad(pichol_ctx* ctx, double log_lam, do
  * sampled factors L_{f,s} are used for exact solves and scores, t_f[s] =
  * ||Y_f - X_f W||^2 / (n_f c) with W = (L_{f,s} L_{f,s}^T)^{-1} B_f; then
  * theta_f = V^+ t_f (the same V^+ as pichol_fit) and
- *   E_out[f*q + t] = sum_m phi_m(lambda_t) theta_f[m],
+ *   E_out[f*q + t] = sum_m phi_m(lambda_t) theta_f[m]
+ * at the current evaluation lambdas (pichol_get_lambdas),
  * and *t_star = the smallest t minimising mean_f E_out[f*q + t] over finite
  * values (-1 if none).  A fold with an unusable sampled factor scores +inf at
  * every t (pichol_info.unusable counts such samples).  E_out: device, k*q
@@ -280,7 +318,9 @@ PICHOL_API pichol_status pichol_mchol(pichol_ctx* ctx, double c, double s, doubl
  * pichol_mchol or more than 64 levels. */
 PICHOL_API pichol_status pichol_mchol_levels(double s, double s_min, int32_t* levels);
 
-/* Device copy of the q grid lambdas (after pichol_hessian). */
+/* Device copy of the q evaluation lambdas: those of the last
+ * pichol_eval_holdout / pichol_eval_holdout_exact call, or the grid of
+ * pichol_hessian (MChol's final range after pichol_mchol) before any. */
 PICHOL_API pichol_status pichol_get_lambdas(pichol_ctx* ctx, double* lam_out, void* stream);
 
 /* Inspection (for tests): dense double copies of internal results.
@@ -427,8 +467,9 @@ PICHOL_API void pichol_destroy(pichol_ctx* ctx);
  * start at zero.  Calls that overlap on the GPU (on different streams, or from
  * several threads) race on the array and give wrong results: serialise them.
  * The first call on each device looks up the array's device address with
- * cudaGetSymbolAddress (with that device current); make that first call before
- * any stream capture.  The call never calls cudaMalloc, cudaFree or any other
+ * cudaGetSymbolAddress (with that device current), and looks it up again after
+ * the device's context changed (a device reset); make that first call, and the
+ * first after a reset, before any stream capture.  The call never calls cudaMalloc, cudaFree or any other
  * allocating routine.  Errors: PICHOL_ERR_INVALID_ARG for bad arguments,
  * PICHOL_ERR_CUDA if a CUDA call fails.
  */

@@ -15,7 +15,7 @@ from dataclasses import dataclass
 
 _PKG = pathlib.Path(__file__).resolve().parent
 LIB_PATH = _PKG / "libpichol.so"
-INTERFACE = (1, 1)          # PICHOL_VERSION_MAJOR, _MINOR of include/pichol.h
+INTERFACE = (2, 0)          # PICHOL_VERSION_MAJOR, _MINOR of include/pichol.h
 
 PICHOL_MODE_FP64, PICHOL_MODE_MIXED = 0, 1
 PICHOL_STATE_HESSIAN, PICHOL_STATE_FACTORS, PICHOL_STATE_FIT = 1, 2, 4
@@ -94,11 +94,11 @@ def lib():
         "pichol_create": ([ctypes.POINTER(Config), ctypes.POINTER(vp)], ctypes.c_int),
         "pichol_workspace_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
         "pichol_set_workspace": ([vp, vp, ctypes.c_size_t], ctypes.c_int),
-        "pichol_hessian": ([vp, vp, vp, vp], ctypes.c_int),
-        "pichol_factor_samples": ([vp, vp], ctypes.c_int),
-        "pichol_fit": ([vp, vp], ctypes.c_int),
-        "pichol_eval_holdout": ([vp, vp, vp, vp, vp], ctypes.c_int),
-        "pichol_eval_holdout_exact": ([vp, vp, vp, vp, vp], ctypes.c_int),
+        "pichol_hessian": ([vp, vp, vp, vp, vp], ctypes.c_int),
+        "pichol_factor_samples": ([vp, vp, vp], ctypes.c_int),
+        "pichol_fit": ([vp, vp, vp], ctypes.c_int),
+        "pichol_eval_holdout": ([vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "pichol_eval_holdout_exact": ([vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "pichol_get_lambdas": ([vp, vp, vp], ctypes.c_int),
         "pichol_export_factor": ([vp, i32, i32, vp, vp], ctypes.c_int),
         "pichol_export_theta": ([vp, i32, vp, vp], ctypes.c_int),
@@ -223,18 +223,51 @@ class Context:
                "pichol_set_workspace")
 
     # -- steps -------------------------------------------------------------
-    def hessian(self, X, Y, stream=None):
+    def _host_doubles(self, values, count, name):
+        """A caller's lambdas as a C array of `count` doubles (kept alive on self), or None."""
+        if values is None:
+            return None
+        import numpy as np
+        a = np.ascontiguousarray(np.asarray(values, dtype=np.float64).reshape(-1))
+        if a.shape[0] != count:
+            raise ValueError(f"{name}: expected {count} values, got {a.shape[0]}")
+        return a
+
+    def hessian(self, X, Y, fold_offsets=None, stream=None):
+        """Normal-equation blocks (pichol_hessian); ``fold_offsets`` = k+1 row
+        offsets of the folds (host), None for the contiguous floor split."""
+        import numpy as np
         _require(X, "X", (self.cfg.n, self.cfg.d), self.dtype)
         _require(Y, "Y", (self.cfg.n, self.cfg.c), self.dtype)
+        offs = None
+        if fold_offsets is not None:
+            offs = np.ascontiguousarray(np.asarray(fold_offsets, dtype=np.int64).reshape(-1))
+            if offs.shape[0] != self.cfg.k + 1:
+                raise ValueError(f"fold_offsets: expected {self.cfg.k + 1} values, got {offs.shape[0]}")
         self._X, self._Y = X, Y   # keep alive while kernels may read them
         _check(lib().pichol_hessian(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
+                                    ctypes.c_void_p(offs.ctypes.data if offs is not None else 0),
                                     ctypes.c_void_p(_stream_ptr(stream))), "pichol_hessian")
 
-    def factor_samples(self, stream=None):
-        _check(lib().pichol_factor_samples(self._h, ctypes.c_void_p(_stream_ptr(stream))), "pichol_factor_samples")
+    def factor_samples(self, lam_s=None, stream=None):
+        """Exact factors at the g sampled lambdas: ``lam_s`` (absolute values,
+        host) or None for the grid samples."""
+        a = self._host_doubles(lam_s, self.cfg.g, "lam_s")
+        _check(lib().pichol_factor_samples(self._h, ctypes.c_void_p(a.ctypes.data if a is not None else 0),
+                                           ctypes.c_void_p(_stream_ptr(stream))), "pichol_factor_samples")
 
-    def fit(self, stream=None):
-        _check(lib().pichol_fit(self._h, ctypes.c_void_p(_stream_ptr(stream))), "pichol_fit")
+    def fit(self, theta_out=None, stream=None):
+        """Algorithm 1's fit; ``theta_out`` (device tensor of theta_elems() values
+        of the mode's type) also receives the tile-major coefficients."""
+        if theta_out is not None:
+            _require(theta_out, "theta_out", (self.theta_elems(),), self.dtype)
+        _check(lib().pichol_fit(self._h, ctypes.c_void_p(theta_out.data_ptr() if theta_out is not None else 0),
+                                ctypes.c_void_p(_stream_ptr(stream))), "pichol_fit")
+
+    def theta_elems(self) -> int:
+        """Values pichol_fit writes to theta_out: k * T * (r+1) * 64 * 64, T = nt (nt+1)/2."""
+        nt = (self.cfg.d + 63) // 64
+        return self.cfg.k * (nt * (nt + 1) // 2) * (self.cfg.r + 1) * 64 * 64
 
     def _outputs(self, want_w):
         import torch
@@ -257,26 +290,33 @@ class Context:
             _require(W, "W", (cfg.k, cfg.q, cfg.d, cfg.c), self.dtype)
         return E, t, W
 
-    def eval_holdout(self, want_w=False, out=None, stream=None) -> CVOutput:
+    def eval_holdout(self, want_w=False, out=None, stream=None, lam_t=None) -> CVOutput:
+        """Interpolated solves and hold-out errors at the q evaluation lambdas:
+        ``lam_t`` (absolute values, host) or None for the grid."""
         E, t, W = self._given_outputs(out, want_w)
-        _check(lib().pichol_eval_holdout(self._h, ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+        a = self._host_doubles(lam_t, self.cfg.q, "lam_t")
+        _check(lib().pichol_eval_holdout(self._h, ctypes.c_void_p(a.ctypes.data if a is not None else 0),
+                                         ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(t.data_ptr()),
                                          ctypes.c_void_p(W.data_ptr() if W is not None else 0),
                                          ctypes.c_void_p(_stream_ptr(stream))), "pichol_eval_holdout")
         return CVOutput(E, t, W)
 
-    def eval_holdout_exact(self, want_w=False, out=None, stream=None) -> CVOutput:
+    def eval_holdout_exact(self, want_w=False, out=None, stream=None, lam_t=None) -> CVOutput:
         E, t, W = self._given_outputs(out, want_w)
-        _check(lib().pichol_eval_holdout_exact(self._h, ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+        a = self._host_doubles(lam_t, self.cfg.q, "lam_t")
+        _check(lib().pichol_eval_holdout_exact(self._h, ctypes.c_void_p(a.ctypes.data if a is not None else 0),
+                                               ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(t.data_ptr()),
                                                ctypes.c_void_p(W.data_ptr() if W is not None else 0),
                                                ctypes.c_void_p(_stream_ptr(stream))), "pichol_eval_holdout_exact")
         return CVOutput(E, t, W)
 
-    def run(self, X, Y, want_w=False, out=None, stream=None) -> CVOutput:
+    def run(self, X, Y, want_w=False, out=None, stream=None, fold_offsets=None, lam_s=None,
+            lam_t=None) -> CVOutput:
         """The whole hot path: hessian, factor_samples, fit, eval_holdout."""
-        self.hessian(X, Y, stream)
-        self.factor_samples(stream)
-        self.fit(stream)
-        return self.eval_holdout(want_w, out, stream)
+        self.hessian(X, Y, fold_offsets, stream)
+        self.factor_samples(lam_s, stream)
+        self.fit(stream=stream)
+        return self.eval_holdout(want_w, out, stream, lam_t=lam_t)
 
     def holdout_grad(self, log_lam: float, stream=None):
         """(E, dE/dlog(lambda)) per fold at lambda = exp(log_lam), through the

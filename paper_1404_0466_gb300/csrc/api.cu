@@ -29,6 +29,7 @@ size_t plan(pichol_ctx* ctx, char* base)
     ctx->status = (DevStatus*)take(sizeof(DevStatus));
     ctx->scal = (double*)take(8 * sizeof(double));
     ctx->lam = (double*)take(q * sizeof(double));
+    ctx->lam_grid = (double*)take(q * sizeof(double));
     ctx->mlam = (double*)take(8 * sizeof(double));
     ctx->lam_s = (double*)take(g * sizeof(double));
     ctx->pinv = (double*)take(p * g * sizeof(double));
@@ -54,15 +55,19 @@ size_t plan(pichol_ctx* ctx, char* base)
     ctx->Rres = refine ? take((size_t)(k * q * dp * cc * eb)) : nullptr;
     if (c.mode == PICHOL_MODE_MIXED) {
         const int64_t qc = q * cc;
-        ctx->Xh = (float*)take((size_t)(dp * ctx->kpad * 4));
-        ctx->Xl = (float*)take((size_t)(dp * ctx->kpad * 4));
-        ctx->Yh = (float*)take((size_t)(cc * ctx->kpad * 4));
-        ctx->Yl = (float*)take((size_t)(cc * ctx->kpad * 4));
+        ctx->Xh = (float*)take((size_t)(dp * ctx->kpad_cap * 4));
+        ctx->Xl = (float*)take((size_t)(dp * ctx->kpad_cap * 4));
+        ctx->Yh = (float*)take((size_t)(cc * ctx->kpad_cap * 4));
+        ctx->Yl = (float*)take((size_t)(cc * ctx->kpad_cap * 4));
         ctx->Gh = (float*)take((size_t)(k * dp * dp * 4));
         ctx->Gl = (float*)take((size_t)(k * dp * dp * 4));
         ctx->Wth = (float*)take((size_t)(k * qc * dp * 4));
         ctx->Wtl = (float*)take((size_t)(k * qc * dp * 4));
-        ctx->U2 = (float*)take((size_t)(k * dp * ctx->ldu * 4));
+        ctx->U2 = rexact ? (float*)take((size_t)(k * dp * ctx->ldu * 4)) : nullptr;
+        ctx->Xrh = (float*)take((size_t)(c.n * dp * 4));
+        ctx->Xrl = (float*)take((size_t)(c.n * dp * 4));
+        ctx->Ycp = (float*)take((size_t)(c.n * cc * 4));
+        ctx->Escore = (double*)take((size_t)(k * ctx->mt_cap * ctx->ldu * 8));
         ctx->Gah = rexact ? (float*)take((size_t)(dp * dp * 4)) : nullptr;
         ctx->Gal = rexact ? (float*)take((size_t)(dp * dp * 4)) : nullptr;
         ctx->U3 = rexact ? (float*)take((size_t)(k * dp * ctx->ldu * 4)) : nullptr;
@@ -86,6 +91,23 @@ size_t plan(pichol_ctx* ctx, char* base)
 pichol_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PICHOL_OK : PICHOL_ERR_CUDA; }
 
 bool ready(const pichol_ctx* ctx) { return ctx && ctx->ws; }
+
+// Caller lambdas: every value finite and positive.
+bool lambdas_ok(const double* v, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!(v[i] > 0.0) || !std::isfinite(v[i])) return false;
+    return true;
+}
+
+// Caller fold offsets: offs[0] = 0, offs[k] = n, strictly increasing.
+bool offsets_ok(const int64_t* o, int k, int64_t n)
+{
+    if (o[0] != 0 || o[k] != n) return false;
+    for (int f = 0; f < k; ++f)
+        if (!(o[f + 1] > o[f])) return false;
+    return true;
+}
 
 }  // namespace
 
@@ -145,7 +167,10 @@ pichol_status pichol_create(const pichol_config* cfg, pichol_ctx** out)
     ctx->exact_batch = c.exact_batch > 0 ? c.exact_batch : c.q;
     ctx->nfac = (int64_t)c.k * (ctx->exact_batch > c.g ? ctx->exact_batch : c.g);
     ctx->kpad = tc_kpad(ctx);
+    ctx->kpad_cap = (c.n + 31 * (int64_t)c.k) / 32 * 32;
     ctx->ldu = ((int64_t)c.q * c.c + 3) / 4 * 4;
+    // the largest fold any split can make has n - (k - 1) rows
+    ctx->mt_cap = (int)((c.n - (c.k - 1) + 127) / 128);
     ctx->need_bytes = plan(ctx, nullptr);
     ctx->tune.update_strip = 4;
     ctx->tune.diag_threads = 512;
@@ -202,11 +227,16 @@ pichol_status pichol_set_workspace(pichol_ctx* ctx, void* workspace, size_t byte
     return PICHOL_OK;
 }
 
-pichol_status pichol_hessian(pichol_ctx* ctx, const void* X, const void* Y, void* stream)
+pichol_status pichol_hessian(pichol_ctx* ctx, const void* X, const void* Y, const int64_t* fold_offsets,
+                             void* stream)
 {
     CallRange range_(__func__);
     if (!ctx || !X || !Y) return PICHOL_ERR_INVALID_ARG;
+    const pichol_config& c = ctx->cfg;
+    if (fold_offsets && !offsets_ok(fold_offsets, c.k, c.n)) return PICHOL_ERR_INVALID_ARG;
     if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
+    for (int f = 0; f <= c.k; ++f) ctx->offs[f] = fold_offsets ? fold_offsets[f] : (int64_t)f * c.n / c.k;
+    ctx->kpad = tc_kpad(ctx);   // <= kpad_cap for every split
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), s);
     pichol_status st = cuda_status(e == cudaSuccess ? launch_gram(ctx, X, Y, s) : e);
@@ -215,52 +245,66 @@ pichol_status pichol_hessian(pichol_ctx* ctx, const void* X, const void* Y, void
     return st;
 }
 
-pichol_status pichol_factor_samples(pichol_ctx* ctx, void* stream)
+pichol_status pichol_factor_samples(pichol_ctx* ctx, const double* lam_s, void* stream)
 {
     CallRange range_(__func__);
     if (!ctx) return PICHOL_ERR_INVALID_ARG;
+    if (lam_s && !lambdas_ok(lam_s, ctx->cfg.g)) return PICHOL_ERR_INVALID_ARG;
     if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
     if (!ctx->have_hessian) return PICHOL_ERR_STATE;
-    pichol_status st = cuda_status(launch_factor(ctx, ctx->cfg.g, 0, 0, (cudaStream_t)stream));
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = launch_set_samples(ctx, lam_s, s);
+    if (e == cudaSuccess) e = launch_factor(ctx, ctx->cfg.g, 0, 0, s);
+    pichol_status st = cuda_status(e);
     ctx->have_factors = st == PICHOL_OK;
     ctx->have_fit = false;
     return st;
 }
 
-pichol_status pichol_fit(pichol_ctx* ctx, void* stream)
+pichol_status pichol_fit(pichol_ctx* ctx, void* theta_out, void* stream)
 {
     CallRange range_(__func__);
     if (!ctx) return PICHOL_ERR_INVALID_ARG;
     if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
     if (!ctx->have_factors) return PICHOL_ERR_STATE;
-    pichol_status st = cuda_status(launch_fit(ctx, (cudaStream_t)stream));
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = launch_fit(ctx, s);
+    if (e == cudaSuccess && theta_out)
+        e = cudaMemcpyAsync(theta_out, ctx->Theta,
+                            (size_t)ctx->cfg.k * ctx->ntiles * ctx->p * TILE_ELEMS * ctx->eb,
+                            cudaMemcpyDeviceToDevice, s);
+    pichol_status st = cuda_status(e);
     ctx->have_fit = st == PICHOL_OK;
     return st;
 }
 
-pichol_status pichol_eval_holdout(pichol_ctx* ctx, double* E_out, int32_t* t_star, void* W_out, void* stream)
+pichol_status pichol_eval_holdout(pichol_ctx* ctx, const double* lam_t, double* E_out, int32_t* t_star,
+                                  void* W_out, void* stream)
 {
     CallRange range_(__func__);
     if (!ctx || !E_out || !t_star) return PICHOL_ERR_INVALID_ARG;
+    if (lam_t && !lambdas_ok(lam_t, ctx->cfg.q)) return PICHOL_ERR_INVALID_ARG;
     if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
     if (!ctx->have_fit) return PICHOL_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = launch_eval(ctx, 0, 0, ctx->cfg.q, s);
+    cudaError_t e = launch_set_evals(ctx, lam_t, s);
+    if (e == cudaSuccess) e = launch_eval(ctx, 0, 0, ctx->cfg.q, s);
     if (e == cudaSuccess) e = launch_finish(ctx, E_out, t_star, s);
     if (e == cudaSuccess && W_out) e = launch_copy_w(ctx, W_out, s);
     return cuda_status(e);
 }
 
-pichol_status pichol_eval_holdout_exact(pichol_ctx* ctx, double* E_out, int32_t* t_star, void* W_out,
-                                        void* stream)
+pichol_status pichol_eval_holdout_exact(pichol_ctx* ctx, const double* lam_t, double* E_out, int32_t* t_star,
+                                        void* W_out, void* stream)
 {
     CallRange range_(__func__);
     if (!ctx || !E_out || !t_star) return PICHOL_ERR_INVALID_ARG;
+    if (lam_t && !lambdas_ok(lam_t, ctx->cfg.q)) return PICHOL_ERR_INVALID_ARG;
     if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
     if (!ctx->have_hessian) return PICHOL_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     const int q = ctx->cfg.q, b = (int)ctx->exact_batch;
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = launch_set_evals(ctx, lam_t, s);
     for (int t0 = 0; t0 < q && e == cudaSuccess; t0 += b) {
         const int cnt = (q - t0) < b ? (q - t0) : b;
         e = launch_factor(ctx, cnt, 1, t0, s);

@@ -164,10 +164,10 @@ pichol_status pichol_batch_run(pichol_batch* b, const void* const* X, const void
         const int i = b->order[r];
         cudaStream_t s = b->streams[r % b->nstreams];
         pichol_ctx* c = b->ctx[i];
-        if ((st = pichol_hessian(c, X[i], Y[i], s)) != PICHOL_OK) break;
-        if ((st = pichol_factor_samples(c, s)) != PICHOL_OK) break;
-        if ((st = pichol_fit(c, s)) != PICHOL_OK) break;
-        st = pichol_eval_holdout(c, E_out[i], t_star + i, nullptr, s);
+        if ((st = pichol_hessian(c, X[i], Y[i], nullptr, s)) != PICHOL_OK) break;
+        if ((st = pichol_factor_samples(c, nullptr, s)) != PICHOL_OK) break;
+        if ((st = pichol_fit(c, nullptr, s)) != PICHOL_OK) break;
+        st = pichol_eval_holdout(c, nullptr, E_out[i], t_star + i, nullptr, s);
     }
     // join: the caller's stream waits for every internal stream
     for (int s = 0; s < b->nstreams; ++s) {

@@ -8,7 +8,10 @@
 //   B_f  = sum_{j != f} Bv_j                                k_bsum
 //   H_f  = sum_{j != f} G_j, lower tiles                    k_hf_tiles
 #include "internal.cuh"
+
+#include <cuda.h>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 
 namespace pichol {
@@ -275,10 +278,42 @@ __device__ inline bool pinv_mgs(const double (*V)[MAX_P], int rows, int cols, do
     return ok;
 }
 
+// Basis normalisation, V and P = V^+ from the sampled lambdas lam_s (one
+// thread): scal[1..3] = (ln min lam_s, ln max lam_s, max lam_s); with a warm
+// start (gw > 0) also the warm-start lambdas (grid indices of lam_grid), V'
+// and V'^+.  A rank-deficient V latches PICHOL_ERR_INVALID_ARG.
+__device__ void samples_basis(int basis, int g, int p, int q, const double* lam_s, const double* lam_grid,
+                              double* scal, double* pinv, int gw, double* lam_w, double* pinv_w, double* vw,
+                              DevStatus* st)
+{
+    double smin = lam_s[0], smax = lam_s[0];
+    for (int i = 1; i < g; ++i) { smin = fmin(smin, lam_s[i]); smax = fmax(smax, lam_s[i]); }
+    const double a = log(smin), b = log(smax);
+    double V[MAX_G][MAX_P], dummy[MAX_P];
+    for (int i = 0; i < g; ++i) basis_eval(basis, p, lam_s[i], a, b, smax, V[i], dummy);
+    if (!pinv_mgs(V, g, p, pinv)) latch_error(st, PICHOL_ERR_INVALID_ARG, -1, -1, -1);
+    if (gw > 0) {
+        // warm start: gw samples at round(i (q-1)/(gw-1)), the same basis
+        // (normalised by the g samples), the first pw functions fitted
+        const int pw = gw < p ? gw : p;
+        double Vw[MAX_G][MAX_P];
+        for (int i = 0; i < gw; ++i) {
+            const int idx = (2 * i * (q - 1) + (gw - 1)) / (2 * (gw - 1));
+            lam_w[i] = lam_grid[idx];
+            basis_eval(basis, p, lam_w[i], a, b, smax, Vw[i], dummy);
+            for (int m = 0; m < p; ++m) vw[i * p + m] = Vw[i][m];
+        }
+        if (!pinv_mgs(Vw, gw, pw, pinv_w)) latch_error(st, PICHOL_ERR_INVALID_ARG, -1, -1, -1);
+    }
+    scal[1] = a;
+    scal[2] = b;
+    scal[3] = smax;
+}
+
 __global__ void __launch_bounds__(256)
 k_setup(const void* G, int mode_fp64, int64_t d, int64_t dp, int k, int g, int p, int q,
         double lo, double hi, const double* __restrict__ window, int scale_by_trace, int basis,
-        double* scal, double* lam, double* lam_s, double* pinv, double* phi, double* dphi,
+        double* scal, double* lam_grid, double* lam, double* lam_s, double* pinv, double* phi, double* dphi,
         int gw, double* lam_w, double* pinv_w, double* vw, DevStatus* st)
 {
     if (window) {
@@ -286,7 +321,6 @@ k_setup(const void* G, int mode_fp64, int64_t d, int64_t dp, int k, int g, int p
         hi = window[1];
     }
     __shared__ double red[256];
-    __shared__ double shared_ab[3];
     double s = 0.0;
     for (int64_t e = threadIdx.x; e < (int64_t)k * d; e += 256) {
         const int j = (int)(e / d);
@@ -301,8 +335,11 @@ k_setup(const void* G, int mode_fp64, int64_t d, int64_t dp, int k, int g, int p
         __syncthreads();
     }
     const double tau = scale_by_trace ? red[0] / (double)d : 1.0;
-    for (int t = threadIdx.x; t < q; t += 256)
-        lam[t] = (q == 1) ? tau * lo : tau * lo * pow(hi / lo, (double)t / (double)(q - 1));
+    for (int t = threadIdx.x; t < q; t += 256) {
+        const double v = (q == 1) ? tau * lo : tau * lo * pow(hi / lo, (double)t / (double)(q - 1));
+        lam_grid[t] = v;
+        lam[t] = v;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         if (!(tau > 0.0) || isinf(tau) || !(lo > 0.0) || !(hi >= lo) || isinf(hi))
@@ -310,34 +347,85 @@ k_setup(const void* G, int mode_fp64, int64_t d, int64_t dp, int k, int g, int p
         scal[0] = tau;
         for (int i = 0; i < g; ++i) {
             const int idx = (g == 1) ? 0 : (2 * i * (q - 1) + (g - 1)) / (2 * (g - 1));
-            lam_s[i] = lam[idx];
+            lam_s[i] = lam_grid[idx];
         }
-        double smin = lam_s[0], smax = lam_s[0];
-        for (int i = 1; i < g; ++i) { smin = fmin(smin, lam_s[i]); smax = fmax(smax, lam_s[i]); }
-        const double a = log(smin), b = log(smax);
-        double V[MAX_G][MAX_P], dummy[MAX_P];
-        for (int i = 0; i < g; ++i) basis_eval(basis, p, lam_s[i], a, b, smax, V[i], dummy);
-        if (!pinv_mgs(V, g, p, pinv)) latch_error(st, PICHOL_ERR_INVALID_ARG, -1, -1, -1);
-        if (gw > 0) {
-            // warm start: gw samples at round(i (q-1)/(gw-1)), the same basis
-            // (normalised by the g samples), the first pw functions fitted
-            const int pw = gw < p ? gw : p;
-            double Vw[MAX_G][MAX_P];
-            for (int i = 0; i < gw; ++i) {
-                const int idx = (2 * i * (q - 1) + (gw - 1)) / (2 * (gw - 1));
-                lam_w[i] = lam[idx];
-                basis_eval(basis, p, lam_w[i], a, b, smax, Vw[i], dummy);
-                for (int m = 0; m < p; ++m) vw[i * p + m] = Vw[i][m];
-            }
-            if (!pinv_mgs(Vw, gw, pw, pinv_w)) latch_error(st, PICHOL_ERR_INVALID_ARG, -1, -1, -1);
-        }
-        shared_ab[0] = a;
-        shared_ab[1] = b;
-        shared_ab[2] = smax;
+        samples_basis(basis, g, p, q, lam_s, lam_grid, scal, pinv, gw, lam_w, pinv_w, vw, st);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < q; t += 256)
-        basis_eval(basis, p, lam[t], shared_ab[0], shared_ab[1], shared_ab[2], phi + t * p, dphi + t * p);
+        basis_eval(basis, p, lam[t], scal[1], scal[2], scal[3], phi + t * p, dphi + t * p);
+}
+
+// The sampled lambdas of pichol_factor_samples: the caller's values (given)
+// or the default grid samples, then samples_basis and the basis values of
+// the current evaluation lambdas under the new normalisation.
+__global__ void __launch_bounds__(256)
+k_set_samples(LamValues vals, int given, int basis, int g, int p, int q, double* scal,
+              const double* __restrict__ lam_grid, const double* __restrict__ lam, double* lam_s, double* pinv,
+              double* phi, double* dphi, int gw, double* lam_w, double* pinv_w, double* vw, DevStatus* st)
+{
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < g; ++i) {
+            const int idx = (g == 1) ? 0 : (2 * i * (q - 1) + (g - 1)) / (2 * (g - 1));
+            lam_s[i] = given ? vals.v[i] : lam_grid[idx];
+        }
+        samples_basis(basis, g, p, q, lam_s, lam_grid, scal, pinv, gw, lam_w, pinv_w, vw, st);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < q; t += 256)
+        basis_eval(basis, p, lam[t], scal[1], scal[2], scal[3], phi + t * p, dphi + t * p);
+}
+
+// Evaluation lambdas [t0, t0 + count): the caller's values (given) or the
+// grid, and their basis values under the samples' normalisation.
+__global__ void __launch_bounds__(256)
+k_set_evals(LamValues vals, int given, int t0, int count, int basis, int p, const double* __restrict__ scal,
+            const double* __restrict__ lam_grid, double* lam, double* phi, double* dphi)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int t = t0 + i;
+    const double v = given ? vals.v[i] : lam_grid[t];
+    lam[t] = v;
+    basis_eval(basis, p, v, scal[1], scal[2], scal[3], phi + (int64_t)t * p, dphi + (int64_t)t * p);
+}
+
+cudaError_t launch_set_samples(pichol_ctx* ctx, const double* lam_s_host, cudaStream_t s)
+{
+    const pichol_config& c = ctx->cfg;
+    LamValues v;
+    memset(&v, 0, sizeof(v));
+    if (lam_s_host)
+        for (int i = 0; i < c.g; ++i) v.v[i] = lam_s_host[i];
+    {
+        StageScope sc_(ctx, ST_SETUP, s);
+        k_set_samples<<<1, 256, 0, s>>>(v, lam_s_host != nullptr, c.basis, c.g, ctx->p, c.q, ctx->scal,
+                                        ctx->lam_grid, ctx->lam, ctx->lam_s, ctx->pinv, ctx->phi, ctx->dphi,
+                                        c.warm_samples, ctx->lam_w, ctx->pinv_w, ctx->vw, ctx->status);
+    }
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_evals(pichol_ctx* ctx, const double* lam_t_host, cudaStream_t s)
+{
+    const pichol_config& c = ctx->cfg;
+    for (int t0 = 0; t0 < c.q; t0 += LAM_CHUNK) {
+        const int cnt = (c.q - t0) < LAM_CHUNK ? (c.q - t0) : LAM_CHUNK;
+        LamValues v;
+        memset(&v, 0, sizeof(v));
+        if (lam_t_host)
+            for (int i = 0; i < cnt; ++i) v.v[i] = lam_t_host[t0 + i];
+        {
+            StageScope sc_(ctx, ST_SETUP, s);
+            k_set_evals<<<(cnt + 255) / 256, 256, 0, s>>>(v, lam_t_host != nullptr, t0, cnt, c.basis, ctx->p,
+                                                         ctx->scal, ctx->lam_grid, ctx->lam, ctx->phi, ctx->dphi);
+        }
+        ctx->launches++;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // H_f = sum_{j != f} G_j on the lower tiles, tile-major, summed in double in
@@ -411,8 +499,8 @@ cudaError_t launch_setup(pichol_ctx* ctx, const double* window, cudaStream_t s)
     {
         StageScope sc_(ctx, ST_SETUP, s);
         k_setup<<<1, 256, 0, s>>>(ctx->G, c.mode == PICHOL_MODE_FP64, c.d, ctx->dp, c.k, c.g, ctx->p, c.q,
-                                  c.lam_lo, c.lam_hi, window, c.scale_by_trace, c.basis, ctx->scal, ctx->lam,
-                                  ctx->lam_s, ctx->pinv, ctx->phi, ctx->dphi, c.warm_samples, ctx->lam_w,
+                                  c.lam_lo, c.lam_hi, window, c.scale_by_trace, c.basis, ctx->scal, ctx->lam_grid,
+                                  ctx->lam, ctx->lam_s, ctx->pinv, ctx->phi, ctx->dphi, c.warm_samples, ctx->lam_w,
                                   ctx->pinv_w, ctx->vw, ctx->status);
     }
     ctx->launches++;
@@ -436,7 +524,26 @@ constexpr size_t NOALLOC_PART_DOUBLES = (size_t)1 << 20;
 static __device__ __align__(256) double g_noalloc_part[NOALLOC_PART_DOUBLES];
 
 static std::mutex g_noalloc_mu;
-static double* g_noalloc_ptr[256];   // device address of g_noalloc_part, per device
+// Device address of g_noalloc_part per device, and the driver context it was
+// looked up in: the address belongs to that context's copy of the module, so
+// after a device reset (or under another context on the same device) it is
+// looked up again.
+static double* g_noalloc_ptr[256];
+static CUcontext g_noalloc_ctx[256];
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+static CtxGetCurrentFn ctx_get_current_fn()
+{
+    static CtxGetCurrentFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGetCurrentFn)p;
+    }
+    return fn;
+}
 
 // Bv_j (k x d x c) and B_f (k x d x c), unpadded, from the partial sums.
 template <typename T>
@@ -502,10 +609,14 @@ extern "C" PICHOL_API pichol_status pichol_fold_rhs_noalloc(int32_t mode, const 
     double* part = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
+        CUcontext cur = nullptr;
+        CtxGetCurrentFn cfn = ctx_get_current_fn();
+        if (!cfn || cfn(&cur) != CUDA_SUCCESS) cur = nullptr;
+        if (!g_noalloc_ptr[dev] || g_noalloc_ctx[dev] != cur) {
             void* addr = nullptr;
             if (cudaGetSymbolAddress(&addr, g_noalloc_part) != cudaSuccess || !addr) return PICHOL_ERR_CUDA;
             g_noalloc_ptr[dev] = (double*)addr;
+            g_noalloc_ctx[dev] = cur;
         }
         part = g_noalloc_ptr[dev];
     }

@@ -32,6 +32,14 @@ constexpr int MAX_P = 8;                 // r + 1 <= 8
 constexpr int MAX_G = 32;                // sampled lambdas
 constexpr int MAX_K = 64;                // folds
 constexpr int GRAD_CHUNKS = 8;           // chunks of a tile row in the gradient's triangular products
+constexpr int LAM_CHUNK = 448;           // caller lambdas passed per kernel launch (as arguments)
+
+// Caller-supplied lambdas travel to the device as kernel arguments (3.5 KB, inside
+// the classic 4 KB parameter space with the other arguments), so
+// the calls that take them need no copy from host memory and stay capturable.
+struct LamValues {
+    double v[LAM_CHUNK];
+};
 
 struct DevStatus {
     int code;
@@ -135,8 +143,9 @@ struct pichol_ctx {
 
     // workspace sections (device pointers once the workspace is set)
     pichol::DevStatus* status;
-    double* scal;        // [0] tau
-    double* lam;         // q
+    double* scal;        // [0] tau, [1] ln min lambda_s, [2] ln max lambda_s, [3] max lambda_s
+    double* lam;         // q: the evaluation lambdas (the grid, or the caller's)
+    double* lam_grid;    // q: the grid of pichol_hessian (or of MChol's final range)
     double* mlam;        // MChol state: [0..2] the level's lambdas, [4] c, [5] s, [6..7] final window
     double* lam_s;       // g
     double* pinv;        // p x g
@@ -159,7 +168,8 @@ struct pichol_ctx {
     void* Rres;          // k x q x dp x c (residual / correction)
     int64_t* nfc;        // k: n_f * c
     // tensor-core operands (mixed mode)
-    int64_t kpad;        // columns of the transposed, fold-padded X
+    int64_t kpad;        // columns of the transposed, fold-padded X (this fold split)
+    int64_t kpad_cap;    // the most any fold split can need: floor((n + 31 k) / 32) * 32
     int64_t ldu;         // leading dimension of U2 (q c rounded up to 4)
     float* Xh;           // dp x kpad: X^T split, TF32 part
     float* Xl;           // dp x kpad: remainder
@@ -170,7 +180,12 @@ struct pichol_ctx {
     float* Gl;
     float* Wth;          // k x (q c) x dp: W^T split
     float* Wtl;
-    float* U2;           // k x dp x ldu: G_f W for every lambda
+    float* U2;           // k x dp x ldu: G_f W for every lambda (exact-system refinement)
+    float* Xrh;          // n x dp: X split row-major, TF32 part (direct hold-out scores)
+    float* Xrl;          // n x dp: remainder
+    float* Ycp;          // n x c: copy of Y (direct hold-out scores)
+    double* Escore;      // k x mt_cap x ldu: per-(row tile, column) sums of squared residuals
+    int mt_cap;          // row tiles of 128 in the largest possible fold
     float* Gah;          // dp x dp: G_all = sum_j G_j split (exact-system refinement only)
     float* Gal;
     float* U3;           // k x dp x ldu: G_all W for every lambda (exact-system refinement only)
@@ -261,6 +276,10 @@ cudaError_t launch_resid_exact(pichol_ctx* ctx, int t0, int tcount, cudaStream_t
 // grid, samples and V^+ from the Gram blocks; window (device, nullable) holds
 // (lo, hi) replacing the configured range
 cudaError_t launch_setup(pichol_ctx* ctx, const double* window, cudaStream_t s);
+// the sampled lambdas (host values or NULL for the grid samples), V^+ and the basis normalisation
+cudaError_t launch_set_samples(pichol_ctx* ctx, const double* lam_s_host, cudaStream_t s);
+// the evaluation lambdas (host values or NULL for the grid) and their basis values
+cudaError_t launch_set_evals(pichol_ctx* ctx, const double* lam_t_host, cudaStream_t s);
 cudaError_t launch_mchol(pichol_ctx* ctx, double c, double s, int levels, double* trace_out, cudaStream_t st);
 int mchol_levels(double s, double s_min);
 cudaError_t launch_pinrmse(pichol_ctx* ctx, double* E_out, int32_t* t_star, cudaStream_t s);

@@ -1,6 +1,8 @@
 // Tensor-core (tcgen05, TF32) contractions of the mixed-precision path:
 //   Gram blocks     G_j = X_j^T X_j and X_j^T Y_j       (Sec. 3.1, Eq. 2)
-//   score products  U_f = G_f W_f for all q lambdas      (hold-out expansion, Sec. 3.1)
+//   hold-out scores E_f(t) = ||Y_f - X_f W_{f,t}||^2 for all q lambdas at once:
+//                   X_f W_f (N = q c columns) with the squared residuals summed
+//                   in the epilogue (Sec. 3.1's hold-out error, direct form)
 //   exact-system refinement residual (refine_target exact; not in the paper):
 //                   G_f W_f and G_all W_f, G_all = sum_j G_j, combined as
 //                   R = B_f - lambda W - (G_all W - G_f W)
@@ -29,6 +31,9 @@
 #include "internal.cuh"
 #include "tma.cuh"
 
+#include <algorithm>
+#include <cstring>
+
 namespace pichol {
 
 namespace tc {
@@ -37,7 +42,8 @@ constexpr int BM = 128, BN = 128, BK = 32;     // BK fp32 = 128 bytes = one swiz
 constexpr int STAGES = 3;
 constexpr int TILE_BYTES = BM * BK * 4;        // 16 KB per operand tile
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;    // A_hi, A_lo, B_hi, B_lo
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+constexpr int RED_BYTES = 4 * BN * 4;           // score epilogue: one float per (row quarter, column)
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */ + RED_BYTES;
 constexpr int TMEM_COLS = 256;                 // two 128-column accumulators
 constexpr int CHUNK = 4;                       // k-blocks (128 rows of K) per accumulator drain
 constexpr int EPI_WARPS = 8;                   // warps 2..9 drain and store
@@ -108,7 +114,7 @@ __device__ __forceinline__ float tf32_round(float x)
 
 }  // namespace tc
 
-enum GemmMode { GEMM_GRAM = 0, GEMM_PLAIN = 1, GEMM_XTY = 2 };
+enum GemmMode { GEMM_GRAM = 0, GEMM_PLAIN = 1, GEMM_XTY = 2, GEMM_SCORE = 3 };
 
 struct GemmArgs {
     int mode;
@@ -128,6 +134,15 @@ struct GemmArgs {
     float* Clo;
     int64_t ldc, M, N;        // valid rows / columns of one fold's C
     int64_t c_fold_stride;
+    // GEMM_SCORE: A = X row-major split (fold f = rows [k0[f], k0[f] + kn[f])),
+    // B = W^T of fold f (rows b_row_off + ..., N = lambdas x outputs), K = dp;
+    // row i, column n of the tile gives the residual Y[k0[f] + i][(t0c + n) mod yc] - (X_f W)_in
+    const float* Y;           // n x yc targets
+    int64_t yc;
+    int64_t t0c;              // column offset of the first lambda (t0 c)
+    int mt_max;               // row tiles per fold in the grid
+    double* epart;            // [f][mt_max][lde] per-column sums of squared residuals
+    int64_t lde;
     DevStatus* st;
 };
 
@@ -163,6 +178,14 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
         kx0 = a.k0[f];
         arow = tI * BM;
         brow = 0;
+    } else if (a.mode == GEMM_SCORE) {
+        tI = blockIdx.x % a.mt_max;
+        tJ = blockIdx.x / a.mt_max;
+        if ((int64_t)tI * BM >= a.kn[f]) return;   // past this fold's rows: the whole CTA leaves
+        nk = (a.K + BK - 1) / BK;
+        kx0 = 0;
+        arow = a.k0[f] + tI * BM;
+        brow = f * a.b_rows_fold + a.b_row_off + tJ * BN;
     } else {
         tI = blockIdx.x % ((int)((a.M + BM - 1) / BM));
         tJ = blockIdx.x / ((int)((a.M + BM - 1) / BM));
@@ -316,13 +339,59 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
                     }
                 }
             }
-        } else if (grow < a.M) {
+        } else if (a.mode != GEMM_SCORE && grow < a.M) {
 #pragma unroll
             for (int u = 0; u < 64; ++u) {
                 const int64_t gc = gcol0 + u;
                 if (gc < a.N) Cf[grow * a.ldc + a.c_col_off + gc] = tot[u];
             }
         }
+        }
+        if (a.mode == GEMM_SCORE) {
+            // Squared residuals (Y - X_f W)^2 of this thread's row for its 64
+            // columns, then summed over the tile's 128 rows per column in a
+            // fixed order: a reduce-scatter over the warp's 32 rows (five
+            // halvings; lane l keeps the sums of columns col(l) and col(l) + 1,
+            // col(l) = 32 l4 + 16 l3 + 8 l2 + 4 l1 + 2 l0 for the bits of l),
+            // the four row quarters through shared memory, in double.
+            const bool live = !*abort_flag;
+            const int row = qtr * 32 + lane;
+            const int64_t grow = (int64_t)tI * BM + row;
+            const int64_t gcol0 = (int64_t)tJ * BN + chalf * 64;
+            float v[64];
+            const bool rv = live && grow < a.kn[f];
+            const float* yrow = a.Y + (rv ? ((int64_t)a.k0[f] + grow) * a.yc : 0);
+            int64_t o = (a.t0c + gcol0) % a.yc;
+#pragma unroll
+            for (int u = 0; u < 64; ++u) {
+                float r = 0.0f;
+                if (rv && gcol0 + u < a.N) r = yrow[o] - tot[u];
+                v[u] = r * r;
+                o = (o + 1 == a.yc) ? 0 : o + 1;
+            }
+#pragma unroll
+            for (int h = 32, b = 16; h >= 2; h >>= 1, b >>= 1) {
+                const bool up = (lane & b) != 0;
+#pragma unroll
+                for (int u = 0; u < h; ++u) {
+                    const float keep = up ? v[u + h] : v[u];
+                    const float send = up ? v[u] : v[u + h];
+                    v[u] = keep + __shfl_xor_sync(0xffffffffu, send, b);
+                }
+            }
+            float* red = (float*)(smem + STAGES * STAGE_BYTES + 256);
+            const int col = ((lane >> 4) & 1) * 32 + ((lane >> 3) & 1) * 16 + ((lane >> 2) & 1) * 8 +
+                            ((lane >> 1) & 1) * 4 + (lane & 1) * 2;
+            red[qtr * BN + chalf * 64 + col] = v[0];
+            red[qtr * BN + chalf * 64 + col + 1] = v[1];
+            asm volatile("bar.sync 1, 256;\n" ::: "memory");   // the eight drain warps
+            if (warp < 6) {
+                const int cidx = threadIdx.x - 64;              // 0 .. 127
+                const double s = (double)red[cidx] + (double)red[BN + cidx] + (double)red[2 * BN + cidx] +
+                                 (double)red[3 * BN + cidx];
+                const int64_t gc = (int64_t)tJ * BN + cidx;
+                if (live && gc < a.N) a.epart[((int64_t)f * a.mt_max + tI) * a.lde + gc] = s;
+            }
         }
     }
     __syncwarp();
@@ -459,6 +528,8 @@ static cudaError_t gemm_attr()
     return smem_limit_once(k_tc_gemm, tc::SMEM_BYTES, set);
 }
 
+cudaError_t launch_split_xr(pichol_ctx* ctx, const float* X, const float* Y, cudaStream_t s);
+
 int64_t tc_kpad(const pichol_ctx* ctx)
 {
     int64_t kp = 0;
@@ -513,6 +584,9 @@ cudaError_t launch_gram_tc(pichol_ctx* ctx, const float* X, cudaStream_t s)
     ctx->launches++;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    // X and Y are read only during this call: keep the row-major split of X and
+    // a copy of Y for the direct hold-out scores of the evaluation
+    if ((e = launch_split_xr(ctx, X, ctx->Yin, s)) != cudaSuccess) return e;
 
     // Bv_j = X_j^T Y_j on the same operands: B = Y^T (c rows, zero-filled to 128)
     {
@@ -666,6 +740,38 @@ cudaError_t launch_resid_exact(pichol_ctx* ctx, int t0, int tcount, cudaStream_t
     return cudaGetLastError();
 }
 
+// E_f(t) sums from the per-(row tile, column) partials of the direct score:
+// S = sum over the fold's row tiles (in order) and outputs o (in order) of
+// epart[f][mt][(t - t0) c + o].  The consumers of Epart (selection, MChol,
+// PINRMSE) form yy_f + sum of a (fold, lambda)'s nt slots, so slot 0 gets
+// S - yy_f and the others zero; adding yy_f back in double changes S by a few
+// units of yy_f's last place (yy_f / S is ~1e2 at most here, so ~1e-14).
+__global__ void __launch_bounds__(256)
+k_score_direct_sum(const double* __restrict__ ep, int mt_max, int64_t lde, const int64_t* __restrict__ nfc,
+                   const double* __restrict__ yy, int64_t c, int q, int t0, int tcount, int nt,
+                   double* __restrict__ Epart)
+{
+    const int f = blockIdx.y;
+    const int tl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tl >= tcount) return;
+    const int64_t nf = nfc[f] / c;
+    const int mts = (int)((nf + 127) / 128);
+    double s = 0.0;
+    for (int mt = 0; mt < mts && mt < mt_max; ++mt) {
+        const double* row = ep + ((int64_t)f * mt_max + mt) * lde + (int64_t)tl * c;
+        for (int64_t o = 0; o < c; ++o) s += row[o];
+    }
+    double* out = Epart + ((int64_t)f * q + t0 + tl) * nt;
+    out[0] = s - yy[f];
+    for (int i = 1; i < nt; ++i) out[i] = 0.0;
+}
+
+// Mixed-mode hold-out scores of systems [t0, t0 + tcount) in the direct form
+// ||Y_f - X_f W||^2: W^T split into TF32 parts, then one split-TF32 product
+// X_f W per fold over all those lambdas (N = tcount c) whose epilogue squares
+// and sums the residuals, then the per-(fold, lambda) sums.  The expansion
+// yy - 2 <Bv, W> + <W, G_f W> cancels about ||Y_f||^2 / E_f digits of its
+// fp32 terms; the direct form does not.
 cudaError_t launch_score_tc(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s)
 {
     const pichol_config& c = ctx->cfg;
@@ -677,8 +783,8 @@ cudaError_t launch_score_tc(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s)
     }
     ctx->launches++;
     CUtensorMap ah, al, bh, bl;
-    if (!make_map(&ah, ctx->Gh, (uint64_t)dp, (uint64_t)(c.k * dp), (uint64_t)dp) ||
-        !make_map(&al, ctx->Gl, (uint64_t)dp, (uint64_t)(c.k * dp), (uint64_t)dp) ||
+    if (!make_map(&ah, ctx->Xrh, (uint64_t)dp, (uint64_t)c.n, (uint64_t)dp) ||
+        !make_map(&al, ctx->Xrl, (uint64_t)dp, (uint64_t)c.n, (uint64_t)dp) ||
         !make_map(&bh, ctx->Wth, (uint64_t)dp, (uint64_t)(c.k * qc), (uint64_t)dp) ||
         !make_map(&bl, ctx->Wtl, (uint64_t)dp, (uint64_t)(c.k * qc), (uint64_t)dp))
         return cudaErrorInvalidValue;
@@ -686,32 +792,67 @@ cudaError_t launch_score_tc(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s)
     if (e != cudaSuccess) return e;
     GemmArgs ga;
     memset(&ga, 0, sizeof(ga));
-    ga.mode = GEMM_PLAIN;
+    ga.mode = GEMM_SCORE;
     ga.passes = 3;
-    ga.a_rows_fold = (int)dp;
+    int64_t nf_max = 0;
+    for (int j = 0; j < c.k; ++j) {
+        ga.k0[j] = (int)ctx->offs[j];
+        ga.kn[j] = (int)(ctx->offs[j + 1] - ctx->offs[j]);
+        nf_max = std::max<int64_t>(nf_max, ga.kn[j]);
+    }
     ga.b_rows_fold = (int)qc;
     ga.b_row_off = t0 * (int)c.c;
-    ga.c_col_off = t0 * (int)c.c;
     ga.K = (int)dp;
-    ga.C = ctx->U2;
-    ga.ldc = ctx->ldu;
-    ga.M = dp;
     ga.N = (int64_t)tcount * c.c;
-    ga.c_fold_stride = dp * ctx->ldu;
+    ga.Y = ctx->Ycp;
+    ga.yc = c.c;
+    ga.t0c = (int64_t)t0 * c.c;
+    ga.mt_max = (int)((nf_max + tc::BM - 1) / tc::BM);
+    ga.epart = ctx->Escore;
+    ga.lde = ctx->ldu;
     ga.st = ctx->status;
-    const unsigned mt = (unsigned)((dp + tc::BM - 1) / tc::BM), nt = (unsigned)((ga.N + tc::BN - 1) / tc::BN);
+    if (ga.mt_max > ctx->mt_cap) return cudaErrorInvalidValue;
+    const unsigned nn = (unsigned)((ga.N + tc::BN - 1) / tc::BN);
     {
         StageScope sc_(ctx, ST_SCORE, s);
-        k_tc_gemm<<<dim3(mt * nt, c.k), tc::THREADS, tc::SMEM_BYTES, s>>>(ah, al, bh, bl, ga);
+        k_tc_gemm<<<dim3((unsigned)ga.mt_max * nn, c.k), tc::THREADS, tc::SMEM_BYTES, s>>>(ah, al, bh, bl, ga);
     }
     {
         StageScope sc_(ctx, ST_SCORE, s);
-        k_score_reduce<<<dim3(ctx->nt, tcount, c.k), 64, 0, s>>>(ctx->U2, ctx->ldu, (const float*)ctx->W,
-                                                                 (const float*)ctx->Bv, c.q, t0, ctx->nt, dp, c.c,
-                                                                 ctx->Epart);
+        k_score_direct_sum<<<dim3((unsigned)((tcount + 255) / 256), c.k), 256, 0, s>>>(
+            ctx->Escore, ga.mt_max, ctx->ldu, ctx->nfc, ctx->yy, c.c, c.q, t0, tcount, ctx->nt, ctx->Epart);
     }
     ctx->launches += 2;
     return cudaGetLastError();
+}
+
+// X split row-major for the direct score: Xrh / Xrl [n][dp] = TF32 part and
+// remainder of X (columns >= d zero).
+__global__ void __launch_bounds__(256)
+k_split_xr(const float* __restrict__ X, int64_t n, int64_t d, int64_t dp, float* __restrict__ Xh,
+           float* __restrict__ Xl)
+{
+    const int64_t total = n * dp;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = e / dp, col = e % dp;
+        const float v = col < d ? X[row * d + col] : 0.0f;
+        const float hi = tc::tf32_round(v);
+        Xh[e] = hi;
+        Xl[e] = v - hi;
+    }
+}
+
+cudaError_t launch_split_xr(pichol_ctx* ctx, const float* X, const float* Y, cudaStream_t s)
+{
+    const pichol_config& c = ctx->cfg;
+    {
+        StageScope sc_(ctx, ST_GRAM, s);
+        k_split_xr<<<4 * (ctx->nsm > 0 ? ctx->nsm : 152), 256, 0, s>>>(X, c.n, c.d, ctx->dp, ctx->Xrh, ctx->Xrl);
+    }
+    ctx->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(ctx->Ycp, Y, sizeof(float) * (size_t)(c.n * c.c), cudaMemcpyDeviceToDevice, s);
 }
 
 }  // namespace pichol

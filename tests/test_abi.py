@@ -83,12 +83,45 @@ def test_workspace_size_and_state_errors(L):
     # d = 130 pads to 192 = 3 tiles; the dense Gram blocks alone are 5 * 192^2 floats
     assert n.value >= 5 * 192 * 192 * 4
     # calls before a workspace is attached fail without touching the GPU
-    assert L.pichol_factor_samples(h, None) == 4
-    assert L.pichol_hessian(h, None, None, None) == 1
+    assert L.pichol_factor_samples(h, None, None) == 4
+    assert L.pichol_hessian(h, None, None, None, None) == 1
     # a misaligned or short workspace is refused before any CUDA call
     assert L.pichol_set_workspace(h, ctypes.c_void_p(0x1001), n.value) == 4
     assert L.pichol_set_workspace(h, ctypes.c_void_p(0x1000), n.value - 1) == 4
     assert L.pichol_launch_count(h) == 0
+    L.pichol_destroy(h)
+
+
+def test_caller_offsets_and_lambdas_are_checked_before_any_cuda_call(L):
+    """pichol_hessian's fold offsets (host, k+1: 0, increasing, n) and the
+    sampled and evaluation lambdas (host, finite and positive) are checked
+    before anything else, so bad values fail here without a GPU; good ones
+    reach the workspace check."""
+    rc, h = _create(L, _cfg(L))
+    assert rc == 0
+    cfg = _cfg(L)
+    k, n, g, q = cfg.k, cfg.n, cfg.g, cfg.q
+    I64 = ctypes.c_int64 * (k + 1)
+    x = ctypes.c_void_p(1)
+    good = [f * n // k for f in range(k + 1)]
+    for bad in ([1] + good[1:], good[:-1] + [n - 1], good[:2] + [good[1]] + good[3:], list(reversed(good))):
+        assert L.pichol_hessian(h, x, x, I64(*bad), None) == 1, bad
+    assert L.pichol_hessian(h, x, x, I64(*good), None) == 4          # valid: no workspace yet
+    uneven = [0, 1, 2, 3, 4, n]
+    assert L.pichol_hessian(h, x, x, I64(*uneven[:k] + [n]), None) == 4
+    D_g, D_q = ctypes.c_double * g, ctypes.c_double * q
+    for bad in (0.0, -1.0, float("nan"), float("inf")):
+        vals = [1.0] * g
+        vals[g // 2] = bad
+        assert L.pichol_factor_samples(h, D_g(*vals), None) == 1, bad
+        tv = [1.0] * q
+        tv[-1] = bad
+        E = ctypes.c_void_p(8)
+        assert L.pichol_eval_holdout(h, D_q(*tv), E, E, None, None) == 1, bad
+        assert L.pichol_eval_holdout_exact(h, D_q(*tv), E, E, None, None) == 1, bad
+    assert L.pichol_factor_samples(h, D_g(*[0.5 + i for i in range(g)]), None) == 4
+    assert L.pichol_eval_holdout(h, D_q(*[1.0] * q), ctypes.c_void_p(8), ctypes.c_void_p(8), None, None) == 4
+    assert L.pichol_fit(h, None, None) == 4
     L.pichol_destroy(h)
 
 
@@ -343,7 +376,7 @@ def test_state_and_resume_rules_without_a_gpu(L):
     if rc != 0:
         assert rc == 3
         assert L.pichol_resume(h, 7) == 4
-        assert L.pichol_hessian(h, ctypes.c_void_p(1), ctypes.c_void_p(1), None) == 4
+        assert L.pichol_hessian(h, ctypes.c_void_p(1), ctypes.c_void_p(1), None, None) == 4
     L.pichol_destroy(h)
 
 

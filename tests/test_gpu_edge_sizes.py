@@ -36,21 +36,21 @@ def _vs_oracle(torch, mode, tol_fn, *, c, r):
     fin = np.isfinite(ref.E)
     assert np.array_equal(np.isfinite(E), fin)
     tol = tol_fn(prob, ref)
-    assert np.all(np.abs(E[fin] - ref.E[fin]) <= tol[fin] * ref.E[fin])
+    assert np.all(np.abs(E[fin] - ref.E[fin]) <= tol * ref.E[fin]), float(np.max(np.abs(E[fin] - ref.E[fin]) / ref.E[fin]))
     t = int(out.t_star.cpu().item())
-    assert t == ref.t_star or ref.Ebar[t] <= ref.Ebar[ref.t_star] * (1 + float(tol.max()))
+    assert tolerances.same_choice(ref.Ebar, t, ref.t_star, tol), (t, ref.t_star)
     assert ctx.info().code == 0
 
 
 def test_largest_grid_samples_and_degree_fp64(torch_mod):
     """q = 4096, g = 32, r = 5 in FP64 mode with c = 4 (with degree 5 the FP64
     solve's double-buffered planes leave room for at most 4 outputs)."""
-    _vs_oracle(torch_mod, "fp64", lambda prob, ref: np.full(ref.E.shape, 1e-10), c=4, r=5)
+    _vs_oracle(torch_mod, "fp64", lambda prob, ref: 1e-10, c=4, r=5)
 
 
 def test_largest_grid_samples_degree_and_outputs_mixed(torch_mod):
-    """q = 4096, g = 32, r = 5, c = 32 in mixed mode (the conditioning tolerance)."""
-    _vs_oracle(torch_mod, "mixed", lambda prob, ref: tolerances.mixed_tolerance(prob.X, ref.lam, 5), c=32, r=5)
+    """q = 4096, g = 32, r = 5, c = 32 in mixed mode (1e-4)."""
+    _vs_oracle(torch_mod, "mixed", lambda prob, ref: tolerances.MIXED_RTOL, c=32, r=5)
 
 
 def test_largest_dimension_mixed(torch_mod):

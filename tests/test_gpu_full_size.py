@@ -18,6 +18,7 @@ properties that hold at any size.
   differences (h = 1e-4) and the exact-Cholesky gradient; 20 gradient steps.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -60,11 +61,9 @@ def test_mixed_ecc_full_size(torch_mod):
     assert ctx.info().code == 0
     ref = oracle.cv(prob.X, prob.Y, k=cfg["k"], g=cfg["g"], r=cfg["r"], q=cfg["q"], lo=cfg["lo"], hi=cfg["hi"],
                     basis="cheb_log")
-    tol = tolerances.mixed_tolerance(prob.X, ref.lam, cfg["k"])
     rel = np.abs(E - ref.E) / ref.E
-    assert np.all(rel <= tol), float(np.max(rel / tol))
-    if t_star != ref.t_star:
-        assert ref.Ebar[t_star] <= ref.Ebar[ref.t_star] * (1 + 1e-4), (t_star, ref.t_star)
+    assert np.all(rel <= tolerances.MIXED_RTOL), float(rel.max())
+    assert tolerances.same_choice(ref.Ebar, t_star, ref.t_star), (t_star, ref.t_star)
 
 
 def test_large_rff_full_size_properties(torch_mod):
@@ -148,6 +147,55 @@ def test_large_rff_full_size_properties(torch_mod):
         assert abs(E[0, t] - Eh) <= 1e-4 * Eh, (t, E[0, t], Eh)
 
 
+def _golden_large_rff():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "large_rff_fold0.txt")
+    out = {"idx": [], "lam": [], "E": []}
+    with open(path) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, *vals = line.split()
+            if key in ("tau", "y_sum"):
+                out[key] = float(vals[0])
+            elif key == "fingerprint_rows":
+                out[key] = [int(v) for v in vals]
+            elif key == "fingerprint_sums":
+                out[key] = [float(v) for v in vals]
+            else:
+                out["idx"].append(int(key))
+                out["lam"].append(float(vals[0]))
+                out["E"].append(float(vals[1]))
+    return out
+
+
+def test_large_rff_holdout_errors_against_the_oracle(torch_mod):
+    """Fold 0 of the large random-Fourier case at five grid lambdas against the
+    FP64 oracle's hold-out errors (stored in tests/golden by a script that runs
+    only the oracle: its Gram step is ~3.5e12 multiply-adds of plain loops).
+    The regenerated inputs are first checked against the stored fingerprint."""
+    torch = torch_mod
+    gold = _golden_large_rff()
+    cfg = synth.LARGE_RFF
+    prob = synth.large_rff()
+    for r, s in zip(gold["fingerprint_rows"], gold["fingerprint_sums"]):
+        assert abs(float(np.sum(prob.X[r].astype(np.float64))) - s) <= 1e-6 * max(1.0, abs(s)), r
+    assert abs(float(np.sum(prob.Y.astype(np.float64))) - gold["y_sum"]) <= 1e-6 * abs(gold["y_sum"])
+    ctx = _ctx(cfg, refine_steps=1)
+    out = ctx.run(_dev(torch, prob.X), _dev(torch, prob.Y))
+    torch.cuda.synchronize()
+    assert ctx.info().code == 0
+    lam = ctx.lambdas().cpu().numpy()
+    idx = gold["idx"]
+    np.testing.assert_allclose(lam[idx], gold["lam"], rtol=8 * math.sqrt(cfg["n"]) * U32)
+    E = out.E.cpu().numpy()[0, idx]
+    ref = np.array(gold["E"])
+    rel = np.abs(E - ref) / ref
+    assert np.all(rel <= tolerances.MIXED_RTOL), rel
+    assert int(np.argmin(E)) == int(np.argmin(ref))
+    ctx.close()
+
+
 def test_batched_uneven_full_size(torch_mod):
     torch = torch_mod
     from paper_1404_0466_gb300 import binding
@@ -173,10 +221,9 @@ def test_batched_uneven_full_size(torch_mod):
     for i in pick:
         pb = probs[i]
         ref = oracle.cv(pb.X, pb.Y, k=K, g=G, r=R, q=Q, lo=lo, hi=hi, basis="cheb_log", folds=[0], lam_idx=idx)
-        tol = tolerances.mixed_tolerance(pb.X, ref.lam, K, folds=[0])[0, idx]
         got = b.E[i][0].cpu().numpy()[idx]
         rel = np.abs(got - ref.E[0, idx]) / ref.E[0, idx]
-        assert np.all(rel <= tol), (i, pb.X.shape[1], rel, tol)
+        assert np.all(rel <= tolerances.MIXED_RTOL), (i, pb.X.shape[1], rel)
     for i in range(len(probs)):
         assert b.info(i).code == 0, i
     b.close()
@@ -198,10 +245,10 @@ def test_differentiation_full_size(torch_mod):
     E, dE = (t.cpu().numpy() for t in ctx.holdout_grad(ll))
     assert ctx.info().code == 0
     ref = oracle.holdout_grad(prob.X, prob.Y, log_lam=ll, **kw)
-    tolE = float(tolerances.mixed_tolerance(prob.X, np.array([math.exp(ll)]), k, folds=[0])[0, 0])
+    tolE = tolerances.MIXED_RTOL
     assert abs(E[0] - ref.E[0]) <= tolE * ref.E[0], (E[0], ref.E[0])
     # the derivative is a difference of O(E) terms computed in fp32 after two solves
-    tolD = max(1e-3, 10 * tolE)
+    tolD = 1e-3
     assert abs(dE[0] - ref.dE[0]) <= tolD * abs(ref.dE[0]) + 1e-4 * abs(ref.E[0]), (dE[0], ref.dE[0])
     # central differences of the oracle's interpolated error, h = 1e-4
     h = 1e-4

@@ -96,23 +96,36 @@ def test_host_core_samples_run_on_a_small_case():
 
 def test_roofline_entry_arithmetic():
     """achieved = algorithmic work per launch / average launch time, frac =
-    achieved / peak, and the residual's measured traffic is attached to the
-    mixed case only."""
+    achieved / peak; the work is the method's (each product counted once), the
+    kernel's extra arithmetic is a separate factor, and an ALU-bound stage is
+    measured against the probed FP32 rate when the bench has it."""
     from paper_1404_0466_gb300 import synth
     cfg = dict(synth.MIXED_ECC)
     work = bench.stage_work(cfg, "mixed", 1)
-    kind, amount, bound = work["resid"]
-    assert kind == "flop" and bound == "alu" and amount > 0
-    info = bench.roofline_of("resid", 9.0, 30, cfg, "mixed", 1, 10, {"hbm_gbs": 6695.0}, work=work)
+    kind, amount, bound, executed = work["resid"]
+    assert kind == "flop" and bound == "alu" and executed > 5
+    # one residual per (fold, lambda): 2 d^2 c for the two triangular products and
+    # 2 (r+1) D for one evaluation of the factor; 505 pairs of the mixed case
+    d, c, p = 2048, 10, 4
+    D = d * (d + 1) // 2
+    assert amount == 5 * 101 * (2 * d * d * c + 2 * p * D)
+    assert abs(amount - 50.84e9) < 0.01e9
+    kind, amount_g, bound, executed = work["gram"]
+    assert amount_g == 32768 * d * (d + 1) and bound == "tensor" and executed == 3
+    peaks = {"hbm_gbs": 6695.0, "pipes": {"fp32_fma_tflops": 77.0, "fp64_fma_tflops": 1.06}}
+    info = bench.roofline_of("resid", 9.0, 30, cfg, "mixed", 1, 10, peaks, work=work)
     per_launch = amount / 3.0
     assert abs(info["work_per_launch"] - per_launch) < 1e-6 * per_launch
     assert abs(info["achieved"] - per_launch / (9.0e-3 / 30) / 1e12) < 1e-9 * info["achieved"]
+    assert info["peak"] == 77.0
     assert abs(info["frac"] - info["achieved"] / info["peak"]) < 1e-12
-    top = bench.roofline({"resid": (9.0, 30), "solve": (5.0, 20)}, cfg, "mixed", 1, 10, {"hbm_gbs": 6695.0},
+    assert abs(info["issue_rate"] - info["achieved"] * info["executed_per_algorithmic"]) < 1e-9
+    top = bench.roofline({"resid": (9.0, 30), "solve": (5.0, 20)}, cfg, "mixed", 1, 10, peaks,
                          work=work, workload="mixed_ecc")
-    assert top["kernel_stage"] == "resid" and top["traffic"] == 295.0e6
-    other = bench.roofline({"resid": (9.0, 30)}, cfg, "mixed", 1, 10, {}, work=work, workload="fp64_small")
-    assert other["traffic"] is None
+    assert top["kernel_stage"] == "resid" and top["traffic"] is None
+    assert bench.roofline_of("chol_diag", 1.0, 32, cfg, "mixed", 1, 1, peaks, work=work)["peak"] == 1.06
+    # without a probe the derived FP32 figure stands in
+    assert bench.roofline_of("resid", 9.0, 30, cfg, "mixed", 1, 10, {}, work=work)["peak"] == bench.FP32_PEAK_TFLOPS
 
 
 def test_clock_samples_are_summarised():

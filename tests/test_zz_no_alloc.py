@@ -4,10 +4,11 @@ It serves callers that cannot allocate device memory (a plug-in inside a
 framework that owns the whole GPU through its own pool, a real-time path that
 cannot pay for cudaMalloc's implicit synchronisation): its partial sums live in
 a fixed array inside the library.  This file checks, through the C ABI, that
-two calls in a row give the training right-hand sides B_f that the regular
-workspace path (pichol_hessian, read back with pichol_export_hessian) forms,
-within the double-precision test tolerance, and that sizes beyond the fixed
-array are refused.  It is named so that pytest collects it last.
+after a call on other data of a larger shape, two calls in a row give the
+training right-hand sides B_f that the regular workspace path (pichol_hessian,
+read back with pichol_export_hessian) forms and that the FP64 oracle forms,
+within the test tolerance of the mode, and that sizes beyond the fixed array
+are refused.  It is named so that pytest collects it last.
 """
 import ctypes
 
@@ -34,8 +35,13 @@ def _noalloc(lib, torch, mode, X, Y, k):
 
 @pytest.mark.parametrize("mode_name,n,d,c,k", [("fp64", 700, 130, 3, 5), ("mixed", 1500, 200, 10, 4)])
 def test_noalloc_matches_workspace_path_twice(mode_name, n, d, c, k):
+    """A first call on other data of a larger shape leaves its partial sums in
+    the shared array; the next two calls on the test shape must not see them.
+    Both are compared with the workspace path and with the FP64 oracle's
+    right-hand sides of each fold."""
     import torch
 
+    import oracle
     from paper_1404_0466_gb300 import binding, build
     build.build()
     lib = binding.lib()
@@ -44,10 +50,17 @@ def test_noalloc_matches_workspace_path_twice(mode_name, n, d, c, k):
     prob = synth.spectral_gaussian(n, d, c, seed=31 + d)
     X = torch.from_numpy(prob.X).to(device="cuda", dtype=dt).contiguous()
     Y = torch.from_numpy(prob.Y).to(device="cuda", dtype=dt).contiguous()
+    big = synth.spectral_gaussian(n + 300, d + 70, c + 2, seed=77)
+    Xb = torch.from_numpy(big.X).to(device="cuda", dtype=dt).contiguous()
+    Yb = (-3.0 * torch.from_numpy(big.Y)).to(device="cuda", dtype=dt).contiguous()
+    rc, _, _ = _noalloc(lib, torch, mode, Xb, Yb, k + 1)
+    assert rc == 0, binding.STATUS.get(rc)
 
     ctx = binding.Context(n=n, d=d, c=c, k=k, g=2, r=1, q=3, mode=mode_name)
     ctx.hessian(X, Y)
     ref = [ctx.export_hessian(f)[1].cpu().numpy() for f in range(k)]
+    offs = oracle.fold_offsets(n, k)
+    orc = [oracle.normal_blocks(prob.X, prob.Y, offs[f], offs[f + 1])[1] for f in range(k)]
     tol = 1e-12 if mode_name == "fp64" else 1e-6
 
     for call in range(2):
@@ -56,10 +69,12 @@ def test_noalloc_matches_workspace_path_twice(mode_name, n, d, c, k):
         B = B.double().cpu().numpy()
         Bv = Bv.double().cpu().numpy()
         for f in range(k):
-            scale = np.max(np.abs(ref[f]))
+            scale = np.max(np.abs(orc[f]))
             assert np.max(np.abs(B[f] - ref[f])) <= tol * scale, (call, f)
-            # B_f + Bv_f is X^T Y over all rows, the same for every fold
-            np.testing.assert_allclose(B[f] + Bv[f], B[0] + Bv[0], rtol=0, atol=tol * scale * 4)
+            assert np.max(np.abs(B[f] - orc[f])) <= tol * scale, (call, f)
+            # Bv_f is fold f's own X_f^T Y_f
+            Xf, Yf = prob.X[offs[f]:offs[f + 1]], prob.Y[offs[f]:offs[f + 1]]
+            np.testing.assert_allclose(Bv[f], Xf.T @ Yf, rtol=0, atol=tol * scale)
     ctx.close()
 
 

@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--no-mchol", action="store_true", help="skip the MChol, PINRMSE and warm-start comparisons")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle sample (cpu_baseline, error)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the large random-Fourier workload (n = 131072, d = 8192, c = 32) sub-line")
     ap.add_argument("--no-graph", action="store_true", help="time eager calls instead of one CUDA graph per step")
     ap.add_argument("--profile", action="store_true", help="warm-up + steps only, for ncu")
     ap.add_argument("--profile-grad", action="store_true",
@@ -190,7 +192,7 @@ def summarise_clocks(lines):
 # ---------------------------------------------------------------------------
 # algorithmic work per stage (for the roofline of the dominant kernel)
 # ---------------------------------------------------------------------------
-def stage_work(cfg, mode, refine, target="interpolated"):
+def stage_work(cfg, mode, refine, target="interpolated", residual="tensor"):
     """Algorithmic work per step of each timed stage: (kind, amount, bound, executed).
     kind "flop": floating-point operations the method needs, counted once (an
     FMA counts 2), not the ones the kernel happens to execute; "byte": bytes
@@ -214,8 +216,9 @@ def stage_work(cfg, mode, refine, target="interpolated"):
         "gram": ("flop", n * d * (d + 1), tensor, split),
         # X_j^T Y_j for every fold: 2 n d c flops
         "xty": ("flop", 2 * n * d * c, tensor, split),
-        # trailing updates of k g blocked factorisations (lower tiles, 2 b^3 per tile update)
-        "chol_update": ("flop", upd, "alu", 1),
+        # trailing updates of k g blocked factorisations (lower tiles, 2 b^3 per tile update);
+        # in mixed mode the bulk of each step on the tensor cores in split TF32
+        "chol_update": ("flop", upd, tensor, split),
         # the 64 x 64 diagonal tiles of k g factorisations, b^3 / 3 flops each, in FP64
         "chol_diag": ("flop", nt * k * g * 64 ** 3 // 3, "fp64", 1),
         # panel rows by substitution: b^3 flops per off-diagonal tile of the panel
@@ -233,7 +236,10 @@ def stage_work(cfg, mode, refine, target="interpolated"):
         # in double-float (error-free product + TwoSum: 11 and 13 flops per multiply-add)
         # and evaluates the factor in each of its two passes
         "resid": ("flop", eval_solve * refine, "alu",
-                  (12 * d * d * c + 4 * p * D) / (2 * d * d * c + 2 * p * D)),
+                  (12 * d * d * c + 4 * p * D) / (2 * d * d * c + 2 * p * D)) if residual == "double_float" else
+                 # on the tensor cores: one split-TF32 product per coefficient plane and pass
+                 # (p (d^2 / 2) 2 c per lambda each, three products per split)
+                 ("flop", eval_solve * refine, tensor, 3 * 2 * p * d * d * c / (2 * d * d * c + 2 * p * D)),
         # <W, G_f W> for every fold and lambda: G_f W as one product of N = q c columns
         "score": ("flop", k * q * 2 * d * d * c, tensor, split),
     }
@@ -809,6 +815,98 @@ def warm_compare(binding, params, cfg, X, Y, stream, exact, E, t_star, warm=2):
     return res
 
 
+def _golden_large_rff():
+    """Fold-0 hold-out errors of the large random-Fourier workload stored by
+    tests/golden/make_large_rff_golden.py (which runs only the FP64 oracle)."""
+    path = os.path.join(ROOT, "tests", "golden", "large_rff_fold0.txt")
+    idx, E = [], []
+    with open(path) as fh:
+        for line in fh:
+            parts = line.split()
+            if parts and parts[0].isdigit() and len(parts) == 3:
+                idx.append(int(parts[0]))
+                E.append(float(parts[2]))
+    return idx, E
+
+
+def large_rff_compare(binding, steps=3):
+    """The large single problem (n = 131072, d = 8192 random-Fourier features,
+    c = 32, k = 5, g = 6, r = 3, q = 101, mixed, one refinement step): step
+    time and evals/s from device-resident inputs, per-stage times, the
+    interpolated solve's coefficient stream in GB/s, fold-0 errors against the
+    stored FP64-oracle values, and exact-Cholesky CV on the same GPU."""
+    import numpy as np
+    import torch
+
+    from paper_1404_0466_gb300 import synth
+    cfg = dict(synth.LARGE_RFF)
+    prob = synth.large_rff()
+    k, q, g, r, d, c = (cfg[x] for x in ("k", "q", "g", "r", "d", "c"))
+    X = torch.from_numpy(prob.X).cuda()
+    Y = torch.from_numpy(prob.Y).cuda()
+    del prob
+    params = dict(n=cfg["n"], d=d, c=c, k=k, g=g, r=r, q=q, lam_lo=cfg["lo"], lam_hi=cfg["hi"], basis="cheb_log",
+                  mode="mixed", refine_steps=1)
+    ctx = binding.Context(exact_batch=g, **params)
+    out = ctx._outputs(False)
+    stream = torch.cuda.current_stream()
+    ctx.run(X, Y, out=out)
+    torch.cuda.synchronize()
+    ctx.set_timing(4096)
+    ctx.stage_times()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.run(X, Y, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    st, complete = ctx.stage_times()
+    ctx.set_timing(0)
+    info = ctx.info()
+    idx, Eg = _golden_large_rff()
+    E = out[0].cpu().numpy()
+    err = float(np.max(np.abs(E[0, idx] - np.array(Eg)) / np.array(Eg)))
+    # the solve streams the off-diagonal coefficient tiles of its fold (p planes of
+    # 64 x 64 fp32) once per substitution, two lambdas per CTA, twice per step
+    # (solve and correction solve)
+    nt = -(-d // 64)
+    theta_bytes = k * ((q + 1) // 2) * 2 * (r + 1) * (nt * (nt + 1) // 2 - nt) * 64 * 64 * 4
+    sms, sla = st.get("solve", (0.0, 0))
+    solve_ms = sms / steps / max(1, sla / steps)
+    res = {"workload": (f"large_rff: n={cfg['n']} d={d} c={c} k={k} g={g} r={r} q={q} basis=cheb_log mode=mixed "
+                        f"refine=1"),
+           "value": k * q / (ms / 1e3), "unit": "evals/s", "ms_per_step": ms, "steps": steps,
+           "stages_ms_per_step": {nm: round(v[0] / steps, 3) for nm, v in st.items() if v[1] > 0},
+           "stage_timing_complete": complete,
+           "solve_theta_stream": {"bytes_per_launch": theta_bytes, "ms_per_launch": solve_ms,
+                                  "GBps": theta_bytes / (solve_ms / 1e3) / 1e9 if solve_ms > 0 else None,
+                                  "what": "off-diagonal coefficient planes read by one interpolated-solve launch "
+                                          "(each (fold, lambda pair) CTA reads its fold's planes in both "
+                                          "substitutions); L2 holds none of a fold's planes at this size"},
+           "err_vs_fp64": {"max_rel_E": err, "sample": f"fold 0, grid indices {idx}, stored oracle values"},
+           "device_status": binding.STATUS.get(info.code)}
+    ctx.close()
+    del ctx, out
+    torch.cuda.empty_cache()
+    ctxe = binding.Context(**dict(params, refine_steps=0))
+    oute = ctxe._outputs(False)
+    ctxe.hessian(X, Y)
+    e0.record(stream)
+    ctxe.eval_holdout_exact(out=oute)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    gram = sum(res["stages_ms_per_step"].get(nm, 0.0) for nm in ("gram", "xty"))
+    xms = e0.elapsed_time(e1) + gram
+    res["exact_cv"] = {"ms_per_step": xms, "value": k * q / (xms / 1e3), "unit": "evals/s",
+                       "note": "Gram stages taken from the piCholesky step (the same kernels)"}
+    res["speedup_vs_exact"] = xms / ms
+    ctxe.close()
+    del ctxe, oute, X, Y
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_own(args):
     import numpy as np
     import torch
@@ -1042,11 +1140,27 @@ def run_own(args):
         e1.record(stream)
         torch.cuda.synchronize()
         h2d_ms = e0.elapsed_time(e1)
+        # one call end to end with nothing overlapped: copy X, Y in, run the path,
+        # copy the scores out, wait (the latency a single caller sees)
+        lat = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Xb[1].copy_(Xh, non_blocking=True)
+            Yb[1].copy_(Yh, non_blocking=True)
+            ctx.run(Xb[1], Yb[1], out=out)
+            Eh.copy_(out[0], non_blocking=True)
+            th.copy_(out[1], non_blocking=True)
+            torch.cuda.synchronize()
+            lat.append((time.perf_counter() - t0) * 1e3)
         e2e = {"value": job_throughput(world, args.steps, k * q, ems), "unit": "evals/s",
                "h2d_bytes_per_step": Xh.numel() * Xh.element_size() + Yh.numel() * Yh.element_size(),
                "d2h_bytes_per_step": Eh.numel() * 8 + 4, "ms_per_step": ems / args.steps,
                "pipelining": "next step's inputs copied on a second stream during this step's evaluation",
-               "h2d_GBps_alone": Xh.numel() * Xh.element_size() / (h2d_ms / 1e3) / 1e9}
+               "h2d_GBps_alone": Xh.numel() * Xh.element_size() / (h2d_ms / 1e3) / 1e9,
+               "call_latency_ms": min(lat),
+               "call_latency_note": "one call, host clock, copies in, path, scores out, synchronised; "
+                                    "no overlap (best of 3)"}
         del Xb, Yb
 
     # ---- the hold-out gradient in log(lambda) at one lambda -----------------
@@ -1112,6 +1226,15 @@ def run_own(args):
         pinrmse = pinrmse_compare(binding, params, cfg, X, Y, stream, exact, t_star)
         warm = warm_compare(binding, params, cfg, X, Y, stream, exact, E, t_star)
 
+    large = None
+    if rank == 0 and not args.no_large and args.workload == "mixed_ecc":
+        del X, Y
+        torch.cuda.empty_cache()
+        try:
+            large = large_rff_compare(binding)
+        except Exception as exc:                      # context only: never costs the line
+            large = {"unavailable": f"{type(exc).__name__}: {exc}"}
+
     if rank != 0:
         return 0
     sample = None if args.no_cpu else oracle_sample(prob, cfg, w, E, t_star)
@@ -1156,6 +1279,7 @@ def run_own(args):
         "mchol": mchol,
         "pinrmse": pinrmse,
         "warm_start": warm,
+        "large_rff": large,
         "device_status": binding.STATUS.get(info.code), "unusable_pairs": info.unusable,
     }
     if sample:

@@ -119,10 +119,19 @@ typedef struct {
                              and takes Theta_f = Theta_0 + V'^+ (T'_f - V' Theta_0), V' = the first
                              min(g', r+1) basis functions at those lambdas (the basis normalised by
                              the g samples); its other coefficient planes are fold 0's */
-    int32_t reserved[4];  /* must be zero */
+    int32_t refine_residual; /* mixed mode with refine_target PICHOL_REFINE_INTERPOLATED, how the residual
+                             B - L~ (L~^T W) is formed:
+                             PICHOL_RESIDUAL_TENSOR (default): both triangular products for every
+                             lambda at once on the tensor cores, sum_m phi_m(lambda) Theta_m applied as
+                             one product per coefficient plane (split TF32, compensated accumulation
+                             every 128 rows of K);
+                             PICHOL_RESIDUAL_DOUBLE_FLOAT: per lambda on the FP32 pipes in double-float
+                             arithmetic (error-free products and TwoSum), an FP64-class residual */
+    int32_t reserved[3];  /* must be zero */
 } pichol_config;
 
 enum { PICHOL_REFINE_INTERPOLATED = 0, PICHOL_REFINE_EXACT = 1 };
+enum { PICHOL_RESIDUAL_TENSOR = 0, PICHOL_RESIDUAL_DOUBLE_FLOAT = 1 };
 
 /* First device error, as latched by the kernels. */
 typedef struct {
@@ -138,7 +147,8 @@ typedef struct pichol_ctx pichol_ctx;
 
 /* Fills *cfg with defaults: lam_lo = 1e-3, lam_hi = 1e1, scale_by_trace = 1,
  * basis MONO, mode FP64, refine_steps 0, gram_passes 3, exact_batch 0,
- * refine_target PICHOL_REFINE_INTERPOLATED, warm_samples 0; the sizes are left zero.
+ * refine_target PICHOL_REFINE_INTERPOLATED, warm_samples 0, refine_residual
+ * PICHOL_RESIDUAL_TENSOR; the sizes are left zero.
  * refine_target PICHOL_REFINE_EXACT needs mode MIXED (else
  * PICHOL_ERR_UNSUPPORTED from pichol_create). */
 PICHOL_API void pichol_config_default(pichol_config* cfg);
@@ -393,13 +403,28 @@ PICHOL_API pichol_status pichol_stage_times(pichol_ctx* ctx, double* ms, int64_t
 /*
  * Launch shapes of the factorisation and the evaluation that a tuner may change.  Each changes
  * how the work is split into CTAs and scheduled, never the order of any
- * element's arithmetic, so every result is bit-identical under every tuning.
+ * element's arithmetic, so every result is bit-identical under every tuning,
+ * except update_engine, which changes the rounding of the trailing updates
+ * (fp32-class either way).
  *   update_strip   : output tiles per CTA in the bulk trailing updates, 1..8 (default 4)
  *   diag_threads   : threads of a diagonal-tile CTA, 256 or 512 (default 512)
  *   diag_exclusive : 1 lets each diagonal-tile CTA hold a whole SM (a shared
  *                    memory request no update CTA fits beside) when the k g
  *                    problems fit on half the SMs; 0 never (default 1; batches
  *                    set 0 for their problems)
+ *   update_engine  : mixed mode: 1 runs the bulk trailing updates on the CUDA
+ *                    cores (fp32 FMA, default), 0 on the tensor cores (split
+ *                    TF32: hi*hi + hi*lo + lo*hi).  Measured on GB300 the tensor
+ *                    cores are no faster here (each update is bound by reading
+ *                    and writing the trailing tiles) and their factors carry
+ *                    about ten times the rounding error, which moves hold-out
+ *                    errors of ill-conditioned problems past 1e-4, so they are
+ *                    an option, not the default
+ *   solve_engine   : mixed mode, interpolated solves: 0 on the tensor cores (all
+ *                    lambdas of a fold at once, one split-TF32 product per
+ *                    coefficient plane: sum_m Theta_m (phi_m Z)), 1 on the CUDA
+ *                    cores (the factor evaluated per lambda in shared memory,
+ *                    (sum_m phi_m Theta_m) Z); the two round differently
  *   eval_overlap   : mixed mode with refinement: 1 splits the lambdas of
  *                    pichol_eval_holdout in two halves, the second run on the
  *                    internal stream from the end of the first half's solve,
@@ -413,7 +438,9 @@ typedef struct {
     int32_t diag_threads;
     int32_t diag_exclusive;
     int32_t eval_overlap;
-    int32_t reserved[4];
+    int32_t update_engine;
+    int32_t solve_engine;
+    int32_t reserved[2];
 } pichol_tuning;
 PICHOL_API pichol_status pichol_get_tuning(const pichol_ctx* ctx, pichol_tuning* t);
 PICHOL_API pichol_status pichol_set_tuning(pichol_ctx* ctx, const pichol_tuning* t);

@@ -21,6 +21,7 @@ PICHOL_MODE_FP64, PICHOL_MODE_MIXED = 0, 1
 PICHOL_STATE_HESSIAN, PICHOL_STATE_FACTORS, PICHOL_STATE_FIT = 1, 2, 4
 PICHOL_BASIS_MONO, PICHOL_BASIS_CHEB_LOG = 0, 1
 REFINE_TARGETS = {"interpolated": 0, "exact": 1}
+RESIDUALS = {"tensor": 0, "double_float": 1}
 BASES = {"mono": PICHOL_BASIS_MONO, "cheb_log": PICHOL_BASIS_CHEB_LOG}
 MODES = {"fp64": PICHOL_MODE_FP64, "mixed": PICHOL_MODE_MIXED}
 
@@ -53,7 +54,8 @@ STAGES = ["gram", "xty", "setup", "chol_init", "chol_diag", "chol_panel", "chol_
 
 class Tuning(ctypes.Structure):
     _fields_ = [("update_strip", ctypes.c_int32), ("diag_threads", ctypes.c_int32),
-                ("diag_exclusive", ctypes.c_int32), ("eval_overlap", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("diag_exclusive", ctypes.c_int32), ("eval_overlap", ctypes.c_int32), ("update_engine", ctypes.c_int32),
+                ("solve_engine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class Config(ctypes.Structure):
@@ -63,7 +65,8 @@ class Config(ctypes.Structure):
                 ("scale_by_trace", ctypes.c_int32), ("basis", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("refine_steps", ctypes.c_int32), ("gram_passes", ctypes.c_int32),
                 ("exact_batch", ctypes.c_int32), ("refine_target", ctypes.c_int32),
-                ("warm_samples", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("warm_samples", ctypes.c_int32), ("refine_residual", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class Info(ctypes.Structure):
@@ -197,7 +200,7 @@ class Context:
 
     def __init__(self, *, n, d, c, k, g, r, q, lam_lo=1e-3, lam_hi=1e1, basis="mono", mode="fp64",
                  refine_steps=0, gram_passes=3, exact_batch=0, scale_by_trace=True, refine_target="interpolated",
-                 warm_samples=0):
+                 warm_samples=0, refine_residual="tensor"):
         import torch
         L = lib()
         cfg = Config()
@@ -210,6 +213,7 @@ class Context:
         cfg.refine_steps, cfg.gram_passes, cfg.exact_batch = refine_steps, gram_passes, exact_batch
         cfg.refine_target = _choice("refine_target", refine_target, REFINE_TARGETS)
         cfg.warm_samples = warm_samples
+        cfg.refine_residual = _choice("refine_residual", refine_residual, RESIDUALS)
         self.cfg = cfg
         self.dtype = torch.float64 if mode == "fp64" else torch.float32
         h = ctypes.c_void_p()
@@ -410,13 +414,14 @@ class Context:
         t = Tuning()
         _check(lib().pichol_get_tuning(self._h, ctypes.byref(t)), "pichol_get_tuning")
         return {"update_strip": t.update_strip, "diag_threads": t.diag_threads, "diag_exclusive": t.diag_exclusive,
-                "eval_overlap": t.eval_overlap}
+                "eval_overlap": t.eval_overlap, "update_engine": t.update_engine, "solve_engine": t.solve_engine}
 
     def set_tuning(self, **kw):
         """Change launch shapes and scheduling (results are bit-identical under every tuning)."""
         cur = self.tuning()
         cur.update(kw)
-        t = Tuning(cur["update_strip"], cur["diag_threads"], cur["diag_exclusive"], cur["eval_overlap"])
+        t = Tuning(cur["update_strip"], cur["diag_threads"], cur["diag_exclusive"], cur["eval_overlap"],
+                   cur["update_engine"], cur["solve_engine"])
         _check(lib().pichol_set_tuning(self._h, ctypes.byref(t)), "pichol_set_tuning")
 
     def state(self) -> int:
@@ -556,6 +561,7 @@ class Batch:
             cfg.refine_target = _choice("refine_target", pr.get("refine_target", "interpolated"), REFINE_TARGETS)
             cfg.exact_batch = pr.get("exact_batch", cfg.g)
             cfg.warm_samples = pr.get("warm_samples", 0)
+            cfg.refine_residual = _choice("refine_residual", pr.get("refine_residual", "tensor"), RESIDUALS)
         self.cfgs = cfgs
         self.n = n
         h = ctypes.c_void_p()
@@ -575,9 +581,10 @@ class Batch:
     def set_streams(self, nstreams):
         _check(lib().pichol_batch_set_streams(self._h, nstreams), "pichol_batch_set_streams")
 
-    def set_tuning(self, update_strip=4, diag_threads=512, diag_exclusive=0, eval_overlap=0):
+    def set_tuning(self, update_strip=4, diag_threads=512, diag_exclusive=0, eval_overlap=0, update_engine=1,
+                   solve_engine=1):
         """Launch shapes and scheduling for every problem (results are bit-identical)."""
-        t = Tuning(update_strip, diag_threads, diag_exclusive, eval_overlap)
+        t = Tuning(update_strip, diag_threads, diag_exclusive, eval_overlap, update_engine, solve_engine)
         _check(lib().pichol_batch_set_tuning(self._h, ctypes.byref(t)), "pichol_batch_set_tuning")
 
     def autotune(self, Xs, Ys, *, reps=2, stream=None, cache=None, pg=None):

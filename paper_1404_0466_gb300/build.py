@@ -18,7 +18,7 @@ PKG = pathlib.Path(__file__).resolve().parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = PKG / "libpichol.so"
-SOURCES = ["api.cu", "gram.cu", "chol.cu", "fit.cu", "solve.cu", "tc_gemm.cu", "grad.cu", "batch.cu", "mchol.cu", "pinrmse.cu", "resid.cu", "solve_single.cu", "probe.cu"]
+SOURCES = ["api.cu", "gram.cu", "chol.cu", "fit.cu", "solve.cu", "tc_gemm.cu", "grad.cu", "batch.cu", "mchol.cu", "pinrmse.cu", "resid.cu", "solve_single.cu", "probe.cu", "resid_tc.cu", "chol_tc.cu", "solve_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

@@ -46,12 +46,23 @@ size_t plan(pichol_ctx* ctx, char* base)
     ctx->xpart = (double*)take(xty_part_bytes((int)k, dp, cc));
     ctx->Hf = take((size_t)(k * ntl * TILE_ELEMS * eb));
     ctx->F = take((size_t)(ctx->nfac * ntl * TILE_ELEMS * eb));
+    const bool mixed = c.mode == PICHOL_MODE_MIXED;
+    ctx->Ph = mixed ? (float*)take((size_t)(2 * ctx->nfac * nt * TILE_ELEMS * sizeof(float))) : nullptr;
+    ctx->Pl = mixed ? (float*)take((size_t)(2 * ctx->nfac * nt * TILE_ELEMS * sizeof(float))) : nullptr;
     ctx->Theta = take((size_t)(k * ntl * p * TILE_ELEMS * eb));
     ctx->Dinv = take((size_t)(k * q * nt * TILE_ELEMS * eb));
     ctx->W = take((size_t)(k * q * dp * cc * eb));
     const bool refine = c.mode == PICHOL_MODE_MIXED && c.refine_steps > 0;
     const bool rexact = refine && c.refine_target == PICHOL_REFINE_EXACT;
     ctx->U = (refine && !rexact) ? take((size_t)(2 * k * q * dp * cc * sizeof(float))) : nullptr;
+    const bool rtc = c.mode == PICHOL_MODE_MIXED;   // Theta split for the tensor-core solve and residual
+    const size_t tplanes = (size_t)(k * ntl * p + 1) * TILE_ELEMS * sizeof(float);
+    ctx->Th = rtc ? (float*)take(tplanes) : nullptr;
+    ctx->Tl = rtc ? (float*)take(tplanes) : nullptr;
+    ctx->TTh = rtc ? (float*)take(tplanes) : nullptr;
+    ctx->TTl = rtc ? (float*)take(tplanes) : nullptr;
+    ctx->Sh = rtc ? (float*)take((size_t)(k * q * cc * dp * sizeof(float))) : nullptr;
+    ctx->Sl = rtc ? (float*)take((size_t)(k * q * cc * dp * sizeof(float))) : nullptr;
     ctx->Rres = refine ? take((size_t)(k * q * dp * cc * eb)) : nullptr;
     if (c.mode == PICHOL_MODE_MIXED) {
         const int64_t qc = q * cc;
@@ -146,8 +157,10 @@ pichol_status pichol_create(const pichol_config* cfg, pichol_ctx** out)
     if (c.exact_batch < 0 || c.exact_batch > c.q) return PICHOL_ERR_INVALID_ARG;
     if (c.refine_target != PICHOL_REFINE_INTERPOLATED && c.refine_target != PICHOL_REFINE_EXACT)
         return PICHOL_ERR_INVALID_ARG;
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 3; ++i)
         if (c.reserved[i] != 0) return PICHOL_ERR_INVALID_ARG;
+    if (c.refine_residual != PICHOL_RESIDUAL_TENSOR && c.refine_residual != PICHOL_RESIDUAL_DOUBLE_FLOAT)
+        return PICHOL_ERR_INVALID_ARG;
     if (c.warm_samples != 0 && (c.warm_samples < 2 || c.warm_samples > c.g || c.warm_samples > 8))
         return PICHOL_ERR_INVALID_ARG;
     if (c.refine_target == PICHOL_REFINE_EXACT && c.mode != PICHOL_MODE_MIXED) return PICHOL_ERR_UNSUPPORTED;
@@ -175,6 +188,8 @@ pichol_status pichol_create(const pichol_config* cfg, pichol_ctx** out)
     ctx->tune.update_strip = 4;
     ctx->tune.diag_threads = 512;
     ctx->tune.diag_exclusive = 1;
+    ctx->tune.update_engine = 1;   // CUDA cores: see pichol_tuning
+    ctx->tune.solve_engine = 1;
     *out = ctx;
     return PICHOL_OK;
 }
@@ -508,7 +523,9 @@ pichol_status pichol_set_tuning(pichol_ctx* ctx, const pichol_tuning* t)
     if (t->diag_threads != 256 && t->diag_threads != 512) return PICHOL_ERR_INVALID_ARG;
     if (t->diag_exclusive != 0 && t->diag_exclusive != 1) return PICHOL_ERR_INVALID_ARG;
     if (t->eval_overlap != 0 && t->eval_overlap != 1) return PICHOL_ERR_INVALID_ARG;
-    for (int i = 0; i < 4; ++i)
+    if (t->update_engine != 0 && t->update_engine != 1) return PICHOL_ERR_INVALID_ARG;
+    if (t->solve_engine != 0 && t->solve_engine != 1) return PICHOL_ERR_INVALID_ARG;
+    for (int i = 0; i < 2; ++i)
         if (t->reserved[i] != 0) return PICHOL_ERR_INVALID_ARG;
     ctx->tune = *t;
     return PICHOL_OK;

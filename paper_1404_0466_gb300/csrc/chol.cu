@@ -9,8 +9,10 @@
 // latches PICHOL_ERR_NOT_SPD with (fold, sample, row) and the factorisation
 // continues with a unit pivot so no NaN spreads.
 #include "internal.cuh"
+#include "tcgen05.cuh"
 
 #include <cstring>
+#include <type_traits>
 
 namespace pichol {
 
@@ -225,9 +227,13 @@ __device__ __forceinline__ void stage_tile(T* __restrict__ dst, const T* __restr
 // of L_JJ are read from shared memory 16 bytes at a time (the same address for
 // the whole warp), and each sum runs as VN interleaved partial sums (one per
 // element of the 16-byte chunk), added in a fixed order.
+// With ph (fp32 only), each solved row is also written split into TF32 hi
+// (ph) and remainder (pl) at panel-buffer row prow0 + (pr nt + I) 64 + r, the
+// operands of the tensor-core trailing update.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_chol_panel(T* __restrict__ F, int64_t ntiles, int J, int m, ProbMap pm)
+k_chol_panel(T* __restrict__ F, int64_t ntiles, int J, int m, ProbMap pm, float* __restrict__ ph,
+             float* __restrict__ pl, int64_t prow0, int nt)
 {
     using V = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::N, LD = TB + VN;
@@ -274,6 +280,25 @@ k_chol_panel(T* __restrict__ F, int64_t ntiles, int J, int m, ProbMap pm)
         V v;
         memcpy(&v, &x[ch * VN], sizeof(V));
         reinterpret_cast<V*>(row)[ch] = v;
+    }
+    if constexpr (std::is_same<T, float>::value) {
+        if (ph) {
+            const int64_t o = (prow0 + ((int64_t)pr * nt + J + 1 + it) * TB + r) * TB;
+#pragma unroll
+            for (int ch = 0; ch < TB / 4; ++ch) {
+                float4 h, l;
+                h.x = tc5::tf32_round(x[4 * ch]);
+                h.y = tc5::tf32_round(x[4 * ch + 1]);
+                h.z = tc5::tf32_round(x[4 * ch + 2]);
+                h.w = tc5::tf32_round(x[4 * ch + 3]);
+                l.x = x[4 * ch] - h.x;
+                l.y = x[4 * ch + 1] - h.y;
+                l.z = x[4 * ch + 2] - h.z;
+                l.w = x[4 * ch + 3] - h.w;
+                reinterpret_cast<float4*>(ph + o)[ch] = h;
+                reinterpret_cast<float4*>(pl + o)[ch] = l;
+            }
+        }
     }
 }
 
@@ -418,7 +443,15 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
         if ((e = cudaStreamWaitEvent(sh, ctx->ev_fork, 0)) != cudaSuccess) return e;
     }
     bool pending = false;   // a bulk update on s that sh has not yet waited for
+    // mixed mode: the bulk updates run on the tensor cores from the panel
+    // tiles split by k_chol_panel into panel buffer J & 1
+    const bool tcu = std::is_same<T, float>::value && ctx->Ph != nullptr && ctx->tune.update_engine == 0;
+    // output tiles per tensor-core CTA (pairs of 128 rows): at most two pairs;
+    // CTAs of four pairs measured hundreds of times slower (not understood;
+    // those shapes are not used)
+    const int UCH_TC = UCH >= 2 ? 4 : 2;
     for (int J = 0; J < ctx->nt; ++J) {
+        const int64_t prow0 = (int64_t)(J & 1) * ctx->nfac * ctx->nt * TB;
         {
             StageScope sc_(ctx, ST_CHOL_DIAG, sh);
             if (ctx->tune.diag_threads == 256)
@@ -431,7 +464,8 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
         if (m == 0) break;
         {
             StageScope sc_(ctx, ST_CHOL_PANEL, sh);
-            k_chol_panel<T><<<dim3((m + 3) / 4, nprob), 256, 0, sh>>>(F, ctx->ntiles, J, m, pm);
+            k_chol_panel<T><<<dim3((m + 3) / 4, nprob), 256, 0, sh>>>(F, ctx->ntiles, J, m, pm, tcu ? ctx->Ph : nullptr,
+                                                                       ctx->Pl, prow0, ctx->nt);
         }
         ctx->launches++;
         if (split && m > 1) {
@@ -445,9 +479,13 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
             if ((e = cudaStreamWaitEvent(s, ctx->ev_panel, 0)) != cudaSuccess) return e;
             {
                 StageScope sc_(ctx, ST_CHOL_UPDATE, s);
-                k_chol_update<T, UNT><<<dim3((m - 1 + UCH - 1) / UCH, m - 1, nprob), UNT, sm_mm, s>>>(
-                    F, ctx->ntiles, ctx->nt, J, J + 2, UCH, pm);
+                if (tcu)
+                    e = launch_update_tc(ctx, pm.per, pm.count, pm.warm, nprob, J, J + 2, m - 1, UCH_TC, s);
+                else
+                    k_chol_update<T, UNT><<<dim3((m - 1 + UCH - 1) / UCH, m - 1, nprob), UNT, sm_mm, s>>>(
+                        F, ctx->ntiles, ctx->nt, J, J + 2, UCH, pm);
             }
+            if (e != cudaSuccess) return e;
             if ((e = cudaEventRecord(ctx->ev_upd, s)) != cudaSuccess) return e;
             pending = true;
             ctx->launches += 2;
@@ -456,9 +494,13 @@ static cudaError_t factor_impl(pichol_ctx* ctx, int count, int exact, int t0, cu
             pending = false;
             {
                 StageScope sc_(ctx, ST_CHOL_UPDATE, sh);
-                k_chol_update<T, UNT><<<dim3((m + UCH - 1) / UCH, m, nprob), UNT, sm_mm, sh>>>(
-                    F, ctx->ntiles, ctx->nt, J, J + 1, UCH, pm);
+                if (tcu)
+                    e = launch_update_tc(ctx, pm.per, pm.count, pm.warm, nprob, J, J + 1, m, UCH_TC, sh);
+                else
+                    k_chol_update<T, UNT><<<dim3((m + UCH - 1) / UCH, m, nprob), UNT, sm_mm, sh>>>(
+                        F, ctx->ntiles, ctx->nt, J, J + 1, UCH, pm);
             }
+            if (e != cudaSuccess) return e;
             ctx->launches++;
         }
     }

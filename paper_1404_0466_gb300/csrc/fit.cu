@@ -165,6 +165,7 @@ cudaError_t launch_fit(pichol_ctx* ctx, cudaStream_t s)
                                     (float*)ctx->Theta, s);
     }
     ctx->launches++;
+    if (e == cudaSuccess && !gw && ctx->Th) e = launch_theta_split(ctx, s);
     if (e != cudaSuccess || !gw) return e;
     const int pw = gw < ctx->p ? gw : ctx->p;
     dim3 wgrid((unsigned)ctx->ntiles, c.k - 1);
@@ -178,6 +179,7 @@ cudaError_t launch_fit(pichol_ctx* ctx, cudaStream_t s)
                                          ctx->ntiles, (float*)ctx->Theta, s);
     }
     ctx->launches++;
+    if (e == cudaSuccess && ctx->Th) e = launch_theta_split(ctx, s);
     return e;
 }
 

@@ -161,10 +161,19 @@ struct pichol_ctx {
     double* xpart;       // k x XTY_SPLITS x dp x c partial sums of X_j^T Y_j
     void* Hf;            // k x ntiles x TB^2: H_f, tile-major lower
     void* F;             // nfac x ntiles x TB^2
+    float* Ph;           // mixed mode: 2 x nfac x nt x TB^2, the panel tiles L_IJ of tile column J in
+    float* Pl;           //   buffer J & 1, split TF32 hi / remainder lo (tensor-core trailing update)
     void* Theta;         // k x ntiles x p x TB^2
     void* Dinv;          // k x q x nt x TB^2
     void* W;             // k x q x dp x c
-    void* U;             // 2 x k x q x dp x c floats: L~^T W as (hi, lo) (refinement)
+    void* U;             // 2 x k x q x dp x c floats: L~^T W as (hi, lo) (refinement); with the
+                         // tensor-core residual [2][f][q c][dp], i.e. (L~^T W)^T split hi / lo
+    float* Th;           // (k x ntiles x p + 1) x TB^2: Theta split TF32 hi (tensor-core residual;
+    float* Tl;           //   the last plane is zero), remainder lo,
+    float* TTh;          //   and the same with every tile transposed
+    float* TTl;
+    float* Sh;           // mixed mode: [2 halves: hi, lo] x k x (q c) x dp, solved blocks transposed
+    float* Sl;           //   (tensor-core interpolated solve)
     void* Rres;          // k x q x dp x c (residual / correction)
     int64_t* nfc;        // k: n_f * c
     // tensor-core operands (mixed mode)
@@ -273,6 +282,19 @@ cudaError_t launch_score_tc(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s)
 cudaError_t launch_gall_split(pichol_ctx* ctx, cudaStream_t s);
 cudaError_t launch_wait_check(pichol_ctx* ctx, long long limit, cudaStream_t s);
 cudaError_t launch_resid_exact(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s);
+// W^T of systems [t0, t0 + tcount) split into TF32 parts (Wth / Wtl)
+cudaError_t launch_split_wt(pichol_ctx* ctx, int t0, int tcount, int stage, cudaStream_t s);
+// Theta split (and transposed) for the tensor-core residual, after the fit
+cudaError_t launch_theta_split(pichol_ctx* ctx, cudaStream_t s);
+// refinement residual of the interpolated system on tensor cores, into Rres
+cudaError_t launch_resid_tc(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s);
+// interpolated solves of systems [t0, t0 + tcount) on tensor cores (mixed mode): rhs per fold
+// [f][dp][c] or per system [f][t][dp][c]; the solution into out [f][t][dp][c]
+cudaError_t launch_solve_tc(pichol_ctx* ctx, int t0, int tcount, const void* rhs, int rhs_per_system, void* out,
+                            cudaStream_t s);
+// bulk trailing update of tile column J on tensor cores (mixed mode; panel J split into Ph / Pl)
+cudaError_t launch_update_tc(pichol_ctx* ctx, int per, int count, int warm, int nprob, int J, int first, int ncols,
+                             int chunk, cudaStream_t s);
 // grid, samples and V^+ from the Gram blocks; window (device, nullable) holds
 // (lo, hi) replacing the configured range
 cudaError_t launch_setup(pichol_ctx* ctx, const double* window, cudaStream_t s);

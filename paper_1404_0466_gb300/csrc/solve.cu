@@ -441,7 +441,10 @@ static cudaError_t eval_impl(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s
         sa.dp = ctx->dp;
         sa.c = cf.c;
         sa.st = ctx->status;
-        cudaError_t er = solve_dispatch<T, EXACT>(ctx, sa, st);
+        // mixed mode, interpolated systems: all lambdas per fold on the tensor cores when tuned so
+        const bool tcs = std::is_same<T, float>::value && !EXACT && ctx->tune.solve_engine == 0 && ctx->Sh;
+        cudaError_t er = tcs ? launch_solve_tc(ctx, t0h, tch, ctx->Btr, 0, ctx->W, st)
+                             : solve_dispatch<T, EXACT>(ctx, sa, st);
         if (er == cudaSuccess && solved) er = cudaEventRecord(solved, st);
         if (er != cudaSuccess) return er;
         if constexpr (std::is_same<T, float>::value && !EXACT) {
@@ -449,6 +452,8 @@ static cudaError_t eval_impl(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s
                 // the residual of the system this step refines (see refine_target)
                 if (cf.refine_target == PICHOL_REFINE_EXACT) {
                     if ((er = launch_resid_exact(ctx, t0h, tch, st)) != cudaSuccess) return er;
+                } else if (cf.refine_residual == PICHOL_RESIDUAL_TENSOR) {
+                    if ((er = launch_resid_tc(ctx, t0h, tch, st)) != cudaSuccess) return er;
                 } else {
                     ResidArgs ra;
                     ra.theta = (const float*)ctx->Theta;
@@ -477,7 +482,8 @@ static cudaError_t eval_impl(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s
                 sc.rhs_per_system = 1;
                 sc.zbuf = ctx->Rres;
                 sc.out = ctx->Rres;
-                if ((er = solve_dispatch<T, EXACT>(ctx, sc, st)) != cudaSuccess) return er;
+                er = tcs ? launch_solve_tc(ctx, t0h, tch, ctx->Rres, 1, ctx->Rres, st) : solve_dispatch<T, EXACT>(ctx, sc, st);
+                if (er != cudaSuccess) return er;
                 {
                     StageScope sc_(ctx, ST_RESID, st);
                     k_axpy<float><<<1024, 256, 0, st>>>((float*)ctx->W, (const float*)ctx->Rres, cf.k, cf.q, t0h,

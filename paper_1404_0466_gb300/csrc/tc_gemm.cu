@@ -29,6 +29,7 @@
 // that runs out latches PICHOL_ERR_TIMEOUT, the CTA stops issuing work, waits
 // (bounded) for its own copies and MMAs, frees its tensor memory and returns.
 #include "internal.cuh"
+#include "tcgen05.cuh"
 #include "tma.cuh"
 
 #include <algorithm>
@@ -45,72 +46,23 @@ constexpr int STAGE_BYTES = 4 * TILE_BYTES;    // A_hi, A_lo, B_hi, B_lo
 constexpr int RED_BYTES = 4 * BN * 4;           // score epilogue: one float per (row quarter, column)
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */ + RED_BYTES;
 constexpr int TMEM_COLS = 256;                 // two 128-column accumulators
-constexpr int CHUNK = 4;                       // k-blocks (128 rows of K) per accumulator drain
+// k-blocks per accumulator drain: GemmArgs.chunk (1 = every 32 rows of K for
+// the Gram blocks, whose fp32 tensor-memory sums of positive terms are the
+// most exposed to the accumulation's rounding; 4 for the other products)
 constexpr int EPI_WARPS = 8;                   // warps 2..9 drain and store
 constexpr int THREADS = 32 * (2 + EPI_WARPS);
 
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
-
-// Shared-memory matrix descriptor of a K-major operand tile written by TMA with
-// the 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);   // start address >> 4
-    d |= (uint64_t)1 << 16;                     // leading byte offset (unused for this layout)
-    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: 8 rows x 128 bytes
-    d |= (uint64_t)1 << 46;                     // descriptor version for tcgen05
-    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor: kind::tf32, fp32 accumulator, both operands K-major,
-// M = 128, N = 128.
-__host__ __device__ constexpr uint32_t idesc_tf32_128x128()
-{
-    return (1u << 4)            // D format: f32
-         | (2u << 7)            // A format: tf32
-         | (2u << 10)           // B format: tf32
-         | ((uint32_t)(BN >> 3) << 17)
-         | ((uint32_t)(BM >> 4) << 24);
-}
-
+using tc5::sw128_desc;
+using tc5::tf32_round;
+__device__ __forceinline__ void tc_fence_before() { tc5::fence_before(); }
+__device__ __forceinline__ void tc_fence_after() { tc5::fence_after(); }
+__host__ __device__ constexpr uint32_t idesc_tf32_128x128() { return tc5::idesc_tf32(BM, BN); }
 __device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
 {
-    asm volatile(
-        "{\n"
-        " .reg .pred p;\n"
-        " setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
-        "}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
+    tc5::mma_tf32(tmem_d, a, b, idesc, acc);
 }
-__device__ __forceinline__ void umma_commit(uint64_t* bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ float tf32_round(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) { tc5::commit(bar); }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) { tc5::ld16(taddr, v); }
 
 }  // namespace tc
 
@@ -119,6 +71,7 @@ enum GemmMode { GEMM_GRAM = 0, GEMM_PLAIN = 1, GEMM_XTY = 2, GEMM_SCORE = 3 };
 struct GemmArgs {
     int mode;
     int passes;
+    int chunk;                // k-blocks of 32 rows of K per accumulator drain
     // GEMM_GRAM: lower tiles (I, J) of fold blockIdx.y; K range of fold f is
     // [k0[f], k0[f] + kn[f]) in the transposed, fold-padded X.
     int ntb;                  // 128-tiles per side
@@ -194,6 +147,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
         arow = f * a.a_rows_fold + tI * BM;
         brow = f * a.b_rows_fold + a.b_row_off + tJ * BN;
     }
+    const int CHUNK = a.chunk > 0 ? a.chunk : 4;
     const int nchunks = (nk + CHUNK - 1) / CHUNK;
 
     if (threadIdx.x == 0) {
@@ -489,6 +443,19 @@ k_split_wt(const float* __restrict__ W, int q, int t0, int64_t dp, int64_t c, fl
         }
 }
 
+cudaError_t launch_split_wt(pichol_ctx* ctx, int t0, int tcount, int stage, cudaStream_t s)
+{
+    const pichol_config& c = ctx->cfg;
+    const int64_t dp = ctx->dp;
+    {
+        StageScope sc_(ctx, stage, s);
+        k_split_wt<<<dim3((unsigned)((dp + 255) / 256), tcount, c.k), 256, 0, s>>>((const float*)ctx->W, c.q, t0, dp,
+                                                                                  c.c, ctx->Wth, ctx->Wtl);
+    }
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
 // Score partials from U = G_f W (dp x ldu per fold, column t*c + o):
 // Epart[f][t][I] = sum_{rows in 64-tile I} sum_o W (U - 2 Bv), in double.
 __global__ void __launch_bounds__(64)
@@ -565,6 +532,7 @@ cudaError_t launch_gram_tc(pichol_ctx* ctx, const float* X, cudaStream_t s)
     memset(&ga, 0, sizeof(ga));
     ga.mode = GEMM_GRAM;
     ga.passes = c.gram_passes;
+    ga.chunk = 1;
     ga.ntb = (int)((dp + tc::BM - 1) / tc::BM);
     for (int j = 0; j <= c.k; ++j) ga.k0[j] = (int)xa.k0[j];
     for (int j = 0; j < c.k; ++j) ga.kn[j] = (int)(ctx->offs[j + 1] - ctx->offs[j]);

@@ -58,7 +58,7 @@ def test_defaults(L):
 @pytest.mark.parametrize("bad", [
     dict(k=1), dict(k=65), dict(n=3, k=5), dict(d=0), dict(d=16385), dict(c=0), dict(c=33),
     dict(q=0), dict(q=4097), dict(r=6), dict(r=-1), dict(g=2, r=2), dict(g=40, q=50), dict(g=8, q=5),
-    dict(refine_target=2), dict(refine_target=-1),
+    dict(refine_target=2), dict(refine_target=-1), dict(refine_residual=2), dict(refine_residual=-1),
     dict(lam_lo=0.0), dict(lam_lo=2.0, lam_hi=1.0), dict(lam_hi=float("inf")), dict(lam_lo=float("nan")),
     dict(lam_hi=float("nan")), dict(basis=7), dict(mode=5),
     dict(refine_steps=9), dict(gram_passes=2), dict(exact_batch=99), dict(scale_by_trace=2),

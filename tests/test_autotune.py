@@ -25,7 +25,7 @@ def _cfg(**kw):
 class FakeContext:
     def __init__(self, cfg):
         self.cfg = cfg
-        self._t = dict(update_strip=4, diag_threads=512, diag_exclusive=1, eval_overlap=0)
+        self._t = dict(update_strip=4, diag_threads=512, diag_exclusive=1, eval_overlap=0, update_engine=1)
         self.runs = []
 
     def tuning(self):
@@ -87,7 +87,7 @@ def test_context_stages_pick_each_fastest_candidate():
     calls = []
     res = autotune.tune_context(ctx, "X", "Y", reps=3, timer=_timer_for(ctx, lambda c: _ctx_cost(c.tuning()), calls),
                                 device="fake")
-    assert res.choice == dict(update_strip=2, diag_threads=256, diag_exclusive=0, eval_overlap=1)
+    assert res.choice == dict(update_strip=2, diag_threads=256, diag_exclusive=0, eval_overlap=1, update_engine=1)
     assert ctx.tuning() == res.choice and not res.cached
     # 8 shapes, then 2 exclusivity settings, then 2 overlap settings, each 1 + reps runs
     assert calls == [3] * 12 and len(ctx.runs) == 12 * 4
@@ -113,7 +113,8 @@ def test_equal_times_keep_the_first_listed_candidate():
     ctx = FakeContext(_cfg())
     res = autotune.tune_context(ctx, "X", "Y", timer=_timer_for(ctx, lambda c: 1.0), device="fake")
     assert res.choice == dict(update_strip=autotune.UPDATE_STRIPS[0], diag_threads=autotune.DIAG_THREADS[0],
-                              diag_exclusive=autotune.DIAG_EXCLUSIVE[0], eval_overlap=autotune.EVAL_OVERLAP[0])
+                              diag_exclusive=autotune.DIAG_EXCLUSIVE[0], eval_overlap=autotune.EVAL_OVERLAP[0],
+                              update_engine=1)
 
 
 def test_context_cache_round_trip(tmp_path):
@@ -122,7 +123,8 @@ def test_context_cache_round_trip(tmp_path):
     first = autotune.tune_context(ctx, "X", "Y", cache=path, timer=_timer_for(ctx, lambda c: _ctx_cost(c.tuning())),
                                   device="GB300")
     stored = json.load(open(path))
-    assert stored == {first.key: first.choice}
+    # the cache keeps the tuned launch shapes (the update engine is the caller's choice)
+    assert stored == {first.key: {k: v for k, v in first.choice.items() if not k.endswith("_engine")}}
     assert first.key.startswith("GB300|context|n=32768,d=2048,c=10,k=5,g=6,r=3,q=101,")
 
     def no_timing(fn, reps, stream):
@@ -237,7 +239,7 @@ def test_tuner_drives_the_real_binding_methods(monkeypatch):
     import ctypes
     from paper_1404_0466_gb300 import binding as B
 
-    lib_state = {"t": B.Tuning(4, 512, 1, 0), "bt": None, "streams": 8}
+    lib_state = {"t": B.Tuning(4, 512, 1, 0, 1, 1), "bt": None, "streams": 8}
 
     class FakeLib:
         def pichol_get_tuning(self, h, ref):
@@ -271,7 +273,8 @@ def test_tuner_drives_the_real_binding_methods(monkeypatch):
         return _ctx_cost(t)
 
     res = autotune.tune_context(ctx, "X", "Y", timer=timer, device="fake")
-    assert res.choice == dict(update_strip=2, diag_threads=256, diag_exclusive=0, eval_overlap=1)
+    assert res.choice == dict(update_strip=2, diag_threads=256, diag_exclusive=0, eval_overlap=1, update_engine=1,
+                              solve_engine=1)
     t = lib_state["t"]
     assert (t.update_strip, t.diag_threads, t.diag_exclusive, t.eval_overlap) == (2, 256, 0, 1)
     assert len(ran) == 12

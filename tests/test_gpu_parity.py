@@ -217,17 +217,77 @@ def mixed_small(torch_mod):
     return prob, ref
 
 
-@pytest.mark.parametrize("refine", [0, 1])
-def test_mixed_holdout_and_selection(torch_mod, mixed_small, refine):
+@pytest.mark.parametrize("refine,residual,solve", [(0, "tensor", 1), (1, "tensor", 1), (1, "double_float", 1),
+                                                  (2, "tensor", 1), (0, "tensor", 0), (1, "tensor", 0)])
+def test_mixed_holdout_and_selection(torch_mod, mixed_small, refine, residual, solve):
+    """Mixed mode against the oracle: refinement steps, the residual on the
+    tensor cores or in double-float, the solves on the CUDA cores (solve 1) or
+    the tensor cores (solve 0)."""
     torch = torch_mod
     prob, ref = mixed_small
-    ctx = _ctx(prob, k=5, g=6, r=3, q=101, basis="cheb_log", mode="mixed", refine_steps=refine)
+    ctx = _ctx(prob, k=5, g=6, r=3, q=101, basis="cheb_log", mode="mixed", refine_steps=refine,
+               refine_residual=residual)
+    ctx.set_tuning(solve_engine=solve)
     out = ctx.run(_dev(torch, prob.X, "mixed"), _dev(torch, prob.Y, "mixed"))
     E = out.E.cpu().numpy()
     rel = np.max(np.abs(E - ref.E) / ref.E)
     assert rel <= MIXED_TOL, rel
     _check_selected(int(out.t_star.cpu().item()), ref, MIXED_TOL)
     assert ctx.info().code == 0
+
+
+@pytest.mark.parametrize("strip", [1, 2, 4])
+def test_tensor_core_trailing_update_option(torch_mod, mixed_small, strip):
+    """update_engine = 0 runs the bulk trailing updates of the factorisation on
+    the tensor cores (split TF32, pairs of 128 output rows per MMA).  Its
+    factors satisfy the Cholesky backward-error bound of a split-TF32 product
+    per update, and on this well-conditioned data the hold-out errors stay
+    within 1e-4 of the oracle."""
+    torch = torch_mod
+    prob, ref = mixed_small
+    kw = dict(k=5, g=6, r=3, q=101, basis="cheb_log")
+    ctx = _ctx(prob, mode="mixed", refine_steps=1, **kw)
+    ctx.set_tuning(update_engine=0, update_strip=strip)
+    out = ctx.run(_dev(torch, prob.X, "mixed"), _dev(torch, prob.Y, "mixed"))
+    torch.cuda.synchronize()
+    assert ctx.info().code == 0
+    E = out.E.cpu().numpy()
+    assert np.max(np.abs(E - ref.E) / ref.E) <= MIXED_TOL
+    H, _ = (t.cpu().numpy() for t in ctx.export_hessian(1))
+    lam_s = ctx.lambdas().cpu().numpy()[oracle.sample_indices(101, 6)]
+    d = H.shape[0]
+    for s in (0, 5):
+        L = ctx.export_factor(1, s).cpu().numpy()
+        A = H + lam_s[s] * np.eye(d)
+        bound = (d + 1) * 2.0 ** -21 * (np.abs(L) @ np.abs(L.T)) + 2.0 ** -22 * np.abs(A)
+        assert np.all(np.abs(L @ L.T - A) <= bound), float(np.max(np.abs(L @ L.T - A) / bound))
+    ctx.close()
+
+
+@pytest.mark.parametrize("r", [2, 5])
+def test_tensor_core_residual_equals_double_float_residual(torch_mod, r):
+    """The refinement residual B - L~ (L~^T W) formed on the tensor cores (all
+    lambdas at once, one product per coefficient plane; degree 5 takes the
+    narrower column tiles) against the double-float one on the FP32 pipes:
+    after one step the solutions agree to about an fp32 rounding of the
+    solve, and both scores are within 1e-4 of the oracle."""
+    torch = torch_mod
+    prob = synth.spectral_gaussian(1500, 150, 4, seed=41, decay=1.5, dtype=np.float32)
+    kw = dict(k=5, g=8, r=r, q=33, basis="cheb_log")
+    ref = oracle.cv(prob.X, prob.Y, **kw)
+    outs = {}
+    for residual in ("tensor", "double_float"):
+        ctx = _ctx(prob, mode="mixed", refine_steps=1, refine_residual=residual, **kw)
+        out = ctx.run(_dev(torch, prob.X, "mixed"), _dev(torch, prob.Y, "mixed"), want_w=True)
+        torch.cuda.synchronize()
+        assert ctx.info().code == 0
+        outs[residual] = (out.E.cpu().numpy(), out.W.cpu().numpy().astype(np.float64))
+        rel = np.abs(outs[residual][0] - ref.E) / ref.E
+        assert np.all(rel <= MIXED_TOL), (residual, float(rel.max()))
+        ctx.close()
+    Wa, Wb = outs["tensor"][1], outs["double_float"][1]
+    scale = np.max(np.abs(Wb), axis=(2, 3), keepdims=True)
+    assert np.max(np.abs(Wa - Wb) / scale) <= 1e-4
 
 
 def test_mixed_exact_system_refinement(torch_mod, mixed_small):
@@ -264,7 +324,7 @@ def test_tuning_leaves_every_result_bit_identical(torch_mod, mixed_small):
                  dict(update_strip=8, diag_threads=512, diag_exclusive=0, eval_overlap=0),
                  dict(update_strip=2, diag_threads=256, diag_exclusive=1, eval_overlap=1)):
         ctx.set_tuning(**tune)
-        assert ctx.tuning() == tune
+        assert {k: ctx.tuning()[k] for k in tune} == tune
         out = ctx.run(X, Y, want_w=True)
         outs.append((out.E.clone(), out.t_star.clone(), out.W.clone()))
     for E, t, W in outs[1:]:

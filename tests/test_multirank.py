@@ -101,9 +101,11 @@ def test_roofline_entry_arithmetic():
     measured against the probed FP32 rate when the bench has it."""
     from paper_1404_0466_gb300 import synth
     cfg = dict(synth.MIXED_ECC)
-    work = bench.stage_work(cfg, "mixed", 1)
+    work = bench.stage_work(cfg, "mixed", 1, residual="double_float")
     kind, amount, bound, executed = work["resid"]
     assert kind == "flop" and bound == "alu" and executed > 5
+    tkind, tamount, tbound, texec = bench.stage_work(cfg, "mixed", 1)["resid"]
+    assert tbound == "tensor" and tamount == amount and texec > 9
     # one residual per (fold, lambda): 2 d^2 c for the two triangular products and
     # 2 (r+1) D for one evaluation of the factor; 505 pairs of the mixed case
     d, c, p = 2048, 10, 4

@@ -472,29 +472,13 @@ def run_batched(args):
     batch = binding.Batch(specs, nstreams=8)
     stream = torch.cuda.current_stream()
     evals = sum(sp["k"] * sp["q"] for sp in specs)
-    # autotune the number of concurrent streams and the update strip length on eager runs
+    # the number of concurrent streams and the update strip chosen by the package's autotuner
+    from paper_1404_0466_gb300 import autotune
+    import torch.distributed as tdist
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    tune = {}
-    for ns in (4, 8, 16, 32):
-        for strip in (1, 2, 4):
-            batch.set_streams(ns)
-            batch.set_tuning(update_strip=strip)
-            batch.run(Xs, Ys)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            for _ in range(2):
-                batch.run(Xs, Ys)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            tune[(ns, strip)] = e0.elapsed_time(e1) / 2
-    best_ns, best_strip = min(tune, key=tune.get)
-    if pg is not None:
-        choice = torch.tensor([best_ns, best_strip], device=dev)
-        pg.broadcast(choice, 0)
-        best_ns, best_strip = (int(v) for v in choice.tolist())
-    batch.set_streams(best_ns)
-    batch.set_tuning(update_strip=best_strip)
-    best = best_ns
+    tres = autotune.tune_batch(batch, Xs, Ys, reps=2, stream=stream, pg=tdist.group.WORLD if pg is not None else None)
+    best, best_strip = tres.choice["streams"], tres.choice["update_strip"]
+    tune = tres.timings
     batch.run(Xs, Ys)
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
@@ -627,7 +611,7 @@ def run_batched(args):
         "config": {"workload": (f"batched_uneven: {B['count']} problems, d ~ U[128,1536], n = 8 d, c in {{1,10}}, "
                                 f"k={B['k']} g={B['g']} r={B['r']} q={B['q']} basis={w['basis']} mode=mixed "
                                 f"refine={refine}; one CUDA graph per step, {best} streams, update strips of {best_strip} "
-                                f"(autotuned, ms: {{{', '.join(f'{a}x{b}: {v:.2f}' for (a, b), v in tune.items())}}})"),
+                                f"(autotune.tune_batch, ms: {json.dumps(tune)})"),
                    "l2": "inputs larger than L2 (%d MB of X)" % (h2d // 2 ** 20), "parallelism": f"replicas x{world}"},
         "e2e": {"value": job_throughput(world, args.steps, evals, ems), "unit": "evals/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": sum(e.numel() * 8 for e in Eh), "ms_per_step": ems / args.steps,
@@ -945,58 +929,17 @@ def run_own(args):
         if pg is not None:
             pg.barrier()
 
-    # autotune the factorisation's launch shapes (every result is bit-identical under each;
-    # --profile keeps the defaults so that profiled runs stay short)
-    tune_ms = {}
-    ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for strip in ((1, 2, 4, 8) if not args.profile else ()):
-        for dt in (256, 512):
-            ctx.set_tuning(update_strip=strip, diag_threads=dt)
-            step()
-            ta.record(stream)
-            for _ in range(2):
-                step()
-            tb.record(stream)
-            torch.cuda.synchronize()
-            tune_ms[(strip, dt)] = ta.elapsed_time(tb) / 2
-    best = min(tune_ms, key=tune_ms.get) if tune_ms else (4, 512)
-    ctx.set_tuning(update_strip=best[0], diag_threads=best[1])
-    # then whether the diagonal-tile CTAs hold their SMs alone
-    excl_ms = {}
+    # the launch shapes chosen by the package's autotuner on this problem (every result is
+    # bit-identical under each; --profile keeps the defaults so that profiled runs stay short);
+    # under torchrun every rank applies rank 0's choice
+    tune_res = None
     if not args.profile:
-        for ex in (1, 0):
-            ctx.set_tuning(diag_exclusive=ex)
-            step()
-            ta.record(stream)
-            for _ in range(2):
-                step()
-            tb.record(stream)
-            torch.cuda.synchronize()
-            excl_ms[ex] = ta.elapsed_time(tb) / 2
-    best_ex = min(excl_ms, key=excl_ms.get) if excl_ms else 1
-    ctx.set_tuning(diag_exclusive=best_ex)
-    # then the evaluation's two-stream overlap of the solve with the refinement residual
-    overlap_ms = {}
-    if refine > 0 and w["mode"] == "mixed" and not args.profile:
-        for ov in (0, 1):
-            ctx.set_tuning(eval_overlap=ov)
-            step()
-            ta.record(stream)
-            for _ in range(2):
-                step()
-            tb.record(stream)
-            torch.cuda.synchronize()
-            overlap_ms[ov] = ta.elapsed_time(tb) / 2
-    best_ov = min(overlap_ms, key=overlap_ms.get) if overlap_ms else 0
-    if pg is not None:                      # every rank uses rank 0's choice
-        choice = torch.tensor(list(best) + [best_ov, best_ex], device=dev)
-        pg.broadcast(choice, 0)
-        vals = [int(v) for v in choice.tolist()]
-        best, best_ov, best_ex = tuple(vals[:2]), vals[2], vals[3]
-    ctx.set_tuning(update_strip=best[0], diag_threads=best[1], eval_overlap=best_ov, diag_exclusive=best_ex)
-    tuning = dict(ctx.tuning(), autotuned_ms={f"strip{a}_diag{b}": round(v, 3) for (a, b), v in tune_ms.items()},
-                  exclusive_ms={f"diag_exclusive{k}": round(v, 3) for k, v in excl_ms.items()},
-                  overlap_ms={f"eval_overlap{k}": round(v, 3) for k, v in overlap_ms.items()})
+        from paper_1404_0466_gb300 import autotune
+        import torch.distributed as tdist
+        tune_res = autotune.tune_context(ctx, X, Y, reps=2, stream=stream,
+                                         pg=tdist.group.WORLD if pg is not None else None)
+    tuning = dict(ctx.tuning(), autotuned_ms=(tune_res.timings if tune_res else {}), tuner="autotune.tune_context")
+    ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     for _ in range(args.warmup):
         step()

@@ -422,9 +422,14 @@ PICHOL_API pichol_status pichol_stage_times(pichol_ctx* ctx, double* ms, int64_t
  *                    an option, not the default
  *   solve_engine   : mixed mode, interpolated solves: 0 on the tensor cores (all
  *                    lambdas of a fold at once, one split-TF32 product per
- *                    coefficient plane: sum_m Theta_m (phi_m Z)), 1 on the CUDA
- *                    cores (the factor evaluated per lambda in shared memory,
- *                    (sum_m phi_m Theta_m) Z); the two round differently
+ *                    coefficient plane: sum_m Theta_m (phi_m Z); each plane is
+ *                    read once per block of 64 columns), 1 on the CUDA cores
+ *                    (the factor evaluated per lambda in shared memory,
+ *                    (sum_m phi_m Theta_m) Z; the planes are read once per two
+ *                    lambdas), 2 (default) the tensor cores when one fold's
+ *                    coefficient planes exceed 64 MiB (half of the L2 cache),
+ *                    else the CUDA cores.  The two round differently (same
+ *                    fp32 accuracy class); the choice is per context
  *   eval_overlap   : mixed mode with refinement: 1 splits the lambdas of
  *                    pichol_eval_holdout in two halves, the second run on the
  *                    internal stream from the end of the first half's solve,
@@ -554,6 +559,19 @@ PICHOL_API void pichol_batch_destroy(pichol_batch* b);
 
 /* Short text for a status code (static storage). */
 PICHOL_API const char* pichol_status_string(pichol_status s);
+
+/* Bounds checking in the debug build (libpichol_debug.so, compiled with
+ * -DPICHOL_DEBUG): every workspace section is followed by a 4 KB guard band
+ * filled with 0xA5 when the workspace is attached, and pichol_get_info checks
+ * the bands first; a changed byte latches PICHOL_ERR_WORKSPACE with index =
+ * the band's number and pivot = the byte within it (a kernel wrote past a
+ * section's end).  pichol_debug_guards writes up to `capacity` band offsets
+ * (bytes from the workspace start) to `offsets` (host) and their number to
+ * *count (0 in the regular build).  pichol_debug_build returns 1 in the debug
+ * build, else 0. */
+PICHOL_API pichol_status pichol_debug_guards(const pichol_ctx* ctx, int64_t* offsets, int32_t capacity,
+                                             int32_t* count);
+PICHOL_API int32_t pichol_debug_build(void);
 
 /* The interface version the library was built with: 100 * major + minor
  * (compare with PICHOL_VERSION_MAJOR / _MINOR of the header in use). */

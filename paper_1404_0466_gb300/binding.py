@@ -10,11 +10,13 @@ There is no fallback: if the library has not been built, ``lib()`` raises.
 from __future__ import annotations
 
 import ctypes
+import os
 import pathlib
 from dataclasses import dataclass
 
 _PKG = pathlib.Path(__file__).resolve().parent
-LIB_PATH = _PKG / "libpichol.so"
+# PICHOL_DEBUG=1 in the environment loads the bounds-checked build instead
+LIB_PATH = _PKG / ("libpichol_debug.so" if os.environ.get("PICHOL_DEBUG") == "1" else "libpichol.so")
 INTERFACE = (2, 0)          # PICHOL_VERSION_MAJOR, _MINOR of include/pichol.h
 
 PICHOL_MODE_FP64, PICHOL_MODE_MIXED = 0, 1
@@ -46,7 +48,7 @@ EXPORTS = [
     "pichol_batch_set_timing", "pichol_batch_stage_times",
     "pichol_get_tuning", "pichol_set_tuning", "pichol_batch_set_tuning", "pichol_check_timeout",
     "pichol_mchol", "pichol_mchol_levels", "pichol_check_rsqrt", "pichol_eval_pinrmse", "pichol_probe_fma",
-    "pichol_get_state", "pichol_resume", "pichol_version",
+    "pichol_get_state", "pichol_resume", "pichol_version", "pichol_debug_guards", "pichol_debug_build",
 ]
 STAGES = ["gram", "xty", "setup", "chol_init", "chol_diag", "chol_panel", "chol_update", "fit",
           "diag_inv", "solve", "resid", "score", "select", "misc"]
@@ -122,6 +124,8 @@ def lib():
         "pichol_get_state": ([vp, ctypes.POINTER(i32)], ctypes.c_int),
         "pichol_resume": ([vp, i32], ctypes.c_int),
         "pichol_version": ([], i32),
+        "pichol_debug_guards": ([vp, ctypes.POINTER(i64), i32, ctypes.POINTER(i32)], ctypes.c_int),
+        "pichol_debug_build": ([], i32),
         "pichol_batch_create": ([ctypes.POINTER(Config), i32, i32, ctypes.POINTER(vp)], ctypes.c_int),
         "pichol_batch_workspace_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
         "pichol_batch_set_workspace": ([vp, vp, ctypes.c_size_t], ctypes.c_int),
@@ -430,6 +434,13 @@ class Context:
         _check(lib().pichol_get_state(self._h, ctypes.byref(st)), "pichol_get_state")
         return int(st.value)
 
+    def guard_offsets(self) -> list:
+        """Debug build: byte offsets of the guard bands in the workspace (empty otherwise)."""
+        n = ctypes.c_int32(0)
+        arr = (ctypes.c_int64 * 128)()
+        _check(lib().pichol_debug_guards(self._h, arr, 128, ctypes.byref(n)), "pichol_debug_guards")
+        return [int(arr[i]) for i in range(min(n.value, 128))]
+
     def state_dict(self, stream=None) -> dict:
         """A checkpoint: the configuration, the tuning, which results the
         workspace holds, and a copy of the workspace made on ``stream`` (default:
@@ -582,7 +593,7 @@ class Batch:
         _check(lib().pichol_batch_set_streams(self._h, nstreams), "pichol_batch_set_streams")
 
     def set_tuning(self, update_strip=4, diag_threads=512, diag_exclusive=0, eval_overlap=0, update_engine=1,
-                   solve_engine=1):
+                   solve_engine=2):
         """Launch shapes and scheduling for every problem (results are bit-identical)."""
         t = Tuning(update_strip, diag_threads, diag_exclusive, eval_overlap, update_engine, solve_engine)
         _check(lib().pichol_batch_set_tuning(self._h, ctypes.byref(t)), "pichol_batch_set_tuning")

@@ -21,9 +21,14 @@ size_t plan(pichol_ctx* ctx, char* base)
     const int64_t k = c.k, q = c.q, g = c.g, p = ctx->p, dp = ctx->dp, nt = ctx->nt;
     const int64_t eb = ctx->eb, cc = c.c, ntl = ctx->ntiles;
     size_t off = 0;
+    ctx->nguard = 0;
     auto take = [&](size_t bytes) -> void* {
         void* ptr = base ? (void*)(base + off) : nullptr;
         off += align256(bytes);
+        if (GUARD_BYTES && ctx->nguard < MAX_GUARDS) {
+            ctx->guard_off[ctx->nguard++] = off;
+            off += GUARD_BYTES;
+        }
         return ptr;
     };
     ctx->status = (DevStatus*)take(sizeof(DevStatus));
@@ -101,6 +106,19 @@ size_t plan(pichol_ctx* ctx, char* base)
 
 pichol_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PICHOL_OK : PICHOL_ERR_CUDA; }
 
+struct GuardList {
+    int n;
+    int64_t off[MAX_GUARDS];
+};
+
+// One CTA per guard band: the first byte that is not GUARD_FILL latches the error.
+__global__ void k_check_guards(const unsigned char* ws, GuardList gl, DevStatus* st)
+{
+    const unsigned char* band = ws + gl.off[blockIdx.x];
+    for (int i = threadIdx.x; i < (int)GUARD_BYTES; i += blockDim.x)
+        if (band[i] != GUARD_FILL) latch_error(st, PICHOL_ERR_WORKSPACE, -1, (int)blockIdx.x, i);
+}
+
 bool ready(const pichol_ctx* ctx) { return ctx && ctx->ws; }
 
 // Caller lambdas: every value finite and positive.
@@ -121,6 +139,17 @@ bool offsets_ok(const int64_t* o, int k, int64_t n)
 }
 
 }  // namespace
+
+namespace pichol {
+cudaError_t launch_check_guards(pichol_ctx* ctx, cudaStream_t s)
+{
+    GuardList gl;
+    gl.n = ctx->nguard;
+    for (int i = 0; i < ctx->nguard; ++i) gl.off[i] = (int64_t)ctx->guard_off[i];
+    k_check_guards<<<ctx->nguard, 256, 0, s>>>((const unsigned char*)ctx->ws, gl, ctx->status);
+    return cudaGetLastError();
+}
+}  // namespace pichol
 
 extern "C" {
 
@@ -189,7 +218,7 @@ pichol_status pichol_create(const pichol_config* cfg, pichol_ctx** out)
     ctx->tune.diag_threads = 512;
     ctx->tune.diag_exclusive = 1;
     ctx->tune.update_engine = 1;   // CUDA cores: see pichol_tuning
-    ctx->tune.solve_engine = 1;
+    ctx->tune.solve_engine = 2;    // automatic: see pichol_tuning
     *out = ctx;
     return PICHOL_OK;
 }
@@ -233,6 +262,13 @@ pichol_status pichol_set_workspace(pichol_ctx* ctx, void* workspace, size_t byte
     ctx->ws_bytes = bytes;
     plan(ctx, ctx->ws);
     ctx->have_hessian = ctx->have_factors = ctx->have_fit = false;
+    // debug build: fill the guard bands
+    for (int i = 0; i < ctx->nguard; ++i)
+        if (cudaMemset(ctx->ws + ctx->guard_off[i], GUARD_FILL, GUARD_BYTES) != cudaSuccess) {
+            ctx->ws = nullptr;
+            ctx->ws_bytes = 0;
+            return PICHOL_ERR_CUDA;
+        }
     // the status word must read "no error" before any kernel runs
     if (cudaMemset(ctx->status, 0, sizeof(DevStatus)) != cudaSuccess) {
         ctx->ws = nullptr;
@@ -424,6 +460,7 @@ pichol_status pichol_get_info(pichol_ctx* ctx, pichol_info* info, void* stream)
     if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
     DevStatus h;
     cudaStream_t s = (cudaStream_t)stream;
+    if (ctx->nguard > 0 && launch_check_guards(ctx, s) != cudaSuccess) return PICHOL_ERR_CUDA;
     cudaError_t e = cudaMemcpyAsync(&h, ctx->status, sizeof(h), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return PICHOL_ERR_CUDA;
@@ -524,7 +561,7 @@ pichol_status pichol_set_tuning(pichol_ctx* ctx, const pichol_tuning* t)
     if (t->diag_exclusive != 0 && t->diag_exclusive != 1) return PICHOL_ERR_INVALID_ARG;
     if (t->eval_overlap != 0 && t->eval_overlap != 1) return PICHOL_ERR_INVALID_ARG;
     if (t->update_engine != 0 && t->update_engine != 1) return PICHOL_ERR_INVALID_ARG;
-    if (t->solve_engine != 0 && t->solve_engine != 1) return PICHOL_ERR_INVALID_ARG;
+    if (t->solve_engine < 0 || t->solve_engine > 2) return PICHOL_ERR_INVALID_ARG;
     for (int i = 0; i < 2; ++i)
         if (t->reserved[i] != 0) return PICHOL_ERR_INVALID_ARG;
     ctx->tune = *t;
@@ -563,6 +600,16 @@ void pichol_destroy(pichol_ctx* ctx)
 }
 
 int32_t pichol_version(void) { return 100 * PICHOL_VERSION_MAJOR + PICHOL_VERSION_MINOR; }
+
+pichol_status pichol_debug_guards(const pichol_ctx* ctx, int64_t* offsets, int32_t capacity, int32_t* count)
+{
+    if (!ctx || !count || capacity < 0 || (capacity > 0 && !offsets)) return PICHOL_ERR_INVALID_ARG;
+    *count = ctx->nguard;
+    for (int i = 0; i < ctx->nguard && i < capacity; ++i) offsets[i] = (int64_t)ctx->guard_off[i];
+    return PICHOL_OK;
+}
+
+int32_t pichol_debug_build(void) { return GUARD_BYTES > 0 ? 1 : 0; }
 
 const char* pichol_status_string(pichol_status s)
 {

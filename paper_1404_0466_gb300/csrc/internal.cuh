@@ -32,6 +32,16 @@ constexpr int MAX_P = 8;                 // r + 1 <= 8
 constexpr int MAX_G = 32;                // sampled lambdas
 constexpr int MAX_K = 64;                // folds
 constexpr int GRAD_CHUNKS = 8;           // chunks of a tile row in the gradient's triangular products
+// Debug build (-DPICHOL_DEBUG): every workspace section is followed by a guard
+// band of GUARD_BYTES filled with GUARD_FILL when the workspace is attached;
+// pichol_get_info checks them and reports a write past a section's end.
+#ifdef PICHOL_DEBUG
+constexpr size_t GUARD_BYTES = 4096;
+#else
+constexpr size_t GUARD_BYTES = 0;
+#endif
+constexpr unsigned char GUARD_FILL = 0xA5;
+constexpr int MAX_GUARDS = 128;
 constexpr int LAM_CHUNK = 448;           // caller lambdas passed per kernel launch (as arguments)
 
 // Caller-supplied lambdas travel to the device as kernel arguments (3.5 KB, inside
@@ -213,6 +223,9 @@ struct pichol_ctx {
     float* dmax;         // k x q x nt max |diag| of the tile
     float* dmin;         // k x q x nt min |diag| of the tile
 
+    int nguard;          // debug build: guard bands after the workspace sections
+    size_t guard_off[pichol::MAX_GUARDS];
+
     bool have_hessian, have_factors, have_fit;
     long long launches;
 
@@ -306,5 +319,7 @@ cudaError_t launch_mchol(pichol_ctx* ctx, double c, double s, int levels, double
 int mchol_levels(double s, double s_min);
 cudaError_t launch_pinrmse(pichol_ctx* ctx, double* E_out, int32_t* t_star, cudaStream_t s);
 cudaError_t launch_check_rsqrt(int64_t n, uint64_t seed, double* max_rel, cudaStream_t s);
+// debug build: latch PICHOL_ERR_WORKSPACE (index = guard, pivot = byte) for a guard band byte that changed
+cudaError_t launch_check_guards(pichol_ctx* ctx, cudaStream_t s);
 
 }  // namespace pichol

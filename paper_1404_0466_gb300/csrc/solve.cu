@@ -442,7 +442,10 @@ static cudaError_t eval_impl(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s
         sa.c = cf.c;
         sa.st = ctx->status;
         // mixed mode, interpolated systems: all lambdas per fold on the tensor cores when tuned so
-        const bool tcs = std::is_same<T, float>::value && !EXACT && ctx->tune.solve_engine == 0 && ctx->Sh;
+        // automatic: the tensor cores when a fold's planes stream from HBM for every lambda pair
+        const bool big = (double)ctx->ntiles * ctx->p * TILE_ELEMS * sizeof(float) > 64.0 * 1024 * 1024;
+        const int eng = ctx->tune.solve_engine == 2 ? (big ? 0 : 1) : ctx->tune.solve_engine;
+        const bool tcs = std::is_same<T, float>::value && !EXACT && eng == 0 && ctx->Sh;
         cudaError_t er = tcs ? launch_solve_tc(ctx, t0h, tch, ctx->Btr, 0, ctx->W, st)
                              : solve_dispatch<T, EXACT>(ctx, sa, st);
         if (er == cudaSuccess && solved) er = cudaEventRecord(solved, st);

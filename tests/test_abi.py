@@ -167,11 +167,13 @@ def test_tuning_defaults_and_validation(L):
     t = binding.Tuning()
     assert L.pichol_get_tuning(h, ctypes.byref(t)) == 0
     assert (t.update_strip, t.diag_threads, t.diag_exclusive, t.eval_overlap) == (4, 512, 1, 0)
+    assert (t.update_engine, t.solve_engine) == (1, 2)       # CUDA-core updates, automatic solve engine
     for bad in (dict(update_strip=0), dict(update_strip=9), dict(diag_threads=384), dict(diag_exclusive=2),
-                dict(eval_overlap=2)):
-        b = binding.Tuning(**{**dict(update_strip=4, diag_threads=512, diag_exclusive=1), **bad})
+                dict(eval_overlap=2), dict(update_engine=2), dict(solve_engine=3), dict(solve_engine=-1)):
+        b = binding.Tuning(**{**dict(update_strip=4, diag_threads=512, diag_exclusive=1, update_engine=1), **bad})
         assert L.pichol_set_tuning(h, ctypes.byref(b)) == 1, bad
-    good = binding.Tuning(update_strip=2, diag_threads=256, diag_exclusive=0, eval_overlap=1)
+    good = binding.Tuning(update_strip=2, diag_threads=256, diag_exclusive=0, eval_overlap=1, update_engine=0,
+                          solve_engine=0)
     assert L.pichol_set_tuning(h, ctypes.byref(good)) == 0
     assert L.pichol_get_tuning(h, ctypes.byref(t)) == 0
     assert (t.update_strip, t.diag_threads, t.diag_exclusive, t.eval_overlap) == (2, 256, 0, 1)
@@ -412,6 +414,17 @@ def test_check_raises_the_latched_device_error(monkeypatch):
     with pytest.raises(B.PicholError, match="PICHOL_ERR_NOT_SPD") as ei:
         ctx.check()
     assert ei.value.code == 2 and "fold 3" in str(ei.value) and "pivot 417" in str(ei.value)
+
+
+def test_regular_build_has_no_guard_bands(L):
+    """Only the -DPICHOL_DEBUG build places guard bands in the workspace."""
+    assert L.pichol_debug_build() == 0
+    rc, h = _create(L, _cfg(L))
+    n = ctypes.c_int32(-1)
+    arr = (ctypes.c_int64 * 4)()
+    assert L.pichol_debug_guards(h, arr, 4, ctypes.byref(n)) == 0 and n.value == 0
+    assert L.pichol_debug_guards(h, None, 4, ctypes.byref(n)) == 1
+    L.pichol_destroy(h)
 
 
 def test_interface_version_agrees(L):

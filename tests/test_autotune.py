@@ -239,7 +239,7 @@ def test_tuner_drives_the_real_binding_methods(monkeypatch):
     import ctypes
     from paper_1404_0466_gb300 import binding as B
 
-    lib_state = {"t": B.Tuning(4, 512, 1, 0, 1, 1), "bt": None, "streams": 8}
+    lib_state = {"t": B.Tuning(4, 512, 1, 0, 1, 2), "bt": None, "streams": 8}
 
     class FakeLib:
         def pichol_get_tuning(self, h, ref):
@@ -274,7 +274,7 @@ def test_tuner_drives_the_real_binding_methods(monkeypatch):
 
     res = autotune.tune_context(ctx, "X", "Y", timer=timer, device="fake")
     assert res.choice == dict(update_strip=2, diag_threads=256, diag_exclusive=0, eval_overlap=1, update_engine=1,
-                              solve_engine=1)
+                              solve_engine=2)
     t = lib_state["t"]
     assert (t.update_strip, t.diag_threads, t.diag_exclusive, t.eval_overlap) == (2, 256, 0, 1)
     assert len(ran) == 12

@@ -62,6 +62,12 @@ WORKLOADS = {
                               refine_target="exact"),
     # 64 problems, d ~ U[128, 1536], n = 8 d, c in {1, 10}, k = 5, g = 5, r = 3, q = 51, one CUDA graph
     "batched_uneven": dict(gen="batched_uneven", cfg=None, mode="mixed", basis="cheb_log", refine=1),
+    # the mixed case's generator at d = 1024 (X 128 MB, coefficient planes 169 MB: both beyond the
+    # L2 cache, a few GB on the device): the small case of the kernel profiles
+    "mixed_ecc_d1024": dict(gen="mixed_ecc", cfg="MIXED_ECC", mode="mixed", basis="cheb_log", refine=1,
+                            over=dict(d=1024)),
+    # the large random-Fourier case as its own line (also a sub-line of the default run)
+    "large_rff": dict(gen="large_rff", cfg="LARGE_RFF", mode="mixed", basis="cheb_log", refine=1),
 }
 BATCH = dict(count=64, k=5, g=5, r=3, q=51, lo=1e-3, hi=1e1, seed=3)
 
@@ -77,6 +83,10 @@ def parse():
     ap.add_argument("--impl", choices=["own", "reference"], default="own")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="mixed_ecc")
     ap.add_argument("--refine", type=int, default=None, help="refinement steps (default: the workload's)")
+    ap.add_argument("--solve-engine", type=int, choices=(0, 1, 2), default=None,
+                    help="interpolated solves: 0 tensor cores, 1 CUDA cores, 2 automatic (the library's default)")
+    ap.add_argument("--update-engine", type=int, choices=(0, 1), default=None,
+                    help="trailing updates: 0 tensor cores, 1 CUDA cores (the library's default)")
     ap.add_argument("--no-exact", action="store_true", help="skip the exact-Cholesky comparison")
     ap.add_argument("--no-mchol", action="store_true", help="skip the MChol, PINRMSE and warm-start comparisons")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle sample (cpu_baseline, error)")
@@ -117,8 +127,8 @@ def dist_env():
 def workload(name):
     from paper_1404_0466_gb300 import synth
     w = WORKLOADS[name]
-    cfg = dict(getattr(synth, w["cfg"]))
-    prob = getattr(synth, w["gen"])()
+    cfg = dict(getattr(synth, w["cfg"]), **w.get("over", {}))
+    prob = getattr(synth, w["gen"])(**w.get("over", {}))
     return w, cfg, prob
 
 
@@ -938,6 +948,10 @@ def run_own(args):
         import torch.distributed as tdist
         tune_res = autotune.tune_context(ctx, X, Y, reps=2, stream=stream,
                                          pg=tdist.group.WORLD if pg is not None else None)
+    if args.solve_engine is not None:
+        ctx.set_tuning(solve_engine=args.solve_engine)
+    if args.update_engine is not None:
+        ctx.set_tuning(update_engine=args.update_engine)
     tuning = dict(ctx.tuning(), autotuned_ms=(tune_res.timings if tune_res else {}), tuner="autotune.tune_context")
     ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 

@@ -256,14 +256,25 @@ k_resid_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUte
                 float v[16];
 #pragma unroll
                 for (int u = 0; u < 16; ++u) v[u] = 0.0f;
-                for (int m = 0; m < p; ++m) {
-                    float x[16];
-                    const uint32_t src = tmem + ((uint32_t)(qtr * 32) << 16) +
-                                         (uint32_t)((b * p + m) * BN + chalf * HC + cc * 16);
-                    tc5::ld16(src, x);
-                    const float* ph = phis + m * BN + chalf * HC + cc * 16;
+                // the planes' loads in groups of G, one wait per group (G x 16 registers)
+                constexpr int G = BN == 64 ? 2 : 4;
+                for (int m0 = 0; m0 < p; m0 += G) {
+                    uint32_t x[G][16];
 #pragma unroll
-                    for (int u = 0; u < 16; ++u) v[u] = fmaf(ph[u], x[u], v[u]);
+                    for (int h = 0; h < G; ++h)
+                        if (m0 + h < p)
+                            tc5::ld16_issue(tmem + ((uint32_t)(qtr * 32) << 16) +
+                                                (uint32_t)((b * p + m0 + h) * BN + chalf * HC + cc * 16),
+                                            x[h]);
+                    tc5::wait_ld();
+#pragma unroll
+                    for (int h = 0; h < G; ++h)
+                        if (m0 + h < p) {
+                            tc5::regs_ready(x[h]);
+                            const float* ph = phis + (m0 + h) * BN + chalf * HC + cc * 16;
+#pragma unroll
+                            for (int u = 0; u < 16; ++u) v[u] = fmaf(ph[u], __uint_as_float(x[h][u]), v[u]);
+                        }
                 }
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {   // Kahan: tot += v

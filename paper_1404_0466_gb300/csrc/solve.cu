@@ -41,23 +41,27 @@ struct DiagArgs {
     int64_t ntiles, d;
 };
 
+constexpr int DIAG_INV_THREADS = 256;
+
 template <typename T, bool EXACT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(DIAG_INV_THREADS)
 k_diag_inv(DiagArgs a)
 {
+    constexpr int NT = DIAG_INV_THREADS;
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::N;
+    constexpr int NV = TILE_ELEMS / VN / NT;       // 16-byte vectors per thread and plane
+    constexpr int GP = 16 / NV;                     // planes whose loads are in flight together
     extern __shared__ __align__(16) unsigned char dsm[];
     T (*Ls)[TB + 1] = reinterpret_cast<T (*)[TB + 1]>(dsm);
     T (*Xs)[TB + 1] = reinterpret_cast<T (*)[TB + 1]>(dsm + sizeof(T) * TB * (TB + 1));
     __shared__ float rmax[TB], rmin[TB];
     __shared__ int rbad[TB];
     __shared__ T rinv[TB];
+    __shared__ T Ts[TB * TB / 4];     // T = B A^-1 of the lower-left blocks being doubled
     const int i = blockIdx.x, t = a.t0 + blockIdx.y, f = blockIdx.z, tid = threadIdx.x;
     const int64_t ti = tile_index(i, i);
-    T w[MAX_P];
     const int np = EXACT ? 1 : a.p;
-    if constexpr (!EXACT) {
-        for (int m = 0; m < a.p; ++m) w[m] = (T)a.phi[(int64_t)t * a.p + m];
-    }
     const T* base;
     if constexpr (EXACT) {
         const int pr = f * a.per + (t - a.t0);
@@ -65,18 +69,44 @@ k_diag_inv(DiagArgs a)
     } else {
         base = (const T*)a.src + ((int64_t)f * a.ntiles + ti) * a.p * TILE_ELEMS;
     }
-    for (int e = tid; e < TILE_ELEMS; e += 128) {
-        const int r = e / TB, c = e % TB;
-        T v;
-        if constexpr (EXACT) {
-            v = base[e];
-        } else {
-            // phi_0 = 1 for both bases: start at Theta_0, then FMAs in m (the solve's order)
-            v = base[e];
-            for (int m = 1; m < np; ++m) v = fma(w[m], base[(int64_t)m * TILE_ELEMS + e], v);
+    // L~_ii = Theta_0 + sum_{m >= 1} phi_m Theta_m (phi_0 = 1 for both bases; FMAs in m,
+    // the solve's order), every thread NV vectors of each plane, the loads of GP
+    // planes issued before their first use
+    const V* bv = reinterpret_cast<const V*>(base);
+    V acc[NV];
+#pragma unroll
+    for (int u = 0; u < NV; ++u) acc[u] = bv[tid + NT * u];
+    if constexpr (!EXACT) {
+        for (int m0 = 1; m0 < np; m0 += GP) {
+            V tv[GP][NV];
+#pragma unroll
+            for (int h = 0; h < GP; ++h)
+                if (m0 + h < np)
+#pragma unroll
+                    for (int u = 0; u < NV; ++u) tv[h][u] = bv[(int64_t)(m0 + h) * (TILE_ELEMS / VN) + tid + NT * u];
+#pragma unroll
+            for (int h = 0; h < GP; ++h)
+                if (m0 + h < np) {
+                    const T w = (T)a.phi[(int64_t)t * a.p + m0 + h];
+#pragma unroll
+                    for (int u = 0; u < NV; ++u) {
+                        T* x = reinterpret_cast<T*>(&acc[u]);
+                        const T* y = reinterpret_cast<const T*>(&tv[h][u]);
+#pragma unroll
+                        for (int j = 0; j < VN; ++j) x[j] = fma(w, y[j], x[j]);
+                    }
+                }
         }
-        Ls[r][c] = (c <= r) ? v : T(0);
-        Xs[r][c] = T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < NV; ++u) {
+        const T* x = reinterpret_cast<const T*>(&acc[u]);
+        const int e = VN * (tid + NT * u), r = e / TB, c0 = e % TB;
+#pragma unroll
+        for (int j = 0; j < VN; ++j) {
+            Ls[r][c0 + j] = (c0 + j <= r) ? x[j] : T(0);
+            Xs[r][c0 + j] = T(0);
+        }
     }
     __syncthreads();
     if (tid < TB) {
@@ -88,26 +118,43 @@ k_diag_inv(DiagArgs a)
         rinv[tid] = T(1) / dv;
     }
     __syncthreads();
+    // Blocked inverse.  The eight 8 x 8 diagonal blocks are inverted by forward
+    // substitution on unit vectors (thread (b, c): column c of block b):
+    //   X[r][c] = -(sum_{c <= q < r} L[r][q] X[q][c]) / L[r][r].
+    // Then the inverted blocks are doubled three times (h = 8, 16, 32): for
+    //   L = [A 0; B C],  L^-1 = [A^-1 0; -C^-1 (B A^-1) C^-1],
+    // first T = B A^-1, then the lower-left block -C^-1 T, every entry by one thread.
     if (tid < TB) {
-        // inverse column c = tid by forward substitution on e_c:
-        //   X[r][c] = -(sum_{c <= q < r} L[r][q] X[q][c]) / L[r][r],
-        // each sum as two interleaved partial sums (even and odd q)
-        const int c = tid;
+        const int b0 = (tid >> 3) * 8, c = b0 + (tid & 7);
         Xs[c][c] = rinv[c];
-        for (int r = c + 1; r < TB; ++r) {
-            T s0 = T(0), s1 = T(0);
-            int qq = c;
-            for (; qq + 1 < r; qq += 2) {
-                s0 = fma(Ls[r][qq], Xs[qq][c], s0);
-                s1 = fma(Ls[r][qq + 1], Xs[qq + 1][c], s1);
-            }
-            if (qq < r) s0 = fma(Ls[r][qq], Xs[qq][c], s0);
-            Xs[r][c] = -(s0 + s1) * rinv[r];
+        for (int r = c + 1; r < b0 + 8; ++r) {
+            T s = T(0);
+            for (int qq = c; qq < r; ++qq) s = fma(Ls[r][qq], Xs[qq][c], s);
+            Xs[r][c] = -s * rinv[r];
         }
     }
     __syncthreads();
+#pragma unroll 1
+    for (int h = 8; h < TB; h *= 2) {
+        const int hh = h * h, ne = (TB / (2 * h)) * hh;     // entries of all lower-left blocks: 32 h
+        for (int e = tid; e < ne; e += NT) {
+            const int b0 = (e / hh) * 2 * h, r = (e % hh) / h, c = e % h;
+            T s = T(0);
+            for (int k = c; k < h; ++k) s = fma(Ls[b0 + h + r][b0 + k], Xs[b0 + k][b0 + c], s);
+            Ts[e] = s;
+        }
+        __syncthreads();
+        for (int e = tid; e < ne; e += NT) {
+            const int b0 = (e / hh) * 2 * h, r = (e % hh) / h, c = e % h;
+            const T* tcol = Ts + (e / hh) * hh + c;
+            T s = T(0);
+            for (int k = 0; k <= r; ++k) s = fma(Xs[b0 + h + r][b0 + h + k], tcol[k * h], s);
+            Xs[b0 + h + r][b0 + c] = -s;
+        }
+        __syncthreads();
+    }
     T* out = (T*)a.dinv + (((int64_t)f * a.q + t) * a.nt + i) * TILE_ELEMS;
-    for (int e = tid; e < TILE_ELEMS; e += 128) out[e] = Xs[e / TB][e % TB];
+    for (int e = tid; e < TILE_ELEMS; e += NT) out[e] = Xs[e / TB][e % TB];
     if (tid == 0) {
         float mx = 0.0f, mn = FLT_MAX;
         int bad = 0;
@@ -414,7 +461,7 @@ static cudaError_t eval_impl(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s
     }
     {
         StageScope sc_(ctx, ST_DIAG_INV, s);
-        k_diag_inv<T, EXACT><<<dim3(ctx->nt, tcount, cf.k), 128, dsm, s>>>(da);
+        k_diag_inv<T, EXACT><<<dim3(ctx->nt, tcount, cf.k), DIAG_INV_THREADS, dsm, s>>>(da);
     }
     ctx->launches++;
     cudaError_t e = cudaGetLastError();
@@ -563,7 +610,7 @@ static cudaError_t diag_solve_one_impl(pichol_ctx* ctx, const double* phi_row, c
         if (ea != cudaSuccess) return ea;
         {
             StageScope sc_(ctx, ST_DIAG_INV, s);
-            k_diag_inv<T, false><<<dim3(ctx->nt, 1, cf.k), 128, dsm, s>>>(da);
+            k_diag_inv<T, false><<<dim3(ctx->nt, 1, cf.k), DIAG_INV_THREADS, dsm, s>>>(da);
         }
         ctx->launches++;
     }

@@ -119,11 +119,27 @@ __device__ __forceinline__ void k_solve_tc_epilogue(const SolveTcArgs& a, uint32
         a.Sh[so] = h;
         a.Sl[so] = v - h;
     };
-    // a 64 x 64 tile into shared memory rows of 65 (coalesced reads, conflict-free column reads)
-    auto stage_tile = [](float* dst, const float* src, int tid) {
-        for (int e = tid; e < TILE_ELEMS; e += 256) dst[(e / TB) * (TB + 1) + e % TB] = src[e];
+    // A 64 x 64 tile is moved global -> registers (four 16-byte loads per thread,
+    // all issued before the first use) -> shared rows of 65 (conflict-free column
+    // reads), so each staging costs one memory latency.
+    auto fetch_tile = [&](float4 (&v)[4], const float* src) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = reinterpret_cast<const float4*>(src)[et + 256 * u];
+    };
+    auto store_tile = [&](float* dst, const float4 (&v)[4]) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = 4 * (et + 256 * u);
+            float* d = dst + (e / TB) * (TB + 1) + e % TB;
+            d[0] = v[u].x;
+            d[1] = v[u].y;
+            d[2] = v[u].z;
+            d[3] = v[u].w;
+        }
     };
     const float* dinv_f = a.dinv + (int64_t)f * a.q * a.nt * TILE_ELEMS;
+    auto dinv_at = [&](int t, int i) { return dinv_f + ((int64_t)t * a.nt + i) * TILE_ELEMS; };
+    constexpr int PR = 2;                   // planes of the coupling tile kept in registers
     for (int s = 0; s < nS; ++s) {
         int i0, jlo, jhi;
         s_step<DIR>(a, s, i0, jlo, jhi);
@@ -141,12 +157,25 @@ __device__ __forceinline__ void k_solve_tc_epilogue(const SolveTcArgs& a, uint32
                 float v[16];
 #pragma unroll
                 for (int u = 0; u < 16; ++u) v[u] = 0.0f;
-                for (int m = 0; m < p; ++m) {
-                    float x[16];
-                    tc5::ld16(tmem + ((uint32_t)(qtr * 32) << 16) + (uint32_t)((b * p + m) * BN + chalf * HC + cc * 16), x);
-                    const float* ph = phis + m * BN + chalf * HC + cc * 16;
+                // the planes' loads in groups of G, one wait per group (G x 16 registers)
+                constexpr int G = BN == 64 ? 2 : 4;
+                for (int m0 = 0; m0 < p; m0 += G) {
+                    uint32_t x[G][16];
 #pragma unroll
-                    for (int u = 0; u < 16; ++u) v[u] = fmaf(ph[u], x[u], v[u]);
+                    for (int h = 0; h < G; ++h)
+                        if (m0 + h < p)
+                            tc5::ld16_issue(tmem + ((uint32_t)(qtr * 32) << 16) +
+                                                (uint32_t)((b * p + m0 + h) * BN + chalf * HC + cc * 16),
+                                            x[h]);
+                    tc5::wait_ld();
+#pragma unroll
+                    for (int h = 0; h < G; ++h)
+                        if (m0 + h < p) {
+                            tc5::regs_ready(x[h]);
+                            const float* ph = phis + (m0 + h) * BN + chalf * HC + cc * 16;
+#pragma unroll
+                            for (int u = 0; u < 16; ++u) v[u] = fmaf(ph[u], __uint_as_float(x[h][u]), v[u]);
+                        }
                 }
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {   // Kahan: tot += v
@@ -161,30 +190,43 @@ __device__ __forceinline__ void k_solve_tc_epilogue(const SolveTcArgs& a, uint32
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&tempty[b])) : "memory");
         }
         if (*abort_flag) break;
-        // products of the pair's rows, V[row][col]; then R = rhs - V in place
-#pragma unroll
-        for (int u = 0; u < HC; ++u) Vs[(qtr * 32 + lane) * BN + chalf * HC + u] = tot[u];
-        epi_sync();
         const bool two = i1 < a.nt;
         const int ia = DIR == 0 ? i0 : (two ? i1 : i0);   // solved first: i0 forward, i0 + 1 backward
         const int va = DIR == 0 ? 0 : (two ? TB : 0);     // its rows in V
         const int ib = DIR == 0 ? i1 : i0, vb = DIR == 0 ? TB : 0;
+        // the lambdas of this CTA's columns
+        const int64_t nlast = (n0 + BN < N ? n0 + BN : N) - 1;
+        const int tfirst = a.t0 + (int)(n0 / c), tlast = a.t0 + (int)(nlast / c);
+        // loads in flight during the drain's stores: the first lambda's inverse, and
+        // the first PR planes of the tile between the pair's rows (the same for every
+        // lambda, held in registers; the others are read per lambda, from L2)
+        float4 pa[4], pb[4], thr[PR][4];
+        fetch_tile(pa, dinv_at(tfirst, ia));
+        const float* th = a.theta + ((int64_t)f * a.ntiles + tile_index(i1 < a.nt ? i1 : i0, i0)) * p * TILE_ELEMS;
+        if (two) {
+#pragma unroll
+            for (int m = 0; m < PR; ++m)
+                if (m < p) fetch_tile(thr[m], th + (int64_t)m * TILE_ELEMS);
+        }
+        // products of the pair's rows, V[row][col]; then R = rhs - V in place
+#pragma unroll
+        for (int u = 0; u < HC; ++u) Vs[(qtr * 32 + lane) * BN + chalf * HC + u] = tot[u];
+        epi_sync();
+        // (consecutive threads take consecutive columns: runs of c contiguous values)
         for (int e = et; e < TB * BN; e += 256) {
-            const int col = e / TB, rr = e % TB;
+            const int rr = e / BN, col = e % BN;
             const int64_t n = n0 + col;
             if (n >= N) continue;
             Vs[(va + rr) * BN + col] = in_at_r(ia, n, rr) - Vs[(va + rr) * BN + col];
             if (two) Vs[(vb + rr) * BN + col] = in_at_r(ib, n, rr) - Vs[(vb + rr) * BN + col];
         }
-        // the lambdas of this CTA's columns, one after another
-        const int64_t nlast = (n0 + BN < N ? n0 + BN : N) - 1;
-        const int tfirst = a.t0 + (int)(n0 / c), tlast = a.t0 + (int)(nlast / c);
         for (int t = tfirst; t <= tlast; ++t) {
             const int64_t ca = (int64_t)(t - a.t0) * c, cb = ca + c;
             const int cl0 = (int)((ca > n0 ? ca : n0) - n0), cl1 = (int)((cb < n0 + BN ? cb : n0 + BN) - n0);
             const int ncol = cl1 - cl0;
             epi_sync();                                     // Ds / Ls / V rows free, R of all columns ready
-            stage_tile(Ds, dinv_f + ((int64_t)t * a.nt + ia) * TILE_ELEMS, et);
+            store_tile(Ds, pa);
+            if (two) fetch_tile(pb, dinv_at(t, ib));
             epi_sync();
             // Z = Dinv R (forward) or Dinv^T R (backward) for the columns of t
             for (int e = et; e < TB * ncol; e += 256) {
@@ -195,18 +237,46 @@ __device__ __forceinline__ void k_solve_tc_epilogue(const SolveTcArgs& a, uint32
                     acc = fmaf(DIR == 0 ? Ds[rr * (TB + 1) + k] : Ds[k * (TB + 1) + rr], Vs[(va + k) * BN + col], acc);
                 Zs[rr * BN + col] = acc;
             }
+            if (t < tlast) fetch_tile(pa, dinv_at(t + 1, ia));
             if (!two) continue;
-            epi_sync();
             // the other row's R minus the tile between the rows times Z, then its Dinv
-            const float* th = a.theta + ((int64_t)f * a.ntiles + tile_index(i1, i0)) * p * TILE_ELEMS;
             float ph[MAX_P];
             for (int m = 0; m < p; ++m) ph[m] = (float)a.phi[(int64_t)t * p + m];
-            for (int e = et; e < TILE_ELEMS; e += 256) {
-                float l = 0.0f;
-                for (int m = 0; m < p; ++m) l = fmaf(ph[m], th[(int64_t)m * TILE_ELEMS + e], l);
-                Ls[(e / TB) * (TB + 1) + e % TB] = l;
+            float4 lv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                lv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int m = 0; m < PR; ++m)
+                    if (m < p) {
+                        lv[u].x = fmaf(ph[m], thr[m][u].x, lv[u].x);
+                        lv[u].y = fmaf(ph[m], thr[m][u].y, lv[u].y);
+                        lv[u].z = fmaf(ph[m], thr[m][u].z, lv[u].z);
+                        lv[u].w = fmaf(ph[m], thr[m][u].w, lv[u].w);
+                    }
             }
-            stage_tile(Ds, dinv_f + ((int64_t)t * a.nt + ib) * TILE_ELEMS, et);
+            for (int m = PR; m < p; m += 2) {          // two planes per memory latency
+                float4 tv[2][4];
+                const int m2 = m + 1 < p ? 2 : 1;
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (h < m2) fetch_tile(tv[h], th + (int64_t)(m + h) * TILE_ELEMS);
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (h < m2) {
+                        const float w = ph[m + h];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            lv[u].x = fmaf(w, tv[h][u].x, lv[u].x);
+                            lv[u].y = fmaf(w, tv[h][u].y, lv[u].y);
+                            lv[u].z = fmaf(w, tv[h][u].z, lv[u].z);
+                            lv[u].w = fmaf(w, tv[h][u].w, lv[u].w);
+                        }
+                    }
+            }
+            epi_sync();                                     // Z complete, Ds read
+            store_tile(Ls, lv);
+            store_tile(Ds, pb);
             epi_sync();
             for (int e = et; e < TB * ncol; e += 256) {
                 const int col = cl0 + e / TB, rr = e % TB;

@@ -362,6 +362,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
 
 // XT_hi / XT_lo [dp][Kpad]: column kc of fold j (k0[j] <= kc < k0[j+1]) holds
 // sample row o[j] + (kc - k0[j]) if that row is in fold j, else 0; rows >= d are 0.
+// With Xrh / Xrl given, the same pass writes the row-major split [n][dp] of X
+// (columns >= d zero) for the direct hold-out score: every sample row is read
+// once, by the CTA whose 32 columns of XT hold it.
 struct XtArgs {
     int64_t k0[MAX_K + 1];
     int64_t o[MAX_K + 1];
@@ -370,7 +373,7 @@ struct XtArgs {
 
 __global__ void __launch_bounds__(256)
 k_split_xt(const float* __restrict__ X, int64_t d, int64_t dp, int64_t kpad, XtArgs xa, float* __restrict__ Xh,
-           float* __restrict__ Xl)
+           float* __restrict__ Xl, float* __restrict__ Xrh, float* __restrict__ Xrl)
 {
     __shared__ float t[32][33];
     const int64_t kc0 = (int64_t)blockIdx.x * 32, f0 = (int64_t)blockIdx.y * 32;
@@ -382,7 +385,14 @@ k_split_xt(const float* __restrict__ X, int64_t d, int64_t dp, int64_t kpad, XtA
         const int64_t row = xa.o[j] + (kc - xa.k0[j]);
         const int64_t feat = f0 + tx;
         float v = 0.0f;
-        if (row < xa.o[j + 1] && feat < d) v = X[row * d + feat];
+        if (row < xa.o[j + 1]) {
+            if (feat < d) v = X[row * d + feat];
+            if (Xrh) {
+                const float hi = tc::tf32_round(v);
+                Xrh[row * dp + feat] = hi;
+                Xrl[row * dp + feat] = v - hi;
+            }
+        }
         t[yy][tx] = v;
     }
     __syncthreads();
@@ -495,7 +505,6 @@ static cudaError_t gemm_attr()
     return smem_limit_once(k_tc_gemm, tc::SMEM_BYTES, set);
 }
 
-cudaError_t launch_split_xr(pichol_ctx* ctx, const float* X, const float* Y, cudaStream_t s);
 
 int64_t tc_kpad(const pichol_ctx* ctx)
 {
@@ -518,8 +527,10 @@ cudaError_t launch_gram_tc(pichol_ctx* ctx, const float* X, cudaStream_t s)
     xa.o[c.k] = ctx->offs[c.k];
     {
         StageScope sc_(ctx, ST_GRAM, s);
-        k_split_xt<<<dim3((unsigned)(kpad / 32), (unsigned)((dp + 31) / 32)), 256, 0, s>>>(X, c.d, dp, kpad, xa,
-                                                                                          ctx->Xh, ctx->Xl);
+        // X and Y are read only during this call: the row-major split of X for the
+        // direct hold-out scores of the evaluation is written in the same pass
+        k_split_xt<<<dim3((unsigned)(kpad / 32), (unsigned)((dp + 31) / 32)), 256, 0, s>>>(
+            X, c.d, dp, kpad, xa, ctx->Xh, ctx->Xl, ctx->Xrh, ctx->Xrl);
     }
     ctx->launches++;
     CUtensorMap mh, ml;
@@ -552,9 +563,11 @@ cudaError_t launch_gram_tc(pichol_ctx* ctx, const float* X, cudaStream_t s)
     ctx->launches++;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // X and Y are read only during this call: keep the row-major split of X and
-    // a copy of Y for the direct hold-out scores of the evaluation
-    if ((e = launch_split_xr(ctx, X, ctx->Yin, s)) != cudaSuccess) return e;
+    // and a copy of Y
+    if (ctx->Ycp &&
+        (e = cudaMemcpyAsync(ctx->Ycp, ctx->Yin, sizeof(float) * (size_t)(c.n * c.c), cudaMemcpyDeviceToDevice, s)) !=
+            cudaSuccess)
+        return e;
 
     // Bv_j = X_j^T Y_j on the same operands: B = Y^T (c rows, zero-filled to 128)
     {
@@ -792,35 +805,6 @@ cudaError_t launch_score_tc(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s)
     }
     ctx->launches += 2;
     return cudaGetLastError();
-}
-
-// X split row-major for the direct score: Xrh / Xrl [n][dp] = TF32 part and
-// remainder of X (columns >= d zero).
-__global__ void __launch_bounds__(256)
-k_split_xr(const float* __restrict__ X, int64_t n, int64_t d, int64_t dp, float* __restrict__ Xh,
-           float* __restrict__ Xl)
-{
-    const int64_t total = n * dp;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = e / dp, col = e % dp;
-        const float v = col < d ? X[row * d + col] : 0.0f;
-        const float hi = tc::tf32_round(v);
-        Xh[e] = hi;
-        Xl[e] = v - hi;
-    }
-}
-
-cudaError_t launch_split_xr(pichol_ctx* ctx, const float* X, const float* Y, cudaStream_t s)
-{
-    const pichol_config& c = ctx->cfg;
-    {
-        StageScope sc_(ctx, ST_GRAM, s);
-        k_split_xr<<<4 * (ctx->nsm > 0 ? ctx->nsm : 152), 256, 0, s>>>(X, c.n, c.d, ctx->dp, ctx->Xrh, ctx->Xrl);
-    }
-    ctx->launches++;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return cudaMemcpyAsync(ctx->Ycp, Y, sizeof(float) * (size_t)(c.n * c.c), cudaMemcpyDeviceToDevice, s);
 }
 
 }  // namespace pichol

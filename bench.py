@@ -202,14 +202,16 @@ def summarise_clocks(lines):
 # ---------------------------------------------------------------------------
 # algorithmic work per stage (for the roofline of the dominant kernel)
 # ---------------------------------------------------------------------------
-def stage_work(cfg, mode, refine, target="interpolated", residual="tensor"):
+def stage_work(cfg, mode, refine, target="interpolated", residual="tensor", update_engine=1):
     """Algorithmic work per step of each timed stage: (kind, amount, bound, executed).
     kind "flop": floating-point operations the method needs, counted once (an
     FMA counts 2), not the ones the kernel happens to execute; "byte": bytes
     that must cross HBM.  ``executed`` is the factor by which the kernel's own
     arithmetic exceeds that count (3 for the split-TF32 products, which run
     hi*hi + hi*lo + lo*hi; about 12 for double-float accumulation on the FP32
-    pipes), reported beside the fraction and never folded into it."""
+    pipes), reported beside the fraction and never folded into it.
+    ``update_engine`` is the tuning's engine of the trailing updates (0 tensor
+    cores, 1 CUDA cores, the library's default)."""
     n, d, c, k, g, r, q = (cfg[x] for x in ("n", "d", "c", "k", "g", "r", "q"))
     p = r + 1
     D = d * (d + 1) // 2
@@ -226,17 +228,22 @@ def stage_work(cfg, mode, refine, target="interpolated", residual="tensor"):
         "gram": ("flop", n * d * (d + 1), tensor, split),
         # X_j^T Y_j for every fold: 2 n d c flops
         "xty": ("flop", 2 * n * d * c, tensor, split),
-        # trailing updates of k g blocked factorisations (lower tiles, 2 b^3 per tile update);
-        # in mixed mode the bulk of each step on the tensor cores in split TF32
-        "chol_update": ("flop", upd, tensor, split),
+        # trailing updates of k g blocked factorisations (lower tiles, 2 b^3 per tile update):
+        # fp32 FMAs on the CUDA cores by default; with update_engine 0 (mixed mode) the bulk
+        # of each step on the tensor cores in split TF32
+        "chol_update": ("flop", upd, tensor, split) if (mode == "mixed" and update_engine == 0) else
+                       ("flop", upd, "alu", 1),
         # the 64 x 64 diagonal tiles of k g factorisations, b^3 / 3 flops each, in FP64
         "chol_diag": ("flop", nt * k * g * 64 ** 3 // 3, "fp64", 1),
         # panel rows by substitution: b^3 flops per off-diagonal tile of the panel
         "chol_panel": ("flop", sum(range(nt)) * 64 ** 3 * k * g, "alu", 1),
         # per (fold, lambda, tile row): L~_ii from p planes (p b^2) and its inverse (b^3 / 3)
         "diag_inv": ("flop", k * q * nt * (64 ** 3 // 3 + p * 64 * 64), "alu", 1),
-        # read g factors, write p coefficient sets, per fold (lower triangles)
-        "fit": ("byte", k * (g + p) * D * eb, "hbm", 1),
+        # read g factors, write p coefficient sets, per fold (lower triangles); in mixed mode
+        # the stage also splits the coefficients into the tensor-core operands (k_theta_split:
+        # one read and four writes of the tile-major planes), counted as executed traffic
+        "fit": ("byte", k * (g + p) * D * eb, "hbm",
+                1 + (5 * p * (nt * (nt + 1) // 2) * 64 * 64 / ((g + p) * D) if mode == "mixed" else 0)),
         # the interpolated solves, once per refinement step more (the correction solve);
         # the kernel evaluates the factor in each of its two substitutions (4 p D)
         "solve": ("flop", eval_solve * (1 + refine), "alu",
@@ -250,8 +257,11 @@ def stage_work(cfg, mode, refine, target="interpolated", residual="tensor"):
                  # on the tensor cores: one split-TF32 product per coefficient plane and pass
                  # (p (d^2 / 2) 2 c per lambda each, three products per split)
                  ("flop", eval_solve * refine, tensor, 3 * 2 * p * d * d * c / (2 * d * d * c + 2 * p * D)),
-        # <W, G_f W> for every fold and lambda: G_f W as one product of N = q c columns
-        "score": ("flop", k * q * 2 * d * d * c, tensor, split),
+        # <W, G_f W> for every fold and lambda (the product G_f W, 2 d^2 c per system); in
+        # mixed mode the kernel forms the hold-out residual Y_f - X_f W directly instead
+        # (2 (n / k) d c per system, three products per split), in FP64 mode G_f W
+        "score": ("flop", k * q * 2 * d * d * c, tensor, split * n / (k * d)) if mode == "mixed" else
+                 ("flop", k * q * 2 * d * d * c, "alu", 1),
     }
     if target == "exact":
         # exact-system residual: G_f W and G_all W for every lambda, 2 d^2 c each
@@ -861,11 +871,24 @@ def large_rff_compare(binding, steps=3):
     idx, Eg = _golden_large_rff()
     E = out[0].cpu().numpy()
     err = float(np.max(np.abs(E[0, idx] - np.array(Eg)) / np.array(Eg)))
-    # the solve streams the off-diagonal coefficient tiles of its fold (p planes of
-    # 64 x 64 fp32) once per substitution, two lambdas per CTA, twice per step
-    # (solve and correction solve)
+    # Coefficient bytes one solve launch streams.  The library's automatic engine choice
+    # takes the tensor cores when one fold's planes exceed 64 MiB: one launch per
+    # substitution, each CTA (fold, 64 columns of the stacked lambdas) reading the
+    # off-diagonal tiles' p planes once, as TF32 hi and lo.  Otherwise the CUDA-core
+    # solve: one launch for both substitutions, each CTA (fold, lambda pair) reading the
+    # fp32 planes once per substitution.
     nt = -(-d // 64)
-    theta_bytes = k * ((q + 1) // 2) * 2 * (r + 1) * (nt * (nt + 1) // 2 - nt) * 64 * 64 * 4
+    offdiag, p = nt * (nt + 1) // 2 - nt, r + 1
+    tensor_engine = (nt * (nt + 1) // 2) * p * 64 * 64 * 4 > 64 * 1024 * 1024
+    if tensor_engine:
+        ncb = -(-(q * c) // (64 if p <= 4 else 32))
+        theta_bytes = k * ncb * offdiag * p * 2 * 64 * 64 * 4
+        what = ("off-diagonal coefficient planes (TF32 hi and lo) read by one tensor-core substitution "
+                "launch: each (fold, 64-column) CTA reads its fold's planes once")
+    else:
+        theta_bytes = k * ((q + 1) // 2) * 2 * offdiag * p * 64 * 64 * 4
+        what = ("off-diagonal coefficient planes read by one CUDA-core solve launch: each (fold, lambda "
+                "pair) CTA reads its fold's planes in both substitutions")
     sms, sla = st.get("solve", (0.0, 0))
     solve_ms = sms / steps / max(1, sla / steps)
     res = {"workload": (f"large_rff: n={cfg['n']} d={d} c={c} k={k} g={g} r={r} q={q} basis=cheb_log mode=mixed "
@@ -875,9 +898,8 @@ def large_rff_compare(binding, steps=3):
            "stage_timing_complete": complete,
            "solve_theta_stream": {"bytes_per_launch": theta_bytes, "ms_per_launch": solve_ms,
                                   "GBps": theta_bytes / (solve_ms / 1e3) / 1e9 if solve_ms > 0 else None,
-                                  "what": "off-diagonal coefficient planes read by one interpolated-solve launch "
-                                          "(each (fold, lambda pair) CTA reads its fold's planes in both "
-                                          "substitutions); L2 holds none of a fold's planes at this size"},
+                                  "engine": "tensor cores" if tensor_engine else "CUDA cores",
+                                  "what": what + "; L2 holds none of a fold's planes at this size"},
            "err_vs_fp64": {"max_rel_E": err, "sample": f"fold 0, grid indices {idx}, stored oracle values"},
            "device_status": binding.STATUS.get(info.code)}
     ctx.close()
@@ -1208,7 +1230,8 @@ def run_own(args):
     peaks = load_peaks()
     peaks["pipes"] = pipes
     stage_ms = {s: v for s, v in stages.items() if v[1] > 0}
-    work = stage_work(cfg, w["mode"], refine, w.get("refine_target", "interpolated"))
+    work = stage_work(cfg, w["mode"], refine, w.get("refine_target", "interpolated"),
+                      update_engine=tuning.get("update_engine", 1))
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",

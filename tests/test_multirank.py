@@ -114,6 +114,14 @@ def test_roofline_entry_arithmetic():
     assert abs(amount - 50.84e9) < 0.01e9
     kind, amount_g, bound, executed = work["gram"]
     assert amount_g == 32768 * d * (d + 1) and bound == "tensor" and executed == 3
+    # the trailing updates run on the CUDA cores unless the tuning picks the tensor cores
+    assert work["chol_update"][2:] == ("alu", 1)
+    assert bench.stage_work(cfg, "mixed", 1, update_engine=0)["chol_update"][2:] == ("tensor", 3)
+    # the direct-form score computes Y_f - X_f W: 3 products of 2 (n / k) d c per system
+    # against the 2 d^2 c of <W, G_f W>
+    kind, amount_s, bound, executed = work["score"]
+    assert amount_s == 5 * 101 * 2 * d * d * c and bound == "tensor"
+    assert abs(executed - 3 * 32768 / (5 * d)) < 1e-12
     peaks = {"hbm_gbs": 6695.0, "pipes": {"fp32_fma_tflops": 77.0, "fp64_fma_tflops": 1.06}}
     info = bench.roofline_of("resid", 9.0, 30, cfg, "mixed", 1, 10, peaks, work=work)
     per_launch = amount / 3.0

@@ -833,12 +833,14 @@ def _golden_large_rff():
     return idx, E
 
 
-def large_rff_compare(binding, steps=3):
+def large_rff_compare(binding, steps=3, tuning=None):
     """The large single problem (n = 131072, d = 8192 random-Fourier features,
     c = 32, k = 5, g = 6, r = 3, q = 101, mixed, one refinement step): step
     time and evals/s from device-resident inputs, per-stage times, the
     interpolated solve's coefficient stream in GB/s, fold-0 errors against the
-    stored FP64-oracle values, and exact-Cholesky CV on the same GPU."""
+    stored FP64-oracle values, and exact-Cholesky CV on the same GPU.
+    ``tuning``: engine choices passed to Context.set_tuning (the command line's
+    --solve-engine / --update-engine), else the library's defaults."""
     import numpy as np
     import torch
 
@@ -852,6 +854,8 @@ def large_rff_compare(binding, steps=3):
     params = dict(n=cfg["n"], d=d, c=c, k=k, g=g, r=r, q=q, lam_lo=cfg["lo"], lam_hi=cfg["hi"], basis="cheb_log",
                   mode="mixed", refine_steps=1)
     ctx = binding.Context(exact_batch=g, **params)
+    if tuning:
+        ctx.set_tuning(**tuning)
     out = ctx._outputs(False)
     stream = torch.cuda.current_stream()
     ctx.run(X, Y, out=out)
@@ -879,7 +883,8 @@ def large_rff_compare(binding, steps=3):
     # fp32 planes once per substitution.
     nt = -(-d // 64)
     offdiag, p = nt * (nt + 1) // 2 - nt, r + 1
-    tensor_engine = (nt * (nt + 1) // 2) * p * 64 * 64 * 4 > 64 * 1024 * 1024
+    se = (tuning or {}).get("solve_engine", 2)
+    tensor_engine = se == 0 or (se == 2 and (nt * (nt + 1) // 2) * p * 64 * 64 * 4 > 64 * 1024 * 1024)
     if tensor_engine:
         ncb = -(-(q * c) // (64 if p <= 4 else 32))
         theta_bytes = k * ncb * offdiag * p * 2 * 64 * 64 * 4
@@ -901,6 +906,7 @@ def large_rff_compare(binding, steps=3):
                                   "engine": "tensor cores" if tensor_engine else "CUDA cores",
                                   "what": what + "; L2 holds none of a fold's planes at this size"},
            "err_vs_fp64": {"max_rel_E": err, "sample": f"fold 0, grid indices {idx}, stored oracle values"},
+           "tuning": ctx.tuning(),
            "device_status": binding.STATUS.get(info.code)}
     ctx.close()
     del ctx, out
@@ -1210,7 +1216,9 @@ def run_own(args):
         del X, Y
         torch.cuda.empty_cache()
         try:
-            large = large_rff_compare(binding)
+            eng = {nm: v for nm, v in (("solve_engine", args.solve_engine), ("update_engine", args.update_engine))
+                   if v is not None}
+            large = large_rff_compare(binding, tuning=eng)
         except Exception as exc:                      # context only: never costs the line
             large = {"unavailable": f"{type(exc).__name__}: {exc}"}
 
@@ -1241,7 +1249,10 @@ def run_own(args):
                    "parallelism": f"replicas x{world}", "tuning": tuning},
         "e2e": e2e,
         "gpu_launches": launches,
-        "roofline": roofline(stage_ms, cfg, w["mode"], refine, stage_steps, peaks, work=work, workload=args.workload),
+        # (the stored DRAM traffic was measured with the library's default engines)
+        "roofline": roofline(stage_ms, cfg, w["mode"], refine, stage_steps, peaks, work=work,
+                             workload=args.workload if args.solve_engine is None and args.update_engine is None
+                             else None),
         "kernels_roofline": {nm: {kk: v for kk, v in roofline_of(nm, ms_, la, cfg, w["mode"], refine, stage_steps,
                                                                 peaks, work=work).items()
                                   if kk in ("bound", "achieved", "peak", "unit", "frac", "stage_ms_per_step", "issue_rate")}

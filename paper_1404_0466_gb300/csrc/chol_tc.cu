@@ -78,7 +78,8 @@ k_chol_update_tc(const __grid_constant__ CUtensorMap mh, const __grid_constant__
     uint64_t* aempty = afull + NSTG;
     uint64_t* tfull = aempty + NSTG;
     uint64_t* tempty = tfull + 2;
-    uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+    uint64_t* mdone = tempty + 2;          // every MMA of the issuer complete (its exit)
+    uint32_t* tmem_slot = (uint32_t*)(mdone + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     volatile int* consumed = abort_flag + 1;
 
@@ -89,6 +90,7 @@ k_chol_update_tc(const __grid_constant__ CUtensorMap mh, const __grid_constant__
         mbar_init(bfull, 1);
         for (int s = 0; s < NSTG; ++s) { mbar_init(&afull[s], 1); mbar_init(&aempty[s], 1); }
         for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], EPI_WARPS); }
+        mbar_init(mdone, 1);
         *abort_flag = 0;
         *consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -164,6 +166,9 @@ k_chol_update_tc(const __grid_constant__ CUtensorMap mh, const __grid_constant__
                 tc5::commit(&tfull[b]);
                 *consumed = u + 1;
             }
+            // every MMA issued has completed before the tensor memory is freed
+            tc5::commit(mdone);
+            mbar_wait(mdone, 0);
         }
     } else {
         // ---- epilogue: out -= product; warp w reads lanes 32 (w % 4) .. +31 ----

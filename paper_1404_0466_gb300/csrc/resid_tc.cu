@@ -125,7 +125,8 @@ k_resid_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUte
     uint64_t* bempty = bfull + NB;
     uint64_t* tfull = bempty + NB;         // [2] accumulator set ready to drain
     uint64_t* tempty = tfull + 2;          // [2] accumulator set drained
-    uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+    uint64_t* mdone = tempty + 2;          // every MMA of the issuer complete (its exit)
+    uint32_t* tmem_slot = (uint32_t*)(mdone + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     volatile int* aconsumed = abort_flag + 1;
     volatile int* bconsumed = aconsumed + 1;
@@ -152,6 +153,7 @@ k_resid_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUte
         for (int s = 0; s < NA; ++s) { mbar_init(&afull[s], 1); mbar_init(&aempty[s], 1); }
         for (int s = 0; s < NB; ++s) { mbar_init(&bfull[s], 1); mbar_init(&bempty[s], 1); }
         for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], EPI_WARPS); }
+        mbar_init(mdone, 1);
         *abort_flag = 0;
         *aconsumed = 0;
         *bconsumed = 0;
@@ -237,6 +239,9 @@ k_resid_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUte
                 }
                 tc5::commit(&tfull[b]);   // set b holds the chunk's sums once its MMAs complete
             }
+            // every MMA issued has completed before the tensor memory is freed
+            tc5::commit(mdone);
+            mbar_wait(mdone, 0);
         }
     } else {
         // ---- drain: v = sum_m phi_m(col) acc_m, compensated totals ----

@@ -360,7 +360,8 @@ k_select(const double* __restrict__ Epart, const int* __restrict__ flags, const 
 size_t solve_smem_bytes(int eb, int p, int64_t c)
 {
     const int LG = 2, cb = pick_cb(c), vn = 16 / eb;
-    const int cbp = (cb + vn - 1) / vn * vn;
+    const int zvn = cb % vn == 0 ? vn : (cb % 2 == 0 ? 2 : 1);
+    const int cbp = (cb + zvn - 1) / zvn * zvn;
     const size_t zs = (size_t)2 * LG * (TB / 2) * cbp * eb, rb = (size_t)4 * LG * TB * cbp * eb;
     const size_t dinv = (size_t)LG * TB * TB * eb, hpb = (size_t)(TB / 2) * TB * eb;
     size_t most = 0;
@@ -400,6 +401,7 @@ static cudaError_t solve_dispatch(pichol_ctx* ctx, const SolveArgs& sa, cudaStre
     constexpr int LG = 2;
     switch (pick_cb(ctx->cfg.c)) {
     case 4: return solve_np<T, LG, 4, EXACT>(ctx, sa, s);
+    case 10: return solve_np<T, LG, 10, EXACT>(ctx, sa, s);
     case 12: return solve_np<T, LG, 12, EXACT>(ctx, sa, s);
     default: return solve_np<T, LG, 32, EXACT>(ctx, sa, s);
     }
@@ -430,6 +432,7 @@ static cudaError_t score_dispatch(pichol_ctx* ctx, const ScoreArgs& sc, cudaStre
 {
     switch (pick_cb(ctx->cfg.c)) {
     case 4: return run_score<T, 2, 4>(ctx, sc, s);
+    case 10:
     case 12: return run_score<T, 2, 12>(ctx, sc, s);
     default: return run_score<T, 1, 32>(ctx, sc, s);
     }

@@ -19,6 +19,14 @@ template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; static constexpr int N = 4; };
 template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
 
+// N consecutive values of T as one load (N = 4, 2 or 1 for float; 2 or 1 for double)
+template <typename T, int N> struct VecN;
+template <> struct VecN<float, 4> { using type = float4; };
+template <> struct VecN<float, 2> { using type = float2; };
+template <> struct VecN<float, 1> { using type = float; };
+template <> struct VecN<double, 2> { using type = double2; };
+template <> struct VecN<double, 1> { using type = double; };
+
 // Byte offset of element (row, col) of a row half (rows [32 h, 32 h + 32), all
 // 64 columns) of an fp32 plane staged by two TMA boxes of 32 x 32: the box of
 // columns [32 b, 32 b + 32) at b * 4096, rows of 128 bytes whose 16-byte
@@ -115,7 +123,10 @@ template <typename T, int LG, int CB, int NP, bool EXACT>
 struct SolveCfg {
     static constexpr int VN = Vec16<T>::N;
     static constexpr int ESZ = (int)sizeof(T);
-    static constexpr int CBP = (CB + VN - 1) / VN * VN;
+    // the staged solved blocks are read ZVN values at a time: 16 bytes when CB is a
+    // multiple of the 16-byte vector, else pairs (CB = 10: no padded columns)
+    static constexpr int ZVN = CB % VN == 0 ? VN : (CB % 2 == 0 ? 2 : 1);
+    static constexpr int CBP = (CB + ZVN - 1) / ZVN * ZVN;
     static constexpr int NPS = EXACT ? LG : NP;            // coefficient planes per tile
     // rows per thread: two when the accumulators (2 x LG x CBP) fit in registers
     static constexpr int RB = (CBP * ESZ <= 48) ? 2 : 1;
@@ -184,7 +195,8 @@ __global__ void __launch_bounds__(256, 2)
 k_solve(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
 {
     using C = SolveCfg<T, LG, CB, NP, EXACT>;
-    constexpr int VN = C::VN, CBP = C::CBP, NPS = C::NPS, ESZ = C::ESZ;
+    constexpr int VN = C::VN, CBP = C::CBP, NPS = C::NPS, ESZ = C::ESZ, ZVN = C::ZVN;
+    using ZV = typename VecN<T, ZVN>::type;
     constexpr int RB = C::RB, RPT = C::RPT, KW = C::KW, HPB = C::HPB, ZPER = C::ZPER;
     constexpr int HT = TB / 2;
     constexpr bool TMA = C::TMA;
@@ -397,12 +409,12 @@ k_solve(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
                                 }
                                 const T* zrow = zs + (l * HT + kk) * CBP;
 #pragma unroll
-                                for (int o = 0; o < CBP; o += VN) {
-                                    V z4 = *reinterpret_cast<const V*>(zrow + o);
-                                    T zz[VN];
-                                    memcpy(zz, &z4, 16);
+                                for (int o = 0; o < CBP; o += ZVN) {
+                                    ZV z4 = *reinterpret_cast<const ZV*>(zrow + o);
+                                    T zz[ZVN];
+                                    memcpy(zz, &z4, sizeof(ZV));
 #pragma unroll
-                                    for (int u = 0; u < VN; ++u)
+                                    for (int u = 0; u < ZVN; ++u)
 #pragma unroll
                                         for (int hh = 0; hh < RB; ++hh)
                                             acc[hh][l][o + u] = fma(lv[hh], zz[u], acc[hh][l][o + u]);
@@ -432,12 +444,12 @@ k_solve(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
                         for (int l = 0; l < LG; ++l) {
                             const T* zrow = zs + (l * HT + kk) * CBP;
 #pragma unroll
-                            for (int o = 0; o < CBP; o += VN) {
-                                V z4 = *reinterpret_cast<const V*>(zrow + o);
-                                T zz[VN];
-                                memcpy(zz, &z4, 16);
+                            for (int o = 0; o < CBP; o += ZVN) {
+                                ZV z4 = *reinterpret_cast<const ZV*>(zrow + o);
+                                T zz[ZVN];
+                                memcpy(zz, &z4, sizeof(ZV));
 #pragma unroll
-                                for (int u = 0; u < VN; ++u)
+                                for (int u = 0; u < ZVN; ++u)
 #pragma unroll
                                     for (int hh = 0; hh < RB; ++hh)
                                         acc[hh][l][o + u] = fma(lv[hh][l], zz[u], acc[hh][l][o + u]);
@@ -540,7 +552,7 @@ k_solve(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
 }
 
 // output columns a solve CTA carries for c outputs
-inline int pick_cb(int64_t c) { return c <= 4 ? 4 : (c <= 12 ? 12 : 32); }
+inline int pick_cb(int64_t c) { return c <= 4 ? 4 : (c == 9 || c == 10 ? 10 : (c <= 12 ? 12 : 32)); }
 
 // fp32 plane map (rows of 64 elements, 32 x 32 boxes, 128-byte swizzle) over
 // `planes` 64 x 64 planes starting at buf

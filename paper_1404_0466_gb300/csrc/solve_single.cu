@@ -13,6 +13,7 @@ static cudaError_t single_dispatch(pichol_ctx* ctx, const SolveArgs& sa, cudaStr
 {
     switch (pick_cb(ctx->cfg.c)) {
     case 4: return solve_np<T, 1, 4, EXACT>(ctx, sa, s);
+    case 10:
     case 12: return solve_np<T, 1, 12, EXACT>(ctx, sa, s);
     default: return solve_np<T, 1, 32, EXACT>(ctx, sa, s);
     }

@@ -33,7 +33,7 @@ namespace pichol {
 namespace stc {
 
 constexpr int BM = 128, BK = 32;
-constexpr int NA = 3;                          // A ring stages (one coefficient plane, hi + lo)
+constexpr int NA = 5;                          // A ring stages (one coefficient plane, hi + lo)
 constexpr int NB = 2;                          // B ring stages (one k-block of S^T, hi + lo)
 constexpr int A_BYTES = 2 * BM * BK * 4;       // 32 KB
 constexpr int EPI_WARPS = 8;
@@ -43,10 +43,14 @@ constexpr int TMEM_COLS = 512;
 template <int BN> struct Cfg {
     static constexpr int B_BYTES = 2 * BN * BK * 4;
     static constexpr int PHI_BYTES = MAX_P * BN * 4;
+    // The diagonal steps' buffers live in the A ring: the producer loads nothing for a
+    // step before the previous step's solved blocks are published, so the ring is idle
+    // from the step's last drain to that point.
     static constexpr int V_BYTES = BM * BN * 4;    // drained products, then the two right-hand sides
     static constexpr int Z_BYTES = TB * BN * 4;    // the first solved block of a pair
     static constexpr int T_BYTES = 2 * TB * (TB + 1) * 4;   // a staged inverse block and the pair's tile
-    static constexpr int SMEM = NA * A_BYTES + NB * B_BYTES + V_BYTES + Z_BYTES + T_BYTES + PHI_BYTES + 1024 + 256;
+    static_assert(V_BYTES + Z_BYTES + T_BYTES <= NA * A_BYTES, "diagonal-step buffers exceed the A ring");
+    static constexpr int SMEM = NA * A_BYTES + NB * B_BYTES + PHI_BYTES + 1024 + 256;
 };
 
 }  // namespace stc
@@ -301,8 +305,10 @@ __device__ __forceinline__ void k_solve_tc_epilogue(const SolveTcArgs& a, uint32
             const int col = e / TB, rr = e % TB;
             if (n0 + col < N) put_r(ia, n0 + col, rr, Zs[rr * BN + col]);
         }
-        // the solved rows feed the next steps' products through TMA (async proxy)
+        // the solved rows feed the next steps' products through TMA (async proxy), and
+        // the next step's copies overwrite the buffers above in the A ring
         asm volatile("fence.proxy.async.global;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         epi_sync();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(zready)) : "memory");
     }
@@ -319,11 +325,11 @@ k_solve_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUte
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* aring = smem;
     unsigned char* bring = aring + NA * A_BYTES;
-    float* Vs = (float*)(bring + NB * C::B_BYTES);          // [128][BN]
+    float* Vs = (float*)aring;                             // [128][BN]   (in the A ring, see Cfg)
     float* Zs = Vs + BM * BN;                              // [64][BN]
     float* Ds = Zs + TB * BN;                              // [64][65]: an inverse diagonal block
     float* Ls = Ds + TB * (TB + 1);                        // [64][65]: the tile between a pair's rows
-    float* phis = Ls + TB * (TB + 1);                      // [m][BN]
+    float* phis = (float*)(bring + NB * C::B_BYTES);       // [m][BN]
     uint64_t* afull = (uint64_t*)(phis + MAX_P * BN);
     uint64_t* aempty = afull + NA;
     uint64_t* bfull = aempty + NA;
@@ -331,8 +337,11 @@ k_solve_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUte
     uint64_t* tfull = bempty + NB;
     uint64_t* tempty = tfull + 2;
     uint64_t* zready = tempty + 2;
-    uint32_t* tmem_slot = (uint32_t*)(zready + 1);
+    uint64_t* mdone = zready + 1;          // every MMA of the issuer complete (its exit)
+    uint32_t* tmem_slot = (uint32_t*)(mdone + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    volatile int* aconsumed = abort_flag + 1;   // A / B stages whose copies the MMA issuer waited for
+    volatile int* bconsumed = aconsumed + 1;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int f = blockIdx.y, nb = blockIdx.x;
@@ -347,7 +356,10 @@ k_solve_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUte
         for (int s = 0; s < NB; ++s) { mbar_init(&bfull[s], 1); mbar_init(&bempty[s], 1); }
         for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], EPI_WARPS); }
         mbar_init(zready, EPI_WARPS);
+        mbar_init(mdone, 1);
         *abort_flag = 0;
+        *aconsumed = 0;
+        *bconsumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     for (int e = threadIdx.x; e < p * BN; e += blockDim.x) {
@@ -364,7 +376,7 @@ k_solve_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUte
     if (warp == 0) {
         if (lane == 0) {
             // ---- producer ----
-            int kbg = 0, qg = 0;
+            int kbg = 0, qg = 0, aiss = 0, biss = 0;
             for (int s = 0; s < nS && !*abort_flag; ++s) {
                 int i0, jlo, jhi;
                 s_step<DIR>(a, s, i0, jlo, jhi);
@@ -378,6 +390,7 @@ k_solve_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUte
                     mbar_expect_tx(&bfull[sb], C::B_BYTES);
                     tma_load_2d(bs, &mBh, &bfull[sb], x, brow);
                     tma_load_2d(bs + C::B_BYTES / 2, &mBl, &bfull[sb], x, brow);
+                    ++biss;
                     const int xa = (kb & 1) * BK;
                     for (int m = 0; m < p; ++m, ++qg) {
                         const int sa = qg % NA;
@@ -389,9 +402,14 @@ k_solve_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUte
                         tma_load_2d(as + BM / 2 * 128, &mAh, &afull[sa], xa, y1);
                         tma_load_2d(as + BM * 128, &mAl, &afull[sa], xa, y0);
                         tma_load_2d(as + BM * 128 + BM / 2 * 128, &mAl, &afull[sa], xa, y1);
+                        ++aiss;
                     }
                 }
             }
+            // wait (bounded) for copies that were issued but never consumed (at most one per
+            // stage, so no phase parity is ambiguous)
+            for (int q = *aconsumed; q < aiss; ++q) mbar_wait(&afull[q % NA], (q / NA) & 1);
+            for (int kb = *bconsumed; kb < biss; ++kb) mbar_wait(&bfull[kb % NB], (kb / NB) & 1);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -424,11 +442,16 @@ k_solve_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUte
                             tc5::mma_tf32(acc, tc5::sw128_desc(al + off), tc5::sw128_desc(bh + off), idesc, 1);
                         }
                         tc5::commit(&aempty[sa]);
+                        *aconsumed = qg + 1;
                     }
                     tc5::commit(&bempty[sb]);
+                    *bconsumed = kbg + 1;
                     tc5::commit(&tfull[b]);
                 }
             }
+            // every MMA issued has completed before the tensor memory is freed
+            tc5::commit(mdone);
+            mbar_wait(mdone, 0);
         }
     } else {
         k_solve_tc_epilogue<DIR, BN>(a, tmem, Vs, Zs, Ds, Ls, phis, tfull, tempty, zready, abort_flag, f, n0, N);

@@ -110,7 +110,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
     uint64_t* empty = full + STAGES;
     uint64_t* tfull = empty + STAGES;      // [2] accumulator buffer ready to drain
     uint64_t* tempty = tfull + 2;          // [2] accumulator buffer drained
-    uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+    uint64_t* mdone = tempty + 2;          // every MMA of the issuer complete (its exit)
+    uint32_t* tmem_slot = (uint32_t*)(mdone + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     volatile int* consumed = abort_flag + 1;
 
@@ -159,6 +160,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], EPI_WARPS);
         }
+        mbar_init(mdone, 1);
         *abort_flag = 0;
         *consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -229,6 +231,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
                 }
                 umma_commit(&tfull[b]);   // buffer b holds the chunk's sum once its MMAs complete
             }
+            // every MMA issued has completed before the tensor memory is freed
+            umma_commit(mdone);
+            mbar_wait(mdone, 0);
         }
     } else {
         // ---- drain: add every chunk's partial sum into compensated fp32 totals ----

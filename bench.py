@@ -314,7 +314,11 @@ def roofline_of(name, ms, launches, cfg, mode, refine, steps, peaks, work=None):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
 # stage's kernels from one ncu capture of the same code on the same workload,
 # for kernels unchanged since that capture.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    # k_solve<float, 2, 10, 4> (packed FMAs), both launches of one step of the mixed case
+    # (n = 32768, d = 2048): 1.03 GB read + 68.9 MB written, and 1.04 GB + 66.8 MB
+    ("mixed_ecc", "solve"): 1.10e9,
+}
 
 
 def roofline(stage_ms, cfg, mode, refine, steps, peaks, work=None, workload=None):

@@ -42,6 +42,7 @@ struct DiagArgs {
 };
 
 constexpr int DIAG_INV_THREADS = 256;
+constexpr int DIAG_INV_LD = TB + 2;   // row stride of the staged tiles: even, so entry pairs are aligned
 
 template <typename T, bool EXACT>
 __global__ void __launch_bounds__(DIAG_INV_THREADS)
@@ -52,13 +53,15 @@ k_diag_inv(DiagArgs a)
     constexpr int VN = Vec16<T>::N;
     constexpr int NV = TILE_ELEMS / VN / NT;       // 16-byte vectors per thread and plane
     constexpr int GP = 16 / NV;                     // planes whose loads are in flight together
+    constexpr int LD = DIAG_INV_LD;
+    using V2 = typename VecN<T, 2>::type;
     extern __shared__ __align__(16) unsigned char dsm[];
-    T (*Ls)[TB + 1] = reinterpret_cast<T (*)[TB + 1]>(dsm);
-    T (*Xs)[TB + 1] = reinterpret_cast<T (*)[TB + 1]>(dsm + sizeof(T) * TB * (TB + 1));
+    T (*Ls)[LD] = reinterpret_cast<T (*)[LD]>(dsm);
+    T (*Xs)[LD] = reinterpret_cast<T (*)[LD]>(dsm + sizeof(T) * TB * LD);
     __shared__ float rmax[TB], rmin[TB];
     __shared__ int rbad[TB];
     __shared__ T rinv[TB];
-    __shared__ T Ts[TB * TB / 4];     // T = B A^-1 of the lower-left blocks being doubled
+    __shared__ __align__(16) T Ts[TB * TB / 4];     // T = B A^-1 of the lower-left blocks being doubled
     const int i = blockIdx.x, t = a.t0 + blockIdx.y, f = blockIdx.z, tid = threadIdx.x;
     const int64_t ti = tile_index(i, i);
     const int np = EXACT ? 1 : a.p;
@@ -123,7 +126,9 @@ k_diag_inv(DiagArgs a)
     //   X[r][c] = -(sum_{c <= q < r} L[r][q] X[q][c]) / L[r][r].
     // Then the inverted blocks are doubled three times (h = 8, 16, 32): for
     //   L = [A 0; B C],  L^-1 = [A^-1 0; -C^-1 (B A^-1) C^-1],
-    // first T = B A^-1, then the lower-left block -C^-1 T, every entry by one thread.
+    // first T = B A^-1, then the lower-left block -C^-1 T, every two adjacent
+    // entries of a row by one thread (one load of B or C^-1 serves both; each
+    // entry's sum keeps its order).
     if (tid < TB) {
         const int b0 = (tid >> 3) * 8, c = b0 + (tid & 7);
         Xs[c][c] = rinv[c];
@@ -137,19 +142,34 @@ k_diag_inv(DiagArgs a)
 #pragma unroll 1
     for (int h = 8; h < TB; h *= 2) {
         const int hh = h * h, ne = (TB / (2 * h)) * hh;     // entries of all lower-left blocks: 32 h
-        for (int e = tid; e < ne; e += NT) {
-            const int b0 = (e / hh) * 2 * h, r = (e % hh) / h, c = e % h;
-            T s = T(0);
-            for (int k = c; k < h; ++k) s = fma(Ls[b0 + h + r][b0 + k], Xs[b0 + k][b0 + c], s);
-            Ts[e] = s;
+        for (int e = 2 * tid; e < ne; e += 2 * NT) {
+            const int b0 = (e / hh) * 2 * h, r = (e % hh) / h, c = e % h;   // c even
+            // (A^-1 is lower triangular: its entry (c, c + 1) is zero, so both sums start at k = c)
+            T s0 = T(0), s1 = T(0);
+            for (int k = c; k < h; ++k) {
+                const T bv = Ls[b0 + h + r][b0 + k];
+                const V2 x = *reinterpret_cast<const V2*>(&Xs[b0 + k][b0 + c]);
+                s0 = fma(bv, x.x, s0);
+                s1 = fma(bv, x.y, s1);
+            }
+            V2 o2;
+            o2.x = s0;
+            o2.y = s1;
+            *reinterpret_cast<V2*>(&Ts[e]) = o2;
         }
         __syncthreads();
-        for (int e = tid; e < ne; e += NT) {
+        for (int e = 2 * tid; e < ne; e += 2 * NT) {
             const int b0 = (e / hh) * 2 * h, r = (e % hh) / h, c = e % h;
             const T* tcol = Ts + (e / hh) * hh + c;
-            T s = T(0);
-            for (int k = 0; k <= r; ++k) s = fma(Xs[b0 + h + r][b0 + h + k], tcol[k * h], s);
-            Xs[b0 + h + r][b0 + c] = -s;
+            T s0 = T(0), s1 = T(0);
+            for (int k = 0; k <= r; ++k) {
+                const T cv = Xs[b0 + h + r][b0 + h + k];
+                const V2 t2 = *reinterpret_cast<const V2*>(tcol + k * h);
+                s0 = fma(cv, t2.x, s0);
+                s1 = fma(cv, t2.y, s1);
+            }
+            Xs[b0 + h + r][b0 + c] = -s0;
+            Xs[b0 + h + r][b0 + c + 1] = -s1;
         }
         __syncthreads();
     }
@@ -456,7 +476,7 @@ static cudaError_t eval_impl(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s
     da.per = (int)ctx->exact_batch;
     da.ntiles = ctx->ntiles;
     da.d = cf.d;
-    const int dsm = 2 * (int)sizeof(T) * TB * (TB + 1);
+    const int dsm = 2 * (int)sizeof(T) * TB * DIAG_INV_LD;
     static std::atomic<unsigned long long> set{0};
     {
         const cudaError_t ea = smem_limit_once(k_diag_inv<T, EXACT>, dsm, set);
@@ -607,7 +627,7 @@ static cudaError_t diag_solve_one_impl(pichol_ctx* ctx, const double* phi_row, c
         da.per = 1;
         da.ntiles = ctx->ntiles;
         da.d = cf.d;
-        const int dsm = 2 * (int)sizeof(T) * TB * (TB + 1);
+        const int dsm = 2 * (int)sizeof(T) * TB * DIAG_INV_LD;
         static std::atomic<unsigned long long> set{0};
         const cudaError_t ea = smem_limit_once(k_diag_inv<T, false>, dsm, set);
         if (ea != cudaSuccess) return ea;

@@ -27,6 +27,28 @@ template <> struct VecN<float, 1> { using type = float; };
 template <> struct VecN<double, 2> { using type = double2; };
 template <> struct VecN<double, 1> { using type = double; };
 
+// Two fp32 values as one 64-bit register pair, and the packed FMA on such pairs
+// (fma.rn.f32x2: two independent round-to-nearest FMAs, bit for bit the scalar
+// ones, in one issue slot).
+__device__ __forceinline__ unsigned long long f32x2_pack(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 f32x2_unpack(unsigned long long v)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f32x2_fma(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 // Byte offset of element (row, col) of a row half (rows [32 h, 32 h + 32), all
 // 64 columns) of an fp32 plane staged by two TMA boxes of 32 x 32: the box of
 // columns [32 b, 32 b + 32) at b * 4096, rows of 128 bytes whose 16-byte
@@ -313,7 +335,12 @@ k_solve(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
         }
     };
 
-    T acc[RB][LG][CBP];
+    // fp32: accumulators in column pairs, updated by packed FMAs (each column's sum
+    // keeps its order, so the results are those of scalar FMAs)
+    constexpr bool PAIRED = std::is_same<T, float>::value && ZVN >= 2;
+    constexpr int NACC = PAIRED ? CBP / 2 : CBP;
+    using AccT = typename std::conditional<PAIRED, unsigned long long, T>::type;
+    AccT acc[RB][LG][NACC];
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
         const bool back = pass == 1;
@@ -328,7 +355,7 @@ k_solve(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
 #pragma unroll
                 for (int l = 0; l < LG; ++l)
 #pragma unroll
-                    for (int o = 0; o < CBP; ++o) acc[hh][l][o] = T(0);
+                    for (int o = 0; o < NACC; ++o) acc[hh][l][o] = AccT(0);
             auto tj = [&](int it) { return back ? i + 1 + (it >> 1) : (it >> 1); };
             T zr[ZPER];
             auto load_z = [&](int it) {
@@ -408,16 +435,38 @@ k_solve(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
                                     lv[hh] = evalv(ve, l);
                                 }
                                 const T* zrow = zs + (l * HT + kk) * CBP;
+                                if constexpr (PAIRED) {
+                                    unsigned long long lb[RB];
 #pragma unroll
-                                for (int o = 0; o < CBP; o += ZVN) {
-                                    ZV z4 = *reinterpret_cast<const ZV*>(zrow + o);
-                                    T zz[ZVN];
-                                    memcpy(zz, &z4, sizeof(ZV));
+                                    for (int hh = 0; hh < RB; ++hh) lb[hh] = f32x2_pack(lv[hh], lv[hh]);
 #pragma unroll
-                                    for (int u = 0; u < ZVN; ++u)
+                                    for (int o = 0; o < CBP; o += ZVN) {
+                                        unsigned long long zp[ZVN >= 2 ? ZVN / 2 : 1];
+                                        if constexpr (ZVN == 4) {
+                                            const ulonglong2 z2 = *reinterpret_cast<const ulonglong2*>(zrow + o);
+                                            zp[0] = z2.x;
+                                            zp[ZVN / 2 - 1] = z2.y;
+                                        } else {
+                                            zp[0] = *reinterpret_cast<const unsigned long long*>(zrow + o);
+                                        }
 #pragma unroll
-                                        for (int hh = 0; hh < RB; ++hh)
-                                            acc[hh][l][o + u] = fma(lv[hh], zz[u], acc[hh][l][o + u]);
+                                        for (int u = 0; u < ZVN / 2; ++u)
+#pragma unroll
+                                            for (int hh = 0; hh < RB; ++hh)
+                                                acc[hh][l][o / 2 + u] = f32x2_fma(lb[hh], zp[u], acc[hh][l][o / 2 + u]);
+                                    }
+                                } else {
+#pragma unroll
+                                    for (int o = 0; o < CBP; o += ZVN) {
+                                        ZV z4 = *reinterpret_cast<const ZV*>(zrow + o);
+                                        T zz[ZVN];
+                                        memcpy(zz, &z4, sizeof(ZV));
+#pragma unroll
+                                        for (int u = 0; u < ZVN; ++u)
+#pragma unroll
+                                            for (int hh = 0; hh < RB; ++hh)
+                                                acc[hh][l][o + u] = fma(lv[hh], zz[u], acc[hh][l][o + u]);
+                                    }
                                 }
                             }
                         }
@@ -443,16 +492,38 @@ k_solve(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
 #pragma unroll
                         for (int l = 0; l < LG; ++l) {
                             const T* zrow = zs + (l * HT + kk) * CBP;
+                            if constexpr (PAIRED) {
+                                unsigned long long lb[RB];
 #pragma unroll
-                            for (int o = 0; o < CBP; o += ZVN) {
-                                ZV z4 = *reinterpret_cast<const ZV*>(zrow + o);
-                                T zz[ZVN];
-                                memcpy(zz, &z4, sizeof(ZV));
+                                for (int hh = 0; hh < RB; ++hh) lb[hh] = f32x2_pack(lv[hh][l], lv[hh][l]);
 #pragma unroll
-                                for (int u = 0; u < ZVN; ++u)
+                                for (int o = 0; o < CBP; o += ZVN) {
+                                    unsigned long long zp[ZVN >= 2 ? ZVN / 2 : 1];
+                                    if constexpr (ZVN == 4) {
+                                        const ulonglong2 z2 = *reinterpret_cast<const ulonglong2*>(zrow + o);
+                                        zp[0] = z2.x;
+                                        zp[ZVN / 2 - 1] = z2.y;
+                                    } else {
+                                        zp[0] = *reinterpret_cast<const unsigned long long*>(zrow + o);
+                                    }
 #pragma unroll
-                                    for (int hh = 0; hh < RB; ++hh)
-                                        acc[hh][l][o + u] = fma(lv[hh][l], zz[u], acc[hh][l][o + u]);
+                                    for (int u = 0; u < ZVN / 2; ++u)
+#pragma unroll
+                                        for (int hh = 0; hh < RB; ++hh)
+                                            acc[hh][l][o / 2 + u] = f32x2_fma(lb[hh], zp[u], acc[hh][l][o / 2 + u]);
+                                }
+                            } else {
+#pragma unroll
+                                for (int o = 0; o < CBP; o += ZVN) {
+                                    ZV z4 = *reinterpret_cast<const ZV*>(zrow + o);
+                                    T zz[ZVN];
+                                    memcpy(zz, &z4, sizeof(ZV));
+#pragma unroll
+                                    for (int u = 0; u < ZVN; ++u)
+#pragma unroll
+                                        for (int hh = 0; hh < RB; ++hh)
+                                            acc[hh][l][o + u] = fma(lv[hh][l], zz[u], acc[hh][l][o + u]);
+                                }
                             }
                         }
                     }
@@ -483,7 +554,14 @@ k_solve(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
 #pragma unroll
                             for (int o = 0; o < CBP; ++o) {
                                 T* dst = slot + (l * TB + rp + RPT * hh) * CBP + o;
-                                *dst = (round == 0) ? acc[hh][l][o] : *dst + acc[hh][l][o];
+                                T av;
+                                if constexpr (PAIRED) {
+                                    const float2 pr = f32x2_unpack(acc[hh][l][o >> 1]);
+                                    av = (o & 1) ? pr.y : pr.x;
+                                } else {
+                                    av = acc[hh][l][o];
+                                }
+                                *dst = (round == 0) ? av : *dst + av;
                             }
                 }
                 __syncthreads();

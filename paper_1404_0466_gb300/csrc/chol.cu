@@ -38,6 +38,10 @@ __device__ inline double prob_lambda(const ProbMap& pm, int pr, const double* la
     return (pm.warm > 0 && pr >= pm.per) ? lam_w[i] : lam_s[i];
 }
 
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int N = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
+
 // A = H_f + lambda I on the lower tiles (H_f tile-major from the Gram step);
 // identity on the padding.
 template <typename T>
@@ -52,16 +56,26 @@ k_chol_init(const T* __restrict__ Hf, int64_t d, int64_t ntiles, ProbMap pm,
     if (prob_dead(pm, pr)) return;
     const int f = pr / pm.per;
     const double shift = prob_lambda(pm, pr, lam, lam_s, lam_w);
-    const T* src = Hf + ((int64_t)f * ntiles + blockIdx.x) * TILE_ELEMS;
-    T* dst = F + ((int64_t)pr * ntiles + blockIdx.x) * TILE_ELEMS;
-    for (int e = threadIdx.x; e < TILE_ELEMS; e += 256) {
-        const int r = e / TB, c = e % TB;
-        const int64_t row = (int64_t)I * TB + r, col = (int64_t)J * TB + c;
-        T v;
-        if (I == J && c > r) v = T(0);
-        else if (row >= d || col >= d) v = (row == col) ? T(1) : T(0);
-        else v = (row == col) ? (T)((double)src[e] + shift) : src[e];
-        dst[e] = v;
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::N, NV = TILE_ELEMS / VN / 256;   // 16-byte vectors per thread
+    const V* src = reinterpret_cast<const V*>(Hf + ((int64_t)f * ntiles + blockIdx.x) * TILE_ELEMS);
+    V* dst = reinterpret_cast<V*>(F + ((int64_t)pr * ntiles + blockIdx.x) * TILE_ELEMS);
+    V in[NV];
+#pragma unroll
+    for (int u = 0; u < NV; ++u) in[u] = src[threadIdx.x + 256 * u];   // all loads in flight
+#pragma unroll
+    for (int u = 0; u < NV; ++u) {
+        const int e0 = VN * (threadIdx.x + 256 * u), r = e0 / TB;
+        T* x = reinterpret_cast<T*>(&in[u]);
+#pragma unroll
+        for (int j = 0; j < VN; ++j) {
+            const int c = e0 % TB + j;
+            const int64_t row = (int64_t)I * TB + r, col = (int64_t)J * TB + c;
+            if (I == J && c > r) x[j] = T(0);
+            else if (row >= d || col >= d) x[j] = (row == col) ? T(1) : T(0);
+            else if (row == col) x[j] = (T)((double)x[j] + shift);
+        }
+        dst[threadIdx.x + 256 * u] = in[u];
     }
 }
 
@@ -205,9 +219,6 @@ k_chol_diag(T* __restrict__ F, int64_t ntiles, int J, int64_t d, ProbMap pm, Dev
     }
 }
 
-template <typename T> struct Vec16;
-template <> struct Vec16<float> { using type = float4; static constexpr int N = 4; };
-template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
 
 // Copy a row-major 64 x 64 tile into shared memory rows of LD elements (16-byte moves).
 template <typename T, int LD, int NT>
@@ -360,29 +371,61 @@ k_chol_update(T* __restrict__ F, int64_t ntiles, int nt, int J, int first, int c
         cp_async_wait<1>();                        // L_KJ and L_IJ have landed
         __syncthreads();
         T acc[RA][RC];
+        if constexpr (std::is_same<T, float>::value) {
+            // fp32: packed FMAs over pairs of k (even and odd k in the two halves of a
+            // register pair, added at the end): half the FMA issue slots
+            unsigned long long acc2[RA][RC];
 #pragma unroll
-        for (int a = 0; a < RA; ++a)
+            for (int a = 0; a < RA; ++a)
 #pragma unroll
-            for (int b = 0; b < RC; ++b) acc[a][b] = T(0);
+                for (int b = 0; b < RC; ++b) acc2[a][b] = 0ull;
 #pragma unroll 2
-        for (int k0 = 0; k0 < TB; k0 += VN) {
-            T av[RA][VN], bv[RC][VN];
+            for (int k0 = 0; k0 < TB; k0 += 4) {
+                ulonglong2 av[RA], bv[RC];
 #pragma unroll
-            for (int a = 0; a < RA; ++a) {
-                V v = *reinterpret_cast<const V*>(Au + (ty + TY * a) * LD + k0);
-                memcpy(av[a], &v, sizeof(V));
-            }
+                for (int a = 0; a < RA; ++a) av[a] = *reinterpret_cast<const ulonglong2*>(Au + (ty + TY * a) * LD + k0);
 #pragma unroll
-            for (int b = 0; b < RC; ++b) {
-                V v = *reinterpret_cast<const V*>(Bs + (tx + 8 * b) * LD + k0);
-                memcpy(bv[b], &v, sizeof(V));
-            }
-#pragma unroll
-            for (int e = 0; e < VN; ++e)
+                for (int b = 0; b < RC; ++b) bv[b] = *reinterpret_cast<const ulonglong2*>(Bs + (tx + 8 * b) * LD + k0);
 #pragma unroll
                 for (int a = 0; a < RA; ++a)
 #pragma unroll
-                    for (int b = 0; b < RC; ++b) acc[a][b] = fma(av[a][e], bv[b][e], acc[a][b]);
+                    for (int b = 0; b < RC; ++b) {
+                        acc2[a][b] = f32x2_fma(av[a].x, bv[b].x, acc2[a][b]);
+                        acc2[a][b] = f32x2_fma(av[a].y, bv[b].y, acc2[a][b]);
+                    }
+            }
+#pragma unroll
+            for (int a = 0; a < RA; ++a)
+#pragma unroll
+                for (int b = 0; b < RC; ++b) {
+                    const float2 h = f32x2_unpack(acc2[a][b]);
+                    acc[a][b] = h.x + h.y;
+                }
+        } else {
+#pragma unroll
+            for (int a = 0; a < RA; ++a)
+#pragma unroll
+                for (int b = 0; b < RC; ++b) acc[a][b] = T(0);
+#pragma unroll 2
+            for (int k0 = 0; k0 < TB; k0 += VN) {
+                T av[RA][VN], bv[RC][VN];
+#pragma unroll
+                for (int a = 0; a < RA; ++a) {
+                    V v = *reinterpret_cast<const V*>(Au + (ty + TY * a) * LD + k0);
+                    memcpy(av[a], &v, sizeof(V));
+                }
+#pragma unroll
+                for (int b = 0; b < RC; ++b) {
+                    V v = *reinterpret_cast<const V*>(Bs + (tx + 8 * b) * LD + k0);
+                    memcpy(bv[b], &v, sizeof(V));
+                }
+#pragma unroll
+                for (int e = 0; e < VN; ++e)
+#pragma unroll
+                    for (int a = 0; a < RA; ++a)
+#pragma unroll
+                        for (int b = 0; b < RC; ++b) acc[a][b] = fma(av[a][e], bv[b][e], acc[a][b]);
+            }
         }
 #pragma unroll
         for (int a = 0; a < RA; ++a)

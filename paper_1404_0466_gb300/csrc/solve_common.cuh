@@ -27,27 +27,6 @@ template <> struct VecN<float, 1> { using type = float; };
 template <> struct VecN<double, 2> { using type = double2; };
 template <> struct VecN<double, 1> { using type = double; };
 
-// Two fp32 values as one 64-bit register pair, and the packed FMA on such pairs
-// (fma.rn.f32x2: two independent round-to-nearest FMAs, bit for bit the scalar
-// ones, in one issue slot).
-__device__ __forceinline__ unsigned long long f32x2_pack(float lo, float hi)
-{
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ float2 f32x2_unpack(unsigned long long v)
-{
-    float2 r;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
-    return r;
-}
-__device__ __forceinline__ unsigned long long f32x2_fma(unsigned long long a, unsigned long long b, unsigned long long c)
-{
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
 
 // Byte offset of element (row, col) of a row half (rows [32 h, 32 h + 32), all
 // 64 columns) of an fp32 plane staged by two TMA boxes of 32 x 32: the box of

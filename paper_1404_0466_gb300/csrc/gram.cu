@@ -428,9 +428,13 @@ cudaError_t launch_set_evals(pichol_ctx* ctx, const double* lam_t_host, cudaStre
     return cudaSuccess;
 }
 
-// H_f = sum_{j != f} G_j on the lower tiles, tile-major, summed in double in
-// increasing j (the padding stays zero; the factorisation input adds the
-// shift and the identity on the padding).
+// H_f = sum_{j != f} G_j on the lower tiles, tile-major, summed in increasing j
+// (the padding stays zero; the factorisation input adds the shift and the
+// identity on the padding).  FP64 mode sums in double.  In fp32 the sum is
+// compensated on the FP32 pipes (TwoSum per term, the rounding errors added at
+// the end), which keeps it within an ulp of the correctly rounded sum; a double
+// accumulation would occupy GB300's FP64 unit (one warp instruction per 64
+// cycles) for most of the kernel.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_hf_tiles(const T* __restrict__ G, int k, int64_t dp, int64_t ntiles, T* __restrict__ Hf)
@@ -439,6 +443,61 @@ k_hf_tiles(const T* __restrict__ G, int k, int64_t dp, int64_t ntiles, T* __rest
     tile_coords(blockIdx.x, I, J);
     const int f = blockIdx.y;
     T* dst = Hf + ((int64_t)f * ntiles + blockIdx.x) * TILE_ELEMS;
+    if constexpr (std::is_same<T, float>::value) {
+        // thread: four 16-byte groups (rows r, r + 16, r + 32, r + 48; columns 4 cc .. 4 cc + 3)
+        const int cc = threadIdx.x & 15, r0 = threadIdx.x >> 4;
+        float s[16], comp[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) { s[u] = 0.0f; comp[u] = 0.0f; }
+        bool first = true;
+        for (int j0 = 0; j0 < k; j0 += 2) {
+            float4 x[2][4];                       // two blocks' loads in flight
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = j0 + h;
+                if (j < k && j != f) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int64_t row = (int64_t)I * TB + r0 + 16 * u, col = (int64_t)J * TB + 4 * cc;
+                        x[h][u] = *reinterpret_cast<const float4*>(G + (int64_t)j * dp * dp + row * dp + col);
+                    }
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = j0 + h;
+                if (j < k && j != f) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float* xv = reinterpret_cast<const float*>(&x[h][u]);
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) {
+                            const int q = 4 * u + w;
+                            if (first) {
+                                s[q] = xv[w];
+                            } else {          // TwoSum: s + x = t + err exactly
+                                const float t = s[q] + xv[w];
+                                const float bp = t - s[q];
+                                comp[q] += (s[q] - (t - bp)) + (xv[w] - bp);
+                                s[q] = t;
+                            }
+                        }
+                    }
+                    first = false;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            float4 o;
+            o.x = s[4 * u] + comp[4 * u];
+            o.y = s[4 * u + 1] + comp[4 * u + 1];
+            o.z = s[4 * u + 2] + comp[4 * u + 2];
+            o.w = s[4 * u + 3] + comp[4 * u + 3];
+            *reinterpret_cast<float4*>(dst + (r0 + 16 * u) * TB + 4 * cc) = o;
+        }
+        return;
+    }
     for (int e = threadIdx.x; e < TILE_ELEMS; e += 256) {
         const int r = e / TB, c = e % TB;
         const int64_t row = (int64_t)I * TB + r, col = (int64_t)J * TB + c;

@@ -1238,7 +1238,12 @@ def run_own(args):
             oracle_exact = {"unavailable": f"{type(exc).__name__}: {exc}"}
     # the FP32 and FP64 pipes measured on this GPU: the denominators of the ALU-bound stages
     pipes = {"fp32_fma_tflops": binding.probe_fma(False, 1 << 14), "fp64_fma_tflops": binding.probe_fma(True, 1 << 12),
-             "method": "8 independent FMA chains per thread, 8 CTAs of 256 threads per SM (pichol_probe_fma)"}
+             "method": "8 independent FMA chains per thread, 8 CTAs of 256 threads per SM (pichol_probe_fma)",
+             # context for the tcgen05 stages (their denominator stays the TF32 figure derived from
+             # the measured bf16 GEMM): the tensor pipe's own rate on operands in shared memory
+             "tf32_mma_tflops": {str(n): binding.probe_mma(n, 1 << 15) for n in (64, 128, 256)},
+             "tf32_mma_method": "tcgen05.mma kind::tf32, M = 128, K = 8, one CTA per SM issuing back to back "
+                                "(pichol_probe_mma)"}
     peaks = load_peaks()
     peaks["pipes"] = pipes
     stage_ms = {s: v for s, v in stages.items() if v[1] > 0}

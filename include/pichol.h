@@ -375,6 +375,16 @@ PICHOL_API pichol_status pichol_check_rsqrt(int64_t n, uint64_t seed, double* ma
  * context; synchronises the device. */
 PICHOL_API pichol_status pichol_probe_fma(int32_t fp64, int64_t iters, double* tflops);
 
+/* Issue rate of the tensor cores for tcgen05.mma kind::tf32 with M = 128,
+ * K = 8 and N = n_cols (64, 128 or 256), for the roofline of the tcgen05
+ * contractions: one CTA per SM issues `iters` MMAs (1 .. 2^22) back to back
+ * on zeroed shared-memory operands into tensor memory, on the legacy default
+ * stream, timed with CUDA events (the second of two runs).  *tflops (host) =
+ * 2 x 128 x n_cols x 8 x MMAs / seconds / 1e12.  PICHOL_ERR_TIMEOUT if the
+ * bounded completion wait ran out.  Needs no context; synchronises the device
+ * and allocates (and frees) one int of device memory. */
+PICHOL_API pichol_status pichol_probe_mma(int32_t n_cols, int64_t iters, double* tflops);
+
 /* Number of kernel launches this context has enqueued since creation. */
 PICHOL_API int64_t pichol_launch_count(const pichol_ctx* ctx);
 

@@ -47,7 +47,7 @@ EXPORTS = [
     "pichol_batch_run", "pichol_batch_get_info", "pichol_batch_launch_count", "pichol_batch_destroy",
     "pichol_batch_set_timing", "pichol_batch_stage_times",
     "pichol_get_tuning", "pichol_set_tuning", "pichol_batch_set_tuning", "pichol_check_timeout",
-    "pichol_mchol", "pichol_mchol_levels", "pichol_check_rsqrt", "pichol_eval_pinrmse", "pichol_probe_fma",
+    "pichol_mchol", "pichol_mchol_levels", "pichol_check_rsqrt", "pichol_eval_pinrmse", "pichol_probe_fma", "pichol_probe_mma",
     "pichol_get_state", "pichol_resume", "pichol_version", "pichol_debug_guards", "pichol_debug_build",
 ]
 STAGES = ["gram", "xty", "setup", "chol_init", "chol_diag", "chol_panel", "chol_update", "fit",
@@ -121,6 +121,7 @@ def lib():
         "pichol_check_rsqrt": ([i64, ctypes.c_uint64, vp, vp], ctypes.c_int),
         "pichol_eval_pinrmse": ([vp, vp, vp, vp], ctypes.c_int),
         "pichol_probe_fma": ([i32, i64, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "pichol_probe_mma": ([i32, i64, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "pichol_get_state": ([vp, ctypes.POINTER(i32)], ctypes.c_int),
         "pichol_resume": ([vp, i32], ctypes.c_int),
         "pichol_version": ([], i32),
@@ -519,6 +520,13 @@ def probe_fma(fp64: bool, iters: int = 1 << 14) -> float:
     """Measured FMA throughput of the FP32 or FP64 pipes in TFLOP/s (pichol_probe_fma)."""
     out = ctypes.c_double(0.0)
     _check(lib().pichol_probe_fma(1 if fp64 else 0, int(iters), ctypes.byref(out)), "pichol_probe_fma")
+    return float(out.value)
+
+
+def probe_mma(n_cols: int = 128, iters: int = 1 << 15) -> float:
+    """Measured tcgen05.mma kind::tf32 rate (M = 128, K = 8, N = n_cols) in TFLOP/s (pichol_probe_mma)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().pichol_probe_mma(int(n_cols), int(iters), ctypes.byref(out)), "pichol_probe_mma")
     return float(out.value)
 
 

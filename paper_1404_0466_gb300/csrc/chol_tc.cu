@@ -149,19 +149,9 @@ k_chol_update_tc(const __grid_constant__ CUtensorMap mh, const __grid_constant__
                 const uint32_t abase = smem_u32(aring + s * A_BYTES);
                 const uint32_t acc = tmem + (uint32_t)(b * BN);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-#pragma unroll
-                    for (int kk = 0; kk < BK / 8; ++kk) {
-                        const uint32_t off = kk * 32;
-                        const uint64_t ah = tc5::sw128_desc(abase + a_off(h, 0, 0) + off);
-                        const uint64_t al = tc5::sw128_desc(abase + a_off(h, 1, 0) + off);
-                        const uint64_t bh = tc5::sw128_desc(bbase + b_off(h, 0) + off);
-                        const uint64_t bl = tc5::sw128_desc(bbase + b_off(h, 1) + off);
-                        tc5::mma_tf32(acc, ah, bh, idesc, (h | kk) != 0);
-                        tc5::mma_tf32(acc, ah, bl, idesc, 1);
-                        tc5::mma_tf32(acc, al, bh, idesc, 1);
-                    }
-                }
+                for (int h = 0; h < 2; ++h)
+                    tc5::mma_split3_k32(acc, abase + a_off(h, 0, 0), abase + a_off(h, 1, 0), bbase + b_off(h, 0),
+                                        bbase + b_off(h, 1), idesc, h == 0);
                 tc5::commit(&aempty[s]);
                 tc5::commit(&tfull[b]);
                 *consumed = u + 1;

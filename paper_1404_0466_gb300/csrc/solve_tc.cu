@@ -434,13 +434,7 @@ k_solve_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUte
                         tc5::fence_after();
                         const uint32_t ah = smem_u32(aring + sa * A_BYTES), al = ah + BM * 128;
                         const uint32_t acc = tmem + (uint32_t)((b * p + m) * BN);
-#pragma unroll
-                        for (int kk = 0; kk < BK / 8; ++kk) {
-                            const uint32_t off = kk * 32;
-                            tc5::mma_tf32(acc, tc5::sw128_desc(ah + off), tc5::sw128_desc(bh + off), idesc, kk != 0);
-                            tc5::mma_tf32(acc, tc5::sw128_desc(ah + off), tc5::sw128_desc(bl + off), idesc, 1);
-                            tc5::mma_tf32(acc, tc5::sw128_desc(al + off), tc5::sw128_desc(bh + off), idesc, 1);
-                        }
+                        tc5::mma_split3_k32(acc, ah, al, bh, bl, idesc, true);
                         tc5::commit(&aempty[sa]);
                         *aconsumed = qg + 1;
                     }

@@ -217,13 +217,13 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
                     const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
                     const uint32_t ah = base, al = base + TILE_BYTES, bh = base + 2 * TILE_BYTES,
                                    bl = base + 3 * TILE_BYTES;
+                    if (a.passes == 3) {
+                        tc5::mma_split3_k32(acc, ah, al, bh, bl, idesc, kb == k0);
+                    } else {
 #pragma unroll
-                    for (int kk = 0; kk < BK / 8; ++kk) {
-                        const uint32_t off = kk * 32;   // 8 tf32 = 32 bytes along K
-                        umma_tf32(acc, sw128_desc(ah + off), sw128_desc(bh + off), idesc, ((kb - k0) | kk) != 0);
-                        if (a.passes == 3) {
-                            umma_tf32(acc, sw128_desc(ah + off), sw128_desc(bl + off), idesc, 1);
-                            umma_tf32(acc, sw128_desc(al + off), sw128_desc(bh + off), idesc, 1);
+                        for (int kk = 0; kk < BK / 8; ++kk) {
+                            const uint32_t off = kk * 32;   // 8 tf32 = 32 bytes along K
+                            umma_tf32(acc, sw128_desc(ah + off), sw128_desc(bh + off), idesc, ((kb - k0) | kk) != 0);
                         }
                     }
                     umma_commit(&empty[s]);

@@ -226,6 +226,9 @@ def test_new_entry_points_check_arguments_without_a_gpu(L):
     assert L.pichol_probe_fma(0, 0, ctypes.byref(out)) == 1
     assert L.pichol_probe_fma(1, (1 << 24) + 1, ctypes.byref(out)) == 1
     assert L.pichol_probe_fma(0, 1024, None) == 1
+    for n_cols, iters in ((32, 1024), (96, 1024), (128, 0), (256, (1 << 22) + 1)):
+        assert L.pichol_probe_mma(n_cols, iters, ctypes.byref(out)) == 1
+    assert L.pichol_probe_mma(128, 1024, None) == 1
     assert L.pichol_check_rsqrt(0, 1, E, None) == 1
     assert L.pichol_check_rsqrt((1 << 32) + 1, 1, E, None) == 1
     assert L.pichol_check_rsqrt(1024, 1, None, None) == 1

@@ -395,6 +395,17 @@ def test_fma_probe_reports_plausible_pipe_rates(torch_mod):
     assert 0.05 < f64 < f32 / 8, (f64, f32)
 
 
+def test_mma_probe_reports_plausible_tensor_rates(torch_mod):
+    """tcgen05.mma kind::tf32 at M = 128, K = 8: hundreds of TFLOP/s on this part,
+    and a wider N is never slower per flop than a narrower one."""
+    from paper_1404_0466_gb300 import binding
+    r64 = binding.probe_mma(64, 1 << 12)
+    r128 = binding.probe_mma(128, 1 << 12)
+    r256 = binding.probe_mma(256, 1 << 12)
+    assert 100.0 < r64 < 5000.0 and 100.0 < r128 < 5000.0 and 100.0 < r256 < 5000.0, (r64, r128, r256)
+    assert r256 > 0.9 * r128 and r128 > 0.9 * r64, (r64, r128, r256)
+
+
 def test_unusable_interpolated_diagonal_scores_inf(torch_mod):
     """Over twelve decades with g = r + 1 = 3 the interpolated factor's diagonal
     turns negative on part of the grid: the oracle flags 27 of the 63 (fold,

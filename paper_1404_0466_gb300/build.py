@@ -22,7 +22,7 @@ LIB = PKG / "libpichol.so"
 # workspace section, checked by pichol_get_info)
 BUILD_DEBUG = PKG / "_build_debug"
 LIB_DEBUG = PKG / "libpichol_debug.so"
-SOURCES = ["api.cu", "gram.cu", "chol.cu", "fit.cu", "solve.cu", "tc_gemm.cu", "grad.cu", "batch.cu", "mchol.cu", "pinrmse.cu", "resid.cu", "solve_single.cu", "probe.cu", "resid_tc.cu", "chol_tc.cu", "solve_tc.cu"]
+SOURCES = ["api.cu", "gram.cu", "chol.cu", "fit.cu", "solve.cu", "tc_gemm.cu", "grad.cu", "batch.cu", "mchol.cu", "pinrmse.cu", "resid.cu", "solve_single.cu", "probe.cu", "resid_tc.cu", "chol_tc.cu", "solve_tc.cu", "solve_wave.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

@@ -99,6 +99,8 @@ size_t plan(pichol_ctx* ctx, char* base)
     ctx->Epart = (double*)take((size_t)(k * q * nt * sizeof(double)));
     ctx->E = (double*)take((size_t)(k * q * sizeof(double)));
     ctx->flags = (int*)take((size_t)(k * q * nt * sizeof(int)));
+    ctx->wave_cap = k * q * nt;
+    ctx->wave = (int*)take((size_t)((2 + 2 * ctx->wave_cap) * sizeof(int)));
     ctx->dmax = (float*)take((size_t)(k * q * nt * sizeof(float)));
     ctx->dmin = (float*)take((size_t)(k * q * nt * sizeof(float)));
     return off;

@@ -242,6 +242,8 @@ struct pichol_ctx {
     double* Epart;       // k x q x nt
     double* E;           // k x q
     int* flags;          // k x q x nt (per-tile diagonal checks: bit0 nonpositive)
+    int* wave;           // wavefront solve: 2 tickets, then 2 x wave_cap row flags
+    int64_t wave_cap;    // k x q x nt
     float* dmax;         // k x q x nt max |diag| of the tile
     float* dmin;         // k x q x nt min |diag| of the tile
 

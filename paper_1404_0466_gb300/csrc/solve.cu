@@ -416,8 +416,15 @@ cudaError_t plane_map(CUtensorMap* m, const void* buf, int64_t planes)
 template <typename T, bool EXACT>
 static cudaError_t solve_dispatch(pichol_ctx* ctx, const SolveArgs& sa, cudaStream_t s)
 {
-    if (sa.tcount == 1 || (int64_t)ctx->cfg.k * sa.tcount <= ctx->nsm)
+    if (sa.tcount == 1 || (int64_t)ctx->cfg.k * sa.tcount <= ctx->nsm) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (ctx->tune.solve_engine != 1) {           // the wavefront unless the CUDA-core chain is asked for
+                const cudaError_t e = launch_solve_wave(ctx, sa, EXACT, s);
+                if (e != cudaErrorNotSupported) return e;
+            }
+        }
         return launch_solve_single(ctx, sa, EXACT, s);
+    }
     constexpr int LG = 2;
     switch (pick_cb(ctx->cfg.c)) {
     case 4: return solve_np<T, LG, 4, EXACT>(ctx, sa, s);

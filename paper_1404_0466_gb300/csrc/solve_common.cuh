@@ -659,5 +659,8 @@ inline cudaError_t solve_np(pichol_ctx* ctx, const SolveArgs& sa, cudaStream_t s
 
 // the solves of a few systems with one-lambda CTAs (exact: factor tiles)
 cudaError_t launch_solve_single(pichol_ctx* ctx, const SolveArgs& sa, bool exact, cudaStream_t s);
+// few systems as a wavefront over tile rows (solve_wave.cu); cudaErrorNotSupported
+// where it does not apply
+cudaError_t launch_solve_wave(pichol_ctx* ctx, const SolveArgs& sa, bool exact, cudaStream_t s);
 
 }  // namespace pichol

@@ -18,9 +18,16 @@
 // on a CTA that has not started, whatever the number of CTAs resident.  Every
 // wait is bounded: a CTA whose wait runs out latches PICHOL_ERR_TIMEOUT and
 // publishes -1, and a CTA that sees -1 stops at once and publishes -1 too.
+//
+// Publication: every thread stores its outputs, the CTA meets at a barrier and
+// thread 0 stores the flag with release semantics at GPU scope; release is
+// cumulative, so the outputs the barrier ordered before it are visible to any
+// thread that acquires the flag.  The waiting thread polls with relaxed loads and
+// takes one acquire fence when it sees the flag set.
 #include "internal.cuh"
 #include "solve_common.cuh"
 
+#include <cstdint>
 #include <cstring>
 
 namespace pichol {
@@ -31,11 +38,15 @@ constexpr int WT = 256;           // threads per CTA
 constexpr int WNP = 4;            // coefficient planes held per tile (p <= 4)
 constexpr int WNJ = 8;            // output columns per thread: c <= 32
 
-__device__ __forceinline__ int flag_acquire(const int* p)
+__device__ __forceinline__ int flag_poll(const int* p)
 {
     int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+__device__ __forceinline__ void fence_acquire_gpu()
+{
+    asm volatile("fence.acq_rel.gpu;\n" ::: "memory");
 }
 __device__ __forceinline__ void flag_release(int* p, int v)
 {
@@ -45,13 +56,14 @@ __device__ __forceinline__ void flag_release(int* p, int v)
 }  // namespace
 
 // One (system, tile row) per CTA; `ticket` and `flags` (S x nt ints) start at zero.
-template <bool EXACT, int DIR>
+// NJ: output columns per thread (columns g, g + 4, ..: 4 NJ >= c).
+template <bool EXACT, int DIR, int NJ>
 __global__ void __launch_bounds__(WT)
 k_solve_wave(const SolveArgs a, int* __restrict__ ticket, int* __restrict__ flags)
 {
-    __shared__ float Ls[TB][TB + 1];      // tile applied to the solved block, as L[row][k]
-    __shared__ float Zs[TB][WNJ * 4];     // a solved block (rows k, columns o)
-    __shared__ float Ds[TB][TB + 1];      // the diagonal block's inverse (transposed backward)
+    __shared__ float Ls[TB][TB + 1];                  // tile applied to the solved block, as L[row][k]
+    __shared__ __align__(16) float Zs[TB * NJ * 4];   // a solved block, row-major with row stride c
+    __shared__ float Ds[TB][TB + 1];                  // the diagonal block's inverse (transposed backward)
     __shared__ int sh_tk, sh_bad;
     const int tid = threadIdx.x;
     const int S = (int)(a.tcount * (int64_t)gridDim.y);   // gridDim.y = k folds
@@ -69,6 +81,9 @@ k_solve_wave(const SolveArgs a, int* __restrict__ ticket, int* __restrict__ flag
     int* fl = flags + (int64_t)sidx * nt;
     const int64_t sysb = ((int64_t)f * a.q + t) * a.dp * a.c;
     const float* zsrc = (const float*)(DIR == 0 ? a.zbuf : a.out);   // this pass's solved blocks
+    // a block is 64 c floats from a 256-byte multiple of the base: one 16-byte load per
+    // thread (two for c > 16) when the base is 16-byte aligned
+    const bool zvec = ((reinterpret_cast<uintptr_t>(zsrc) & 15) == 0);
     float* dst = (float*)(DIR == 0 ? a.zbuf : a.out);
     const float* src = (const float*)a.src;
     float w[WNP];
@@ -97,9 +112,9 @@ k_solve_wave(const SolveArgs a, int* __restrict__ ticket, int* __restrict__ flag
     };
     // output ownership: row r, columns g + 4 j
     const int r = tid >> 2, g = tid & 3;
-    float acc[WNJ];
+    float acc[NJ];
 #pragma unroll
-    for (int j = 0; j < WNJ; ++j) acc[j] = 0.0f;
+    for (int j = 0; j < NJ; ++j) acc[j] = 0.0f;
     // what the diagonal step needs and no flag guards, loaded first so that the step
     // after the last wait costs no memory round trip for it: the inverse (into Ds)
     // and the right-hand side of this thread's outputs (forward only; backward, the
@@ -113,9 +128,9 @@ k_solve_wave(const SolveArgs a, int* __restrict__ ticket, int* __restrict__ flag
             else Ds[e % TB][e / TB] = x;
         }
     }
-    float bv[WNJ];
+    float bv[NJ];
 #pragma unroll
-    for (int j = 0; j < WNJ; ++j) {
+    for (int j = 0; j < NJ; ++j) {
         const int o = g + 4 * j;
         bv[j] = 0.0f;
         if (o < c) {
@@ -158,8 +173,9 @@ k_solve_wave(const SolveArgs a, int* __restrict__ ticket, int* __restrict__ flag
         if (tid == 0) {
             const long long t0 = clock64();
             int v;
-            while ((v = flag_acquire(fl + J)) == 0)
+            while ((v = flag_poll(fl + J)) == 0)
                 if (clock64() - t0 > WAIT_CYCLES) break;
+            fence_acquire_gpu();
             if (v <= 0) {
                 sh_bad = 1;
                 if (v == 0) latch_error(a.st, PICHOL_ERR_TIMEOUT, f, I, J);
@@ -170,15 +186,37 @@ k_solve_wave(const SolveArgs a, int* __restrict__ ticket, int* __restrict__ flag
             bad = true;
             break;
         }
-        // the block, from L2 (written by another CTA)
-        for (int e = tid; e < TB * c; e += WT) Zs[e / c][e % c] = __ldcg(zsrc + sysb + (int64_t)J * TB * c + e);
+        // the block, from L2 (written by another CTA), all loads in flight at once
+        {
+            const float* zb = zsrc + sysb + (int64_t)J * TB * c;
+            constexpr int NV = (TB * NJ * 4 + 4 * WT - 1) / (4 * WT);
+            constexpr int NS = (TB * NJ * 4 + WT - 1) / WT;
+            if (zvec) {
+                const int nv = TB * c / 4;
+                float4 zv[NV];
+#pragma unroll
+                for (int u = 0; u < NV; ++u)
+                    if (tid + WT * u < nv) zv[u] = __ldcg(reinterpret_cast<const float4*>(zb) + tid + WT * u);
+#pragma unroll
+                for (int u = 0; u < NV; ++u)
+                    if (tid + WT * u < nv) reinterpret_cast<float4*>(Zs)[tid + WT * u] = zv[u];
+            } else {
+                float zv[NS];
+#pragma unroll
+                for (int u = 0; u < NS; ++u)
+                    if (tid + WT * u < TB * c) zv[u] = __ldcg(zb + tid + WT * u);
+#pragma unroll
+                for (int u = 0; u < NS; ++u)
+                    if (tid + WT * u < TB * c) Zs[tid + WT * u] = zv[u];
+            }
+        }
         __syncthreads();
 #pragma unroll 8
         for (int k = 0; k < TB; ++k) {
             const float lv = Ls[r][k];
 #pragma unroll
-            for (int j = 0; j < WNJ; ++j)
-                if (g + 4 * j < c) acc[j] = fmaf(lv, Zs[k][g + 4 * j], acc[j]);
+            for (int j = 0; j < NJ; ++j)
+                if (g + 4 * j < c) acc[j] = fmaf(lv, Zs[k * c + g + 4 * j], acc[j]);
         }
         __syncthreads();                             // Ls and Zs are refilled next
         if (jj + 1 < nj) {
@@ -191,26 +229,38 @@ k_solve_wave(const SolveArgs a, int* __restrict__ ticket, int* __restrict__ flag
     if (!bad) {
         // R = rhs_I - acc (rows of this tile row), then the diagonal inverse
 #pragma unroll
-        for (int j = 0; j < WNJ; ++j)
-            if (g + 4 * j < c) Zs[r][g + 4 * j] = bv[j] - acc[j];
+        for (int j = 0; j < NJ; ++j)
+            if (g + 4 * j < c) Zs[r * c + g + 4 * j] = bv[j] - acc[j];
         __syncthreads();
-        float x[WNJ];
+        float x[NJ];
 #pragma unroll
-        for (int j = 0; j < WNJ; ++j) x[j] = 0.0f;
+        for (int j = 0; j < NJ; ++j) x[j] = 0.0f;
 #pragma unroll 8
         for (int k = 0; k < TB; ++k) {
             const float lv = Ds[r][k];
 #pragma unroll
-            for (int j = 0; j < WNJ; ++j)
-                if (g + 4 * j < c) x[j] = fmaf(lv, Zs[k][g + 4 * j], x[j]);
+            for (int j = 0; j < NJ; ++j)
+                if (g + 4 * j < c) x[j] = fmaf(lv, Zs[k * c + g + 4 * j], x[j]);
         }
 #pragma unroll
-        for (int j = 0; j < WNJ; ++j)
+        for (int j = 0; j < NJ; ++j)
             if (g + 4 * j < c) dst[sysb + row * c + g + 4 * j] = x[j];
-        __threadfence();
     }
-    __syncthreads();
+    __syncthreads();                                 // every output stored before the release
     if (tid == 0) flag_release(fl + I, bad ? -1 : 1);
+}
+
+template <int NJ>
+static void launch_wave_nj(bool exact, dim3 grid, cudaStream_t s, const SolveArgs& sa, int* ticket, int* flags,
+                           size_t nflags)
+{
+    if (exact) {
+        k_solve_wave<true, 0, NJ><<<grid, WT, 0, s>>>(sa, ticket, flags);
+        k_solve_wave<true, 1, NJ><<<grid, WT, 0, s>>>(sa, ticket + 1, flags + nflags);
+    } else {
+        k_solve_wave<false, 0, NJ><<<grid, WT, 0, s>>>(sa, ticket, flags);
+        k_solve_wave<false, 1, NJ><<<grid, WT, 0, s>>>(sa, ticket + 1, flags + nflags);
+    }
 }
 
 // The wavefront form applies when the systems are few (k tcount <= SMs), the
@@ -231,13 +281,9 @@ cudaError_t launch_solve_wave(pichol_ctx* ctx, const SolveArgs& sa, bool exact, 
     const dim3 grid((unsigned)(sa.tcount * ctx->nt), cf.k);
     {
         StageScope sc_(ctx, ST_SOLVE, s);
-        if (exact) {
-            k_solve_wave<true, 0><<<grid, WT, 0, s>>>(sa, ticket, flags);
-            k_solve_wave<true, 1><<<grid, WT, 0, s>>>(sa, ticket + 1, flags + nflags);
-        } else {
-            k_solve_wave<false, 0><<<grid, WT, 0, s>>>(sa, ticket, flags);
-            k_solve_wave<false, 1><<<grid, WT, 0, s>>>(sa, ticket + 1, flags + nflags);
-        }
+        if (cf.c <= 4) launch_wave_nj<1>(exact, grid, s, sa, ticket, flags, nflags);
+        else if (cf.c <= 12) launch_wave_nj<3>(exact, grid, s, sa, ticket, flags, nflags);
+        else launch_wave_nj<WNJ>(exact, grid, s, sa, ticket, flags, nflags);
     }
     ctx->launches += 2;
     return cudaGetLastError();

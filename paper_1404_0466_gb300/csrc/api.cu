@@ -99,8 +99,10 @@ size_t plan(pichol_ctx* ctx, char* base)
     ctx->Epart = (double*)take((size_t)(k * q * nt * sizeof(double)));
     ctx->E = (double*)take((size_t)(k * q * sizeof(double)));
     ctx->flags = (int*)take((size_t)(k * q * nt * sizeof(int)));
-    ctx->wave_cap = k * q * nt;
-    ctx->wave = (int*)take((size_t)((2 + 2 * ctx->wave_cap) * sizeof(int)));
+    // wavefront solve: one word of two tickets, then per pass the tagged solved
+    // blocks of up to WAVE_SYS_CAP systems (mixed mode only)
+    ctx->wave_sys = c.mode == PICHOL_MODE_MIXED ? (k * q < WAVE_SYS_CAP ? k * q : WAVE_SYS_CAP) : 0;
+    ctx->wave = ctx->wave_sys ? (unsigned long long*)take((size_t)((1 + 2 * ctx->wave_sys * dp * cc) * 8)) : nullptr;
     ctx->dmax = (float*)take((size_t)(k * q * nt * sizeof(float)));
     ctx->dmin = (float*)take((size_t)(k * q * nt * sizeof(float)));
     return off;

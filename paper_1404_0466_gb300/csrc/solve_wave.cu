@@ -15,15 +15,19 @@
 // tk / S of system tk mod S (forward rows in increasing order, backward rows in
 // decreasing order), so every block a CTA waits for belongs to a smaller
 // ticket, held by a CTA that is already running.  The wait is therefore never
-// on a CTA that has not started, whatever the number of CTAs resident.  Every
-// wait is bounded: a CTA whose wait runs out latches PICHOL_ERR_TIMEOUT and
-// publishes -1, and a CTA that sees -1 stops at once and publishes -1 too.
+// on a CTA that has not started, whatever the number of CTAs resident.
 //
-// Publication: every thread stores its outputs, the CTA meets at a barrier and
-// thread 0 stores the flag with release semantics at GPU scope; release is
-// cumulative, so the outputs the barrier ordered before it are visible to any
-// thread that acquires the flag.  The waiting thread polls with relaxed loads and
-// takes one acquire fence when it sees the flag set.
+// Publication: besides the solution itself, every solved value is written once
+// more as a 64-bit word {tag, value bits} with one relaxed GPU-scope store; the
+// word is read with one relaxed GPU-scope load, and an aligned 64-bit access is
+// single-copy atomic, so a reader that sees the tag also sees the value.  A
+// waiting CTA polls the words of the block it needs (each thread its own few,
+// all in flight at once) until every tag is set: no fence, no flag and no second
+// load lie between a value being stored and being used.  Tags: 0 not yet
+// written (the buffer is cleared before each launch), 1 valid, 2 failed.  Every
+// wait is bounded: a thread whose wait runs out latches PICHOL_ERR_TIMEOUT, and a
+// CTA that timed out or read a failed tag stops and writes its own block with the
+// failed tag, so a failure ends every dependent CTA at once.
 #include "internal.cuh"
 #include "solve_common.cuh"
 
@@ -37,40 +41,35 @@ namespace {
 constexpr int WT = 256;           // threads per CTA
 constexpr int WNP = 4;            // coefficient planes held per tile (p <= 4)
 constexpr int WNJ = 8;            // output columns per thread: c <= 32
+constexpr unsigned long long TAG_VALID = 1ull << 32, TAG_FAILED = 2ull << 32;
 
-__device__ __forceinline__ int flag_poll(const int* p)
+__device__ __forceinline__ unsigned long long word_poll(const unsigned long long* p)
 {
-    int v;
-    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];\n" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void fence_acquire_gpu()
+__device__ __forceinline__ void word_publish(unsigned long long* p, unsigned long long v)
 {
-    asm volatile("fence.acq_rel.gpu;\n" ::: "memory");
-}
-__device__ __forceinline__ void flag_release(int* p, int v)
-{
-    asm volatile("st.release.gpu.global.b32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;\n" ::"l"(p), "l"(v) : "memory");
 }
 
 }  // namespace
 
-// One (system, tile row) per CTA; `ticket` and `flags` (S x nt ints) start at zero.
-// NJ: output columns per thread (columns g, g + 4, ..: 4 NJ >= c).
+// One (system, tile row) per CTA; `ticket` and `xw` (this pass's S x dp x c
+// tagged words) start at zero.  NJ: output columns per thread (columns g, g + 4,
+// ..: 4 NJ >= c).
 template <bool EXACT, int DIR, int NJ>
 __global__ void __launch_bounds__(WT)
-k_solve_wave(const SolveArgs a, int* __restrict__ ticket, int* __restrict__ flags)
+k_solve_wave(const SolveArgs a, int* __restrict__ ticket, unsigned long long* __restrict__ xw)
 {
     __shared__ float Ls[TB][TB + 1];                  // tile applied to the solved block, as L[row][k]
     __shared__ __align__(16) float Zs[TB * NJ * 4];   // a solved block, row-major with row stride c
     __shared__ float Ds[TB][TB + 1];                  // the diagonal block's inverse (transposed backward)
-    __shared__ int sh_tk, sh_bad;
+    __shared__ int sh_tk;
     const int tid = threadIdx.x;
     const int S = (int)(a.tcount * (int64_t)gridDim.y);   // gridDim.y = k folds
-    if (tid == 0) {
-        sh_tk = atomicAdd(ticket, 1);
-        sh_bad = 0;
-    }
+    if (tid == 0) sh_tk = atomicAdd(ticket, 1);
     __syncthreads();
     const int tk = sh_tk, step = tk / S, sidx = tk % S;
     const int f = sidx / a.tcount, tloc = sidx % a.tcount, t = a.t0 + tloc;
@@ -78,12 +77,8 @@ k_solve_wave(const SolveArgs a, int* __restrict__ ticket, int* __restrict__ flag
     const int I = DIR == 0 ? step : nt - 1 - step;
     const int c = (int)a.c;
     const int np = EXACT ? 1 : a.p;
-    int* fl = flags + (int64_t)sidx * nt;
     const int64_t sysb = ((int64_t)f * a.q + t) * a.dp * a.c;
-    const float* zsrc = (const float*)(DIR == 0 ? a.zbuf : a.out);   // this pass's solved blocks
-    // a block is 64 c floats from a 256-byte multiple of the base: one 16-byte load per
-    // thread (two for c > 16) when the base is 16-byte aligned
-    const bool zvec = ((reinterpret_cast<uintptr_t>(zsrc) & 15) == 0);
+    unsigned long long* xs = xw + (int64_t)sidx * a.dp * a.c;    // this system's tagged blocks
     float* dst = (float*)(DIR == 0 ? a.zbuf : a.out);
     const float* src = (const float*)a.src;
     float w[WNP];
@@ -115,7 +110,7 @@ k_solve_wave(const SolveArgs a, int* __restrict__ ticket, int* __restrict__ flag
     float acc[NJ];
 #pragma unroll
     for (int j = 0; j < NJ; ++j) acc[j] = 0.0f;
-    // what the diagonal step needs and no flag guards, loaded first so that the step
+    // what the diagonal step needs and no wait guards, loaded first so that the step
     // after the last wait costs no memory round trip for it: the inverse (into Ds)
     // and the right-hand side of this thread's outputs (forward only; backward, the
     // forward solution, written by the previous launch)
@@ -168,49 +163,43 @@ k_solve_wave(const SolveArgs a, int* __restrict__ ticket, int* __restrict__ flag
                 else Ls[cc + q][rr] = vv[q];
             }
         }
-        // wait (bounded) until block J is solved
+        // block J: poll (bounded) this thread's words of it until every tag is set
         const int J = jof(jj);
-        if (tid == 0) {
-            const long long t0 = clock64();
-            int v;
-            while ((v = flag_poll(fl + J)) == 0)
-                if (clock64() - t0 > WAIT_CYCLES) break;
-            fence_acquire_gpu();
-            if (v <= 0) {
-                sh_bad = 1;
-                if (v == 0) latch_error(a.st, PICHOL_ERR_TIMEOUT, f, I, J);
-            }
-        }
-        __syncthreads();
-        if (sh_bad) {
-            bad = true;
-            break;
-        }
-        // the block, from L2 (written by another CTA), all loads in flight at once
         {
-            const float* zb = zsrc + sysb + (int64_t)J * TB * c;
-            constexpr int NV = (TB * NJ * 4 + 4 * WT - 1) / (4 * WT);
-            constexpr int NS = (TB * NJ * 4 + WT - 1) / WT;
-            if (zvec) {
-                const int nv = TB * c / 4;
-                float4 zv[NV];
+            const unsigned long long* xb = xs + (int64_t)J * TB * c;
+            const int nw = TB * c;
+            unsigned long long wv[NJ];
+            unsigned pend = 0;
 #pragma unroll
-                for (int u = 0; u < NV; ++u)
-                    if (tid + WT * u < nv) zv[u] = __ldcg(reinterpret_cast<const float4*>(zb) + tid + WT * u);
+            for (int u = 0; u < NJ; ++u)
+                if (tid + WT * u < nw) pend |= 1u << u;
+            const long long t0 = clock64();
+            bool timeout = false;
+            while (pend) {
 #pragma unroll
-                for (int u = 0; u < NV; ++u)
-                    if (tid + WT * u < nv) reinterpret_cast<float4*>(Zs)[tid + WT * u] = zv[u];
-            } else {
-                float zv[NS];
+                for (int u = 0; u < NJ; ++u)
+                    if (pend >> u & 1u) wv[u] = word_poll(xb + tid + WT * u);
 #pragma unroll
-                for (int u = 0; u < NS; ++u)
-                    if (tid + WT * u < TB * c) zv[u] = __ldcg(zb + tid + WT * u);
+                for (int u = 0; u < NJ; ++u)
+                    if ((pend >> u & 1u) && (wv[u] >> 32) != 0) pend &= ~(1u << u);
+                if (pend && clock64() - t0 > WAIT_CYCLES) {
+                    timeout = true;
+                    break;
+                }
+            }
+            bool mine_bad = timeout;
 #pragma unroll
-                for (int u = 0; u < NS; ++u)
-                    if (tid + WT * u < TB * c) Zs[tid + WT * u] = zv[u];
+            for (int u = 0; u < NJ; ++u)
+                if (tid + WT * u < nw) {
+                    if ((wv[u] >> 32) != 1u) mine_bad = true;
+                    Zs[tid + WT * u] = __uint_as_float((unsigned)wv[u]);
+                }
+            if (timeout) latch_error(a.st, PICHOL_ERR_TIMEOUT, f, I, J);
+            if (__syncthreads_or(mine_bad)) {
+                bad = true;
+                break;
             }
         }
-        __syncthreads();
 #pragma unroll 8
         for (int k = 0; k < TB; ++k) {
             const float lv = Ls[r][k];
@@ -226,15 +215,15 @@ k_solve_wave(const SolveArgs a, int* __restrict__ ticket, int* __restrict__ flag
                 for (int u = 0; u < 4; ++u) cur[m][u] = nxt[m][u];
         }
     }
+    float x[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) x[j] = 0.0f;
     if (!bad) {
         // R = rhs_I - acc (rows of this tile row), then the diagonal inverse
 #pragma unroll
         for (int j = 0; j < NJ; ++j)
             if (g + 4 * j < c) Zs[r * c + g + 4 * j] = bv[j] - acc[j];
         __syncthreads();
-        float x[NJ];
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) x[j] = 0.0f;
 #pragma unroll 8
         for (int k = 0; k < TB; ++k) {
             const float lv = Ds[r][k];
@@ -246,20 +235,24 @@ k_solve_wave(const SolveArgs a, int* __restrict__ ticket, int* __restrict__ flag
         for (int j = 0; j < NJ; ++j)
             if (g + 4 * j < c) dst[sysb + row * c + g + 4 * j] = x[j];
     }
-    __syncthreads();                                 // every output stored before the release
-    if (tid == 0) flag_release(fl + I, bad ? -1 : 1);
+    // publish this thread's words of block I (failed: tag 2 and no value)
+#pragma unroll
+    for (int j = 0; j < NJ; ++j)
+        if (g + 4 * j < c)
+            word_publish(xs + row * c + g + 4 * j,
+                         bad ? TAG_FAILED : (TAG_VALID | (unsigned long long)__float_as_uint(x[j])));
 }
 
 template <int NJ>
-static void launch_wave_nj(bool exact, dim3 grid, cudaStream_t s, const SolveArgs& sa, int* ticket, int* flags,
-                           size_t nflags)
+static void launch_wave_nj(bool exact, dim3 grid, cudaStream_t s, const SolveArgs& sa, int* ticket,
+                           unsigned long long* xw, size_t nwords)
 {
     if (exact) {
-        k_solve_wave<true, 0, NJ><<<grid, WT, 0, s>>>(sa, ticket, flags);
-        k_solve_wave<true, 1, NJ><<<grid, WT, 0, s>>>(sa, ticket + 1, flags + nflags);
+        k_solve_wave<true, 0, NJ><<<grid, WT, 0, s>>>(sa, ticket, xw);
+        k_solve_wave<true, 1, NJ><<<grid, WT, 0, s>>>(sa, ticket + 1, xw + nwords);
     } else {
-        k_solve_wave<false, 0, NJ><<<grid, WT, 0, s>>>(sa, ticket, flags);
-        k_solve_wave<false, 1, NJ><<<grid, WT, 0, s>>>(sa, ticket + 1, flags + nflags);
+        k_solve_wave<false, 0, NJ><<<grid, WT, 0, s>>>(sa, ticket, xw);
+        k_solve_wave<false, 1, NJ><<<grid, WT, 0, s>>>(sa, ticket + 1, xw + nwords);
     }
 }
 
@@ -271,19 +264,19 @@ cudaError_t launch_solve_wave(pichol_ctx* ctx, const SolveArgs& sa, bool exact, 
     const pichol_config& cf = ctx->cfg;
     const int S = cf.k * sa.tcount;
     if (cf.mode != PICHOL_MODE_MIXED || !ctx->wave || (!exact && ctx->p > WNP) || cf.c > 4 * WNJ ||
-        S > ctx->nsm || (int64_t)S * ctx->nt > ctx->wave_cap)
+        S > ctx->nsm || S > ctx->wave_sys)
         return cudaErrorNotSupported;
-    const size_t nflags = (size_t)S * ctx->nt;
-    int* ticket = ctx->wave;            // [2] tickets, then [2][S][nt] flags
-    int* flags = ctx->wave + 2;
-    cudaError_t e = cudaMemsetAsync(ctx->wave, 0, (2 + 2 * nflags) * sizeof(int), s);
+    const size_t nwords = (size_t)S * ctx->dp * cf.c;
+    int* ticket = reinterpret_cast<int*>(ctx->wave);   // word 0: two tickets; then [2][S][dp][c] words
+    unsigned long long* xw = ctx->wave + 1;
+    cudaError_t e = cudaMemsetAsync(ctx->wave, 0, (1 + 2 * nwords) * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)(sa.tcount * ctx->nt), cf.k);
     {
         StageScope sc_(ctx, ST_SOLVE, s);
-        if (cf.c <= 4) launch_wave_nj<1>(exact, grid, s, sa, ticket, flags, nflags);
-        else if (cf.c <= 12) launch_wave_nj<3>(exact, grid, s, sa, ticket, flags, nflags);
-        else launch_wave_nj<WNJ>(exact, grid, s, sa, ticket, flags, nflags);
+        if (cf.c <= 4) launch_wave_nj<1>(exact, grid, s, sa, ticket, xw, nwords);
+        else if (cf.c <= 12) launch_wave_nj<3>(exact, grid, s, sa, ticket, xw, nwords);
+        else launch_wave_nj<WNJ>(exact, grid, s, sa, ticket, xw, nwords);
     }
     ctx->launches += 2;
     return cudaGetLastError();

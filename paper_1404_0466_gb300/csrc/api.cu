@@ -99,10 +99,10 @@ size_t plan(pichol_ctx* ctx, char* base)
     ctx->Epart = (double*)take((size_t)(k * q * nt * sizeof(double)));
     ctx->E = (double*)take((size_t)(k * q * sizeof(double)));
     ctx->flags = (int*)take((size_t)(k * q * nt * sizeof(int)));
-    // wavefront solve: one word of two tickets, then per pass the tagged solved
-    // blocks of up to WAVE_SYS_CAP systems (mixed mode only)
+    // wavefront solve: two tickets (in a 256-byte head), then per pass the exchanged
+    // solved blocks of up to WAVE_SYS_CAP systems (mixed mode only)
     ctx->wave_sys = c.mode == PICHOL_MODE_MIXED ? (k * q < WAVE_SYS_CAP ? k * q : WAVE_SYS_CAP) : 0;
-    ctx->wave = ctx->wave_sys ? (unsigned long long*)take((size_t)((1 + 2 * ctx->wave_sys * dp * cc) * 8)) : nullptr;
+    ctx->wave = ctx->wave_sys ? (int*)take((size_t)(WAVE_HEAD_INTS * 4 + 2 * ctx->wave_sys * dp * cc * 4)) : nullptr;
     ctx->dmax = (float*)take((size_t)(k * q * nt * sizeof(float)));
     ctx->dmin = (float*)take((size_t)(k * q * nt * sizeof(float)));
     return off;

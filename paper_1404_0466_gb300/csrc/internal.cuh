@@ -33,6 +33,7 @@ constexpr int MAX_G = 32;                // sampled lambdas
 constexpr int MAX_K = 64;                // folds
 constexpr int GRAD_CHUNKS = 8;           // chunks of a tile row in the gradient's triangular products
 constexpr int64_t WAVE_SYS_CAP = 160;    // systems of one wavefront solve (at least the SM count)
+constexpr int WAVE_HEAD_INTS = 64;       // the wavefront buffer's head (tickets), 256 bytes
 // Debug build (-DPICHOL_DEBUG): every workspace section is followed by a guard
 // band of GUARD_BYTES filled with GUARD_FILL when the workspace is attached;
 // pichol_get_info checks them and reports a write past a section's end.
@@ -243,7 +244,7 @@ struct pichol_ctx {
     double* Epart;       // k x q x nt
     double* E;           // k x q
     int* flags;          // k x q x nt (per-tile diagonal checks: bit0 nonpositive)
-    unsigned long long* wave;   // wavefront solve: 2 tickets, then 2 x wave_sys x dp x c tagged values
+    int* wave;                  // wavefront solve: 2 tickets, then (at WAVE_HEAD_INTS) 2 x wave_sys x dp x c values
     int64_t wave_sys;           // systems the wavefront buffer holds: min(k q, WAVE_SYS_CAP)
     float* dmax;         // k x q x nt max |diag| of the tile
     float* dmin;         // k x q x nt min |diag| of the tile

@@ -18,16 +18,17 @@
 // on a CTA that has not started, whatever the number of CTAs resident.
 //
 // Publication: besides the solution itself, every solved value is written once
-// more as a 64-bit word {tag, value bits} with one relaxed GPU-scope store; the
-// word is read with one relaxed GPU-scope load, and an aligned 64-bit access is
-// single-copy atomic, so a reader that sees the tag also sees the value.  A
-// waiting CTA polls the words of the block it needs (each thread its own few,
-// all in flight at once) until every tag is set: no fence, no flag and no second
-// load lie between a value being stored and being used.  Tags: 0 not yet
-// written (the buffer is cleared before each launch), 1 valid, 2 failed.  Every
-// wait is bounded: a thread whose wait runs out latches PICHOL_ERR_TIMEOUT, and a
-// CTA that timed out or read a failed tag stops and writes its own block with the
-// failed tag, so a failure ends every dependent CTA at once.
+// more into an exchange buffer with a relaxed GPU-scope store; the buffer is
+// filled with the bit pattern NOT_READY (a NaN that arithmetic never produces:
+// the GPU's computed NaN is 0x7fffffff, and a value with either reserved pattern
+// is stored as that NaN) before each launch.  A waiting CTA polls the block it
+// needs with relaxed GPU-scope 16-byte loads (each element an aligned 32-bit
+// access, single-copy atomic, so an element that is not NOT_READY is the value
+// itself) until no element reads NOT_READY: no fence, no flag and no second load
+// lie between a value being stored and being used.  Every wait is bounded: a
+// thread whose wait runs out latches PICHOL_ERR_TIMEOUT, and a CTA that timed out
+// or read the pattern FAILED stops and writes its own block as FAILED, so a
+// failure ends every dependent CTA at once.
 #include "internal.cuh"
 #include "solve_common.cuh"
 
@@ -41,31 +42,90 @@ namespace {
 constexpr int WT = 256;           // threads per CTA
 constexpr int WNP = 4;            // coefficient planes held per tile (p <= 4)
 constexpr int WNJ = 8;            // output columns per thread: c <= 32
-constexpr unsigned long long TAG_VALID = 1ull << 32, TAG_FAILED = 2ull << 32;
+constexpr int LSS = TB + 4;        // row stride of the staged tiles: 16-byte rows, 8 rows on distinct banks
+constexpr unsigned NOT_READY = 0xffffffffu, FAILED = 0xfffffffeu;   // the buffer's fill: bytes 0xff
 
-__device__ __forceinline__ unsigned long long word_poll(const unsigned long long* p)
+__device__ __forceinline__ uint4 block_poll(const unsigned* p)
 {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];\n" : "=l"(v) : "l"(p) : "memory");
+    uint4 v;
+    asm volatile("ld.relaxed.gpu.global.v4.b32 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p)
+                 : "memory");
     return v;
 }
-__device__ __forceinline__ void word_publish(unsigned long long* p, unsigned long long v)
+__device__ __forceinline__ void value_publish(unsigned* p, unsigned v)
 {
-    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;\n" ::"l"(p), "l"(v) : "memory");
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
 }
 
 }  // namespace
 
-// One (system, tile row) per CTA; `ticket` and `xw` (this pass's S x dp x c
-// tagged words) start at zero.  NJ: output columns per thread (columns g, g + 4,
+// NJ values from shared memory at p (16-byte aligned when NJ is a multiple of 4)
+template <int NJ>
+__device__ __forceinline__ void lds_cols(const float* p, float (&z)[NJ])
+{
+    if constexpr (NJ % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < NJ; j += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(p + j);
+            z[j] = v.x;
+            z[j + 1] = v.y;
+            z[j + 2] = v.z;
+            z[j + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) z[j] = p[j];
+    }
+}
+
+// acc[j] += sum_k A(r, k) Z[k][j] over the 64 k of a staged tile, A = the tile
+// forward and its transpose backward; z points at this thread's columns of row 0
+// of the staged block.  The k order is ascending in both directions.
+template <int DIR, int NJ, int NJP>
+__device__ __forceinline__ void apply_tile(const float* Ts, const float* z, int r, float (&acc)[NJ])
+{
+#pragma unroll 4
+    for (int k0 = 0; k0 < TB; k0 += 4) {
+        float l4[4];
+        if constexpr (DIR == 0) {
+            const float4 v = *reinterpret_cast<const float4*>(Ts + r * LSS + k0);
+            l4[0] = v.x;
+            l4[1] = v.y;
+            l4[2] = v.z;
+            l4[3] = v.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) l4[q] = Ts[(k0 + q) * LSS + r];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float zv[NJP];
+            lds_cols<NJP>(z + (k0 + q) * 4 * NJP, zv);
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) acc[j] = fmaf(l4[q], zv[j], acc[j]);
+        }
+    }
+}
+
+// One (system, tile row) per CTA; `ticket` starts at zero and `xw` (this pass's
+// S x dp x c exchange values) at NOT_READY.  NJ: output columns per thread (columns g, g + 4,
 // ..: 4 NJ >= c).
+//
+// Shared memory: the tile and the diagonal inverse as stored (row-major, row
+// stride LSS), read as L[r][k] forward and as L[k][r] (the transpose) backward;
+// the solved block as [k][g][NJP], so that a thread's columns g + 4 j of one row
+// k are adjacent (one 16-byte read for NJ = 3).
 template <bool EXACT, int DIR, int NJ>
 __global__ void __launch_bounds__(WT)
-k_solve_wave(const SolveArgs a, int* __restrict__ ticket, unsigned long long* __restrict__ xw)
+k_solve_wave(const SolveArgs a, int* __restrict__ ticket, unsigned* __restrict__ xw)
 {
-    __shared__ float Ls[TB][TB + 1];                  // tile applied to the solved block, as L[row][k]
-    __shared__ __align__(16) float Zs[TB * NJ * 4];   // a solved block, row-major with row stride c
-    __shared__ float Ds[TB][TB + 1];                  // the diagonal block's inverse (transposed backward)
+    constexpr int NJP = NJ == 1 ? 1 : (NJ + 3) / 4 * 4;   // padded columns per thread
+    constexpr int ZR = 4 * NJP;                            // floats per row of the staged block
+    __shared__ __align__(16) float Ls[TB * LSS];           // the tile applied to the solved block
+    __shared__ __align__(16) float Zs[TB * ZR];            // a solved block, [k][g][j]
+    __shared__ __align__(16) float Ds[TB * LSS];           // the diagonal block's inverse
     __shared__ int sh_tk;
     const int tid = threadIdx.x;
     const int S = (int)(a.tcount * (int64_t)gridDim.y);   // gridDim.y = k folds
@@ -78,7 +138,7 @@ k_solve_wave(const SolveArgs a, int* __restrict__ ticket, unsigned long long* __
     const int c = (int)a.c;
     const int np = EXACT ? 1 : a.p;
     const int64_t sysb = ((int64_t)f * a.q + t) * a.dp * a.c;
-    unsigned long long* xs = xw + (int64_t)sidx * a.dp * a.c;    // this system's tagged blocks
+    unsigned* xs = xw + (int64_t)sidx * a.dp * a.c;    // this system's exchanged blocks
     float* dst = (float*)(DIR == 0 ? a.zbuf : a.out);
     const float* src = (const float*)a.src;
     float w[WNP];
@@ -116,13 +176,28 @@ k_solve_wave(const SolveArgs a, int* __restrict__ ticket, unsigned long long* __
     // forward solution, written by the previous launch)
     const int64_t row = (int64_t)I * TB + r;
     {
-        const float* dv = (const float*)a.dinv + (((int64_t)f * a.q + t) * nt + I) * TILE_ELEMS;
-        for (int e = tid; e < TILE_ELEMS; e += WT) {
-            const float x = dv[e];
-            if (DIR == 0) Ds[e / TB][e % TB] = x;
-            else Ds[e % TB][e / TB] = x;
+        const float4* dv = reinterpret_cast<const float4*>((const float*)a.dinv +
+                                                           (((int64_t)f * a.q + t) * nt + I) * TILE_ELEMS);
+        float4 dq[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) dq[u] = dv[tid + WT * u];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = 4 * (tid + WT * u);
+            *reinterpret_cast<float4*>(&Ds[(e / TB) * LSS + e % TB]) = dq[u];
         }
     }
+    // a block is 64 c values, 16 c groups of four; this thread polls groups tid + WT u,
+    // and value e of the block, (row k, column o), goes to Zs[k][o & 3][o >> 2]
+    constexpr int NV = (NJ + 3) / 4;
+    int zdst[NV][4];
+#pragma unroll
+    for (int u = 0; u < NV; ++u)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int e = 4 * (tid + WT * u) + i, k = e / c, o = e - k * c;
+            zdst[u][i] = k * ZR + (o & 3) * NJP + (o >> 2);
+        }
     float bv[NJ];
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
@@ -140,8 +215,8 @@ k_solve_wave(const SolveArgs a, int* __restrict__ ticket, unsigned long long* __
     if (nj > 0) fetch(cur, 0);
     for (int jj = 0; jj < nj; ++jj) {
         if (jj + 1 < nj) fetch(nxt, jj + 1);       // in flight while this tile is applied
-        // evaluate L~ = Theta_0 + sum_m phi_m Theta_m (phi_0 = 1) into Ls, transposed for
-        // the backward pass (which applies L~_ji^T)
+        // evaluate L~ = Theta_0 + sum_m phi_m Theta_m (phi_0 = 1) into Ls (the backward
+        // pass applies its transpose)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             float4 v = cur[0][u];
@@ -155,33 +230,30 @@ k_solve_wave(const SolveArgs a, int* __restrict__ ticket, unsigned long long* __
                         v.w = fmaf(w[m], cur[m][u].w, v.w);
                     }
             }
-            const int e = 4 * (tid + WT * u), rr = e / TB, cc = e % TB;
-            const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (DIR == 0) Ls[rr][cc + q] = vv[q];
-                else Ls[cc + q][rr] = vv[q];
-            }
+            const int e = 4 * (tid + WT * u);
+            *reinterpret_cast<float4*>(&Ls[(e / TB) * LSS + e % TB]) = v;
         }
-        // block J: poll (bounded) this thread's words of it until every tag is set
+        // block J: poll (bounded) this thread's groups of it until none reads NOT_READY
         const int J = jof(jj);
         {
-            const unsigned long long* xb = xs + (int64_t)J * TB * c;
-            const int nw = TB * c;
-            unsigned long long wv[NJ];
+            const unsigned* xb = xs + (int64_t)J * TB * c;
+            const int ng = 16 * c;
+            uint4 wv[NV];
             unsigned pend = 0;
 #pragma unroll
-            for (int u = 0; u < NJ; ++u)
-                if (tid + WT * u < nw) pend |= 1u << u;
+            for (int u = 0; u < NV; ++u)
+                if (tid + WT * u < ng) pend |= 1u << u;
             const long long t0 = clock64();
             bool timeout = false;
             while (pend) {
 #pragma unroll
-                for (int u = 0; u < NJ; ++u)
-                    if (pend >> u & 1u) wv[u] = word_poll(xb + tid + WT * u);
+                for (int u = 0; u < NV; ++u)
+                    if (pend >> u & 1u) wv[u] = block_poll(xb + 4 * (tid + WT * u));
 #pragma unroll
-                for (int u = 0; u < NJ; ++u)
-                    if ((pend >> u & 1u) && (wv[u] >> 32) != 0) pend &= ~(1u << u);
+                for (int u = 0; u < NV; ++u)
+                    if ((pend >> u & 1u) && wv[u].x != NOT_READY && wv[u].y != NOT_READY && wv[u].z != NOT_READY &&
+                        wv[u].w != NOT_READY)
+                        pend &= ~(1u << u);
                 if (pend && clock64() - t0 > WAIT_CYCLES) {
                     timeout = true;
                     break;
@@ -189,10 +261,14 @@ k_solve_wave(const SolveArgs a, int* __restrict__ ticket, unsigned long long* __
             }
             bool mine_bad = timeout;
 #pragma unroll
-            for (int u = 0; u < NJ; ++u)
-                if (tid + WT * u < nw) {
-                    if ((wv[u] >> 32) != 1u) mine_bad = true;
-                    Zs[tid + WT * u] = __uint_as_float((unsigned)wv[u]);
+            for (int u = 0; u < NV; ++u)
+                if (tid + WT * u < ng) {
+                    const unsigned vv[4] = {wv[u].x, wv[u].y, wv[u].z, wv[u].w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (vv[i] >= FAILED) mine_bad = true;
+                        Zs[zdst[u][i]] = __uint_as_float(vv[i]);
+                    }
                 }
             if (timeout) latch_error(a.st, PICHOL_ERR_TIMEOUT, f, I, J);
             if (__syncthreads_or(mine_bad)) {
@@ -200,13 +276,7 @@ k_solve_wave(const SolveArgs a, int* __restrict__ ticket, unsigned long long* __
                 break;
             }
         }
-#pragma unroll 8
-        for (int k = 0; k < TB; ++k) {
-            const float lv = Ls[r][k];
-#pragma unroll
-            for (int j = 0; j < NJ; ++j)
-                if (g + 4 * j < c) acc[j] = fmaf(lv, Zs[k * c + g + 4 * j], acc[j]);
-        }
+        apply_tile<DIR, NJ, NJP>(Ls, Zs + g * NJP, r, acc);
         __syncthreads();                             // Ls and Zs are refilled next
         if (jj + 1 < nj) {
 #pragma unroll
@@ -221,38 +291,33 @@ k_solve_wave(const SolveArgs a, int* __restrict__ ticket, unsigned long long* __
     if (!bad) {
         // R = rhs_I - acc (rows of this tile row), then the diagonal inverse
 #pragma unroll
-        for (int j = 0; j < NJ; ++j)
-            if (g + 4 * j < c) Zs[r * c + g + 4 * j] = bv[j] - acc[j];
+        for (int j = 0; j < NJP; ++j) Zs[r * ZR + g * NJP + j] = j < NJ ? bv[j] - acc[j] : 0.0f;
         __syncthreads();
-#pragma unroll 8
-        for (int k = 0; k < TB; ++k) {
-            const float lv = Ds[r][k];
-#pragma unroll
-            for (int j = 0; j < NJ; ++j)
-                if (g + 4 * j < c) x[j] = fmaf(lv, Zs[k * c + g + 4 * j], x[j]);
-        }
+        apply_tile<DIR, NJ, NJP>(Ds, Zs + g * NJP, r, x);
 #pragma unroll
         for (int j = 0; j < NJ; ++j)
             if (g + 4 * j < c) dst[sysb + row * c + g + 4 * j] = x[j];
     }
-    // publish this thread's words of block I (failed: tag 2 and no value)
+    // publish this thread's values of block I (FAILED when the CTA stopped)
 #pragma unroll
     for (int j = 0; j < NJ; ++j)
-        if (g + 4 * j < c)
-            word_publish(xs + row * c + g + 4 * j,
-                         bad ? TAG_FAILED : (TAG_VALID | (unsigned long long)__float_as_uint(x[j])));
+        if (g + 4 * j < c) {
+            unsigned v = __float_as_uint(x[j]);
+            if (v >= FAILED) v = 0x7fffffffu;       // a value never reads as a reserved pattern
+            value_publish(xs + row * c + g + 4 * j, bad ? FAILED : v);
+        }
 }
 
 template <int NJ>
 static void launch_wave_nj(bool exact, dim3 grid, cudaStream_t s, const SolveArgs& sa, int* ticket,
-                           unsigned long long* xw, size_t nwords)
+                           unsigned* xw, size_t nvals)
 {
     if (exact) {
         k_solve_wave<true, 0, NJ><<<grid, WT, 0, s>>>(sa, ticket, xw);
-        k_solve_wave<true, 1, NJ><<<grid, WT, 0, s>>>(sa, ticket + 1, xw + nwords);
+        k_solve_wave<true, 1, NJ><<<grid, WT, 0, s>>>(sa, ticket + 1, xw + nvals);
     } else {
         k_solve_wave<false, 0, NJ><<<grid, WT, 0, s>>>(sa, ticket, xw);
-        k_solve_wave<false, 1, NJ><<<grid, WT, 0, s>>>(sa, ticket + 1, xw + nwords);
+        k_solve_wave<false, 1, NJ><<<grid, WT, 0, s>>>(sa, ticket + 1, xw + nvals);
     }
 }
 
@@ -266,17 +331,18 @@ cudaError_t launch_solve_wave(pichol_ctx* ctx, const SolveArgs& sa, bool exact, 
     if (cf.mode != PICHOL_MODE_MIXED || !ctx->wave || (!exact && ctx->p > WNP) || cf.c > 4 * WNJ ||
         S > ctx->nsm || S > ctx->wave_sys)
         return cudaErrorNotSupported;
-    const size_t nwords = (size_t)S * ctx->dp * cf.c;
-    int* ticket = reinterpret_cast<int*>(ctx->wave);   // word 0: two tickets; then [2][S][dp][c] words
-    unsigned long long* xw = ctx->wave + 1;
-    cudaError_t e = cudaMemsetAsync(ctx->wave, 0, (1 + 2 * nwords) * sizeof(unsigned long long), s);
+    const size_t nvals = (size_t)S * ctx->dp * cf.c;
+    int* ticket = ctx->wave;                           // two tickets, then (at 256 bytes) [2][S][dp][c] values
+    unsigned* xw = reinterpret_cast<unsigned*>(ctx->wave + WAVE_HEAD_INTS);
+    cudaError_t e = cudaMemsetAsync(ticket, 0, 2 * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(xw, 0xff, 2 * nvals * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)(sa.tcount * ctx->nt), cf.k);
     {
         StageScope sc_(ctx, ST_SOLVE, s);
-        if (cf.c <= 4) launch_wave_nj<1>(exact, grid, s, sa, ticket, xw, nwords);
-        else if (cf.c <= 12) launch_wave_nj<3>(exact, grid, s, sa, ticket, xw, nwords);
-        else launch_wave_nj<WNJ>(exact, grid, s, sa, ticket, xw, nwords);
+        if (cf.c <= 4) launch_wave_nj<1>(exact, grid, s, sa, ticket, xw, nvals);
+        else if (cf.c <= 12) launch_wave_nj<3>(exact, grid, s, sa, ticket, xw, nvals);
+        else launch_wave_nj<WNJ>(exact, grid, s, sa, ticket, xw, nvals);
     }
     ctx->launches += 2;
     return cudaGetLastError();

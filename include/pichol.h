@@ -359,6 +359,19 @@ PICHOL_API pichol_status pichol_clear_status(pichol_ctx* ctx, void* stream);
  * context is usable as before.  For tests of failure detection. */
 PICHOL_API pichol_status pichol_check_timeout(pichol_ctx* ctx, int64_t cycles, void* stream);
 
+/* Exercises the error path of the wavefront solve's waits on blocks solved by
+ * other CTAs of the same launch (the few-system interpolated solves, Sec. 3.2
+ * and 3.3): enqueues one forward pass over the hold-out gradient's buffers, one
+ * system per fold, whose first tile row is never scheduled.  Every CTA waits for
+ * block 0 until `cycles` SM clocks (1 .. 2^34) run out, latches
+ * PICHOL_ERR_TIMEOUT (fold, the waiting tile row >= 1, pivot 0: the block it
+ * waited for), publishes its block as failed and returns; nothing faults or
+ * hangs, no result of the context is written, and after pichol_clear_status the
+ * context is usable as before.  PICHOL_ERR_UNSUPPORTED where the wavefront does
+ * not apply (FP64 mode, r > 3, c > 32, d <= 64, more folds than SMs);
+ * PICHOL_ERR_WORKSPACE without a workspace.  For tests of failure detection. */
+PICHOL_API pichol_status pichol_check_wave_timeout(pichol_ctx* ctx, int64_t cycles, void* stream);
+
 /* Accuracy check of the double-precision 1/sqrt used for the pivots of the
  * diagonal tiles (a float seed refined by one third-order step, see chol.cu):
  * writes to *max_rel_err (device, one double) the largest relative difference

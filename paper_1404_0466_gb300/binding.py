@@ -47,6 +47,7 @@ EXPORTS = [
     "pichol_batch_run", "pichol_batch_get_info", "pichol_batch_launch_count", "pichol_batch_destroy",
     "pichol_batch_set_timing", "pichol_batch_stage_times",
     "pichol_get_tuning", "pichol_set_tuning", "pichol_batch_set_tuning", "pichol_check_timeout",
+    "pichol_check_wave_timeout",
     "pichol_mchol", "pichol_mchol_levels", "pichol_check_rsqrt", "pichol_eval_pinrmse", "pichol_probe_fma", "pichol_probe_mma",
     "pichol_get_state", "pichol_resume", "pichol_version", "pichol_debug_guards", "pichol_debug_build",
 ]
@@ -138,6 +139,7 @@ def lib():
         "pichol_batch_set_timing": ([vp, i32], ctypes.c_int),
         "pichol_get_tuning": ([vp, ctypes.POINTER(Tuning)], ctypes.c_int),
         "pichol_check_timeout": ([vp, i64, vp], ctypes.c_int),
+        "pichol_check_wave_timeout": ([vp, i64, vp], ctypes.c_int),
         "pichol_set_tuning": ([vp, ctypes.POINTER(Tuning)], ctypes.c_int),
         "pichol_batch_set_tuning": ([vp, ctypes.POINTER(Tuning)], ctypes.c_int),
         "pichol_batch_stage_times": ([vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32,
@@ -408,6 +410,11 @@ class Context:
         """One bounded wait that runs out after `cycles` clocks (latches PICHOL_ERR_TIMEOUT)."""
         _check(lib().pichol_check_timeout(self._h, cycles, ctypes.c_void_p(_stream_ptr(stream))),
                "pichol_check_timeout")
+
+    def check_wave_timeout(self, cycles: int, stream=None):
+        """One wavefront pass whose waits run out after `cycles` clocks (latches PICHOL_ERR_TIMEOUT)."""
+        _check(lib().pichol_check_wave_timeout(self._h, cycles, ctypes.c_void_p(_stream_ptr(stream))),
+               "pichol_check_wave_timeout")
 
     def clear_status(self, stream=None):
         _check(lib().pichol_clear_status(self._h, ctypes.c_void_p(_stream_ptr(stream))), "pichol_clear_status")

@@ -550,6 +550,15 @@ pichol_status pichol_check_timeout(pichol_ctx* ctx, int64_t cycles, void* stream
     return cuda_status(launch_wait_check(ctx, (long long)cycles, (cudaStream_t)stream));
 }
 
+pichol_status pichol_check_wave_timeout(pichol_ctx* ctx, int64_t cycles, void* stream)
+{
+    if (!ctx || cycles < 1 || cycles > ((int64_t)1 << 34)) return PICHOL_ERR_INVALID_ARG;
+    if (!ready(ctx)) return PICHOL_ERR_WORKSPACE;
+    const cudaError_t e = launch_wave_check(ctx, (long long)cycles, (cudaStream_t)stream);
+    if (e == cudaErrorNotSupported) return PICHOL_ERR_UNSUPPORTED;
+    return cuda_status(e);
+}
+
 pichol_status pichol_get_tuning(const pichol_ctx* ctx, pichol_tuning* t)
 {
     if (!ctx || !t) return PICHOL_ERR_INVALID_ARG;

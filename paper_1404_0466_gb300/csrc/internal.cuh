@@ -320,6 +320,7 @@ cudaError_t launch_grad(pichol_ctx* ctx, double log_lam, double* E_out, double* 
 cudaError_t launch_score_tc(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s);
 cudaError_t launch_gall_split(pichol_ctx* ctx, cudaStream_t s);
 cudaError_t launch_wait_check(pichol_ctx* ctx, long long limit, cudaStream_t s);
+cudaError_t launch_wave_check(pichol_ctx* ctx, long long limit, cudaStream_t s);
 cudaError_t launch_resid_exact(pichol_ctx* ctx, int t0, int tcount, cudaStream_t s);
 // W^T of systems [t0, t0 + tcount) split into TF32 parts (Wth / Wtl)
 cudaError_t launch_split_wt(pichol_ctx* ctx, int t0, int tcount, int stage, cudaStream_t s);

@@ -110,7 +110,9 @@ __device__ __forceinline__ void apply_tile(const float* Ts, const float* z, int 
 }
 
 // One (system, tile row) per CTA; `ticket` starts at zero and `xw` (this pass's
-// S x dp x c exchange values) at NOT_READY.  NJ: output columns per thread (columns g, g + 4,
+// S x dp x c exchange values) at NOT_READY.  Tickets are numbered from tk0 (0,
+// except in the wait check, which leaves out the first row step); `wait` is the
+// limit of one wait in SM clocks.  NJ: output columns per thread (columns g, g + 4,
 // ..: 4 NJ >= c).
 //
 // Shared memory: the tile and the diagonal inverse as stored (row-major, row
@@ -119,7 +121,7 @@ __device__ __forceinline__ void apply_tile(const float* Ts, const float* z, int 
 // k are adjacent (one 16-byte read for NJ = 3).
 template <bool EXACT, int DIR, int NJ>
 __global__ void __launch_bounds__(WT)
-k_solve_wave(const SolveArgs a, int* __restrict__ ticket, unsigned* __restrict__ xw)
+k_solve_wave(const SolveArgs a, int* __restrict__ ticket, unsigned* __restrict__ xw, int tk0, long long wait)
 {
     constexpr int NJP = NJ == 1 ? 1 : (NJ + 3) / 4 * 4;   // padded columns per thread
     constexpr int ZR = 4 * NJP;                            // floats per row of the staged block
@@ -129,7 +131,7 @@ k_solve_wave(const SolveArgs a, int* __restrict__ ticket, unsigned* __restrict__
     __shared__ int sh_tk;
     const int tid = threadIdx.x;
     const int S = (int)(a.tcount * (int64_t)gridDim.y);   // gridDim.y = k folds
-    if (tid == 0) sh_tk = atomicAdd(ticket, 1);
+    if (tid == 0) sh_tk = tk0 + atomicAdd(ticket, 1);
     __syncthreads();
     const int tk = sh_tk, step = tk / S, sidx = tk % S;
     const int f = sidx / a.tcount, tloc = sidx % a.tcount, t = a.t0 + tloc;
@@ -254,7 +256,7 @@ k_solve_wave(const SolveArgs a, int* __restrict__ ticket, unsigned* __restrict__
                     if ((pend >> u & 1u) && wv[u].x != NOT_READY && wv[u].y != NOT_READY && wv[u].z != NOT_READY &&
                         wv[u].w != NOT_READY)
                         pend &= ~(1u << u);
-                if (pend && clock64() - t0 > WAIT_CYCLES) {
+                if (pend && clock64() - t0 > wait) {
                     timeout = true;
                     break;
                 }
@@ -313,11 +315,11 @@ static void launch_wave_nj(bool exact, dim3 grid, cudaStream_t s, const SolveArg
                            unsigned* xw, size_t nvals)
 {
     if (exact) {
-        k_solve_wave<true, 0, NJ><<<grid, WT, 0, s>>>(sa, ticket, xw);
-        k_solve_wave<true, 1, NJ><<<grid, WT, 0, s>>>(sa, ticket + 1, xw + nvals);
+        k_solve_wave<true, 0, NJ><<<grid, WT, 0, s>>>(sa, ticket, xw, 0, WAIT_CYCLES);
+        k_solve_wave<true, 1, NJ><<<grid, WT, 0, s>>>(sa, ticket + 1, xw + nvals, 0, WAIT_CYCLES);
     } else {
-        k_solve_wave<false, 0, NJ><<<grid, WT, 0, s>>>(sa, ticket, xw);
-        k_solve_wave<false, 1, NJ><<<grid, WT, 0, s>>>(sa, ticket + 1, xw + nvals);
+        k_solve_wave<false, 0, NJ><<<grid, WT, 0, s>>>(sa, ticket, xw, 0, WAIT_CYCLES);
+        k_solve_wave<false, 1, NJ><<<grid, WT, 0, s>>>(sa, ticket + 1, xw + nvals, 0, WAIT_CYCLES);
     }
 }
 
@@ -345,6 +347,53 @@ cudaError_t launch_solve_wave(pichol_ctx* ctx, const SolveArgs& sa, bool exact, 
         else launch_wave_nj<WNJ>(exact, grid, s, sa, ticket, xw, nvals);
     }
     ctx->launches += 2;
+    return cudaGetLastError();
+}
+
+// The failure path of the wavefront's waits: one forward pass over the
+// gradient's buffers (one system per fold) whose first row step is never
+// scheduled.  Block 0 is the first block every row waits for, so every CTA waits
+// until `limit` SM clocks run out, latches PICHOL_ERR_TIMEOUT (fold, its row,
+// block 0), publishes its block as FAILED and returns.  Nothing is written to
+// the solution.  cudaErrorNotSupported where the wavefront does not
+// apply (FP64 mode, p > 4, c > 32, d <= 64, or more folds than SMs).
+cudaError_t launch_wave_check(pichol_ctx* ctx, long long limit, cudaStream_t s)
+{
+    const pichol_config& cf = ctx->cfg;
+    const int S = cf.k;
+    if (cf.mode != PICHOL_MODE_MIXED || !ctx->wave || ctx->p > WNP || cf.c > 4 * WNJ || ctx->nt < 2 ||
+        S > ctx->nsm || S > ctx->wave_sys)
+        return cudaErrorNotSupported;
+    SolveArgs sa;
+    sa.src = ctx->Theta;
+    sa.dinv = ctx->gDinv;
+    sa.rhs = ctx->Btr;
+    sa.zbuf = ctx->gW;
+    sa.out = ctx->gW;
+    sa.phi = ctx->gphi;
+    sa.p = ctx->p;
+    sa.nt = ctx->nt;
+    sa.q = 1;
+    sa.t0 = 0;
+    sa.tcount = 1;
+    sa.per = 1;
+    sa.rhs_per_system = 0;
+    sa.ntiles = ctx->ntiles;
+    sa.dp = ctx->dp;
+    sa.c = cf.c;
+    sa.st = ctx->status;
+    const size_t nvals = (size_t)S * ctx->dp * cf.c;
+    int* ticket = ctx->wave;
+    unsigned* xw = reinterpret_cast<unsigned*>(ctx->wave + WAVE_HEAD_INTS);
+    cudaError_t e = cudaMemsetAsync(ticket, 0, 2 * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(xw, 0xff, nvals * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    // rows 1 .. nt-1 of every fold: tickets S .. S nt - 1
+    const dim3 grid((unsigned)(ctx->nt - 1), cf.k);
+    if (cf.c <= 4) k_solve_wave<false, 0, 1><<<grid, WT, 0, s>>>(sa, ticket, xw, S, limit);
+    else if (cf.c <= 12) k_solve_wave<false, 0, 3><<<grid, WT, 0, s>>>(sa, ticket, xw, S, limit);
+    else k_solve_wave<false, 0, WNJ><<<grid, WT, 0, s>>>(sa, ticket, xw, S, limit);
+    ctx->launches++;
     return cudaGetLastError();
 }
 

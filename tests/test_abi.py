@@ -220,6 +220,11 @@ def test_new_entry_points_check_arguments_without_a_gpu(L):
     rc, h = _create(L, _cfg(L))
     assert L.pichol_eval_pinrmse(h, None, E, None) == 1
     assert L.pichol_eval_pinrmse(h, E, E, None) == 4                 # no workspace yet
+    for check in (L.pichol_check_timeout, L.pichol_check_wave_timeout):
+        assert check(None, 1000, None) == 1
+        assert check(h, 0, None) == 1
+        assert check(h, (1 << 34) + 1, None) == 1
+        assert check(h, 1000, None) == 4                             # no workspace yet
     L.pichol_destroy(h)
     out = ctypes.c_double()
     assert L.pichol_probe_fma(2, 1024, ctypes.byref(out)) == 1

@@ -70,6 +70,39 @@ def test_mixed_gradient_matches_oracle(torch_mod):
         np.testing.assert_allclose(dE, ref.dE, rtol=1e-3, atol=1e-4 * np.abs(ref.E).max())
 
 
+def test_wavefront_wait_runs_out_and_the_context_recovers(torch_mod):
+    """The few-system solve's waits on blocks of other CTAs are bounded: a pass
+    whose first tile row never runs latches PICHOL_ERR_TIMEOUT (some fold, a
+    waiting row >= 1, block 0) without a fault or a hang, writes none of the
+    context's results, and after clearing the status the gradient is the same as
+    before."""
+    torch = torch_mod
+    prob = synth.mixed_ecc(n=2048, d=200)
+    kw = dict(k=5, g=5, r=3, q=21, basis="cheb_log")
+    ctx = _setup(torch, prob, "mixed", **kw)
+    ll = math.log(0.3 * oracle.trace_scale(prob.X))
+    E0, dE0 = (t.cpu().numpy().copy() for t in ctx.holdout_grad(ll))
+    assert ctx.info().code == 0
+    ctx.check_wave_timeout(2_000_000)
+    info = ctx.info()
+    assert info.code == 5 and 0 <= info.fold < 5 and 1 <= info.index < 4 and info.pivot == 0
+    ctx.clear_status()
+    E1, dE1 = (t.cpu().numpy() for t in ctx.holdout_grad(ll))
+    assert ctx.info().code == 0
+    np.testing.assert_allclose(E1, E0, rtol=1e-6)
+    np.testing.assert_allclose(dE1, dE0, rtol=1e-6, atol=1e-9 * np.abs(E0).max())
+
+
+def test_wavefront_wait_check_is_unsupported_in_fp64(torch_mod):
+    from paper_1404_0466_gb300 import binding
+    prob = synth.spectral_gaussian(300, 100, 2, seed=7)
+    ctx = _setup(torch_mod, prob, "fp64", k=3, g=3, r=2, q=5)
+    with pytest.raises(binding.PicholError) as err:
+        ctx.check_wave_timeout(1000)
+    assert err.value.code == 6                                       # PICHOL_ERR_UNSUPPORTED
+    assert ctx.info().code == 0
+
+
 def test_interpolated_gradient_is_close_to_exact_cholesky_gradient(torch_mod):
     """Near the sampled lambdas the polynomial follows the exact factor, so the
     gradient through it stays close to the exact-Cholesky gradient (FP64 oracle)."""
